@@ -1,0 +1,158 @@
+/* xl — GB300-native differentiable free-space optics (C ABI).
+ *
+ * The hot path of the differentiable optics simulator of XLuminA (arXiv 2310.08408): free-space
+ * propagation of sampled complex fields by scalar / vectorial Rayleigh-Sommerfeld (RS / VRS)
+ * and by the chirped z-transform (CZT / VCZT), the optical elements the optimiser tunes (SLM
+ * and super-SLM phase masks, thin lenses, polarisers, wave plates), the camera intensity and
+ * spot-size losses, the hand-written adjoints of all of them, and Adam.
+ * Paper passages: Methods, "Features and performance" (propagators, elements, camera);
+ * Methods, "Loss function"; Results and Methods on Adam.
+ *
+ * Conventions
+ *   - Time dependence exp(-i w t): outgoing waves exp(+i k r), k = 2 pi / wavelength.
+ *   - Lengths in one unit throughout (micrometres in the tests); wavelength in the same unit.
+ *   - A grid samples x_m = x0 + m dx (m < nx), y_n = y0 + n dy (n < ny).
+ *   - Complex arrays are interleaved (re, im): complex64 (XL_C64) or complex128 (XL_C128),
+ *     row-major [batch][component][ny][nx], x fastest, contiguous.
+ *   - Gradients follow g = dL/dRe u + i dL/dIm u, so dL = Re sum conj(g) du.
+ *
+ * Ownership and streams
+ *   - Every field, mask, loss and gradient pointer is caller-owned DEVICE memory unless stated.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream).
+ *   - The library owns a cache of transfer spectra and chirps keyed by (grid, wavelength, z,
+ *     window, precision) and a per-stream workspace; both grow on demand with cudaMalloc and are
+ *     released by xl_cache_clear(). Calls that would allocate must not run inside stream
+ *     capture: warm them up (same sizes) before capturing a CUDA graph.
+ *
+ * Errors
+ *   - Argument checks happen on the host before any launch and return XL_ERR_ARG or
+ *     XL_ERR_UNSUPPORTED with nothing enqueued.
+ *   - CUDA failures return XL_ERR_CUDA; allocation failures XL_ERR_NOMEM.
+ *   - xl_last_error() returns a thread-local message describing the last failure.
+ */
+#ifndef XL_H_
+#define XL_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t xl_status;
+#define XL_OK 0
+#define XL_ERR_ARG 1
+#define XL_ERR_CUDA 2
+#define XL_ERR_NOMEM 3
+#define XL_ERR_UNSUPPORTED 4
+#define XL_ERR_TIMEOUT 5
+#define XL_ERR_NONFINITE 6
+
+/* precision of fields (and of phase masks: float for XL_C64, double for XL_C128) */
+#define XL_C64 0
+#define XL_C128 1
+
+/* flags */
+#define XL_Z_DEVICE 1 /* z (and element parameters) are read from device memory at run time */
+
+/* Sampling grid: x_m = x0 + m dx, y_n = y0 + n dy. */
+typedef struct xl_grid {
+  int32_t nx, ny;
+  double dx, dy, x0, y0;
+} xl_grid;
+
+/* CZT output window: X_p = xo0 + p dxo (p < mx), Y_q = yo0 + q dyo (q < my). */
+typedef struct xl_window {
+  int32_t mx, my;
+  double dxo, dyo, xo0, yo0;
+} xl_window;
+
+/* Library version string. */
+const char* xl_version(void);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* xl_last_error(void);
+
+/* Frees every cached spectrum / chirp table and every workspace (synchronises the device). */
+xl_status xl_cache_clear(void);
+
+/* Bytes currently held by the spectrum cache and the workspaces. */
+int64_t xl_cache_bytes(void);
+
+/* ---------------------------------------------------------------------------------------------
+ * Scalar RS propagation (Methods, "Features and performance": FFT-based numerical integration of
+ * the Rayleigh-Sommerfeld integral).
+ *
+ * Discrete definition (reading: first RS integral, rectangle rule, output grid = input grid):
+ *   u_out[q][p] = sum_{n<ny, m<nx} u_in[n][m] h[p-m][q-n],
+ *   h[a][b] = (dx dy / 2 pi) z (1/r - i k) exp(i k r) / r^2,  r = sqrt((a dx)^2 + (b dy)^2 + z^2).
+ * Realisation: zero-pad to [2ny][2nx], 2D FFT, multiply by the cached 2D DFT of h placed at
+ * (a mod 2nx, b mod 2ny), inverse FFT, crop.
+ *
+ * u_in, u_out: [batch][ny][nx] complex (dtype). u_out may not alias u_in.
+ * z:           [batch] distances (> 0); host array, or device array with flags & XL_Z_DEVICE
+ *              (then the transfer spectrum is regenerated in-stream on every call).
+ * Supported:   nx, ny powers of two in [32, 4096]; batch >= 0 (0 is a no-op).
+ * -------------------------------------------------------------------------------------------*/
+xl_status xl_rs_propagate(const void* u_in, void* u_out, int32_t batch, const xl_grid* grid,
+                          double wavelength, const double* z, int32_t flags, int32_t dtype,
+                          void* stream);
+
+/* Adjoint of xl_rs_propagate (same sizes):
+ *   g_in = P^H g_out   (convolution with conj(h[-a][-b]), i.e. the spectrum conj(H)),
+ *   g_z[b] = Re sum conj(g_out) dU_out/dz   (dh/dz spectrum, Parseval in the frequency domain).
+ * g_in may be NULL (no field gradient); g_z may be NULL (no distance gradient) and needs u_in.
+ * g_z: [batch] doubles, device memory, overwritten. */
+xl_status xl_rs_propagate_backward(const void* g_out, const void* u_in, void* g_in, double* g_z,
+                                   int32_t batch, const xl_grid* grid, double wavelength,
+                                   const double* z, int32_t flags, int32_t dtype, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Vectorial RS (Methods, "Features and performance"; VRS of Ye et al., cited with RS).
+ * Reading: Ex' = h * Ex, Ey' = h * Ey, Ez' = h_x * Ex + h_y * Ey with
+ *   h_x[a][b] = -(a dx / z) h[a][b],  h_y[a][b] = -(b dy / z) h[a][b]
+ * (the divergence-free completion of the transverse RS field).
+ * exy_in: [batch][2][ny][nx]; exyz_out: [batch][3][ny][nx]. Other arguments as xl_rs_propagate.
+ * -------------------------------------------------------------------------------------------*/
+xl_status xl_vrs_propagate(const void* exy_in, void* exyz_out, int32_t batch, const xl_grid* grid,
+                           double wavelength, const double* z, int32_t flags, int32_t dtype,
+                           void* stream);
+
+/* Adjoint of xl_vrs_propagate: g_exyz [batch][3][ny][nx] -> g_exy [batch][2][ny][nx] (nullable),
+ * g_z [batch] (nullable, needs exy_in). */
+xl_status xl_vrs_propagate_backward(const void* g_exyz, const void* exy_in, void* g_exy,
+                                    double* g_z, int32_t batch, const xl_grid* grid,
+                                    double wavelength, const double* z, int32_t flags,
+                                    int32_t dtype, void* stream);
+
+
+/* ---------------------------------------------------------------------------------------------
+ * CZT propagation onto an output window (Methods, "Features and performance": the chirped
+ * z-transform, an accelerated RS variant that samples an arbitrary region of interest; Bluestein
+ * method of the cited Hu et al.).
+ * Reading: the Fresnel form of the RS integral evaluated on the window,
+ *   u_out[q][p] = exp(ikz)/(i lambda z) dx dy sum_{n,m} u_in[n][m]
+ *                 exp(i k [(X_p - x_m)^2 + (Y_q - y_n)^2] / (2 z)),
+ * realised by Bluestein chirp multiplies and padded FFT convolutions (length 2^ceil(log2(N+M-1)))
+ * separately along x and y.
+ * vectorial = 0: u_in [batch][ny][nx] -> u_out [batch][my][mx].
+ * vectorial = 1: u_in [batch][2][ny][nx] (Ex, Ey) -> u_out [batch][3][my][mx] (Ex', Ey', Ez'),
+ *   Ez' = sum [-(X_p - x_m)/z Ex - (Y_q - y_n)/z Ey] K (the VRS kernel ratio applied to CZT).
+ * Supported: any nx, ny, mx, my >= 1 with N + M - 1 <= 8192 per axis. z as in xl_rs_propagate.
+ * -------------------------------------------------------------------------------------------*/
+xl_status xl_czt_propagate(const void* u_in, void* u_out, int32_t batch, int32_t vectorial,
+                           const xl_grid* grid, const xl_window* window, double wavelength,
+                           const double* z, int32_t flags, int32_t dtype, void* stream);
+
+/* Adjoint of xl_czt_propagate: g_out [batch][1 or 3][my][mx] -> g_in [batch][1 or 2][ny][nx]
+ * (the conjugate-chirp convolutions in reverse order). */
+xl_status xl_czt_propagate_backward(const void* g_out, void* g_in, int32_t batch,
+                                    int32_t vectorial, const xl_grid* grid,
+                                    const xl_window* window, double wavelength, const double* z,
+                                    int32_t flags, int32_t dtype, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XL_H_ */

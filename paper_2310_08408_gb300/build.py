@@ -1,0 +1,83 @@
+"""Builds the C-ABI CUDA library ``_build/libxl.so`` for sm_103a (GB300) in-tree.
+
+Every ``csrc/*.cu`` is compiled by nvcc in parallel with
+``-gencode arch=compute_103a,code=sm_103a -O3 -lineinfo`` and linked into one shared library
+with the CUDA runtime linked statically, so the library has no dependency beyond the driver.
+An object is rebuilt when its source or any ``csrc`` header is newer than it.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import glob
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+OUT = os.path.join(HERE, "_build")
+LIB = os.path.join(OUT, "libxl.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+         "--expt-relaxed-constexpr"]
+
+
+def _nvcc() -> str:
+    for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: the xl CUDA library cannot be built")
+
+
+def _headers_mtime() -> float:
+    hs = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
+    hs.append(os.path.join(HERE, "..", "include", "xl.h"))
+    return max(os.path.getmtime(h) for h in hs if os.path.exists(h))
+
+
+def build(verbose: bool = False, jobs: int | None = None, ptxas_verbose: bool = False) -> str:
+    """Compile (incrementally) and link the library; returns its path."""
+    os.makedirs(OUT, exist_ok=True)
+    nvcc = _nvcc()
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    hdr = _headers_mtime()
+    todo = []
+    objs = []
+    for s in srcs:
+        o = os.path.join(OUT, os.path.basename(s)[:-3] + ".o")
+        objs.append(o)
+        if not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr):
+            todo.append((s, o))
+
+    def compile_one(so):
+        s, o = so
+        cmd = [nvcc, *ARCH, *FLAGS, "-c", s, "-o", o + ".tmp"]
+        if ptxas_verbose:
+            cmd += ["-Xptxas", "-v"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {os.path.basename(s)}:\n{r.stderr[-8000:]}")
+        os.replace(o + ".tmp", o)
+        return r.stderr
+
+    if todo:
+        n = jobs or min(len(todo), os.cpu_count() or 4)
+        with cf.ThreadPoolExecutor(max_workers=n) as ex:
+            for (s, _), log in zip(todo, ex.map(compile_one, todo)):
+                if verbose:
+                    print(f"[xl build] {os.path.basename(s)}", file=sys.stderr)
+                    if ptxas_verbose:
+                        print(log, file=sys.stderr)
+    if todo or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
+        tmp = LIB + f".tmp{os.getpid()}"
+        cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr[-8000:]}")
+        os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(verbose=True, ptxas_verbose="-v" in sys.argv))

@@ -1,0 +1,182 @@
+// C ABI of CZT / VCZT propagation onto an output window and its adjoint (host orchestration of
+// xl_czt_kernels.cuh). Methods, "Features and performance": the chirped z-transform propagates
+// onto an arbitrarily selected and sampled region of interest.
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+#include "xl_czt_launch.h"
+
+namespace xl {
+namespace {
+
+int czt_len(int n, int m) {
+  int L = 64;
+  while (L < n + m - 1) L <<= 1;
+  return L;
+}
+
+xl_status check_czt(const xl_grid* g, const xl_window* w, double wavelength, int32_t batch,
+                    const double* z, int32_t flags, int32_t dtype) {
+  if (!g || !w) return fail(XL_ERR_ARG, "grid or window is NULL");
+  if (g->nx < 1 || g->ny < 1 || w->mx < 1 || w->my < 1)
+    return fail(XL_ERR_ARG, "grid and window sizes must be positive");
+  if (g->nx + w->mx - 1 > 8192 || g->ny + w->my - 1 > 8192)
+    return fail(XL_ERR_UNSUPPORTED, "N + M - 1 must not exceed 8192 per axis");
+  if (!(g->dx > 0) || !(g->dy > 0) || !(w->dxo > 0) || !(w->dyo > 0))
+    return fail(XL_ERR_ARG, "pitches must be positive");
+  if (!std::isfinite(g->x0) || !std::isfinite(g->y0) || !std::isfinite(w->xo0) || !std::isfinite(w->yo0))
+    return fail(XL_ERR_ARG, "origins must be finite");
+  if (!(wavelength > 0) || !std::isfinite(wavelength)) return fail(XL_ERR_ARG, "bad wavelength");
+  if (batch < 0) return fail(XL_ERR_ARG, "batch < 0");
+  if (dtype != XL_C64 && dtype != XL_C128) return fail(XL_ERR_ARG, "bad dtype");
+  if (flags & ~XL_Z_DEVICE) return fail(XL_ERR_ARG, "unknown flag bits");
+  if (batch > 0 && !z) return fail(XL_ERR_ARG, "z is NULL");
+  if (batch > 0 && !(flags & XL_Z_DEVICE))
+    for (int32_t b = 0; b < batch; ++b)
+      if (!(z[b] > 0) || !std::isfinite(z[b])) return fail(XL_ERR_ARG, "z must be positive and finite");
+  return XL_OK;
+}
+
+CztTabArgs tab_args(const xl_grid* g, const xl_window* w, double wavelength) {
+  CztTabArgs a;
+  a.nx = g->nx; a.ny = g->ny; a.mx = w->mx; a.my = w->my;
+  a.Lx = czt_len(g->nx, w->mx);
+  a.Ly = czt_len(g->ny, w->my);
+  a.x0 = g->x0; a.dx = g->dx; a.y0 = g->y0; a.dy = g->dy;
+  a.xo0 = w->xo0; a.dxo = w->dxo; a.yo0 = w->yo0; a.dyo = w->dyo;
+  a.k = kTwoPi / wavelength;
+  a.lambda = wavelength;
+  a.zdev = nullptr;
+  a.zval = 0;
+  a.off_y = (int64_t)a.nx + a.mx + 2 * (int64_t)a.Lx;
+  return a;
+}
+
+int64_t tab_elems(const CztTabArgs& a) { return a.off_y + a.ny + a.my + 2 * (int64_t)a.Ly; }
+
+template <typename T>
+xl_status get_tables(const xl_grid* g, const xl_window* w, double wavelength, const double* z,
+                     int32_t flags, int32_t dtype, void* dev_tab, cudaStream_t s, const void** out) {
+  CztTabArgs a = tab_args(g, w, wavelength);
+  if (flags & XL_Z_DEVICE) {
+    a.zdev = z;
+    XL_TRY(czt_tables<T>(dev_tab, a, s));
+    *out = dev_tab;
+    return XL_OK;
+  }
+  a.zval = *z;
+  std::string key = "czt";
+  key_put(key, *g);
+  key_put(key, *w);
+  key_put(key, wavelength);
+  key_put(key, *z);
+  key_put(key, dtype);
+  void* p = nullptr;
+  XL_TRY(cached_table(key, (size_t)tab_elems(a) * sizeof(cplx<T>), s,
+                      [&](void* buf) { return czt_tables<T>(buf, a, s); }, &p));
+  *out = p;
+  return XL_OK;
+}
+
+template <typename T>
+void axes(const void* tab, const CztTabArgs& a, Axis<cplx<T>>* ax, Axis<cplx<T>>* ay) {
+  const cplx<T>* t = (const cplx<T>*)tab;
+  ax->pre = t;
+  ax->post = t + a.nx;
+  ax->bhat = t + a.nx + a.mx;
+  ax->bhat_adj = t + a.nx + a.mx + a.Lx;
+  const cplx<T>* u = t + a.off_y;
+  ay->pre = u;
+  ay->post = u + a.ny;
+  ay->bhat = u + a.ny + a.my;
+  ay->bhat_adj = u + a.ny + a.my + a.Ly;
+}
+
+template <typename T>
+xl_status run(bool adjoint, const void* in, void* out, int32_t batch, int32_t vec,
+              const xl_grid* g, const xl_window* w, double wavelength, const double* z,
+              int32_t flags, int32_t dtype, cudaStream_t s) {
+  const CztTabArgs ta = tab_args(g, w, wavelength);
+  const bool zdev = (flags & XL_Z_DEVICE) != 0;
+  const int cT = vec ? 3 : 1;
+  const size_t cs = sizeof(cplx<T>);
+  const int64_t tplane = (int64_t)w->mx * g->ny;
+  const int64_t in_plane = (int64_t)g->nx * g->ny, win_plane = (int64_t)w->mx * w->my;
+  // batch elements per launch: T planes within ~48 MB (L2-resident between the passes)
+  int chunk = (int)std::max<int64_t>(1, ((int64_t)48 << 20) / (cT * tplane * (int64_t)cs));
+  if (zdev) chunk = 1;
+  chunk = std::min<int>(chunk, batch);
+  auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
+  const size_t t_bytes = (size_t)chunk * cT * tplane * cs;
+  const size_t tab_bytes = zdev ? (size_t)tab_elems(ta) * cs : 0;
+  void* ws = nullptr;
+  XL_TRY(workspace(s, al(t_bytes) + al(tab_bytes), &ws));
+  void* Tb = ws;
+  void* dev_tab = (char*)ws + al(t_bytes);
+  CztDims d;
+  d.nx = g->nx; d.ny = g->ny; d.mx = w->mx; d.my = w->my;
+  d.x0 = g->x0; d.dx = g->dx; d.y0 = g->y0; d.dy = g->dy;
+  d.xo0 = w->xo0; d.dxo = w->dxo; d.yo0 = w->yo0; d.dyo = w->dyo;
+  const int cin = vec ? 2 : 1, cwin = vec ? 3 : 1;
+  for (int32_t b0 = 0; b0 < batch;) {
+    int nb = 1;
+    if (!zdev)
+      while (nb < chunk && b0 + nb < batch && z[b0 + nb] == z[b0]) ++nb;
+    const void* tab = nullptr;
+    XL_TRY(get_tables<T>(g, w, wavelength, z + b0, flags, dtype, dev_tab, s, &tab));
+    Axis<cplx<T>> ax, ay;
+    axes<T>(tab, ta, &ax, &ay);
+    d.zdev = zdev ? z + b0 : nullptr;
+    d.zval = zdev ? 0.0 : z[b0];
+    if (!adjoint) {
+      const char* src = (const char*)in + (size_t)b0 * cin * in_plane * cs;
+      char* dst = (char*)out + (size_t)b0 * cwin * win_plane * cs;
+      XL_TRY(czt_pass<T>(CZT_FWD_X, vec, ta.Lx, src, Tb, d, ax, nb, s));
+      XL_TRY(czt_pass<T>(CZT_FWD_Y, vec, ta.Ly, Tb, dst, d, ay, nb, s));
+    } else {
+      const char* src = (const char*)in + (size_t)b0 * cwin * win_plane * cs;
+      char* dst = (char*)out + (size_t)b0 * cin * in_plane * cs;
+      XL_TRY(czt_pass<T>(CZT_ADJ_Y, vec, ta.Ly, src, Tb, d, ay, nb, s));
+      XL_TRY(czt_pass<T>(CZT_ADJ_X, vec, ta.Lx, Tb, dst, d, ax, nb, s));
+    }
+    b0 += nb;
+  }
+  return XL_OK;
+}
+
+xl_status dispatch(bool adjoint, const void* in, void* out, int32_t batch, int32_t vec,
+                   const xl_grid* g, const xl_window* w, double wavelength, const double* z,
+                   int32_t flags, int32_t dtype, void* stream) {
+  XL_TRY(check_czt(g, w, wavelength, batch, z, flags, dtype));
+  if (batch == 0) return XL_OK;
+  if (!in || !out) return fail(XL_ERR_ARG, "field pointer is NULL");
+  if (in == out) return fail(XL_ERR_ARG, "output may not alias the input");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == XL_C128) return run<double>(adjoint, in, out, batch, vec != 0, g, w, wavelength, z, flags, dtype, s);
+  return run<float>(adjoint, in, out, batch, vec != 0, g, w, wavelength, z, flags, dtype, s);
+}
+
+}  // namespace
+}  // namespace xl
+
+using namespace xl;
+
+extern "C" {
+
+xl_status xl_czt_propagate(const void* u_in, void* u_out, int32_t batch, int32_t vectorial,
+                           const xl_grid* grid, const xl_window* window, double wavelength,
+                           const double* z, int32_t flags, int32_t dtype, void* stream) {
+  return dispatch(false, u_in, u_out, batch, vectorial, grid, window, wavelength, z, flags, dtype,
+                  stream);
+}
+
+xl_status xl_czt_propagate_backward(const void* g_out, void* g_in, int32_t batch,
+                                    int32_t vectorial, const xl_grid* grid,
+                                    const xl_window* window, double wavelength, const double* z,
+                                    int32_t flags, int32_t dtype, void* stream) {
+  return dispatch(true, g_out, g_in, batch, vectorial, grid, window, wavelength, z, flags, dtype,
+                  stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// Definitions of the CZT launchers for one precision; included with XL_REAL defined.
+#include "xl_czt_launch.h"
+
+namespace xl {
+
+namespace {
+
+template <typename T, int L, bool VEC>
+xl_status pass_LV(int which, const void* src, void* dst, const CztDims& d, const Axis<cplx<T>>& ax,
+                  int nb, cudaStream_t s) {
+  constexpr int ROWS = czt_rows<L, sizeof(cplx<T>)>();
+  const size_t sm = (size_t)ROWS * srow(L) * sizeof(cplx<T>);
+  const void* tw;
+  XL_TRY(twiddles(L, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
+  const cplx<T>* twc = (const cplx<T>*)tw;
+  const dim3 blk(ROWS * (L / 16));
+  switch (which) {
+    case CZT_FWD_X:
+      XL_TRY(smem_attr((const void*)k_czt_fwd_x<T, L, VEC>, sm));
+      k_czt_fwd_x<T, L, VEC><<<dim3((d.ny + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
+          (const cplx<T>*)src, (cplx<T>*)dst, d, ax, twc);
+      break;
+    case CZT_FWD_Y:
+      XL_TRY(smem_attr((const void*)k_czt_fwd_y<T, L, VEC>, sm));
+      k_czt_fwd_y<T, L, VEC><<<dim3((d.mx + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
+          (const cplx<T>*)src, (cplx<T>*)dst, d, ax, twc);
+      break;
+    case CZT_ADJ_Y:
+      XL_TRY(smem_attr((const void*)k_czt_adj_y<T, L, VEC>, sm));
+      k_czt_adj_y<T, L, VEC><<<dim3((d.mx + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
+          (const cplx<T>*)src, (cplx<T>*)dst, d, ax, twc);
+      break;
+    case CZT_ADJ_X:
+      XL_TRY(smem_attr((const void*)k_czt_adj_x<T, L, VEC>, sm));
+      k_czt_adj_x<T, L, VEC><<<dim3((d.ny + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
+          (const cplx<T>*)src, (cplx<T>*)dst, d, ax, twc);
+      break;
+    default:
+      return fail(XL_ERR_ARG, "czt_pass: bad pass");
+  }
+  XL_CUDA_TRY(cudaGetLastError());
+  return XL_OK;
+}
+
+template <typename T, int L>
+xl_status bhat_L(cplx<T>* rows, int64_t stride, cudaStream_t s) {
+  const size_t sm = (size_t)srow(L) * sizeof(cplx<T>);
+  const void* tw;
+  XL_TRY(twiddles(L, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
+  XL_TRY(smem_attr((const void*)k_czt_bhat<T, L>, sm));
+  k_czt_bhat<T, L><<<2, L / 16, sm, s>>>(rows, stride, (const cplx<T>*)tw);
+  XL_CUDA_TRY(cudaGetLastError());
+  return XL_OK;
+}
+
+template <typename T>
+xl_status bhat(int L, cplx<T>* rows, int64_t stride, cudaStream_t s) {
+  switch (L) {
+    case 64: return bhat_L<T, 64>(rows, stride, s);
+    case 128: return bhat_L<T, 128>(rows, stride, s);
+    case 256: return bhat_L<T, 256>(rows, stride, s);
+    case 512: return bhat_L<T, 512>(rows, stride, s);
+    case 1024: return bhat_L<T, 1024>(rows, stride, s);
+    case 2048: return bhat_L<T, 2048>(rows, stride, s);
+    case 4096: return bhat_L<T, 4096>(rows, stride, s);
+    case 8192: return bhat_L<T, 8192>(rows, stride, s);
+  }
+  return fail(XL_ERR_UNSUPPORTED, "czt: unsupported transform length");
+}
+
+}  // namespace
+
+template <>
+xl_status czt_pass<XL_REAL>(int which, bool vec, int L, const void* src, void* dst,
+                            const CztDims& d, const Axis<cplx<XL_REAL>>& ax, int nb, cudaStream_t s) {
+#define CP(LL)                                                                           \
+  case LL:                                                                               \
+    return vec ? pass_LV<XL_REAL, LL, true>(which, src, dst, d, ax, nb, s)              \
+               : pass_LV<XL_REAL, LL, false>(which, src, dst, d, ax, nb, s);
+  switch (L) {
+    CP(64) CP(128) CP(256) CP(512) CP(1024) CP(2048) CP(4096) CP(8192)
+  }
+#undef CP
+  return fail(XL_ERR_UNSUPPORTED, "czt: unsupported transform length");
+}
+
+template <>
+xl_status czt_tables<XL_REAL>(void* tab, const CztTabArgs& a, cudaStream_t s) {
+  typedef cplx<XL_REAL> C;
+  const int64_t total = (int64_t)a.nx + a.mx + 2 * (int64_t)a.Lx + a.ny + a.my + 2 * (int64_t)a.Ly;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 1024);
+  k_czt_tables<XL_REAL><<<blocks, 256, 0, s>>>((C*)tab, a);
+  XL_CUDA_TRY(cudaGetLastError());
+  C* t = (C*)tab;
+  XL_TRY(bhat<XL_REAL>(a.Lx, t + a.nx + a.mx, a.Lx, s));
+  XL_TRY(bhat<XL_REAL>(a.Ly, t + a.off_y + a.ny + a.my, a.Ly, s));
+  return XL_OK;
+}
+
+}  // namespace xl

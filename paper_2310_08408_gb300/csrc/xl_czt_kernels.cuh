@@ -1,0 +1,424 @@
+// CZT / VCZT propagation kernels (Methods, "Features and performance": the chirped z-transform
+// evaluates the propagation on an arbitrarily placed and sampled output window; Bluestein method).
+//
+// Reading: the CZT propagator is the Fresnel form of the RS integral on the output window
+//   U1(X_p, Y_q) = exp(ikz)/(i lambda z) dx dy sum_{m,n} U0[n][m] A_x(p, m) A_y(q, n),
+//   A(p, m) = exp(i k (X_p - x_m)^2 / (2 z)).
+// With X_p = X0 + p d, x_m = x0 + m D and alpha = k d D / z, Bluestein's identity
+// p m = (p^2 + m^2 - (p - m)^2) / 2 factors A(p, m) = post(p) pre(m) b(p - m):
+//   pre(m)  = exp(i [k x_m^2/(2z) - (k/z) X0 m D - alpha m^2/2]),
+//   post(p) = exp(i [k X_p^2/(2z) - (k/z) (X0 x0 + p d x0) - alpha p^2/2]),
+//   b(j)    = exp(i alpha j^2 / 2).
+// Each axis is then a linear convolution with b, evaluated as a cyclic one of length
+// L = 2^ceil(log2(N + M - 1)) (zero-padded input, b placed at j mod L for -(N-1) <= j <= M-1).
+// The two axes run as two passes (x, then y); the intermediate is stored transposed so both
+// passes read rows. All chirp phases are computed in double precision and reduced modulo 2 pi
+// before rounding (xl_czt.cu, k_czt_tables); bhat = DFT_L(b) / L carries the 1/L of the inverse
+// transform, and the y-axis post-chirp carries exp(ikz)/(i lambda z) dx dy.
+//
+// Vectorial CZT: Ex' = C Ex, Ey' = C Ey, and Ez' from the kernel -(offset / z) A, which by
+// linearity equals -(1/z) [X_p Ex' + Y_q Ey' - C(x Ex + y Ey)]; the third transform is of
+// S = x Ex + y Ey and the combination is formed in registers by the y pass.
+// Adjoint: each axis is the conjugate-chirp convolution of length L in the other direction
+// (pre-multiply conj(post), kernel b* placed for -(M-1) <= j <= N-1, post-multiply conj(pre)).
+// Vectorial adjoint: g_Ex = C^H(Gx - (X/z) Gz) + (x/z) C^H(Gz), g_Ey likewise with y.
+#pragma once
+
+#include "xl_fft.cuh"
+
+namespace xl {
+
+// One axis of chirp tables (device, complex T). Layout of the table buffer per axis:
+// pre[N] | post[M] | bhat[L] | bhat_adj[L].
+template <typename C> struct Axis {
+  const C* pre;
+  const C* post;
+  const C* bhat;
+  const C* bhat_adj;
+};
+
+struct CztDims {
+  int nx, ny, mx, my;
+  double x0, dx, y0, dy;      // input grid
+  double xo0, dxo, yo0, dyo;  // output window
+  const double* zdev;         // device z (or nullptr)
+  double zval;
+};
+
+template <int L, int CS> __host__ __device__ constexpr int czt_rows() {
+  return CS == 8 ? (L >= 8192 ? 2 : ((4096 / L) > 4 ? 4096 / L : 4))
+                 : (L >= 8192 ? 1 : ((4096 / L) > 2 ? 4096 / L : 2));
+}
+
+// Convolution of the register row with the chirp kernel: FFT, multiply by bhat, inverse FFT.
+template <int L, typename C>
+__device__ __forceinline__ void chirp_conv(C (&v)[16], C* row, int t, const C* __restrict__ tw,
+                                           const C* __restrict__ bhat) {
+  constexpr int TT = L / 16;
+  team_fft<L, -1>(v, row, t, tw);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = cmul(v[q], __ldg(bhat + t + q * TT));
+  team_fft<L, +1>(v, row, t, tw);
+}
+
+// Writes the team's register row (first n_out entries) to its smem row, then the block stores
+// ROWS rows transposed: dst[j * ld + c0 + r] for j < n_out, r < ROWS (c0 + r < n_cols).
+template <int L, int ROWS, typename C>
+__device__ __forceinline__ void store_transposed(const C (&v)[16], C* sm, int team, int t, int n_out,
+                                                 C* __restrict__ dst, int64_t ld, int c0, int n_cols) {
+  constexpr int TT = L / 16;
+  constexpr int SR = srow(L);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) sm[team * SR + spad(t + q * TT)] = v[q];
+  __syncthreads();
+  for (int j = threadIdx.x; j < n_out; j += ROWS * TT) {
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+      if (c0 + r < n_cols) dst[(int64_t)j * ld + c0 + r] = sm[r * SR + spad(j)];
+  }
+}
+
+// Loads ROWS columns transposed: the team's row r gets src[j * ld + c0 + r] for j < n_in
+// (zero beyond), times pre[j] (pre may be null), into registers.
+template <int L, int ROWS, typename C>
+__device__ __forceinline__ void load_transposed(C (&v)[16], C* sm, int team, int t, int n_in,
+                                                const C* __restrict__ src, int64_t ld, int c0,
+                                                int n_cols) {
+  constexpr int TT = L / 16;
+  constexpr int SR = srow(L);
+  typedef decltype(v[0].x) T;
+  __syncthreads();
+  for (int j = threadIdx.x; j < L; j += ROWS * TT) {
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+      sm[r * SR + spad(j)] = (j < n_in && c0 + r < n_cols) ? src[(int64_t)j * ld + c0 + r] : mk((T)0, (T)0);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = sm[team * SR + spad(t + q * TT)];
+  __syncthreads();
+}
+
+__device__ __forceinline__ double czt_z(const CztDims& d) { return d.zdev ? *d.zdev : d.zval; }
+
+// Forward x pass. Planes of element b: input cin (1 or 2), T planes cT (1 or 3). For VEC the
+// third T plane is the transform of S = x Ex + y Ey.
+// grid: (ceil(ny / ROWS), nbatch). T plane layout: [mx][ny] (row p holds all n).
+template <typename T, int L, bool VEC>
+__global__ void __launch_bounds__(czt_rows<L, sizeof(cplx<T>)>() * (L / 16))
+k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d, Axis<cplx<T>> ax,
+            const cplx<T>* __restrict__ tw) {
+  typedef cplx<T> C;
+  constexpr int ROWS = czt_rows<L, sizeof(C)>();
+  constexpr int TT = L / 16;
+  constexpr int SR = srow(L);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int team = threadIdx.x / TT, t = threadIdx.x % TT;
+  const int b = blockIdx.y;
+  const int n0 = blockIdx.x * ROWS;
+  const int n = min(n0 + team, d.ny - 1);  // teams past the edge compute a valid row, store nothing
+  const int cin = VEC ? 2 : 1, cT = VEC ? 3 : 1;
+  const int64_t plane = (int64_t)d.nx * d.ny, tplane = (int64_t)d.mx * d.ny;
+  C* row = sm + team * SR;
+#pragma unroll 1
+  for (int c = 0; c < cT; ++c) {
+    C v[16];
+    const C* s0 = in + ((int64_t)b * cin) * plane + (int64_t)n * d.nx;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int m = t + q * TT;
+      C a = mk((T)0, (T)0);
+      if (m < d.nx) {
+        if (c < 2) {
+          a = s0[c * plane + m];
+        } else {
+          const T xm = (T)(d.x0 + m * d.dx), yn = (T)(d.y0 + n * d.dy);
+          a = cadd(cscale(s0[m], xm), cscale(s0[plane + m], yn));
+        }
+        a = cmul(a, __ldg(ax.pre + m));
+      }
+      v[q] = a;
+    }
+    chirp_conv<L>(v, row, t, tw, ax.bhat);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int p = t + q * TT;
+      if (p < d.mx) v[q] = cmul(v[q], __ldg(ax.post + p));
+    }
+    store_transposed<L, ROWS>(v, sm, team, t, d.mx, Tb + ((int64_t)b * cT + c) * tplane, d.ny, n0,
+                              d.ny);
+  }
+}
+
+// Forward y pass: rows p of the T planes -> window planes [my][mx] (stored transposed).
+// For VEC the y pass forms Ez' = -(1/z)(X_p Ex' + Y_q Ey' - S') in registers.
+// grid: (ceil(mx / ROWS), nbatch).
+template <typename T, int L, bool VEC>
+__global__ void __launch_bounds__(czt_rows<L, sizeof(cplx<T>)>() * (L / 16))
+k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d, Axis<cplx<T>> ay,
+            const cplx<T>* __restrict__ tw) {
+  typedef cplx<T> C;
+  constexpr int ROWS = czt_rows<L, sizeof(C)>();
+  constexpr int TT = L / 16;
+  constexpr int SR = srow(L);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int team = threadIdx.x / TT, t = threadIdx.x % TT;
+  const int b = blockIdx.y;
+  const int p0 = blockIdx.x * ROWS;
+  const int p = min(p0 + team, d.mx - 1);
+  const int cT = VEC ? 3 : 1;
+  const int64_t tplane = (int64_t)d.mx * d.ny, oplane = (int64_t)d.mx * d.my;
+  C* row = sm + team * SR;
+  C ex[16], ey[16];
+#pragma unroll 1
+  for (int c = 0; c < cT; ++c) {
+    C v[16];
+    const C* s = Tb + ((int64_t)b * cT + c) * tplane + (int64_t)p * d.ny;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int n = t + q * TT;
+      v[q] = n < d.ny ? cmul(s[n], __ldg(ay.pre + n)) : mk((T)0, (T)0);
+    }
+    chirp_conv<L>(v, row, t, tw, ay.bhat);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int qq = t + q * TT;
+      if (qq < d.my) v[q] = cmul(v[q], __ldg(ay.post + qq));
+    }
+    if constexpr (VEC) {
+      if (c == 0) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) ex[q] = v[q];
+      } else if (c == 1) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) ey[q] = v[q];
+      } else {
+        const double z = czt_z(d);
+        const T iz = (T)(-1.0 / z);
+        const T Xp = (T)(d.xo0 + p * d.dxo);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const T Yq = (T)(d.yo0 + (t + q * TT) * d.dyo);
+          v[q] = cscale(csub(cadd(cscale(ex[q], Xp), cscale(ey[q], Yq)), v[q]), iz);
+        }
+      }
+    }
+    store_transposed<L, ROWS>(v, sm, team, t, d.my, out + ((int64_t)b * cT + c) * oplane, d.mx, p0,
+                              d.mx);
+  }
+}
+
+// Adjoint y pass: columns p of the window gradient planes [my][mx] -> T planes [mx][ny] (rows).
+// VEC: T planes A = C_y^H(Gx - (X_p/z) Gz), B = C_y^H(Gy - (Y_q/z) Gz), Z = C_y^H(Gz).
+// grid: (ceil(mx / ROWS), nbatch).
+template <typename T, int L, bool VEC>
+__global__ void __launch_bounds__(czt_rows<L, sizeof(cplx<T>)>() * (L / 16))
+k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, Axis<cplx<T>> ay,
+            const cplx<T>* __restrict__ tw) {
+  typedef cplx<T> C;
+  constexpr int ROWS = czt_rows<L, sizeof(C)>();
+  constexpr int TT = L / 16;
+  constexpr int SR = srow(L);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int team = threadIdx.x / TT, t = threadIdx.x % TT;
+  const int b = blockIdx.y;
+  const int p0 = blockIdx.x * ROWS;
+  const int p = min(p0 + team, d.mx - 1);
+  const bool live = p0 + team < d.mx;
+  const int cT = VEC ? 3 : 1;
+  const int64_t tplane = (int64_t)d.mx * d.ny, oplane = (int64_t)d.mx * d.my;
+  C* row = sm + team * SR;
+  C gz[16];
+  if constexpr (VEC) load_transposed<L, ROWS>(gz, sm, team, t, d.my, G + ((int64_t)b * 3 + 2) * oplane, d.mx, p0, d.mx);
+#pragma unroll 1
+  for (int c = 0; c < cT; ++c) {
+    C v[16];
+    if (c < 2) {
+      load_transposed<L, ROWS>(v, sm, team, t, d.my, G + ((int64_t)b * cT + c) * oplane, d.mx, p0, d.mx);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = gz[q];
+    }
+    if constexpr (VEC) {
+      if (c < 2) {
+        const T iz = (T)(1.0 / czt_z(d));
+        const T Xp = (T)(d.xo0 + p * d.dxo);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const T w = c == 0 ? Xp : (T)(d.yo0 + (t + q * TT) * d.dyo);
+          v[q] = csub(v[q], cscale(gz[q], w * iz));
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int qq = t + q * TT;
+      v[q] = qq < d.my ? cmulc(v[q], __ldg(ay.post + qq)) : mk((T)0, (T)0);
+    }
+    chirp_conv<L>(v, row, t, tw, ay.bhat_adj);
+    if (live) {
+      C* dst = Tb + ((int64_t)b * cT + c) * tplane + (int64_t)p * d.ny;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int n = t + q * TT;
+        if (n < d.ny) dst[n] = cmulc(v[q], __ldg(ay.pre + n));
+      }
+    }
+  }
+}
+
+// Adjoint x pass: columns n of the T planes -> input-grid gradient rows [ny][nx].
+// VEC: g_Ex = C_x^H(A) + (x/z) C_x^H(Z), g_Ey = C_x^H(B) + (y/z) C_x^H(Z).
+// grid: (ceil(ny / ROWS), nbatch).
+template <typename T, int L, bool VEC>
+__global__ void __launch_bounds__(czt_rows<L, sizeof(cplx<T>)>() * (L / 16))
+k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d, Axis<cplx<T>> ax,
+            const cplx<T>* __restrict__ tw) {
+  typedef cplx<T> C;
+  constexpr int ROWS = czt_rows<L, sizeof(C)>();
+  constexpr int TT = L / 16;
+  constexpr int SR = srow(L);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int team = threadIdx.x / TT, t = threadIdx.x % TT;
+  const int b = blockIdx.y;
+  const int n0 = blockIdx.x * ROWS;
+  const int n = min(n0 + team, d.ny - 1);
+  const bool live = n0 + team < d.ny;
+  const int cT = VEC ? 3 : 1, cout = VEC ? 2 : 1;
+  const int64_t tplane = (int64_t)d.mx * d.ny, plane = (int64_t)d.nx * d.ny;
+  C* row = sm + team * SR;
+  C zz[16];
+  if constexpr (VEC) {
+    load_transposed<L, ROWS>(zz, sm, team, t, d.mx, Tb + ((int64_t)b * 3 + 2) * tplane, d.ny, n0, d.ny);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int pp = t + q * TT;
+      zz[q] = pp < d.mx ? cmulc(zz[q], __ldg(ax.post + pp)) : mk((T)0, (T)0);
+    }
+    chirp_conv<L>(zz, row, t, tw, ax.bhat_adj);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int m = t + q * TT;
+      zz[q] = m < d.nx ? cmulc(zz[q], __ldg(ax.pre + m)) : mk((T)0, (T)0);
+    }
+  }
+#pragma unroll 1
+  for (int c = 0; c < cout; ++c) {
+    C v[16];
+    load_transposed<L, ROWS>(v, sm, team, t, d.mx, Tb + ((int64_t)b * cT + c) * tplane, d.ny, n0, d.ny);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int pp = t + q * TT;
+      v[q] = pp < d.mx ? cmulc(v[q], __ldg(ax.post + pp)) : mk((T)0, (T)0);
+    }
+    chirp_conv<L>(v, row, t, tw, ax.bhat_adj);
+    if (live) {
+      C* dst = gin + ((int64_t)b * cout + c) * plane + (int64_t)n * d.nx;
+      const T iz = VEC ? (T)(1.0 / czt_z(d)) : (T)0;
+      const T yn = (T)(d.y0 + n * d.dy);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int m = t + q * TT;
+        if (m < d.nx) {
+          C r = cmulc(v[q], __ldg(ax.pre + m));
+          if constexpr (VEC) {
+            const T w = c == 0 ? (T)(d.x0 + m * d.dx) : yn;
+            r = cadd(r, cscale(zz[q], w * iz));
+          }
+          dst[m] = r;
+        }
+      }
+    }
+  }
+}
+
+// Chirp tables for both axes. Entries: x axis then y axis, each pre[N] | post[M] | b_fwd[L] |
+// b_adj[L] (the b arrays are transformed afterwards by k_czt_bhat). Double-precision phases,
+// reduced modulo 2 pi, rounded once.
+struct CztTabArgs {
+  int nx, ny, mx, my, Lx, Ly;
+  double x0, dx, y0, dy, xo0, dxo, yo0, dyo, k, lambda;
+  const double* zdev;
+  double zval;
+  int64_t off_y;  // element offset of the y-axis block
+};
+
+__device__ __forceinline__ double red2pi(double x) { return x - kTwoPi * rint(x * (1.0 / kTwoPi)); }
+
+template <typename T>
+__global__ void k_czt_tables(cplx<T>* __restrict__ tab, CztTabArgs a) {
+  typedef cplx<T> C;
+  const double z = a.zdev ? *a.zdev : a.zval;
+  const int64_t tx = (int64_t)a.nx + a.mx + 2 * (int64_t)a.Lx;
+  const int64_t ty = (int64_t)a.ny + a.my + 2 * (int64_t)a.Ly;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tx + ty;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const bool isy = i >= tx;
+    const int64_t j = isy ? i - tx : i;
+    const int N = isy ? a.ny : a.nx, M = isy ? a.my : a.mx, L = isy ? a.Ly : a.Lx;
+    const double s0 = isy ? a.y0 : a.x0, D = isy ? a.dy : a.dx;
+    const double S0 = isy ? a.yo0 : a.xo0, dd = isy ? a.dyo : a.dxo;
+    const double alpha = a.k * dd * D / z;
+    double ph;
+    bool zero = false;
+    double amp_re = 1.0, amp_im = 0.0;  // extra complex factor (y post-chirp prefactor)
+    if (j < N) {  // pre(m)
+      const double m = (double)j, xm = s0 + m * D;
+      ph = red2pi(a.k * xm * xm / (2.0 * z)) - red2pi(a.k / z * S0 * m * D) - red2pi(0.5 * alpha * m * m);
+    } else if (j < N + M) {  // post(p)
+      const double p = (double)(j - N), Xp = S0 + p * dd;
+      ph = red2pi(a.k * Xp * Xp / (2.0 * z)) - red2pi(a.k / z * (S0 * s0 + p * dd * s0)) -
+           red2pi(0.5 * alpha * p * p);
+      if (isy) {
+        // exp(ikz) / (i lambda z) dx dy = exp(i (kz - pi/2)) dx dy / (lambda z)
+        ph += red2pi(a.k * z) - 0.5 * kPi;
+        amp_re = a.dx * a.dy / (a.lambda * z);
+      }
+    } else {  // b placed mod L: forward for -(N-1) <= jj <= M-1, adjoint (conj) for -(M-1) <= jj <= N-1
+      const bool adj = j >= N + M + L;
+      const int64_t idx = j - N - M - (adj ? L : 0);
+      const int64_t jj = idx <= (adj ? N - 1 : M - 1) ? idx : idx - L;
+      const int64_t lo = adj ? -(M - 1) : -(N - 1);
+      zero = jj < lo;
+      ph = red2pi(0.5 * alpha * (double)jj * (double)jj);
+      if (adj) ph = -ph;
+    }
+    C v;
+    if (zero) {
+      v = mk((T)0, (T)0);
+    } else {
+      ph = red2pi(ph);
+      T sn, cs;
+      xsincos((T)ph, &sn, &cs);
+      v = mk((T)(cs * amp_re), (T)(sn * amp_re));
+      (void)amp_im;
+    }
+    tab[(isy ? a.off_y : 0) + j] = v;
+  }
+}
+
+// In-place DFT of rows of length L (one team per row), scaled by 1/L: the chirp kernels.
+template <typename T, int L>
+__global__ void __launch_bounds__(L / 16) k_czt_bhat(cplx<T>* __restrict__ rows, int64_t stride,
+                                                    const cplx<T>* __restrict__ tw) {
+  typedef cplx<T> C;
+  constexpr int TT = L / 16;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int t = threadIdx.x;
+  C* r = rows + blockIdx.x * stride;
+  C v[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = r[t + q * TT];
+  team_fft<L, -1>(v, sm, t, tw);
+  const T s = (T)(1.0 / L);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) r[t + q * TT] = cscale(v[q], s);
+}
+
+}  // namespace xl

@@ -1,0 +1,178 @@
+// Shared-memory Stockham FFT engine (radix 16 stages, one final radix 2/4/8 stage).
+//
+// A "team" of L/16 threads transforms one row of length L (a power of two, 64..8192). Each
+// thread keeps 16 complex values in registers; on entry and on exit thread t holds element
+// t + q*(L/16) in v[q] (q = 0..15), natural order. The first stage reads the registers, every
+// later stage reads the team's padded shared-memory row, and the last stage leaves its result
+// in registers, so a caller can fuse zero-padding into the load, a spectral multiply between
+// a forward and an inverse transform, and cropping into the store without extra passes.
+//
+// Stage s (sub-transform size Ns, radix R) of the autosort Stockham formulation: butterfly j
+// reads x[j + r L/R] (r < R), multiplies element r by W_{Ns R}^{(j mod Ns) r}, takes an R-point
+// DFT, and writes y[(j div Ns) Ns R + (j mod Ns) + r Ns]. Twiddles come from a table of
+// exp(-2 pi i m / L) built in double precision on the host (conjugated for inverse transforms).
+// Shared-memory rows carry one pad element per 16 so that the stride-16 writes of the first
+// stage hit distinct banks.
+//
+// All teams of a block run the same instruction stream and meet at the same __syncthreads();
+// callers keep every thread on the FFT path (only global loads/stores are predicated).
+#pragma once
+
+#include "xl_common.cuh"
+
+namespace xl {
+
+__host__ __device__ constexpr int cilog2(int n) { return n <= 1 ? 0 : 1 + cilog2(n >> 1); }
+__host__ __device__ __forceinline__ constexpr int spad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int srow(int L) { return L + L / 16; }  // padded row length
+
+// x * (DIR i): rotation by +-90 degrees (W_4 for the transform direction DIR = -1 / +1)
+template <int DIR, typename C> __device__ __forceinline__ C rot90(C a) {
+  return DIR < 0 ? mk(a.y, -a.x) : mk(-a.y, a.x);
+}
+
+template <int DIR, typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
+  C t = a;
+  a = cadd(a, b);
+  b = csub(t, b);
+}
+
+template <int DIR, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+  C s02 = cadd(a0, a2), d02 = csub(a0, a2);
+  C s13 = cadd(a1, a3), d13 = rot90<DIR>(csub(a1, a3));
+  a0 = cadd(s02, s13);
+  a2 = csub(s02, s13);
+  a1 = cadd(d02, d13);
+  a3 = csub(d02, d13);
+}
+
+// x * exp(DIR i pi/4)
+template <int DIR, typename C> __device__ __forceinline__ C w8_1(C a) {
+  typedef decltype(a.x) T;
+  const T h = (T)0.70710678118654752440084436210484903;
+  return DIR < 0 ? mk((a.x + a.y) * h, (a.y - a.x) * h) : mk((a.x - a.y) * h, (a.y + a.x) * h);
+}
+// x * exp(DIR i 3pi/4)
+template <int DIR, typename C> __device__ __forceinline__ C w8_3(C a) {
+  typedef decltype(a.x) T;
+  const T h = (T)0.70710678118654752440084436210484903;
+  return DIR < 0 ? mk((-a.x + a.y) * h, (-a.y - a.x) * h) : mk((-a.x - a.y) * h, (-a.y + a.x) * h);
+}
+
+// In-place 8-point DFT of v[o + s*k], k = 0..7 (natural order in and out).
+template <int DIR, int S, typename C> __device__ __forceinline__ void dft8s(C* v) {
+  C e0 = v[0], e1 = v[2 * S], e2 = v[4 * S], e3 = v[6 * S];
+  C o0 = v[S], o1 = v[3 * S], o2 = v[5 * S], o3 = v[7 * S];
+  dft4<DIR>(e0, e1, e2, e3);
+  dft4<DIR>(o0, o1, o2, o3);
+  o1 = w8_1<DIR>(o1);
+  o2 = rot90<DIR>(o2);
+  o3 = w8_3<DIR>(o3);
+  v[0] = cadd(e0, o0);
+  v[4 * S] = csub(e0, o0);
+  v[S] = cadd(e1, o1);
+  v[5 * S] = csub(e1, o1);
+  v[2 * S] = cadd(e2, o2);
+  v[6 * S] = csub(e2, o2);
+  v[3 * S] = cadd(e3, o3);
+  v[7 * S] = csub(e3, o3);
+}
+
+// In-place 16-point DFT of v[s*k], k = 0..15: two 8-point DFTs of the even and odd samples
+// and the W_16^k combination.
+template <int DIR, int S, typename C> __device__ __forceinline__ void dft16s(C* v) {
+  typedef decltype(v[0].x) T;
+  C e[8], o[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    e[k] = v[2 * k * S];
+    o[k] = v[(2 * k + 1) * S];
+  }
+  dft8s<DIR, 1>(e);
+  dft8s<DIR, 1>(o);
+  const T c1 = (T)0.92387953251128675612818318939678829;  // cos(pi/8)
+  const T s1 = (T)0.38268343236508977172845998403039887;  // sin(pi/8)
+  const T sd = (T)DIR;
+  // W16^k = cos(pi k / 8) + DIR i sin(pi k / 8)
+  o[1] = cmul(o[1], mk(c1, sd * s1));
+  o[2] = w8_1<DIR>(o[2]);
+  o[3] = cmul(o[3], mk(s1, sd * c1));
+  o[4] = rot90<DIR>(o[4]);
+  o[5] = cmul(o[5], mk(-s1, sd * c1));
+  o[6] = w8_3<DIR>(o[6]);
+  o[7] = cmul(o[7], mk(-c1, sd * s1));
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    v[k * S] = cadd(e[k], o[k]);
+    v[(k + 8) * S] = csub(e[k], o[k]);
+  }
+}
+
+template <int R, int DIR, int S, typename C> __device__ __forceinline__ void dftR(C* v) {
+  if constexpr (R == 16) dft16s<DIR, S>(v);
+  else if constexpr (R == 8) dft8s<DIR, S>(v);
+  else if constexpr (R == 4) dft4<DIR>(v[0], v[S], v[2 * S], v[3 * S]);
+  else if constexpr (R == 2) dft2<DIR>(v[0], v[S]);
+}
+
+template <int L> struct FFTShape {
+  static constexpr int LOG = cilog2(L);
+  static constexpr int N16 = LOG / 4;              // radix-16 stages
+  static constexpr int REM = LOG % 4;              // log2 of the last stage's radix (0: none)
+  static constexpr int NST = N16 + (REM ? 1 : 0);  // number of stages
+  static constexpr int TT = L / 16;                // threads per team
+  static_assert((1 << LOG) == L && L >= 64 && L <= 8192, "FFT length: power of two in [64, 8192]");
+};
+
+template <typename C> __device__ __forceinline__ C twiddle(const C* __restrict__ tw, int m, bool inv) {
+  C w = __ldg(tw + m);
+  return inv ? cconj(w) : w;
+}
+
+// Stage S (>= 1) of the transform; Ns = 16^S for the radix-16 prefix.
+template <int L, int DIR, int S, typename C>
+__device__ __forceinline__ void fft_stage(C (&v)[16], C* sm, int t, const C* __restrict__ tw) {
+  typedef FFTShape<L> Sh;
+  constexpr bool last = (S == Sh::NST - 1);
+  constexpr int R = (last && Sh::REM) ? (1 << Sh::REM) : 16;
+  constexpr int B = 16 / R;
+  constexpr int Ns = 1 << (4 * S);
+  constexpr int TT = Sh::TT;
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < B; ++b)
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[b + B * r] = sm[spad(t + (b + B * r) * TT)];
+  if constexpr (!last) __syncthreads();
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int j = t + b * TT;
+    const int k = j & (Ns - 1);
+    const int step = k * (L / (Ns * R));
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[b + B * r] = cmul(v[b + B * r], twiddle(tw, step * r, DIR > 0));
+    dftR<R, DIR, B>(v + b);
+  }
+  if constexpr (!last) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int j = t + b * TT;
+      const int base = (j / Ns) * Ns * R + (j & (Ns - 1));
+#pragma unroll
+      for (int r = 0; r < R; ++r) sm[spad(base + r * Ns)] = v[b + B * r];
+    }
+    fft_stage<L, DIR, (S + 1 < Sh::NST ? S + 1 : S)>(v, sm, t, tw);
+  }
+}
+
+// Full length-L transform of one row held by a team (see the file comment for the layout).
+// sm: the team's padded shared-memory row (srow(L) elements).
+template <int L, int DIR, typename C>
+__device__ __forceinline__ void team_fft(C (&v)[16], C* sm, int t, const C* __restrict__ tw) {
+  dft16s<DIR, 1>(v);  // stage 0: radix 16, Ns = 1, no twiddles
+#pragma unroll
+  for (int r = 0; r < 16; ++r) sm[spad(t * 16 + r)] = v[r];
+  fft_stage<L, DIR, 1>(v, sm, t, tw);
+}
+
+}  // namespace xl

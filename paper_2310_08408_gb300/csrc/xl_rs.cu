@@ -1,0 +1,264 @@
+// C ABI of scalar and vectorial RS propagation and their adjoints (host orchestration of the
+// kernels in xl_rs_kernels.cuh). Methods, "Features and performance": FFT-based numerical
+// integration of the Rayleigh-Sommerfeld integral, scalar (RS) and vectorial (VRS).
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "xl_rs_launch.h"
+
+namespace xl {
+
+namespace {
+
+struct Spectra {
+  unsigned kinds = 0;
+  int slot[NKIND];
+  int count = 0;
+  explicit Spectra(unsigned k) : kinds(k) {
+    for (int i = 0; i < NKIND; ++i) slot[i] = (k & (1u << i)) ? count++ : -1;
+  }
+};
+
+xl_status check_grid(const xl_grid* g, double wavelength) {
+  if (!g) return fail(XL_ERR_ARG, "grid is NULL");
+  if (!is_pow2(g->nx) || !is_pow2(g->ny) || g->nx < 32 || g->ny < 32 || g->nx > 4096 ||
+      g->ny > 4096)
+    return fail(XL_ERR_UNSUPPORTED, "nx, ny must be powers of two in [32, 4096]");
+  if (!(g->dx > 0) || !(g->dy > 0) || !std::isfinite(g->dx) || !std::isfinite(g->dy))
+    return fail(XL_ERR_ARG, "pixel pitch must be positive and finite");
+  if (!(wavelength > 0) || !std::isfinite(wavelength))
+    return fail(XL_ERR_ARG, "wavelength must be positive and finite");
+  return XL_OK;
+}
+
+xl_status check_common(int32_t batch, const double* z, int32_t flags, int32_t dtype) {
+  if (batch < 0) return fail(XL_ERR_ARG, "batch < 0");
+  if (dtype != XL_C64 && dtype != XL_C128) return fail(XL_ERR_ARG, "dtype must be XL_C64 or XL_C128");
+  if (flags & ~XL_Z_DEVICE) return fail(XL_ERR_ARG, "unknown flag bits");
+  if (batch > 0 && !z) return fail(XL_ERR_ARG, "z is NULL");
+  if (batch > 0 && !(flags & XL_Z_DEVICE))
+    for (int32_t b = 0; b < batch; ++b)
+      if (!(z[b] > 0) || !std::isfinite(z[b]))
+        return fail(XL_ERR_ARG, "z must be positive and finite");
+  return XL_OK;
+}
+
+GenArgs gen_args(const xl_grid* g, double wavelength, const Spectra& sp) {
+  GenArgs a;
+  a.nx = g->nx;
+  a.ny = g->ny;
+  a.dx = g->dx;
+  a.dy = g->dy;
+  a.k = kTwoPi / wavelength;
+  a.zval = 0;
+  a.zdev = nullptr;
+  a.kinds = sp.kinds;
+  a.s_plane = (int64_t)(g->nx + 1) * g->ny;
+  a.hq_kind = (int64_t)(g->nx + 1) * (g->ny + 1);
+  a.scale = 1.0 / (4.0 * (double)g->nx * (double)g->ny);
+  for (int i = 0; i < NKIND; ++i) a.slot[i] = sp.slot[i];
+  return a;
+}
+
+template <typename T>
+xl_status generate(void* S, void* Hq, const GenArgs& a, cudaStream_t s) {
+  return rs_generate<T>(S, Hq, a, s);
+}
+
+// Spectra for one distance: cached (host z) or generated into `dev_hq` (device z).
+xl_status get_spectra(const xl_grid* g, double wavelength, const Spectra& sp, int32_t dtype,
+                      const double* z, int32_t flags, void* dev_s, void* dev_hq, cudaStream_t s,
+                      const void** out) {
+  GenArgs a = gen_args(g, wavelength, sp);
+  const size_t cs = dtype_csize(dtype);
+  const size_t hq_bytes = (size_t)sp.count * a.hq_kind * cs;
+  auto run = [&](void* S, void* Hq) -> xl_status {
+    return dtype == XL_C128 ? generate<double>(S, Hq, a, s) : generate<float>(S, Hq, a, s);
+  };
+  if (flags & XL_Z_DEVICE) {
+    a.zdev = z;
+    XL_TRY(run(dev_s, dev_hq));
+    *out = dev_hq;
+    return XL_OK;
+  }
+  a.zval = *z;
+  std::string key = "rs";
+  key_put(key, sp.kinds);
+  key_put(key, g->nx);
+  key_put(key, g->ny);
+  key_put(key, g->dx);
+  key_put(key, g->dy);
+  key_put(key, wavelength);
+  key_put(key, *z);
+  key_put(key, dtype);
+  void* p = nullptr;
+  XL_TRY(cached_table(key, hq_bytes, s, [&](void* Hq) -> xl_status {
+    void* S = nullptr;
+    XL_TRY(workspace(s, (size_t)sp.count * a.s_plane * cs, &S, 1));
+    return run(S, Hq);
+  }, &p));
+  *out = p;
+  return XL_OK;
+}
+
+P2Args p2_args(const xl_grid* g, const Spectra& sp, int cT, int cU) {
+  P2Args a;
+  a.nx = g->nx;
+  a.ny = g->ny;
+  a.t_plane = (int64_t)2 * g->nx * g->ny;
+  a.hq_kind = (int64_t)(g->nx + 1) * (g->ny + 1);
+  a.cT = cT;
+  a.cU = cU;
+  a.want_field = 1;
+  a.want_dz = 0;
+  a.conj = 0;
+  for (int i = 0; i < NKIND; ++i) a.slot[i] = sp.slot[i];
+  return a;
+}
+
+template <typename T>
+xl_status launch_reduce(const double* part, int n, double* out, int nb, cudaStream_t s) {
+  k_reduce_rows<<<nb, 256, 0, s>>>(part, n, out);
+  XL_CUDA_TRY(cudaGetLastError());
+  return XL_OK;
+}
+
+// How many batch elements one launch processes: keep the T planes of a launch within about
+// 48 MB so that they stay resident in L2 between the passes.
+int chunk_size(int64_t t_bytes_per_elem, int32_t remaining) {
+  int64_t c = ((int64_t)48 << 20) / (t_bytes_per_elem > 0 ? t_bytes_per_elem : 1);
+  if (c < 1) c = 1;
+  return (int)(c < remaining ? c : remaining);
+}
+
+enum Op { OP_RS_FWD, OP_RS_BWD, OP_VRS_FWD, OP_VRS_BWD };
+
+template <typename T>
+xl_status run_op(Op op, const void* in, const void* u_in, void* out, double* g_z, int32_t batch,
+                 const xl_grid* g, double wavelength, const double* z, int32_t flags, int32_t dtype,
+                 cudaStream_t s) {
+  const bool vec = (op == OP_VRS_FWD || op == OP_VRS_BWD);
+  const bool bwd = (op == OP_RS_BWD || op == OP_VRS_BWD);
+  const bool want_field = !bwd || out != nullptr;
+  const bool want_dz = bwd && g_z != nullptr;
+  unsigned kinds = 0;
+  if (!vec) {
+    if (want_field) kinds |= 1u << KH;
+    if (want_dz) kinds |= 1u << KDH;
+  } else {
+    if (want_field || !bwd) kinds |= (1u << KH) | (1u << KHX) | (1u << KHY);
+    if (want_dz) kinds |= (1u << KH) | (1u << KHX) | (1u << KHY) | (1u << KDH) | (1u << KDHX) |
+                          (1u << KDHY);
+  }
+  if (!kinds) return XL_OK;  // nothing requested
+  Spectra sp(kinds);
+  const int nx = g->nx, ny = g->ny;
+  const size_t cs = sizeof(cplx<T>);
+  const int64_t t_plane = (int64_t)2 * nx * ny;
+  const int64_t plane = (int64_t)nx * ny;
+  // planes per element: input to pass 1, T planes, U planes (dz), output of pass 3
+  const int cin = op == OP_RS_FWD || op == OP_RS_BWD ? 1 : (op == OP_VRS_FWD ? 2 : 3);
+  const int cT = vec ? 3 : 1;
+  const int cU = want_dz ? (vec ? 2 : 1) : 0;
+  const int cout = op == OP_VRS_FWD ? 3 : (op == OP_VRS_BWD ? 2 : 1);
+  const int p2blocks = rs_pass2_blocks<T>(nx, ny);
+  const bool zdev = (flags & XL_Z_DEVICE) != 0;
+  const int64_t elem_ws = (int64_t)(cT + cU) * t_plane * cs;
+  const int chunk_max = zdev ? 1 : chunk_size(elem_ws, batch);
+  // workspace: T (chunk * cT planes) | U (chunk * cU planes) | dz partials | [S | Hq] (device z)
+  const size_t t_bytes = (size_t)chunk_max * cT * t_plane * cs;
+  const size_t u_bytes = (size_t)chunk_max * cU * t_plane * cs;
+  const size_t dz_bytes = want_dz ? (size_t)chunk_max * p2blocks * sizeof(double) : 0;
+  const size_t s_bytes = zdev ? (size_t)sp.count * (nx + 1) * ny * cs : 0;
+  const size_t hq_bytes = zdev ? (size_t)sp.count * (nx + 1) * (ny + 1) * cs : 0;
+  auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
+  void* ws = nullptr;
+  XL_TRY(workspace(s, al(t_bytes) + al(u_bytes) + al(dz_bytes) + al(s_bytes) + al(hq_bytes), &ws));
+  char* w = (char*)ws;
+  void* Tb = w;
+  void* Ub = w + al(t_bytes);
+  double* dzp = (double*)(w + al(t_bytes) + al(u_bytes));
+  void* dev_s = w + al(t_bytes) + al(u_bytes) + al(dz_bytes);
+  void* dev_hq = (char*)dev_s + al(s_bytes);
+
+  const char* src = (const char*)in;
+  const char* usrc = (const char*)u_in;
+  char* dst = (char*)out;
+  for (int32_t b0 = 0; b0 < batch;) {
+    // elements sharing one distance go in one launch
+    int nb = 1;
+    if (!zdev)
+      while (nb < chunk_max && b0 + nb < batch && z[b0 + nb] == z[b0]) ++nb;
+    const void* Hq = nullptr;
+    XL_TRY(get_spectra(g, wavelength, sp, dtype, z + b0, flags, dev_s, dev_hq, s, &Hq));
+    XL_TRY(rs_pass1<T>(src + (size_t)b0 * cin * plane * cs, Tb, nx, ny, cin, cT, nb * cin, s));
+    if (want_dz)
+      XL_TRY(rs_pass1<T>(usrc + (size_t)b0 * cU * plane * cs, Ub, nx, ny, cU, cU, nb * cU, s));
+    P2Args a = p2_args(g, sp, cT, cU);
+    a.want_field = want_field;
+    a.want_dz = want_dz;
+    int mode = op == OP_RS_FWD ? P2_RS : op == OP_VRS_FWD ? P2_VRS : op == OP_RS_BWD ? P2_RS_BWD
+                                                                                    : P2_VRS_BWD;
+    XL_TRY(rs_pass2<T>(mode, Tb, Ub, Hq, dzp, a, nb, s));
+    if (want_dz) XL_TRY(launch_reduce<T>(dzp, p2blocks, g_z + b0, nb, s));
+    if (want_field)
+      XL_TRY(rs_pass3<T>(Tb, dst + (size_t)b0 * cout * plane * cs, nx, ny, cout, cT, nb * cout, s));
+    b0 += nb;
+  }
+  return XL_OK;
+}
+
+xl_status dispatch(Op op, const void* in, const void* u_in, void* out, double* g_z, int32_t batch,
+                   const xl_grid* g, double wavelength, const double* z, int32_t flags,
+                   int32_t dtype, void* stream) {
+  XL_TRY(check_grid(g, wavelength));
+  XL_TRY(check_common(batch, z, flags, dtype));
+  if (batch == 0) return XL_OK;
+  const bool bwd = (op == OP_RS_BWD || op == OP_VRS_BWD);
+  if (!in) return fail(XL_ERR_ARG, "input field is NULL");
+  if (!bwd && !out) return fail(XL_ERR_ARG, "output field is NULL");
+  if (bwd && g_z && !u_in) return fail(XL_ERR_ARG, "g_z requested but the forward input is NULL");
+  if (!bwd && in == out) return fail(XL_ERR_ARG, "output may not alias the input");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == XL_C128) return run_op<double>(op, in, u_in, out, g_z, batch, g, wavelength, z, flags, dtype, s);
+  return run_op<float>(op, in, u_in, out, g_z, batch, g, wavelength, z, flags, dtype, s);
+}
+
+}  // namespace
+}  // namespace xl
+
+using namespace xl;
+
+extern "C" {
+
+xl_status xl_rs_propagate(const void* u_in, void* u_out, int32_t batch, const xl_grid* grid,
+                          double wavelength, const double* z, int32_t flags, int32_t dtype,
+                          void* stream) {
+  return dispatch(OP_RS_FWD, u_in, nullptr, u_out, nullptr, batch, grid, wavelength, z, flags,
+                  dtype, stream);
+}
+
+xl_status xl_rs_propagate_backward(const void* g_out, const void* u_in, void* g_in, double* g_z,
+                                   int32_t batch, const xl_grid* grid, double wavelength,
+                                   const double* z, int32_t flags, int32_t dtype, void* stream) {
+  return dispatch(OP_RS_BWD, g_out, u_in, g_in, g_z, batch, grid, wavelength, z, flags, dtype,
+                  stream);
+}
+
+xl_status xl_vrs_propagate(const void* exy_in, void* exyz_out, int32_t batch, const xl_grid* grid,
+                           double wavelength, const double* z, int32_t flags, int32_t dtype,
+                           void* stream) {
+  return dispatch(OP_VRS_FWD, exy_in, nullptr, exyz_out, nullptr, batch, grid, wavelength, z,
+                  flags, dtype, stream);
+}
+
+xl_status xl_vrs_propagate_backward(const void* g_exyz, const void* exy_in, void* g_exy,
+                                    double* g_z, int32_t batch, const xl_grid* grid,
+                                    double wavelength, const double* z, int32_t flags,
+                                    int32_t dtype, void* stream) {
+  return dispatch(OP_VRS_BWD, g_exyz, exy_in, g_exy, g_z, batch, grid, wavelength, z, flags, dtype,
+                  stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,156 @@
+// Definitions of the RS launchers for one precision; included by xl_rs_c64.cu / xl_rs_c128.cu
+// with XL_REAL defined.
+#include "xl_rs_launch.h"
+
+namespace xl {
+
+namespace {
+
+template <typename T, int LX>
+xl_status pass1_L(const void* in, void* Tb, int nx, int ny, int cin, int cT, int np, cudaStream_t s) {
+  constexpr int ROWS = rows_transp<LX, sizeof(cplx<T>)>();
+  const size_t sm = (size_t)ROWS * srow(LX) * sizeof(cplx<T>);
+  const void* tw;
+  XL_TRY(twiddles(LX, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
+  XL_TRY(smem_attr((const void*)k_rs_pass1<T, LX>, sm));
+  dim3 grid((ny + ROWS - 1) / ROWS, np);
+  k_rs_pass1<T, LX><<<grid, ROWS * (LX / 16), sm, s>>>(
+      (const cplx<T>*)in, (cplx<T>*)Tb, nx, ny, cin, cT, (const cplx<T>*)tw);
+  XL_CUDA_TRY(cudaGetLastError());
+  return XL_OK;
+}
+
+template <typename T, int LX>
+xl_status pass3_L(const void* Tb, void* out, int nx, int ny, int cout, int cT, int np, cudaStream_t s) {
+  constexpr int ROWS = rows_transp<LX, sizeof(cplx<T>)>();
+  const size_t sm = (size_t)ROWS * srow(LX) * sizeof(cplx<T>);
+  const void* tw;
+  XL_TRY(twiddles(LX, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
+  XL_TRY(smem_attr((const void*)k_rs_pass3<T, LX>, sm));
+  dim3 grid((ny + ROWS - 1) / ROWS, np);
+  k_rs_pass3<T, LX><<<grid, ROWS * (LX / 16), sm, s>>>(
+      (const cplx<T>*)Tb, (cplx<T>*)out, nx, ny, cout, cT, (const cplx<T>*)tw);
+  XL_CUDA_TRY(cudaGetLastError());
+  return XL_OK;
+}
+
+template <typename T, int LY, int MODE>
+xl_status pass2_LM(void* Tb, const void* Ub, const void* Hq, double* dz, const P2Args& a, int nb,
+                   cudaStream_t s) {
+  constexpr int ROWS = rows_cols<LY>();
+  const size_t sm = (size_t)ROWS * srow(LY) * sizeof(cplx<T>);
+  const void* tw;
+  XL_TRY(twiddles(LY, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
+  XL_TRY(smem_attr((const void*)k_rs_pass2<T, LY, MODE>, sm));
+  const int LX = 2 * a.nx;
+  dim3 grid((LX + ROWS - 1) / ROWS, nb);
+  k_rs_pass2<T, LY, MODE><<<grid, ROWS * (LY / 16), sm, s>>>(
+      (cplx<T>*)Tb, (const cplx<T>*)Ub, (const cplx<T>*)Hq, dz, a, (const cplx<T>*)tw);
+  XL_CUDA_TRY(cudaGetLastError());
+  return XL_OK;
+}
+
+template <typename T, int LY>
+xl_status pass2_L(int mode, void* Tb, const void* Ub, const void* Hq, double* dz, const P2Args& a,
+                  int nb, cudaStream_t s) {
+  switch (mode) {
+    case P2_RS: return pass2_LM<T, LY, P2_RS>(Tb, Ub, Hq, dz, a, nb, s);
+    case P2_VRS: return pass2_LM<T, LY, P2_VRS>(Tb, Ub, Hq, dz, a, nb, s);
+    case P2_RS_BWD: return pass2_LM<T, LY, P2_RS_BWD>(Tb, Ub, Hq, dz, a, nb, s);
+    case P2_VRS_BWD: return pass2_LM<T, LY, P2_VRS_BWD>(Tb, Ub, Hq, dz, a, nb, s);
+  }
+  return fail(XL_ERR_ARG, "rs_pass2: bad mode");
+}
+
+template <typename T, int LX, int LY>
+xl_status gen_LL(void* S, void* Hq, const GenArgs& g, cudaStream_t s) {
+  constexpr int RA = rows_transp<LX, sizeof(cplx<T>)>();
+  constexpr int RB = rows_cols<LY>();
+  const size_t sa = (size_t)RA * srow(LX) * sizeof(cplx<T>);
+  const size_t sb = (size_t)RB * srow(LY) * sizeof(cplx<T>);
+  const void *twx, *twy;
+  XL_TRY(twiddles(LX, sizeof(T) == 8 ? XL_C128 : XL_C64, &twx));
+  XL_TRY(twiddles(LY, sizeof(T) == 8 ? XL_C128 : XL_C64, &twy));
+  XL_TRY(smem_attr((const void*)k_gen_pass_a<T, LX>, sa));
+  XL_TRY(smem_attr((const void*)k_gen_pass_b<T, LY>, sb));
+  k_gen_pass_a<T, LX><<<(g.ny + RA - 1) / RA, RA * (LX / 16), sa, s>>>((cplx<T>*)S, g,
+                                                                      (const cplx<T>*)twx);
+  XL_CUDA_TRY(cudaGetLastError());
+  k_gen_pass_b<T, LY><<<(g.nx + 1 + RB - 1) / RB, RB * (LY / 16), sb, s>>>(
+      (const cplx<T>*)S, (cplx<T>*)Hq, g, (const cplx<T>*)twy);
+  XL_CUDA_TRY(cudaGetLastError());
+  return XL_OK;
+}
+
+template <typename T, int LX>
+xl_status gen_L(void* S, void* Hq, const GenArgs& g, cudaStream_t s) {
+  switch (2 * g.ny) {
+    case 64: return gen_LL<T, LX, 64>(S, Hq, g, s);
+    case 128: return gen_LL<T, LX, 128>(S, Hq, g, s);
+    case 256: return gen_LL<T, LX, 256>(S, Hq, g, s);
+    case 512: return gen_LL<T, LX, 512>(S, Hq, g, s);
+    case 1024: return gen_LL<T, LX, 1024>(S, Hq, g, s);
+    case 2048: return gen_LL<T, LX, 2048>(S, Hq, g, s);
+    case 4096: return gen_LL<T, LX, 4096>(S, Hq, g, s);
+    case 8192: return gen_LL<T, LX, 8192>(S, Hq, g, s);
+  }
+  return fail(XL_ERR_UNSUPPORTED, "rs_generate: unsupported ny");
+}
+
+}  // namespace
+
+#define XL_SWITCH_L(L, CALL)                               \
+  switch (L) {                                             \
+    case 64: return CALL(64);                              \
+    case 128: return CALL(128);                            \
+    case 256: return CALL(256);                            \
+    case 512: return CALL(512);                            \
+    case 1024: return CALL(1024);                          \
+    case 2048: return CALL(2048);                          \
+    case 4096: return CALL(4096);                          \
+    case 8192: return CALL(8192);                          \
+  }
+
+template <>
+xl_status rs_pass1<XL_REAL>(const void* in, void* Tb, int nx, int ny, int cin, int cT, int np,
+                            cudaStream_t s) {
+#define C1(L) pass1_L<XL_REAL, L>(in, Tb, nx, ny, cin, cT, np, s)
+  XL_SWITCH_L(2 * nx, C1)
+#undef C1
+  return fail(XL_ERR_UNSUPPORTED, "rs_pass1: unsupported nx");
+}
+
+template <>
+xl_status rs_pass3<XL_REAL>(const void* Tb, void* out, int nx, int ny, int cout, int cT, int np,
+                            cudaStream_t s) {
+#define C3(L) pass3_L<XL_REAL, L>(Tb, out, nx, ny, cout, cT, np, s)
+  XL_SWITCH_L(2 * nx, C3)
+#undef C3
+  return fail(XL_ERR_UNSUPPORTED, "rs_pass3: unsupported nx");
+}
+
+template <>
+xl_status rs_pass2<XL_REAL>(int mode, void* Tb, const void* Ub, const void* Hq, double* dz,
+                            const P2Args& a, int nb, cudaStream_t s) {
+#define C2(L) pass2_L<XL_REAL, L>(mode, Tb, Ub, Hq, dz, a, nb, s)
+  XL_SWITCH_L(2 * a.ny, C2)
+#undef C2
+  return fail(XL_ERR_UNSUPPORTED, "rs_pass2: unsupported ny");
+}
+
+template <>
+int rs_pass2_blocks<XL_REAL>(int nx, int ny) {
+  const int LY = 2 * ny, TT = LY / 16;
+  const int rows = (256 / TT) > 1 ? 256 / TT : 1;
+  return (2 * nx + rows - 1) / rows;
+}
+
+template <>
+xl_status rs_generate<XL_REAL>(void* S, void* Hq, const GenArgs& g, cudaStream_t s) {
+#define CG(L) gen_L<XL_REAL, L>(S, Hq, g, s)
+  XL_SWITCH_L(2 * g.nx, CG)
+#undef CG
+  return fail(XL_ERR_UNSUPPORTED, "rs_generate: unsupported nx");
+}
+
+}  // namespace xl

@@ -1,0 +1,456 @@
+// RS / VRS propagation kernels: a three-pass zero-padded 2D FFT convolution and the
+// transfer-spectrum generator (Methods, "Features and performance": FFT-based numerical
+// integration of the Rayleigh-Sommerfeld integral, scalar and vectorial).
+//
+// Layout. A field plane is [ny][nx]. The padded transform size is LX = 2 nx by LY = 2 ny. The
+// intermediate after the row pass is stored transposed as T[kx][y] (LX rows of ny values): only
+// the ny non-zero input rows exist, so the padded grid is never materialised (half the bytes of a
+// [LY][LX] array), and at 2048^2 complex64 one plane of T (67 MB) stays resident in the 126 MB L2
+// between the passes.
+//   pass 1  row FFT along x of every input row (zero-padding fused into the load), store T.
+//   pass 2  per kx: FFT along y (zero-padded), multiply by the spectrum, inverse FFT along y,
+//           keep the first ny outputs, store in place. Spectral reductions (dz) are fused here.
+//   pass 3  per y: inverse FFT along x, keep the first nx outputs (crop fused into the store).
+//
+// Spectra. The sampled kernels are even or odd in each offset (h even/even, h_x odd in a, h_y odd
+// in b), so their DFTs have the same parity and only the quadrant kx in [0, nx], ky in [0, ny]
+// is stored: Hq[kind][kx][ky], ((nx+1) x (ny+1) per kind), scaled by 1 / (LX LY) so that pass 2
+// needs no separate normalisation. The generator evaluates the kernel with the phase k r
+// computed in double precision as k z + k rho^2 / (r + z) (no cancellation), each term reduced
+// modulo 2 pi, before a single-precision sincos; it then runs the same two-pass FFT.
+#pragma once
+
+#include "xl_fft.cuh"
+
+namespace xl {
+
+// kernel kinds (bit i of a kind mask selects spectrum i)
+enum { KH = 0, KHX = 1, KHY = 2, KDH = 3, KDHX = 4, KDHY = 5, NKIND = 6 };
+__host__ __device__ constexpr bool kind_odd_x(int k) { return k == KHX || k == KDHX; }
+__host__ __device__ constexpr bool kind_odd_y(int k) { return k == KHY || k == KDHY; }
+
+// Rows per block: the transposing passes (1 and 3) write/read whole 32-byte sectors per kx when
+// a block holds at least 32 / sizeof(complex) rows; pass 2 aims at 256 threads per block.
+template <int L, int CS> __host__ __device__ constexpr int rows_transp() {
+  return CS == 8 ? (L >= 8192 ? 2 : ((4096 / L) > 4 ? 4096 / L : 4))
+                 : (L >= 8192 ? 1 : ((4096 / L) > 2 ? 4096 / L : 2));
+}
+template <int L> __host__ __device__ constexpr int rows_cols() { return (4096 / L) > 1 ? 4096 / L : 1; }
+
+// Geometry of one propagation (scalars passed by value to every kernel).
+struct RsGeom {
+  int nx, ny;
+  double dx, dy;
+  double k;  // 2 pi / wavelength
+};
+
+// ---------------------------------------------------------------------------------------------
+// Spectrum access: value of spectrum `kind` at full-grid frequency (kx, ky), kx < LX, ky < LY.
+template <typename C>
+__device__ __forceinline__ C spec_at(const C* __restrict__ Hk, int kx, int ky, int nx, int ny,
+                                     bool oddx, bool oddy) {
+  const int LX = 2 * nx, LY = 2 * ny;
+  const bool fx = kx > nx, fy = ky > ny;
+  const int ax = fx ? LX - kx : kx, ay = fy ? LY - ky : ky;
+  C h = __ldg(Hk + (int64_t)ax * (ny + 1) + ay);
+  if ((oddx && fx) != (oddy && fy)) h = mk(-h.x, -h.y);
+  return h;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Pass 1: row FFT (forward) of planes [ny][nx] into T[kx][y].
+// Plane p of the input maps to plane (p / cin) * cT + (p % cin) of the T buffer.
+template <typename T, int LX>
+__global__ void __launch_bounds__(rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16))
+k_rs_pass1(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, int nx, int ny, int cin,
+           int cT, const cplx<T>* __restrict__ tw) {
+  typedef cplx<T> C;
+  constexpr int ROWS = rows_transp<LX, sizeof(cplx<T>)>();
+  constexpr int TT = LX / 16;
+  constexpr int SR = srow(LX);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int team = threadIdx.x / TT, t = threadIdx.x % TT;
+  const int p = blockIdx.y;
+  const int y0 = blockIdx.x * ROWS;
+  const int y = y0 + team;
+  const C* src = in + (int64_t)p * nx * ny + (int64_t)y * nx;
+  C* dst = Tb + ((int64_t)(p / cin) * cT + (p % cin)) * (int64_t)LX * ny;
+  C v[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = (q < 8 && y < ny) ? src[t + q * TT] : mk((T)0, (T)0);
+  C* row = sm + team * SR;
+  team_fft<LX, -1>(v, row, t, tw);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) row[spad(t + q * TT)] = v[q];
+  __syncthreads();
+  // transposed store: each thread writes ROWS consecutive y of one kx
+  for (int kx = threadIdx.x; kx < LX; kx += ROWS * TT) {
+    C* d = dst + (int64_t)kx * ny + y0;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+      if (y0 + r < ny) d[r] = sm[r * SR + spad(kx)];
+  }
+}
+
+// Pass 3: inverse row FFT from T[kx][y] into planes [ny][nx] (crop to x < nx).
+// Plane p of the output maps to plane (p / cout) * cT + (p % cout) of T.
+template <typename T, int LX>
+__global__ void __launch_bounds__(rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16))
+k_rs_pass3(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, int nx, int ny, int cout,
+           int cT, const cplx<T>* __restrict__ tw) {
+  typedef cplx<T> C;
+  constexpr int ROWS = rows_transp<LX, sizeof(cplx<T>)>();
+  constexpr int TT = LX / 16;
+  constexpr int SR = srow(LX);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int team = threadIdx.x / TT, t = threadIdx.x % TT;
+  const int p = blockIdx.y;
+  const int y0 = blockIdx.x * ROWS;
+  const C* src = Tb + ((int64_t)(p / cout) * cT + (p % cout)) * (int64_t)LX * ny;
+  for (int kx = threadIdx.x; kx < LX; kx += ROWS * TT) {
+    const C* s = src + (int64_t)kx * ny + y0;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+      if (y0 + r < ny) sm[r * SR + spad(kx)] = s[r];
+  }
+  __syncthreads();
+  C* row = sm + team * SR;
+  C v[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = row[spad(t + q * TT)];
+  __syncthreads();
+  team_fft<LX, +1>(v, row, t, tw);
+  const int y = y0 + team;
+  if (y < ny) {
+    C* d = out + (int64_t)p * nx * ny + (int64_t)y * nx;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) d[t + q * TT] = v[q];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Pass 2 modes.
+enum {
+  P2_RS = 0,        // T0 <- IFFT(FFT(T0) * S0)                      (S0 = H or conj H)
+  P2_VRS = 1,       // T0,T1,T2 <- from T0,T1: x*Hz, y*Hz, x*Hx + y*Hy
+  P2_RS_BWD = 2,    // T0 <- IFFT(FFT(T0) conj Hz); dz partial from T0, U0 (optional)
+  P2_VRS_BWD = 3,   // T0,T1 <- from T0,T1,T2 (gx, gy, gz) with conj spectra; dz from U0,U1
+};
+
+struct P2Args {
+  int nx, ny;
+  int64_t t_plane;      // elements of one T plane (LX * ny)
+  int64_t hq_kind;      // elements of one spectrum quadrant ((nx+1)(ny+1))
+  int cT;               // T planes per batch element
+  int cU;               // U planes per batch element (dz)
+  int want_field;       // write the field result (backward: g_in requested)
+  int want_dz;          // accumulate the dz partials
+  int conj;             // P2_RS: use conj(H) (adjoint without dz)
+  int slot[NKIND];      // spectrum kind -> slot in the Hq buffer (-1: absent)
+};
+
+template <typename C>
+__device__ __forceinline__ void load_col(C (&v)[16], const C* __restrict__ src, int t, int TT) {
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = q < 8 ? src[t + q * TT] : mk((decltype(v[0].x))0, (decltype(v[0].x))0);
+}
+template <typename C>
+__device__ __forceinline__ void store_col(const C (&v)[16], C* __restrict__ dst, int t, int TT) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) dst[t + q * TT] = v[q];
+}
+
+// Block-wide sum of a double (one value per thread) -> thread 0; sbuf holds 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sbuf) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sbuf[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) s += sbuf[i];
+  return s;
+}
+
+// grid: (ceil(LX / ROWS), nbatch). Hq: spectra [NKIND slots used by mode][nx+1][ny+1].
+// dz_part: [nbatch][LX] partial sums (one per kx), reduced later in fixed order.
+template <typename T, int LY, int MODE>
+__global__ void __launch_bounds__(rows_cols<LY>() * (LY / 16))
+k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<T>* __restrict__ Hq,
+           double* __restrict__ dz_part, P2Args a, const cplx<T>* __restrict__ tw) {
+  typedef cplx<T> C;
+  constexpr int ROWS = rows_cols<LY>();
+  constexpr int TT = LY / 16;
+  constexpr int SR = srow(LY);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  __shared__ double red[32];
+  const int team = threadIdx.x / TT, t = threadIdx.x % TT;
+  const int LX = 2 * a.nx;
+  const int kx_raw = blockIdx.x * ROWS + team;
+  const bool live = kx_raw < LX;
+  const int kx = live ? kx_raw : LX - 1;  // dead teams run the same code on a valid row, no stores
+  const int b = blockIdx.y;
+  C* row = sm + team * SR;
+  C* T0 = Tb + (int64_t)b * a.cT * a.t_plane + (int64_t)kx * a.ny;
+  const int64_t HK = a.hq_kind;
+  C v[16];
+  double dz = 0.0;
+
+  if constexpr (MODE == P2_RS) {
+    load_col(v, T0, t, TT);
+    team_fft<LY, -1>(v, row, t, tw);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      C h = spec_at(Hq + a.slot[KH] * HK, kx, t + q * TT, a.nx, a.ny, false, false);
+      v[q] = a.conj ? cmulc(v[q], h) : cmul(v[q], h);
+    }
+    team_fft<LY, +1>(v, row, t, tw);
+    if (live) store_col(v, T0, t, TT);
+  } else if constexpr (MODE == P2_VRS) {
+    C* T1 = T0 + a.t_plane;
+    C* T2 = T1 + a.t_plane;
+    C z[16];
+    load_col(v, T0, t, TT);
+    team_fft<LY, -1>(v, row, t, tw);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int ky = t + q * TT;
+      z[q] = cmul(v[q], spec_at(Hq + a.slot[KHX] * HK, kx, ky, a.nx, a.ny, true, false));
+      v[q] = cmul(v[q], spec_at(Hq + a.slot[KH] * HK, kx, ky, a.nx, a.ny, false, false));
+    }
+    team_fft<LY, +1>(v, row, t, tw);
+    if (live) store_col(v, T0, t, TT);
+    load_col(v, T1, t, TT);
+    team_fft<LY, -1>(v, row, t, tw);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int ky = t + q * TT;
+      z[q] = cadd(z[q], cmul(v[q], spec_at(Hq + a.slot[KHY] * HK, kx, ky, a.nx, a.ny, false, true)));
+      v[q] = cmul(v[q], spec_at(Hq + a.slot[KH] * HK, kx, ky, a.nx, a.ny, false, false));
+    }
+    team_fft<LY, +1>(v, row, t, tw);
+    if (live) store_col(v, T1, t, TT);
+    team_fft<LY, +1>(z, row, t, tw);
+    if (live) store_col(z, T2, t, TT);
+  } else if constexpr (MODE == P2_RS_BWD) {
+    load_col(v, T0, t, TT);
+    team_fft<LY, -1>(v, row, t, tw);
+    if (a.want_dz) {
+      C u[16];
+      const C* U0 = Ub + (int64_t)b * a.cU * a.t_plane + (int64_t)kx * a.ny;
+      load_col(u, U0, t, TT);
+      team_fft<LY, -1>(u, row, t, tw);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        C hd = spec_at(Hq + a.slot[KDH] * HK, kx, t + q * TT, a.nx, a.ny, false, false);
+        dz += (double)cdot_re(v[q], cmul(u[q], hd));
+      }
+    }
+    if (a.want_field) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        v[q] = cmulc(v[q], spec_at(Hq + a.slot[KH] * HK, kx, t + q * TT, a.nx, a.ny, false, false));
+      team_fft<LY, +1>(v, row, t, tw);
+      if (live) store_col(v, T0, t, TT);
+    }
+  } else if constexpr (MODE == P2_VRS_BWD) {
+    C* T1 = T0 + a.t_plane;
+    C* T2 = T1 + a.t_plane;
+    C z[16];
+    load_col(z, T2, t, TT);
+    team_fft<LY, -1>(z, row, t, tw);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      C* Tc = c == 0 ? T0 : T1;
+      load_col(v, Tc, t, TT);
+      team_fft<LY, -1>(v, row, t, tw);
+      const int kodd = c == 0 ? KHX : KHY;
+      const int kdodd = c == 0 ? KDHX : KDHY;
+      if (a.want_dz) {
+        C u[16];
+        const C* Uc = Ub + ((int64_t)b * a.cU + c) * a.t_plane + (int64_t)kx * a.ny;
+        load_col(u, Uc, t, TT);
+        team_fft<LY, -1>(u, row, t, tw);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int ky = t + q * TT;
+          C hd = spec_at(Hq + a.slot[KDH] * HK, kx, ky, a.nx, a.ny, false, false);
+          C ho = spec_at(Hq + a.slot[kdodd] * HK, kx, ky, a.nx, a.ny, c == 0, c == 1);
+          dz += (double)cdot_re(v[q], cmul(u[q], hd)) + (double)cdot_re(z[q], cmul(u[q], ho));
+        }
+      }
+      if (a.want_field) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int ky = t + q * TT;
+          C hz = spec_at(Hq + a.slot[KH] * HK, kx, ky, a.nx, a.ny, false, false);
+          C ho = spec_at(Hq + a.slot[kodd] * HK, kx, ky, a.nx, a.ny, c == 0, c == 1);
+          v[q] = cadd(cmulc(v[q], hz), cmulc(z[q], ho));
+        }
+        team_fft<LY, +1>(v, row, t, tw);
+        if (live) store_col(v, Tc, t, TT);
+      }
+    }
+  }
+  if (MODE == P2_RS_BWD || MODE == P2_VRS_BWD) {
+    if (a.want_dz) {
+      // per-kx partial: reduce inside each team (teams are whole warps or sub-warp groups)
+      double s = block_sum(live ? dz : 0.0, red);
+      if (threadIdx.x == 0) dz_part[(int64_t)b * gridDim.x + blockIdx.x] = s;
+    }
+  }
+}
+
+// Fixed-order final reduction of the dz partials: g_z[b] = sum_i part[b][i].
+static __global__ void k_reduce_rows(const double* __restrict__ part, int n, double* __restrict__ out) {
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[(int64_t)b * n + i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) out[b] = s;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Spectrum generation.
+struct GenArgs {
+  int nx, ny;
+  double dx, dy, k;
+  double zval;            // host distance (used when zdev == nullptr)
+  const double* zdev;     // device distance
+  unsigned kinds;         // bit mask of the spectra to produce
+  int64_t s_plane;        // elements of one S plane ((nx+1) * ny)
+  int64_t hq_kind;        // elements of one quadrant
+  double scale;           // 1 / (LX LY)
+  int slot[NKIND];        // kind -> slot of the S / Hq buffers (-1: not produced)
+};
+
+// Kernel sample of spectrum `kind` for offsets (a, b): r and the phase k r in double
+// precision, the amplitude factors in T.
+template <typename T>
+__device__ __forceinline__ cplx<T> rs_sample(int kind, int a, int b, const GenArgs& g, double z,
+                                             double kz_red) {
+  typedef cplx<T> C;
+  const double X = a * g.dx, Y = b * g.dy;
+  const double rho2 = X * X + Y * Y;
+  const double r = sqrt(rho2 + z * z);
+  double ph = g.k * rho2 / (r + z);
+  ph -= kTwoPi * rint(ph * (1.0 / kTwoPi));
+  ph += kz_red;
+  T sn, cs;
+  xsincos((T)ph, &sn, &cs);
+  const C e = mk(cs, sn);
+  const double C0 = g.dx * g.dy / kTwoPi;
+  const double ir = 1.0 / r, ir2 = ir * ir;
+  // h = C0 z (1/r - i k) e / r^2
+  const C h = cmul(e, mk((T)(C0 * z * ir * ir2), (T)(-C0 * z * g.k * ir2)));
+  if (kind == KH) return h;
+  if (kind == KHX) return cscale(h, (T)(-X / z));
+  if (kind == KHY) return cscale(h, (T)(-Y / z));
+  // dh/dz = C0 e [(1/r^3 - i k / r^2) + z^2 (k^2/r^3 + 3 i k / r^4 - 3 / r^5)]
+  const double ir3 = ir2 * ir, z2 = z * z, k = g.k;
+  const double re = ir3 + z2 * (k * k * ir3 - 3.0 * ir3 * ir2);
+  const double im = -k * ir2 + z2 * 3.0 * k * ir2 * ir2;
+  const C dh = cmul(e, mk((T)(C0 * re), (T)(C0 * im)));
+  if (kind == KDH) return dh;
+  // d/dz[-(X/z) h] = -(X/z)(dh - h/z)
+  const C dmh = csub(dh, cscale(h, (T)(1.0 / z)));
+  return cscale(dmh, kind == KDHX ? (T)(-X / z) : (T)(-Y / z));
+}
+
+__device__ __forceinline__ double reduce_2pi(double x) { return x - kTwoPi * rint(x * (1.0 / kTwoPi)); }
+
+// Generator pass A: for each b in [0, ny) and each kind, FFT along a of the kernel row placed
+// mod LX; keep kx in [0, nx]; store transposed S[kind][kx][b].
+template <typename T, int LX>
+__global__ void __launch_bounds__(rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16))
+k_gen_pass_a(cplx<T>* __restrict__ S, GenArgs g, const cplx<T>* __restrict__ tw) {
+  typedef cplx<T> C;
+  constexpr int ROWS = rows_transp<LX, sizeof(cplx<T>)>();
+  constexpr int TT = LX / 16;
+  constexpr int SR = srow(LX);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int team = threadIdx.x / TT, t = threadIdx.x % TT;
+  const int b0 = blockIdx.x * ROWS;
+  const int b = b0 + team;
+  const double z = g.zdev ? *g.zdev : g.zval;
+  const double kz_red = reduce_2pi(g.k * z);
+  C* row = sm + team * SR;
+  for (int kind = 0; kind < NKIND; ++kind) {
+    if (!(g.kinds & (1u << kind))) continue;  // uniform over the block
+    C v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int i = t + q * TT;
+      const int a = i < g.nx ? i : i - LX;
+      v[q] = (i == g.nx || b >= g.ny) ? mk((T)0, (T)0) : rs_sample<T>(kind, a, b, g, z, kz_red);
+    }
+    team_fft<LX, -1>(v, row, t, tw);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) row[spad(t + q * TT)] = v[q];
+    __syncthreads();
+    C* dst = S + (int64_t)g.slot[kind] * g.s_plane;
+    for (int kx = threadIdx.x; kx <= g.nx; kx += ROWS * TT) {
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r)
+        if (b0 + r < g.ny) dst[(int64_t)kx * g.ny + b0 + r] = sm[r * SR + spad(kx)];
+    }
+    __syncthreads();
+  }
+}
+
+// Generator pass B: for each kx in [0, nx] and kind, FFT along b of the even/odd extension of
+// S[kind][kx][.]; keep ky in [0, ny]; store Hq[kind][kx][ky] * scale.
+template <typename T, int LY>
+__global__ void __launch_bounds__(rows_cols<LY>() * (LY / 16))
+k_gen_pass_b(const cplx<T>* __restrict__ S, cplx<T>* __restrict__ Hq, GenArgs g,
+             const cplx<T>* __restrict__ tw) {
+  typedef cplx<T> C;
+  constexpr int ROWS = rows_cols<LY>();
+  constexpr int TT = LY / 16;
+  constexpr int SR = srow(LY);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int team = threadIdx.x / TT, t = threadIdx.x % TT;
+  const int kx_raw = blockIdx.x * ROWS + team;
+  const bool live = kx_raw <= g.nx;
+  const int kx = live ? kx_raw : g.nx;
+  C* row = sm + team * SR;
+  for (int kind = 0; kind < NKIND; ++kind) {
+    if (!(g.kinds & (1u << kind))) continue;
+    const C* src = S + (int64_t)g.slot[kind] * g.s_plane + (int64_t)kx * g.ny;
+    const bool odd = kind_odd_y(kind);
+    C v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int j = t + q * TT;
+      if (j < g.ny) {
+        v[q] = src[j];
+      } else if (j == g.ny) {
+        v[q] = mk((T)0, (T)0);
+      } else {
+        C s = src[LY - j];
+        v[q] = odd ? mk(-s.x, -s.y) : s;
+      }
+    }
+    team_fft<LY, -1>(v, row, t, tw);
+    if (live) {
+      C* dst = Hq + (int64_t)g.slot[kind] * g.hq_kind + (int64_t)kx * (g.ny + 1);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int ky = t + q * TT;
+        if (ky <= g.ny) dst[ky] = cscale(v[q], (T)g.scale);
+      }
+    }
+  }
+}
+
+}  // namespace xl

@@ -1,0 +1,225 @@
+// Host runtime: error strings, twiddle tables, workspaces, table cache.
+#include <cstdlib>
+#include <cstring>
+#include <list>
+#include <map>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+#include <cmath>
+
+#include "xl_runtime.h"
+
+namespace xl {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+xl_status fail(xl_status code, const std::string& msg) {
+  set_error(msg);
+  return code;
+}
+
+xl_status cuda_status(cudaError_t e, const char* where) {
+  cudaGetLastError();  // clear a sticky launch error so the next call starts clean
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  set_error(m);
+  return e == cudaErrorMemoryAllocation ? XL_ERR_NOMEM : XL_ERR_CUDA;
+}
+
+size_t dtype_csize(int dtype) { return dtype == XL_C128 ? 16 : 8; }
+
+namespace {
+
+struct Entry {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  cudaEvent_t ready = nullptr;
+  cudaStream_t owner = nullptr;
+  std::list<std::string>::iterator lru_it;
+};
+
+struct DeviceState {
+  std::map<std::pair<int, int>, void*> tw;                        // (L, dtype) -> table
+  std::map<std::pair<cudaStream_t, int>, std::pair<void*, size_t>> ws;  // workspaces
+  std::unordered_map<std::string, Entry> cache;
+  std::list<std::string> lru;  // front = most recent
+  size_t cache_bytes = 0;
+};
+
+std::mutex g_mu;
+std::map<int, DeviceState> g_dev;
+std::map<const void*, size_t> g_smem_set;
+
+size_t cache_cap() {
+  static size_t cap = [] {
+    const char* e = std::getenv("XL_CACHE_BYTES");
+    return e ? (size_t)std::strtoull(e, nullptr, 10) : (size_t)8 << 30;
+  }();
+  return cap;
+}
+
+DeviceState& cur(int* dev_out = nullptr) {
+  int d = 0;
+  cudaGetDevice(&d);
+  if (dev_out) *dev_out = d;
+  return g_dev[d];
+}
+
+}  // namespace
+
+xl_status smem_attr(const void* func, size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_smem_set.find(func);
+  if (it != g_smem_set.end() && it->second >= bytes) return XL_OK;
+  XL_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  g_smem_set[func] = bytes;
+  return XL_OK;
+}
+
+xl_status twiddles(int L, int dtype, const void** out) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  DeviceState& st = cur();
+  auto key = std::make_pair(L, dtype);
+  auto it = st.tw.find(key);
+  if (it != st.tw.end()) {
+    *out = it->second;
+    return XL_OK;
+  }
+  std::vector<double> w(2 * (size_t)L);
+  for (int m = 0; m < L; ++m) {
+    // exp(-2 pi i m / L) in double precision, rounded once to the table's precision
+    double ang = -kTwoPi * (double)m / (double)L;
+    w[2 * m] = std::cos(ang);
+    w[2 * m + 1] = std::sin(ang);
+  }
+  void* d = nullptr;
+  size_t bytes = (size_t)L * dtype_csize(dtype);
+  XL_CUDA_TRY(cudaMalloc(&d, bytes));
+  if (dtype == XL_C128) {
+    XL_CUDA_TRY(cudaMemcpy(d, w.data(), bytes, cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> f(2 * (size_t)L);
+    for (size_t i = 0; i < f.size(); ++i) f[i] = (float)w[i];
+    XL_CUDA_TRY(cudaMemcpy(d, f.data(), bytes, cudaMemcpyHostToDevice));
+  }
+  st.tw[key] = d;
+  *out = d;
+  return XL_OK;
+}
+
+xl_status workspace(cudaStream_t stream, size_t bytes, void** out, int slot) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  DeviceState& st = cur();
+  auto& e = st.ws[std::make_pair(stream, slot)];
+  if (e.second < bytes) {
+    if (e.first) {
+      XL_CUDA_TRY(cudaStreamSynchronize(stream));
+      XL_CUDA_TRY(cudaFree(e.first));
+      e.first = nullptr;
+      e.second = 0;
+    }
+    size_t n = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    cudaError_t err = cudaMalloc(&p, n);
+    if (err != cudaSuccess) return cuda_status(err, "workspace cudaMalloc");
+    e.first = p;
+    e.second = n;
+  }
+  *out = e.first;
+  return XL_OK;
+}
+
+xl_status cached_table(const std::string& key, size_t bytes, cudaStream_t stream,
+                       const std::function<xl_status(void*)>& gen, void** out) {
+  std::unique_lock<std::mutex> lk(g_mu);
+  int dev = 0;
+  DeviceState& st = cur(&dev);
+  auto it = st.cache.find(key);
+  if (it != st.cache.end()) {
+    Entry& e = it->second;
+    st.lru.erase(e.lru_it);
+    st.lru.push_front(key);
+    e.lru_it = st.lru.begin();
+    if (e.owner != stream) XL_CUDA_TRY(cudaStreamWaitEvent(stream, e.ready, 0));
+    *out = e.ptr;
+    return XL_OK;
+  }
+  // evict least-recently-used entries until the new one fits under the cap
+  while (!st.lru.empty() && st.cache_bytes + bytes > cache_cap()) {
+    std::string victim = st.lru.back();
+    st.lru.pop_back();
+    Entry& v = st.cache[victim];
+    XL_CUDA_TRY(cudaEventSynchronize(v.ready));
+    XL_CUDA_TRY(cudaFree(v.ptr));
+    XL_CUDA_TRY(cudaEventDestroy(v.ready));
+    st.cache_bytes -= v.bytes;
+    st.cache.erase(victim);
+  }
+  Entry e;
+  e.bytes = bytes;
+  e.owner = stream;
+  cudaError_t err = cudaMalloc(&e.ptr, bytes);
+  if (err != cudaSuccess) return cuda_status(err, "spectrum cache cudaMalloc");
+  XL_CUDA_TRY(cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming));
+  lk.unlock();
+  xl_status s = gen(e.ptr);
+  lk.lock();
+  if (s != XL_OK) {
+    cudaFree(e.ptr);
+    cudaEventDestroy(e.ready);
+    return s;
+  }
+  XL_CUDA_TRY(cudaEventRecord(e.ready, stream));
+  st.lru.push_front(key);
+  e.lru_it = st.lru.begin();
+  st.cache_bytes += bytes;
+  st.cache[key] = e;
+  *out = e.ptr;
+  return XL_OK;
+}
+
+}  // namespace xl
+
+using namespace xl;
+
+extern "C" {
+
+const char* xl_version(void) { return "xl 0.1 (sm_103a)"; }
+
+const char* xl_last_error(void) { return g_last_error.c_str(); }
+
+xl_status xl_cache_clear(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int dev0 = 0;
+  cudaGetDevice(&dev0);
+  for (auto& kv : g_dev) {
+    XL_CUDA_TRY(cudaSetDevice(kv.first));
+    XL_CUDA_TRY(cudaDeviceSynchronize());
+    DeviceState& st = kv.second;
+    for (auto& c : st.cache) {
+      cudaFree(c.second.ptr);
+      cudaEventDestroy(c.second.ready);
+    }
+    st.cache.clear();
+    st.lru.clear();
+    st.cache_bytes = 0;
+    for (auto& w : st.ws) cudaFree(w.second.first);
+    st.ws.clear();
+  }
+  XL_CUDA_TRY(cudaSetDevice(dev0));
+  return XL_OK;
+}
+
+int64_t xl_cache_bytes(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int64_t n = 0;
+  for (auto& kv : g_dev) {
+    n += (int64_t)kv.second.cache_bytes;
+    for (auto& w : kv.second.ws) n += (int64_t)w.second.second;
+  }
+  return n;
+}
+
+}  // extern "C"

@@ -1,0 +1,40 @@
+// Host-side runtime of the xl library: twiddle tables, per-stream workspaces and the cache of
+// transfer spectra / chirp tables. All state is per device and guarded by one mutex.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <functional>
+#include <string>
+
+#include "xl_common.cuh"
+
+namespace xl {
+
+// Table of exp(-2 pi i m / L), m < L, in the precision of dtype (float2 or double2), computed in
+// double precision on the host. Created on first use (synchronous upload).
+xl_status twiddles(int L, int dtype, const void** out);
+
+// Workspace of at least `bytes` for `stream` on the current device. Growing it synchronises the
+// device (cudaFree); the pointer stays valid until the next call that grows it or xl_cache_clear.
+xl_status workspace(cudaStream_t stream, size_t bytes, void** out, int slot = 0);
+
+// Cache of generated tables. The key is an opaque byte string built by the caller. On a miss
+// the buffer is allocated (evicting least-recently-used entries above the byte cap), `gen` is
+// enqueued on `stream` to fill it, and an event is recorded; on a hit from another stream the
+// stream waits on that event.
+xl_status cached_table(const std::string& key, size_t bytes, cudaStream_t stream,
+                       const std::function<xl_status(void*)>& gen, void** out);
+
+// Key helper: appends the raw bytes of a value.
+template <typename V> inline void key_put(std::string& k, const V& v) {
+  k.append(reinterpret_cast<const char*>(&v), sizeof(V));
+}
+
+// Sets the dynamic shared memory limit of a kernel once (per process).
+xl_status smem_attr(const void* func, size_t bytes);
+
+size_t dtype_csize(int dtype);  // bytes of one complex element
+
+}  // namespace xl
