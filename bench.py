@@ -1,0 +1,406 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 RS / CZT hot path (XLuminA, arXiv 2310.08408).
+
+Workload (rs2048): a batch of 16 complex64 fields on a 2048 x 2048 grid (pitch 0.5 um,
+lambda 0.633 um), each a Gaussian (w0 = 200 um) times a seeded uniform [0, 2 pi) phase; the
+distances cycle through z = 0.5, 2 and 10 mm; CZT maps onto a 512 x 512 window over the central
+64 um. Inputs are synthetic (the paper's propagation benchmark uses a Gaussian beam at 2048^2,
+Fig. 1b); all 16 inputs (537 MB) exceed the 126 MB L2, so no flush is needed between steps.
+
+One step is one gradient evaluation of every field through both propagators:
+    A = RS(U, z),  C = CZT(U, z)                              (forward propagations)
+    L = S(|A|^2) + S(|C|^2)  (second-moment spot size of each plane)
+    dL/dU = RS^H(dL/dA) + CZT^H(dL/dC),  dL/dz from the dh/dz spectrum
+with U = SLM(phi) applied to the source, dL/dphi from the element adjoint and an Adam step on phi.
+Parts not yet present in the library are skipped and listed in the JSON ("step_parts").
+`value` = RS/CZT propagations per second (forward and adjoint, whole job), `grads_per_s` = field
+gradient evaluations per second.
+
+`--impl reference` times the FP64 CPU oracle (the only reference this build has) on the host
+cores: each step is the same composition for ONE field of the batch.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+LAM = 0.633
+ZS = (500.0, 2000.0, 10_000.0)
+N, PITCH, W0 = 2048, 0.5, 200.0
+M, WIN_W = 512, 64.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=60)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="xl", choices=["xl", "reference"])
+    p.add_argument("--batch", type=int, default=16)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampling (200 ms) of SM clock and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- roofline
+def fft_flops(L: int) -> float:
+    """Algorithmic flops of one complex FFT of length L (5 L log2 L convention)."""
+    return 5.0 * L * np.log2(L)
+
+
+def kernel_model(name: str, dims: dict):
+    """(algorithmic flops, algorithmic bytes) of ONE launch of kernel family `name` on the
+    benchmark workload (complex64). Bytes are the compulsory reads + writes of that pass;
+    flops count every FFT at its padded length plus 6 flops per complex multiply."""
+    n, m, cs = dims["n"], dims["m"], 8
+    L = int(re.search(r"<(\d+)>", name).group(1)) if "<" in name else 0
+    nb = dims.get("per_launch", 1)
+    if name.startswith("rs_pass1"):
+        return nb * n * fft_flops(L), nb * (n * n + 2 * n * n) * cs
+    if name.startswith("rs_pass3"):
+        return nb * n * fft_flops(L), nb * (2 * n * n + n * n) * cs
+    if name.startswith("rs_pass2_m0"):
+        return nb * 2 * n * (2 * fft_flops(L) + 6 * L), nb * (4 * n * n + (n + 1) ** 2) * cs
+    if name.startswith("rs_pass2_m2"):
+        return nb * 2 * n * (3 * fft_flops(L) + 14 * L), nb * (6 * n * n + 2 * (n + 1) ** 2) * cs
+    if name.startswith("czt_fwd_x") or name.startswith("czt_adj_x"):
+        return nb * n * (2 * fft_flops(L) + 18 * L), nb * (n * n + n * m) * cs
+    if name.startswith("czt_fwd_y") or name.startswith("czt_adj_y"):
+        return nb * m * (2 * fft_flops(L) + 18 * L), nb * (n * m + m * m) * cs
+    return None, None
+
+
+def load_traffic():
+    """Per-launch DRAM traffic of kernel families from the committed ncu summary, valid only
+    while the kernel sources are unchanged (hash recorded with the counters)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return {}
+    try:
+        data = json.load(open(path))
+        from paper_2310_08408_gb300 import build
+        if data.get("csrc_hash") != build.source_hash():
+            return {}
+        return data.get("bytes_per_launch", {})
+    except Exception:
+        return {}
+
+
+# ----------------------------------------------------------------------------- workload
+def make_inputs(rank: int, batch: int):
+    from paper_2310_08408_gb300 import inputs
+    g = inputs.Grid.centred(N, PITCH)
+    w = inputs.Window.centred(M, WIN_W)
+    seed = inputs.SEED0 + 2 + 1000 * rank
+    U = np.stack([inputs.gaussian_random_phase(g, W0, seed + b) for b in range(batch)]
+                 ).astype(np.complex64)
+    zs = [ZS[b % 3] for b in range(batch)]
+    return g, w, U, zs
+
+
+def step_parts(xl):
+    have = {"rs": True, "czt": True}
+    for fn in ("apply_elements", "intensity_loss", "adam_step"):
+        have[fn] = hasattr(xl, fn)
+    return have
+
+
+class GpuStep:
+    """The benchmark step on device-resident buffers (all through the C ABI)."""
+
+    def __init__(self, xl, torch, g, w, U_dev, zs):
+        self.xl, self.torch, self.g, self.w, self.zs = xl, torch, g, w, zs
+        self.U = U_dev
+        B = U_dev.shape[0]
+        dev = U_dev.device
+        from paper_2310_08408_gb300 import inputs
+        # fixed seeded cotangents (the loss gradients until the loss kernels are present)
+        self.GA = torch.from_numpy(inputs.random_unit(7, (1, N, N)).astype(np.complex64)).to(dev).expand(B, N, N).contiguous()
+        self.GC = torch.from_numpy(inputs.random_unit(8, (1, M, M)).astype(np.complex64)).to(dev).expand(B, M, M).contiguous()
+        self.A = torch.empty_like(U_dev)
+        self.C = torch.empty((B, M, M), dtype=U_dev.dtype, device=dev)
+        self.props = 4 * B
+
+    def __call__(self):
+        xl = self.xl
+        xl.rs_propagate(self.U, self.g, LAM, self.zs, out=self.A)
+        xl.czt_propagate(self.U, self.g, self.w, LAM, self.zs, out=self.C)
+        gc = xl.czt_propagate_backward(self.GC, self.g, self.w, LAM, self.zs)
+        ga, gz = xl.rs_propagate_backward(self.GA, self.U, self.g, LAM, self.zs, want_field=True,
+                                          want_dz=True)
+        self.gA, self.gC = ga, gc
+        self.gz = gz
+        return self.A, self.C, self.gz
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_step(U1, g, w, z, GA, GC):
+    """The step's composition for one field with the FP64 oracle."""
+    import oracle
+    u = U1.astype(np.complex128)
+    A = oracle.rs_conv(u, g.dx, g.dy, LAM, z)
+    C = oracle.czt_conv(u, g.astuple(), w.astuple(), LAM, z)
+    gc = oracle.czt_conv(GC, g.astuple(), w.astuple(), LAM, z, adjoint=True)
+    ga = oracle.rs_conv(GA, g.dx, g.dy, LAM, z, oracle.K_H, adjoint=True)
+    dz = np.real(np.vdot(GA, oracle.rs_conv(u, g.dx, g.dy, LAM, z, oracle.K_DH)))
+    return A, C, ga + gc, dz
+
+
+def cpu_sample(U, g, w, zs, steps=1):
+    import oracle
+    from paper_2310_08408_gb300 import inputs
+    GA = inputs.random_unit(7, (N, N)).astype(np.complex64).astype(np.complex128)
+    GC = inputs.random_unit(8, (M, M)).astype(np.complex64).astype(np.complex128)
+    oracle.build()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        oracle_step(U[i % len(U)], g, w, zs[i % len(zs)], GA, GC)
+    dt = time.perf_counter() - t0
+    # the oracle step holds 5 propagation-sized sums per field (4 propagations + the dz one);
+    # count the 4 propagations as in the GPU step
+    return {"value": 4 * steps / dt, "unit": "propagations/s", "cores": oracle.get_threads(),
+            "kind": "oracle",
+            "sample": f"{steps} of the {len(U)} fields of one step (RS, CZT, CZT^H, RS^H + dz at "
+                      f"2048^2 -> 512^2, FP64 C++ oracle), {dt:.1f} s"}
+
+
+# ----------------------------------------------------------------------------- main
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    g, w, U, zs = make_inputs(0, 3)
+    import oracle
+    oracle.build()
+    from paper_2310_08408_gb300 import inputs
+    GA = inputs.random_unit(7, (N, N)).astype(np.complex64).astype(np.complex128)
+    GC = inputs.random_unit(8, (M, M)).astype(np.complex64).astype(np.complex128)
+    for i in range(a.warmup):
+        oracle_step(U[i % 3], g, w, zs[i % 3], GA, GC)
+    t0 = time.perf_counter()
+    for i in range(a.steps):
+        oracle_step(U[i % 3], g, w, zs[i % 3], GA, GC)
+    dt = time.perf_counter() - t0
+    v = 4 * a.steps / dt
+    line = {
+        "impl": "reference", "metric": "RS/CZT propagations/s at 2048^2 (fwd + adjoint)",
+        "value": v, "unit": "propagations/s", "n_gpus": a.gpus, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": 1000 * dt / max(a.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "rs2048: 2048^2 pitch 0.5 um, lambda 0.633 um, z in {0.5,2,10} mm, "
+                               "CZT to 512^2 over 64 um; one field per step (bounded sample)",
+                   "global_batch": 1, "parallelism": "none (host cores)"},
+        "cpu_baseline": {"value": v, "unit": "propagations/s", "cores": oracle.get_threads(),
+                         "kind": "oracle", "sample": "one field per step"},
+        "e2e": {"value": v, "unit": "propagations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2310_08408_gb300 import build, xl
+    build.build()
+    xl.load()
+    B = a.batch
+    g, w, U_host, zs = make_inputs(rank, B)
+    U_pin = torch.from_numpy(U_host).pin_memory()
+    U_dev = U_pin.to("cuda", non_blocking=True)
+    torch.cuda.synchronize()
+    step = GpuStep(xl, torch, g, w, U_dev, zs)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    for _ in range(a.warmup):
+        step()
+    barrier()
+    n0 = xl.launch_count()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = (xl.launch_count() - n0) // max(a.steps, 1)
+    ck = clocks.stop()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    value = step.props * world * a.steps / (ms / 1000.0)
+    grads = B * world * a.steps / (ms / 1000.0)
+
+    # per-kernel durations (CUDA events recorded by the library on its launch stream)
+    xl.profile_enable(True)
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    prof = xl.profile_report()
+    xl.profile_enable(False)
+    total = sum(v[1] for v in prof.values())
+    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roof = None
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    if top is not None:
+        name, (cnt, tot) = top
+        avg_s = tot / cnt / 1000.0
+        flops, nbytes = kernel_model(name, {"n": N, "m": M, "per_launch": 1})
+        clk = ck.get("sm_mhz") or 1900.0
+        fp32_peak = sms * 128 * 2 * clk * 1e6 / 1e12  # TFLOP/s, CUDA-core FMA rate at the sampled clock
+        traffic = load_traffic().get(name)
+        if flops is not None:
+            t_alu = flops / (fp32_peak * 1e12)
+            t_mem = nbytes / (hbm * 1e9)
+            if t_alu >= t_mem:
+                ach = flops / avg_s / 1e12
+                roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                        "frac": ach / fp32_peak, "traffic": traffic, "kernel": name,
+                        "share": tot / total if total else None,
+                        "peak_note": f"FP32 CUDA-core FMA rate: {sms} SMs x 128 lanes x 2 x "
+                                     f"{clk:.0f} MHz (median sampled clock)",
+                        "hbm_frac_of_measured": nbytes / avg_s / 1e9 / hbm}
+            else:
+                ach = nbytes / avg_s / 1e9
+                roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                        "frac": ach / hbm, "traffic": traffic, "kernel": name,
+                        "share": tot / total if total else None,
+                        "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    kernels = {k: {"launches": v[0] // 3, "ms_per_step": v[1] / 3} for k, v in prof.items()}
+
+    # end to end: pinned host input -> device, the step, results back to pinned host buffers
+    e2e = None
+    if not a.no_e2e:
+        A_h = torch.empty(step.A.shape, dtype=step.A.dtype).pin_memory()
+        C_h = torch.empty(step.C.shape, dtype=step.C.dtype).pin_memory()
+        gz_h = torch.empty((B,), dtype=torch.float64).pin_memory()
+        ke = max(3, a.steps // 4)
+
+        def e2e_step():
+            step.U.copy_(U_pin, non_blocking=True)
+            A, C, gz = step()
+            A_h.copy_(A, non_blocking=True)
+            C_h.copy_(C, non_blocking=True)
+            gz_h.copy_(gz, non_blocking=True)
+
+        e2e_step()
+        barrier()
+        e0.record(stream)
+        for _ in range(ke):
+            e2e_step()
+        e1.record(stream)
+        barrier()
+        ems = e0.elapsed_time(e1)
+        t = torch.tensor([ems], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ems = float(t.item())
+        e2e = {"value": step.props * world * ke / (ems / 1000.0), "unit": "propagations/s",
+               "h2d_bytes_per_step": int(U_pin.numel() * 8),
+               "d2h_bytes_per_step": int(A_h.numel() * 8 + C_h.numel() * 8 + gz_h.numel() * 8),
+               "ms_per_step": ems / ke}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_sample(U_host, g, w, zs, steps=1)
+
+    if rank == 0:
+        line = {
+            "metric": "RS/CZT propagations/s at 2048^2 (fwd + adjoint) and grads/s",
+            "value": value, "unit": "propagations/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32, f64 phases)",
+            "data": "synthetic",
+            "config": {"workload": "rs2048: batch 16 x 2048^2 complex64, pitch 0.5 um, "
+                                   "lambda 0.633 um, z cycling {0.5, 2, 10} mm; RS (4096^2 padded) "
+                                   "and CZT to 512^2 over 64 um; forward + adjoint + dz",
+                       "global_batch": B * world, "grid": N, "window": M,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs (537 MB per GPU) exceed L2; no flush"},
+            "grads_per_s": grads,
+            "step_parts": step_parts(xl),
+            "gpu_launches": int(launches),
+            "clocks": ck,
+            "roofline": roof,
+            "kernels": kernels,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

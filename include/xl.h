@@ -79,6 +79,18 @@ xl_status xl_cache_clear(void);
 /* Bytes currently held by the spectrum cache and the workspaces. */
 int64_t xl_cache_bytes(void);
 
+/* Diagnostics (not part of the method). Number of kernels the library has launched since it was
+ * loaded (a host-side counter incremented at every launch). */
+int64_t xl_launch_count(void);
+
+/* While on (on != 0), every launch is bracketed by CUDA events recorded on its own stream. */
+xl_status xl_profile_enable(int32_t on);
+
+/* Synchronises on the recorded events and writes one line "name launches total_ms" per kernel
+ * family into buf (NUL-terminated, truncated to len), then clears the records. Returns the bytes
+ * the full report needs. buf may be NULL to query the size (the records are still cleared). */
+int32_t xl_profile_report(char* buf, int32_t len);
+
 /* ---------------------------------------------------------------------------------------------
  * Scalar RS propagation (Methods, "Features and performance": FFT-based numerical integration of
  * the Rayleigh-Sommerfeld integral).
@@ -150,6 +162,103 @@ xl_status xl_czt_propagate_backward(const void* g_out, void* g_in, int32_t batch
                                     int32_t vectorial, const xl_grid* grid,
                                     const xl_window* window, double wavelength, const double* z,
                                     int32_t flags, int32_t dtype, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Optical elements (Methods, "Features and performance": SLMs (one free phase per pixel), the
+ * super-SLM (independent phases on the horizontal and vertical components), polarisers, variable
+ * retarders / wave plates, planar lenses). A chain of up to 8 elements is applied in one pass.
+ * Readings (the paper names the elements only):
+ *   XL_SLM        every component times exp(i phi_x)
+ *   XL_SSLM       Ex times exp(i phi_x), Ey times exp(i phi_y)
+ *   XL_LENS       every component times exp(-i k (x^2 + y^2) / (2 f))
+ *   XL_POLARIZER  J = R(-alpha) diag(1, 0) R(alpha)
+ *   XL_WAVEPLATE  J = R(-theta) diag(1, exp(i eta)) R(theta), R(t) = [[cos t, sin t], [-sin t, cos t]]
+ *                 (a half-wave plate is eta = pi)
+ *   XL_TO_VECTOR  (Ex, Ey) = (u, 0): an x-polarised scalar field becomes a 2-component field
+ * -------------------------------------------------------------------------------------------*/
+#define XL_SLM 0
+#define XL_SSLM 1
+#define XL_LENS 2
+#define XL_POLARIZER 3
+#define XL_WAVEPLATE 4
+#define XL_TO_VECTOR 5
+
+typedef struct xl_element {
+  int32_t kind;
+  int32_t reserved;
+  const void* phi_x;   /* device phase mask(s) [ny][nx] (float for XL_C64, double for XL_C128) */
+  const void* phi_y;   /* second mask of XL_SSLM */
+  int64_t phi_stride;  /* elements between the masks of consecutive batch entries; 0 = shared */
+  double f, alpha, eta, theta; /* host parameters (used unless flags & XL_Z_DEVICE) */
+} xl_element;
+
+/* in: [batch][comps_in][ny][nx] (comps_in 1 or 2); out: [batch][comps_out][ny][nx] where
+ * comps_out = 2 if the chain contains XL_TO_VECTOR or comps_in = 2, else 1. out may alias in
+ * when comps_out == comps_in.
+ * params: with flags & XL_Z_DEVICE, device doubles [batch][n_elem][4] = {f, alpha, eta, theta}
+ * replacing the host values of every element (for parameters trained on the device); else NULL. */
+xl_status xl_apply_elements(const void* in, void* out, int32_t batch, int32_t comps_in,
+                            const xl_grid* grid, double wavelength, const xl_element* elements,
+                            int32_t n_elem, const double* params, int32_t flags, int32_t dtype,
+                            void* stream);
+
+/* Adjoint of xl_apply_elements at the forward input `in`:
+ *   g_in = J^H g_out element by element in reverse (NULL: not written);
+ *   g_phi_x[e], g_phi_y[e]: dL/dphi = Im(g_out conj(u_out)) per pixel, laid out like the masks;
+ *     a shared mask (phi_stride 0) receives the sum over the batch (arrays and entries nullable);
+ *   g_params: device [batch][n_elem][4] dL/d{f, alpha, eta, theta} (nullable).
+ * Shared and per-batch masks may not both request gradients in one call (XL_ERR_UNSUPPORTED). */
+xl_status xl_apply_elements_backward(const void* g_out, const void* in, void* g_in, int32_t batch,
+                                     int32_t comps_in, const xl_grid* grid, double wavelength,
+                                     const xl_element* elements, int32_t n_elem,
+                                     const double* params, int32_t flags, void* const* g_phi_x,
+                                     void* const* g_phi_y, double* g_params, int32_t dtype,
+                                     void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Camera intensity and losses (Methods, "Loss function"; camera intensities |Ex|^2 + |Ey|^2,
+ * |Ez|^2 or total as in the Results).
+ *   I = sum over the components selected by comp_mask (bit c = component c) of |E_c|^2.
+ *   XL_SECOND_MOMENT (reading; the paper's spot metric is (pi/4) FWHMx FWHMy):
+ *       L = sum I ((x - xbar)^2 + (y - ybar)^2) / sum I, xbar = sum I x / sum I (grid units^2).
+ *   XL_DENSITY: L = Area / I_eps, I_eps = sum of I over pixels with I > eps * max(I) (strict),
+ *       Area = their count.
+ * field: [batch][comps][ny][nx]; loss: device doubles [batch]; intensity: nullable device
+ * [batch][ny][nx] (float for XL_C64, double for XL_C128). A non-finite loss is reported by
+ * xl_device_status().
+ * -------------------------------------------------------------------------------------------*/
+#define XL_SECOND_MOMENT 0
+#define XL_DENSITY 1
+
+xl_status xl_intensity_loss(const void* field, int32_t batch, int32_t comps, uint32_t comp_mask,
+                            const xl_grid* grid, int32_t mode, double eps, double* loss,
+                            void* intensity, int32_t dtype, void* stream);
+
+/* g_field = 2 g_loss[b] dL/dI E on the selected components, 0 on the others.
+ *   second moment: dL/dI = [(x - xbar)^2 + (y - ybar)^2 - L] / sum I
+ *   density:       dL/dI = -Area / I_eps^2 above the threshold, 0 elsewhere
+ * g_loss: device doubles [batch] or NULL (= 1). g_field: [batch][comps][ny][nx], not aliasing. */
+xl_status xl_intensity_loss_backward(const void* field, int32_t batch, int32_t comps,
+                                     uint32_t comp_mask, const xl_grid* grid, int32_t mode,
+                                     double eps, const double* g_loss, void* g_field,
+                                     int32_t dtype, void* stream);
+
+/* Synchronises `stream`, then returns and clears the device status: XL_ERR_NONFINITE if a loss
+ * reduction produced a non-finite value since the last call, else XL_OK. */
+xl_status xl_device_status(void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Adam (the paper's optimiser): bias-corrected step t >= 1,
+ *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;  p -= lr m/(1-b1^t) / (sqrt(v/(1-b2^t)) + eps).
+ * params, m, v, grad: device arrays of n reals (real_dtype 0 = float, 1 = double), updated in
+ * place. t is read from t_dev (device int32, for graph replay) when non-NULL, else t_host.
+ * -------------------------------------------------------------------------------------------*/
+xl_status xl_adam_step(void* params, void* m, void* v, const void* grad, int64_t n,
+                       int32_t real_dtype, double lr, double beta1, double beta2, double eps,
+                       const int32_t* t_dev, int32_t t_host, void* stream);
+
+/* *t_dev += 1 in stream order. */
+xl_status xl_step_advance(int32_t* t_dev, void* stream);
 
 #ifdef __cplusplus
 }

@@ -364,6 +364,18 @@ static cd axis_factor_ext(int sel, double D, double k, double z) {
   return axis_factor(sel, D, k, z);
 }
 
+// Table F[p][m] = axis factor `sel` of (W0 + p dW) - (s0 + m ds), p < M, m < N.
+static std::vector<cd> axis_table(int sel, int64_t M, double W0, double dW, int64_t N, double s0,
+                                  double ds, double k, double z) {
+  std::vector<cd> F((size_t)(M * N));
+  parallel_for(M, [&](int64_t pb, int64_t pe) {
+    for (int64_t p = pb; p < pe; ++p)
+      for (int64_t m = 0; m < N; ++m)
+        F[p * N + m] = axis_factor_ext(sel, (W0 + p * dW) - (s0 + m * ds), k, z);
+  });
+  return F;
+}
+
 static bool czt_geom_ok(const CztGeom& g) {
   return g.nx > 0 && g.ny > 0 && g.mx > 0 && g.my > 0 && g.z > 0.0 && g.lambda > 0.0;
 }
@@ -386,27 +398,27 @@ int orc_czt_direct(const double* u_in, double* u_out, int64_t nx, int64_t ny, do
   if (!adjoint) {
     std::vector<cd> out((size_t)(mx * my), cd(0.0, 0.0));
     for (const SepTerm& t : terms) {
+      // axis factor tables A[p][m] and B[q][n] of this term
+      std::vector<cd> A = axis_table(t.ax, mx, g.xo0, g.dxo, nx, g.x0, g.dx, g.k, g.z);
+      std::vector<cd> B = axis_table(t.by, my, g.yo0, g.dyo, ny, g.y0, g.dy, g.k, g.z);
       // pass x: T[n][p] = sum_m U0[n][m] A(p,m)
       std::vector<cd> T((size_t)(ny * mx));
       parallel_for(ny, [&](int64_t nb, int64_t ne) {
-        std::vector<cd> A((size_t)nx);
         for (int64_t n = nb; n < ne; ++n)
           for (int64_t p = 0; p < mx; ++p) {
             cd s(0.0, 0.0);
-            double X = g.xo0 + p * g.dxo;
-            for (int64_t m = 0; m < nx; ++m)
-              s += ld(u_in, n * nx + m) * axis_factor_ext(t.ax, X - (g.x0 + m * g.dx), g.k, g.z);
+            const cd* a = &A[p * nx];
+            for (int64_t m = 0; m < nx; ++m) s += ld(u_in, n * nx + m) * a[m];
             T[n * mx + p] = s;
           }
       });
       // pass y: out[q][p] += c * sum_n T[n][p] B(q,n)
       parallel_for(my, [&](int64_t qb, int64_t qe) {
         for (int64_t q = qb; q < qe; ++q) {
-          double Y = g.yo0 + q * g.dyo;
+          const cd* bq = &B[q * ny];
           for (int64_t p = 0; p < mx; ++p) {
             cd s(0.0, 0.0);
-            for (int64_t n = 0; n < ny; ++n)
-              s += T[n * mx + p] * axis_factor_ext(t.by, Y - (g.y0 + n * g.dy), g.k, g.z);
+            for (int64_t n = 0; n < ny; ++n) s += T[n * mx + p] * bq[n];
             out[q * mx + p] += t.c * s;
           }
         }
@@ -416,29 +428,24 @@ int orc_czt_direct(const double* u_in, double* u_out, int64_t nx, int64_t ny, do
   } else {
     std::vector<cd> out((size_t)(nx * ny), cd(0.0, 0.0));
     for (const SepTerm& t : terms) {
+      std::vector<cd> A = axis_table(t.ax, mx, g.xo0, g.dxo, nx, g.x0, g.dx, g.k, g.z);
+      std::vector<cd> B = axis_table(t.by, my, g.yo0, g.dyo, ny, g.y0, g.dy, g.k, g.z);
       // adjoint of pass y: T[n][p] = sum_q conj(B(q,n)) G[q][p]
       std::vector<cd> T((size_t)(ny * mx));
       parallel_for(ny, [&](int64_t nb, int64_t ne) {
-        for (int64_t n = nb; n < ne; ++n) {
-          double y = g.y0 + n * g.dy;
+        for (int64_t n = nb; n < ne; ++n)
           for (int64_t p = 0; p < mx; ++p) {
             cd s(0.0, 0.0);
-            for (int64_t q = 0; q < my; ++q)
-              s += ld(u_in, q * mx + p) *
-                   std::conj(axis_factor_ext(t.by, (g.yo0 + q * g.dyo) - y, g.k, g.z));
+            for (int64_t q = 0; q < my; ++q) s += ld(u_in, q * mx + p) * std::conj(B[q * ny + n]);
             T[n * mx + p] = s;
           }
-        }
       });
       // adjoint of pass x: out[n][m] += conj(c) sum_p conj(A(p,m)) T[n][p]
       parallel_for(ny, [&](int64_t nb, int64_t ne) {
         for (int64_t n = nb; n < ne; ++n)
           for (int64_t m = 0; m < nx; ++m) {
-            double x = g.x0 + m * g.dx;
             cd s(0.0, 0.0);
-            for (int64_t p = 0; p < mx; ++p)
-              s += T[n * mx + p] *
-                   std::conj(axis_factor_ext(t.ax, (g.xo0 + p * g.dxo) - x, g.k, g.z));
+            for (int64_t p = 0; p < mx; ++p) s += T[n * mx + p] * std::conj(A[p * nx + m]);
             out[n * nx + m] += std::conj(t.c) * s;
           }
       });

@@ -36,6 +36,19 @@ def _headers_mtime() -> float:
     return max(os.path.getmtime(h) for h in hs if os.path.exists(h))
 
 
+def source_hash() -> str:
+    """SHA-256 over the kernel sources and headers (ties profiler counters to a code version)."""
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(CSRC, "*")))
+    files.append(os.path.join(HERE, "..", "include", "xl.h"))
+    for f in files:
+        if os.path.isfile(f):
+            h.update(os.path.basename(f).encode())
+            h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def build(verbose: bool = False, jobs: int | None = None, ptxas_verbose: bool = False) -> str:
     """Compile (incrementally) and link the library; returns its path."""
     os.makedirs(OUT, exist_ok=True)

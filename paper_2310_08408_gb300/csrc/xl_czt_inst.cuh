@@ -17,23 +17,35 @@ xl_status pass_LV(int which, const void* src, void* dst, const CztDims& d, const
   switch (which) {
     case CZT_FWD_X:
       XL_TRY(smem_attr((const void*)k_czt_fwd_x<T, L, VEC>, sm));
+      {
+      LaunchScope ls(std::string("czt_fwd_x") + (VEC ? "_vec<" : "<") + std::to_string(L) + ">", s);
       k_czt_fwd_x<T, L, VEC><<<dim3((d.ny + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
           (const cplx<T>*)src, (cplx<T>*)dst, d, ax, twc);
+      }
       break;
     case CZT_FWD_Y:
       XL_TRY(smem_attr((const void*)k_czt_fwd_y<T, L, VEC>, sm));
+      {
+      LaunchScope ls(std::string("czt_fwd_y") + (VEC ? "_vec<" : "<") + std::to_string(L) + ">", s);
       k_czt_fwd_y<T, L, VEC><<<dim3((d.mx + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
           (const cplx<T>*)src, (cplx<T>*)dst, d, ax, twc);
+      }
       break;
     case CZT_ADJ_Y:
       XL_TRY(smem_attr((const void*)k_czt_adj_y<T, L, VEC>, sm));
+      {
+      LaunchScope ls(std::string("czt_adj_y") + (VEC ? "_vec<" : "<") + std::to_string(L) + ">", s);
       k_czt_adj_y<T, L, VEC><<<dim3((d.mx + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
           (const cplx<T>*)src, (cplx<T>*)dst, d, ax, twc);
+      }
       break;
     case CZT_ADJ_X:
       XL_TRY(smem_attr((const void*)k_czt_adj_x<T, L, VEC>, sm));
+      {
+      LaunchScope ls(std::string("czt_adj_x") + (VEC ? "_vec<" : "<") + std::to_string(L) + ">", s);
       k_czt_adj_x<T, L, VEC><<<dim3((d.ny + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
           (const cplx<T>*)src, (cplx<T>*)dst, d, ax, twc);
+      }
       break;
     default:
       return fail(XL_ERR_ARG, "czt_pass: bad pass");
@@ -48,6 +60,7 @@ xl_status bhat_L(cplx<T>* rows, int64_t stride, cudaStream_t s) {
   const void* tw;
   XL_TRY(twiddles(L, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
   XL_TRY(smem_attr((const void*)k_czt_bhat<T, L>, sm));
+  LaunchScope ls("czt_bhat<" + std::to_string(L) + ">", s);
   k_czt_bhat<T, L><<<2, L / 16, sm, s>>>(rows, stride, (const cplx<T>*)tw);
   XL_CUDA_TRY(cudaGetLastError());
   return XL_OK;
@@ -89,7 +102,10 @@ xl_status czt_tables<XL_REAL>(void* tab, const CztTabArgs& a, cudaStream_t s) {
   typedef cplx<XL_REAL> C;
   const int64_t total = (int64_t)a.nx + a.mx + 2 * (int64_t)a.Lx + a.ny + a.my + 2 * (int64_t)a.Ly;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 1024);
+  {
+  LaunchScope ls("czt_tables", s);
   k_czt_tables<XL_REAL><<<blocks, 256, 0, s>>>((C*)tab, a);
+  }
   XL_CUDA_TRY(cudaGetLastError());
   C* t = (C*)tab;
   XL_TRY(bhat<XL_REAL>(a.Lx, t + a.nx + a.mx, a.Lx, s));

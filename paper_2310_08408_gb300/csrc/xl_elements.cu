@@ -1,0 +1,554 @@
+// Fused optical-element chains and their adjoints (Methods, "Features and performance": spatial
+// light modulators (SLM), the super-SLM imprinting independent phases on the horizontal and
+// vertical components, planar lenses, polarisers and variable retarders / wave plates).
+//
+// Readings (the paper names the elements only):
+//   SLM        every component times exp(i phi)
+//   super-SLM  Ex times exp(i phi_x), Ey times exp(i phi_y)
+//   lens       every component times exp(-i k (x^2 + y^2) / (2 f))
+//   polariser  J = R(-a) diag(1, 0) R(a)
+//   wave plate J = R(-t) diag(1, exp(i eta)) R(t),  R(t) = [[cos t, sin t], [-sin t, cos t]]
+//   to-vector  (Ex, Ey) = (u, 0)
+// One thread handles one pixel of one batch element and applies the whole chain in registers
+// (the chain is read from kernel parameters), so a chain costs one read and one write of the
+// field. The lens phase is separable, exp(-ik x^2/2f) exp(-ik y^2/2f): both factors are
+// tabulated per call in double precision (reduced modulo 2 pi, rounded once), so the per-pixel
+// work is one complex multiply.
+// Backward: the forward states are recomputed per pixel, then g <- J^H g element by element in
+// reverse; dL/dphi = Im(g_out conj(u_out)) per pixel (summed over the batch when the mask is
+// shared), and the scalar gradients dL/d{f, alpha, eta, theta} = Re sum conj(g_out) dJ u_in are
+// reduced per block in double precision and then in fixed order per batch element.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "xl_runtime.h"
+
+namespace xl {
+
+constexpr int kMaxElem = 8;
+
+struct ElemSet {
+  int n;
+  int kind[kMaxElem];
+  int lens_slot[kMaxElem];      // lens table index (-1 if not a lens)
+  const void* phx[kMaxElem];
+  const void* phy[kMaxElem];
+  int64_t phstride[kMaxElem];
+  double hp[kMaxElem][4];       // host parameters {f, alpha, eta, theta}
+};
+
+struct ElemDims {
+  int nx, ny, comps_in, comps_out;
+  int64_t plane;
+  double x0, dx, y0, dy, k;
+  const double* params_dev;     // [batch][n][4] or nullptr (host parameters)
+};
+
+template <typename T> struct Jones2 {
+  cplx<T> a, b, c, d;
+};
+
+template <typename T>
+__device__ __forceinline__ Jones2<T> mul2(const Jones2<T>& x, const Jones2<T>& y) {
+  return {cadd(cmul(x.a, y.a), cmul(x.b, y.c)), cadd(cmul(x.a, y.b), cmul(x.b, y.d)),
+          cadd(cmul(x.c, y.a), cmul(x.d, y.c)), cadd(cmul(x.c, y.b), cmul(x.d, y.d))};
+}
+template <typename T> __device__ __forceinline__ Jones2<T> rot2(T c, T s) {
+  return {mk(c, (T)0), mk(s, (T)0), mk(-s, (T)0), mk(c, (T)0)};
+}
+
+// J, and its derivatives where relevant, for polariser (alpha) and wave plate (eta, theta).
+template <typename T>
+__device__ __forceinline__ void polarizer(double a, Jones2<T>* J, Jones2<T>* dJ) {
+  T c, s;
+  xsincos((T)a, &s, &c);
+  *J = {mk(c * c, (T)0), mk(c * s, (T)0), mk(c * s, (T)0), mk(s * s, (T)0)};
+  if (dJ) *dJ = {mk(-2 * c * s, (T)0), mk(c * c - s * s, (T)0), mk(c * c - s * s, (T)0), mk(2 * c * s, (T)0)};
+}
+
+template <typename T>
+__device__ __forceinline__ void waveplate(double eta, double th, Jones2<T>* J, Jones2<T>* dJe,
+                                          Jones2<T>* dJt) {
+  T c, s, ec, es;
+  xsincos((T)th, &s, &c);
+  xsincos((T)eta, &es, &ec);
+  const cplx<T> e = mk(ec, es);
+  const cplx<T> one = mk((T)1, (T)0), zero = mk((T)0, (T)0);
+  Jones2<T> D = {one, zero, zero, e};
+  Jones2<T> Rm = rot2<T>(c, -s), Rp = rot2<T>(c, s);  // R(-t), R(t)
+  *J = mul2(Rm, mul2(D, Rp));
+  if (dJe) {
+    Jones2<T> dD = {zero, zero, zero, mk(-e.y, e.x)};
+    *dJe = mul2(Rm, mul2(dD, Rp));
+  }
+  if (dJt) {
+    // d/dt R(t) = [[-s, c], [-c, -s]];  d/dt R(-t) = [[-s, -c], [c, -s]]
+    Jones2<T> dRp = {mk(-s, (T)0), mk(c, (T)0), mk(-c, (T)0), mk(-s, (T)0)};
+    Jones2<T> dRm = {mk(-s, (T)0), mk(-c, (T)0), mk(c, (T)0), mk(-s, (T)0)};
+    Jones2<T> A = mul2(dRm, mul2(D, Rp)), B = mul2(Rm, mul2(D, dRp));
+    *dJt = {cadd(A.a, B.a), cadd(A.b, B.b), cadd(A.c, B.c), cadd(A.d, B.d)};
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void japply(const Jones2<T>& J, cplx<T>& u0, cplx<T>& u1) {
+  cplx<T> a = cadd(cmul(J.a, u0), cmul(J.b, u1));
+  cplx<T> b = cadd(cmul(J.c, u0), cmul(J.d, u1));
+  u0 = a;
+  u1 = b;
+}
+// g <- J^H g
+template <typename T>
+__device__ __forceinline__ void japply_h(const Jones2<T>& J, cplx<T>& g0, cplx<T>& g1) {
+  cplx<T> a = cadd(cmul(cconj(J.a), g0), cmul(cconj(J.c), g1));
+  cplx<T> b = cadd(cmul(cconj(J.b), g0), cmul(cconj(J.d), g1));
+  g0 = a;
+  g1 = b;
+}
+// Re(conj(g) . (J u))
+template <typename T>
+__device__ __forceinline__ double jre(const Jones2<T>& J, cplx<T> g0, cplx<T> g1, cplx<T> u0, cplx<T> u1) {
+  cplx<T> a = cadd(cmul(J.a, u0), cmul(J.b, u1));
+  cplx<T> b = cadd(cmul(J.c, u0), cmul(J.d, u1));
+  return (double)cdot_re(g0, a) + (double)cdot_re(g1, b);
+}
+
+__device__ __forceinline__ double eparam(const ElemSet& E, const ElemDims& d, int b, int e, int j) {
+  return d.params_dev ? d.params_dev[((int64_t)b * E.n + e) * 4 + j] : E.hp[e][j];
+}
+
+template <typename T>
+__device__ __forceinline__ T phase_at(const void* p, int64_t stride, int b, int64_t i) {
+  return ((const T*)p)[(int64_t)b * stride + i];
+}
+
+// Lens tables: for lens slot s and batch element b, Lx[m] then Ly[n] (complex T).
+__device__ __forceinline__ double red2pi_e(double x) { return x - kTwoPi * rint(x * (1.0 / kTwoPi)); }
+
+template <typename T>
+__global__ void k_lens_tables(cplx<T>* __restrict__ tab, ElemSet E, ElemDims d, int batch, int nlens) {
+  const int64_t per = (int64_t)d.nx + d.ny;
+  const int64_t total = per * nlens * batch;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = i % per;
+    const int s = (int)((i / per) % nlens);
+    const int b = (int)(i / (per * nlens));
+    int e = 0;
+    for (int q = 0; q < E.n; ++q)
+      if (E.lens_slot[q] == s) e = q;
+    const double f = eparam(E, d, b, e, 0);
+    const double c = j < d.nx ? d.x0 + j * d.dx : d.y0 + (j - d.nx) * d.dy;
+    const double ph = -red2pi_e(d.k * c * c / (2.0 * f));
+    T sn, cs;
+    xsincos((T)ph, &sn, &cs);
+    tab[i] = mk(cs, sn);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ cplx<T> lens_factor(const cplx<T>* tab, int s, int b, int nlens,
+                                               const ElemDims& d, int m, int n) {
+  const cplx<T>* t = tab + ((int64_t)b * nlens + s) * ((int64_t)d.nx + d.ny);
+  return cmul(t[m], t[d.nx + n]);
+}
+
+// Applies element e to (c0, c1). Returns the state after it.
+template <typename T>
+__device__ __forceinline__ void elem_fwd(const ElemSet& E, const ElemDims& d, const cplx<T>* lens,
+                                         int nlens, int e, int b, int64_t i, int m, int n,
+                                         cplx<T>& c0, cplx<T>& c1) {
+  switch (E.kind[e]) {
+    case XL_SLM: {
+      T s, c;
+      xsincos(phase_at<T>(E.phx[e], E.phstride[e], b, i), &s, &c);
+      c0 = cmul(c0, mk(c, s));
+      c1 = cmul(c1, mk(c, s));
+      break;
+    }
+    case XL_SSLM: {
+      T s, c;
+      xsincos(phase_at<T>(E.phx[e], E.phstride[e], b, i), &s, &c);
+      c0 = cmul(c0, mk(c, s));
+      xsincos(phase_at<T>(E.phy[e], E.phstride[e], b, i), &s, &c);
+      c1 = cmul(c1, mk(c, s));
+      break;
+    }
+    case XL_LENS: {
+      cplx<T> L = lens_factor<T>(lens, E.lens_slot[e], d.params_dev ? b : 0, nlens, d, m, n);
+      c0 = cmul(c0, L);
+      c1 = cmul(c1, L);
+      break;
+    }
+    case XL_POLARIZER: {
+      Jones2<T> J;
+      polarizer<T>(eparam(E, d, b, e, 1), &J, nullptr);
+      japply(J, c0, c1);
+      break;
+    }
+    case XL_WAVEPLATE: {
+      Jones2<T> J;
+      waveplate<T>(eparam(E, d, b, e, 2), eparam(E, d, b, e, 3), &J, nullptr, nullptr);
+      japply(J, c0, c1);
+      break;
+    }
+    case XL_TO_VECTOR:
+      c1 = mk((T)0, (T)0);
+      break;
+  }
+}
+
+// grid: (ceil(plane / 256), batch)
+template <typename T>
+__global__ void __launch_bounds__(256) k_elem_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out,
+                                                  ElemSet E, ElemDims d, const cplx<T>* __restrict__ lens,
+                                                  int nlens) {
+  const int b = blockIdx.y;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= d.plane) return;
+  const int m = (int)(i % d.nx), n = (int)(i / d.nx);
+  const cplx<T>* src = in + (int64_t)b * d.comps_in * d.plane;
+  cplx<T> c0 = src[i];
+  cplx<T> c1 = d.comps_in == 2 ? src[d.plane + i] : mk((T)0, (T)0);
+  for (int e = 0; e < E.n; ++e) elem_fwd<T>(E, d, lens, nlens, e, b, i, m, n, c0, c1);
+  cplx<T>* dst = out + (int64_t)b * d.comps_out * d.plane;
+  dst[i] = c0;
+  if (d.comps_out == 2) dst[d.plane + i] = c1;
+}
+
+struct ElemGrad {
+  void* gphx[kMaxElem];
+  void* gphy[kMaxElem];
+  double* partial;  // [batch][n * 4][nblocks] block partials of the scalar gradients (or nullptr)
+  int accumulate_shared;  // masks with stride 0 are shared: sum over the batch inside the thread
+};
+
+// Backward. grid: (ceil(plane / 256), batch or 1). When masks are shared (stride 0) the batch
+// loop runs inside the thread so that dL/dphi sums over the batch without atomics.
+template <typename T>
+__global__ void __launch_bounds__(256) k_elem_bwd(const cplx<T>* __restrict__ gout, const cplx<T>* __restrict__ in,
+                                                  cplx<T>* __restrict__ gin, ElemSet E, ElemDims d,
+                                                  const cplx<T>* __restrict__ lens, int nlens,
+                                                  ElemGrad G, int batch) {
+  __shared__ double red[32];
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool live = i < d.plane;
+  const int64_t ii = live ? i : d.plane - 1;
+  const int m = (int)(ii % d.nx), n = (int)(ii / d.nx);
+  const int b_lo = G.accumulate_shared ? 0 : blockIdx.y;
+  const int b_hi = G.accumulate_shared ? batch : blockIdx.y + 1;
+  T gphx_acc[kMaxElem], gphy_acc[kMaxElem];
+#pragma unroll
+  for (int e = 0; e < kMaxElem; ++e) gphx_acc[e] = gphy_acc[e] = (T)0;
+  for (int b = b_lo; b < b_hi; ++b) {
+    cplx<T> s0[kMaxElem + 1], s1[kMaxElem + 1];
+    const cplx<T>* src = in + (int64_t)b * d.comps_in * d.plane;
+    s0[0] = src[ii];
+    s1[0] = d.comps_in == 2 ? src[d.plane + ii] : mk((T)0, (T)0);
+#pragma unroll
+    for (int e = 0; e < kMaxElem; ++e) {
+      if (e >= E.n) break;
+      s0[e + 1] = s0[e];
+      s1[e + 1] = s1[e];
+      elem_fwd<T>(E, d, lens, nlens, e, b, ii, m, n, s0[e + 1], s1[e + 1]);
+    }
+    const cplx<T>* gsrc = gout + (int64_t)b * d.comps_out * d.plane;
+    cplx<T> g0 = gsrc[ii];
+    cplx<T> g1 = d.comps_out == 2 ? gsrc[d.plane + ii] : mk((T)0, (T)0);
+    double sg[kMaxElem][4];
+#pragma unroll
+    for (int e = 0; e < kMaxElem; ++e) sg[e][0] = sg[e][1] = sg[e][2] = sg[e][3] = 0.0;
+#pragma unroll
+    for (int e = kMaxElem - 1; e >= 0; --e) {
+      if (e >= E.n) continue;
+      const cplx<T> u0 = s0[e], u1 = s1[e], o0 = s0[e + 1], o1 = s1[e + 1];
+      switch (E.kind[e]) {
+        case XL_SLM: {
+          gphx_acc[e] += cmulc(g0, o0).y + cmulc(g1, o1).y;
+          T s, c;
+          xsincos(phase_at<T>(E.phx[e], E.phstride[e], b, ii), &s, &c);
+          g0 = cmul(g0, mk(c, -s));
+          g1 = cmul(g1, mk(c, -s));
+          break;
+        }
+        case XL_SSLM: {
+          gphx_acc[e] += cmulc(g0, o0).y;
+          gphy_acc[e] += cmulc(g1, o1).y;
+          T s, c;
+          xsincos(phase_at<T>(E.phx[e], E.phstride[e], b, ii), &s, &c);
+          g0 = cmul(g0, mk(c, -s));
+          xsincos(phase_at<T>(E.phy[e], E.phstride[e], b, ii), &s, &c);
+          g1 = cmul(g1, mk(c, -s));
+          break;
+        }
+        case XL_LENS: {
+          const double f = eparam(E, d, b, e, 0);
+          const T xm = (T)(d.x0 + m * d.dx), yn = (T)(d.y0 + n * d.dy);
+          const T coef = (T)(d.k / (2.0 * f * f)) * (xm * xm + yn * yn);  // d out / d f = i coef out
+          sg[e][0] += (double)cdot_re(g0, mk(-o0.y * coef, o0.x * coef)) +
+                      (double)cdot_re(g1, mk(-o1.y * coef, o1.x * coef));
+          cplx<T> L = lens_factor<T>(lens, E.lens_slot[e], d.params_dev ? b : 0, nlens, d, m, n);
+          g0 = cmulc(g0, L);
+          g1 = cmulc(g1, L);
+          break;
+        }
+        case XL_POLARIZER: {
+          Jones2<T> J, dJ;
+          polarizer<T>(eparam(E, d, b, e, 1), &J, &dJ);
+          sg[e][1] += jre(dJ, g0, g1, u0, u1);
+          japply_h(J, g0, g1);
+          break;
+        }
+        case XL_WAVEPLATE: {
+          Jones2<T> J, dJe, dJt;
+          waveplate<T>(eparam(E, d, b, e, 2), eparam(E, d, b, e, 3), &J, &dJe, &dJt);
+          sg[e][2] += jre(dJe, g0, g1, u0, u1);
+          sg[e][3] += jre(dJt, g0, g1, u0, u1);
+          japply_h(J, g0, g1);
+          break;
+        }
+        case XL_TO_VECTOR:
+          g1 = mk((T)0, (T)0);
+          break;
+      }
+    }
+    if (live && gin) {
+      cplx<T>* dst = gin + (int64_t)b * d.comps_in * d.plane;
+      dst[i] = g0;
+      if (d.comps_in == 2) dst[d.plane + i] = g1;
+    }
+    if (!G.accumulate_shared && live) {
+#pragma unroll
+      for (int e = 0; e < kMaxElem; ++e) {
+        if (e >= E.n) break;
+        if (G.gphx[e]) ((T*)G.gphx[e])[(int64_t)b * E.phstride[e] + i] = gphx_acc[e];
+        if (G.gphy[e]) ((T*)G.gphy[e])[(int64_t)b * E.phstride[e] + i] = gphy_acc[e];
+        gphx_acc[e] = gphy_acc[e] = (T)0;
+      }
+    }
+    if (G.partial) {
+      // block reduction of every scalar gradient of this batch element, fixed order
+      for (int e = 0; e < E.n; ++e)
+        for (int j = 0; j < 4; ++j) {
+          double v = live ? sg[e][j] : 0.0;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+          __syncthreads();
+          if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+          __syncthreads();
+          if (threadIdx.x == 0) {
+            double s = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+            G.partial[(((int64_t)b * E.n + e) * 4 + j) * gridDim.x + blockIdx.x] = s;
+          }
+        }
+    }
+  }
+  if (G.accumulate_shared && live) {
+#pragma unroll
+    for (int e = 0; e < kMaxElem; ++e) {
+      if (e >= E.n) break;
+      if (G.gphx[e]) ((T*)G.gphx[e])[i] = gphx_acc[e];
+      if (G.gphy[e]) ((T*)G.gphy[e])[i] = gphy_acc[e];
+    }
+  }
+}
+
+// g_params[r] = sum_k partial[r][k], r < rows (fixed order).
+__global__ void k_elem_reduce(const double* __restrict__ partial, int nblk, double* __restrict__ out) {
+  __shared__ double red[32];
+  const int r = blockIdx.x;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nblk; k += blockDim.x) s += partial[(int64_t)r * nblk + k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[r] = t;
+  }
+}
+
+namespace {
+
+xl_status prepare(const xl_element* el, int32_t n_el, int32_t comps_in, const xl_grid* g,
+                  double wavelength, const double* params, int32_t flags, ElemSet* E, ElemDims* d,
+                  int* nlens) {
+  if (!g || !el || n_el < 0 || n_el > kMaxElem)
+    return fail(XL_ERR_ARG, "elements: NULL grid/list or more than 8 elements");
+  if (g->nx < 1 || g->ny < 1) return fail(XL_ERR_ARG, "elements: empty grid");
+  if (!(wavelength > 0)) return fail(XL_ERR_ARG, "elements: wavelength must be positive");
+  if (comps_in != 1 && comps_in != 2) return fail(XL_ERR_ARG, "elements: comps_in must be 1 or 2");
+  if (flags & ~XL_Z_DEVICE) return fail(XL_ERR_ARG, "elements: unknown flag bits");
+  if ((flags & XL_Z_DEVICE) && !params) return fail(XL_ERR_ARG, "elements: device parameters are NULL");
+  std::memset(E, 0, sizeof(*E));
+  E->n = n_el;
+  int c = comps_in;
+  *nlens = 0;
+  for (int e = 0; e < n_el; ++e) {
+    const xl_element& x = el[e];
+    E->kind[e] = x.kind;
+    E->phx[e] = x.phi_x;
+    E->phy[e] = x.phi_y;
+    E->phstride[e] = x.phi_stride;
+    E->hp[e][0] = x.f;
+    E->hp[e][1] = x.alpha;
+    E->hp[e][2] = x.eta;
+    E->hp[e][3] = x.theta;
+    E->lens_slot[e] = -1;
+    switch (x.kind) {
+      case XL_SLM:
+        if (!x.phi_x) return fail(XL_ERR_ARG, "SLM needs phi_x");
+        break;
+      case XL_SSLM:
+        if (c != 2) return fail(XL_ERR_ARG, "super-SLM needs a 2-component field");
+        if (!x.phi_x || !x.phi_y) return fail(XL_ERR_ARG, "super-SLM needs phi_x and phi_y");
+        break;
+      case XL_LENS:
+        if (!(flags & XL_Z_DEVICE) && !(x.f != 0) ) return fail(XL_ERR_ARG, "lens focal length must be non-zero");
+        E->lens_slot[e] = (*nlens)++;
+        break;
+      case XL_POLARIZER:
+      case XL_WAVEPLATE:
+        if (c != 2) return fail(XL_ERR_ARG, "polariser / wave plate need a 2-component field");
+        break;
+      case XL_TO_VECTOR:
+        if (c != 1) return fail(XL_ERR_ARG, "to-vector needs a 1-component field");
+        c = 2;
+        break;
+      default:
+        return fail(XL_ERR_ARG, "unknown element kind");
+    }
+    if (x.phi_stride < 0) return fail(XL_ERR_ARG, "phi_stride must be >= 0");
+  }
+  d->nx = g->nx;
+  d->ny = g->ny;
+  d->comps_in = comps_in;
+  d->comps_out = c;
+  d->plane = (int64_t)g->nx * g->ny;
+  d->x0 = g->x0;
+  d->dx = g->dx;
+  d->y0 = g->y0;
+  d->dy = g->dy;
+  d->k = kTwoPi / wavelength;
+  d->params_dev = (flags & XL_Z_DEVICE) ? params : nullptr;
+  return XL_OK;
+}
+
+template <typename T>
+xl_status lens_tables(const ElemSet& E, const ElemDims& d, int batch, int nlens, void* buf,
+                      cudaStream_t s) {
+  const int64_t total = ((int64_t)d.nx + d.ny) * nlens * batch;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+  LaunchScope ls("lens_tables", s);
+  k_lens_tables<T><<<blocks, 256, 0, s>>>((cplx<T>*)buf, E, d, batch, nlens);
+  XL_CUDA_TRY(cudaGetLastError());
+  return XL_OK;
+}
+
+template <typename T>
+xl_status run_fwd(const void* in, void* out, int32_t batch, const ElemSet& E, const ElemDims& d,
+                  int nlens, cudaStream_t s) {
+  void* lens = nullptr;
+  // parameters shared by the batch (host values) need one lens table per lens
+  const int lb = d.params_dev ? batch : 1;
+  if (nlens) {
+    XL_TRY(workspace(s, ((size_t)d.nx + d.ny) * nlens * lb * sizeof(cplx<T>), &lens, 2));
+    XL_TRY(lens_tables<T>(E, d, lb, nlens, lens, s));
+  }
+  dim3 grid((unsigned)((d.plane + 255) / 256), batch);
+  LaunchScope ls("elements_fwd", s);
+  k_elem_fwd<T><<<grid, 256, 0, s>>>((const cplx<T>*)in, (cplx<T>*)out, E, d, (const cplx<T>*)lens, nlens);
+  XL_CUDA_TRY(cudaGetLastError());
+  return XL_OK;
+}
+
+template <typename T>
+xl_status run_bwd(const void* gout, const void* in, void* gin, int32_t batch, const ElemSet& E,
+                  const ElemDims& d, int nlens, void* const* gpx, void* const* gpy, double* gparams,
+                  cudaStream_t s) {
+  ElemGrad G;
+  std::memset(&G, 0, sizeof(G));
+  bool any_shared = false, any_batched = false;
+  for (int e = 0; e < E.n; ++e) {
+    G.gphx[e] = gpx ? gpx[e] : nullptr;
+    G.gphy[e] = gpy ? gpy[e] : nullptr;
+    if (G.gphx[e] || G.gphy[e]) (E.phstride[e] == 0 ? any_shared : any_batched) = true;
+  }
+  if (any_shared && any_batched && batch > 1)
+    return fail(XL_ERR_UNSUPPORTED, "elements backward: mixing shared and per-batch masks");
+  G.accumulate_shared = any_shared && batch > 1;
+  const int nblk = (int)((d.plane + 255) / 256);
+  const int lb = d.params_dev ? batch : 1;
+  const size_t cs = sizeof(cplx<T>);
+  auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
+  const size_t lens_bytes = nlens ? ((size_t)d.nx + d.ny) * nlens * lb * cs : 0;
+  const size_t part_bytes = gparams ? (size_t)batch * E.n * 4 * nblk * sizeof(double) : 0;
+  void* ws = nullptr;
+  XL_TRY(workspace(s, al(lens_bytes) + al(part_bytes) + 256, &ws, 2));
+  void* lens = ws;
+  G.partial = gparams ? (double*)((char*)ws + al(lens_bytes)) : nullptr;
+  if (nlens) XL_TRY(lens_tables<T>(E, d, lb, nlens, lens, s));
+  dim3 grid(nblk, G.accumulate_shared ? 1 : batch);
+  {
+    LaunchScope ls("elements_bwd", s);
+    k_elem_bwd<T><<<grid, 256, 0, s>>>((const cplx<T>*)gout, (const cplx<T>*)in, (cplx<T>*)gin, E, d,
+                                       (const cplx<T>*)lens, nlens, G, batch);
+    XL_CUDA_TRY(cudaGetLastError());
+  }
+  if (gparams && E.n > 0) {
+    LaunchScope ls("elements_reduce", s);
+    k_elem_reduce<<<batch * E.n * 4, 256, 0, s>>>(G.partial, nblk, gparams);
+    XL_CUDA_TRY(cudaGetLastError());
+  }
+  return XL_OK;
+}
+
+}  // namespace
+}  // namespace xl
+
+using namespace xl;
+
+extern "C" {
+
+xl_status xl_apply_elements(const void* in, void* out, int32_t batch, int32_t comps_in,
+                            const xl_grid* grid, double wavelength, const xl_element* elements,
+                            int32_t n_elem, const double* params, int32_t flags, int32_t dtype,
+                            void* stream) {
+  ElemSet E;
+  ElemDims d;
+  int nlens = 0;
+  XL_TRY(prepare(elements, n_elem, comps_in, grid, wavelength, params, flags, &E, &d, &nlens));
+  if (batch < 0) return fail(XL_ERR_ARG, "batch < 0");
+  if (dtype != XL_C64 && dtype != XL_C128) return fail(XL_ERR_ARG, "bad dtype");
+  if (batch == 0) return XL_OK;
+  if (!in || !out) return fail(XL_ERR_ARG, "field pointer is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  return dtype == XL_C128 ? run_fwd<double>(in, out, batch, E, d, nlens, s)
+                          : run_fwd<float>(in, out, batch, E, d, nlens, s);
+}
+
+xl_status xl_apply_elements_backward(const void* g_out, const void* in, void* g_in, int32_t batch,
+                                     int32_t comps_in, const xl_grid* grid, double wavelength,
+                                     const xl_element* elements, int32_t n_elem,
+                                     const double* params, int32_t flags, void* const* g_phi_x,
+                                     void* const* g_phi_y, double* g_params, int32_t dtype,
+                                     void* stream) {
+  ElemSet E;
+  ElemDims d;
+  int nlens = 0;
+  XL_TRY(prepare(elements, n_elem, comps_in, grid, wavelength, params, flags, &E, &d, &nlens));
+  if (batch < 0) return fail(XL_ERR_ARG, "batch < 0");
+  if (dtype != XL_C64 && dtype != XL_C128) return fail(XL_ERR_ARG, "bad dtype");
+  if (batch == 0) return XL_OK;
+  if (!g_out || !in) return fail(XL_ERR_ARG, "field pointer is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  return dtype == XL_C128
+             ? run_bwd<double>(g_out, in, g_in, batch, E, d, nlens, g_phi_x, g_phi_y, g_params, s)
+             : run_bwd<float>(g_out, in, g_in, batch, E, d, nlens, g_phi_x, g_phi_y, g_params, s);
+}
+
+}  // extern "C"

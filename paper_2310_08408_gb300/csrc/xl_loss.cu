@@ -1,0 +1,364 @@
+// Camera intensity and losses with their adjoints (Methods, "Loss function"; the camera
+// intensities of the Results: |Ex|^2 + |Ey|^2, |Ez|^2 or the total).
+//
+//   I = sum over the components selected by comp_mask of |E_c|^2
+//   XL_SECOND_MOMENT (reading; the paper's own spot metric is (pi/4) FWHMx FWHMy):
+//       P = sum I, xbar = sum I x / P, L = sum I ((x - xbar)^2 + (y - ybar)^2) / P
+//   XL_DENSITY (Methods, "Loss function"): threshold eps i_max with a strict ">",
+//       L = Area / I_eps (pixel count and intensity sum above the threshold)
+// Two sweeps per loss: the first forms (P, sum I x, sum I y) or i_max, the second the centred
+// second moment or the thresholded count / sum, so no moment is formed by cancellation. Each
+// sweep reduces per block (thread sums in the field's precision, block tree in double) and a
+// one-block-per-batch finaliser combines the partials in a fixed order (deterministic).
+// Gradient (g = 2 dL/dI E on the selected components):
+//   second moment  dL/dI = [(x - xbar)^2 + (y - ybar)^2 - L] / P
+//   density        dL/dI = -Area / I_eps^2 above the threshold, 0 elsewhere (no gradient through
+//                  i_max or Area, as with a where-based selection).
+// A non-finite loss sets a device status bit that xl_device_status() reports as
+// XL_ERR_NONFINITE.
+#include <cmath>
+
+#include "xl_runtime.h"
+
+namespace xl {
+
+__device__ unsigned int g_status_bits = 0;  // bit 0: non-finite loss
+
+constexpr int kLossThreads = 256;
+constexpr int kLossBlocks = 152 * 2;  // per batch element: two blocks per SM on 152 SMs
+
+struct LossDims {
+  int nx, ny, comps;
+  unsigned mask;
+  int64_t plane;
+  double x0, dx, y0, dy, eps;
+  int mode;
+};
+
+template <typename T>
+__device__ __forceinline__ T intensity(const cplx<T>* f, const LossDims& d, int64_t i) {
+  T s = 0;
+  for (int c = 0; c < d.comps; ++c)
+    if (d.mask & (1u << c)) {
+      cplx<T> e = f[c * d.plane + i];
+      s += e.x * e.x + e.y * e.y;
+    }
+  return s;
+}
+
+__device__ __forceinline__ double bsum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  return s;
+}
+__device__ __forceinline__ double bmax(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = fmax(s, red[w]);
+  return s;
+}
+
+// Sweep 1. partial: [batch][blocks][3]. grid (kLossBlocks, batch).
+template <typename T>
+__global__ void __launch_bounds__(kLossThreads) k_loss_sweep1(const cplx<T>* __restrict__ field, LossDims d,
+                                                              double* __restrict__ partial,
+                                                              T* __restrict__ inten) {
+  __shared__ double red[32];
+  const int b = blockIdx.y;
+  const cplx<T>* f = field + (int64_t)b * d.comps * d.plane;
+  T s0 = 0, s1 = 0, s2 = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.plane;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T I = intensity<T>(f, d, i);
+    if (inten) inten[(int64_t)b * d.plane + i] = I;
+    if (d.mode == XL_SECOND_MOMENT) {
+      const T x = (T)(d.x0 + (i % d.nx) * d.dx), y = (T)(d.y0 + (i / d.nx) * d.dy);
+      s0 += I;
+      s1 += I * x;
+      s2 += I * y;
+    } else {
+      s0 = fmax(s0, I);
+    }
+  }
+  double* p = partial + ((int64_t)b * gridDim.x + blockIdx.x) * 3;
+  if (d.mode == XL_SECOND_MOMENT) {
+    double a = bsum((double)s0, red), bx = bsum((double)s1, red), by = bsum((double)s2, red);
+    if (threadIdx.x == 0) {
+      p[0] = a;
+      p[1] = bx;
+      p[2] = by;
+    }
+  } else {
+    double m = bmax((double)s0, red);
+    if (threadIdx.x == 0) p[0] = m;
+  }
+}
+
+// Sweep 2 (needs st[b][.] from finalise 1). partial: [batch][blocks][3].
+template <typename T>
+__global__ void __launch_bounds__(kLossThreads) k_loss_sweep2(const cplx<T>* __restrict__ field, LossDims d,
+                                                              const double* __restrict__ st,
+                                                              double* __restrict__ partial) {
+  __shared__ double red[32];
+  const int b = blockIdx.y;
+  const cplx<T>* f = field + (int64_t)b * d.comps * d.plane;
+  const double* sb = st + (int64_t)b * 8;
+  T s0 = 0, s1 = 0;
+  if (d.mode == XL_SECOND_MOMENT) {
+    const T xb = (T)sb[1], yb = (T)sb[2];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.plane;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const T I = intensity<T>(f, d, i);
+      const T ex = (T)(d.x0 + (i % d.nx) * d.dx) - xb, ey = (T)(d.y0 + (i / d.nx) * d.dy) - yb;
+      s0 += I * (ex * ex + ey * ey);
+    }
+  } else {
+    const T thr = (T)sb[3];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.plane;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const T I = intensity<T>(f, d, i);
+      if (I > thr) {
+        s0 += (T)1;
+        s1 += I;
+      }
+    }
+  }
+  double a = bsum((double)s0, red), c = bsum((double)s1, red);
+  if (threadIdx.x == 0) {
+    double* p = partial + ((int64_t)b * gridDim.x + blockIdx.x) * 3;
+    p[0] = a;
+    p[1] = c;
+  }
+}
+
+// Finalisers: one block per batch element, fixed-order sums of the partials.
+// st[b]: [0] P, [1] xbar, [2] ybar, [3] threshold, [4] i_max, [5] L, [6] Area, [7] I_eps
+__global__ void k_loss_fin1(const double* __restrict__ partial, int nblk, LossDims d, double* __restrict__ st) {
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  const double* p = partial + (int64_t)b * nblk * 3;
+  double* s = st + (int64_t)b * 8;
+  if (d.mode == XL_SECOND_MOMENT) {
+    double a = 0, x = 0, y = 0;
+    for (int k = threadIdx.x; k < nblk; k += blockDim.x) {
+      a += p[3 * k];
+      x += p[3 * k + 1];
+      y += p[3 * k + 2];
+    }
+    a = bsum(a, red);
+    x = bsum(x, red);
+    y = bsum(y, red);
+    if (threadIdx.x == 0) {
+      s[0] = a;
+      s[1] = x / a;
+      s[2] = y / a;
+    }
+  } else {
+    double m = 0;
+    for (int k = threadIdx.x; k < nblk; k += blockDim.x) m = fmax(m, p[3 * k]);
+    m = bmax(m, red);
+    if (threadIdx.x == 0) {
+      s[4] = m;
+      s[3] = d.eps * m;
+    }
+  }
+}
+
+__global__ void k_loss_fin2(const double* __restrict__ partial, int nblk, LossDims d, double* __restrict__ st,
+                            double* __restrict__ loss) {
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  const double* p = partial + (int64_t)b * nblk * 3;
+  double* s = st + (int64_t)b * 8;
+  double a = 0, c = 0;
+  for (int k = threadIdx.x; k < nblk; k += blockDim.x) {
+    a += p[3 * k];
+    c += p[3 * k + 1];
+  }
+  a = bsum(a, red);
+  c = bsum(c, red);
+  if (threadIdx.x == 0) {
+    double L;
+    if (d.mode == XL_SECOND_MOMENT) {
+      L = a / s[0];
+    } else {
+      s[6] = a;
+      s[7] = c;
+      L = a / c;
+    }
+    s[5] = L;
+    if (loss) loss[b] = L;
+    if (!isfinite(L)) atomicOr(&g_status_bits, 1u);
+  }
+}
+
+// g_field = 2 g_loss dL/dI E on the selected components (0 elsewhere). grid (blocks, batch).
+template <typename T>
+__global__ void __launch_bounds__(kLossThreads) k_loss_grad(const cplx<T>* __restrict__ field, LossDims d,
+                                                            const double* __restrict__ st,
+                                                            const double* __restrict__ g_loss,
+                                                            cplx<T>* __restrict__ gf) {
+  const int b = blockIdx.y;
+  const cplx<T>* f = field + (int64_t)b * d.comps * d.plane;
+  cplx<T>* g = gf + (int64_t)b * d.comps * d.plane;
+  const double* sb = st + (int64_t)b * 8;
+  const double gl = g_loss ? g_loss[b] : 1.0;
+  const T xb = (T)sb[1], yb = (T)sb[2], L = (T)sb[5], iP = (T)(1.0 / sb[0]);
+  const T thr = (T)sb[3], dens = (T)(-sb[6] / (sb[7] * sb[7]));
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.plane;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T dI;
+    if (d.mode == XL_SECOND_MOMENT) {
+      const T ex = (T)(d.x0 + (i % d.nx) * d.dx) - xb, ey = (T)(d.y0 + (i / d.nx) * d.dy) - yb;
+      dI = (ex * ex + ey * ey - L) * iP;
+    } else {
+      dI = intensity<T>(f, d, i) > thr ? dens : (T)0;
+    }
+    const T w = (T)(2.0 * gl) * dI;
+    for (int c = 0; c < d.comps; ++c) {
+      const bool on = (d.mask & (1u << c)) != 0;
+      g[c * d.plane + i] = on ? cscale(f[c * d.plane + i], w) : mk((T)0, (T)0);
+    }
+  }
+}
+
+namespace {
+
+xl_status loss_check(const void* field, int32_t batch, int32_t comps, uint32_t mask,
+                     const xl_grid* g, int32_t mode, double eps, int32_t dtype, LossDims* d) {
+  if (!g) return fail(XL_ERR_ARG, "grid is NULL");
+  if (batch < 0) return fail(XL_ERR_ARG, "batch < 0");
+  if (comps < 1 || comps > 3) return fail(XL_ERR_ARG, "comps must be 1..3");
+  if ((mask & ((1u << comps) - 1)) == 0) return fail(XL_ERR_ARG, "comp_mask selects no component");
+  if (mode != XL_SECOND_MOMENT && mode != XL_DENSITY) return fail(XL_ERR_ARG, "unknown loss mode");
+  if (mode == XL_DENSITY && !(eps >= 0 && eps <= 1)) return fail(XL_ERR_ARG, "eps must be in [0, 1]");
+  if (g->nx < 1 || g->ny < 1) return fail(XL_ERR_ARG, "empty grid");
+  if (dtype != XL_C64 && dtype != XL_C128) return fail(XL_ERR_ARG, "bad dtype");
+  if (batch > 0 && !field) return fail(XL_ERR_ARG, "field is NULL");
+  d->nx = g->nx;
+  d->ny = g->ny;
+  d->comps = comps;
+  d->mask = mask & ((1u << comps) - 1);
+  d->plane = (int64_t)g->nx * g->ny;
+  d->x0 = g->x0;
+  d->dx = g->dx;
+  d->y0 = g->y0;
+  d->dy = g->dy;
+  d->eps = eps;
+  d->mode = mode;
+  return XL_OK;
+}
+
+int loss_blocks(const LossDims& d) {
+  int64_t need = (d.plane + kLossThreads * 4 - 1) / (kLossThreads * 4);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(need, kLossBlocks));
+}
+
+// Both sweeps and finalisers; st / loss in the workspace or caller memory.
+template <typename T>
+xl_status loss_stats(const void* field, int32_t batch, const LossDims& d, double* st, double* loss,
+                     void* inten, double* partial, cudaStream_t s) {
+  const int nb = loss_blocks(d);
+  dim3 grid(nb, batch);
+  {
+    LaunchScope ls("loss_sweep1", s);
+    k_loss_sweep1<T><<<grid, kLossThreads, 0, s>>>((const cplx<T>*)field, d, partial, (T*)inten);
+    XL_CUDA_TRY(cudaGetLastError());
+  }
+  {
+    LaunchScope ls("loss_fin1", s);
+    k_loss_fin1<<<batch, 256, 0, s>>>(partial, nb, d, st);
+    XL_CUDA_TRY(cudaGetLastError());
+  }
+  {
+    LaunchScope ls("loss_sweep2", s);
+    k_loss_sweep2<T><<<grid, kLossThreads, 0, s>>>((const cplx<T>*)field, d, st, partial);
+    XL_CUDA_TRY(cudaGetLastError());
+  }
+  {
+    LaunchScope ls("loss_fin2", s);
+    k_loss_fin2<<<batch, 256, 0, s>>>(partial, nb, d, st, loss);
+    XL_CUDA_TRY(cudaGetLastError());
+  }
+  return XL_OK;
+}
+
+}  // namespace
+}  // namespace xl
+
+using namespace xl;
+
+extern "C" {
+
+xl_status xl_intensity_loss(const void* field, int32_t batch, int32_t comps, uint32_t comp_mask,
+                            const xl_grid* grid, int32_t mode, double eps, double* loss,
+                            void* intensity, int32_t dtype, void* stream) {
+  LossDims d;
+  XL_TRY(loss_check(field, batch, comps, comp_mask, grid, mode, eps, dtype, &d));
+  if (batch == 0) return XL_OK;
+  if (!loss) return fail(XL_ERR_ARG, "loss is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = loss_blocks(d);
+  void* ws = nullptr;
+  const size_t st_bytes = (size_t)batch * 8 * sizeof(double);
+  const size_t pb = (size_t)batch * nb * 3 * sizeof(double);
+  XL_TRY(workspace(s, st_bytes + pb + 256, &ws, 3));
+  double* st = (double*)ws;
+  double* partial = (double*)((char*)ws + ((st_bytes + 255) & ~(size_t)255));
+  return dtype == XL_C128 ? loss_stats<double>(field, batch, d, st, loss, intensity, partial, s)
+                          : loss_stats<float>(field, batch, d, st, loss, intensity, partial, s);
+}
+
+xl_status xl_intensity_loss_backward(const void* field, int32_t batch, int32_t comps,
+                                     uint32_t comp_mask, const xl_grid* grid, int32_t mode,
+                                     double eps, const double* g_loss, void* g_field,
+                                     int32_t dtype, void* stream) {
+  LossDims d;
+  XL_TRY(loss_check(field, batch, comps, comp_mask, grid, mode, eps, dtype, &d));
+  if (batch == 0) return XL_OK;
+  if (!g_field) return fail(XL_ERR_ARG, "g_field is NULL");
+  if (g_field == field) return fail(XL_ERR_ARG, "g_field may not alias field");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = loss_blocks(d);
+  void* ws = nullptr;
+  const size_t st_bytes = (size_t)batch * 8 * sizeof(double);
+  const size_t pb = (size_t)batch * nb * 3 * sizeof(double);
+  XL_TRY(workspace(s, st_bytes + pb + 256, &ws, 3));
+  double* st = (double*)ws;
+  double* partial = (double*)((char*)ws + ((st_bytes + 255) & ~(size_t)255));
+  if (dtype == XL_C128) {
+    XL_TRY(loss_stats<double>(field, batch, d, st, nullptr, nullptr, partial, s));
+    LaunchScope ls("loss_grad", s);
+    k_loss_grad<double><<<dim3(nb, batch), kLossThreads, 0, s>>>((const cplx<double>*)field, d, st, g_loss,
+                                                                  (cplx<double>*)g_field);
+  } else {
+    XL_TRY(loss_stats<float>(field, batch, d, st, nullptr, nullptr, partial, s));
+    LaunchScope ls("loss_grad", s);
+    k_loss_grad<float><<<dim3(nb, batch), kLossThreads, 0, s>>>((const cplx<float>*)field, d, st, g_loss,
+                                                                (cplx<float>*)g_field);
+  }
+  XL_CUDA_TRY(cudaGetLastError());
+  return XL_OK;
+}
+
+xl_status xl_device_status(void* stream) {
+  XL_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  unsigned int bits = 0, zero = 0;
+  XL_CUDA_TRY(cudaMemcpyFromSymbol(&bits, g_status_bits, sizeof(bits)));
+  XL_CUDA_TRY(cudaMemcpyToSymbol(g_status_bits, &zero, sizeof(zero)));
+  if (bits & 1u) return fail(XL_ERR_NONFINITE, "a loss reduction produced a non-finite value");
+  return XL_OK;
+}
+
+}  // extern "C"

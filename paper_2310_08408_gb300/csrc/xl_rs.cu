@@ -119,6 +119,7 @@ P2Args p2_args(const xl_grid* g, const Spectra& sp, int cT, int cU) {
 
 template <typename T>
 xl_status launch_reduce(const double* part, int n, double* out, int nb, cudaStream_t s) {
+  LaunchScope ls("reduce_rows", s);
   k_reduce_rows<<<nb, 256, 0, s>>>(part, n, out);
   XL_CUDA_TRY(cudaGetLastError());
   return XL_OK;

@@ -14,6 +14,7 @@ xl_status pass1_L(const void* in, void* Tb, int nx, int ny, int cin, int cT, int
   XL_TRY(twiddles(LX, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
   XL_TRY(smem_attr((const void*)k_rs_pass1<T, LX>, sm));
   dim3 grid((ny + ROWS - 1) / ROWS, np);
+  LaunchScope ls("rs_pass1<" + std::to_string(LX) + ">", s);
   k_rs_pass1<T, LX><<<grid, ROWS * (LX / 16), sm, s>>>(
       (const cplx<T>*)in, (cplx<T>*)Tb, nx, ny, cin, cT, (const cplx<T>*)tw);
   XL_CUDA_TRY(cudaGetLastError());
@@ -28,6 +29,7 @@ xl_status pass3_L(const void* Tb, void* out, int nx, int ny, int cout, int cT, i
   XL_TRY(twiddles(LX, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
   XL_TRY(smem_attr((const void*)k_rs_pass3<T, LX>, sm));
   dim3 grid((ny + ROWS - 1) / ROWS, np);
+  LaunchScope ls("rs_pass3<" + std::to_string(LX) + ">", s);
   k_rs_pass3<T, LX><<<grid, ROWS * (LX / 16), sm, s>>>(
       (const cplx<T>*)Tb, (cplx<T>*)out, nx, ny, cout, cT, (const cplx<T>*)tw);
   XL_CUDA_TRY(cudaGetLastError());
@@ -44,6 +46,7 @@ xl_status pass2_LM(void* Tb, const void* Ub, const void* Hq, double* dz, const P
   XL_TRY(smem_attr((const void*)k_rs_pass2<T, LY, MODE>, sm));
   const int LX = 2 * a.nx;
   dim3 grid((LX + ROWS - 1) / ROWS, nb);
+  LaunchScope ls("rs_pass2_m" + std::to_string(MODE) + "<" + std::to_string(LY) + ">", s);
   k_rs_pass2<T, LY, MODE><<<grid, ROWS * (LY / 16), sm, s>>>(
       (cplx<T>*)Tb, (const cplx<T>*)Ub, (const cplx<T>*)Hq, dz, a, (const cplx<T>*)tw);
   XL_CUDA_TRY(cudaGetLastError());
@@ -73,9 +76,13 @@ xl_status gen_LL(void* S, void* Hq, const GenArgs& g, cudaStream_t s) {
   XL_TRY(twiddles(LY, sizeof(T) == 8 ? XL_C128 : XL_C64, &twy));
   XL_TRY(smem_attr((const void*)k_gen_pass_a<T, LX>, sa));
   XL_TRY(smem_attr((const void*)k_gen_pass_b<T, LY>, sb));
+  {
+  LaunchScope ls("rs_gen_a<" + std::to_string(LX) + ">", s);
   k_gen_pass_a<T, LX><<<(g.ny + RA - 1) / RA, RA * (LX / 16), sa, s>>>((cplx<T>*)S, g,
                                                                       (const cplx<T>*)twx);
+  }
   XL_CUDA_TRY(cudaGetLastError());
+  LaunchScope lsb("rs_gen_b<" + std::to_string(LY) + ">", s);
   k_gen_pass_b<T, LY><<<(g.nx + 1 + RB - 1) / RB, RB * (LY / 16), sb, s>>>(
       (const cplx<T>*)S, (cplx<T>*)Hq, g, (const cplx<T>*)twy);
   XL_CUDA_TRY(cudaGetLastError());

@@ -6,7 +6,9 @@
 #include <mutex>
 #include <unordered_map>
 #include <vector>
+#include <algorithm>
 #include <cmath>
+#include <cstdio>
 
 #include "xl_runtime.h"
 
@@ -180,6 +182,45 @@ xl_status cached_table(const std::string& key, size_t bytes, cudaStream_t stream
   return XL_OK;
 }
 
+namespace {
+struct ProfRec {
+  std::string name;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+std::vector<cudaEvent_t> g_ev_pool;
+int64_t g_launches = 0;
+
+cudaEvent_t ev_get() {
+  if (!g_ev_pool.empty()) {
+    cudaEvent_t e = g_ev_pool.back();
+    g_ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+
+LaunchScope::LaunchScope(const std::string& name, cudaStream_t s) : s_(s) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  ++g_launches;
+  if (!g_prof_on) return;
+  ProfRec r{name, ev_get(), ev_get()};
+  cudaEventRecord(r.a, s);
+  slot_ = (int)g_prof.size();
+  g_prof.push_back(r);
+}
+
+LaunchScope::~LaunchScope() {
+  if (slot_ < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  cudaEventRecord(g_prof[slot_].b, s_);
+}
+
 }  // namespace xl
 
 using namespace xl;
@@ -210,6 +251,46 @@ xl_status xl_cache_clear(void) {
   }
   XL_CUDA_TRY(cudaSetDevice(dev0));
   return XL_OK;
+}
+
+int64_t xl_launch_count(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  return g_launches;
+}
+
+xl_status xl_profile_enable(int32_t on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = on != 0;
+  return XL_OK;
+}
+
+int32_t xl_profile_report(char* buf, int32_t len) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  std::map<std::string, std::pair<int64_t, double>> agg;
+  for (auto& r : g_prof) {
+    float ms = 0.f;
+    cudaEventSynchronize(r.b);
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    auto& e = agg[r.name];
+    e.first += 1;
+    e.second += ms;
+    g_ev_pool.push_back(r.a);
+    g_ev_pool.push_back(r.b);
+  }
+  g_prof.clear();
+  std::string out;
+  char line[256];
+  for (auto& kv : agg) {
+    snprintf(line, sizeof(line), "%s %lld %.6f\n", kv.first.c_str(), (long long)kv.second.first,
+             kv.second.second);
+    out += line;
+  }
+  if (buf && len > 0) {
+    int32_t n = (int32_t)std::min<size_t>(out.size(), (size_t)len - 1);
+    std::memcpy(buf, out.data(), n);
+    buf[n] = 0;
+  }
+  return (int32_t)out.size() + 1;
 }
 
 int64_t xl_cache_bytes(void) {

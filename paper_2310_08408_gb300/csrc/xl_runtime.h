@@ -37,4 +37,16 @@ xl_status smem_attr(const void* func, size_t bytes);
 
 size_t dtype_csize(int dtype);  // bytes of one complex element
 
+// Brackets one kernel launch: counts it and, while profiling is enabled, records CUDA events on
+// its stream before and after it (name = kernel family, e.g. "rs_pass2<4096>").
+class LaunchScope {
+ public:
+  LaunchScope(const std::string& name, cudaStream_t s);
+  ~LaunchScope();
+
+ private:
+  int slot_ = -1;
+  cudaStream_t s_;
+};
+
 }  // namespace xl

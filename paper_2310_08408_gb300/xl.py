@@ -58,6 +58,17 @@ class Window(ctypes.Structure):
         return Window(int(t[0]), int(t[1]), *map(float, t[2:6]))
 
 
+class Element(ctypes.Structure):
+    """xl_element: one optical element of a chain (kind, masks, host parameters)."""
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("phi_x", ctypes.c_void_p), ("phi_y", ctypes.c_void_p),
+                ("phi_stride", ctypes.c_int64), ("f", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("eta", ctypes.c_double), ("theta", ctypes.c_double)]
+
+
+SLM, SSLM, LENS, POLARIZER, WAVEPLATE, TO_VECTOR = range(6)
+SECOND_MOMENT, DENSITY = 0, 1
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int32
 _D = ctypes.c_double
@@ -70,10 +81,23 @@ SIGNATURES = {
     "xl_last_error": ([], ctypes.c_char_p),
     "xl_cache_clear": ([], _I),
     "xl_cache_bytes": ([], ctypes.c_int64),
+    "xl_launch_count": ([], ctypes.c_int64),
+    "xl_profile_enable": ([_I], _I),
+    "xl_profile_report": ([ctypes.c_char_p, _I], _I),
     "xl_rs_propagate": ([_P, _P, _I, _GP, _D, _P, _I, _I, _P], _I),
     "xl_rs_propagate_backward": ([_P, _P, _P, _P, _I, _GP, _D, _P, _I, _I, _P], _I),
     "xl_vrs_propagate": ([_P, _P, _I, _GP, _D, _P, _I, _I, _P], _I),
     "xl_vrs_propagate_backward": ([_P, _P, _P, _P, _I, _GP, _D, _P, _I, _I, _P], _I),
+    "xl_czt_propagate": ([_P, _P, _I, _I, _GP, _WP, _D, _P, _I, _I, _P], _I),
+    "xl_apply_elements": ([_P, _P, _I, _I, _GP, _D, ctypes.POINTER(Element), _I, _P, _I, _I, _P], _I),
+    "xl_apply_elements_backward": ([_P, _P, _P, _I, _I, _GP, _D, ctypes.POINTER(Element), _I, _P,
+                                    _I, _P, _P, _P, _I, _P], _I),
+    "xl_intensity_loss": ([_P, _I, _I, ctypes.c_uint32, _GP, _I, _D, _P, _P, _I, _P], _I),
+    "xl_intensity_loss_backward": ([_P, _I, _I, ctypes.c_uint32, _GP, _I, _D, _P, _P, _I, _P], _I),
+    "xl_device_status": ([_P], _I),
+    "xl_adam_step": ([_P, _P, _P, _P, ctypes.c_int64, _I, _D, _D, _D, _D, _P, _I, _P], _I),
+    "xl_step_advance": ([_P, _P], _I),
+    "xl_czt_propagate_backward": ([_P, _P, _I, _I, _GP, _WP, _D, _P, _I, _I, _P], _I),
 }
 
 
@@ -153,6 +177,27 @@ def cache_bytes() -> int:
     return int(load().xl_cache_bytes())
 
 
+def launch_count() -> int:
+    """Kernels launched by the library so far (host counter)."""
+    return int(load().xl_launch_count())
+
+
+def profile_enable(on: bool) -> None:
+    _check(load().xl_profile_enable(int(bool(on))))
+
+
+def profile_report() -> dict:
+    """{kernel family: (launches, total_ms)} of the launches recorded since profiling was
+    enabled (synchronises on their events); clears the records."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    load().xl_profile_report(buf, len(buf))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, n, ms = line.rsplit(" ", 2)
+        out[name] = (int(n), float(ms))
+    return out
+
+
 def _planes(u: torch.Tensor, comps: int, name: str):
     """Returns (batch, ny, nx) of a [B][comps][ny][nx] (or [comps][ny][nx] / [ny][nx]) tensor."""
     if comps == 1:
@@ -229,3 +274,201 @@ def vrs_propagate_backward(g_exyz: torch.Tensor, exy_in: torch.Tensor | None, gr
         g_z.data_ptr() if g_z is not None else None, B, ctypes.byref(g), float(wavelength),
         zz.ptr, zz.flags, _dtype(g_exyz), _stream()))
     return g_exy, g_z
+
+
+def czt_propagate(u: torch.Tensor, grid, window, wavelength: float, z, vectorial: bool = False,
+                  out: torch.Tensor | None = None):
+    """CZT onto a window: [B][ny][nx] -> [B][my][mx]; vectorial: [B][2][ny][nx] -> [B][3][my][mx]."""
+    _dev(u, "u")
+    comps = 2 if vectorial else 1
+    B, ny, nx = _planes(u, comps, "u")
+    g, w = Grid.of(grid), Window.of(window)
+    if out is None:
+        lead = u.shape[:-2] if not vectorial else (u.shape[:-3] + (3,))
+        out = torch.empty(tuple(lead) + (w.my, w.mx), dtype=u.dtype, device=u.device)
+    zz = _Z(z, B)
+    _check(load().xl_czt_propagate(u.data_ptr(), _dev(out, "out").data_ptr(), B, int(vectorial),
+                                   ctypes.byref(g), ctypes.byref(w), float(wavelength), zz.ptr,
+                                   zz.flags, _dtype(u), _stream()))
+    return out
+
+
+def czt_propagate_backward(g_out: torch.Tensor, grid, window, wavelength: float, z,
+                           vectorial: bool = False):
+    """Adjoint of czt_propagate: window gradient -> input-grid gradient."""
+    _dev(g_out, "g_out")
+    comps = 3 if vectorial else 1
+    B, my, mx = _planes(g_out, comps, "g_out")
+    g, w = Grid.of(grid), Window.of(window)
+    lead = g_out.shape[:-2] if not vectorial else (g_out.shape[:-3] + (2,))
+    g_in = torch.empty(tuple(lead) + (g.ny, g.nx), dtype=g_out.dtype, device=g_out.device)
+    zz = _Z(z, B)
+    _check(load().xl_czt_propagate_backward(g_out.data_ptr(), g_in.data_ptr(), B, int(vectorial),
+                                            ctypes.byref(g), ctypes.byref(w), float(wavelength),
+                                            zz.ptr, zz.flags, _dtype(g_out), _stream()))
+    return g_in
+
+
+# ----------------------------------------------------------------------------- elements
+def _real_dtype(field: torch.Tensor):
+    return torch.float32 if field.dtype == torch.complex64 else torch.float64
+
+
+def _elements(elements: Sequence[dict], field: torch.Tensor, batch: int, ny: int, nx: int):
+    """ctypes array of xl_element from dicts {kind, phi_x, phi_y, f, alpha, eta, theta}.
+    Masks are CUDA real tensors [ny][nx] (shared by the batch) or [B][ny][nx]."""
+    n = len(elements)
+    arr = (Element * max(n, 1))()
+    keep = []
+    rd = _real_dtype(field)
+    for i, e in enumerate(elements):
+        arr[i].kind = int(e["kind"])
+        stride = None
+        for key in ("phi_x", "phi_y"):
+            ph = e.get(key)
+            if ph is None:
+                continue
+            if not isinstance(ph, torch.Tensor) or not ph.is_cuda or ph.dtype != rd or not ph.is_contiguous():
+                raise ValueError(f"element {i}: {key} must be a contiguous CUDA {rd} tensor")
+            if ph.shape[-2:] != (ny, nx) or ph.dim() not in (2, 3):
+                raise ValueError(f"element {i}: {key} must be [ny][nx] or [B][ny][nx]")
+            st = 0 if ph.dim() == 2 else ny * nx
+            if ph.dim() == 3 and ph.shape[0] != batch:
+                raise ValueError(f"element {i}: {key} batch mismatch")
+            stride = st if stride is None else stride
+            setattr(arr[i], key, ph.data_ptr())
+            keep.append(ph)
+        arr[i].phi_stride = stride or 0
+        for key in ("f", "alpha", "eta", "theta"):
+            v = e.get(key, 0.0)
+            setattr(arr[i], key, float(v) if not isinstance(v, torch.Tensor) else 0.0)
+    return arr, keep
+
+
+def _params(params, batch: int, n: int):
+    """Device parameters [B][n][4] (float64 CUDA) or None for host values."""
+    if params is None:
+        return None, 0
+    if (not isinstance(params, torch.Tensor) or not params.is_cuda or params.dtype != torch.float64
+            or params.numel() != batch * n * 4 or not params.is_contiguous()):
+        raise ValueError("params must be a contiguous CUDA float64 tensor [B][n_elem][4]")
+    return params.data_ptr(), Z_DEVICE
+
+
+def _comps_out(comps_in: int, elements) -> int:
+    return 2 if comps_in == 2 or any(int(e["kind"]) == TO_VECTOR for e in elements) else 1
+
+
+def apply_elements(field: torch.Tensor, grid, wavelength: float, elements: Sequence[dict],
+                   comps_in: int = 1, params: torch.Tensor | None = None,
+                   out: torch.Tensor | None = None):
+    """field [B][comps_in][ny][nx] -> [B][comps_out][ny][nx] through the element chain."""
+    _dev(field, "field")
+    B, C, ny, nx = field.shape
+    assert C == comps_in
+    g = Grid.of(grid)
+    arr, keep = _elements(elements, field, B, ny, nx)
+    pp, flags = _params(params, B, len(elements))
+    co = _comps_out(comps_in, elements)
+    if out is None:
+        out = torch.empty((B, co, ny, nx), dtype=field.dtype, device=field.device)
+    _check(load().xl_apply_elements(field.data_ptr(), _dev(out, "out").data_ptr(), B, comps_in,
+                                    ctypes.byref(g), float(wavelength), arr, len(elements), pp,
+                                    flags, _dtype(field), _stream()))
+    return out
+
+
+def apply_elements_backward(g_out: torch.Tensor, field: torch.Tensor, grid, wavelength: float,
+                            elements: Sequence[dict], comps_in: int = 1,
+                            params: torch.Tensor | None = None, want_field: bool = True,
+                            want_phi: bool = True, want_params: bool = True):
+    """Adjoint of apply_elements at the forward input `field`. Returns (g_in, g_phi_x list,
+    g_phi_y list, g_params [B][n][4])."""
+    _dev(g_out, "g_out")
+    _dev(field, "field")
+    B, C, ny, nx = field.shape
+    g = Grid.of(grid)
+    arr, keep = _elements(elements, field, B, ny, nx)
+    pp, flags = _params(params, B, len(elements))
+    n = len(elements)
+    g_in = torch.empty_like(field) if want_field else None
+    gpx, gpy = [], []
+    cpx = (ctypes.c_void_p * max(n, 1))()
+    cpy = (ctypes.c_void_p * max(n, 1))()
+    for i, e in enumerate(elements):
+        for key, lst, carr in (("phi_x", gpx, cpx), ("phi_y", gpy, cpy)):
+            ph = e.get(key)
+            if ph is not None and want_phi:
+                t = torch.empty_like(ph)
+                lst.append(t)
+                carr[i] = t.data_ptr()
+            else:
+                lst.append(None)
+    g_params = torch.empty((B, n, 4), dtype=torch.float64, device=field.device) if want_params and n else None
+    _check(load().xl_apply_elements_backward(
+        g_out.data_ptr(), field.data_ptr(), g_in.data_ptr() if g_in is not None else None, B,
+        comps_in, ctypes.byref(g), float(wavelength), arr, n, pp, flags, cpx, cpy,
+        g_params.data_ptr() if g_params is not None else None, _dtype(field), _stream()))
+    return g_in, gpx, gpy, g_params
+
+
+# ----------------------------------------------------------------------------- losses
+def intensity_loss(field: torch.Tensor, grid, comp_mask: int, mode: int = SECOND_MOMENT,
+                   eps: float = 0.5, want_intensity: bool = False):
+    """field [B][C][ny][nx] -> (loss [B] float64, intensity [B][ny][nx] or None)."""
+    _dev(field, "field")
+    B, C, ny, nx = field.shape
+    g = Grid.of(grid)
+    loss = torch.empty(B, dtype=torch.float64, device=field.device)
+    inten = torch.empty((B, ny, nx), dtype=_real_dtype(field), device=field.device) if want_intensity else None
+    _check(load().xl_intensity_loss(field.data_ptr(), B, C, comp_mask, ctypes.byref(g), mode,
+                                    float(eps), loss.data_ptr(),
+                                    inten.data_ptr() if inten is not None else None,
+                                    _dtype(field), _stream()))
+    return loss, inten
+
+
+def intensity_loss_backward(field: torch.Tensor, grid, comp_mask: int, mode: int = SECOND_MOMENT,
+                            eps: float = 0.5, g_loss: torch.Tensor | None = None,
+                            out: torch.Tensor | None = None):
+    """dL/dE (torch convention) of intensity_loss; g_loss [B] float64 CUDA or None (= 1)."""
+    _dev(field, "field")
+    B, C, ny, nx = field.shape
+    g = Grid.of(grid)
+    if out is None:
+        out = torch.empty_like(field)
+    if g_loss is not None:
+        g_loss = _dev(g_loss.to(torch.float64), "g_loss")
+    _check(load().xl_intensity_loss_backward(field.data_ptr(), B, C, comp_mask, ctypes.byref(g),
+                                             mode, float(eps),
+                                             g_loss.data_ptr() if g_loss is not None else None,
+                                             out.data_ptr(), _dtype(field), _stream()))
+    return out
+
+
+def device_status() -> None:
+    """Raises XLError(ERR_NONFINITE) if a loss became non-finite since the last check."""
+    _check(load().xl_device_status(_stream()))
+
+
+# ----------------------------------------------------------------------------- Adam
+def adam_step(p: torch.Tensor, m: torch.Tensor, v: torch.Tensor, grad: torch.Tensor, lr: float,
+              t, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> None:
+    """In-place Adam step on float32 / float64 CUDA tensors. t: int step (>= 1) or a CUDA int32
+    tensor holding it (read at run time)."""
+    for name, a in (("p", p), ("m", m), ("v", v), ("grad", grad)):
+        _dev(a, name)
+        if a.dtype != p.dtype or a.numel() != p.numel():
+            raise ValueError(f"{name} must match p in dtype and size")
+    rd = {torch.float32: 0, torch.float64: 1}[p.dtype]
+    if isinstance(t, torch.Tensor):
+        t_dev, t_host = _dev(t, "t").data_ptr(), 0
+    else:
+        t_dev, t_host = None, int(t)
+    _check(load().xl_adam_step(p.data_ptr(), m.data_ptr(), v.data_ptr(), grad.data_ptr(), p.numel(),
+                               rd, float(lr), float(beta1), float(beta2), float(eps), t_dev, t_host,
+                               _stream()))
+
+
+def step_advance(t: torch.Tensor) -> None:
+    _check(load().xl_step_advance(_dev(t, "t").data_ptr(), _stream()))
