@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--batch", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-table", action="store_true", help="skip the batched optical-table section")
+    p.add_argument("--table-setups", type=int, default=256)
+    p.add_argument("--table-steps", type=int, default=4)
     return p.parse_args()
 
 
@@ -149,6 +152,11 @@ def make_inputs(rank: int, batch: int):
     return g, w, U, zs
 
 
+def inputs_seed(rank: int) -> int:
+    from paper_2310_08408_gb300 import inputs
+    return inputs.SEED0 + 5 + 1000 * rank
+
+
 def step_parts(xl):
     have = {"rs": True, "czt": True}
     for fn in ("apply_elements", "intensity_loss", "adam_step"):
@@ -182,6 +190,55 @@ class GpuStep:
         self.gA, self.gC = ga, gc
         self.gz = gz
         return self.A, self.C, self.gz
+
+
+# ----------------------------------------------------------------------------- optical tables
+TABLE_CFG = dict(wavelength=0.6328, extent=1024.0, w0=200.0, f=5000.0, cam_m=256, cam_width=64.0,
+                 lr=0.01, lr_z=1.0)
+
+
+def table_section(xl, torch, setups: int, steps: int, seed: int):
+    """Batched optical tables: `setups` setups with N drawn from {512, 1024, 2048} (seeded,
+    pitch = 1024 um / N), fwd + bwd + Adam per step replayed from one CUDA graph; compared with
+    the same library in complex128, one setup per call, eager launches (the plain FP64
+    single-instance GPU path), timed per grid size and weighted by the same mix."""
+    from paper_2310_08408_gb300 import inputs
+    u = inputs.uniform(seed, setups)
+    grid_n = [512 * (2 ** int(3 * x)) for x in u]
+    init = [[0.3, 20_000.0, 20_000.0] for _ in range(setups)]
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b = xl.Batch(TABLE_CFG, grid_n, init, seed)
+    b.step(use_graph=True)   # eager warm-up (sizes every workspace)
+    b.step(use_graph=True)   # capture + first replay
+    torch.cuda.synchronize()
+    n0 = xl.launch_count()
+    e0.record(stream)
+    for _ in range(steps):
+        b.step(use_graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    b.close()
+    # the complex128 single-instance path, one setup per size
+    f64 = {}
+    for n in (512, 1024, 2048):
+        one = xl.Batch(dict(TABLE_CFG, dtype="c128"), [n], [[0.3, 20_000.0, 20_000.0]], seed)
+        one.step(use_graph=False)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        one.step(use_graph=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        f64[n] = e0.elapsed_time(e1)
+        one.close()
+    t64 = sum(f64[n] for n in grid_n)
+    counts = {n: grid_n.count(n) for n in (512, 1024, 2048)}
+    return {"workload": f"{setups} optical tables (N mix {counts}), fwd+bwd+Adam, CUDA graph",
+            "grads_per_s": setups / (ms / 1000.0), "ms_per_step": ms,
+            "fp64_single_instance_grads_per_s": setups / (t64 / 1000.0),
+            "fp64_ms_per_setup": f64,
+            "speedup_vs_fp64_single_instance": t64 / ms}
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -371,6 +428,10 @@ def main():
                "d2h_bytes_per_step": int(A_h.numel() * 8 + C_h.numel() * 8 + gz_h.numel() * 8),
                "ms_per_step": ems / ke}
 
+    table = None
+    if not a.no_table:
+        table = table_section(xl, torch, a.table_setups, a.table_steps, inputs_seed(rank))
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_sample(U_host, g, w, zs, steps=1)
@@ -389,6 +450,7 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs (537 MB per GPU) exceed L2; no flush"},
             "grads_per_s": grads,
+            "tables": table,
             "step_parts": step_parts(xl),
             "gpu_launches": int(launches),
             "clocks": ck,

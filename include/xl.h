@@ -150,13 +150,16 @@ xl_status xl_vrs_propagate_backward(const void* g_exyz, const void* exy_in, void
  * vectorial = 0: u_in [batch][ny][nx] -> u_out [batch][my][mx].
  * vectorial = 1: u_in [batch][2][ny][nx] (Ex, Ey) -> u_out [batch][3][my][mx] (Ex', Ey', Ez'),
  *   Ez' = sum [-(X_p - x_m)/z Ex - (Y_q - y_n)/z Ey] K (the VRS kernel ratio applied to CZT).
+ * vectorial = 2: as 1, but u_in is a 3-component field [batch][3][ny][nx] whose Ez plane is not
+ *   used (the propagated Ez follows from the transverse components); the adjoint writes a zero
+ *   gradient into that plane.
  * Supported: any nx, ny, mx, my >= 1 with N + M - 1 <= 8192 per axis. z as in xl_rs_propagate.
  * -------------------------------------------------------------------------------------------*/
 xl_status xl_czt_propagate(const void* u_in, void* u_out, int32_t batch, int32_t vectorial,
                            const xl_grid* grid, const xl_window* window, double wavelength,
                            const double* z, int32_t flags, int32_t dtype, void* stream);
 
-/* Adjoint of xl_czt_propagate: g_out [batch][1 or 3][my][mx] -> g_in [batch][1 or 2][ny][nx]
+/* Adjoint of xl_czt_propagate: g_out [batch][1 or 3][my][mx] -> g_in [batch][1, 2 or 3][ny][nx]
  * (the conjugate-chirp convolutions in reverse order). */
 xl_status xl_czt_propagate_backward(const void* g_out, void* g_in, int32_t batch,
                                     int32_t vectorial, const xl_grid* grid,
@@ -192,9 +195,10 @@ typedef struct xl_element {
   double f, alpha, eta, theta; /* host parameters (used unless flags & XL_Z_DEVICE) */
 } xl_element;
 
-/* in: [batch][comps_in][ny][nx] (comps_in 1 or 2); out: [batch][comps_out][ny][nx] where
- * comps_out = 2 if the chain contains XL_TO_VECTOR or comps_in = 2, else 1. out may alias in
- * when comps_out == comps_in.
+/* in: [batch][comps_in][ny][nx] (comps_in 1, 2 or 3); out: [batch][comps_out][ny][nx] where
+ * comps_out = 2 if the chain contains XL_TO_VECTOR, else comps_in. For 3-component fields
+ * (Ex, Ey, Ez) masks and lenses act on all components, Jones elements on (Ex, Ey) only. out may
+ * alias in when comps_out == comps_in.
  * params: with flags & XL_Z_DEVICE, device doubles [batch][n_elem][4] = {f, alpha, eta, theta}
  * replacing the host values of every element (for parameters trained on the device); else NULL. */
 xl_status xl_apply_elements(const void* in, void* out, int32_t batch, int32_t comps_in,
@@ -259,6 +263,62 @@ xl_status xl_adam_step(void* params, void* m, void* v, const void* grad, int64_t
 
 /* *t_dev += 1 in stream order. */
 xl_status xl_step_advance(int32_t* t_dev, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Batched optical-table optimisation (the paper batches independent setups / samples with vmap:
+ * Methods "Data-driven rediscovery", "Features and performance"; virtual tables of Results
+ * "Towards large-scale discovery"). Every setup is the table
+ *   x-polarised Gaussian -> SLM1 (phi1) -> RS z1 -> SLM2 (phi2) -> to-vector -> half-wave plate
+ *   (theta) -> VRS z2 -> lens f -> VCZT f onto the camera -> second-moment spot size of the
+ *   total intensity,
+ * with its own grid size N (pitch = extent / N), masks, theta, z1 and z2. Setups are grouped by N
+ * and each stage of a group runs as one batched library call with device-resident parameters.
+ * xl_batch_step runs forward, backward and one Adam step (lr for masks and theta, lr_z for the
+ * distances; beta1 0.9, beta2 0.999, eps 1e-8) for all setups. With use_graph the step runs on a
+ * stream owned by the batch, ordered after and before `stream` by events: the first such call is
+ * eager (it sizes every workspace), the second captures the step into a CUDA graph, and every
+ * later call replays that graph.
+ * Masks start uniform in [0, 2 pi): SplitMix64 (seed + setup index for phi1, + 0x10000 for phi2),
+ * one draw per pixel in row-major order; the source is exp(-rho^2 / w0^2).
+ * -------------------------------------------------------------------------------------------*/
+typedef struct xl_table_config {
+  double wavelength; /* lambda */
+  double extent;     /* physical width of every input grid (pitch = extent / N) */
+  double w0;         /* source waist */
+  double f;          /* lens focal length = VCZT distance */
+  double cam_width;  /* camera window width (centred) */
+  double lr;         /* Adam step size for the masks and theta */
+  double lr_z;       /* Adam step size for z1 and z2 */
+  int32_t cam_m;     /* camera pixels per side */
+  int32_t dtype;     /* XL_C64 or XL_C128 */
+} xl_table_config;
+
+typedef struct xl_batch xl_batch; /* opaque; owns all per-setup device buffers */
+
+/* grid_n: [n_setups] powers of two in [32, 4096]; init: host [n_setups][3] = {theta, z1, z2}.
+ * Allocates with cudaMalloc (call outside stream capture). */
+xl_status xl_batch_create(const xl_table_config* cfg, int32_t n_setups, const int32_t* grid_n,
+                          const double* init, uint64_t seed, xl_batch** out, void* stream);
+
+/* One optimisation step of every setup (see above). */
+xl_status xl_batch_step(xl_batch* batch, int32_t use_graph, void* stream);
+
+#define XL_BATCH_LOSS 0         /* double: the loss of the last step (before its Adam update) */
+#define XL_BATCH_SCALARS 1      /* double[3]: theta, z1, z2 (current values) */
+#define XL_BATCH_GRAD_SCALARS 2 /* double[3]: dL/dtheta, dL/dz1, dL/dz2 of the last step */
+#define XL_BATCH_PHI1 3         /* real[N][N] (float for XL_C64, double for XL_C128) */
+#define XL_BATCH_PHI2 4
+#define XL_BATCH_GRAD_PHI1 5
+#define XL_BATCH_GRAD_PHI2 6
+
+/* Copies one quantity of one setup to host memory (synchronises the stream). */
+xl_status xl_batch_read(xl_batch* batch, int32_t what, int32_t setup, void* host_out, void* stream);
+
+/* Grid size N of a setup (-1 if out of range). */
+int32_t xl_batch_grid(xl_batch* batch, int32_t setup);
+
+/* Frees every buffer and the captured graph (synchronises the device). */
+xl_status xl_batch_destroy(xl_batch* batch);
 
 #ifdef __cplusplus
 }

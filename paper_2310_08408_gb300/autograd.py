@@ -1,0 +1,136 @@
+"""torch.autograd.Function wrappers over the C ABI: every forward and backward is a library call.
+
+Gradient convention: PyTorch's gradient of a real loss with respect to a complex tensor is
+dL/dRe + i dL/dIm, the convention of the library's *_backward entry points, so the adjoints pass
+through unchanged. Distances and element parameters are float64 CUDA tensors (read by the kernels
+at run time, so the same code serves a captured CUDA graph); phase masks are float32 (complex64
+fields) or float64 (complex128 fields).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import xl
+
+
+def _dev_z(z: torch.Tensor, batch: int) -> torch.Tensor:
+    z = z.reshape(-1)
+    if z.numel() == 1 and batch > 1:
+        z = z.expand(batch)
+    return z.contiguous()
+
+
+class RSPropagate(torch.autograd.Function):
+    """u [B][ny][nx] -> RS(u, z); z: float64 CUDA tensor [B] (or [1])."""
+
+    @staticmethod
+    def forward(ctx, u, z, grid, wavelength):
+        zz = _dev_z(z.detach(), u.shape[0])
+        ctx.save_for_backward(u, zz)
+        ctx.grid, ctx.wl, ctx.zshape = grid, wavelength, z.shape
+        return xl.rs_propagate(u.contiguous(), grid, wavelength, zz)
+
+    @staticmethod
+    def backward(ctx, g):
+        u, zz = ctx.saved_tensors
+        need_u, need_z = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        g_in, g_z = xl.rs_propagate_backward(g.contiguous(), u if need_z else None, ctx.grid, ctx.wl,
+                                             zz, want_field=need_u, want_dz=need_z)
+        if g_z is not None:
+            g_z = g_z.reshape(-1).sum().reshape(ctx.zshape) if ctx.zshape.numel() == 1 else g_z.reshape(ctx.zshape)
+        return g_in, g_z, None, None
+
+
+class VRSPropagate(torch.autograd.Function):
+    """exy [B][2][ny][nx] -> [B][3][ny][nx]."""
+
+    @staticmethod
+    def forward(ctx, exy, z, grid, wavelength):
+        zz = _dev_z(z.detach(), exy.shape[0])
+        ctx.save_for_backward(exy, zz)
+        ctx.grid, ctx.wl, ctx.zshape = grid, wavelength, z.shape
+        return xl.vrs_propagate(exy.contiguous(), grid, wavelength, zz)
+
+    @staticmethod
+    def backward(ctx, g):
+        exy, zz = ctx.saved_tensors
+        need_u, need_z = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        g_in, g_z = xl.vrs_propagate_backward(g.contiguous(), exy if need_z else None, ctx.grid,
+                                              ctx.wl, zz, want_field=need_u, want_dz=need_z)
+        if g_z is not None:
+            g_z = g_z.reshape(-1).sum().reshape(ctx.zshape) if ctx.zshape.numel() == 1 else g_z.reshape(ctx.zshape)
+        return g_in, g_z, None, None
+
+
+class CZTPropagate(torch.autograd.Function):
+    """CZT onto a window (scalar [B][ny][nx] or vectorial [B][2][ny][nx]); z is not
+    differentiated (the CZT distance is the lens focal length in the optical tables)."""
+
+    @staticmethod
+    def forward(ctx, u, z, grid, window, wavelength, vectorial):
+        zz = _dev_z(z.detach(), u.shape[0])
+        ctx.save_for_backward(zz)
+        ctx.grid, ctx.window, ctx.wl, ctx.vec = grid, window, wavelength, vectorial
+        return xl.czt_propagate(u.contiguous(), grid, window, wavelength, zz, vectorial=vectorial)
+
+    @staticmethod
+    def backward(ctx, g):
+        (zz,) = ctx.saved_tensors
+        g_in = xl.czt_propagate_backward(g.contiguous(), ctx.grid, ctx.window, ctx.wl, zz,
+                                         vectorial=ctx.vec)
+        return g_in, None, None, None, None, None
+
+
+class Elements(torch.autograd.Function):
+    """Element chain. kinds: list of element kinds; masks: list (per element) of (phi_x, phi_y)
+    tensors or None; params: float64 CUDA [B][n][4] {f, alpha, eta, theta} (differentiable)."""
+
+    @staticmethod
+    def forward(ctx, field, params, grid, wavelength, kinds, comps_in, *masks):
+        mk = [m if m.numel() else None for m in masks]
+        els = [dict(kind=k, phi_x=mk[2 * i], phi_y=mk[2 * i + 1]) for i, k in enumerate(kinds)]
+        ctx.save_for_backward(field, params, *[m for m in masks])
+        ctx.grid, ctx.wl, ctx.kinds, ctx.comps_in, ctx.els_n = grid, wavelength, kinds, comps_in, len(kinds)
+        return xl.apply_elements(field.contiguous(), grid, wavelength, els, comps_in=comps_in,
+                                 params=params.detach().contiguous())
+
+    @staticmethod
+    def backward(ctx, g):
+        field, params, *masks = ctx.saved_tensors
+        masks = [m if m.numel() else None for m in masks]
+        els = [dict(kind=k, phi_x=masks[2 * i], phi_y=masks[2 * i + 1]) for i, k in enumerate(ctx.kinds)]
+        g_in, gpx, gpy, gp = xl.apply_elements_backward(
+            g.contiguous(), field, ctx.grid, ctx.wl, els, comps_in=ctx.comps_in,
+            params=params.detach().contiguous(), want_field=ctx.needs_input_grad[0],
+            want_phi=any(ctx.needs_input_grad[6:]), want_params=ctx.needs_input_grad[1])
+        gmasks = []
+        for i in range(len(ctx.kinds)):
+            gmasks += [gpx[i], gpy[i]]
+        return (g_in, gp, None, None, None, None, *gmasks)
+
+
+def elements(field, grid, wavelength, kinds, masks, params, comps_in):
+    """Applies an element chain; masks[i] = (phi_x or None, phi_y or None)."""
+    flat = []
+    for mx, my in masks:
+        for m in (mx, my):
+            flat.append(m if m is not None else torch.empty(0, device=field.device))
+    return Elements.apply(field, params, grid, wavelength, list(kinds), comps_in, *flat)
+
+
+class IntensityLoss(torch.autograd.Function):
+    """field [B][C][ny][nx] -> loss [B] (float64)."""
+
+    @staticmethod
+    def forward(ctx, field, grid, comp_mask, mode, eps):
+        ctx.save_for_backward(field)
+        ctx.grid, ctx.mask, ctx.mode, ctx.eps = grid, comp_mask, mode, eps
+        loss, _ = xl.intensity_loss(field.contiguous(), grid, comp_mask, mode, eps)
+        return loss
+
+    @staticmethod
+    def backward(ctx, g_loss):
+        (field,) = ctx.saved_tensors
+        g = xl.intensity_loss_backward(field, ctx.grid, ctx.mask, ctx.mode, ctx.eps,
+                                       g_loss=g_loss.contiguous())
+        return g, None, None, None, None

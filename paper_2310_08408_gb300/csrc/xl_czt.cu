@@ -94,7 +94,7 @@ void axes(const void* tab, const CztTabArgs& a, Axis<cplx<T>>* ax, Axis<cplx<T>>
 }
 
 template <typename T>
-xl_status run(bool adjoint, const void* in, void* out, int32_t batch, int32_t vec,
+xl_status run(bool adjoint, const void* in, void* out, int32_t batch, bool vec, int in_planes,
               const xl_grid* g, const xl_window* w, double wavelength, const double* z,
               int32_t flags, int32_t dtype, cudaStream_t s) {
   const CztTabArgs ta = tab_args(g, w, wavelength);
@@ -118,7 +118,8 @@ xl_status run(bool adjoint, const void* in, void* out, int32_t batch, int32_t ve
   d.nx = g->nx; d.ny = g->ny; d.mx = w->mx; d.my = w->my;
   d.x0 = g->x0; d.dx = g->dx; d.y0 = g->y0; d.dy = g->dy;
   d.xo0 = w->xo0; d.dxo = w->dxo; d.yo0 = w->yo0; d.dyo = w->dyo;
-  const int cin = vec ? 2 : 1, cwin = vec ? 3 : 1;
+  const int cin = in_planes, cwin = vec ? 3 : 1;
+  d.in_planes = in_planes;
   for (int32_t b0 = 0; b0 < batch;) {
     int nb = 1;
     if (!zdev)
@@ -139,6 +140,10 @@ xl_status run(bool adjoint, const void* in, void* out, int32_t batch, int32_t ve
       char* dst = (char*)out + (size_t)b0 * cin * in_plane * cs;
       XL_TRY(czt_pass<T>(CZT_ADJ_Y, vec, ta.Ly, src, Tb, d, ay, nb, s));
       XL_TRY(czt_pass<T>(CZT_ADJ_X, vec, ta.Lx, Tb, dst, d, ax, nb, s));
+      if (in_planes == 3) {
+        // the unused Ez plane of a 3-component input receives a zero gradient
+        XL_CUDA_TRY(cudaMemset2DAsync(dst + 2 * in_plane * cs, 3 * in_plane * cs, 0, in_plane * cs, nb, s));
+      }
     }
     b0 += nb;
   }
@@ -152,9 +157,11 @@ xl_status dispatch(bool adjoint, const void* in, void* out, int32_t batch, int32
   if (batch == 0) return XL_OK;
   if (!in || !out) return fail(XL_ERR_ARG, "field pointer is NULL");
   if (in == out) return fail(XL_ERR_ARG, "output may not alias the input");
+  if (vec < 0 || vec > 2) return fail(XL_ERR_ARG, "vectorial must be 0, 1 or 2");
   cudaStream_t s = (cudaStream_t)stream;
-  if (dtype == XL_C128) return run<double>(adjoint, in, out, batch, vec != 0, g, w, wavelength, z, flags, dtype, s);
-  return run<float>(adjoint, in, out, batch, vec != 0, g, w, wavelength, z, flags, dtype, s);
+  const int in_planes = vec == 0 ? 1 : (vec == 1 ? 2 : 3);
+  if (dtype == XL_C128) return run<double>(adjoint, in, out, batch, vec != 0, in_planes, g, w, wavelength, z, flags, dtype, s);
+  return run<float>(adjoint, in, out, batch, vec != 0, in_planes, g, w, wavelength, z, flags, dtype, s);
 }
 
 }  // namespace

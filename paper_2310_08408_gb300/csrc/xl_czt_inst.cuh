@@ -9,7 +9,7 @@ template <typename T, int L, bool VEC>
 xl_status pass_LV(int which, const void* src, void* dst, const CztDims& d, const Axis<cplx<T>>& ax,
                   int nb, cudaStream_t s) {
   constexpr int ROWS = czt_rows<L, sizeof(cplx<T>)>();
-  const size_t sm = (size_t)ROWS * srow(L) * sizeof(cplx<T>);
+  const size_t sm = (size_t)ROWS * rpitch(L) * sizeof(cplx<T>);
   const void* tw;
   XL_TRY(twiddles(L, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
   const cplx<T>* twc = (const cplx<T>*)tw;

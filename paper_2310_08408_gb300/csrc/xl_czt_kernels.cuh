@@ -43,6 +43,8 @@ struct CztDims {
   double xo0, dxo, yo0, dyo;  // output window
   const double* zdev;         // device z (or nullptr)
   double zval;
+  int in_planes;              // planes per batch element of the input-grid field (fwd x input,
+                              // adjoint x output): 1, 2, or 3 (a vector field whose Ez is unused)
 };
 
 template <int L, int CS> __host__ __device__ constexpr int czt_rows() {
@@ -61,42 +63,35 @@ __device__ __forceinline__ void chirp_conv(C (&v)[16], C* row, int t, const C* _
   team_fft<L, +1>(v, row, t, tw);
 }
 
-// Writes the team's register row (first n_out entries) to its smem row, then the block stores
-// ROWS rows transposed: dst[j * ld + c0 + r] for j < n_out, r < ROWS (c0 + r < n_cols).
+// Writes the team's register row to its shared-memory row (pitch rpitch(L)), then the block
+// stores the first n_out entries of its ROWS rows transposed: dst[j * ld + c0 + r]. Ends with a
+// barrier: callers that transform again reuse the same rows.
 template <int L, int ROWS, typename C>
 __device__ __forceinline__ void store_transposed(const C (&v)[16], C* sm, int team, int t, int n_out,
                                                  C* __restrict__ dst, int64_t ld, int c0, int n_cols) {
   constexpr int TT = L / 16;
-  constexpr int SR = srow(L);
+  constexpr int P = rpitch(L);
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < 16; ++q) sm[team * SR + spad(t + q * TT)] = v[q];
+  for (int q = 0; q < 16; ++q) sm[team * P + spad(t + q * TT)] = v[q];
   __syncthreads();
-  for (int j = threadIdx.x; j < n_out; j += ROWS * TT) {
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r)
-      if (c0 + r < n_cols) dst[(int64_t)j * ld + c0 + r] = sm[r * SR + spad(j)];
-  }
+  store_rows_transposed<ROWS, P>(sm, n_out, dst, ld, c0, n_cols);
+  __syncthreads();
 }
 
-// Loads ROWS columns transposed: the team's row r gets src[j * ld + c0 + r] for j < n_in
-// (zero beyond), times pre[j] (pre may be null), into registers.
+// Loads ROWS columns transposed: the team's row r gets src[j * ld + c0 + r] for j < n_in (zero
+// up to L), into registers.
 template <int L, int ROWS, typename C>
 __device__ __forceinline__ void load_transposed(C (&v)[16], C* sm, int team, int t, int n_in,
                                                 const C* __restrict__ src, int64_t ld, int c0,
                                                 int n_cols) {
   constexpr int TT = L / 16;
-  constexpr int SR = srow(L);
-  typedef decltype(v[0].x) T;
+  constexpr int P = rpitch(L);
   __syncthreads();
-  for (int j = threadIdx.x; j < L; j += ROWS * TT) {
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r)
-      sm[r * SR + spad(j)] = (j < n_in && c0 + r < n_cols) ? src[(int64_t)j * ld + c0 + r] : mk((T)0, (T)0);
-  }
+  load_rows_transposed<ROWS, P>(sm, n_in, L, src, ld, c0, n_cols);
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = sm[team * SR + spad(t + q * TT)];
+  for (int q = 0; q < 16; ++q) v[q] = sm[team * P + spad(t + q * TT)];
   __syncthreads();
 }
 
@@ -112,20 +107,20 @@ k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d,
   typedef cplx<T> C;
   constexpr int ROWS = czt_rows<L, sizeof(C)>();
   constexpr int TT = L / 16;
-  constexpr int SR = srow(L);
+  constexpr int SR = rpitch(L);
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
   const int b = blockIdx.y;
   const int n0 = blockIdx.x * ROWS;
   const int n = min(n0 + team, d.ny - 1);  // teams past the edge compute a valid row, store nothing
-  const int cin = VEC ? 2 : 1, cT = VEC ? 3 : 1;
+  const int cT = VEC ? 3 : 1;
   const int64_t plane = (int64_t)d.nx * d.ny, tplane = (int64_t)d.mx * d.ny;
   C* row = sm + team * SR;
 #pragma unroll 1
   for (int c = 0; c < cT; ++c) {
     C v[16];
-    const C* s0 = in + ((int64_t)b * cin) * plane + (int64_t)n * d.nx;
+    const C* s0 = in + ((int64_t)b * d.in_planes) * plane + (int64_t)n * d.nx;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int m = t + q * TT;
@@ -162,7 +157,7 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
   typedef cplx<T> C;
   constexpr int ROWS = czt_rows<L, sizeof(C)>();
   constexpr int TT = L / 16;
-  constexpr int SR = srow(L);
+  constexpr int SR = rpitch(L);
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
@@ -221,7 +216,7 @@ k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, 
   typedef cplx<T> C;
   constexpr int ROWS = czt_rows<L, sizeof(C)>();
   constexpr int TT = L / 16;
-  constexpr int SR = srow(L);
+  constexpr int SR = rpitch(L);
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
@@ -281,7 +276,7 @@ k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d
   typedef cplx<T> C;
   constexpr int ROWS = czt_rows<L, sizeof(C)>();
   constexpr int TT = L / 16;
-  constexpr int SR = srow(L);
+  constexpr int SR = rpitch(L);
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
@@ -318,7 +313,7 @@ k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d
     }
     chirp_conv<L>(v, row, t, tw, ax.bhat_adj);
     if (live) {
-      C* dst = gin + ((int64_t)b * cout + c) * plane + (int64_t)n * d.nx;
+      C* dst = gin + ((int64_t)b * d.in_planes + c) * plane + (int64_t)n * d.nx;
       const T iz = VEC ? (T)(1.0 / czt_z(d)) : (T)0;
       const T yn = (T)(d.y0 + n * d.dy);
 #pragma unroll

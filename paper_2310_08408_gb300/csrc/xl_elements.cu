@@ -9,6 +9,8 @@
 //   polariser  J = R(-a) diag(1, 0) R(a)
 //   wave plate J = R(-t) diag(1, exp(i eta)) R(t),  R(t) = [[cos t, sin t], [-sin t, cos t]]
 //   to-vector  (Ex, Ey) = (u, 0)
+// Three-component fields (Ex, Ey, Ez): phase masks and lenses act on all three components, Jones
+// elements on (Ex, Ey) only.
 // One thread handles one pixel of one batch element and applies the whole chain in registers
 // (the chain is read from kernel parameters), so a chain costs one read and one write of the
 // field. The lens phase is separable, exp(-ik x^2/2f) exp(-ik y^2/2f): both factors are
@@ -158,13 +160,14 @@ __device__ __forceinline__ cplx<T> lens_factor(const cplx<T>* tab, int s, int b,
 template <typename T>
 __device__ __forceinline__ void elem_fwd(const ElemSet& E, const ElemDims& d, const cplx<T>* lens,
                                          int nlens, int e, int b, int64_t i, int m, int n,
-                                         cplx<T>& c0, cplx<T>& c1) {
+                                         cplx<T>& c0, cplx<T>& c1, cplx<T>& c2) {
   switch (E.kind[e]) {
     case XL_SLM: {
       T s, c;
       xsincos(phase_at<T>(E.phx[e], E.phstride[e], b, i), &s, &c);
       c0 = cmul(c0, mk(c, s));
       c1 = cmul(c1, mk(c, s));
+      c2 = cmul(c2, mk(c, s));
       break;
     }
     case XL_SSLM: {
@@ -179,6 +182,7 @@ __device__ __forceinline__ void elem_fwd(const ElemSet& E, const ElemDims& d, co
       cplx<T> L = lens_factor<T>(lens, E.lens_slot[e], d.params_dev ? b : 0, nlens, d, m, n);
       c0 = cmul(c0, L);
       c1 = cmul(c1, L);
+      c2 = cmul(c2, L);
       break;
     }
     case XL_POLARIZER: {
@@ -210,11 +214,13 @@ __global__ void __launch_bounds__(256) k_elem_fwd(const cplx<T>* __restrict__ in
   const int m = (int)(i % d.nx), n = (int)(i / d.nx);
   const cplx<T>* src = in + (int64_t)b * d.comps_in * d.plane;
   cplx<T> c0 = src[i];
-  cplx<T> c1 = d.comps_in == 2 ? src[d.plane + i] : mk((T)0, (T)0);
-  for (int e = 0; e < E.n; ++e) elem_fwd<T>(E, d, lens, nlens, e, b, i, m, n, c0, c1);
+  cplx<T> c1 = d.comps_in >= 2 ? src[d.plane + i] : mk((T)0, (T)0);
+  cplx<T> c2 = d.comps_in == 3 ? src[2 * d.plane + i] : mk((T)0, (T)0);
+  for (int e = 0; e < E.n; ++e) elem_fwd<T>(E, d, lens, nlens, e, b, i, m, n, c0, c1, c2);
   cplx<T>* dst = out + (int64_t)b * d.comps_out * d.plane;
   dst[i] = c0;
-  if (d.comps_out == 2) dst[d.plane + i] = c1;
+  if (d.comps_out >= 2) dst[d.plane + i] = c1;
+  if (d.comps_out == 3) dst[2 * d.plane + i] = c2;
 }
 
 struct ElemGrad {
@@ -242,34 +248,38 @@ __global__ void __launch_bounds__(256) k_elem_bwd(const cplx<T>* __restrict__ go
 #pragma unroll
   for (int e = 0; e < kMaxElem; ++e) gphx_acc[e] = gphy_acc[e] = (T)0;
   for (int b = b_lo; b < b_hi; ++b) {
-    cplx<T> s0[kMaxElem + 1], s1[kMaxElem + 1];
+    cplx<T> s0[kMaxElem + 1], s1[kMaxElem + 1], s2[kMaxElem + 1];
     const cplx<T>* src = in + (int64_t)b * d.comps_in * d.plane;
     s0[0] = src[ii];
-    s1[0] = d.comps_in == 2 ? src[d.plane + ii] : mk((T)0, (T)0);
+    s1[0] = d.comps_in >= 2 ? src[d.plane + ii] : mk((T)0, (T)0);
+    s2[0] = d.comps_in == 3 ? src[2 * d.plane + ii] : mk((T)0, (T)0);
 #pragma unroll
     for (int e = 0; e < kMaxElem; ++e) {
       if (e >= E.n) break;
       s0[e + 1] = s0[e];
       s1[e + 1] = s1[e];
-      elem_fwd<T>(E, d, lens, nlens, e, b, ii, m, n, s0[e + 1], s1[e + 1]);
+      s2[e + 1] = s2[e];
+      elem_fwd<T>(E, d, lens, nlens, e, b, ii, m, n, s0[e + 1], s1[e + 1], s2[e + 1]);
     }
     const cplx<T>* gsrc = gout + (int64_t)b * d.comps_out * d.plane;
     cplx<T> g0 = gsrc[ii];
-    cplx<T> g1 = d.comps_out == 2 ? gsrc[d.plane + ii] : mk((T)0, (T)0);
+    cplx<T> g1 = d.comps_out >= 2 ? gsrc[d.plane + ii] : mk((T)0, (T)0);
+    cplx<T> g2 = d.comps_out == 3 ? gsrc[2 * d.plane + ii] : mk((T)0, (T)0);
     double sg[kMaxElem][4];
 #pragma unroll
     for (int e = 0; e < kMaxElem; ++e) sg[e][0] = sg[e][1] = sg[e][2] = sg[e][3] = 0.0;
 #pragma unroll
     for (int e = kMaxElem - 1; e >= 0; --e) {
       if (e >= E.n) continue;
-      const cplx<T> u0 = s0[e], u1 = s1[e], o0 = s0[e + 1], o1 = s1[e + 1];
+      const cplx<T> u0 = s0[e], u1 = s1[e], o0 = s0[e + 1], o1 = s1[e + 1], o2 = s2[e + 1];
       switch (E.kind[e]) {
         case XL_SLM: {
-          gphx_acc[e] += cmulc(g0, o0).y + cmulc(g1, o1).y;
+          gphx_acc[e] += cmulc(g0, o0).y + cmulc(g1, o1).y + cmulc(g2, o2).y;
           T s, c;
           xsincos(phase_at<T>(E.phx[e], E.phstride[e], b, ii), &s, &c);
           g0 = cmul(g0, mk(c, -s));
           g1 = cmul(g1, mk(c, -s));
+          g2 = cmul(g2, mk(c, -s));
           break;
         }
         case XL_SSLM: {
@@ -287,10 +297,12 @@ __global__ void __launch_bounds__(256) k_elem_bwd(const cplx<T>* __restrict__ go
           const T xm = (T)(d.x0 + m * d.dx), yn = (T)(d.y0 + n * d.dy);
           const T coef = (T)(d.k / (2.0 * f * f)) * (xm * xm + yn * yn);  // d out / d f = i coef out
           sg[e][0] += (double)cdot_re(g0, mk(-o0.y * coef, o0.x * coef)) +
-                      (double)cdot_re(g1, mk(-o1.y * coef, o1.x * coef));
+                      (double)cdot_re(g1, mk(-o1.y * coef, o1.x * coef)) +
+                      (double)cdot_re(g2, mk(-o2.y * coef, o2.x * coef));
           cplx<T> L = lens_factor<T>(lens, E.lens_slot[e], d.params_dev ? b : 0, nlens, d, m, n);
           g0 = cmulc(g0, L);
           g1 = cmulc(g1, L);
+          g2 = cmulc(g2, L);
           break;
         }
         case XL_POLARIZER: {
@@ -316,7 +328,8 @@ __global__ void __launch_bounds__(256) k_elem_bwd(const cplx<T>* __restrict__ go
     if (live && gin) {
       cplx<T>* dst = gin + (int64_t)b * d.comps_in * d.plane;
       dst[i] = g0;
-      if (d.comps_in == 2) dst[d.plane + i] = g1;
+      if (d.comps_in >= 2) dst[d.plane + i] = g1;
+      if (d.comps_in == 3) dst[2 * d.plane + i] = g2;
     }
     if (!G.accumulate_shared && live) {
 #pragma unroll
@@ -381,7 +394,7 @@ xl_status prepare(const xl_element* el, int32_t n_el, int32_t comps_in, const xl
     return fail(XL_ERR_ARG, "elements: NULL grid/list or more than 8 elements");
   if (g->nx < 1 || g->ny < 1) return fail(XL_ERR_ARG, "elements: empty grid");
   if (!(wavelength > 0)) return fail(XL_ERR_ARG, "elements: wavelength must be positive");
-  if (comps_in != 1 && comps_in != 2) return fail(XL_ERR_ARG, "elements: comps_in must be 1 or 2");
+  if (comps_in < 1 || comps_in > 3) return fail(XL_ERR_ARG, "elements: comps_in must be 1, 2 or 3");
   if (flags & ~XL_Z_DEVICE) return fail(XL_ERR_ARG, "elements: unknown flag bits");
   if ((flags & XL_Z_DEVICE) && !params) return fail(XL_ERR_ARG, "elements: device parameters are NULL");
   std::memset(E, 0, sizeof(*E));
@@ -404,7 +417,7 @@ xl_status prepare(const xl_element* el, int32_t n_el, int32_t comps_in, const xl
         if (!x.phi_x) return fail(XL_ERR_ARG, "SLM needs phi_x");
         break;
       case XL_SSLM:
-        if (c != 2) return fail(XL_ERR_ARG, "super-SLM needs a 2-component field");
+        if (c < 2) return fail(XL_ERR_ARG, "super-SLM needs a vector field");
         if (!x.phi_x || !x.phi_y) return fail(XL_ERR_ARG, "super-SLM needs phi_x and phi_y");
         break;
       case XL_LENS:
@@ -413,7 +426,7 @@ xl_status prepare(const xl_element* el, int32_t n_el, int32_t comps_in, const xl
         break;
       case XL_POLARIZER:
       case XL_WAVEPLATE:
-        if (c != 2) return fail(XL_ERR_ARG, "polariser / wave plate need a 2-component field");
+        if (c < 2) return fail(XL_ERR_ARG, "polariser / wave plate need a vector field");
         break;
       case XL_TO_VECTOR:
         if (c != 1) return fail(XL_ERR_ARG, "to-vector needs a 1-component field");

@@ -10,7 +10,8 @@
 // Stage s (sub-transform size Ns, radix R) of the autosort Stockham formulation: butterfly j
 // reads x[j + r L/R] (r < R), multiplies element r by W_{Ns R}^{(j mod Ns) r}, takes an R-point
 // DFT, and writes y[(j div Ns) Ns R + (j mod Ns) + r Ns]. Twiddles come from a table of
-// exp(-2 pi i m / L) built in double precision on the host (conjugated for inverse transforms).
+// exp(-2 pi i k r / (Ns R)) per stage, each rounded once from double precision on the host
+// (conjugated for inverse transforms), read as contiguous 16-byte vectors by each butterfly.
 // Shared-memory rows carry one pad element per 16 so that the stride-16 writes of the first
 // stage hit distinct banks.
 //
@@ -124,9 +125,46 @@ template <int L> struct FFTShape {
   static_assert((1 << LOG) == L && L >= 64 && L <= 8192, "FFT length: power of two in [64, 8192]");
 };
 
-template <typename C> __device__ __forceinline__ C twiddle(const C* __restrict__ tw, int m, bool inv) {
-  C w = __ldg(tw + m);
-  return inv ? cconj(w) : w;
+// Twiddle table layout: for every stage S >= 1 (sub-transform size Ns, radix R) a block of
+// Ns x R entries tw[off_S + k R + r] = exp(-2 pi i k r / (Ns R)), each rounded once from double
+// precision on the host, so a butterfly reads its R twiddles as contiguous 16-byte vectors.
+__host__ __device__ constexpr int tw_stage_offset(int L, int S) {
+  // stages 1.. S-1 precede stage S; stage s >= 1 has Ns = 16^s entries per r (R = 16 except a
+  // final smaller radix)
+  int off = 0, Ns = 16;
+  for (int s = 1; s < S; ++s) {
+    const int R = (Ns * 16 <= L) ? 16 : L / Ns;
+    off += Ns * R;
+    Ns *= R;
+  }
+  return off;
+}
+__host__ __device__ constexpr int tw_table_size(int L) { return tw_stage_offset(L, cilog2(L) / 4 + (cilog2(L) % 4 ? 1 : 0)); }
+
+// Multiplies v[B r] by W_{Ns R}^{k r}, r = 1..R-1 (conjugated for inverse transforms).
+template <int R, int B, typename C>
+__device__ __forceinline__ void apply_twiddles(C* v, const C* __restrict__ row, bool inv) {
+  typedef decltype(v[0].x) T;
+  if constexpr (sizeof(C) == 8) {
+    const float4* p = reinterpret_cast<const float4*>(row);
+#pragma unroll
+    for (int h = 0; h < R / 2; ++h) {
+      const float4 w = __ldg(p + h);
+      if (h > 0) {
+        const C w0 = mk((T)w.x, (T)(inv ? -w.y : w.y));
+        v[2 * h * B] = cmul(v[2 * h * B], w0);
+      }
+      const C w1 = mk((T)w.z, (T)(inv ? -w.w : w.w));
+      v[(2 * h + 1) * B] = cmul(v[(2 * h + 1) * B], w1);
+    }
+  } else {
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      C w = __ldg(row + r);
+      if (inv) w = cconj(w);
+      v[r * B] = cmul(v[r * B], w);
+    }
+  }
 }
 
 // Stage S (>= 1) of the transform; Ns = 16^S for the radix-16 prefix.
@@ -148,9 +186,7 @@ __device__ __forceinline__ void fft_stage(C (&v)[16], C* sm, int t, const C* __r
   for (int b = 0; b < B; ++b) {
     const int j = t + b * TT;
     const int k = j & (Ns - 1);
-    const int step = k * (L / (Ns * R));
-#pragma unroll
-    for (int r = 1; r < R; ++r) v[b + B * r] = cmul(v[b + B * r], twiddle(tw, step * r, DIR > 0));
+    apply_twiddles<R, B>(v + b, tw + tw_stage_offset(L, S) + k * R, DIR > 0);
     dftR<R, DIR, B>(v + b);
   }
   if constexpr (!last) {
@@ -163,6 +199,47 @@ __device__ __forceinline__ void fft_stage(C (&v)[16], C* sm, int t, const C* __r
     }
     fft_stage<L, DIR, (S + 1 < Sh::NST ? S + 1 : S)>(v, sm, t, tw);
   }
+}
+
+// Row pitch (in elements) of a block's shared-memory rows: at least srow(L) and congruent to
+// 4 modulo 16, so that lanes reading the same column of 4 consecutive rows (the transposed
+// stores and loads) fall in distinct banks.
+__host__ __device__ constexpr int rpitch(int L) { return srow(L) + ((4 - srow(L) % 16) + 16) % 16; }
+
+// Transposed block store: rows 0..ROWS-1 of the block's shared memory (pitch P) hold the
+// first n_out entries of ROWS transforms; element j of row r goes to dst[j * ld + c0 + r]
+// (r with c0 + r < n_cols). Lanes are grouped so that each warp instruction writes whole
+// 32-byte sectors (G = 32 / sizeof(C) consecutive rows of one j per group of lanes).
+template <int ROWS, int P, typename C>
+__device__ __forceinline__ void store_rows_transposed(const C* sm, int n_out, C* __restrict__ dst,
+                                                      int64_t ld, int c0, int n_cols) {
+  constexpr int G0 = 32 / (int)sizeof(C);
+  constexpr int G = G0 < ROWS ? G0 : ROWS;
+  constexpr int LG = G == 4 ? 2 : (G == 2 ? 1 : 0);
+#pragma unroll 1
+  for (int grp = 0; grp < ROWS / G; ++grp)
+    for (int e = threadIdx.x; e < n_out * G; e += blockDim.x) {
+      const int r = grp * G + (e & (G - 1)), j = e >> LG;
+      if (c0 + r < n_cols) dst[(int64_t)j * ld + c0 + r] = sm[r * P + spad(j)];
+    }
+}
+
+// Transposed block load (inverse of the store): row r of shared memory gets
+// src[j * ld + c0 + r] for j < n_in and zero for n_in <= j < n_fill.
+template <int ROWS, int P, typename C>
+__device__ __forceinline__ void load_rows_transposed(C* sm, int n_in, int n_fill,
+                                                     const C* __restrict__ src, int64_t ld, int c0,
+                                                     int n_cols) {
+  typedef decltype(sm[0].x) T;
+  constexpr int G0 = 32 / (int)sizeof(C);
+  constexpr int G = G0 < ROWS ? G0 : ROWS;
+  constexpr int LG = G == 4 ? 2 : (G == 2 ? 1 : 0);
+#pragma unroll 1
+  for (int grp = 0; grp < ROWS / G; ++grp)
+    for (int e = threadIdx.x; e < n_fill * G; e += blockDim.x) {
+      const int r = grp * G + (e & (G - 1)), j = e >> LG;
+      sm[r * P + spad(j)] = (j < n_in && c0 + r < n_cols) ? src[(int64_t)j * ld + c0 + r] : mk((T)0, (T)0);
+    }
 }
 
 // Full length-L transform of one row held by a team (see the file comment for the layout).

@@ -9,7 +9,7 @@ namespace {
 template <typename T, int LX>
 xl_status pass1_L(const void* in, void* Tb, int nx, int ny, int cin, int cT, int np, cudaStream_t s) {
   constexpr int ROWS = rows_transp<LX, sizeof(cplx<T>)>();
-  const size_t sm = (size_t)ROWS * srow(LX) * sizeof(cplx<T>);
+  const size_t sm = (size_t)ROWS * rpitch(LX) * sizeof(cplx<T>);
   const void* tw;
   XL_TRY(twiddles(LX, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
   XL_TRY(smem_attr((const void*)k_rs_pass1<T, LX>, sm));
@@ -24,7 +24,7 @@ xl_status pass1_L(const void* in, void* Tb, int nx, int ny, int cin, int cT, int
 template <typename T, int LX>
 xl_status pass3_L(const void* Tb, void* out, int nx, int ny, int cout, int cT, int np, cudaStream_t s) {
   constexpr int ROWS = rows_transp<LX, sizeof(cplx<T>)>();
-  const size_t sm = (size_t)ROWS * srow(LX) * sizeof(cplx<T>);
+  const size_t sm = (size_t)ROWS * rpitch(LX) * sizeof(cplx<T>);
   const void* tw;
   XL_TRY(twiddles(LX, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
   XL_TRY(smem_attr((const void*)k_rs_pass3<T, LX>, sm));
@@ -40,7 +40,7 @@ template <typename T, int LY, int MODE>
 xl_status pass2_LM(void* Tb, const void* Ub, const void* Hq, double* dz, const P2Args& a, int nb,
                    cudaStream_t s) {
   constexpr int ROWS = rows_cols<LY>();
-  const size_t sm = (size_t)ROWS * srow(LY) * sizeof(cplx<T>);
+  const size_t sm = (size_t)p2_rows_per_team<MODE>() * ROWS * srow(LY) * sizeof(cplx<T>);
   const void* tw;
   XL_TRY(twiddles(LY, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
   XL_TRY(smem_attr((const void*)k_rs_pass2<T, LY, MODE>, sm));
@@ -69,7 +69,7 @@ template <typename T, int LX, int LY>
 xl_status gen_LL(void* S, void* Hq, const GenArgs& g, cudaStream_t s) {
   constexpr int RA = rows_transp<LX, sizeof(cplx<T>)>();
   constexpr int RB = rows_cols<LY>();
-  const size_t sa = (size_t)RA * srow(LX) * sizeof(cplx<T>);
+  const size_t sa = (size_t)RA * rpitch(LX) * sizeof(cplx<T>);
   const size_t sb = (size_t)RB * srow(LY) * sizeof(cplx<T>);
   const void *twx, *twy;
   XL_TRY(twiddles(LX, sizeof(T) == 8 ? XL_C128 : XL_C64, &twx));

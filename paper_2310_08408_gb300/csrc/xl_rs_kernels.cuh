@@ -37,13 +37,6 @@ template <int L, int CS> __host__ __device__ constexpr int rows_transp() {
 }
 template <int L> __host__ __device__ constexpr int rows_cols() { return (4096 / L) > 1 ? 4096 / L : 1; }
 
-// Geometry of one propagation (scalars passed by value to every kernel).
-struct RsGeom {
-  int nx, ny;
-  double dx, dy;
-  double k;  // 2 pi / wavelength
-};
-
 // ---------------------------------------------------------------------------------------------
 // Spectrum access: value of spectrum `kind` at full-grid frequency (kx, ky), kx < LX, ky < LY.
 template <typename C>
@@ -65,9 +58,9 @@ __global__ void __launch_bounds__(rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16)
 k_rs_pass1(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, int nx, int ny, int cin,
            int cT, const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
-  constexpr int ROWS = rows_transp<LX, sizeof(cplx<T>)>();
+  constexpr int ROWS = rows_transp<LX, sizeof(C)>();
   constexpr int TT = LX / 16;
-  constexpr int SR = srow(LX);
+  constexpr int P = rpitch(LX);
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
@@ -79,19 +72,13 @@ k_rs_pass1(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, int nx, int
   C v[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = (q < 8 && y < ny) ? src[t + q * TT] : mk((T)0, (T)0);
-  C* row = sm + team * SR;
+  C* row = sm + team * P;
   team_fft<LX, -1>(v, row, t, tw);
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < 16; ++q) row[spad(t + q * TT)] = v[q];
   __syncthreads();
-  // transposed store: each thread writes ROWS consecutive y of one kx
-  for (int kx = threadIdx.x; kx < LX; kx += ROWS * TT) {
-    C* d = dst + (int64_t)kx * ny + y0;
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r)
-      if (y0 + r < ny) d[r] = sm[r * SR + spad(kx)];
-  }
+  store_rows_transposed<ROWS, P>(sm, LX, dst, ny, y0, ny);
 }
 
 // Pass 3: inverse row FFT from T[kx][y] into planes [ny][nx] (crop to x < nx).
@@ -101,23 +88,18 @@ __global__ void __launch_bounds__(rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16)
 k_rs_pass3(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, int nx, int ny, int cout,
            int cT, const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
-  constexpr int ROWS = rows_transp<LX, sizeof(cplx<T>)>();
+  constexpr int ROWS = rows_transp<LX, sizeof(C)>();
   constexpr int TT = LX / 16;
-  constexpr int SR = srow(LX);
+  constexpr int P = rpitch(LX);
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
   const int p = blockIdx.y;
   const int y0 = blockIdx.x * ROWS;
   const C* src = Tb + ((int64_t)(p / cout) * cT + (p % cout)) * (int64_t)LX * ny;
-  for (int kx = threadIdx.x; kx < LX; kx += ROWS * TT) {
-    const C* s = src + (int64_t)kx * ny + y0;
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r)
-      if (y0 + r < ny) sm[r * SR + spad(kx)] = s[r];
-  }
+  load_rows_transposed<ROWS, P>(sm, LX, LX, src, ny, y0, ny);
   __syncthreads();
-  C* row = sm + team * SR;
+  C* row = sm + team * P;
   C v[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = row[spad(t + q * TT)];
@@ -152,6 +134,33 @@ struct P2Args {
   int slot[NKIND];      // spectrum kind -> slot in the Hq buffer (-1: absent)
 };
 
+// Spectrum `Hk` along one kx row at ky = t + q TT (TT = LY / 16, ny = 8 TT): the quadrant row
+// ax = mirror(kx) is fixed per row; ky mirrors for q > 8 (and for q == 8 when t > 0).
+template <typename C>
+__device__ __forceinline__ C spec_row(const C* __restrict__ hrow, int q, int t, int TT, bool flipx,
+                                      bool oddx, bool oddy) {
+  bool fy;
+  int ay;
+  if (q < 8) {  // q is a compile-time constant after unrolling
+    fy = false;
+    ay = t + q * TT;
+  } else if (q == 8) {
+    fy = t > 0;
+    ay = fy ? 8 * TT - t : 8 * TT;
+  } else {
+    fy = true;
+    ay = (16 - q) * TT - t;
+  }
+  C h = __ldg(hrow + ay);
+  if ((oddx && flipx) != (oddy && fy)) h = mk(-h.x, -h.y);
+  return h;
+}
+
+// Compiler-only memory fence: keeps the spectrum loads of the multiply loops in groups of four
+// (without it all 16-32 loads are hoisted ahead of the arithmetic and the registers spill).
+#define XL_GROUP_FENCE(q) \
+  if (((q) & 3) == 3) asm volatile("" ::: "memory")
+
 template <typename C>
 __device__ __forceinline__ void load_col(C (&v)[16], const C* __restrict__ src, int t, int TT) {
 #pragma unroll
@@ -177,10 +186,22 @@ __device__ __forceinline__ double block_sum(double v, double* sbuf) {
   return s;
 }
 
-// grid: (ceil(LX / ROWS), nbatch). Hq: spectra [NKIND slots used by mode][nx+1][ny+1].
-// dz_part: [nbatch][LX] partial sums (one per kx), reduced later in fixed order.
+// Blocks per SM the register budget of each pass-2 mode aims at (256-thread blocks).
+template <int MODE> __host__ __device__ constexpr int p2_min_blocks() {
+  return MODE == P2_RS ? 4 : (MODE == P2_RS_BWD ? 3 : 2);
+}
+// Shared-memory rows per team of each mode (VRS modes keep the Ez spectrum in a second row).
+template <int MODE> __host__ __device__ constexpr int p2_rows_per_team() {
+  return (MODE == P2_VRS || MODE == P2_VRS_BWD) ? 2 : 1;
+}
+
+// grid: (ceil(LX / ROWS), nbatch). Hq: spectra [slots][nx+1][ny+1].
+// dz_part: [nbatch][gridDim.x] partial sums, reduced later in fixed order.
 template <typename T, int LY, int MODE>
-__global__ void __launch_bounds__(rows_cols<LY>() * (LY / 16))
+__global__ void __launch_bounds__(rows_cols<LY>() * (LY / 16),
+                                  (p2_min_blocks<MODE>() * 256) / (rows_cols<LY>() * (LY / 16)) > 0
+                                      ? (p2_min_blocks<MODE>() * 256) / (rows_cols<LY>() * (LY / 16))
+                                      : 1)
 k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<T>* __restrict__ Hq,
            double* __restrict__ dz_part, P2Args a, const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
@@ -198,31 +219,37 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
   const int b = blockIdx.y;
   C* row = sm + team * SR;
   C* T0 = Tb + (int64_t)b * a.cT * a.t_plane + (int64_t)kx * a.ny;
-  const int64_t HK = a.hq_kind;
+  const bool flipx = kx > a.nx;
+  const int64_t hrow_off = (int64_t)(flipx ? LX - kx : kx) * (a.ny + 1);
+  auto H = [&](int kind) { return Hq + a.slot[kind] * a.hq_kind + hrow_off; };
   C v[16];
   double dz = 0.0;
 
   if constexpr (MODE == P2_RS) {
     load_col(v, T0, t, TT);
     team_fft<LY, -1>(v, row, t, tw);
+    const C* h = H(KH);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      C h = spec_at(Hq + a.slot[KH] * HK, kx, t + q * TT, a.nx, a.ny, false, false);
-      v[q] = a.conj ? cmulc(v[q], h) : cmul(v[q], h);
+      const C hv = spec_row(h, q, t, TT, flipx, false, false);
+      v[q] = a.conj ? cmulc(v[q], hv) : cmul(v[q], hv);
     }
     team_fft<LY, +1>(v, row, t, tw);
     if (live) store_col(v, T0, t, TT);
   } else if constexpr (MODE == P2_VRS) {
+    // Ez accumulates in a second shared-memory row of the team (each thread touches only its
+    // own elements t + q TT, so no synchronisation is needed for it).
     C* T1 = T0 + a.t_plane;
     C* T2 = T1 + a.t_plane;
-    C z[16];
+    C* zr = sm + ROWS * SR + team * SR;
+    const C *hz = H(KH), *hx = H(KHX), *hy = H(KHY);
     load_col(v, T0, t, TT);
     team_fft<LY, -1>(v, row, t, tw);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const int ky = t + q * TT;
-      z[q] = cmul(v[q], spec_at(Hq + a.slot[KHX] * HK, kx, ky, a.nx, a.ny, true, false));
-      v[q] = cmul(v[q], spec_at(Hq + a.slot[KH] * HK, kx, ky, a.nx, a.ny, false, false));
+      zr[spad(t + q * TT)] = cmul(v[q], spec_row(hx, q, t, TT, flipx, true, false));
+      v[q] = cmul(v[q], spec_row(hz, q, t, TT, flipx, false, false));
+      XL_GROUP_FENCE(q);
     }
     team_fft<LY, +1>(v, row, t, tw);
     if (live) store_col(v, T0, t, TT);
@@ -230,14 +257,17 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
     team_fft<LY, -1>(v, row, t, tw);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const int ky = t + q * TT;
-      z[q] = cadd(z[q], cmul(v[q], spec_at(Hq + a.slot[KHY] * HK, kx, ky, a.nx, a.ny, false, true)));
-      v[q] = cmul(v[q], spec_at(Hq + a.slot[KH] * HK, kx, ky, a.nx, a.ny, false, false));
+      const int iz = spad(t + q * TT);
+      zr[iz] = cadd(zr[iz], cmul(v[q], spec_row(hy, q, t, TT, flipx, false, true)));
+      v[q] = cmul(v[q], spec_row(hz, q, t, TT, flipx, false, false));
+      XL_GROUP_FENCE(q);
     }
     team_fft<LY, +1>(v, row, t, tw);
     if (live) store_col(v, T1, t, TT);
-    team_fft<LY, +1>(z, row, t, tw);
-    if (live) store_col(z, T2, t, TT);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = zr[spad(t + q * TT)];
+    team_fft<LY, +1>(v, row, t, tw);
+    if (live) store_col(v, T2, t, TT);
   } else if constexpr (MODE == P2_RS_BWD) {
     load_col(v, T0, t, TT);
     team_fft<LY, -1>(v, row, t, tw);
@@ -246,61 +276,63 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
       const C* U0 = Ub + (int64_t)b * a.cU * a.t_plane + (int64_t)kx * a.ny;
       load_col(u, U0, t, TT);
       team_fft<LY, -1>(u, row, t, tw);
+      const C* hd = H(KDH);
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        C hd = spec_at(Hq + a.slot[KDH] * HK, kx, t + q * TT, a.nx, a.ny, false, false);
-        dz += (double)cdot_re(v[q], cmul(u[q], hd));
+        dz += (double)cdot_re(v[q], cmul(u[q], spec_row(hd, q, t, TT, flipx, false, false)));
+        XL_GROUP_FENCE(q);
       }
     }
     if (a.want_field) {
+      const C* h = H(KH);
 #pragma unroll
-      for (int q = 0; q < 16; ++q)
-        v[q] = cmulc(v[q], spec_at(Hq + a.slot[KH] * HK, kx, t + q * TT, a.nx, a.ny, false, false));
+      for (int q = 0; q < 16; ++q) v[q] = cmulc(v[q], spec_row(h, q, t, TT, flipx, false, false));
       team_fft<LY, +1>(v, row, t, tw);
       if (live) store_col(v, T0, t, TT);
     }
   } else if constexpr (MODE == P2_VRS_BWD) {
+    // the spectrum of gz lives in a second shared-memory row of the team (thread-private entries)
     C* T1 = T0 + a.t_plane;
     C* T2 = T1 + a.t_plane;
-    C z[16];
-    load_col(z, T2, t, TT);
-    team_fft<LY, -1>(z, row, t, tw);
+    C* zr = sm + ROWS * SR + team * SR;
+    load_col(v, T2, t, TT);
+    team_fft<LY, -1>(v, row, t, tw);
 #pragma unroll
+    for (int q = 0; q < 16; ++q) zr[spad(t + q * TT)] = v[q];
+#pragma unroll 1
     for (int c = 0; c < 2; ++c) {
       C* Tc = c == 0 ? T0 : T1;
       load_col(v, Tc, t, TT);
       team_fft<LY, -1>(v, row, t, tw);
-      const int kodd = c == 0 ? KHX : KHY;
-      const int kdodd = c == 0 ? KDHX : KDHY;
+      const bool ox = c == 0, oy = c == 1;
       if (a.want_dz) {
         C u[16];
         const C* Uc = Ub + ((int64_t)b * a.cU + c) * a.t_plane + (int64_t)kx * a.ny;
         load_col(u, Uc, t, TT);
         team_fft<LY, -1>(u, row, t, tw);
+        const C *hd = H(KDH), *ho = H(c == 0 ? KDHX : KDHY);
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          const int ky = t + q * TT;
-          C hd = spec_at(Hq + a.slot[KDH] * HK, kx, ky, a.nx, a.ny, false, false);
-          C ho = spec_at(Hq + a.slot[kdodd] * HK, kx, ky, a.nx, a.ny, c == 0, c == 1);
-          dz += (double)cdot_re(v[q], cmul(u[q], hd)) + (double)cdot_re(z[q], cmul(u[q], ho));
+          dz += (double)cdot_re(v[q], cmul(u[q], spec_row(hd, q, t, TT, flipx, false, false))) +
+                (double)cdot_re(zr[spad(t + q * TT)], cmul(u[q], spec_row(ho, q, t, TT, flipx, ox, oy)));
+          XL_GROUP_FENCE(q);
         }
       }
       if (a.want_field) {
+        const C *hz = H(KH), *ho = H(c == 0 ? KHX : KHY);
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          const int ky = t + q * TT;
-          C hz = spec_at(Hq + a.slot[KH] * HK, kx, ky, a.nx, a.ny, false, false);
-          C ho = spec_at(Hq + a.slot[kodd] * HK, kx, ky, a.nx, a.ny, c == 0, c == 1);
-          v[q] = cadd(cmulc(v[q], hz), cmulc(z[q], ho));
+          v[q] = cadd(cmulc(v[q], spec_row(hz, q, t, TT, flipx, false, false)),
+                      cmulc(zr[spad(t + q * TT)], spec_row(ho, q, t, TT, flipx, ox, oy)));
+          XL_GROUP_FENCE(q);
         }
         team_fft<LY, +1>(v, row, t, tw);
         if (live) store_col(v, Tc, t, TT);
       }
     }
   }
-  if (MODE == P2_RS_BWD || MODE == P2_VRS_BWD) {
+  if constexpr (MODE == P2_RS_BWD || MODE == P2_VRS_BWD) {
     if (a.want_dz) {
-      // per-kx partial: reduce inside each team (teams are whole warps or sub-warp groups)
       double s = block_sum(live ? dz : 0.0, red);
       if (threadIdx.x == 0) dz_part[(int64_t)b * gridDim.x + blockIdx.x] = s;
     }
@@ -331,40 +363,143 @@ struct GenArgs {
   int slot[NKIND];        // kind -> slot of the S / Hq buffers (-1: not produced)
 };
 
-// Kernel sample of spectrum `kind` for offsets (a, b): r and the phase k r in double
-// precision, the amplitude factors in T.
+// ---------------------------------------------------------------------------------------------
+// Double-float arithmetic (an unevaluated sum hi + lo of two floats, about 44 significant bits;
+// Dekker 1971 / Knuth's two-sum, with the fused multiply-add giving exact products). It carries
+// the phase k r of the single-precision spectrum generator: r up to ~1.5 mm and k ~ 10 / um give
+// phases of ~1e4 rad that must be known to ~1e-6 rad before the final sincos, which single
+// precision cannot do and double precision does at a small fraction of the FP32 rate on GB300.
+struct df {
+  float hi, lo;
+};
+__device__ __forceinline__ df df_two_prod(float a, float b) {
+  const float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ df df_norm(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ df df_of(double d) {
+  const float hi = (float)d;
+  return {hi, (float)(d - (double)hi)};
+}
+__device__ __forceinline__ df df_add(df x, df y) {
+  df s = df_two_sum(x.hi, y.hi);
+  return df_norm(s.hi, s.lo + x.lo + y.lo);
+}
+__device__ __forceinline__ df df_neg(df x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ df df_mul(df x, df y) {
+  df p = df_two_prod(x.hi, y.hi);
+  return df_norm(p.hi, p.lo + (x.hi * y.lo + x.lo * y.hi));
+}
+__device__ __forceinline__ df df_mul_f(df x, float y) {
+  df p = df_two_prod(x.hi, y);
+  return df_norm(p.hi, fmaf(x.lo, y, p.lo));
+}
+__device__ __forceinline__ df df_div(df x, df y) {
+  const float q1 = x.hi / y.hi;
+  df r = df_add(x, df_neg(df_mul_f(y, q1)));
+  const float q2 = r.hi / y.hi;
+  r = df_add(r, df_neg(df_mul_f(y, q2)));
+  const float q3 = r.hi / y.hi;
+  df q = df_norm(q1, q2);
+  return df_add(q, {q3, 0.f});
+}
+__device__ __forceinline__ df df_sqrt(df x) {
+  const float y = sqrtf(x.hi);
+  const df e = df_add(x, df_neg(df_two_prod(y, y)));
+  return df_norm(y, e.hi / (2.f * y));
+}
+
+// Per-thread constants of the kernel samples for one distance.
+template <typename T> struct RsPhase;
+template <> struct RsPhase<float> {
+  df dx2, dy2, z, z2, k, twopi;
+  float kz_red, zf, kf, c0, dxf, dyf;
+  __device__ RsPhase(const GenArgs& g, double zz) {
+    dxf = (float)g.dx;
+    dyf = (float)g.dy;
+    dx2 = df_of(g.dx * g.dx);
+    dy2 = df_of(g.dy * g.dy);
+    z = df_of(zz);
+    z2 = df_of(zz * zz);
+    k = df_of(g.k);
+    twopi = df_of(kTwoPi);
+    kz_red = (float)(g.k * zz - kTwoPi * rint(g.k * zz / kTwoPi));
+    zf = (float)zz;
+    kf = (float)g.k;
+    c0 = (float)(g.dx * g.dy / kTwoPi);
+  }
+};
+template <> struct RsPhase<double> {
+  double kz_red;
+  __device__ RsPhase(const GenArgs& g, double zz) {
+    kz_red = g.k * zz - kTwoPi * rint(g.k * zz / kTwoPi);
+  }
+};
+
+// dh/dz and the odd kinds from h, r and the unit phasor (shared by both precisions).
+template <typename T>
+__device__ __forceinline__ cplx<T> rs_kinds(int kind, cplx<T> e, T r, T X, T Y, T z, T k, T c0) {
+  typedef cplx<T> C;
+  const T ir = (T)1 / r, ir2 = ir * ir, ir3 = ir2 * ir;
+  // h = c0 z (1/r - i k) e / r^2
+  const C h = cmul(e, mk(c0 * z * ir3, -c0 * z * k * ir2));
+  if (kind == KH) return h;
+  if (kind == KHX) return cscale(h, -X / z);
+  if (kind == KHY) return cscale(h, -Y / z);
+  // dh/dz = c0 e [(1/r^3 - i k / r^2) + z^2 (k^2/r^3 + 3 i k / r^4 - 3 / r^5)]
+  const T z2 = z * z;
+  const T re = ir3 + z2 * (k * k * ir3 - (T)3 * ir3 * ir2);
+  const T im = -k * ir2 + z2 * (T)3 * k * ir2 * ir2;
+  const C dh = cmul(e, mk(c0 * re, c0 * im));
+  if (kind == KDH) return dh;
+  // d/dz[-(X/z) h] = -(X/z)(dh - h/z)
+  const C dmh = csub(dh, cscale(h, (T)1 / z));
+  return cscale(dmh, kind == KDHX ? -X / z : -Y / z);
+}
+
+// Kernel sample of spectrum `kind` at pixel offset (a, b). Single precision: r and the phase
+// k (r - z) = k rho^2 / (r + z) in double-float (exact a^2, b^2 times dx^2, dy^2), reduced
+// modulo 2 pi before adding k z mod 2 pi and one sincosf. Double precision: the same formula in
+// double.
 template <typename T>
 __device__ __forceinline__ cplx<T> rs_sample(int kind, int a, int b, const GenArgs& g, double z,
-                                             double kz_red) {
-  typedef cplx<T> C;
+                                             const RsPhase<T>& P);
+
+template <>
+__device__ __forceinline__ cplx<float> rs_sample<float>(int kind, int a, int b, const GenArgs& g,
+                                                        double z, const RsPhase<float>& P) {
+  const float A = (float)(a * a), B = (float)(b * b);  // exact (|a|, |b| < 4096)
+  const df rho2 = df_add(df_mul_f(P.dx2, A), df_mul_f(P.dy2, B));
+  const df r = df_sqrt(df_add(rho2, P.z2));
+  const df ph = df_div(df_mul(P.k, rho2), df_add(r, P.z));
+  const float n = rintf(ph.hi * 0.15915494309189535f);
+  const df red = df_add(ph, df_neg(df_mul_f(P.twopi, n)));
+  float sn, cs;
+  sincosf(red.hi + red.lo + P.kz_red, &sn, &cs);
+  const float X = (float)a * P.dxf, Y = (float)b * P.dyf;
+  return rs_kinds<float>(kind, make_float2(cs, sn), r.hi, X, Y, P.zf, P.kf, P.c0);
+}
+
+template <>
+__device__ __forceinline__ cplx<double> rs_sample<double>(int kind, int a, int b, const GenArgs& g,
+                                                          double z, const RsPhase<double>& P) {
   const double X = a * g.dx, Y = b * g.dy;
   const double rho2 = X * X + Y * Y;
   const double r = sqrt(rho2 + z * z);
   double ph = g.k * rho2 / (r + z);
   ph -= kTwoPi * rint(ph * (1.0 / kTwoPi));
-  ph += kz_red;
-  T sn, cs;
-  xsincos((T)ph, &sn, &cs);
-  const C e = mk(cs, sn);
-  const double C0 = g.dx * g.dy / kTwoPi;
-  const double ir = 1.0 / r, ir2 = ir * ir;
-  // h = C0 z (1/r - i k) e / r^2
-  const C h = cmul(e, mk((T)(C0 * z * ir * ir2), (T)(-C0 * z * g.k * ir2)));
-  if (kind == KH) return h;
-  if (kind == KHX) return cscale(h, (T)(-X / z));
-  if (kind == KHY) return cscale(h, (T)(-Y / z));
-  // dh/dz = C0 e [(1/r^3 - i k / r^2) + z^2 (k^2/r^3 + 3 i k / r^4 - 3 / r^5)]
-  const double ir3 = ir2 * ir, z2 = z * z, k = g.k;
-  const double re = ir3 + z2 * (k * k * ir3 - 3.0 * ir3 * ir2);
-  const double im = -k * ir2 + z2 * 3.0 * k * ir2 * ir2;
-  const C dh = cmul(e, mk((T)(C0 * re), (T)(C0 * im)));
-  if (kind == KDH) return dh;
-  // d/dz[-(X/z) h] = -(X/z)(dh - h/z)
-  const C dmh = csub(dh, cscale(h, (T)(1.0 / z)));
-  return cscale(dmh, kind == KDHX ? (T)(-X / z) : (T)(-Y / z));
+  double sn, cs;
+  sincos(ph + P.kz_red, &sn, &cs);
+  return rs_kinds<double>(kind, make_double2(cs, sn), r, X, Y, z, g.k, g.dx * g.dy / kTwoPi);
 }
 
-__device__ __forceinline__ double reduce_2pi(double x) { return x - kTwoPi * rint(x * (1.0 / kTwoPi)); }
 
 // Generator pass A: for each b in [0, ny) and each kind, FFT along a of the kernel row placed
 // mod LX; keep kx in [0, nx]; store transposed S[kind][kx][b].
@@ -372,17 +507,17 @@ template <typename T, int LX>
 __global__ void __launch_bounds__(rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16))
 k_gen_pass_a(cplx<T>* __restrict__ S, GenArgs g, const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
-  constexpr int ROWS = rows_transp<LX, sizeof(cplx<T>)>();
+  constexpr int ROWS = rows_transp<LX, sizeof(C)>();
   constexpr int TT = LX / 16;
-  constexpr int SR = srow(LX);
+  constexpr int P = rpitch(LX);
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
   const int b0 = blockIdx.x * ROWS;
   const int b = b0 + team;
   const double z = g.zdev ? *g.zdev : g.zval;
-  const double kz_red = reduce_2pi(g.k * z);
-  C* row = sm + team * SR;
+  const RsPhase<T> ph(g, z);
+  C* row = sm + team * P;
   for (int kind = 0; kind < NKIND; ++kind) {
     if (!(g.kinds & (1u << kind))) continue;  // uniform over the block
     C v[16];
@@ -390,19 +525,14 @@ k_gen_pass_a(cplx<T>* __restrict__ S, GenArgs g, const cplx<T>* __restrict__ tw)
     for (int q = 0; q < 16; ++q) {
       const int i = t + q * TT;
       const int a = i < g.nx ? i : i - LX;
-      v[q] = (i == g.nx || b >= g.ny) ? mk((T)0, (T)0) : rs_sample<T>(kind, a, b, g, z, kz_red);
+      v[q] = (i == g.nx || b >= g.ny) ? mk((T)0, (T)0) : rs_sample<T>(kind, a, b, g, z, ph);
     }
     team_fft<LX, -1>(v, row, t, tw);
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < 16; ++q) row[spad(t + q * TT)] = v[q];
     __syncthreads();
-    C* dst = S + (int64_t)g.slot[kind] * g.s_plane;
-    for (int kx = threadIdx.x; kx <= g.nx; kx += ROWS * TT) {
-#pragma unroll
-      for (int r = 0; r < ROWS; ++r)
-        if (b0 + r < g.ny) dst[(int64_t)kx * g.ny + b0 + r] = sm[r * SR + spad(kx)];
-    }
+    store_rows_transposed<ROWS, P>(sm, g.nx + 1, S + (int64_t)g.slot[kind] * g.s_plane, g.ny, b0, g.ny);
     __syncthreads();
   }
 }

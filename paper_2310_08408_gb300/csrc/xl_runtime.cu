@@ -89,20 +89,29 @@ xl_status twiddles(int L, int dtype, const void** out) {
     *out = it->second;
     return XL_OK;
   }
-  std::vector<double> w(2 * (size_t)L);
-  for (int m = 0; m < L; ++m) {
-    // exp(-2 pi i m / L) in double precision, rounded once to the table's precision
-    double ang = -kTwoPi * (double)m / (double)L;
-    w[2 * m] = std::cos(ang);
-    w[2 * m + 1] = std::sin(ang);
+  // per-stage blocks: stage s >= 1 has Ns x R entries exp(-2 pi i k r / (Ns R)) (the layout of
+  // apply_twiddles in xl_fft.cuh)
+  std::vector<double> w;
+  int Ns = 16;
+  while (Ns < L) {
+    const int R = (Ns * 16 <= L) ? 16 : L / Ns;
+    for (int k = 0; k < Ns; ++k)
+      for (int r = 0; r < R; ++r) {
+        const double ang = -kTwoPi * (double)k * (double)r / ((double)Ns * (double)R);
+        w.push_back(std::cos(ang));
+        w.push_back(std::sin(ang));
+      }
+    Ns *= R;
   }
+  if (w.empty()) w.assign(2, 0.0);
   void* d = nullptr;
-  size_t bytes = (size_t)L * dtype_csize(dtype);
+  const size_t n = w.size() / 2;
+  size_t bytes = n * dtype_csize(dtype);
   XL_CUDA_TRY(cudaMalloc(&d, bytes));
   if (dtype == XL_C128) {
     XL_CUDA_TRY(cudaMemcpy(d, w.data(), bytes, cudaMemcpyHostToDevice));
   } else {
-    std::vector<float> f(2 * (size_t)L);
+    std::vector<float> f(w.size());
     for (size_t i = 0; i < f.size(); ++i) f[i] = (float)w[i];
     XL_CUDA_TRY(cudaMemcpy(d, f.data(), bytes, cudaMemcpyHostToDevice));
   }

@@ -12,8 +12,9 @@
 
 namespace xl {
 
-// Table of exp(-2 pi i m / L), m < L, in the precision of dtype (float2 or double2), computed in
-// double precision on the host. Created on first use (synchronous upload).
+// Twiddle tables of a length-L transform in the precision of dtype (float2 or double2): for each
+// stage s >= 1 (sub-transform size Ns, radix R) the Ns x R values exp(-2 pi i k r / (Ns R)),
+// computed in double precision on the host. Created on first use (synchronous upload).
 xl_status twiddles(int L, int dtype, const void** out);
 
 // Workspace of at least `bytes` for `stream` on the current device. Growing it synchronises the

@@ -69,6 +69,15 @@ class Element(ctypes.Structure):
 SLM, SSLM, LENS, POLARIZER, WAVEPLATE, TO_VECTOR = range(6)
 SECOND_MOMENT, DENSITY = 0, 1
 
+class TableConfig(ctypes.Structure):
+    """xl_table_config of the batched optical-table optimiser."""
+    _fields_ = [("wavelength", ctypes.c_double), ("extent", ctypes.c_double), ("w0", ctypes.c_double),
+                ("f", ctypes.c_double), ("cam_width", ctypes.c_double), ("lr", ctypes.c_double),
+                ("lr_z", ctypes.c_double), ("cam_m", ctypes.c_int32), ("dtype", ctypes.c_int32)]
+
+
+BATCH_LOSS, BATCH_SCALARS, BATCH_GRAD_SCALARS, BATCH_PHI1, BATCH_PHI2, BATCH_GRAD_PHI1, BATCH_GRAD_PHI2 = range(7)
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int32
 _D = ctypes.c_double
@@ -97,6 +106,12 @@ SIGNATURES = {
     "xl_device_status": ([_P], _I),
     "xl_adam_step": ([_P, _P, _P, _P, ctypes.c_int64, _I, _D, _D, _D, _D, _P, _I, _P], _I),
     "xl_step_advance": ([_P, _P], _I),
+    "xl_batch_create": ([ctypes.POINTER(TableConfig), _I, _P, _P, ctypes.c_uint64,
+                         ctypes.POINTER(ctypes.c_void_p), _P], _I),
+    "xl_batch_step": ([_P, _I, _P], _I),
+    "xl_batch_read": ([_P, _I, _I, _P, _P], _I),
+    "xl_batch_grid": ([_P, _I], _I),
+    "xl_batch_destroy": ([_P], _I),
     "xl_czt_propagate_backward": ([_P, _P, _I, _I, _GP, _WP, _D, _P, _I, _I, _P], _I),
 }
 
@@ -276,11 +291,13 @@ def vrs_propagate_backward(g_exyz: torch.Tensor, exy_in: torch.Tensor | None, gr
     return g_exy, g_z
 
 
-def czt_propagate(u: torch.Tensor, grid, window, wavelength: float, z, vectorial: bool = False,
+def czt_propagate(u: torch.Tensor, grid, window, wavelength: float, z, vectorial=False,
                   out: torch.Tensor | None = None):
-    """CZT onto a window: [B][ny][nx] -> [B][my][mx]; vectorial: [B][2][ny][nx] -> [B][3][my][mx]."""
+    """CZT onto a window: [B][ny][nx] -> [B][my][mx]; vectorial (1): [B][2][ny][nx] ->
+    [B][3][my][mx]; vectorial 2: [B][3][ny][nx] (Ez unused) -> [B][3][my][mx]."""
     _dev(u, "u")
-    comps = 2 if vectorial else 1
+    vectorial = int(vectorial)
+    comps = {0: 1, 1: 2, 2: 3}[vectorial]
     B, ny, nx = _planes(u, comps, "u")
     g, w = Grid.of(grid), Window.of(window)
     if out is None:
@@ -294,13 +311,14 @@ def czt_propagate(u: torch.Tensor, grid, window, wavelength: float, z, vectorial
 
 
 def czt_propagate_backward(g_out: torch.Tensor, grid, window, wavelength: float, z,
-                           vectorial: bool = False):
+                           vectorial=False):
     """Adjoint of czt_propagate: window gradient -> input-grid gradient."""
     _dev(g_out, "g_out")
+    vectorial = int(vectorial)
     comps = 3 if vectorial else 1
     B, my, mx = _planes(g_out, comps, "g_out")
     g, w = Grid.of(grid), Window.of(window)
-    lead = g_out.shape[:-2] if not vectorial else (g_out.shape[:-3] + (2,))
+    lead = g_out.shape[:-2] if not vectorial else (g_out.shape[:-3] + ({1: 2, 2: 3}[vectorial],))
     g_in = torch.empty(tuple(lead) + (g.ny, g.nx), dtype=g_out.dtype, device=g_out.device)
     zz = _Z(z, B)
     _check(load().xl_czt_propagate_backward(g_out.data_ptr(), g_in.data_ptr(), B, int(vectorial),
@@ -356,7 +374,7 @@ def _params(params, batch: int, n: int):
 
 
 def _comps_out(comps_in: int, elements) -> int:
-    return 2 if comps_in == 2 or any(int(e["kind"]) == TO_VECTOR for e in elements) else 1
+    return 2 if any(int(e["kind"]) == TO_VECTOR for e in elements) else comps_in
 
 
 def apply_elements(field: torch.Tensor, grid, wavelength: float, elements: Sequence[dict],
@@ -472,3 +490,53 @@ def adam_step(p: torch.Tensor, m: torch.Tensor, v: torch.Tensor, grad: torch.Ten
 
 def step_advance(t: torch.Tensor) -> None:
     _check(load().xl_step_advance(_dev(t, "t").data_ptr(), _stream()))
+
+
+# ----------------------------------------------------------------------------- batched tables
+class Batch:
+    """Many optical-table setups optimised together (xl_batch_*). cfg: dict with wavelength,
+    extent, w0, f, cam_m, cam_width, lr, lr_z, dtype ("c64" / "c128"); grid_n: list of N per
+    setup; init: [n][3] = (theta, z1, z2)."""
+
+    def __init__(self, cfg: dict, grid_n, init, seed: int):
+        self.cfg = TableConfig(float(cfg["wavelength"]), float(cfg["extent"]), float(cfg["w0"]),
+                               float(cfg["f"]), float(cfg["cam_width"]), float(cfg["lr"]),
+                               float(cfg["lr_z"]), int(cfg["cam_m"]),
+                               C128 if cfg.get("dtype", "c64") == "c128" else C64)
+        self.n = len(grid_n)
+        gn = np.ascontiguousarray(grid_n, dtype=np.int32)
+        ini = np.ascontiguousarray(init, dtype=np.float64).reshape(self.n, 3)
+        h = ctypes.c_void_p()
+        _check(load().xl_batch_create(ctypes.byref(self.cfg), self.n, gn.ctypes.data,
+                                      ini.ctypes.data, int(seed) & (2 ** 64 - 1), ctypes.byref(h),
+                                      _stream()))
+        self.h = h
+
+    def step(self, use_graph: bool = True) -> None:
+        _check(load().xl_batch_step(self.h, int(use_graph), _stream()))
+
+    def grid(self, setup: int) -> int:
+        return int(load().xl_batch_grid(self.h, setup))
+
+    def read(self, what: int, setup: int) -> np.ndarray:
+        n = self.grid(setup)
+        rd = np.float64 if self.cfg.dtype == C128 else np.float32
+        if what == BATCH_LOSS:
+            out = np.zeros(1)
+        elif what in (BATCH_SCALARS, BATCH_GRAD_SCALARS):
+            out = np.zeros(3)
+        else:
+            out = np.zeros((n, n), rd)
+        _check(load().xl_batch_read(self.h, what, setup, out.ctypes.data, _stream()))
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            _check(load().xl_batch_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

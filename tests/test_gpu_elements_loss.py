@@ -15,16 +15,18 @@ pytestmark = pytest.mark.gpu
 LAM = 0.6328
 
 
+# SLM -> lens -> to-vector -> wave plate -> super-SLM -> polariser (the wave plate gives Ey a
+# non-zero value before the super-SLM so that both of its masks receive a gradient)
 def _chain(ph, px, py):
     return [dict(kind=0, phi_x=ph), dict(kind=2, f=3000.0), dict(kind=5),
-            dict(kind=1, phi_x=px, phi_y=py), dict(kind=4, eta=2.1, theta=0.35),
+            dict(kind=4, eta=2.1, theta=0.35), dict(kind=1, phi_x=px, phi_y=py),
             dict(kind=3, alpha=-0.4)]
 
 
 def _oracle_chain(ph, px, py):
     return [dict(kind=oracle.SLM, phi_x=ph), dict(kind=oracle.LENS, f=3000.0),
-            dict(kind=oracle.TO_VECTOR), dict(kind=oracle.SSLM, phi_x=px, phi_y=py),
-            dict(kind=oracle.WAVEPLATE, eta=2.1, theta=0.35), dict(kind=oracle.POLARIZER, alpha=-0.4)]
+            dict(kind=oracle.TO_VECTOR), dict(kind=oracle.WAVEPLATE, eta=2.1, theta=0.35),
+            dict(kind=oracle.SSLM, phi_x=px, phi_y=py), dict(kind=oracle.POLARIZER, alpha=-0.4)]
 
 
 @pytest.mark.parametrize("dtype,rdtype,tol", [(np.complex64, np.float32, TOL_C64),
@@ -53,7 +55,7 @@ def test_element_chain_forward_backward(dtype, rdtype, tol, shared):
                                                           u[b].astype(np.complex128), g.astuple(),
                                                           LAM, och)
         assert rel(to_np(g_in)[b], rg) < tol
-        for k, (arr, idx) in enumerate(((gpx, 0), (gpx, 3), (gpy, 3))):
+        for k, (arr, idx) in enumerate(((gpx, 0), (gpx, 4), (gpy, 4))):
             got = to_np(arr[idx])
             rr = (rpx if arr is gpx else rpy)[idx]
             if shared:
@@ -61,11 +63,11 @@ def test_element_chain_forward_backward(dtype, rdtype, tol, shared):
             else:
                 assert rel(got[b], rr) < 10 * tol
         gpn = to_np(gp)[b]
-        for e, j in ((1, 0), (4, 2), (4, 3), (5, 1)):
+        for e, j in ((1, 0), (3, 2), (3, 3), (5, 1)):
             assert abs(gpn[e, j] - rp[e, j]) <= 1e-5 * max(1.0, abs(rp[e, j])) if dtype == np.complex64 \
                 else abs(gpn[e, j] - rp[e, j]) <= 1e-10 * max(1.0, abs(rp[e, j]))
     if shared:
-        for k, (arr, idx) in enumerate(((gpx, 0), (gpx, 3), (gpy, 3))):
+        for k, (arr, idx) in enumerate(((gpx, 0), (gpx, 4), (gpy, 4))):
             assert rel(to_np(arr[idx]), gsum[k]) < 10 * tol
 
 
