@@ -54,6 +54,12 @@ typedef int32_t xl_status;
 
 /* flags */
 #define XL_Z_DEVICE 1 /* z (and element parameters) are read from device memory at run time */
+/* Backward passes only: the loss is invariant under a constant phase factor on the propagated
+ * field (true for camera-intensity losses behind linear optics). dL/dz then leaves out the term
+ * Re(ik <g_out, u_out>) of the e^{ikz} rotation, which is zero in exact arithmetic but, computed
+ * in single precision, adds rounding noise up to k |g_out| |u_out| to a derivative that is often
+ * four orders of magnitude smaller. The distance derivative uses the spectrum of dh/dz - ik h. */
+#define XL_PHASE_INVARIANT 2
 
 /* Sampling grid: x_m = x0 + m dx, y_n = y0 + n dy. */
 typedef struct xl_grid {

@@ -21,13 +21,15 @@ def _dev_z(z: torch.Tensor, batch: int) -> torch.Tensor:
 
 
 class RSPropagate(torch.autograd.Function):
-    """u [B][ny][nx] -> RS(u, z); z: float64 CUDA tensor [B] (or [1])."""
+    """u [B][ny][nx] -> RS(u, z); z: float64 CUDA tensor [B] (or [1]). phase_invariant: the loss
+    ignores a constant phase on the output (intensity losses behind linear optics), which lets
+    the distance derivative drop an exactly-zero, noise-prone term (XL_PHASE_INVARIANT)."""
 
     @staticmethod
-    def forward(ctx, u, z, grid, wavelength):
+    def forward(ctx, u, z, grid, wavelength, phase_invariant=False):
         zz = _dev_z(z.detach(), u.shape[0])
         ctx.save_for_backward(u, zz)
-        ctx.grid, ctx.wl, ctx.zshape = grid, wavelength, z.shape
+        ctx.grid, ctx.wl, ctx.zshape, ctx.pinv = grid, wavelength, z.shape, phase_invariant
         return xl.rs_propagate(u.contiguous(), grid, wavelength, zz)
 
     @staticmethod
@@ -35,20 +37,21 @@ class RSPropagate(torch.autograd.Function):
         u, zz = ctx.saved_tensors
         need_u, need_z = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
         g_in, g_z = xl.rs_propagate_backward(g.contiguous(), u if need_z else None, ctx.grid, ctx.wl,
-                                             zz, want_field=need_u, want_dz=need_z)
+                                             zz, want_field=need_u, want_dz=need_z,
+                                             phase_invariant=ctx.pinv)
         if g_z is not None:
             g_z = g_z.reshape(-1).sum().reshape(ctx.zshape) if ctx.zshape.numel() == 1 else g_z.reshape(ctx.zshape)
-        return g_in, g_z, None, None
+        return g_in, g_z, None, None, None
 
 
 class VRSPropagate(torch.autograd.Function):
-    """exy [B][2][ny][nx] -> [B][3][ny][nx]."""
+    """exy [B][2][ny][nx] -> [B][3][ny][nx] (phase_invariant as in RSPropagate)."""
 
     @staticmethod
-    def forward(ctx, exy, z, grid, wavelength):
+    def forward(ctx, exy, z, grid, wavelength, phase_invariant=False):
         zz = _dev_z(z.detach(), exy.shape[0])
         ctx.save_for_backward(exy, zz)
-        ctx.grid, ctx.wl, ctx.zshape = grid, wavelength, z.shape
+        ctx.grid, ctx.wl, ctx.zshape, ctx.pinv = grid, wavelength, z.shape, phase_invariant
         return xl.vrs_propagate(exy.contiguous(), grid, wavelength, zz)
 
     @staticmethod
@@ -56,10 +59,11 @@ class VRSPropagate(torch.autograd.Function):
         exy, zz = ctx.saved_tensors
         need_u, need_z = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
         g_in, g_z = xl.vrs_propagate_backward(g.contiguous(), exy if need_z else None, ctx.grid,
-                                              ctx.wl, zz, want_field=need_u, want_dz=need_z)
+                                              ctx.wl, zz, want_field=need_u, want_dz=need_z,
+                                              phase_invariant=ctx.pinv)
         if g_z is not None:
             g_z = g_z.reshape(-1).sum().reshape(ctx.zshape) if ctx.zshape.numel() == 1 else g_z.reshape(ctx.zshape)
-        return g_in, g_z, None, None
+        return g_in, g_z, None, None, None
 
 
 class CZTPropagate(torch.autograd.Function):

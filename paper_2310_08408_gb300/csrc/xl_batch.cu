@@ -214,11 +214,14 @@ xl_status group_step(xl_batch* b, Group& G, cudaStream_t s) {
   XL_TRY(xl_czt_propagate_backward(G.g5, G.g4, cnt, 2, g, &win, lam, G.zf.data(), 0, dt, s));
   XL_TRY(xl_apply_elements_backward(G.g4, G.a3, G.g3, cnt, 3, g, lam, e_lens, 1, G.pl, XL_Z_DEVICE,
                                     nullptr, nullptr, nullptr, dt, s));
-  XL_TRY(xl_vrs_propagate_backward(G.g3, G.a2, G.g2, G.gz2, cnt, g, lam, G.z2, XL_Z_DEVICE, dt, s));
+  // the camera loss is invariant under a constant phase on every plane: drop the e^{ikz} term
+  XL_TRY(xl_vrs_propagate_backward(G.g3, G.a2, G.g2, G.gz2, cnt, g, lam, G.z2,
+                                   XL_Z_DEVICE | XL_PHASE_INVARIANT, dt, s));
   void* gpx_mid[3] = {G.gphi2, nullptr, nullptr};
   XL_TRY(xl_apply_elements_backward(G.g2, G.a1, G.g1, cnt, 1, g, lam, e_mid, 3, G.p2, XL_Z_DEVICE,
                                     gpx_mid, nullptr, G.gp2, dt, s));
-  XL_TRY(xl_rs_propagate_backward(G.g1, G.a0, G.g0, G.gz1, cnt, g, lam, G.z1, XL_Z_DEVICE, dt, s));
+  XL_TRY(xl_rs_propagate_backward(G.g1, G.a0, G.g0, G.gz1, cnt, g, lam, G.z1,
+                                  XL_Z_DEVICE | XL_PHASE_INVARIANT, dt, s));
   void* gpx1[1] = {G.gphi1};
   XL_TRY(xl_apply_elements_backward(G.g0, G.src, nullptr, cnt, 1, g, lam, e_slm1, 1, G.p1,
                                     XL_Z_DEVICE, gpx1, nullptr, nullptr, dt, s));

@@ -11,7 +11,7 @@
 // reads x[j + r L/R] (r < R), multiplies element r by W_{Ns R}^{(j mod Ns) r}, takes an R-point
 // DFT, and writes y[(j div Ns) Ns R + (j mod Ns) + r Ns]. Twiddles come from a table of
 // exp(-2 pi i k r / (Ns R)) per stage, each rounded once from double precision on the host
-// (conjugated for inverse transforms), read as contiguous 16-byte vectors by each butterfly.
+// (conjugated for inverse transforms), laid out so that every warp's twiddle load is coalesced.
 // Shared-memory rows carry one pad element per 16 so that the stride-16 writes of the first
 // stage hit distinct banks.
 //
@@ -126,11 +126,10 @@ template <int L> struct FFTShape {
 };
 
 // Twiddle table layout: for every stage S >= 1 (sub-transform size Ns, radix R) a block of
-// Ns x R entries tw[off_S + k R + r] = exp(-2 pi i k r / (Ns R)), each rounded once from double
-// precision on the host, so a butterfly reads its R twiddles as contiguous 16-byte vectors.
+// R x Ns entries tw[off_S + r Ns + k] = exp(-2 pi i k r / (Ns R)), each rounded once from double
+// precision on the host. For a fixed r the lanes of a warp (consecutive butterflies, consecutive
+// k) read consecutive entries, so every twiddle load is coalesced.
 __host__ __device__ constexpr int tw_stage_offset(int L, int S) {
-  // stages 1.. S-1 precede stage S; stage s >= 1 has Ns = 16^s entries per r (R = 16 except a
-  // final smaller radix)
   int off = 0, Ns = 16;
   for (int s = 1; s < S; ++s) {
     const int R = (Ns * 16 <= L) ? 16 : L / Ns;
@@ -139,31 +138,16 @@ __host__ __device__ constexpr int tw_stage_offset(int L, int S) {
   }
   return off;
 }
-__host__ __device__ constexpr int tw_table_size(int L) { return tw_stage_offset(L, cilog2(L) / 4 + (cilog2(L) % 4 ? 1 : 0)); }
 
-// Multiplies v[B r] by W_{Ns R}^{k r}, r = 1..R-1 (conjugated for inverse transforms).
-template <int R, int B, typename C>
-__device__ __forceinline__ void apply_twiddles(C* v, const C* __restrict__ row, bool inv) {
-  typedef decltype(v[0].x) T;
-  if constexpr (sizeof(C) == 8) {
-    const float4* p = reinterpret_cast<const float4*>(row);
+// Multiplies v[B r] by W_{Ns R}^{k r}, r = 1..R-1 (conjugated for inverse transforms);
+// `col` points at entry (r = 0, k) of the stage block.
+template <int R, int B, int Ns, typename C>
+__device__ __forceinline__ void apply_twiddles(C* v, const C* __restrict__ col, bool inv) {
 #pragma unroll
-    for (int h = 0; h < R / 2; ++h) {
-      const float4 w = __ldg(p + h);
-      if (h > 0) {
-        const C w0 = mk((T)w.x, (T)(inv ? -w.y : w.y));
-        v[2 * h * B] = cmul(v[2 * h * B], w0);
-      }
-      const C w1 = mk((T)w.z, (T)(inv ? -w.w : w.w));
-      v[(2 * h + 1) * B] = cmul(v[(2 * h + 1) * B], w1);
-    }
-  } else {
-#pragma unroll
-    for (int r = 1; r < R; ++r) {
-      C w = __ldg(row + r);
-      if (inv) w = cconj(w);
-      v[r * B] = cmul(v[r * B], w);
-    }
+  for (int r = 1; r < R; ++r) {
+    C w = __ldg(col + r * Ns);
+    if (inv) w = cconj(w);
+    v[r * B] = cmul(v[r * B], w);
   }
 }
 
@@ -186,7 +170,7 @@ __device__ __forceinline__ void fft_stage(C (&v)[16], C* sm, int t, const C* __r
   for (int b = 0; b < B; ++b) {
     const int j = t + b * TT;
     const int k = j & (Ns - 1);
-    apply_twiddles<R, B>(v + b, tw + tw_stage_offset(L, S) + k * R, DIR > 0);
+    apply_twiddles<R, B, Ns>(v + b, tw + tw_stage_offset(L, S) + k, DIR > 0);
     dftR<R, DIR, B>(v + b);
   }
   if constexpr (!last) {
@@ -244,9 +228,13 @@ __device__ __forceinline__ void load_rows_transposed(C* sm, int n_in, int n_fill
 
 // Full length-L transform of one row held by a team (see the file comment for the layout).
 // sm: the team's padded shared-memory row (srow(L) elements).
+// The barrier after the register-only first stage orders its shared-memory writes after every
+// read of the row by a previous transform (a forward transform's last stage reads the row just
+// before a caller multiplies and runs the inverse transform on the same row).
 template <int L, int DIR, typename C>
 __device__ __forceinline__ void team_fft(C (&v)[16], C* sm, int t, const C* __restrict__ tw) {
   dft16s<DIR, 1>(v);  // stage 0: radix 16, Ns = 1, no twiddles
+  __syncthreads();
 #pragma unroll
   for (int r = 0; r < 16; ++r) sm[spad(t * 16 + r)] = v[r];
   fft_stage<L, DIR, 1>(v, sm, t, tw);

@@ -35,7 +35,7 @@ xl_status check_grid(const xl_grid* g, double wavelength) {
 xl_status check_common(int32_t batch, const double* z, int32_t flags, int32_t dtype) {
   if (batch < 0) return fail(XL_ERR_ARG, "batch < 0");
   if (dtype != XL_C64 && dtype != XL_C128) return fail(XL_ERR_ARG, "dtype must be XL_C64 or XL_C128");
-  if (flags & ~XL_Z_DEVICE) return fail(XL_ERR_ARG, "unknown flag bits");
+  if (flags & ~(XL_Z_DEVICE | XL_PHASE_INVARIANT)) return fail(XL_ERR_ARG, "unknown flag bits");
   if (batch > 0 && !z) return fail(XL_ERR_ARG, "z is NULL");
   if (batch > 0 && !(flags & XL_Z_DEVICE))
     for (int32_t b = 0; b < batch; ++b)
@@ -58,6 +58,7 @@ GenArgs gen_args(const xl_grid* g, double wavelength, const Spectra& sp) {
   a.hq_kind = (int64_t)(g->nx + 1) * (g->ny + 1);
   a.scale = 1.0 / (4.0 * (double)g->nx * (double)g->ny);
   for (int i = 0; i < NKIND; ++i) a.slot[i] = sp.slot[i];
+  a.dz_rest = 0;
   return a;
 }
 
@@ -71,6 +72,7 @@ xl_status get_spectra(const xl_grid* g, double wavelength, const Spectra& sp, in
                       const double* z, int32_t flags, void* dev_s, void* dev_hq, cudaStream_t s,
                       const void** out) {
   GenArgs a = gen_args(g, wavelength, sp);
+  a.dz_rest = (flags & XL_PHASE_INVARIANT) ? 1 : 0;
   const size_t cs = dtype_csize(dtype);
   const size_t hq_bytes = (size_t)sp.count * a.hq_kind * cs;
   auto run = [&](void* S, void* Hq) -> xl_status {
@@ -85,6 +87,7 @@ xl_status get_spectra(const xl_grid* g, double wavelength, const Spectra& sp, in
   a.zval = *z;
   std::string key = "rs";
   key_put(key, sp.kinds);
+  key_put(key, a.dz_rest);
   key_put(key, g->nx);
   key_put(key, g->ny);
   key_put(key, g->dx);
@@ -221,6 +224,7 @@ xl_status dispatch(Op op, const void* in, const void* u_in, void* out, double* g
   if (!bwd && !out) return fail(XL_ERR_ARG, "output field is NULL");
   if (bwd && g_z && !u_in) return fail(XL_ERR_ARG, "g_z requested but the forward input is NULL");
   if (!bwd && in == out) return fail(XL_ERR_ARG, "output may not alias the input");
+  if (!bwd && (flags & XL_PHASE_INVARIANT)) return fail(XL_ERR_ARG, "XL_PHASE_INVARIANT applies to backward passes");
   cudaStream_t s = (cudaStream_t)stream;
   if (dtype == XL_C128) return run_op<double>(op, in, u_in, out, g_z, batch, g, wavelength, z, flags, dtype, s);
   return run_op<float>(op, in, u_in, out, g_z, batch, g, wavelength, z, flags, dtype, s);

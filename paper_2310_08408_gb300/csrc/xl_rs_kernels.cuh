@@ -361,6 +361,7 @@ struct GenArgs {
   int64_t hq_kind;        // elements of one quadrant
   double scale;           // 1 / (LX LY)
   int slot[NKIND];        // kind -> slot of the S / Hq buffers (-1: not produced)
+  int dz_rest;            // distance-derivative kinds carry dh/dz - i k h (phase-invariant losses)
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -445,7 +446,8 @@ template <> struct RsPhase<double> {
 
 // dh/dz and the odd kinds from h, r and the unit phasor (shared by both precisions).
 template <typename T>
-__device__ __forceinline__ cplx<T> rs_kinds(int kind, cplx<T> e, T r, T X, T Y, T z, T k, T c0) {
+__device__ __forceinline__ cplx<T> rs_kinds(int kind, cplx<T> e, T r, T X, T Y, T z, T k, T c0,
+                                            bool rest) {
   typedef cplx<T> C;
   const T ir = (T)1 / r, ir2 = ir * ir, ir3 = ir2 * ir;
   // h = c0 z (1/r - i k) e / r^2
@@ -457,7 +459,17 @@ __device__ __forceinline__ cplx<T> rs_kinds(int kind, cplx<T> e, T r, T X, T Y, 
   const T z2 = z * z;
   const T re = ir3 + z2 * (k * k * ir3 - (T)3 * ir3 * ir2);
   const T im = -k * ir2 + z2 * (T)3 * k * ir2 * ir2;
-  const C dh = cmul(e, mk(c0 * re, c0 * im));
+  C dh;
+  if (!rest) {
+    dh = cmul(e, mk(c0 * re, c0 * im));
+  } else {
+    // dh/dz - i k h without cancellation (r - z = rho^2 / (r + z)):
+    //   c0 e [ 1/r^3 - 3 z^2/r^5 - k^2 z rho^2 / ((r + z) r^3)  +  i k (3 z^2/r^4 - 1/r^2 - z/r^3) ]
+    const T rho2 = X * X + Y * Y;
+    const T rr = ir3 - (T)3 * z2 * ir3 * ir2 - k * k * z * rho2 * ir3 / (r + z);
+    const T ri = k * ((T)3 * z2 * ir2 * ir2 - ir2 - z * ir3);
+    dh = cmul(e, mk(c0 * rr, c0 * ri));
+  }
   if (kind == KDH) return dh;
   // d/dz[-(X/z) h] = -(X/z)(dh - h/z)
   const C dmh = csub(dh, cscale(h, (T)1 / z));
@@ -484,7 +496,7 @@ __device__ __forceinline__ cplx<float> rs_sample<float>(int kind, int a, int b, 
   float sn, cs;
   sincosf(red.hi + red.lo + P.kz_red, &sn, &cs);
   const float X = (float)a * P.dxf, Y = (float)b * P.dyf;
-  return rs_kinds<float>(kind, make_float2(cs, sn), r.hi, X, Y, P.zf, P.kf, P.c0);
+  return rs_kinds<float>(kind, make_float2(cs, sn), r.hi, X, Y, P.zf, P.kf, P.c0, g.dz_rest != 0);
 }
 
 template <>
@@ -497,7 +509,8 @@ __device__ __forceinline__ cplx<double> rs_sample<double>(int kind, int a, int b
   ph -= kTwoPi * rint(ph * (1.0 / kTwoPi));
   double sn, cs;
   sincos(ph + P.kz_red, &sn, &cs);
-  return rs_kinds<double>(kind, make_double2(cs, sn), r, X, Y, z, g.k, g.dx * g.dy / kTwoPi);
+  return rs_kinds<double>(kind, make_double2(cs, sn), r, X, Y, z, g.k, g.dx * g.dy / kTwoPi,
+                          g.dz_rest != 0);
 }
 
 

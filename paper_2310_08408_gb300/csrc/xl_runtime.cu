@@ -89,14 +89,14 @@ xl_status twiddles(int L, int dtype, const void** out) {
     *out = it->second;
     return XL_OK;
   }
-  // per-stage blocks: stage s >= 1 has Ns x R entries exp(-2 pi i k r / (Ns R)) (the layout of
-  // apply_twiddles in xl_fft.cuh)
+  // per-stage blocks: stage s >= 1 has R x Ns entries exp(-2 pi i k r / (Ns R)), r-major (the
+  // layout read by apply_twiddles in xl_fft.cuh)
   std::vector<double> w;
   int Ns = 16;
   while (Ns < L) {
     const int R = (Ns * 16 <= L) ? 16 : L / Ns;
-    for (int k = 0; k < Ns; ++k)
-      for (int r = 0; r < R; ++r) {
+    for (int r = 0; r < R; ++r)
+      for (int k = 0; k < Ns; ++k) {
         const double ang = -kTwoPi * (double)k * (double)r / ((double)Ns * (double)R);
         w.push_back(std::cos(ang));
         w.push_back(std::sin(ang));
@@ -153,8 +153,7 @@ xl_status cached_table(const std::string& key, size_t bytes, cudaStream_t stream
     st.lru.erase(e.lru_it);
     st.lru.push_front(key);
     e.lru_it = st.lru.begin();
-    if (e.owner != stream) XL_CUDA_TRY(cudaStreamWaitEvent(stream, e.ready, 0));
-    *out = e.ptr;
+    *out = e.ptr;  // complete: the generating call synchronised its stream
     return XL_OK;
   }
   // evict least-recently-used entries until the new one fits under the cap
@@ -182,7 +181,10 @@ xl_status cached_table(const std::string& key, size_t bytes, cudaStream_t stream
     cudaEventDestroy(e.ready);
     return s;
   }
+  // Wait for the generation on the host (misses happen once per table), so that every stream,
+  // and every later graph capture, may use the entry without an event dependency.
   XL_CUDA_TRY(cudaEventRecord(e.ready, stream));
+  XL_CUDA_TRY(cudaEventSynchronize(e.ready));
   st.lru.push_front(key);
   e.lru_it = st.lru.begin();
   st.cache_bytes += bytes;

@@ -13,7 +13,7 @@
 namespace xl {
 
 // Twiddle tables of a length-L transform in the precision of dtype (float2 or double2): for each
-// stage s >= 1 (sub-transform size Ns, radix R) the Ns x R values exp(-2 pi i k r / (Ns R)),
+// stage s >= 1 (sub-transform size Ns, radix R) the R x Ns values exp(-2 pi i k r / (Ns R)),
 // computed in double precision on the host. Created on first use (synchronous upload).
 xl_status twiddles(int L, int dtype, const void** out);
 
@@ -23,8 +23,7 @@ xl_status workspace(cudaStream_t stream, size_t bytes, void** out, int slot = 0)
 
 // Cache of generated tables. The key is an opaque byte string built by the caller. On a miss
 // the buffer is allocated (evicting least-recently-used entries above the byte cap), `gen` is
-// enqueued on `stream` to fill it, and an event is recorded; on a hit from another stream the
-// stream waits on that event.
+// enqueued on `stream` to fill it and the host waits for it, so a hit needs no synchronisation.
 xl_status cached_table(const std::string& key, size_t bytes, cudaStream_t stream,
                        const std::function<xl_status(void*)>& gen, void** out);
 

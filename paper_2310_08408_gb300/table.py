@@ -41,7 +41,8 @@ def table_loss(geo: TableGeometry, src, phi1, phi2, theta, z1, z2):
     p1 = torch.zeros((B, 1, 4), dtype=torch.float64, device=dev)
     a0 = A.elements(src, g, lam, [xl.SLM], [(phi1, None)], p1, 1)
     # RS over z1
-    a1 = A.RSPropagate.apply(a0[:, 0], z1, g, lam)[:, None]
+    # the camera loss ignores a constant phase on every plane (phase_invariant distance gradients)
+    a1 = A.RSPropagate.apply(a0[:, 0], z1, g, lam, True)[:, None]
     # SLM2, to-vector, half-wave plate (eta = pi) at theta
     wp = torch.stack([zero, zero, zero + math.pi, theta], dim=1)
     p2 = torch.stack([torch.zeros_like(wp), torch.zeros_like(wp), wp], dim=1).contiguous()
@@ -49,7 +50,7 @@ def table_loss(geo: TableGeometry, src, phi1, phi2, theta, z1, z2):
                                                                        (None, None)], p2, 1)
     # VRS over z2 (Ex, Ey, Ez); the lens acts on all three components; VCZT propagates the
     # transverse ones and re-forms Ez on the camera window (the input Ez plane is not used)
-    a3 = A.VRSPropagate.apply(a2, z2, g, lam)
+    a3 = A.VRSPropagate.apply(a2, z2, g, lam, True)
     pl = torch.zeros((B, 1, 4), dtype=torch.float64, device=dev)
     pl[:, 0, 0] = geo.f
     a4 = A.elements(a3, g, lam, [xl.LENS], [(None, None)], pl, 3)

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libxl.so")
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_UNSUPPORTED, ERR_TIMEOUT, ERR_NONFINITE = range(7)
 C64, C128 = 0, 1
 Z_DEVICE = 1
+PHASE_INVARIANT = 2
 
 _lock = threading.Lock()
 _lib = None
@@ -242,8 +243,10 @@ def rs_propagate(u: torch.Tensor, grid, wavelength: float, z, out: torch.Tensor 
 
 
 def rs_propagate_backward(g_out: torch.Tensor, u_in: torch.Tensor | None, grid, wavelength: float,
-                          z, want_field: bool = True, want_dz: bool = False):
-    """Adjoint of rs_propagate: returns (g_in or None, g_z [B] float64 or None)."""
+                          z, want_field: bool = True, want_dz: bool = False,
+                          phase_invariant: bool = False):
+    """Adjoint of rs_propagate: returns (g_in or None, g_z [B] float64 or None).
+    phase_invariant: the loss ignores a constant phase on the output (XL_PHASE_INVARIANT)."""
     _dev(g_out, "g_out")
     B, ny, nx = _planes(g_out, 1, "g_out")
     g = Grid.of(grid)
@@ -253,7 +256,8 @@ def rs_propagate_backward(g_out: torch.Tensor, u_in: torch.Tensor | None, grid, 
     _check(load().xl_rs_propagate_backward(
         g_out.data_ptr(), _dev(u_in, "u_in").data_ptr() if u_in is not None else None,
         g_in.data_ptr() if g_in is not None else None, g_z.data_ptr() if g_z is not None else None,
-        B, ctypes.byref(g), float(wavelength), zz.ptr, zz.flags, _dtype(g_out), _stream()))
+        B, ctypes.byref(g), float(wavelength), zz.ptr,
+        zz.flags | (PHASE_INVARIANT if phase_invariant else 0), _dtype(g_out), _stream()))
     return g_in, g_z
 
 
@@ -272,7 +276,8 @@ def vrs_propagate(exy: torch.Tensor, grid, wavelength: float, z, out: torch.Tens
 
 
 def vrs_propagate_backward(g_exyz: torch.Tensor, exy_in: torch.Tensor | None, grid,
-                           wavelength: float, z, want_field: bool = True, want_dz: bool = False):
+                           wavelength: float, z, want_field: bool = True, want_dz: bool = False,
+                           phase_invariant: bool = False):
     """Adjoint of vrs_propagate: returns (g_exy or None, g_z or None)."""
     _dev(g_exyz, "g_exyz")
     B, ny, nx = _planes(g_exyz, 3, "g_exyz")
@@ -287,7 +292,7 @@ def vrs_propagate_backward(g_exyz: torch.Tensor, exy_in: torch.Tensor | None, gr
         g_exyz.data_ptr(), _dev(exy_in, "exy_in").data_ptr() if exy_in is not None else None,
         g_exy.data_ptr() if g_exy is not None else None,
         g_z.data_ptr() if g_z is not None else None, B, ctypes.byref(g), float(wavelength),
-        zz.ptr, zz.flags, _dtype(g_exyz), _stream()))
+        zz.ptr, zz.flags | (PHASE_INVARIANT if phase_invariant else 0), _dtype(g_exyz), _stream()))
     return g_exy, g_z
 
 

@@ -137,3 +137,28 @@ def test_rs_argument_errors():
     # empty batch is a no-op
     e0 = torch.zeros((0, 64, 64), dtype=torch.complex64, device="cuda")
     assert xl.rs_propagate(e0, (64, 64, 1.0, 1.0, 0.0, 0.0), LAM, []).shape == (0, 64, 64)
+
+
+@pytest.mark.parametrize("vectorial", [False, True])
+def test_phase_invariant_distance_gradient(vectorial):
+    """XL_PHASE_INVARIANT drops Re(ik <g, u_out>) from dL/dz: on a random cotangent the two
+    results differ by exactly that term (oracle), in complex128."""
+    xl = lib()
+    g = inputs.Grid.centred(64, 0.5)
+    z = 45.0
+    k = 2 * np.pi / LAM
+    if vectorial:
+        u = inputs.random_jones(g, 10.0, 61)
+        G = inputs.random_unit(62, (3, 64, 64))
+        out = oracle.vrs(u, 0.5, 0.5, LAM, z)
+        fb = xl.vrs_propagate_backward
+    else:
+        u = inputs.gaussian_random_phase(g, 10.0, 61)
+        G = inputs.random_unit(62, (64, 64))
+        out = oracle.rs_conv(u, 0.5, 0.5, LAM, z)
+        fb = xl.rs_propagate_backward
+    ud, Gd = to_dev(u[None], np.complex128), to_dev(G[None], np.complex128)
+    _, gz = fb(Gd, ud, g, LAM, z, want_field=False, want_dz=True)
+    _, gzp = fb(Gd, ud, g, LAM, z, want_field=False, want_dz=True, phase_invariant=True)
+    term = np.real(1j * k * np.vdot(G, out))
+    assert abs((to_np(gz)[0] - to_np(gzp)[0]) - term) / abs(term) < 1e-9
