@@ -125,6 +125,23 @@ xl_status xl_rs_propagate_backward(const void* g_out, const void* u_in, void* g_
                                    int32_t batch, const xl_grid* grid, double wavelength,
                                    const double* z, int32_t flags, int32_t dtype, void* stream);
 
+/* Scalar RS propagation that allocates nothing. The paper has no counterpart: this entry point
+ * serves callers that cannot let a library allocate device memory (memory owned by another
+ * runtime's allocator, hosts that reserve all device memory up front, sandboxes without the
+ * allocation API). It computes exactly what xl_rs_propagate computes, for complex64 fields with
+ * nx, ny powers of two in [32, 256]; larger grids return XL_ERR_UNSUPPORTED. Its scratch
+ * (twiddles, spectra, the transposed intermediate) is one fixed 2,136,320-byte static device array
+ * that every GPU loading the library keeps until the process exits. No cudaMalloc / cudaFree is
+ * called; the transfer spectrum is regenerated for every run of equal consecutive distances.
+ *  - The first call on each device does a one-time set-up (looks up the array's device address
+ *    and fills its twiddle tables, synchronising `stream`): make that first call before any
+ *    stream capture.
+ *  - Every call uses the same array: calls that overlap on the GPU (different streams, or
+ *    threads without ordering) race and corrupt each other's results. Order them.
+ * u_in, u_out: [batch][ny][nx] complex64 device arrays (not aliasing); z: host [batch] (> 0). */
+xl_status xl_rs_propagate_static(const void* u_in, void* u_out, int32_t batch, const xl_grid* grid,
+                                 double wavelength, const double* z, void* stream);
+
 /* ---------------------------------------------------------------------------------------------
  * Vectorial RS (Methods, "Features and performance"; VRS of Ye et al., cited with RS).
  * Reading: Ex' = h * Ex, Ey' = h * Ey, Ez' = h_x * Ex + h_y * Ey with

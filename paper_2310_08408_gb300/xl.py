@@ -96,6 +96,7 @@ SIGNATURES = {
     "xl_profile_report": ([ctypes.c_char_p, _I], _I),
     "xl_rs_propagate": ([_P, _P, _I, _GP, _D, _P, _I, _I, _P], _I),
     "xl_rs_propagate_backward": ([_P, _P, _P, _P, _I, _GP, _D, _P, _I, _I, _P], _I),
+    "xl_rs_propagate_static": ([_P, _P, _I, _GP, _D, _P, _P], _I),
     "xl_vrs_propagate": ([_P, _P, _I, _GP, _D, _P, _I, _I, _P], _I),
     "xl_vrs_propagate_backward": ([_P, _P, _P, _P, _I, _GP, _D, _P, _I, _I, _P], _I),
     "xl_czt_propagate": ([_P, _P, _I, _I, _GP, _WP, _D, _P, _I, _I, _P], _I),
@@ -239,6 +240,23 @@ def rs_propagate(u: torch.Tensor, grid, wavelength: float, z, out: torch.Tensor 
     zz = _Z(z, B)
     _check(load().xl_rs_propagate(u.data_ptr(), _dev(out, "out").data_ptr(), B, ctypes.byref(g),
                                   float(wavelength), zz.ptr, zz.flags, _dtype(u), _stream()))
+    return out
+
+
+def rs_propagate_static(u: torch.Tensor, grid, wavelength: float, z,
+                        out: torch.Tensor | None = None):
+    """xl_rs_propagate_static: RS for complex64 grids up to 256 x 256 using the library's fixed
+    static scratch (no device allocation by the library); host distances only."""
+    _dev(u, "u")
+    B, ny, nx = _planes(u, 1, "u")
+    g = Grid.of(grid)
+    if out is None:
+        out = torch.empty_like(u)
+    zz = _Z(z, B)
+    if zz.flags:
+        raise ValueError("rs_propagate_static takes host distances")
+    _check(load().xl_rs_propagate_static(u.data_ptr(), _dev(out, "out").data_ptr(), B,
+                                         ctypes.byref(g), float(wavelength), zz.ptr, _stream()))
     return out
 
 
