@@ -85,6 +85,13 @@ def _sig(lib):
                                                 _D, _I32, _D, _D, _P]
     lib.orc_sted.argtypes = [_P, _P, _D, _I64, _P]
     lib.orc_adam.argtypes = [_P, _P, _P, _P, _I64, _D, _D, _D, _D, _I64]
+    lib.orc_loss_from_intensity.argtypes = [_P, _I64, _I64, _D, _D, _D, _D, _I32, _D, _P, _P]
+    lib.orc_loss_from_intensity.restype = _I32
+    lib.orc_sted_backward.argtypes = [_P, _P, _D, _P, _I64, _P, _P]
+    lib.orc_softmin.argtypes = [_P, _I64, _I64, _D, _P, _P]
+    lib.orc_adamw.argtypes = [_P, _P, _P, _P, _I64, _D, _D, _D, _D, _D, _I64]
+    lib.orc_mse.argtypes = [_P, _P, _I64, _P]
+    lib.orc_mse.restype = _D
     for name in ("orc_fft", "orc_fft2", "orc_rs_fft", "orc_rs_direct", "orc_rs_direct_points",
                  "orc_czt_direct", "orc_czt_brute", "orc_czt_points", "orc_elements_forward",
                  "orc_elements_backward", "orc_intensity_loss", "orc_intensity_loss_backward"):
@@ -348,3 +355,46 @@ def adam(p, m, v, g, lr, t, b1=0.9, b2=0.999, eps=1e-8):
         assert a.dtype == np.float64 and a.flags.c_contiguous
     g = _c(g, np.float64)
     _load().orc_adam(_ptr(p), _ptr(m), _ptr(v), _ptr(g), p.size, lr, b1, b2, eps, t)
+
+
+def loss_from_intensity(I, grid, mode=SECOND_MOMENT, eps=0.5, want_grad=False):
+    """Loss of an intensity image [ny, nx]; returns (loss, dL/dI or None)."""
+    nx, ny, dx, dy, x0, y0 = grid
+    I = _c(I, np.float64)
+    loss = np.zeros(1)
+    dI = np.empty_like(I) if want_grad else None
+    _check(_load().orc_loss_from_intensity(_ptr(I), nx, ny, dx, dy, x0, y0, mode, eps, _ptr(loss),
+                                           _ptr(dI)), "loss_from_intensity")
+    return float(loss[0]), dI
+
+
+def sted_backward(i_ex, i_dep, beta, g_eff):
+    """(dL/dI_ex, dL/dI_dep) from dL/dI_eff."""
+    a, b, g = (_c(x, np.float64).ravel() for x in (i_ex, i_dep, g_eff))
+    ge, gd = np.empty_like(a), np.empty_like(a)
+    _load().orc_sted_backward(_ptr(a), _ptr(b), beta, _ptr(g), a.size, _ptr(ge), _ptr(gd))
+    sh = np.shape(i_ex)
+    return ge.reshape(sh), gd.reshape(sh)
+
+
+def softmin(losses, beta):
+    """losses [batch, n_det] -> (softmin [batch], weights [batch, n_det])."""
+    l = _c(np.atleast_2d(losses), np.float64)
+    out = np.empty(l.shape[0])
+    w = np.empty_like(l)
+    _load().orc_softmin(_ptr(l), l.shape[0], l.shape[1], beta, _ptr(out), _ptr(w))
+    return out, w
+
+
+def adamw(p, m, v, g, lr, t, wd, b1=0.9, b2=0.999, eps=1e-8):
+    """One AdamW step in place (float64 arrays)."""
+    g = _c(g, np.float64)
+    _load().orc_adamw(_ptr(p), _ptr(m), _ptr(v), _ptr(g), p.size, lr, b1, b2, eps, wd, t)
+
+
+def mse(I, target, want_grad=False):
+    I = _c(I, np.float64)
+    t = _c(target, np.float64)
+    dI = np.empty_like(I) if want_grad else None
+    L = _load().orc_mse(_ptr(I), _ptr(t), I.size, _ptr(dI))
+    return float(L), dI

@@ -877,4 +877,117 @@ void orc_adam(double* p, double* m, double* v, const double* g, int64_t n, doubl
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// Losses of an intensity image (the same definitions as above, from I directly), their
+// gradients dL/dI, the STED derivative, softmin over detectors, AdamW and MSE.
+// ------------------------------------------------------------------------------------------
+static double sm_loss_and_grad(const double* I, int64_t nx, int64_t ny, double dx, double dy,
+                               double x0, double y0, double* dI) {
+  double S = 0, Sx = 0, Sy = 0;
+  for (int64_t n = 0; n < ny; ++n)
+    for (int64_t m = 0; m < nx; ++m) {
+      double v = I[n * nx + m];
+      S += v;
+      Sx += v * (x0 + m * dx);
+      Sy += v * (y0 + n * dy);
+    }
+  double xb = Sx / S, yb = Sy / S, V = 0;
+  for (int64_t n = 0; n < ny; ++n)
+    for (int64_t m = 0; m < nx; ++m) {
+      double ex = x0 + m * dx - xb, ey = y0 + n * dy - yb;
+      V += I[n * nx + m] * (ex * ex + ey * ey);
+    }
+  double L = V / S;
+  if (dI)
+    for (int64_t n = 0; n < ny; ++n)
+      for (int64_t m = 0; m < nx; ++m) {
+        double ex = x0 + m * dx - xb, ey = y0 + n * dy - yb;
+        dI[n * nx + m] = (ex * ex + ey * ey - L) / S;
+      }
+  return L;
+}
+
+static double density_loss_and_grad(const double* I, int64_t P, double eps, double* dI) {
+  double imax = 0;
+  for (int64_t i = 0; i < P; ++i) imax = std::max(imax, I[i]);
+  double thr = eps * imax, Ie = 0, area = 0;
+  for (int64_t i = 0; i < P; ++i)
+    if (I[i] > thr) {
+      Ie += I[i];
+      area += 1.0;
+    }
+  if (dI)
+    for (int64_t i = 0; i < P; ++i) dI[i] = I[i] > thr ? -area / (Ie * Ie) : 0.0;
+  return area / Ie;
+}
+
+// Loss of an intensity image (mode 0 second moment, 1 density); dI (nullable) gets dL/dI.
+int orc_loss_from_intensity(const double* I, int64_t nx, int64_t ny, double dx, double dy, double x0,
+                            double y0, int mode, double eps, double* loss_out, double* dI) {
+  if (nx < 1 || ny < 1) return -1;
+  if (mode == 0) *loss_out = sm_loss_and_grad(I, nx, ny, dx, dy, x0, y0, dI);
+  else if (mode == 1) *loss_out = density_loss_and_grad(I, nx * ny, eps, dI);
+  else return -1;
+  return 0;
+}
+
+// STED derivatives (Methods, "Stimulated emission depletion model", by differentiating the
+// effective intensity): with r = I_dep / I_ex,
+//   dI_eff/dI_ex  = 1 - beta + beta exp(-r) (1 + r),   dI_eff/dI_dep = -beta exp(-r);
+// at I_ex = 0 (where I_eff = 0) the limits for I_dep > 0: (1 - beta, 0).
+void orc_sted_backward(const double* i_ex, const double* i_dep, double beta, const double* g_eff,
+                       int64_t n, double* g_ex, double* g_dep) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (i_ex[i] > 0.0) {
+      double r = i_dep[i] / i_ex[i], e = std::exp(-r);
+      g_ex[i] = g_eff[i] * (1.0 - beta + beta * e * (1.0 + r));
+      g_dep[i] = g_eff[i] * (-beta * e);
+    } else {
+      g_ex[i] = g_eff[i] * (1.0 - beta);
+      g_dep[i] = 0.0;
+    }
+  }
+}
+
+// Softmin over detectors (Methods, "Rediscovery through exploration of optical topologies": the
+// update follows the detector with the smallest loss through a smooth minimum):
+//   softmin(l) = -log(sum_d exp(-beta l_d)) / beta;  weights w_d = d softmin / d l_d
+//   = exp(-beta l_d) / sum exp(-beta l) (computed with the minimum subtracted).
+void orc_softmin(const double* l, int64_t batch, int64_t n, double beta, double* out, double* w) {
+  for (int64_t b = 0; b < batch; ++b) {
+    const double* lb = l + b * n;
+    double mn = lb[0];
+    for (int64_t d = 1; d < n; ++d) mn = std::min(mn, lb[d]);
+    double s = 0;
+    for (int64_t d = 0; d < n; ++d) s += std::exp(-beta * (lb[d] - mn));
+    out[b] = mn - std::log(s) / beta;
+    if (w)
+      for (int64_t d = 0; d < n; ++d) w[b * n + d] = std::exp(-beta * (lb[d] - mn)) / s;
+  }
+}
+
+// AdamW (decoupled weight decay, Loshchilov & Hutter): the Adam step of orc_adam plus
+// p -= lr * wd * p (using p before the step).
+void orc_adamw(double* p, double* m, double* v, const double* g, int64_t n, double lr, double b1,
+               double b2, double eps, double wd, int64_t t) {
+  double c1 = 1.0 - std::pow(b1, (double)t), c2 = 1.0 - std::pow(b2, (double)t);
+  for (int64_t i = 0; i < n; ++i) {
+    m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+    v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+    p[i] -= lr * ((m[i] / c1) / (std::sqrt(v[i] / c2) + eps) + wd * p[i]);
+  }
+}
+
+// Mean squared error between an intensity image and a target (Results, "Data-driven
+// rediscovery": L = MSE(I_det, I_GT)); dI (nullable) gets dL/dI = 2 (I - I_GT) / P.
+double orc_mse(const double* I, const double* target, int64_t P, double* dI) {
+  double s = 0;
+  for (int64_t i = 0; i < P; ++i) {
+    double d = I[i] - target[i];
+    s += d * d;
+    if (dI) dI[i] = 2.0 * d / (double)P;
+  }
+  return s / (double)P;
+}
+
 }  // extern "C"
