@@ -256,6 +256,7 @@ xl_status xl_apply_elements_backward(const void* g_out, const void* in, void* g_
  * -------------------------------------------------------------------------------------------*/
 #define XL_SECOND_MOMENT 0
 #define XL_DENSITY 1
+#define XL_MSE 2 /* mean (I - I_target)^2 (Results, "Data-driven rediscovery"); needs the _ex form */
 
 xl_status xl_intensity_loss(const void* field, int32_t batch, int32_t comps, uint32_t comp_mask,
                             const xl_grid* grid, int32_t mode, double eps, double* loss,
@@ -270,6 +271,35 @@ xl_status xl_intensity_loss_backward(const void* field, int32_t batch, int32_t c
                                      double eps, const double* g_loss, void* g_field,
                                      int32_t dtype, void* stream);
 
+/* Extended camera losses.
+ *   field_dep (nullable): a depletion field of the same layout; I is then the STED effective
+ *     intensity (Methods, "Stimulated emission depletion model")
+ *       I_eff = I_ex [1 - beta (1 - exp(-I_dep / I_ex))], I_eff = 0 where I_ex = 0,
+ *     with I_ex, I_dep the selected-component intensities of field and field_dep, 0 <= beta <= 1.
+ *   target (XL_MSE only): device [batch][ny][nx] target intensities (float / double).
+ * Other arguments as xl_intensity_loss. */
+xl_status xl_intensity_loss_ex(const void* field, const void* field_dep, const void* target,
+                               int32_t batch, int32_t comps, uint32_t comp_mask,
+                               const xl_grid* grid, int32_t mode, double eps, double beta,
+                               double* loss, void* intensity, int32_t dtype, void* stream);
+
+/* Gradient of xl_intensity_loss_ex: g_field (and g_field_dep when field_dep is given) through
+ *   dI_eff/dI_ex = 1 - beta + beta e^{-r} (1 + r),  dI_eff/dI_dep = -beta e^{-r},  r = I_dep/I_ex
+ * (limits (1 - beta, 0) at I_ex = 0); XL_MSE: dL/dI = 2 (I - I_target) / (nx ny). */
+xl_status xl_intensity_loss_ex_backward(const void* field, const void* field_dep,
+                                        const void* target, int32_t batch, int32_t comps,
+                                        uint32_t comp_mask, const xl_grid* grid, int32_t mode,
+                                        double eps, double beta, const double* g_loss,
+                                        void* g_field, void* g_field_dep, int32_t dtype,
+                                        void* stream);
+
+/* Softmin over detectors (Methods, "Rediscovery through exploration of optical topologies": the
+ * parameter update follows the detector with the smallest loss through a smooth minimum):
+ *   out[b] = -log(sum_d exp(-beta losses[b][d])) / beta,
+ *   weights[b][d] = d out[b] / d losses[b][d] (nullable). Device doubles; beta > 0. */
+xl_status xl_softmin(const double* losses, int32_t batch, int32_t n_det, double beta, double* out,
+                     double* weights, void* stream);
+
 /* Synchronises `stream`, then returns and clears the device status: XL_ERR_NONFINITE if a loss
  * reduction produced a non-finite value since the last call, else XL_OK. */
 xl_status xl_device_status(void* stream);
@@ -283,6 +313,12 @@ xl_status xl_device_status(void* stream);
 xl_status xl_adam_step(void* params, void* m, void* v, const void* grad, int64_t n,
                        int32_t real_dtype, double lr, double beta1, double beta2, double eps,
                        const int32_t* t_dev, int32_t t_host, void* stream);
+
+/* AdamW (decoupled weight decay, used by the paper's data-driven and topology runs with
+ * weight decay 1e-4): the Adam step above and p -= lr * weight_decay * p (p before the step). */
+xl_status xl_adamw_step(void* params, void* m, void* v, const void* grad, int64_t n,
+                        int32_t real_dtype, double lr, double beta1, double beta2, double eps,
+                        double weight_decay, const int32_t* t_dev, int32_t t_host, void* stream);
 
 /* *t_dev += 1 in stream order. */
 xl_status xl_step_advance(int32_t* t_dev, void* stream);

@@ -2,6 +2,8 @@
 // Methods, Adam with step sizes 0.1, 0.01 and 0.03; Kingma & Ba). Bias-corrected, step t >= 1:
 //   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
 //   p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+// AdamW (the decoupled weight decay the paper's data-driven and topology runs use: Methods,
+// weight decay 1e-4) also subtracts lr * wd * p (p before the step).
 // The step number can live on the device so that a captured CUDA graph replays correct bias
 // corrections; xl_step_advance increments it in-stream.
 #include <cmath>
@@ -12,7 +14,7 @@ namespace xl {
 
 struct AdamArgs {
   int64_t n;
-  double lr, b1, b2, eps;
+  double lr, b1, b2, eps, wd;
   const int32_t* t_dev;
   int32_t t_host;
 };
@@ -20,16 +22,17 @@ struct AdamArgs {
 template <typename R>
 __global__ void __launch_bounds__(256) k_adam(R* __restrict__ p, R* __restrict__ m, R* __restrict__ v,
                                               const R* __restrict__ g, AdamArgs a) {
-  __shared__ R c[3];
+  __shared__ R c[4];
   if (threadIdx.x == 0) {
     const double t = (double)(a.t_dev ? *a.t_dev : a.t_host);
     const double c1 = 1.0 - pow(a.b1, t), c2 = 1.0 - pow(a.b2, t);
     c[0] = (R)(a.lr / c1);  // lr / (1 - b1^t)
     c[1] = (R)(1.0 / c2);   // 1 / (1 - b2^t)
     c[2] = (R)a.eps;
+    c[3] = (R)(a.lr * a.wd);  // decoupled weight decay (AdamW)
   }
   __syncthreads();
-  const R b1 = (R)a.b1, b2 = (R)a.b2, s = c[0], iv = c[1], eps = c[2];
+  const R b1 = (R)a.b1, b2 = (R)a.b2, s = c[0], iv = c[1], eps = c[2], dec = c[3];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const R gi = g[i];
@@ -37,7 +40,8 @@ __global__ void __launch_bounds__(256) k_adam(R* __restrict__ p, R* __restrict__
     const R vi = b2 * v[i] + ((R)1 - b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
-    p[i] -= s * mi / (sqrt(vi * iv) + eps);
+    const R pi = p[i];
+    p[i] = pi - s * mi / (sqrt(vi * iv) + eps) - dec * pi;
   }
 }
 
@@ -49,9 +53,9 @@ using namespace xl;
 
 extern "C" {
 
-xl_status xl_adam_step(void* params, void* m, void* v, const void* grad, int64_t n,
-                       int32_t real_dtype, double lr, double beta1, double beta2, double eps,
-                       const int32_t* t_dev, int32_t t_host, void* stream) {
+xl_status xl_adamw_step(void* params, void* m, void* v, const void* grad, int64_t n,
+                        int32_t real_dtype, double lr, double beta1, double beta2, double eps,
+                        double weight_decay, const int32_t* t_dev, int32_t t_host, void* stream) {
   if (n < 0) return fail(XL_ERR_ARG, "n < 0");
   if (real_dtype != 0 && real_dtype != 1) return fail(XL_ERR_ARG, "real_dtype must be 0 (float) or 1 (double)");
   if (!(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
@@ -59,7 +63,8 @@ xl_status xl_adam_step(void* params, void* m, void* v, const void* grad, int64_t
   if (!t_dev && t_host < 1) return fail(XL_ERR_ARG, "step number must be >= 1");
   if (n == 0) return XL_OK;
   if (!params || !m || !v || !grad) return fail(XL_ERR_ARG, "NULL pointer");
-  AdamArgs a{n, lr, beta1, beta2, eps, t_dev, t_host};
+  if (!(weight_decay >= 0) || !std::isfinite(weight_decay)) return fail(XL_ERR_ARG, "weight decay must be >= 0");
+  AdamArgs a{n, lr, beta1, beta2, eps, weight_decay, t_dev, t_host};
   cudaStream_t s = (cudaStream_t)stream;
   const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
   LaunchScope ls("adam", s);
@@ -69,6 +74,13 @@ xl_status xl_adam_step(void* params, void* m, void* v, const void* grad, int64_t
     k_adam<float><<<blocks, 256, 0, s>>>((float*)params, (float*)m, (float*)v, (const float*)grad, a);
   XL_CUDA_TRY(cudaGetLastError());
   return XL_OK;
+}
+
+xl_status xl_adam_step(void* params, void* m, void* v, const void* grad, int64_t n,
+                       int32_t real_dtype, double lr, double beta1, double beta2, double eps,
+                       const int32_t* t_dev, int32_t t_host, void* stream) {
+  return xl_adamw_step(params, m, v, grad, n, real_dtype, lr, beta1, beta2, eps, 0.0, t_dev, t_host,
+                       stream);
 }
 
 xl_status xl_step_advance(int32_t* t_dev, void* stream) {

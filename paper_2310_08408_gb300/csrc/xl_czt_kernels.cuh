@@ -48,8 +48,11 @@ struct CztDims {
 };
 
 template <int L, int CS> __host__ __device__ constexpr int czt_rows() {
-  return CS == 8 ? (L >= 8192 ? 2 : ((4096 / L) > 4 ? 4096 / L : 4))
+  return CS == 8 ? (L >= 4096 ? 2 : ((4096 / L) > 4 ? 4096 / L : 4))
                  : (L >= 8192 ? 1 : ((4096 / L) > 2 ? 4096 / L : 2));
+}
+template <int THREADS> __host__ __device__ constexpr int czt_min_blocks() {
+  return (1024 / THREADS) > 1 ? 1024 / THREADS : 1;
 }
 
 // Convolution of the register row with the chirp kernel: FFT, multiply by bhat, inverse FFT.
@@ -101,7 +104,8 @@ __device__ __forceinline__ double czt_z(const CztDims& d) { return d.zdev ? *d.z
 // third T plane is the transform of S = x Ex + y Ey.
 // grid: (ceil(ny / ROWS), nbatch). T plane layout: [mx][ny] (row p holds all n).
 template <typename T, int L, bool VEC>
-__global__ void __launch_bounds__(czt_rows<L, sizeof(cplx<T>)>() * (L / 16))
+__global__ void __launch_bounds__(czt_rows<L, sizeof(cplx<T>)>() * (L / 16),
+                                  czt_min_blocks<czt_rows<L, sizeof(cplx<T>)>() * (L / 16)>())
 k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d, Axis<cplx<T>> ax,
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
@@ -151,7 +155,8 @@ k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d,
 // For VEC the y pass forms Ez' = -(1/z)(X_p Ex' + Y_q Ey' - S') in registers.
 // grid: (ceil(mx / ROWS), nbatch).
 template <typename T, int L, bool VEC>
-__global__ void __launch_bounds__(czt_rows<L, sizeof(cplx<T>)>() * (L / 16))
+__global__ void __launch_bounds__(czt_rows<L, sizeof(cplx<T>)>() * (L / 16),
+                                  czt_min_blocks<czt_rows<L, sizeof(cplx<T>)>() * (L / 16)>())
 k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d, Axis<cplx<T>> ay,
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
@@ -210,7 +215,8 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
 // VEC: T planes A = C_y^H(Gx - (X_p/z) Gz), B = C_y^H(Gy - (Y_q/z) Gz), Z = C_y^H(Gz).
 // grid: (ceil(mx / ROWS), nbatch).
 template <typename T, int L, bool VEC>
-__global__ void __launch_bounds__(czt_rows<L, sizeof(cplx<T>)>() * (L / 16))
+__global__ void __launch_bounds__(czt_rows<L, sizeof(cplx<T>)>() * (L / 16),
+                                  czt_min_blocks<czt_rows<L, sizeof(cplx<T>)>() * (L / 16)>())
 k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, Axis<cplx<T>> ay,
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
@@ -270,7 +276,8 @@ k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, 
 // VEC: g_Ex = C_x^H(A) + (x/z) C_x^H(Z), g_Ey = C_x^H(B) + (y/z) C_x^H(Z).
 // grid: (ceil(ny / ROWS), nbatch).
 template <typename T, int L, bool VEC>
-__global__ void __launch_bounds__(czt_rows<L, sizeof(cplx<T>)>() * (L / 16))
+__global__ void __launch_bounds__(czt_rows<L, sizeof(cplx<T>)>() * (L / 16),
+                                  czt_min_blocks<czt_rows<L, sizeof(cplx<T>)>() * (L / 16)>())
 k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d, Axis<cplx<T>> ax,
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;

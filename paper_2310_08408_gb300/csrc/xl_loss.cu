@@ -14,6 +14,9 @@
 //   second moment  dL/dI = [(x - xbar)^2 + (y - ybar)^2 - L] / P
 //   density        dL/dI = -Area / I_eps^2 above the threshold, 0 elsewhere (no gradient through
 //                  i_max or Area, as with a where-based selection).
+//   XL_MSE (Results, "Data-driven rediscovery"): L = mean (I - I_target)^2, one sweep.
+// Optionally I is the STED effective intensity of an excitation and a depletion field (Methods,
+// "Stimulated emission depletion model"), fused into both sweeps and the gradient.
 // A non-finite loss sets a device status bit that xl_device_status() reports as
 // XL_ERR_NONFINITE.
 #include <cmath>
@@ -33,10 +36,13 @@ struct LossDims {
   int64_t plane;
   double x0, dx, y0, dy, eps;
   int mode;
+  const void* dep;     // depletion field (STED effective intensity) or nullptr
+  double beta;         // STED quenching efficiency
+  const void* target;  // MSE target intensity [batch][ny][nx] (real) or nullptr
 };
 
 template <typename T>
-__device__ __forceinline__ T intensity(const cplx<T>* f, const LossDims& d, int64_t i) {
+__device__ __forceinline__ T intensity_of(const cplx<T>* f, const LossDims& d, int64_t i) {
   T s = 0;
   for (int c = 0; c < d.comps; ++c)
     if (d.mask & (1u << c)) {
@@ -44,6 +50,22 @@ __device__ __forceinline__ T intensity(const cplx<T>* f, const LossDims& d, int6
       s += e.x * e.x + e.y * e.y;
     }
   return s;
+}
+
+// STED effective intensity (Methods, "Stimulated emission depletion model"):
+// I_eff = I_ex [1 - beta (1 - exp(-I_dep / I_ex))], 0 where I_ex = 0.
+template <typename T> __device__ __forceinline__ T sted_eff(T ie, T idp, T beta) {
+  return ie > (T)0 ? ie * ((T)1 - beta * ((T)1 - exp(-idp / ie))) : (T)0;
+}
+
+// Camera intensity of batch element b at pixel i: |E|^2 over the selected components, or the
+// STED effective intensity of the excitation (f) and depletion (d.dep) fields.
+template <typename T>
+__device__ __forceinline__ T intensity(const cplx<T>* f, const LossDims& d, int64_t i, int b) {
+  const T ie = intensity_of<T>(f, d, i);
+  if (!d.dep) return ie;
+  const cplx<T>* g = (const cplx<T>*)d.dep + (int64_t)b * d.comps * d.plane;
+  return sted_eff<T>(ie, intensity_of<T>(g, d, i), (T)d.beta);
 }
 
 __device__ __forceinline__ double bsum(double v, double* red) {
@@ -80,19 +102,22 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_sweep1(const cplx<T>* __r
   T s0 = 0, s1 = 0, s2 = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.plane;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const T I = intensity<T>(f, d, i);
+    const T I = intensity<T>(f, d, i, b);
     if (inten) inten[(int64_t)b * d.plane + i] = I;
     if (d.mode == XL_SECOND_MOMENT) {
       const T x = (T)(d.x0 + (i % d.nx) * d.dx), y = (T)(d.y0 + (i / d.nx) * d.dy);
       s0 += I;
       s1 += I * x;
       s2 += I * y;
+    } else if (d.mode == XL_MSE) {
+      const T e = I - ((const T*)d.target)[(int64_t)b * d.plane + i];
+      s0 += e * e;
     } else {
       s0 = fmax(s0, I);
     }
   }
   double* p = partial + ((int64_t)b * gridDim.x + blockIdx.x) * 3;
-  if (d.mode == XL_SECOND_MOMENT) {
+  if (d.mode == XL_SECOND_MOMENT || d.mode == XL_MSE) {
     double a = bsum((double)s0, red), bx = bsum((double)s1, red), by = bsum((double)s2, red);
     if (threadIdx.x == 0) {
       p[0] = a;
@@ -115,11 +140,13 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_sweep2(const cplx<T>* __r
   const cplx<T>* f = field + (int64_t)b * d.comps * d.plane;
   const double* sb = st + (int64_t)b * 8;
   T s0 = 0, s1 = 0;
-  if (d.mode == XL_SECOND_MOMENT) {
+  if (d.mode == XL_MSE) {
+    // single sweep: nothing to add
+  } else if (d.mode == XL_SECOND_MOMENT) {
     const T xb = (T)sb[1], yb = (T)sb[2];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.plane;
          i += (int64_t)gridDim.x * blockDim.x) {
-      const T I = intensity<T>(f, d, i);
+      const T I = intensity<T>(f, d, i, b);
       const T ex = (T)(d.x0 + (i % d.nx) * d.dx) - xb, ey = (T)(d.y0 + (i / d.nx) * d.dy) - yb;
       s0 += I * (ex * ex + ey * ey);
     }
@@ -127,7 +154,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_sweep2(const cplx<T>* __r
     const T thr = (T)sb[3];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.plane;
          i += (int64_t)gridDim.x * blockDim.x) {
-      const T I = intensity<T>(f, d, i);
+      const T I = intensity<T>(f, d, i, b);
       if (I > thr) {
         s0 += (T)1;
         s1 += I;
@@ -149,7 +176,7 @@ __global__ void k_loss_fin1(const double* __restrict__ partial, int nblk, LossDi
   const int b = blockIdx.x;
   const double* p = partial + (int64_t)b * nblk * 3;
   double* s = st + (int64_t)b * 8;
-  if (d.mode == XL_SECOND_MOMENT) {
+  if (d.mode == XL_SECOND_MOMENT || d.mode == XL_MSE) {
     double a = 0, x = 0, y = 0;
     for (int k = threadIdx.x; k < nblk; k += blockDim.x) {
       a += p[3 * k];
@@ -161,8 +188,8 @@ __global__ void k_loss_fin1(const double* __restrict__ partial, int nblk, LossDi
     y = bsum(y, red);
     if (threadIdx.x == 0) {
       s[0] = a;
-      s[1] = x / a;
-      s[2] = y / a;
+      s[1] = d.mode == XL_MSE ? 0.0 : x / a;
+      s[2] = d.mode == XL_MSE ? 0.0 : y / a;
     }
   } else {
     double m = 0;
@@ -192,6 +219,8 @@ __global__ void k_loss_fin2(const double* __restrict__ partial, int nblk, LossDi
     double L;
     if (d.mode == XL_SECOND_MOMENT) {
       L = a / s[0];
+    } else if (d.mode == XL_MSE) {
+      L = s[0] / (double)d.plane;
     } else {
       s[6] = a;
       s[7] = c;
@@ -203,45 +232,87 @@ __global__ void k_loss_fin2(const double* __restrict__ partial, int nblk, LossDi
   }
 }
 
-// g_field = 2 g_loss dL/dI E on the selected components (0 elsewhere). grid (blocks, batch).
+// g_field = 2 g_loss dL/dI E on the selected components (0 elsewhere); with a depletion field
+// the chain rule through I_eff gives g_field = 2 g dL/dI_eff dI_eff/dI_ex E_ex and
+// g_dep = 2 g dL/dI_eff dI_eff/dI_dep E_dep, with dI_eff/dI_ex = 1 - beta + beta e^{-r} (1 + r),
+// dI_eff/dI_dep = -beta e^{-r}, r = I_dep / I_ex (limits (1 - beta, 0) at I_ex = 0).
+// grid (blocks, batch).
 template <typename T>
 __global__ void __launch_bounds__(kLossThreads) k_loss_grad(const cplx<T>* __restrict__ field, LossDims d,
                                                             const double* __restrict__ st,
                                                             const double* __restrict__ g_loss,
-                                                            cplx<T>* __restrict__ gf) {
+                                                            cplx<T>* __restrict__ gf,
+                                                            cplx<T>* __restrict__ gdep) {
   const int b = blockIdx.y;
   const cplx<T>* f = field + (int64_t)b * d.comps * d.plane;
+  const cplx<T>* fd = d.dep ? (const cplx<T>*)d.dep + (int64_t)b * d.comps * d.plane : nullptr;
   cplx<T>* g = gf + (int64_t)b * d.comps * d.plane;
+  cplx<T>* gd = gdep ? gdep + (int64_t)b * d.comps * d.plane : nullptr;
   const double* sb = st + (int64_t)b * 8;
   const double gl = g_loss ? g_loss[b] : 1.0;
   const T xb = (T)sb[1], yb = (T)sb[2], L = (T)sb[5], iP = (T)(1.0 / sb[0]);
   const T thr = (T)sb[3], dens = (T)(-sb[6] / (sb[7] * sb[7]));
+  const T beta = (T)d.beta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.plane;
        i += (int64_t)gridDim.x * blockDim.x) {
     T dI;
     if (d.mode == XL_SECOND_MOMENT) {
       const T ex = (T)(d.x0 + (i % d.nx) * d.dx) - xb, ey = (T)(d.y0 + (i / d.nx) * d.dy) - yb;
       dI = (ex * ex + ey * ey - L) * iP;
+    } else if (d.mode == XL_MSE) {
+      dI = (T)2 * (intensity<T>(f, d, i, b) - ((const T*)d.target)[(int64_t)b * d.plane + i]) /
+           (T)d.plane;
     } else {
-      dI = intensity<T>(f, d, i) > thr ? dens : (T)0;
+      dI = intensity<T>(f, d, i, b) > thr ? dens : (T)0;
     }
-    const T w = (T)(2.0 * gl) * dI;
+    T wex = (T)(2.0 * gl) * dI, wdp = (T)0;
+    if (fd) {
+      const T ie = intensity_of<T>(f, d, i), idp = intensity_of<T>(fd, d, i);
+      if (ie > (T)0) {
+        const T r = idp / ie, e = exp(-r);
+        wdp = wex * (-beta * e);
+        wex = wex * ((T)1 - beta + beta * e * ((T)1 + r));
+      } else {
+        wex = wex * ((T)1 - beta);
+      }
+    }
     for (int c = 0; c < d.comps; ++c) {
       const bool on = (d.mask & (1u << c)) != 0;
-      g[c * d.plane + i] = on ? cscale(f[c * d.plane + i], w) : mk((T)0, (T)0);
+      g[c * d.plane + i] = on ? cscale(f[c * d.plane + i], wex) : mk((T)0, (T)0);
+      if (gd) gd[c * d.plane + i] = on ? cscale(fd[c * d.plane + i], wdp) : mk((T)0, (T)0);
     }
   }
+}
+
+// softmin over detectors: out[b] = -log(sum_d exp(-beta l[b][d])) / beta (minimum subtracted),
+// w[b][d] = d out[b] / d l[b][d] = exp(-beta (l - min)) / sum.
+__global__ void k_softmin(const double* __restrict__ l, int batch, int n, double beta,
+                          double* __restrict__ out, double* __restrict__ w) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  const double* lb = l + (int64_t)b * n;
+  double mn = lb[0];
+  for (int d = 1; d < n; ++d) mn = fmin(mn, lb[d]);
+  double s = 0;
+  for (int d = 0; d < n; ++d) s += exp(-beta * (lb[d] - mn));
+  out[b] = mn - log(s) / beta;
+  if (w)
+    for (int d = 0; d < n; ++d) w[(int64_t)b * n + d] = exp(-beta * (lb[d] - mn)) / s;
 }
 
 namespace {
 
 xl_status loss_check(const void* field, int32_t batch, int32_t comps, uint32_t mask,
-                     const xl_grid* g, int32_t mode, double eps, int32_t dtype, LossDims* d) {
+                     const xl_grid* g, int32_t mode, double eps, int32_t dtype, LossDims* d,
+                     const void* dep = nullptr, double beta = 0.0, const void* target = nullptr) {
   if (!g) return fail(XL_ERR_ARG, "grid is NULL");
   if (batch < 0) return fail(XL_ERR_ARG, "batch < 0");
   if (comps < 1 || comps > 3) return fail(XL_ERR_ARG, "comps must be 1..3");
   if ((mask & ((1u << comps) - 1)) == 0) return fail(XL_ERR_ARG, "comp_mask selects no component");
-  if (mode != XL_SECOND_MOMENT && mode != XL_DENSITY) return fail(XL_ERR_ARG, "unknown loss mode");
+  if (mode != XL_SECOND_MOMENT && mode != XL_DENSITY && mode != XL_MSE)
+    return fail(XL_ERR_ARG, "unknown loss mode");
+  if (mode == XL_MSE && !target) return fail(XL_ERR_ARG, "XL_MSE needs a target intensity");
+  if (dep && !(beta >= 0 && beta <= 1)) return fail(XL_ERR_ARG, "STED beta must be in [0, 1]");
   if (mode == XL_DENSITY && !(eps >= 0 && eps <= 1)) return fail(XL_ERR_ARG, "eps must be in [0, 1]");
   if (g->nx < 1 || g->ny < 1) return fail(XL_ERR_ARG, "empty grid");
   if (dtype != XL_C64 && dtype != XL_C128) return fail(XL_ERR_ARG, "bad dtype");
@@ -257,6 +328,9 @@ xl_status loss_check(const void* field, int32_t batch, int32_t comps, uint32_t m
   d->dy = g->dy;
   d->eps = eps;
   d->mode = mode;
+  d->dep = dep;
+  d->beta = beta;
+  d->target = target;
   return XL_OK;
 }
 
@@ -301,11 +375,13 @@ using namespace xl;
 
 extern "C" {
 
-xl_status xl_intensity_loss(const void* field, int32_t batch, int32_t comps, uint32_t comp_mask,
-                            const xl_grid* grid, int32_t mode, double eps, double* loss,
-                            void* intensity, int32_t dtype, void* stream) {
+xl_status xl_intensity_loss_ex(const void* field, const void* field_dep, const void* target,
+                               int32_t batch, int32_t comps, uint32_t comp_mask,
+                               const xl_grid* grid, int32_t mode, double eps, double beta,
+                               double* loss, void* intensity, int32_t dtype, void* stream) {
   LossDims d;
-  XL_TRY(loss_check(field, batch, comps, comp_mask, grid, mode, eps, dtype, &d));
+  XL_TRY(loss_check(field, batch, comps, comp_mask, grid, mode, eps, dtype, &d, field_dep, beta,
+                    target));
   if (batch == 0) return XL_OK;
   if (!loss) return fail(XL_ERR_ARG, "loss is NULL");
   cudaStream_t s = (cudaStream_t)stream;
@@ -320,15 +396,27 @@ xl_status xl_intensity_loss(const void* field, int32_t batch, int32_t comps, uin
                           : loss_stats<float>(field, batch, d, st, loss, intensity, partial, s);
 }
 
-xl_status xl_intensity_loss_backward(const void* field, int32_t batch, int32_t comps,
-                                     uint32_t comp_mask, const xl_grid* grid, int32_t mode,
-                                     double eps, const double* g_loss, void* g_field,
-                                     int32_t dtype, void* stream) {
+xl_status xl_intensity_loss(const void* field, int32_t batch, int32_t comps, uint32_t comp_mask,
+                            const xl_grid* grid, int32_t mode, double eps, double* loss,
+                            void* intensity, int32_t dtype, void* stream) {
+  if (mode == XL_MSE) return fail(XL_ERR_ARG, "XL_MSE needs xl_intensity_loss_ex (a target)");
+  return xl_intensity_loss_ex(field, nullptr, nullptr, batch, comps, comp_mask, grid, mode, eps,
+                              0.0, loss, intensity, dtype, stream);
+}
+
+xl_status xl_intensity_loss_ex_backward(const void* field, const void* field_dep,
+                                        const void* target, int32_t batch, int32_t comps,
+                                        uint32_t comp_mask, const xl_grid* grid, int32_t mode,
+                                        double eps, double beta, const double* g_loss,
+                                        void* g_field, void* g_field_dep, int32_t dtype,
+                                        void* stream) {
   LossDims d;
-  XL_TRY(loss_check(field, batch, comps, comp_mask, grid, mode, eps, dtype, &d));
+  XL_TRY(loss_check(field, batch, comps, comp_mask, grid, mode, eps, dtype, &d, field_dep, beta,
+                    target));
   if (batch == 0) return XL_OK;
   if (!g_field) return fail(XL_ERR_ARG, "g_field is NULL");
   if (g_field == field) return fail(XL_ERR_ARG, "g_field may not alias field");
+  if (field_dep && !g_field_dep) return fail(XL_ERR_ARG, "g_field_dep is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   const int nb = loss_blocks(d);
   void* ws = nullptr;
@@ -340,14 +428,38 @@ xl_status xl_intensity_loss_backward(const void* field, int32_t batch, int32_t c
   if (dtype == XL_C128) {
     XL_TRY(loss_stats<double>(field, batch, d, st, nullptr, nullptr, partial, s));
     LaunchScope ls("loss_grad", s);
-    k_loss_grad<double><<<dim3(nb, batch), kLossThreads, 0, s>>>((const cplx<double>*)field, d, st, g_loss,
-                                                                  (cplx<double>*)g_field);
+    k_loss_grad<double><<<dim3(nb, batch), kLossThreads, 0, s>>>(
+        (const cplx<double>*)field, d, st, g_loss, (cplx<double>*)g_field,
+        (cplx<double>*)(field_dep ? g_field_dep : nullptr));
   } else {
     XL_TRY(loss_stats<float>(field, batch, d, st, nullptr, nullptr, partial, s));
     LaunchScope ls("loss_grad", s);
-    k_loss_grad<float><<<dim3(nb, batch), kLossThreads, 0, s>>>((const cplx<float>*)field, d, st, g_loss,
-                                                                (cplx<float>*)g_field);
+    k_loss_grad<float><<<dim3(nb, batch), kLossThreads, 0, s>>>(
+        (const cplx<float>*)field, d, st, g_loss, (cplx<float>*)g_field,
+        (cplx<float>*)(field_dep ? g_field_dep : nullptr));
   }
+  XL_CUDA_TRY(cudaGetLastError());
+  return XL_OK;
+}
+
+xl_status xl_intensity_loss_backward(const void* field, int32_t batch, int32_t comps,
+                                     uint32_t comp_mask, const xl_grid* grid, int32_t mode,
+                                     double eps, const double* g_loss, void* g_field,
+                                     int32_t dtype, void* stream) {
+  if (mode == XL_MSE) return fail(XL_ERR_ARG, "XL_MSE needs xl_intensity_loss_ex_backward");
+  return xl_intensity_loss_ex_backward(field, nullptr, nullptr, batch, comps, comp_mask, grid,
+                                       mode, eps, 0.0, g_loss, g_field, nullptr, dtype, stream);
+}
+
+xl_status xl_softmin(const double* losses, int32_t batch, int32_t n_det, double beta, double* out,
+                     double* weights, void* stream) {
+  if (batch < 0 || n_det < 1) return fail(XL_ERR_ARG, "softmin: bad sizes");
+  if (!(beta > 0) || !std::isfinite(beta)) return fail(XL_ERR_ARG, "softmin: beta must be > 0");
+  if (batch == 0) return XL_OK;
+  if (!losses || !out) return fail(XL_ERR_ARG, "softmin: NULL pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  LaunchScope ls("softmin", s);
+  k_softmin<<<(batch + 127) / 128, 128, 0, s>>>(losses, batch, n_det, beta, out, weights);
   XL_CUDA_TRY(cudaGetLastError());
   return XL_OK;
 }

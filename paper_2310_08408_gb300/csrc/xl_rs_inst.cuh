@@ -23,7 +23,7 @@ xl_status pass1_L(const void* in, void* Tb, int nx, int ny, int cin, int cT, int
 
 template <typename T, int LX>
 xl_status pass3_L(const void* Tb, void* out, int nx, int ny, int cout, int cT, int np, cudaStream_t s) {
-  constexpr int ROWS = rows_transp<LX, sizeof(cplx<T>)>();
+  constexpr int ROWS = rows_p3<LX, sizeof(cplx<T>)>();
   const size_t sm = (size_t)ROWS * rpitch(LX) * sizeof(cplx<T>);
   const void* tw;
   XL_TRY(twiddles(LX, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));

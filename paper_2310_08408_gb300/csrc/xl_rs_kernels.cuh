@@ -31,9 +31,20 @@ __host__ __device__ constexpr bool kind_odd_y(int k) { return k == KHY || k == K
 
 // Rows per block: the transposing passes (1 and 3) write/read whole 32-byte sectors per kx when
 // a block holds at least 32 / sizeof(complex) rows; pass 2 aims at 256 threads per block.
+// Pass 1 (and the generator's first pass): 4 rows at L = 4096 (whole sectors per kx, measured
+// fastest); pass 3: 2 rows at L >= 4096 (two or more resident blocks per SM, measured fastest).
 template <int L, int CS> __host__ __device__ constexpr int rows_transp() {
   return CS == 8 ? (L >= 8192 ? 2 : ((4096 / L) > 4 ? 4096 / L : 4))
                  : (L >= 8192 ? 1 : ((4096 / L) > 2 ? 4096 / L : 2));
+}
+template <int L, int CS> __host__ __device__ constexpr int rows_p3() {
+  return CS == 8 ? (L >= 4096 ? 2 : ((4096 / L) > 4 ? 4096 / L : 4))
+                 : (L >= 8192 ? 1 : ((4096 / L) > 2 ? 4096 / L : 2));
+}
+// Minimum resident blocks the transposing kernels ask the register allocator for (two blocks of
+// 512 threads, or one of 1024).
+template <int THREADS> __host__ __device__ constexpr int min_blocks_1024() {
+  return (1024 / THREADS) > 1 ? 1024 / THREADS : 1;
 }
 template <int L> __host__ __device__ constexpr int rows_cols() { return (4096 / L) > 1 ? 4096 / L : 1; }
 
@@ -54,7 +65,8 @@ __device__ __forceinline__ C spec_at(const C* __restrict__ Hk, int kx, int ky, i
 // Pass 1: row FFT (forward) of planes [ny][nx] into T[kx][y].
 // Plane p of the input maps to plane (p / cin) * cT + (p % cin) of the T buffer.
 template <typename T, int LX>
-__global__ void __launch_bounds__(rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16))
+__global__ void __launch_bounds__(rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16),
+                                  min_blocks_1024<rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16)>())
 k_rs_pass1(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, int nx, int ny, int cin,
            int cT, const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
@@ -84,11 +96,12 @@ k_rs_pass1(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, int nx, int
 // Pass 3: inverse row FFT from T[kx][y] into planes [ny][nx] (crop to x < nx).
 // Plane p of the output maps to plane (p / cout) * cT + (p % cout) of T.
 template <typename T, int LX>
-__global__ void __launch_bounds__(rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16))
+__global__ void __launch_bounds__(rows_p3<LX, sizeof(cplx<T>)>() * (LX / 16),
+                                  min_blocks_1024<rows_p3<LX, sizeof(cplx<T>)>() * (LX / 16)>())
 k_rs_pass3(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, int nx, int ny, int cout,
            int cT, const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
-  constexpr int ROWS = rows_transp<LX, sizeof(C)>();
+  constexpr int ROWS = rows_p3<LX, sizeof(C)>();
   constexpr int TT = LX / 16;
   constexpr int P = rpitch(LX);
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -517,7 +530,8 @@ __device__ __forceinline__ cplx<double> rs_sample<double>(int kind, int a, int b
 // Generator pass A: for each b in [0, ny) and each kind, FFT along a of the kernel row placed
 // mod LX; keep kx in [0, nx]; store transposed S[kind][kx][b].
 template <typename T, int LX>
-__global__ void __launch_bounds__(rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16))
+__global__ void __launch_bounds__(rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16),
+                                  min_blocks_1024<rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16)>())
 k_gen_pass_a(cplx<T>* __restrict__ S, GenArgs g, const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
   constexpr int ROWS = rows_transp<LX, sizeof(C)>();

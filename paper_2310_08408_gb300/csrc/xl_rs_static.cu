@@ -125,11 +125,14 @@ xl_status run_static(const float2* in, float2* out, int32_t batch, const xl_grid
   pa.slot[KH] = 0;
 
   // every launch below needs less than 48 KB of shared memory (transform lengths <= 512)
-  constexpr int RA = rows_transp<LX, 8>(), RB = rows_cols<LY>(), RC = rows_cols<LY>();
+  constexpr int RA = rows_transp<LX, 8>(), R3 = rows_p3<LX, 8>(), RB = rows_cols<LY>(),
+                RC = rows_cols<LY>();
   const size_t smA = (size_t)RA * rpitch(LX) * sizeof(float2);
+  const size_t sm3 = (size_t)R3 * rpitch(LX) * sizeof(float2);
   const size_t smB = (size_t)RB * srow(LY) * sizeof(float2);
   const size_t smP2 = (size_t)RC * srow(LY) * sizeof(float2);
-  static_assert(RA * rpitch(LX) * 8 <= 48 * 1024 && RB * srow(LY) * 8 <= 48 * 1024, "smem");
+  static_assert(RA * rpitch(LX) * 8 <= 48 * 1024 && R3 * rpitch(LX) * 8 <= 48 * 1024 &&
+                    RB * srow(LY) * 8 <= 48 * 1024, "smem");
   const int64_t plane = (int64_t)nx * ny;
   for (int32_t b = 0; b < batch; ++b) {
     if (b == 0 || z[b] != z[b - 1]) {
@@ -145,7 +148,7 @@ xl_status run_static(const float2* in, float2* out, int32_t batch, const xl_grid
     k_rs_pass2<float, LY, P2_RS><<<dim3((LX + RC - 1) / RC, 1), RC * (LY / 16), smP2, s>>>(
         T, nullptr, Hq, nullptr, pa, twy);
     XL_CUDA_TRY(cudaGetLastError());
-    k_rs_pass3<float, LX><<<dim3((ny + RA - 1) / RA, 1), RA * (LX / 16), smA, s>>>(
+    k_rs_pass3<float, LX><<<dim3((ny + R3 - 1) / R3, 1), R3 * (LX / 16), sm3, s>>>(
         T, out + b * plane, nx, ny, 1, 1, twx);
     XL_CUDA_TRY(cudaGetLastError());
   }

@@ -68,7 +68,7 @@ class Element(ctypes.Structure):
 
 
 SLM, SSLM, LENS, POLARIZER, WAVEPLATE, TO_VECTOR = range(6)
-SECOND_MOMENT, DENSITY = 0, 1
+SECOND_MOMENT, DENSITY, MSE = 0, 1, 2
 
 class TableConfig(ctypes.Structure):
     """xl_table_config of the batched optical-table optimiser."""
@@ -105,8 +105,13 @@ SIGNATURES = {
                                     _I, _P, _P, _P, _I, _P], _I),
     "xl_intensity_loss": ([_P, _I, _I, ctypes.c_uint32, _GP, _I, _D, _P, _P, _I, _P], _I),
     "xl_intensity_loss_backward": ([_P, _I, _I, ctypes.c_uint32, _GP, _I, _D, _P, _P, _I, _P], _I),
+    "xl_intensity_loss_ex": ([_P, _P, _P, _I, _I, ctypes.c_uint32, _GP, _I, _D, _D, _P, _P, _I, _P], _I),
+    "xl_intensity_loss_ex_backward": ([_P, _P, _P, _I, _I, ctypes.c_uint32, _GP, _I, _D, _D, _P, _P,
+                                       _P, _I, _P], _I),
+    "xl_softmin": ([_P, _I, _I, _D, _P, _P, _P], _I),
     "xl_device_status": ([_P], _I),
     "xl_adam_step": ([_P, _P, _P, _P, ctypes.c_int64, _I, _D, _D, _D, _D, _P, _I, _P], _I),
+    "xl_adamw_step": ([_P, _P, _P, _P, ctypes.c_int64, _I, _D, _D, _D, _D, _D, _P, _I, _P], _I),
     "xl_step_advance": ([_P, _P], _I),
     "xl_batch_create": ([ctypes.POINTER(TableConfig), _I, _P, _P, ctypes.c_uint64,
                          ctypes.POINTER(ctypes.c_void_p), _P], _I),
@@ -487,6 +492,54 @@ def intensity_loss_backward(field: torch.Tensor, grid, comp_mask: int, mode: int
     return out
 
 
+def intensity_loss_ex(field: torch.Tensor, grid, comp_mask: int, mode: int = SECOND_MOMENT,
+                      eps: float = 0.5, field_dep: torch.Tensor | None = None, beta: float = 1.0,
+                      target: torch.Tensor | None = None, want_intensity: bool = False):
+    """Camera loss of |E|^2, of the STED effective intensity (field_dep given) or the MSE to a
+    target intensity (mode MSE). Returns (loss [B], intensity or None)."""
+    _dev(field, "field")
+    B, C, ny, nx = field.shape
+    g = Grid.of(grid)
+    loss = torch.empty(B, dtype=torch.float64, device=field.device)
+    inten = torch.empty((B, ny, nx), dtype=_real_dtype(field), device=field.device) if want_intensity else None
+    _check(load().xl_intensity_loss_ex(
+        field.data_ptr(), _dev(field_dep, "field_dep").data_ptr() if field_dep is not None else None,
+        _dev(target, "target").data_ptr() if target is not None else None, B, C, comp_mask,
+        ctypes.byref(g), mode, float(eps), float(beta), loss.data_ptr(),
+        inten.data_ptr() if inten is not None else None, _dtype(field), _stream()))
+    return loss, inten
+
+
+def intensity_loss_ex_backward(field: torch.Tensor, grid, comp_mask: int, mode: int = SECOND_MOMENT,
+                               eps: float = 0.5, field_dep: torch.Tensor | None = None,
+                               beta: float = 1.0, target: torch.Tensor | None = None,
+                               g_loss: torch.Tensor | None = None):
+    """Returns (g_field, g_field_dep or None)."""
+    _dev(field, "field")
+    B, C, ny, nx = field.shape
+    g = Grid.of(grid)
+    gf = torch.empty_like(field)
+    gd = torch.empty_like(field_dep) if field_dep is not None else None
+    _check(load().xl_intensity_loss_ex_backward(
+        field.data_ptr(), field_dep.data_ptr() if field_dep is not None else None,
+        _dev(target, "target").data_ptr() if target is not None else None, B, C, comp_mask,
+        ctypes.byref(g), mode, float(eps), float(beta),
+        _dev(g_loss, "g_loss").data_ptr() if g_loss is not None else None, gf.data_ptr(),
+        gd.data_ptr() if gd is not None else None, _dtype(field), _stream()))
+    return gf, gd
+
+
+def softmin(losses: torch.Tensor, beta: float, want_weights: bool = True):
+    """losses [B][n_det] float64 CUDA -> (softmin [B], weights [B][n_det] or None)."""
+    _dev(losses, "losses")
+    B, n = losses.shape
+    out = torch.empty(B, dtype=torch.float64, device=losses.device)
+    w = torch.empty_like(losses) if want_weights else None
+    _check(load().xl_softmin(losses.data_ptr(), B, n, float(beta), out.data_ptr(),
+                             w.data_ptr() if w is not None else None, _stream()))
+    return out, w
+
+
 def device_status() -> None:
     """Raises XLError(ERR_NONFINITE) if a loss became non-finite since the last check."""
     _check(load().xl_device_status(_stream()))
@@ -509,6 +562,19 @@ def adam_step(p: torch.Tensor, m: torch.Tensor, v: torch.Tensor, grad: torch.Ten
     _check(load().xl_adam_step(p.data_ptr(), m.data_ptr(), v.data_ptr(), grad.data_ptr(), p.numel(),
                                rd, float(lr), float(beta1), float(beta2), float(eps), t_dev, t_host,
                                _stream()))
+
+
+def adamw_step(p: torch.Tensor, m: torch.Tensor, v: torch.Tensor, grad: torch.Tensor, lr: float,
+               t, weight_decay: float, beta1: float = 0.9, beta2: float = 0.999,
+               eps: float = 1e-8) -> None:
+    """In-place AdamW step (decoupled weight decay)."""
+    for name, a in (("p", p), ("m", m), ("v", v), ("grad", grad)):
+        _dev(a, name)
+    rd = {torch.float32: 0, torch.float64: 1}[p.dtype]
+    t_dev, t_host = (t.data_ptr(), 0) if isinstance(t, torch.Tensor) else (None, int(t))
+    _check(load().xl_adamw_step(p.data_ptr(), m.data_ptr(), v.data_ptr(), grad.data_ptr(),
+                                p.numel(), rd, float(lr), float(beta1), float(beta2), float(eps),
+                                float(weight_decay), t_dev, t_host, _stream()))
 
 
 def step_advance(t: torch.Tensor) -> None:
