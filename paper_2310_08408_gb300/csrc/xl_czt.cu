@@ -49,11 +49,11 @@ CztTabArgs tab_args(const xl_grid* g, const xl_window* w, double wavelength) {
   a.lambda = wavelength;
   a.zdev = nullptr;
   a.zval = 0;
-  a.off_y = (int64_t)a.nx + a.mx + 2 * (int64_t)a.Lx;
+  a.off_y = (int64_t)a.nx + a.mx + a.Lx;
   return a;
 }
 
-int64_t tab_elems(const CztTabArgs& a) { return a.off_y + a.ny + a.my + 2 * (int64_t)a.Ly; }
+int64_t tab_elems(const CztTabArgs& a) { return a.off_y + a.ny + a.my + a.Ly; }
 
 template <typename T>
 xl_status get_tables(const xl_grid* g, const xl_window* w, double wavelength, const double* z,
@@ -85,12 +85,10 @@ void axes(const void* tab, const CztTabArgs& a, Axis<cplx<T>>* ax, Axis<cplx<T>>
   ax->pre = t;
   ax->post = t + a.nx;
   ax->bhat = t + a.nx + a.mx;
-  ax->bhat_adj = t + a.nx + a.mx + a.Lx;
   const cplx<T>* u = t + a.off_y;
   ay->pre = u;
   ay->post = u + a.ny;
   ay->bhat = u + a.ny + a.my;
-  ay->bhat_adj = u + a.ny + a.my + a.Ly;
 }
 
 template <typename T>
@@ -120,6 +118,7 @@ xl_status run(bool adjoint, const void* in, void* out, int32_t batch, bool vec, 
   d.xo0 = w->xo0; d.dxo = w->dxo; d.yo0 = w->yo0; d.dyo = w->dyo;
   const int cin = in_planes, cwin = vec ? 3 : 1;
   d.in_planes = in_planes;
+  d.adjoint = adjoint ? 1 : 0;
   for (int32_t b0 = 0; b0 < batch;) {
     int nb = 1;
     if (!zdev)

@@ -8,8 +8,8 @@ namespace {
 template <typename T, int L, bool VEC>
 xl_status pass_LV(int which, const void* src, void* dst, const CztDims& d, const Axis<cplx<T>>& ax,
                   int nb, cudaStream_t s) {
-  constexpr int ROWS = czt_rows<L, sizeof(cplx<T>)>();
-  const size_t sm = (size_t)ROWS * rpitch(L) * sizeof(cplx<T>);
+  constexpr int ROWS = czt_rows<L, sizeof(cplx<T>), VEC>();
+  const size_t sm = czt_smem_bytes<L, sizeof(cplx<T>), VEC>();
   const void* tw;
   XL_TRY(twiddles(L, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
   const cplx<T>* twc = (const cplx<T>*)tw;
@@ -61,7 +61,7 @@ xl_status bhat_L(cplx<T>* rows, int64_t stride, cudaStream_t s) {
   XL_TRY(twiddles(L, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
   XL_TRY(smem_attr((const void*)k_czt_bhat<T, L>, sm));
   LaunchScope ls("czt_bhat<" + std::to_string(L) + ">", s);
-  k_czt_bhat<T, L><<<2, L / 16, sm, s>>>(rows, stride, (const cplx<T>*)tw);
+  k_czt_bhat<T, L><<<1, L / 16, sm, s>>>(rows, stride, (const cplx<T>*)tw);
   XL_CUDA_TRY(cudaGetLastError());
   return XL_OK;
 }
@@ -100,7 +100,7 @@ xl_status czt_pass<XL_REAL>(int which, bool vec, int L, const void* src, void* d
 template <>
 xl_status czt_tables<XL_REAL>(void* tab, const CztTabArgs& a, cudaStream_t s) {
   typedef cplx<XL_REAL> C;
-  const int64_t total = (int64_t)a.nx + a.mx + 2 * (int64_t)a.Lx + a.ny + a.my + 2 * (int64_t)a.Ly;
+  const int64_t total = (int64_t)a.nx + a.mx + a.Lx + a.ny + a.my + a.Ly;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 1024);
   {
   LaunchScope ls("czt_tables", s);

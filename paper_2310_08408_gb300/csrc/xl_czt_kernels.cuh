@@ -21,6 +21,8 @@
 // S = x Ex + y Ey and the combination is formed in registers by the y pass.
 // Adjoint: each axis is the conjugate-chirp convolution of length L in the other direction
 // (pre-multiply conj(post), kernel b* placed for -(M-1) <= j <= N-1, post-multiply conj(pre)).
+// Because b is even in j, that kernel is b placed for the forward range, mirrored and
+// conjugated, and its DFT is conj(bhat): one table per axis serves both directions.
 // Vectorial adjoint: g_Ex = C^H(Gx - (X/z) Gz) + (x/z) C^H(Gz), g_Ey likewise with y.
 #pragma once
 
@@ -29,12 +31,11 @@
 namespace xl {
 
 // One axis of chirp tables (device, complex T). Layout of the table buffer per axis:
-// pre[N] | post[M] | bhat[L] | bhat_adj[L].
+// pre[N] | post[M] | bhat[L].
 template <typename C> struct Axis {
   const C* pre;
   const C* post;
   const C* bhat;
-  const C* bhat_adj;
 };
 
 struct CztDims {
@@ -43,26 +44,75 @@ struct CztDims {
   double xo0, dxo, yo0, dyo;  // output window
   const double* zdev;         // device z (or nullptr)
   double zval;
+  int adjoint;                // 1 for the adjoint passes: the chirp spectrum is conj(bhat)
   int in_planes;              // planes per batch element of the input-grid field (fwd x input,
                               // adjoint x output): 1, 2, or 3 (a vector field whose Ez is unused)
 };
 
-template <int L, int CS> __host__ __device__ constexpr int czt_rows() {
-  return CS == 8 ? (L >= 4096 ? 2 : ((4096 / L) > 4 ? 4096 / L : 4))
-                 : (L >= 8192 ? 1 : ((4096 / L) > 2 ? 4096 / L : 2));
+// Launch shape of the row passes. A block holds ROWS teams of L/16 threads; the scalar passes
+// use all of shared memory for the teams' transform rows. The vectorial passes carry one
+// 16-element complex array per thread across transforms (the Ez accumulator of the forward y
+// pass, Gz in the adjoint y pass, C_x^H(Z) in the adjoint x pass): they run a quarter as many teams
+// per block and keep that array in a second, thread-private shared-memory row per team when it
+// fits (in registers otherwise), so that the transforms do not spill. Their loops over the 2-3
+// planes are unrolled on purpose: as runtime loops, the compiler hoisted loop-invariant work of
+// the transforms out of them and spilled 400-600 bytes a thread.
+template <int L, int CS, bool VEC = false> __host__ __device__ constexpr int czt_rows() {
+  constexpr int r = CS == 8 ? (L >= 4096 ? 2 : ((4096 / L) > 4 ? 4096 / L : 4))
+                            : (L >= 8192 ? 1 : ((4096 / L) > 2 ? 4096 / L : 2));
+  return VEC ? (r / 4 > 1 ? r / 4 : 1) : r;
 }
-template <int THREADS> __host__ __device__ constexpr int czt_min_blocks() {
-  return (1024 / THREADS) > 1 ? 1024 / THREADS : 1;
+template <int L, int CS, bool VEC> __host__ __device__ constexpr bool czt_stash_smem() {
+  return VEC && (size_t)2 * czt_rows<L, CS, VEC>() * rpitch(L) * CS <= (size_t)227 * 1024;
+}
+template <int L, int CS, bool VEC> __host__ __device__ constexpr size_t czt_smem_bytes() {
+  return (size_t)czt_rows<L, CS, VEC>() * (czt_stash_smem<L, CS, VEC>() ? 2 : 1) * rpitch(L) * CS;
+}
+template <int L, int CS, bool VEC> __host__ __device__ constexpr int czt_threads() {
+  return czt_rows<L, CS, VEC>() * (L / 16);
+}
+// Resident blocks per SM the register budget aims at: up to 1024 threads, as shared memory allows
+// (1 KB of each block's shared memory is reserved by the runtime).
+template <int L, int CS, bool VEC> __host__ __device__ constexpr int czt_min_blocks() {
+  constexpr int by_threads = 1024 / czt_threads<L, CS, VEC>() > 1 ? 1024 / czt_threads<L, CS, VEC>() : 1;
+  constexpr int by_smem = (int)(((size_t)228 * 1024) / (czt_smem_bytes<L, CS, VEC>() + 1024));
+  return by_smem < 1 ? 1 : (by_smem < by_threads ? by_smem : by_threads);
 }
 
-// Convolution of the register row with the chirp kernel: FFT, multiply by bhat, inverse FFT.
+// Thread-private 16-element stash (element q of thread t is row element t + q L/16), in a shared
+// memory row or in registers.
+template <typename C, int TT, bool SMEM> struct Stash {
+  C r[16];
+  __device__ __forceinline__ void init(C*, int) {}
+  __device__ __forceinline__ C get(int q) const { return r[q]; }
+  __device__ __forceinline__ void set(int q, C v) { r[q] = v; }
+};
+template <typename C, int TT> struct Stash<C, TT, true> {
+  C* p;
+  int t;
+  __device__ __forceinline__ void init(C* row, int tt) { p = row; t = tt; }
+  __device__ __forceinline__ C get(int q) const { return p[spad(t + q * TT)]; }
+  __device__ __forceinline__ void set(int q, C v) { p[spad(t + q * TT)] = v; }
+};
+
+// Convolution of the register row with the chirp kernel: FFT, multiply by bhat (conj(bhat) for
+// the adjoint), inverse FFT. The direction is a runtime value on purpose: the two multiply
+// loops become separate basic blocks, which keeps the compiler from interleaving the inverse
+// transform's loads and address arithmetic into the forward transform (with both transforms in
+// one block, two back-to-back transforms of length 4096 spilled about 500 bytes a thread at the
+// 64-register budget that two 512-thread blocks per SM allow).
 template <int L, typename C>
 __device__ __forceinline__ void chirp_conv(C (&v)[16], C* row, int t, const C* __restrict__ tw,
-                                           const C* __restrict__ bhat) {
+                                           const C* __restrict__ bhat, bool cj) {
   constexpr int TT = L / 16;
   team_fft<L, -1>(v, row, t, tw);
+  if (cj) {
 #pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = cmul(v[q], __ldg(bhat + t + q * TT));
+    for (int q = 0; q < 16; ++q) v[q] = cmulc(v[q], __ldg(bhat + t + q * TT));
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = cmul(v[q], __ldg(bhat + t + q * TT));
+  }
   team_fft<L, +1>(v, row, t, tw);
 }
 
@@ -100,16 +150,28 @@ __device__ __forceinline__ void load_transposed(C (&v)[16], C* sm, int team, int
 
 __device__ __forceinline__ double czt_z(const CztDims& d) { return d.zdev ? *d.zdev : d.zval; }
 
+#define XL_CZT_BOUNDS(T, L, VEC) \
+  __launch_bounds__(czt_threads<L, sizeof(cplx<T>), VEC>(), czt_min_blocks<L, sizeof(cplx<T>), VEC>())
+
+// Coordinates of the samples a thread holds, s0 + (t + q L/16) D, as base + q step in T (one
+// double-precision operation per row instead of one per sample: FP64 runs at a small fraction
+// of the FP32 rate).
+template <typename T> struct Coord {
+  T base, step;
+  __device__ __forceinline__ Coord(double s0, double D, int t, int TT)
+      : base((T)(s0 + t * D)), step((T)(TT * D)) {}
+  __device__ __forceinline__ T at(int q) const { return base + (T)q * step; }
+};
+
 // Forward x pass. Planes of element b: input cin (1 or 2), T planes cT (1 or 3). For VEC the
 // third T plane is the transform of S = x Ex + y Ey.
 // grid: (ceil(ny / ROWS), nbatch). T plane layout: [mx][ny] (row p holds all n).
 template <typename T, int L, bool VEC>
-__global__ void __launch_bounds__(czt_rows<L, sizeof(cplx<T>)>() * (L / 16),
-                                  czt_min_blocks<czt_rows<L, sizeof(cplx<T>)>() * (L / 16)>())
+__global__ void XL_CZT_BOUNDS(T, L, VEC)
 k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d, Axis<cplx<T>> ax,
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
-  constexpr int ROWS = czt_rows<L, sizeof(C)>();
+  constexpr int ROWS = czt_rows<L, sizeof(C), VEC>();
   constexpr int TT = L / 16;
   constexpr int SR = rpitch(L);
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -121,7 +183,9 @@ k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d,
   const int cT = VEC ? 3 : 1;
   const int64_t plane = (int64_t)d.nx * d.ny, tplane = (int64_t)d.mx * d.ny;
   C* row = sm + team * SR;
-#pragma unroll 1
+  const Coord<T> xm(d.x0, d.dx, t, TT);
+  const T yn = (T)(d.y0 + n * d.dy);
+#pragma unroll
   for (int c = 0; c < cT; ++c) {
     C v[16];
     const C* s0 = in + ((int64_t)b * d.in_planes) * plane + (int64_t)n * d.nx;
@@ -130,17 +194,13 @@ k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d,
       const int m = t + q * TT;
       C a = mk((T)0, (T)0);
       if (m < d.nx) {
-        if (c < 2) {
-          a = s0[c * plane + m];
-        } else {
-          const T xm = (T)(d.x0 + m * d.dx), yn = (T)(d.y0 + n * d.dy);
-          a = cadd(cscale(s0[m], xm), cscale(s0[plane + m], yn));
-        }
+        if (c < 2) a = s0[c * plane + m];
+        else a = cadd(cscale(s0[m], xm.at(q)), cscale(s0[plane + m], yn));
         a = cmul(a, __ldg(ax.pre + m));
       }
       v[q] = a;
     }
-    chirp_conv<L>(v, row, t, tw, ax.bhat);
+    chirp_conv<L>(v, row, t, tw, ax.bhat, d.adjoint);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int p = t + q * TT;
@@ -152,15 +212,15 @@ k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d,
 }
 
 // Forward y pass: rows p of the T planes -> window planes [my][mx] (stored transposed).
-// For VEC the y pass forms Ez' = -(1/z)(X_p Ex' + Y_q Ey' - S') in registers.
+// For VEC the y pass forms Ez' = -(1/z)(X_p Ex' + Y_q Ey' - S'), accumulating X_p Ex' + Y_q Ey'
+// in the thread's stash.
 // grid: (ceil(mx / ROWS), nbatch).
 template <typename T, int L, bool VEC>
-__global__ void __launch_bounds__(czt_rows<L, sizeof(cplx<T>)>() * (L / 16),
-                                  czt_min_blocks<czt_rows<L, sizeof(cplx<T>)>() * (L / 16)>())
+__global__ void XL_CZT_BOUNDS(T, L, VEC)
 k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d, Axis<cplx<T>> ay,
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
-  constexpr int ROWS = czt_rows<L, sizeof(C)>();
+  constexpr int ROWS = czt_rows<L, sizeof(C), VEC>();
   constexpr int TT = L / 16;
   constexpr int SR = rpitch(L);
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -172,8 +232,15 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
   const int cT = VEC ? 3 : 1;
   const int64_t tplane = (int64_t)d.mx * d.ny, oplane = (int64_t)d.mx * d.my;
   C* row = sm + team * SR;
-  C ex[16], ey[16];
-#pragma unroll 1
+  Stash<C, TT, czt_stash_smem<L, sizeof(C), VEC>()> acc;
+  acc.init(sm + (ROWS + team) * SR, t);
+  T Xp = (T)0, iz = (T)0;
+  if constexpr (VEC) {
+    Xp = (T)(d.xo0 + p * d.dxo);
+    iz = (T)(-1.0 / czt_z(d));
+  }
+  const Coord<T> yq(d.yo0, d.dyo, t, TT);
+#pragma unroll
   for (int c = 0; c < cT; ++c) {
     C v[16];
     const C* s = Tb + ((int64_t)b * cT + c) * tplane + (int64_t)p * d.ny;
@@ -182,7 +249,7 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
       const int n = t + q * TT;
       v[q] = n < d.ny ? cmul(s[n], __ldg(ay.pre + n)) : mk((T)0, (T)0);
     }
-    chirp_conv<L>(v, row, t, tw, ay.bhat);
+    chirp_conv<L>(v, row, t, tw, ay.bhat, d.adjoint);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int qq = t + q * TT;
@@ -191,19 +258,13 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
     if constexpr (VEC) {
       if (c == 0) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) ex[q] = v[q];
+        for (int q = 0; q < 16; ++q) acc.set(q, cscale(v[q], Xp));
       } else if (c == 1) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) ey[q] = v[q];
+        for (int q = 0; q < 16; ++q) acc.set(q, cadd(acc.get(q), cscale(v[q], yq.at(q))));
       } else {
-        const double z = czt_z(d);
-        const T iz = (T)(-1.0 / z);
-        const T Xp = (T)(d.xo0 + p * d.dxo);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const T Yq = (T)(d.yo0 + (t + q * TT) * d.dyo);
-          v[q] = cscale(csub(cadd(cscale(ex[q], Xp), cscale(ey[q], Yq)), v[q]), iz);
-        }
+        for (int q = 0; q < 16; ++q) v[q] = cscale(csub(acc.get(q), v[q]), iz);
       }
     }
     store_transposed<L, ROWS>(v, sm, team, t, d.my, out + ((int64_t)b * cT + c) * oplane, d.mx, p0,
@@ -212,15 +273,16 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
 }
 
 // Adjoint y pass: columns p of the window gradient planes [my][mx] -> T planes [mx][ny] (rows).
-// VEC: T planes A = C_y^H(Gx - (X_p/z) Gz), B = C_y^H(Gy - (Y_q/z) Gz), Z = C_y^H(Gz).
+// VEC: T planes A = C_y^H(Gx - (X_p/z) Gz), B = C_y^H(Gy - (Y_q/z) Gz), Z = C_y^H(Gz); Gz is
+// loaded once into the thread's stash.
 // grid: (ceil(mx / ROWS), nbatch).
 template <typename T, int L, bool VEC>
-__global__ void __launch_bounds__(czt_rows<L, sizeof(cplx<T>)>() * (L / 16),
-                                  czt_min_blocks<czt_rows<L, sizeof(cplx<T>)>() * (L / 16)>())
+__global__ void XL_CZT_BOUNDS(T, L, VEC)
 k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, Axis<cplx<T>> ay,
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
-  constexpr int ROWS = czt_rows<L, sizeof(C)>();
+  constexpr int ROWS = czt_rows<L, sizeof(C), VEC>();
+  constexpr bool SMST = czt_stash_smem<L, sizeof(C), VEC>();
   constexpr int TT = L / 16;
   constexpr int SR = rpitch(L);
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -233,25 +295,36 @@ k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, 
   const int cT = VEC ? 3 : 1;
   const int64_t tplane = (int64_t)d.mx * d.ny, oplane = (int64_t)d.mx * d.my;
   C* row = sm + team * SR;
-  C gz[16];
-  if constexpr (VEC) load_transposed<L, ROWS>(gz, sm, team, t, d.my, G + ((int64_t)b * 3 + 2) * oplane, d.mx, p0, d.mx);
-#pragma unroll 1
+  Stash<C, TT, SMST> gz;
+  gz.init(sm + (ROWS + team) * SR, t);
+  T Xp = (T)0, iz = (T)0;
+  if constexpr (VEC) {
+    Xp = (T)(d.xo0 + p * d.dxo);
+    iz = (T)(1.0 / czt_z(d));
+    const C* gzsrc = G + ((int64_t)b * 3 + 2) * oplane;
+    if constexpr (SMST) {
+      load_rows_transposed<ROWS, SR>(sm + ROWS * SR, d.my, L, gzsrc, d.mx, p0, d.mx);
+      __syncthreads();
+    } else {
+      load_transposed<L, ROWS>(gz.r, sm, team, t, d.my, gzsrc, d.mx, p0, d.mx);
+    }
+  }
+  const Coord<T> yq(d.yo0, d.dyo, t, TT);
+#pragma unroll
   for (int c = 0; c < cT; ++c) {
     C v[16];
     if (c < 2) {
       load_transposed<L, ROWS>(v, sm, team, t, d.my, G + ((int64_t)b * cT + c) * oplane, d.mx, p0, d.mx);
     } else {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = gz[q];
+      for (int q = 0; q < 16; ++q) v[q] = gz.get(q);
     }
     if constexpr (VEC) {
       if (c < 2) {
-        const T iz = (T)(1.0 / czt_z(d));
-        const T Xp = (T)(d.xo0 + p * d.dxo);
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          const T w = c == 0 ? Xp : (T)(d.yo0 + (t + q * TT) * d.dyo);
-          v[q] = csub(v[q], cscale(gz[q], w * iz));
+          const T w = c == 0 ? Xp : yq.at(q);
+          v[q] = csub(v[q], cscale(gz.get(q), w * iz));
         }
       }
     }
@@ -260,7 +333,7 @@ k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, 
       const int qq = t + q * TT;
       v[q] = qq < d.my ? cmulc(v[q], __ldg(ay.post + qq)) : mk((T)0, (T)0);
     }
-    chirp_conv<L>(v, row, t, tw, ay.bhat_adj);
+    chirp_conv<L>(v, row, t, tw, ay.bhat, d.adjoint);
     if (live) {
       C* dst = Tb + ((int64_t)b * cT + c) * tplane + (int64_t)p * d.ny;
 #pragma unroll
@@ -273,15 +346,15 @@ k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, 
 }
 
 // Adjoint x pass: columns n of the T planes -> input-grid gradient rows [ny][nx].
-// VEC: g_Ex = C_x^H(A) + (x/z) C_x^H(Z), g_Ey = C_x^H(B) + (y/z) C_x^H(Z).
+// VEC: g_Ex = C_x^H(A) + (x/z) C_x^H(Z), g_Ey = C_x^H(B) + (y/z) C_x^H(Z); (1/z) C_x^H(Z) is
+// transformed first and kept in the thread's stash.
 // grid: (ceil(ny / ROWS), nbatch).
 template <typename T, int L, bool VEC>
-__global__ void __launch_bounds__(czt_rows<L, sizeof(cplx<T>)>() * (L / 16),
-                                  czt_min_blocks<czt_rows<L, sizeof(cplx<T>)>() * (L / 16)>())
+__global__ void XL_CZT_BOUNDS(T, L, VEC)
 k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d, Axis<cplx<T>> ax,
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
-  constexpr int ROWS = czt_rows<L, sizeof(C)>();
+  constexpr int ROWS = czt_rows<L, sizeof(C), VEC>();
   constexpr int TT = L / 16;
   constexpr int SR = rpitch(L);
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -294,22 +367,27 @@ k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d
   const int cT = VEC ? 3 : 1, cout = VEC ? 2 : 1;
   const int64_t tplane = (int64_t)d.mx * d.ny, plane = (int64_t)d.nx * d.ny;
   C* row = sm + team * SR;
-  C zz[16];
+  Stash<C, TT, czt_stash_smem<L, sizeof(C), VEC>()> zz;
+  zz.init(sm + (ROWS + team) * SR, t);
+  const Coord<T> xm(d.x0, d.dx, t, TT);
+  const T yn = (T)(d.y0 + n * d.dy);
   if constexpr (VEC) {
-    load_transposed<L, ROWS>(zz, sm, team, t, d.mx, Tb + ((int64_t)b * 3 + 2) * tplane, d.ny, n0, d.ny);
+    const T iz = (T)(1.0 / czt_z(d));
+    C v[16];
+    load_transposed<L, ROWS>(v, sm, team, t, d.mx, Tb + ((int64_t)b * 3 + 2) * tplane, d.ny, n0, d.ny);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int pp = t + q * TT;
-      zz[q] = pp < d.mx ? cmulc(zz[q], __ldg(ax.post + pp)) : mk((T)0, (T)0);
+      v[q] = pp < d.mx ? cmulc(v[q], __ldg(ax.post + pp)) : mk((T)0, (T)0);
     }
-    chirp_conv<L>(zz, row, t, tw, ax.bhat_adj);
+    chirp_conv<L>(v, row, t, tw, ax.bhat, d.adjoint);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int m = t + q * TT;
-      zz[q] = m < d.nx ? cmulc(zz[q], __ldg(ax.pre + m)) : mk((T)0, (T)0);
+      zz.set(q, m < d.nx ? cscale(cmulc(v[q], __ldg(ax.pre + m)), iz) : mk((T)0, (T)0));
     }
   }
-#pragma unroll 1
+#pragma unroll
   for (int c = 0; c < cout; ++c) {
     C v[16];
     load_transposed<L, ROWS>(v, sm, team, t, d.mx, Tb + ((int64_t)b * cT + c) * tplane, d.ny, n0, d.ny);
@@ -318,20 +396,15 @@ k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d
       const int pp = t + q * TT;
       v[q] = pp < d.mx ? cmulc(v[q], __ldg(ax.post + pp)) : mk((T)0, (T)0);
     }
-    chirp_conv<L>(v, row, t, tw, ax.bhat_adj);
+    chirp_conv<L>(v, row, t, tw, ax.bhat, d.adjoint);
     if (live) {
       C* dst = gin + ((int64_t)b * d.in_planes + c) * plane + (int64_t)n * d.nx;
-      const T iz = VEC ? (T)(1.0 / czt_z(d)) : (T)0;
-      const T yn = (T)(d.y0 + n * d.dy);
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int m = t + q * TT;
         if (m < d.nx) {
           C r = cmulc(v[q], __ldg(ax.pre + m));
-          if constexpr (VEC) {
-            const T w = c == 0 ? (T)(d.x0 + m * d.dx) : yn;
-            r = cadd(r, cscale(zz[q], w * iz));
-          }
+          if constexpr (VEC) r = cadd(r, cscale(zz.get(q), c == 0 ? xm.at(q) : yn));
           dst[m] = r;
         }
       }
@@ -339,9 +412,9 @@ k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d
   }
 }
 
-// Chirp tables for both axes. Entries: x axis then y axis, each pre[N] | post[M] | b_fwd[L] |
-// b_adj[L] (the b arrays are transformed afterwards by k_czt_bhat). Double-precision phases,
-// reduced modulo 2 pi, rounded once.
+// Chirp tables for both axes. Entries: x axis then y axis, each pre[N] | post[M] | b[L] (b is
+// transformed afterwards by k_czt_bhat). Double-precision phases, reduced modulo 2 pi, rounded
+// once.
 struct CztTabArgs {
   int nx, ny, mx, my, Lx, Ly;
   double x0, dx, y0, dy, xo0, dxo, yo0, dyo, k, lambda;
@@ -356,8 +429,8 @@ template <typename T>
 __global__ void k_czt_tables(cplx<T>* __restrict__ tab, CztTabArgs a) {
   typedef cplx<T> C;
   const double z = a.zdev ? *a.zdev : a.zval;
-  const int64_t tx = (int64_t)a.nx + a.mx + 2 * (int64_t)a.Lx;
-  const int64_t ty = (int64_t)a.ny + a.my + 2 * (int64_t)a.Ly;
+  const int64_t tx = (int64_t)a.nx + a.mx + a.Lx;
+  const int64_t ty = (int64_t)a.ny + a.my + a.Ly;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tx + ty;
        i += (int64_t)gridDim.x * blockDim.x) {
     const bool isy = i >= tx;
@@ -381,14 +454,11 @@ __global__ void k_czt_tables(cplx<T>* __restrict__ tab, CztTabArgs a) {
         ph += red2pi(a.k * z) - 0.5 * kPi;
         amp_re = a.dx * a.dy / (a.lambda * z);
       }
-    } else {  // b placed mod L: forward for -(N-1) <= jj <= M-1, adjoint (conj) for -(M-1) <= jj <= N-1
-      const bool adj = j >= N + M + L;
-      const int64_t idx = j - N - M - (adj ? L : 0);
-      const int64_t jj = idx <= (adj ? N - 1 : M - 1) ? idx : idx - L;
-      const int64_t lo = adj ? -(M - 1) : -(N - 1);
-      zero = jj < lo;
+    } else {  // b placed mod L for -(N-1) <= jj <= M-1
+      const int64_t idx = j - N - M;
+      const int64_t jj = idx <= M - 1 ? idx : idx - L;
+      zero = jj < -(N - 1);
       ph = red2pi(0.5 * alpha * (double)jj * (double)jj);
-      if (adj) ph = -ph;
     }
     C v;
     if (zero) {
