@@ -79,22 +79,6 @@ template <int L, int CS, bool VEC> __host__ __device__ constexpr int czt_min_blo
   return by_smem < 1 ? 1 : (by_smem < by_threads ? by_smem : by_threads);
 }
 
-// Thread-private 16-element stash (element q of thread t is row element t + q L/16), in a shared
-// memory row or in registers.
-template <typename C, int TT, bool SMEM> struct Stash {
-  C r[16];
-  __device__ __forceinline__ void init(C*, int) {}
-  __device__ __forceinline__ C get(int q) const { return r[q]; }
-  __device__ __forceinline__ void set(int q, C v) { r[q] = v; }
-};
-template <typename C, int TT> struct Stash<C, TT, true> {
-  C* p;
-  int t;
-  __device__ __forceinline__ void init(C* row, int tt) { p = row; t = tt; }
-  __device__ __forceinline__ C get(int q) const { return p[spad(t + q * TT)]; }
-  __device__ __forceinline__ void set(int q, C v) { p[spad(t + q * TT)] = v; }
-};
-
 // Convolution of the register row with the chirp kernel: FFT, multiply by bhat (conj(bhat) for
 // the adjoint), inverse FFT. The direction is a runtime value on purpose: the two multiply
 // loops become separate basic blocks, which keeps the compiler from interleaving the inverse

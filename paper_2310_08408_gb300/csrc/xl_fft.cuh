@@ -226,6 +226,22 @@ __device__ __forceinline__ void load_rows_transposed(C* sm, int n_in, int n_fill
     }
 }
 
+// Thread-private 16-element stash (element q of thread t is row element t + q L/16), in a shared
+// memory row or in registers.
+template <typename C, int TT, bool SMEM> struct Stash {
+  C r[16];
+  __device__ __forceinline__ void init(C*, int) {}
+  __device__ __forceinline__ C get(int q) const { return r[q]; }
+  __device__ __forceinline__ void set(int q, C v) { r[q] = v; }
+};
+template <typename C, int TT> struct Stash<C, TT, true> {
+  C* p;
+  int t;
+  __device__ __forceinline__ void init(C* row, int tt) { p = row; t = tt; }
+  __device__ __forceinline__ C get(int q) const { return p[spad(t + q * TT)]; }
+  __device__ __forceinline__ void set(int q, C v) { p[spad(t + q * TT)] = v; }
+};
+
 // Full length-L transform of one row held by a team (see the file comment for the layout).
 // sm: the team's padded shared-memory row (srow(L) elements).
 // The barrier after the register-only first stage orders its shared-memory writes after every

@@ -40,7 +40,11 @@ template <typename T, int LY, int MODE>
 xl_status pass2_LM(void* Tb, const void* Ub, const void* Hq, double* dz, const P2Args& a, int nb,
                    cudaStream_t s) {
   constexpr int ROWS = rows_cols<LY>();
-  const size_t sm = (size_t)p2_rows_per_team<MODE>() * ROWS * srow(LY) * sizeof(cplx<T>);
+  const size_t sm = (size_t)p2_rows_per_team<T, LY, MODE>() * ROWS * srow(LY) * sizeof(cplx<T>);
+  if (sm > (size_t)227 * 1024)
+    return fail(XL_ERR_UNSUPPORTED,
+                "vectorial RS: a column of this length needs more shared memory than an SM has "
+                "(complex128 with nx = 4096)");
   const void* tw;
   XL_TRY(twiddles(LY, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
   XL_TRY(smem_attr((const void*)k_rs_pass2<T, LY, MODE>, sm));

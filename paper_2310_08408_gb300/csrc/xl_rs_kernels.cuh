@@ -41,10 +41,11 @@ template <int L, int CS> __host__ __device__ constexpr int rows_p3() {
   return CS == 8 ? (L >= 4096 ? 2 : ((4096 / L) > 4 ? 4096 / L : 4))
                  : (L >= 8192 ? 1 : ((4096 / L) > 2 ? 4096 / L : 2));
 }
-// Minimum resident blocks the transposing kernels ask the register allocator for (two blocks of
-// 512 threads, or one of 1024).
-template <int THREADS> __host__ __device__ constexpr int min_blocks_1024() {
-  return (1024 / THREADS) > 1 ? 1024 / THREADS : 1;
+// Minimum resident blocks the transposing kernels ask the register allocator for: 1024 threads
+// an SM for complex64 (64 registers a thread), 512 for complex128 (128 registers: an element
+// takes four).
+template <int THREADS, int CS> __host__ __device__ constexpr int min_blocks_rows() {
+  return ((CS == 8 ? 1024 : 512) / THREADS) > 1 ? (CS == 8 ? 1024 : 512) / THREADS : 1;
 }
 template <int L> __host__ __device__ constexpr int rows_cols() { return (4096 / L) > 1 ? 4096 / L : 1; }
 
@@ -66,7 +67,7 @@ __device__ __forceinline__ C spec_at(const C* __restrict__ Hk, int kx, int ky, i
 // Plane p of the input maps to plane (p / cin) * cT + (p % cin) of the T buffer.
 template <typename T, int LX>
 __global__ void __launch_bounds__(rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16),
-                                  min_blocks_1024<rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16)>())
+                                  min_blocks_rows<rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16), sizeof(cplx<T>)>())
 k_rs_pass1(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, int nx, int ny, int cin,
            int cT, const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
@@ -97,7 +98,7 @@ k_rs_pass1(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, int nx, int
 // Plane p of the output maps to plane (p / cout) * cT + (p % cout) of T.
 template <typename T, int LX>
 __global__ void __launch_bounds__(rows_p3<LX, sizeof(cplx<T>)>() * (LX / 16),
-                                  min_blocks_1024<rows_p3<LX, sizeof(cplx<T>)>() * (LX / 16)>())
+                                  min_blocks_rows<rows_p3<LX, sizeof(cplx<T>)>() * (LX / 16), sizeof(cplx<T>)>())
 k_rs_pass3(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, int nx, int ny, int cout,
            int cT, const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
@@ -169,6 +170,12 @@ __device__ __forceinline__ C spec_row(const C* __restrict__ hrow, int q, int t, 
   return h;
 }
 
+// Block-scope memory fence placed after a transform: memory operations are not moved across
+// it, so the compiler cannot pull the next transform's loads and stores (and the registers they
+// hold) into this one. In the vectorial forward pass, five transforms in one block otherwise
+// spilled 424 bytes a thread at 128 registers.
+__device__ __forceinline__ void transform_fence() { __threadfence_block(); }
+
 // Compiler-only memory fence: keeps the spectrum loads of the multiply loops in groups of four
 // (without it all 16-32 loads are hoisted ahead of the arithmetic and the registers spill).
 #define XL_GROUP_FENCE(q) \
@@ -203,18 +210,30 @@ __device__ __forceinline__ double block_sum(double v, double* sbuf) {
 template <int MODE> __host__ __device__ constexpr int p2_min_blocks() {
   return MODE == P2_RS ? 4 : (MODE == P2_RS_BWD ? 3 : 2);
 }
-// Shared-memory rows per team of each mode (VRS modes keep the Ez spectrum in a second row).
-template <int MODE> __host__ __device__ constexpr int p2_rows_per_team() {
-  return (MODE == P2_VRS || MODE == P2_VRS_BWD) ? 2 : 1;
+// Shared-memory rows per team of each mode. VRS modes keep the Ez or Gz spectrum in a second
+// row; the adjoints with a distance gradient park U's column spectrum (times the dz spectrum for
+// the scalar adjoint) in one more row when it fits in an SM's shared memory (in registers
+// otherwise), so that one 16-element array is live per transform.
+template <typename T, int LY, int MODE> __host__ __device__ constexpr bool p2_ustash_smem() {
+  return (MODE == P2_RS_BWD || MODE == P2_VRS_BWD) &&
+         (size_t)(MODE == P2_RS_BWD ? 2 : 3) * rows_cols<LY>() * srow(LY) * sizeof(cplx<T>) <=
+             (size_t)227 * 1024;
+}
+template <typename T, int LY, int MODE> __host__ __device__ constexpr int p2_rows_per_team() {
+  return (MODE == P2_VRS || MODE == P2_VRS_BWD ? 2 : 1) + (p2_ustash_smem<T, LY, MODE>() ? 1 : 0);
 }
 
 // grid: (ceil(LX / ROWS), nbatch). Hq: spectra [slots][nx+1][ny+1].
 // dz_part: [nbatch][gridDim.x] partial sums, reduced later in fixed order.
+// Resident blocks of a pass-2 launch the register budget aims at (halved for complex128).
+template <typename T, int LY, int MODE> __host__ __device__ constexpr int p2_launch_min_blocks() {
+  return (p2_min_blocks<MODE>() * 256 / (int)(sizeof(T) / 4)) / (rows_cols<LY>() * (LY / 16)) > 0
+             ? (p2_min_blocks<MODE>() * 256 / (int)(sizeof(T) / 4)) / (rows_cols<LY>() * (LY / 16))
+             : 1;
+}
+
 template <typename T, int LY, int MODE>
-__global__ void __launch_bounds__(rows_cols<LY>() * (LY / 16),
-                                  (p2_min_blocks<MODE>() * 256) / (rows_cols<LY>() * (LY / 16)) > 0
-                                      ? (p2_min_blocks<MODE>() * 256) / (rows_cols<LY>() * (LY / 16))
-                                      : 1)
+__global__ void __launch_bounds__(rows_cols<LY>() * (LY / 16), p2_launch_min_blocks<T, LY, MODE>())
 k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<T>* __restrict__ Hq,
            double* __restrict__ dz_part, P2Args a, const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
@@ -258,6 +277,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
     const C *hz = H(KH), *hx = H(KHX), *hy = H(KHY);
     load_col(v, T0, t, TT);
     team_fft<LY, -1>(v, row, t, tw);
+    transform_fence();
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       zr[spad(t + q * TT)] = cmul(v[q], spec_row(hx, q, t, TT, flipx, true, false));
@@ -265,9 +285,11 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
       XL_GROUP_FENCE(q);
     }
     team_fft<LY, +1>(v, row, t, tw);
+    transform_fence();
     if (live) store_col(v, T0, t, TT);
     load_col(v, T1, t, TT);
     team_fft<LY, -1>(v, row, t, tw);
+    transform_fence();
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int iz = spad(t + q * TT);
@@ -276,25 +298,37 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
       XL_GROUP_FENCE(q);
     }
     team_fft<LY, +1>(v, row, t, tw);
+    transform_fence();
     if (live) store_col(v, T1, t, TT);
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = zr[spad(t + q * TT)];
     team_fft<LY, +1>(v, row, t, tw);
+    transform_fence();
     if (live) store_col(v, T2, t, TT);
   } else if constexpr (MODE == P2_RS_BWD) {
-    load_col(v, T0, t, TT);
-    team_fft<LY, -1>(v, row, t, tw);
+    // With dz, U's column spectrum times the dz spectrum is formed first and parked (thread-
+    // private entries). The 16 products of a thread are summed in T, the rest of the sum in
+    // double (FP64 runs at a small fraction of the FP32 rate).
+    Stash<C, TT, p2_ustash_smem<T, LY, MODE>()> ur;
+    ur.init(sm + ROWS * SR + team * SR, t);
     if (a.want_dz) {
-      C u[16];
       const C* U0 = Ub + (int64_t)b * a.cU * a.t_plane + (int64_t)kx * a.ny;
-      load_col(u, U0, t, TT);
-      team_fft<LY, -1>(u, row, t, tw);
+      load_col(v, U0, t, TT);
+      team_fft<LY, -1>(v, row, t, tw);
       const C* hd = H(KDH);
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        dz += (double)cdot_re(v[q], cmul(u[q], spec_row(hd, q, t, TT, flipx, false, false)));
+        ur.set(q, cmul(v[q], spec_row(hd, q, t, TT, flipx, false, false)));
         XL_GROUP_FENCE(q);
       }
+    }
+    load_col(v, T0, t, TT);
+    team_fft<LY, -1>(v, row, t, tw);
+    if (a.want_dz) {
+      T acc = (T)0;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) acc += cdot_re(v[q], ur.get(q));
+      dz = (double)acc;
     }
     if (a.want_field) {
       const C* h = H(KH);
@@ -304,32 +338,42 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
       if (live) store_col(v, T0, t, TT);
     }
   } else if constexpr (MODE == P2_VRS_BWD) {
-    // the spectrum of gz lives in a second shared-memory row of the team (thread-private entries)
+    // the spectrum of gz lives in a second shared-memory row of the team, U_c's column spectrum
+    // (with dz) in a third when it fits (thread-private entries). The plane loop is unrolled: as a
+    // runtime loop its invariant transform work was hoisted out of it and spilled.
     C* T1 = T0 + a.t_plane;
     C* T2 = T1 + a.t_plane;
     C* zr = sm + ROWS * SR + team * SR;
+    Stash<C, TT, p2_ustash_smem<T, LY, MODE>()> ur;
+    ur.init(sm + 2 * ROWS * SR + team * SR, t);
     load_col(v, T2, t, TT);
     team_fft<LY, -1>(v, row, t, tw);
 #pragma unroll
     for (int q = 0; q < 16; ++q) zr[spad(t + q * TT)] = v[q];
-#pragma unroll 1
+#pragma unroll
     for (int c = 0; c < 2; ++c) {
       C* Tc = c == 0 ? T0 : T1;
-      load_col(v, Tc, t, TT);
-      team_fft<LY, -1>(v, row, t, tw);
       const bool ox = c == 0, oy = c == 1;
       if (a.want_dz) {
-        C u[16];
         const C* Uc = Ub + ((int64_t)b * a.cU + c) * a.t_plane + (int64_t)kx * a.ny;
-        load_col(u, Uc, t, TT);
-        team_fft<LY, -1>(u, row, t, tw);
+        load_col(v, Uc, t, TT);
+        team_fft<LY, -1>(v, row, t, tw);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) ur.set(q, v[q]);
+      }
+      load_col(v, Tc, t, TT);
+      team_fft<LY, -1>(v, row, t, tw);
+      if (a.want_dz) {
         const C *hd = H(KDH), *ho = H(c == 0 ? KDHX : KDHY);
+        T acc = (T)0;
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          dz += (double)cdot_re(v[q], cmul(u[q], spec_row(hd, q, t, TT, flipx, false, false))) +
-                (double)cdot_re(zr[spad(t + q * TT)], cmul(u[q], spec_row(ho, q, t, TT, flipx, ox, oy)));
+          const C u = ur.get(q);
+          acc += cdot_re(v[q], cmul(u, spec_row(hd, q, t, TT, flipx, false, false))) +
+                 cdot_re(zr[spad(t + q * TT)], cmul(u, spec_row(ho, q, t, TT, flipx, ox, oy)));
           XL_GROUP_FENCE(q);
         }
+        dz += (double)acc;
       }
       if (a.want_field) {
         const C *hz = H(KH), *ho = H(c == 0 ? KHX : KHY);
@@ -531,7 +575,7 @@ __device__ __forceinline__ cplx<double> rs_sample<double>(int kind, int a, int b
 // mod LX; keep kx in [0, nx]; store transposed S[kind][kx][b].
 template <typename T, int LX>
 __global__ void __launch_bounds__(rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16),
-                                  min_blocks_1024<rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16)>())
+                                  min_blocks_rows<rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16), sizeof(cplx<T>)>())
 k_gen_pass_a(cplx<T>* __restrict__ S, GenArgs g, const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
   constexpr int ROWS = rows_transp<LX, sizeof(C)>();
