@@ -156,6 +156,7 @@ k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d,
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
   constexpr int ROWS = czt_rows<L, sizeof(C), VEC>();
+  static_assert(team_barriers_fit<L>(ROWS * (L / 16)), "too many teams for the named barriers");
   constexpr int TT = L / 16;
   constexpr int SR = rpitch(L);
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -205,6 +206,7 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
   constexpr int ROWS = czt_rows<L, sizeof(C), VEC>();
+  static_assert(team_barriers_fit<L>(ROWS * (L / 16)), "too many teams for the named barriers");
   constexpr int TT = L / 16;
   constexpr int SR = rpitch(L);
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -266,6 +268,7 @@ k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, 
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
   constexpr int ROWS = czt_rows<L, sizeof(C), VEC>();
+  static_assert(team_barriers_fit<L>(ROWS * (L / 16)), "too many teams for the named barriers");
   constexpr bool SMST = czt_stash_smem<L, sizeof(C), VEC>();
   constexpr int TT = L / 16;
   constexpr int SR = rpitch(L);
@@ -339,6 +342,7 @@ k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
   constexpr int ROWS = czt_rows<L, sizeof(C), VEC>();
+  static_assert(team_barriers_fit<L>(ROWS * (L / 16)), "too many teams for the named barriers");
   constexpr int TT = L / 16;
   constexpr int SR = rpitch(L);
   extern __shared__ __align__(16) unsigned char smraw[];

@@ -15,8 +15,11 @@
 // Shared-memory rows carry one pad element per 16 so that the stride-16 writes of the first
 // stage hit distinct banks.
 //
-// All teams of a block run the same instruction stream and meet at the same __syncthreads();
-// callers keep every thread on the FFT path (only global loads/stores are predicated).
+// A row is private to its team, so the barriers inside a transform are team barriers (a warp
+// barrier when the team fits in one warp, one named barrier per team otherwise): the teams of a
+// block run independently between the block-wide barriers that callers place around the
+// transposing loads and stores. Callers keep every thread on the FFT path (only global loads and
+// stores are predicated), and a block holds at most 15 teams of 64 or more threads.
 #pragma once
 
 #include "xl_common.cuh"
@@ -151,6 +154,21 @@ __device__ __forceinline__ void apply_twiddles(C* v, const C* __restrict__ col, 
   }
 }
 
+// Barrier of the team that owns a row (ids 1.. of the named barriers; 0 is __syncthreads).
+template <int L> __device__ __forceinline__ void team_sync() {
+  constexpr int TT = L / 16;
+  if constexpr (TT <= 32) {
+    __syncwarp();
+  } else {
+    const int id = 1 + (int)(threadIdx.x / TT);
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(TT) : "memory");
+  }
+}
+// Whether a block of `threads` threads fits the team barriers of length-L transforms.
+template <int L> __host__ __device__ constexpr bool team_barriers_fit(int threads) {
+  return L / 16 <= 32 || threads / (L / 16) <= 15;
+}
+
 // Stage S (>= 1) of the transform; Ns = 16^S for the radix-16 prefix.
 template <int L, int DIR, int S, typename C>
 __device__ __forceinline__ void fft_stage(C (&v)[16], C* sm, int t, const C* __restrict__ tw) {
@@ -160,12 +178,12 @@ __device__ __forceinline__ void fft_stage(C (&v)[16], C* sm, int t, const C* __r
   constexpr int B = 16 / R;
   constexpr int Ns = 1 << (4 * S);
   constexpr int TT = Sh::TT;
-  __syncthreads();
+  team_sync<L>();
 #pragma unroll
   for (int b = 0; b < B; ++b)
 #pragma unroll
     for (int r = 0; r < R; ++r) v[b + B * r] = sm[spad(t + (b + B * r) * TT)];
-  if constexpr (!last) __syncthreads();
+  if constexpr (!last) team_sync<L>();
 #pragma unroll
   for (int b = 0; b < B; ++b) {
     const int j = t + b * TT;
@@ -244,13 +262,13 @@ template <typename C, int TT> struct Stash<C, TT, true> {
 
 // Full length-L transform of one row held by a team (see the file comment for the layout).
 // sm: the team's padded shared-memory row (srow(L) elements).
-// The barrier after the register-only first stage orders its shared-memory writes after every
-// read of the row by a previous transform (a forward transform's last stage reads the row just
+// The team barrier after the register-only first stage orders its shared-memory writes after
+// every read of the row by a previous transform (a forward transform's last stage reads the row just
 // before a caller multiplies and runs the inverse transform on the same row).
 template <int L, int DIR, typename C>
 __device__ __forceinline__ void team_fft(C (&v)[16], C* sm, int t, const C* __restrict__ tw) {
   dft16s<DIR, 1>(v);  // stage 0: radix 16, Ns = 1, no twiddles
-  __syncthreads();
+  team_sync<L>();
 #pragma unroll
   for (int r = 0; r < 16; ++r) sm[spad(t * 16 + r)] = v[r];
   fft_stage<L, DIR, 1>(v, sm, t, tw);

@@ -205,9 +205,11 @@ xl_status run_op(Op op, const void* in, const void* u_in, void* out, double* g_z
     int mode = op == OP_RS_FWD ? P2_RS : op == OP_VRS_FWD ? P2_VRS : op == OP_RS_BWD ? P2_RS_BWD
                                                                                     : P2_VRS_BWD;
     XL_TRY(rs_pass2<T>(mode, Tb, Ub, Hq, dzp, a, nb, s));
-    if (want_dz) XL_TRY(launch_reduce<T>(dzp, p2blocks, g_z + b0, nb, s));
+    // the distance partials are summed by pass 3 when it runs, else by their own launch
+    if (want_dz && !want_field) XL_TRY(launch_reduce<T>(dzp, p2blocks, g_z + b0, nb, s));
     if (want_field)
-      XL_TRY(rs_pass3<T>(Tb, dst + (size_t)b0 * cout * plane * cs, nx, ny, cout, cT, nb * cout, s));
+      XL_TRY(rs_pass3<T>(Tb, dst + (size_t)b0 * cout * plane * cs, nx, ny, cout, cT, nb * cout, s,
+                         want_dz ? DzReduce{dzp, p2blocks, g_z + b0} : DzReduce{nullptr, 0, nullptr}));
     b0 += nb;
   }
   return XL_OK;

@@ -22,7 +22,8 @@ xl_status pass1_L(const void* in, void* Tb, int nx, int ny, int cin, int cT, int
 }
 
 template <typename T, int LX>
-xl_status pass3_L(const void* Tb, void* out, int nx, int ny, int cout, int cT, int np, cudaStream_t s) {
+xl_status pass3_L(const void* Tb, void* out, int nx, int ny, int cout, int cT, int np, cudaStream_t s,
+                  DzReduce red) {
   constexpr int ROWS = rows_p3<LX, sizeof(cplx<T>)>();
   const size_t sm = (size_t)ROWS * rpitch(LX) * sizeof(cplx<T>);
   const void* tw;
@@ -31,7 +32,7 @@ xl_status pass3_L(const void* Tb, void* out, int nx, int ny, int cout, int cT, i
   dim3 grid((ny + ROWS - 1) / ROWS, np);
   LaunchScope ls("rs_pass3<" + std::to_string(LX) + ">", s);
   k_rs_pass3<T, LX><<<grid, ROWS * (LX / 16), sm, s>>>(
-      (const cplx<T>*)Tb, (cplx<T>*)out, nx, ny, cout, cT, (const cplx<T>*)tw);
+      (const cplx<T>*)Tb, (cplx<T>*)out, nx, ny, cout, cT, (const cplx<T>*)tw, red);
   XL_CUDA_TRY(cudaGetLastError());
   return XL_OK;
 }
@@ -133,8 +134,8 @@ xl_status rs_pass1<XL_REAL>(const void* in, void* Tb, int nx, int ny, int cin, i
 
 template <>
 xl_status rs_pass3<XL_REAL>(const void* Tb, void* out, int nx, int ny, int cout, int cT, int np,
-                            cudaStream_t s) {
-#define C3(L) pass3_L<XL_REAL, L>(Tb, out, nx, ny, cout, cT, np, s)
+                            cudaStream_t s, DzReduce red) {
+#define C3(L) pass3_L<XL_REAL, L>(Tb, out, nx, ny, cout, cT, np, s, red)
   XL_SWITCH_L(2 * nx, C3)
 #undef C3
   return fail(XL_ERR_UNSUPPORTED, "rs_pass3: unsupported nx");

@@ -72,6 +72,7 @@ k_rs_pass1(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, int nx, int
            int cT, const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
   constexpr int ROWS = rows_transp<LX, sizeof(C)>();
+  static_assert(team_barriers_fit<LX>(ROWS * (LX / 16)), "too many teams for the named barriers");
   constexpr int TT = LX / 16;
   constexpr int P = rpitch(LX);
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -94,15 +95,39 @@ k_rs_pass1(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, int nx, int
   store_rows_transposed<ROWS, P>(sm, LX, dst, ny, y0, ny);
 }
 
+// Block-wide sum of a double (one value per thread) -> thread 0; sbuf holds 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sbuf) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sbuf[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) s += sbuf[i];
+  return s;
+}
+
+// Optional fixed-order reduction of the pass-2 distance partials, done by the blocks of
+// column 0 of pass 3 (which runs right after pass 2 on the same stream):
+// out[b] = sum_i part[b * n + i] for the batch element b of the block's plane.
+struct DzReduce {
+  const double* part;
+  int n;
+  double* out;
+};
+
 // Pass 3: inverse row FFT from T[kx][y] into planes [ny][nx] (crop to x < nx).
 // Plane p of the output maps to plane (p / cout) * cT + (p % cout) of T.
 template <typename T, int LX>
 __global__ void __launch_bounds__(rows_p3<LX, sizeof(cplx<T>)>() * (LX / 16),
                                   min_blocks_rows<rows_p3<LX, sizeof(cplx<T>)>() * (LX / 16), sizeof(cplx<T>)>())
 k_rs_pass3(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, int nx, int ny, int cout,
-           int cT, const cplx<T>* __restrict__ tw) {
+           int cT, const cplx<T>* __restrict__ tw, DzReduce red) {
   typedef cplx<T> C;
   constexpr int ROWS = rows_p3<LX, sizeof(C)>();
+  static_assert(team_barriers_fit<LX>(ROWS * (LX / 16)), "too many teams for the named barriers");
   constexpr int TT = LX / 16;
   constexpr int P = rpitch(LX);
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -110,6 +135,14 @@ k_rs_pass3(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, int nx, in
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
   const int p = blockIdx.y;
   const int y0 = blockIdx.x * ROWS;
+  if (red.part != nullptr && blockIdx.x == 0 && p % cout == 0) {
+    __shared__ double rbuf[32];
+    const int b = p / cout;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < red.n; i += blockDim.x) acc += red.part[(int64_t)b * red.n + i];
+    acc = block_sum(acc, rbuf);
+    if (threadIdx.x == 0) red.out[b] = acc;
+  }
   const C* src = Tb + ((int64_t)(p / cout) * cT + (p % cout)) * (int64_t)LX * ny;
   load_rows_transposed<ROWS, P>(sm, LX, LX, src, ny, y0, ny);
   __syncthreads();
@@ -192,20 +225,6 @@ __device__ __forceinline__ void store_col(const C (&v)[16], C* __restrict__ dst,
   for (int q = 0; q < 8; ++q) dst[t + q * TT] = v[q];
 }
 
-// Block-wide sum of a double (one value per thread) -> thread 0; sbuf holds 32 doubles.
-__device__ __forceinline__ double block_sum(double v, double* sbuf) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) sbuf[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) s += sbuf[i];
-  return s;
-}
-
 // Blocks per SM the register budget of each pass-2 mode aims at (256-thread blocks).
 template <int MODE> __host__ __device__ constexpr int p2_min_blocks() {
   return MODE == P2_RS ? 4 : (MODE == P2_RS_BWD ? 3 : 2);
@@ -238,6 +257,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
            double* __restrict__ dz_part, P2Args a, const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
   constexpr int ROWS = rows_cols<LY>();
+  static_assert(team_barriers_fit<LY>(ROWS * (LY / 16)), "too many teams for the named barriers");
   constexpr int TT = LY / 16;
   constexpr int SR = srow(LY);
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -579,6 +599,7 @@ __global__ void __launch_bounds__(rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16)
 k_gen_pass_a(cplx<T>* __restrict__ S, GenArgs g, const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
   constexpr int ROWS = rows_transp<LX, sizeof(C)>();
+  static_assert(team_barriers_fit<LX>(ROWS * (LX / 16)), "too many teams for the named barriers");
   constexpr int TT = LX / 16;
   constexpr int P = rpitch(LX);
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -616,6 +637,7 @@ k_gen_pass_b(const cplx<T>* __restrict__ S, cplx<T>* __restrict__ Hq, GenArgs g,
              const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
   constexpr int ROWS = rows_cols<LY>();
+  static_assert(team_barriers_fit<LY>(ROWS * (LY / 16)), "too many teams for the named barriers");
   constexpr int TT = LY / 16;
   constexpr int SR = srow(LY);
   extern __shared__ __align__(16) unsigned char smraw[];

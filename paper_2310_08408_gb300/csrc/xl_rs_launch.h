@@ -11,10 +11,11 @@ namespace xl {
 template <typename T>
 xl_status rs_pass1(const void* in, void* Tb, int nx, int ny, int cin, int cT, int nplanes,
                    cudaStream_t s);
-// pass 3: T -> nplanes output planes (plane map p -> (p / cout) * cT + p % cout)
+// pass 3: T -> nplanes output planes (plane map p -> (p / cout) * cT + p % cout); optionally
+// also reduces the pass-2 distance partials (red.part non-null)
 template <typename T>
 xl_status rs_pass3(const void* Tb, void* out, int nx, int ny, int cout, int cT, int nplanes,
-                   cudaStream_t s);
+                   cudaStream_t s, DzReduce red = DzReduce{nullptr, 0, nullptr});
 // pass 2 over nbatch elements; dz_part gets nbatch * rs_pass2_blocks() partials
 template <typename T>
 xl_status rs_pass2(int mode, void* Tb, const void* Ub, const void* Hq, double* dz_part,

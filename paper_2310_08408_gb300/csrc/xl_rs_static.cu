@@ -149,7 +149,7 @@ xl_status run_static(const float2* in, float2* out, int32_t batch, const xl_grid
         T, nullptr, Hq, nullptr, pa, twy);
     XL_CUDA_TRY(cudaGetLastError());
     k_rs_pass3<float, LX><<<dim3((ny + R3 - 1) / R3, 1), R3 * (LX / 16), sm3, s>>>(
-        T, out + b * plane, nx, ny, 1, 1, twx);
+        T, out + b * plane, nx, ny, 1, 1, twx, DzReduce{nullptr, 0, nullptr});
     XL_CUDA_TRY(cudaGetLastError());
   }
   return XL_OK;
