@@ -178,15 +178,17 @@ class GpuStep:
         self.GC = torch.from_numpy(inputs.random_unit(8, (1, M, M)).astype(np.complex64)).to(dev).expand(B, M, M).contiguous()
         self.A = torch.empty_like(U_dev)
         self.C = torch.empty((B, M, M), dtype=U_dev.dtype, device=dev)
+        # the forward RS keeps the row transforms of U for the adjoint's distance gradient
+        self.S = xl.save_buffer(U_dev)
         self.props = 4 * B
 
     def __call__(self):
         xl = self.xl
-        xl.rs_propagate(self.U, self.g, LAM, self.zs, out=self.A)
+        xl.rs_propagate(self.U, self.g, LAM, self.zs, out=self.A, saved=self.S)
         xl.czt_propagate(self.U, self.g, self.w, LAM, self.zs, out=self.C)
         gc = xl.czt_propagate_backward(self.GC, self.g, self.w, LAM, self.zs)
-        ga, gz = xl.rs_propagate_backward(self.GA, self.U, self.g, LAM, self.zs, want_field=True,
-                                          want_dz=True)
+        ga, gz = xl.rs_propagate_backward(self.GA, None, self.g, LAM, self.zs, want_field=True,
+                                          want_dz=True, saved=self.S)
         self.gA, self.gC = ga, gc
         self.gz = gz
         return self.A, self.C, self.gz

@@ -28,17 +28,21 @@ class RSPropagate(torch.autograd.Function):
     @staticmethod
     def forward(ctx, u, z, grid, wavelength, phase_invariant=False):
         zz = _dev_z(z.detach(), u.shape[0])
-        ctx.save_for_backward(u, zz)
+        u = u.contiguous()
+        # a distance gradient needs the input's row transforms, which the forward keeps
+        saved = xl.save_buffer(u) if ctx.needs_input_grad[1] else u.new_empty(0)
+        ctx.save_for_backward(saved, zz)
         ctx.grid, ctx.wl, ctx.zshape, ctx.pinv = grid, wavelength, z.shape, phase_invariant
-        return xl.rs_propagate(u.contiguous(), grid, wavelength, zz)
+        return xl.rs_propagate(u, grid, wavelength, zz, saved=saved if saved.numel() else None)
 
     @staticmethod
     def backward(ctx, g):
-        u, zz = ctx.saved_tensors
+        saved, zz = ctx.saved_tensors
         need_u, need_z = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
-        g_in, g_z = xl.rs_propagate_backward(g.contiguous(), u if need_z else None, ctx.grid, ctx.wl,
-                                             zz, want_field=need_u, want_dz=need_z,
-                                             phase_invariant=ctx.pinv)
+        g_in, g_z = xl.rs_propagate_backward(g.contiguous(), None, ctx.grid, ctx.wl, zz,
+                                             want_field=need_u, want_dz=need_z,
+                                             phase_invariant=ctx.pinv,
+                                             saved=saved if need_z else None)
         if g_z is not None:
             g_z = g_z.reshape(-1).sum().reshape(ctx.zshape) if ctx.zshape.numel() == 1 else g_z.reshape(ctx.zshape)
         return g_in, g_z, None, None, None
@@ -50,17 +54,20 @@ class VRSPropagate(torch.autograd.Function):
     @staticmethod
     def forward(ctx, exy, z, grid, wavelength, phase_invariant=False):
         zz = _dev_z(z.detach(), exy.shape[0])
-        ctx.save_for_backward(exy, zz)
+        exy = exy.contiguous()
+        saved = xl.save_buffer(exy, 2) if ctx.needs_input_grad[1] else exy.new_empty(0)
+        ctx.save_for_backward(saved, zz)
         ctx.grid, ctx.wl, ctx.zshape, ctx.pinv = grid, wavelength, z.shape, phase_invariant
-        return xl.vrs_propagate(exy.contiguous(), grid, wavelength, zz)
+        return xl.vrs_propagate(exy, grid, wavelength, zz, saved=saved if saved.numel() else None)
 
     @staticmethod
     def backward(ctx, g):
-        exy, zz = ctx.saved_tensors
+        saved, zz = ctx.saved_tensors
         need_u, need_z = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
-        g_in, g_z = xl.vrs_propagate_backward(g.contiguous(), exy if need_z else None, ctx.grid,
-                                              ctx.wl, zz, want_field=need_u, want_dz=need_z,
-                                              phase_invariant=ctx.pinv)
+        g_in, g_z = xl.vrs_propagate_backward(g.contiguous(), None, ctx.grid, ctx.wl, zz,
+                                              want_field=need_u, want_dz=need_z,
+                                              phase_invariant=ctx.pinv,
+                                              saved=saved if need_z else None)
         if g_z is not None:
             g_z = g_z.reshape(-1).sum().reshape(ctx.zshape) if ctx.zshape.numel() == 1 else g_z.reshape(ctx.zshape)
         return g_in, g_z, None, None, None

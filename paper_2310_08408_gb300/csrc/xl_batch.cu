@@ -34,6 +34,7 @@ struct Group {
   void *src = nullptr, *a0 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *a4 = nullptr,
        *a5 = nullptr;
   void *g5 = nullptr, *g4 = nullptr, *g3 = nullptr, *g2 = nullptr, *g1 = nullptr, *g0 = nullptr;
+  void *s1 = nullptr, *s2 = nullptr;  // row transforms the RS / VRS forwards keep for the adjoints
   void *phi1 = nullptr, *phi2 = nullptr, *gphi1 = nullptr, *gphi2 = nullptr;  // real T [count][n][n]
   void *m1 = nullptr, *v1 = nullptr, *m2 = nullptr, *v2 = nullptr;            // Adam moments (real T)
   double *p1 = nullptr, *p2 = nullptr, *pl = nullptr;  // element params [count][n_el][4]
@@ -133,7 +134,8 @@ xl_status group_alloc(xl_batch* b, Group& G, const double* init, uint64_t seed, 
       {&G.a2, cnt * 2 * plane * cs},  {&G.a3, cnt * 3 * plane * cs}, {&G.a4, cnt * 3 * plane * cs},
       {&G.a5, cnt * 3 * cam * cs},    {&G.g5, cnt * 3 * cam * cs},   {&G.g4, cnt * 3 * plane * cs},
       {&G.g3, cnt * 3 * plane * cs},  {&G.g2, cnt * 2 * plane * cs}, {&G.g1, cnt * plane * cs},
-      {&G.g0, cnt * plane * cs},      {&G.phi1, cnt * plane * rs},   {&G.phi2, cnt * plane * rs},
+      {&G.g0, cnt * plane * cs},      {&G.s1, cnt * 2 * plane * cs}, {&G.s2, cnt * 4 * plane * cs},
+      {&G.phi1, cnt * plane * rs},    {&G.phi2, cnt * plane * rs},
       {&G.gphi1, cnt * plane * rs},   {&G.gphi2, cnt * plane * rs},  {&G.m1, cnt * plane * rs},
       {&G.v1, cnt * plane * rs},      {&G.m2, cnt * plane * rs},     {&G.v2, cnt * plane * rs},
       {(void**)&G.p1, cnt * 4 * 8},   {(void**)&G.p2, cnt * 12 * 8}, {(void**)&G.pl, cnt * 4 * 8},
@@ -202,9 +204,9 @@ xl_status group_step(xl_batch* b, Group& G, cudaStream_t s) {
   xl_element e_lens[1] = {el(XL_LENS)};
   // forward
   XL_TRY(xl_apply_elements(G.src, G.a0, cnt, 1, g, lam, e_slm1, 1, G.p1, XL_Z_DEVICE, dt, s));
-  XL_TRY(xl_rs_propagate(G.a0, G.a1, cnt, g, lam, G.z1, XL_Z_DEVICE, dt, s));
+  XL_TRY(xl_rs_propagate_save(G.a0, G.a1, G.s1, cnt, g, lam, G.z1, XL_Z_DEVICE, dt, s));
   XL_TRY(xl_apply_elements(G.a1, G.a2, cnt, 1, g, lam, e_mid, 3, G.p2, XL_Z_DEVICE, dt, s));
-  XL_TRY(xl_vrs_propagate(G.a2, G.a3, cnt, g, lam, G.z2, XL_Z_DEVICE, dt, s));
+  XL_TRY(xl_vrs_propagate_save(G.a2, G.a3, G.s2, cnt, g, lam, G.z2, XL_Z_DEVICE, dt, s));
   XL_TRY(xl_apply_elements(G.a3, G.a4, cnt, 3, g, lam, e_lens, 1, G.pl, XL_Z_DEVICE, dt, s));
   // the VCZT distance is the fixed focal length: host distances, cached chirp tables
   XL_TRY(xl_czt_propagate(G.a4, G.a5, cnt, 2, g, &win, lam, G.zf.data(), 0, dt, s));
@@ -215,13 +217,13 @@ xl_status group_step(xl_batch* b, Group& G, cudaStream_t s) {
   XL_TRY(xl_apply_elements_backward(G.g4, G.a3, G.g3, cnt, 3, g, lam, e_lens, 1, G.pl, XL_Z_DEVICE,
                                     nullptr, nullptr, nullptr, dt, s));
   // the camera loss is invariant under a constant phase on every plane: drop the e^{ikz} term
-  XL_TRY(xl_vrs_propagate_backward(G.g3, G.a2, G.g2, G.gz2, cnt, g, lam, G.z2,
-                                   XL_Z_DEVICE | XL_PHASE_INVARIANT, dt, s));
+  XL_TRY(xl_vrs_propagate_backward_saved(G.g3, G.s2, G.g2, G.gz2, cnt, g, lam, G.z2,
+                                         XL_Z_DEVICE | XL_PHASE_INVARIANT, dt, s));
   void* gpx_mid[3] = {G.gphi2, nullptr, nullptr};
   XL_TRY(xl_apply_elements_backward(G.g2, G.a1, G.g1, cnt, 1, g, lam, e_mid, 3, G.p2, XL_Z_DEVICE,
                                     gpx_mid, nullptr, G.gp2, dt, s));
-  XL_TRY(xl_rs_propagate_backward(G.g1, G.a0, G.g0, G.gz1, cnt, g, lam, G.z1,
-                                  XL_Z_DEVICE | XL_PHASE_INVARIANT, dt, s));
+  XL_TRY(xl_rs_propagate_backward_saved(G.g1, G.s1, G.g0, G.gz1, cnt, g, lam, G.z1,
+                                        XL_Z_DEVICE | XL_PHASE_INVARIANT, dt, s));
   void* gpx1[1] = {G.gphi1};
   XL_TRY(xl_apply_elements_backward(G.g0, G.src, nullptr, cnt, 1, g, lam, e_slm1, 1, G.p1,
                                     XL_Z_DEVICE, gpx1, nullptr, nullptr, dt, s));

@@ -117,6 +117,8 @@ P2Args p2_args(const xl_grid* g, const Spectra& sp, int cT, int cU) {
   a.want_dz = 0;
   a.conj = 0;
   for (int i = 0; i < NKIND; ++i) a.slot[i] = sp.slot[i];
+  a.src = nullptr;
+  a.cS = 0;
   return a;
 }
 
@@ -138,10 +140,12 @@ int chunk_size(int64_t t_bytes_per_elem, int32_t remaining) {
 
 enum Op { OP_RS_FWD, OP_RS_BWD, OP_VRS_FWD, OP_VRS_BWD };
 
+// save_out (forward): receives the row transforms of the input planes, [batch][cin][2nx][ny];
+// save_in (adjoint): those row transforms in place of u_in for the distance gradient.
 template <typename T>
 xl_status run_op(Op op, const void* in, const void* u_in, void* out, double* g_z, int32_t batch,
                  const xl_grid* g, double wavelength, const double* z, int32_t flags, int32_t dtype,
-                 cudaStream_t s) {
+                 cudaStream_t s, void* save_out = nullptr, const void* save_in = nullptr) {
   const bool vec = (op == OP_VRS_FWD || op == OP_VRS_BWD);
   const bool bwd = (op == OP_RS_BWD || op == OP_VRS_BWD);
   const bool want_field = !bwd || out != nullptr;
@@ -168,11 +172,12 @@ xl_status run_op(Op op, const void* in, const void* u_in, void* out, double* g_z
   const int cout = op == OP_VRS_FWD ? 3 : (op == OP_VRS_BWD ? 2 : 1);
   const int p2blocks = rs_pass2_blocks<T>(nx, ny);
   const bool zdev = (flags & XL_Z_DEVICE) != 0;
-  const int64_t elem_ws = (int64_t)(cT + cU) * t_plane * cs;
+  const int cUw = save_in ? 0 : cU;  // U planes computed into the workspace
+  const int64_t elem_ws = (int64_t)(cT + cUw) * t_plane * cs;
   const int chunk_max = zdev ? 1 : chunk_size(elem_ws, batch);
   // workspace: T (chunk * cT planes) | U (chunk * cU planes) | dz partials | [S | Hq] (device z)
   const size_t t_bytes = (size_t)chunk_max * cT * t_plane * cs;
-  const size_t u_bytes = (size_t)chunk_max * cU * t_plane * cs;
+  const size_t u_bytes = (size_t)chunk_max * cUw * t_plane * cs;
   const size_t dz_bytes = want_dz ? (size_t)chunk_max * p2blocks * sizeof(double) : 0;
   const size_t s_bytes = zdev ? (size_t)sp.count * (nx + 1) * ny * cs : 0;
   const size_t hq_bytes = zdev ? (size_t)sp.count * (nx + 1) * (ny + 1) * cs : 0;
@@ -196,15 +201,28 @@ xl_status run_op(Op op, const void* in, const void* u_in, void* out, double* g_z
       while (nb < chunk_max && b0 + nb < batch && z[b0 + nb] == z[b0]) ++nb;
     const void* Hq = nullptr;
     XL_TRY(get_spectra(g, wavelength, sp, dtype, z + b0, flags, dev_s, dev_hq, s, &Hq));
-    XL_TRY(rs_pass1<T>(src + (size_t)b0 * cin * plane * cs, Tb, nx, ny, cin, cT, nb * cin, s));
-    if (want_dz)
-      XL_TRY(rs_pass1<T>(usrc + (size_t)b0 * cU * plane * cs, Ub, nx, ny, cU, cU, nb * cU, s));
     P2Args a = p2_args(g, sp, cT, cU);
+    if (save_out) {
+      // the row transforms go to the caller's buffer, which pass 2 reads without overwriting
+      char* sv = (char*)save_out + (size_t)b0 * cin * t_plane * cs;
+      XL_TRY(rs_pass1<T>(src + (size_t)b0 * cin * plane * cs, sv, nx, ny, cin, cin, nb * cin, s));
+      a.src = sv;
+      a.cS = cin;
+    } else {
+      XL_TRY(rs_pass1<T>(src + (size_t)b0 * cin * plane * cs, Tb, nx, ny, cin, cT, nb * cin, s));
+    }
+    const void* Ucur = Ub;
+    if (want_dz) {
+      if (save_in)
+        Ucur = (const char*)save_in + (size_t)b0 * cU * t_plane * cs;
+      else
+        XL_TRY(rs_pass1<T>(usrc + (size_t)b0 * cU * plane * cs, Ub, nx, ny, cU, cU, nb * cU, s));
+    }
     a.want_field = want_field;
     a.want_dz = want_dz;
     int mode = op == OP_RS_FWD ? P2_RS : op == OP_VRS_FWD ? P2_VRS : op == OP_RS_BWD ? P2_RS_BWD
                                                                                     : P2_VRS_BWD;
-    XL_TRY(rs_pass2<T>(mode, Tb, Ub, Hq, dzp, a, nb, s));
+    XL_TRY(rs_pass2<T>(mode, Tb, Ucur, Hq, dzp, a, nb, s));
     // the distance partials are summed by pass 3 when it runs, else by their own launch
     if (want_dz && !want_field) XL_TRY(launch_reduce<T>(dzp, p2blocks, g_z + b0, nb, s));
     if (want_field)
@@ -215,21 +233,29 @@ xl_status run_op(Op op, const void* in, const void* u_in, void* out, double* g_z
   return XL_OK;
 }
 
+// u_in (adjoint) is the forward input, or with `saved` set the forward's saved row transforms.
 xl_status dispatch(Op op, const void* in, const void* u_in, void* out, double* g_z, int32_t batch,
                    const xl_grid* g, double wavelength, const double* z, int32_t flags,
-                   int32_t dtype, void* stream) {
+                   int32_t dtype, void* stream, void* save_out = nullptr, bool saved = false) {
   XL_TRY(check_grid(g, wavelength));
   XL_TRY(check_common(batch, z, flags, dtype));
   if (batch == 0) return XL_OK;
   const bool bwd = (op == OP_RS_BWD || op == OP_VRS_BWD);
   if (!in) return fail(XL_ERR_ARG, "input field is NULL");
   if (!bwd && !out) return fail(XL_ERR_ARG, "output field is NULL");
-  if (bwd && g_z && !u_in) return fail(XL_ERR_ARG, "g_z requested but the forward input is NULL");
+  if (bwd && g_z && !u_in)
+    return fail(XL_ERR_ARG, saved ? "g_z requested but the saved row transforms are NULL"
+                                   : "g_z requested but the forward input is NULL");
   if (!bwd && in == out) return fail(XL_ERR_ARG, "output may not alias the input");
   if (!bwd && (flags & XL_PHASE_INVARIANT)) return fail(XL_ERR_ARG, "XL_PHASE_INVARIANT applies to backward passes");
+  if (save_out && (save_out == in || save_out == out))
+    return fail(XL_ERR_ARG, "the save buffer may not alias the fields");
   cudaStream_t s = (cudaStream_t)stream;
-  if (dtype == XL_C128) return run_op<double>(op, in, u_in, out, g_z, batch, g, wavelength, z, flags, dtype, s);
-  return run_op<float>(op, in, u_in, out, g_z, batch, g, wavelength, z, flags, dtype, s);
+  const void* uf = saved ? nullptr : u_in;
+  const void* us = saved ? u_in : nullptr;
+  if (dtype == XL_C128)
+    return run_op<double>(op, in, uf, out, g_z, batch, g, wavelength, z, flags, dtype, s, save_out, us);
+  return run_op<float>(op, in, uf, out, g_z, batch, g, wavelength, z, flags, dtype, s, save_out, us);
 }
 
 }  // namespace
@@ -266,6 +292,38 @@ xl_status xl_vrs_propagate_backward(const void* g_exyz, const void* exy_in, void
                                     int32_t dtype, void* stream) {
   return dispatch(OP_VRS_BWD, g_exyz, exy_in, g_exy, g_z, batch, grid, wavelength, z, flags, dtype,
                   stream);
+}
+
+xl_status xl_rs_propagate_save(const void* u_in, void* u_out, void* saved, int32_t batch,
+                               const xl_grid* grid, double wavelength, const double* z,
+                               int32_t flags, int32_t dtype, void* stream) {
+  if (!saved) return fail(XL_ERR_ARG, "saved is NULL");
+  return dispatch(OP_RS_FWD, u_in, nullptr, u_out, nullptr, batch, grid, wavelength, z, flags,
+                  dtype, stream, saved);
+}
+
+xl_status xl_rs_propagate_backward_saved(const void* g_out, const void* saved, void* g_in,
+                                         double* g_z, int32_t batch, const xl_grid* grid,
+                                         double wavelength, const double* z, int32_t flags,
+                                         int32_t dtype, void* stream) {
+  return dispatch(OP_RS_BWD, g_out, saved, g_in, g_z, batch, grid, wavelength, z, flags, dtype,
+                  stream, nullptr, true);
+}
+
+xl_status xl_vrs_propagate_save(const void* exy_in, void* exyz_out, void* saved, int32_t batch,
+                                const xl_grid* grid, double wavelength, const double* z,
+                                int32_t flags, int32_t dtype, void* stream) {
+  if (!saved) return fail(XL_ERR_ARG, "saved is NULL");
+  return dispatch(OP_VRS_FWD, exy_in, nullptr, exyz_out, nullptr, batch, grid, wavelength, z,
+                  flags, dtype, stream, saved);
+}
+
+xl_status xl_vrs_propagate_backward_saved(const void* g_exyz, const void* saved, void* g_exy,
+                                          double* g_z, int32_t batch, const xl_grid* grid,
+                                          double wavelength, const double* z, int32_t flags,
+                                          int32_t dtype, void* stream) {
+  return dispatch(OP_VRS_BWD, g_exyz, saved, g_exy, g_z, batch, grid, wavelength, z, flags,
+                  dtype, stream, nullptr, true);
 }
 
 }  // extern "C"

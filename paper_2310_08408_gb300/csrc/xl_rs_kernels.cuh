@@ -179,6 +179,9 @@ struct P2Args {
   int want_dz;          // accumulate the dz partials
   int conj;             // P2_RS: use conj(H) (adjoint without dz)
   int slot[NKIND];      // spectrum kind -> slot in the Hq buffer (-1: absent)
+  const void* src;      // forward modes: read the row transforms from here ([b][cS][LX][ny])
+                        // instead of T, which then only receives the results (nullable)
+  int cS;               // planes per batch element of src
 };
 
 // Spectrum `Hk` along one kx row at ky = t + q TT (TT = LY / 16, ny = 8 TT): the quadrant row
@@ -277,8 +280,12 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
   C v[16];
   double dz = 0.0;
 
+  // forward modes may read their inputs from a separate, preserved buffer
+  const C* S0 = a.src ? reinterpret_cast<const C*>(a.src) + (int64_t)b * a.cS * a.t_plane +
+                            (int64_t)kx * a.ny
+                      : T0;
   if constexpr (MODE == P2_RS) {
-    load_col(v, T0, t, TT);
+    load_col(v, S0, t, TT);
     team_fft<LY, -1>(v, row, t, tw);
     const C* h = H(KH);
 #pragma unroll
@@ -295,7 +302,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
     C* T2 = T1 + a.t_plane;
     C* zr = sm + ROWS * SR + team * SR;
     const C *hz = H(KH), *hx = H(KHX), *hy = H(KHY);
-    load_col(v, T0, t, TT);
+    load_col(v, S0, t, TT);
     team_fft<LY, -1>(v, row, t, tw);
     transform_fence();
 #pragma unroll
@@ -307,7 +314,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
     team_fft<LY, +1>(v, row, t, tw);
     transform_fence();
     if (live) store_col(v, T0, t, TT);
-    load_col(v, T1, t, TT);
+    load_col(v, S0 + a.t_plane, t, TT);
     team_fft<LY, -1>(v, row, t, tw);
     transform_fence();
 #pragma unroll

@@ -99,6 +99,10 @@ SIGNATURES = {
     "xl_rs_propagate_static": ([_P, _P, _I, _GP, _D, _P, _P], _I),
     "xl_vrs_propagate": ([_P, _P, _I, _GP, _D, _P, _I, _I, _P], _I),
     "xl_vrs_propagate_backward": ([_P, _P, _P, _P, _I, _GP, _D, _P, _I, _I, _P], _I),
+    "xl_rs_propagate_save": ([_P, _P, _P, _I, _GP, _D, _P, _I, _I, _P], _I),
+    "xl_rs_propagate_backward_saved": ([_P, _P, _P, _P, _I, _GP, _D, _P, _I, _I, _P], _I),
+    "xl_vrs_propagate_save": ([_P, _P, _P, _I, _GP, _D, _P, _I, _I, _P], _I),
+    "xl_vrs_propagate_backward_saved": ([_P, _P, _P, _P, _I, _GP, _D, _P, _I, _I, _P], _I),
     "xl_czt_propagate": ([_P, _P, _I, _I, _GP, _WP, _D, _P, _I, _I, _P], _I),
     "xl_apply_elements": ([_P, _P, _I, _I, _GP, _D, ctypes.POINTER(Element), _I, _P, _I, _I, _P], _I),
     "xl_apply_elements_backward": ([_P, _P, _P, _I, _I, _GP, _D, ctypes.POINTER(Element), _I, _P,
@@ -235,17 +239,33 @@ def _planes(u: torch.Tensor, comps: int, name: str):
     raise ValueError(f"{name}: bad shape {tuple(u.shape)} for {comps} component(s)")
 
 
-def rs_propagate(u: torch.Tensor, grid, wavelength: float, z, out: torch.Tensor | None = None):
-    """Scalar RS propagation of [B][ny][nx] (or [ny][nx]) planes; returns the same shape."""
+def rs_propagate(u: torch.Tensor, grid, wavelength: float, z, out: torch.Tensor | None = None,
+                 saved: torch.Tensor | None = None):
+    """Scalar RS propagation of [B][ny][nx] (or [ny][nx]) planes; returns the same shape.
+    saved: optional [B][2nx][ny] tensor that receives the row transforms of the input for
+    rs_propagate_backward(..., saved=...) (xl_rs_propagate_save); see save_buffer()."""
     _dev(u, "u")
     B, ny, nx = _planes(u, 1, "u")
     g = Grid.of(grid)
     if out is None:
         out = torch.empty_like(u)
     zz = _Z(z, B)
+    if saved is not None:
+        _check(load().xl_rs_propagate_save(u.data_ptr(), _dev(out, "out").data_ptr(),
+                                           _dev(saved, "saved").data_ptr(), B, ctypes.byref(g),
+                                           float(wavelength), zz.ptr, zz.flags, _dtype(u),
+                                           _stream()))
+        return out
     _check(load().xl_rs_propagate(u.data_ptr(), _dev(out, "out").data_ptr(), B, ctypes.byref(g),
                                   float(wavelength), zz.ptr, zz.flags, _dtype(u), _stream()))
     return out
+
+
+def save_buffer(field: torch.Tensor, comps: int = 1) -> torch.Tensor:
+    """Buffer for the row transforms a forward RS (comps 1) or VRS (comps 2) call saves for its
+    adjoint: [B][comps][2nx][ny] of the field's dtype."""
+    B, ny, nx = _planes(field, comps, "field")
+    return torch.empty((B, comps, 2 * nx, ny), dtype=field.dtype, device=field.device)
 
 
 def rs_propagate_static(u: torch.Tensor, grid, wavelength: float, z,
@@ -267,16 +287,20 @@ def rs_propagate_static(u: torch.Tensor, grid, wavelength: float, z,
 
 def rs_propagate_backward(g_out: torch.Tensor, u_in: torch.Tensor | None, grid, wavelength: float,
                           z, want_field: bool = True, want_dz: bool = False,
-                          phase_invariant: bool = False):
+                          phase_invariant: bool = False, saved: torch.Tensor | None = None):
     """Adjoint of rs_propagate: returns (g_in or None, g_z [B] float64 or None).
-    phase_invariant: the loss ignores a constant phase on the output (XL_PHASE_INVARIANT)."""
+    phase_invariant: the loss ignores a constant phase on the output (XL_PHASE_INVARIANT).
+    saved: the row transforms a forward call saved; used in place of u_in."""
     _dev(g_out, "g_out")
     B, ny, nx = _planes(g_out, 1, "g_out")
     g = Grid.of(grid)
     g_in = torch.empty_like(g_out) if want_field else None
     g_z = torch.empty(B, dtype=torch.float64, device=g_out.device) if want_dz else None
     zz = _Z(z, B)
-    _check(load().xl_rs_propagate_backward(
+    fn = load().xl_rs_propagate_backward
+    if saved is not None:
+        fn, u_in = load().xl_rs_propagate_backward_saved, saved
+    _check(fn(
         g_out.data_ptr(), _dev(u_in, "u_in").data_ptr() if u_in is not None else None,
         g_in.data_ptr() if g_in is not None else None, g_z.data_ptr() if g_z is not None else None,
         B, ctypes.byref(g), float(wavelength), zz.ptr,
@@ -284,8 +308,10 @@ def rs_propagate_backward(g_out: torch.Tensor, u_in: torch.Tensor | None, grid, 
     return g_in, g_z
 
 
-def vrs_propagate(exy: torch.Tensor, grid, wavelength: float, z, out: torch.Tensor | None = None):
-    """Vectorial RS: [B][2][ny][nx] -> [B][3][ny][nx] (also [2][ny][nx] -> [3][ny][nx])."""
+def vrs_propagate(exy: torch.Tensor, grid, wavelength: float, z, out: torch.Tensor | None = None,
+                  saved: torch.Tensor | None = None):
+    """Vectorial RS: [B][2][ny][nx] -> [B][3][ny][nx] (also [2][ny][nx] -> [3][ny][nx]).
+    saved: optional [B][2][2nx][ny] tensor for vrs_propagate_backward(..., saved=...)."""
     _dev(exy, "exy")
     B, ny, nx = _planes(exy, 2, "exy")
     g = Grid.of(grid)
@@ -293,6 +319,12 @@ def vrs_propagate(exy: torch.Tensor, grid, wavelength: float, z, out: torch.Tens
         shape = (3, ny, nx) if exy.dim() == 3 else (B, 3, ny, nx)
         out = torch.empty(shape, dtype=exy.dtype, device=exy.device)
     zz = _Z(z, B)
+    if saved is not None:
+        _check(load().xl_vrs_propagate_save(exy.data_ptr(), _dev(out, "out").data_ptr(),
+                                            _dev(saved, "saved").data_ptr(), B, ctypes.byref(g),
+                                            float(wavelength), zz.ptr, zz.flags, _dtype(exy),
+                                            _stream()))
+        return out
     _check(load().xl_vrs_propagate(exy.data_ptr(), _dev(out, "out").data_ptr(), B, ctypes.byref(g),
                                    float(wavelength), zz.ptr, zz.flags, _dtype(exy), _stream()))
     return out
@@ -300,8 +332,9 @@ def vrs_propagate(exy: torch.Tensor, grid, wavelength: float, z, out: torch.Tens
 
 def vrs_propagate_backward(g_exyz: torch.Tensor, exy_in: torch.Tensor | None, grid,
                            wavelength: float, z, want_field: bool = True, want_dz: bool = False,
-                           phase_invariant: bool = False):
-    """Adjoint of vrs_propagate: returns (g_exy or None, g_z or None)."""
+                           phase_invariant: bool = False, saved: torch.Tensor | None = None):
+    """Adjoint of vrs_propagate: returns (g_exy or None, g_z or None); saved as in
+    rs_propagate_backward."""
     _dev(g_exyz, "g_exyz")
     B, ny, nx = _planes(g_exyz, 3, "g_exyz")
     g = Grid.of(grid)
@@ -311,7 +344,10 @@ def vrs_propagate_backward(g_exyz: torch.Tensor, exy_in: torch.Tensor | None, gr
         g_exy = torch.empty(shape, dtype=g_exyz.dtype, device=g_exyz.device)
     g_z = torch.empty(B, dtype=torch.float64, device=g_exyz.device) if want_dz else None
     zz = _Z(z, B)
-    _check(load().xl_vrs_propagate_backward(
+    fn = load().xl_vrs_propagate_backward
+    if saved is not None:
+        fn, exy_in = load().xl_vrs_propagate_backward_saved, saved
+    _check(fn(
         g_exyz.data_ptr(), _dev(exy_in, "exy_in").data_ptr() if exy_in is not None else None,
         g_exy.data_ptr() if g_exy is not None else None,
         g_z.data_ptr() if g_z is not None else None, B, ctypes.byref(g), float(wavelength),
