@@ -38,6 +38,7 @@ LAM = 0.633
 ZS = (500.0, 2000.0, 10_000.0)
 N, PITCH, W0 = 2048, 0.5, 200.0
 M, WIN_W = 512, 64.0
+E2E_CHUNK = 4  # fields per device pass of the end-to-end (host-staged) measurement
 
 
 def parse():
@@ -222,6 +223,18 @@ def table_section(xl, torch, setups: int, steps: int, seed: int):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     b.close()
+    # one table of 1024^2 (complex64, graph replay): the single-setup rate
+    one = xl.Batch(TABLE_CFG, [1024], [[0.3, 20_000.0, 20_000.0]], seed)
+    one.step(use_graph=True)
+    one.step(use_graph=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(20):
+        one.step(use_graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms1024 = e0.elapsed_time(e1) / 20
+    one.close()
     # the complex128 single-instance path, one setup per size
     f64 = {}
     for n in (512, 1024, 2048):
@@ -240,6 +253,7 @@ def table_section(xl, torch, setups: int, steps: int, seed: int):
             "grads_per_s": setups / (ms / 1000.0), "ms_per_step": ms,
             "fp64_single_instance_grads_per_s": setups / (t64 / 1000.0),
             "fp64_ms_per_setup": f64,
+            "table1024_grads_per_s": 1000.0 / ms1024,
             "speedup_vs_fp64_single_instance": t64 / ms}
 
 
@@ -356,6 +370,24 @@ def main():
     value = step.props * world * a.steps / (ms / 1000.0)
     grads = B * world * a.steps / (ms / 1000.0)
 
+    # batch 1 (one field per step, z = 0.5 mm): the latency-bound end of the same step
+    batch1 = None
+    if B > 1:
+        s1 = GpuStep(xl, torch, g, w, U_dev[:1].contiguous(), zs[:1])
+        for _ in range(3):
+            s1()
+        barrier()
+        k1 = max(10, a.steps // 2)
+        e0.record(stream)
+        for _ in range(k1):
+            s1()
+        e1.record(stream)
+        barrier()
+        ms1 = e0.elapsed_time(e1) / k1
+        batch1 = {"value": s1.props / (ms1 / 1000.0), "unit": "propagations/s", "ms_per_step": ms1,
+                  "steps": k1, "note": "one 2048^2 field, z = 0.5 mm, same four propagations"}
+        del s1
+
     # per-kernel durations (CUDA events recorded by the library on its launch stream)
     xl.profile_enable(True)
     for _ in range(3):
@@ -398,20 +430,35 @@ def main():
                         "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     kernels = {k: {"launches": v[0] // 3, "ms_per_step": v[1] / 3} for k, v in prof.items()}
 
-    # end to end: pinned host input -> device, the step, results back to pinned host buffers
+    # end to end: pinned host input -> device, the step, results back to pinned host buffers,
+    # streamed in chunks of E2E_CHUNK fields so that the copies overlap the kernels
     e2e = None
     if not a.no_e2e:
+        from paper_2310_08408_gb300.pipeline import HostPipeline
         A_h = torch.empty(step.A.shape, dtype=step.A.dtype).pin_memory()
         C_h = torch.empty(step.C.shape, dtype=step.C.dtype).pin_memory()
         gz_h = torch.empty((B,), dtype=torch.float64).pin_memory()
         ke = max(3, a.steps // 4)
+        ch = min(E2E_CHUNK, B)
+        pipe = HostPipeline([((N, N), U_pin.dtype)],
+                            [((N, N), step.A.dtype), ((M, M), step.C.dtype), ((), torch.float64)],
+                            chunk=ch)
+        with torch.cuda.stream(pipe.compute_stream):
+            S_c = xl.save_buffer(step.U[:ch])
+        GA_c, GC_c = step.GA[:ch], step.GC[:ch]
+
+        def chunk_step(ins, outs, lo, n):
+            (U,), (A, C, gz) = ins, outs
+            zc = zs[lo:lo + n]
+            xl.rs_propagate(U, g, LAM, zc, out=A, saved=S_c[:n])
+            xl.czt_propagate(U, g, w, LAM, zc, out=C)
+            xl.czt_propagate_backward(GC_c[:n], g, w, LAM, zc)
+            _, gzc = xl.rs_propagate_backward(GA_c[:n], None, g, LAM, zc, want_field=True,
+                                              want_dz=True, saved=S_c[:n])
+            gz.copy_(gzc)
 
         def e2e_step():
-            step.U.copy_(U_pin, non_blocking=True)
-            A, C, gz = step()
-            A_h.copy_(A, non_blocking=True)
-            C_h.copy_(C, non_blocking=True)
-            gz_h.copy_(gz, non_blocking=True)
+            pipe.run([U_pin], [A_h, C_h, gz_h], chunk_step)
 
         e2e_step()
         barrier()
@@ -452,6 +499,7 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs (537 MB per GPU) exceed L2; no flush"},
             "grads_per_s": grads,
+            "batch1": batch1,
             "tables": table,
             "step_parts": step_parts(xl),
             "gpu_launches": int(launches),
