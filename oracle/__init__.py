@@ -92,6 +92,8 @@ def _sig(lib):
     lib.orc_adamw.argtypes = [_P, _P, _P, _P, _I64, _D, _D, _D, _D, _D, _I64]
     lib.orc_mse.argtypes = [_P, _P, _I64, _P]
     lib.orc_mse.restype = _D
+    lib.orc_beam_splitter.argtypes = [_P, _P, _I64, _D, _P, _P]
+    lib.orc_beam_splitter_backward.argtypes = [_P, _P, _P, _P, _I64, _D, _P, _P, _P]
     for name in ("orc_fft", "orc_fft2", "orc_rs_fft", "orc_rs_direct", "orc_rs_direct_points",
                  "orc_czt_direct", "orc_czt_brute", "orc_czt_points", "orc_elements_forward",
                  "orc_elements_backward", "orc_intensity_loss", "orc_intensity_loss_backward"):
@@ -398,3 +400,29 @@ def mse(I, target, want_grad=False):
     dI = np.empty_like(I) if want_grad else None
     L = _load().orc_mse(_ptr(I), _ptr(t), I.size, _ptr(dI))
     return float(L), dI
+
+
+def beam_splitter(a, b, R):
+    """Lossless beam splitter of reflectance R: (out_t, out_r) = (t a + i r b, i r a + t b);
+    a or b None is a zero input."""
+    ref = a if a is not None else b
+    a = _c(a, np.complex128).ravel() if a is not None else None
+    b = _c(b, np.complex128).ravel() if b is not None else None
+    n = (a if a is not None else b).size
+    ot, orr = np.empty(n, np.complex128), np.empty(n, np.complex128)
+    _load().orc_beam_splitter(_ptr(a), _ptr(b), n, float(R), _ptr(ot), _ptr(orr))
+    sh = np.shape(ref)
+    return ot.reshape(sh), orr.reshape(sh)
+
+
+def beam_splitter_backward(g_t, g_r, a, b, R):
+    """(g_a, g_b, dL/dR) of beam_splitter from the output gradients (None = zero)."""
+    arrs = [_c(x, np.complex128).ravel() if x is not None else None for x in (g_t, g_r, a, b)]
+    ref = next(x for x in (g_t, g_r, a, b) if x is not None)
+    n = next(x for x in arrs if x is not None).size
+    ga, gb = np.empty(n, np.complex128), np.empty(n, np.complex128)
+    gR = np.zeros(1)
+    _load().orc_beam_splitter_backward(*[_ptr(x) for x in arrs], n, float(R), _ptr(ga), _ptr(gb),
+                                       _ptr(gR))
+    sh = np.shape(ref)
+    return ga.reshape(sh), gb.reshape(sh), float(gR[0])

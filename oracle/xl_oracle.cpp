@@ -990,4 +990,42 @@ double orc_mse(const double* I, const double* target, int64_t P, double* dI) {
   return s / (double)P;
 }
 
+// Lossless, non-polarising beam splitter (Results, "Towards large-scale discovery", and Methods,
+// "The large-scale search space": beam splitters with a continuous ratio in [0, 1] connect the
+// paths of the optical table). Reading: R is the reflected intensity fraction, amplitudes
+// t = sqrt(1 - R), r = sqrt(R), and the reflected amplitude carries the factor i (the symmetric
+// unitary convention):  out_t = t a + i r b,  out_r = i r a + t b.  a or b NULL: a zero input.
+void orc_beam_splitter(const cd* a, const cd* b, int64_t n, double R, cd* out_t, cd* out_r) {
+  const double t = std::sqrt(1.0 - R), r = std::sqrt(R);
+  const cd ir(0.0, r);
+  for (int64_t i = 0; i < n; ++i) {
+    const cd av = a ? a[i] : cd(0.0), bv = b ? b[i] : cd(0.0);
+    out_t[i] = t * av + ir * bv;
+    out_r[i] = ir * av + t * bv;
+  }
+}
+
+// Adjoint of orc_beam_splitter (the conjugate transpose of [[t, i r], [i r, t]]):
+//   g_a = t g_t - i r g_r,  g_b = -i r g_t + t g_r,
+// and dL/dR = Re sum conj(g_t) d out_t/dR + conj(g_r) d out_r/dR with dt/dR = -1/(2t),
+// dr/dR = 1/(2r) (unbounded at R = 0 and R = 1). g_t, g_r, a, b may be NULL (zero).
+void orc_beam_splitter_backward(const cd* g_t, const cd* g_r, const cd* a, const cd* b, int64_t n,
+                                double R, cd* g_a, cd* g_b, double* g_R) {
+  const double t = std::sqrt(1.0 - R), r = std::sqrt(R);
+  const cd ir(0.0, r);
+  const double dt = -0.5 / t, dr = 0.5 / r;
+  double acc = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    const cd gt = g_t ? g_t[i] : cd(0.0), gr = g_r ? g_r[i] : cd(0.0);
+    const cd av = a ? a[i] : cd(0.0), bv = b ? b[i] : cd(0.0);
+    if (g_a) g_a[i] = t * gt - ir * gr;
+    if (g_b) g_b[i] = -ir * gt + t * gr;
+    if (g_R) {
+      const cd dot = dt * av + cd(0.0, dr) * bv, dor = cd(0.0, dr) * av + dt * bv;
+      acc += std::real(std::conj(gt) * dot) + std::real(std::conj(gr) * dor);
+    }
+  }
+  if (g_R) *g_R = acc;
+}
+
 }  // extern "C"
