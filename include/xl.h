@@ -334,6 +334,30 @@ xl_status xl_softmin(const double* losses, int32_t batch, int32_t n_det, double 
 xl_status xl_device_status(void* stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Beam splitters (Results, "Towards large-scale discovery"; Methods, "The large-scale search
+ * space": beam splitters with a continuous ratio in [0, 1] connect the paths of the table).
+ * Reading: lossless and non-polarising, R = reflected intensity fraction, t = sqrt(1 - R),
+ * r = sqrt(R), the reflected amplitude carrying the factor i:
+ *   out_t = t a + i r b,   out_r = i r a + t b    (every component alike).
+ * a, b, out_t, out_r: [batch][elems] complex (dtype) device arrays, `elems` = components x pixels
+ *   of one batch element; a or b NULL is a zero input, out_t or out_r NULL is not written.
+ *   Outputs may alias inputs (each element is read before it is written).
+ * R: [batch] device doubles in [0, 1] (trainable).
+ * Errors: XL_ERR_ARG for a NULL R (non-empty call), negative sizes or a bad dtype;
+ *   XL_ERR_UNSUPPORTED for batch > 65535.
+ * -------------------------------------------------------------------------------------------*/
+xl_status xl_beam_splitter(const void* a, const void* b, void* out_t, void* out_r, int32_t batch,
+                           int64_t elems, const double* R, int32_t dtype, void* stream);
+
+/* Adjoint: g_a = t g_t - i r g_r, g_b = -i r g_t + t g_r (each nullable), and
+ * g_R[b] = dL/dR = Re sum conj(g_t) d out_t/dR + conj(g_r) d out_r/dR (device doubles,
+ * nullable; needs the forward inputs a, b). dL/dR is unbounded at R = 0 and R = 1 (inf or NaN
+ * there): optimise an unconstrained parameter mapped into (0, 1). g_t, g_r NULL: zero. */
+xl_status xl_beam_splitter_backward(const void* g_t, const void* g_r, const void* a, const void* b,
+                                    void* g_a, void* g_b, double* g_R, int32_t batch, int64_t elems,
+                                    const double* R, int32_t dtype, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
  * Adam (the paper's optimiser): bias-corrected step t >= 1,
  *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;  p -= lr m/(1-b1^t) / (sqrt(v/(1-b2^t)) + eps).
  * params, m, v, grad: device arrays of n reals (real_dtype 0 = float, 1 = double), updated in

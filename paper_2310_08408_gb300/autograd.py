@@ -92,6 +92,25 @@ class CZTPropagate(torch.autograd.Function):
         return g_in, None, None, None, None, None
 
 
+class BeamSplitter(torch.autograd.Function):
+    """(a, b, R) -> (out_t, out_r): lossless beam splitter of reflectance R (float64 CUDA [B]);
+    a and b are fields of the same shape [B][...]."""
+
+    @staticmethod
+    def forward(ctx, a, b, R):
+        a, b, Rc = a.contiguous(), b.contiguous(), R.detach().contiguous()
+        ctx.save_for_backward(a, b, Rc)
+        return xl.beam_splitter(a, b, Rc)
+
+    @staticmethod
+    def backward(ctx, g_t, g_r):
+        a, b, R = ctx.saved_tensors
+        need_a, need_b, need_R = ctx.needs_input_grad
+        g_a, g_b, g_R = xl.beam_splitter_backward(g_t.contiguous(), g_r.contiguous(), a, b, R,
+                                                  want_a=need_a, want_b=need_b, want_R=need_R)
+        return g_a, g_b, g_R
+
+
 class Elements(torch.autograd.Function):
     """Element chain. kinds: list of element kinds; masks: list (per element) of (phi_x, phi_y)
     tensors or None; params: float64 CUDA [B][n][4] {f, alpha, eta, theta} (differentiable)."""

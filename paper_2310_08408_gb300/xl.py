@@ -114,6 +114,8 @@ SIGNATURES = {
                                        _P, _I, _P], _I),
     "xl_softmin": ([_P, _I, _I, _D, _P, _P, _P], _I),
     "xl_device_status": ([_P], _I),
+    "xl_beam_splitter": ([_P, _P, _P, _P, _I, ctypes.c_int64, _P, _I, _P], _I),
+    "xl_beam_splitter_backward": ([_P, _P, _P, _P, _P, _P, _P, _I, ctypes.c_int64, _P, _I, _P], _I),
     "xl_adam_step": ([_P, _P, _P, _P, ctypes.c_int64, _I, _D, _D, _D, _D, _P, _I, _P], _I),
     "xl_adamw_step": ([_P, _P, _P, _P, ctypes.c_int64, _I, _D, _D, _D, _D, _D, _P, _I, _P], _I),
     "xl_step_advance": ([_P, _P], _I),
@@ -579,6 +581,45 @@ def softmin(losses: torch.Tensor, beta: float, want_weights: bool = True):
 def device_status() -> None:
     """Raises XLError(ERR_NONFINITE) if a loss became non-finite since the last check."""
     _check(load().xl_device_status(_stream()))
+
+
+# ----------------------------------------------------------------------------- beam splitters
+def _ptr_or_none(t, name):
+    return _dev(t, name).data_ptr() if t is not None else None
+
+
+def beam_splitter(a: torch.Tensor | None, b: torch.Tensor | None, R: torch.Tensor,
+                  out_t: torch.Tensor | None = None, out_r: torch.Tensor | None = None):
+    """Lossless beam splitter of reflectance R [B] (float64 CUDA): returns (out_t, out_r) =
+    (t a + i r b, i r a + t b) for fields [B][...] (a or b None: a zero input)."""
+    ref = a if a is not None else b
+    if ref is None:
+        raise ValueError("beam_splitter needs at least one input")
+    B = ref.shape[0]
+    elems = ref[0].numel()
+    out_t = torch.empty_like(ref) if out_t is None else out_t
+    out_r = torch.empty_like(ref) if out_r is None else out_r
+    _check(load().xl_beam_splitter(_ptr_or_none(a, "a"), _ptr_or_none(b, "b"),
+                                   _dev(out_t, "out_t").data_ptr(), _dev(out_r, "out_r").data_ptr(),
+                                   B, elems, _dev(R, "R").data_ptr(), _dtype(ref), _stream()))
+    return out_t, out_r
+
+
+def beam_splitter_backward(g_t, g_r, a, b, R: torch.Tensor, want_a: bool = True,
+                           want_b: bool = True, want_R: bool = True):
+    """Adjoint of beam_splitter: returns (g_a or None, g_b or None, g_R [B] float64 or None)."""
+    ref = next(x for x in (g_t, g_r, a, b) if x is not None)
+    B = ref.shape[0]
+    elems = ref[0].numel()
+    g_a = torch.empty_like(ref) if want_a else None
+    g_b = torch.empty_like(ref) if want_b else None
+    g_R = torch.empty(B, dtype=torch.float64, device=ref.device) if want_R else None
+    _check(load().xl_beam_splitter_backward(
+        _ptr_or_none(g_t, "g_t"), _ptr_or_none(g_r, "g_r"), _ptr_or_none(a, "a"),
+        _ptr_or_none(b, "b"), g_a.data_ptr() if g_a is not None else None,
+        g_b.data_ptr() if g_b is not None else None, g_R.data_ptr() if g_R is not None else None,
+        B, elems, _dev(R, "R").data_ptr(), _dtype(ref), _stream()))
+    return g_a, g_b, g_R
 
 
 # ----------------------------------------------------------------------------- Adam
