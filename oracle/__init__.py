@@ -93,6 +93,9 @@ def _sig(lib):
     lib.orc_mse.argtypes = [_P, _P, _I64, _P]
     lib.orc_mse.restype = _D
     lib.orc_beam_splitter.argtypes = [_P, _P, _I64, _D, _P, _P]
+    lib.orc_asczt.argtypes = [_P, _P, _I64, _I64, _D, _D, _D, _D, _I64, _I64, _D, _D, _D, _D, _D,
+                              _D, _I32, _I32]
+    lib.orc_asczt.restype = _I32
     lib.orc_beam_splitter_backward.argtypes = [_P, _P, _P, _P, _I64, _D, _P, _P, _P]
     for name in ("orc_fft", "orc_fft2", "orc_rs_fft", "orc_rs_direct", "orc_rs_direct_points",
                  "orc_czt_direct", "orc_czt_brute", "orc_czt_points", "orc_elements_forward",
@@ -426,3 +429,22 @@ def beam_splitter_backward(g_t, g_r, a, b, R):
                                        _ptr(gR))
     sh = np.shape(ref)
     return ga.reshape(sh), gb.reshape(sh), float(gR[0])
+
+
+AS_H, AS_DH = 0, 1
+
+
+def asczt(u, grid, window, wavelength, z, kind=AS_H, adjoint=False):
+    """Angular-spectrum CZT: u [ny][nx] -> [my][mx] on the window (adjoint: window -> grid).
+    grid = (nx, ny, dx, dy, x0, y0), window = (mx, my, dxo, dyo, xo0, yo0); kind AS_DH gives the
+    distance derivative of the forward map."""
+    nx, ny, dx, dy, x0, y0 = grid
+    mx, my, dxo, dyo, xo0, yo0 = window
+    src = _c(u, np.complex128)
+    shape = (ny, nx) if adjoint else (my, mx)
+    out = np.empty(shape, np.complex128)
+    st = _load().orc_asczt(_ptr(src), _ptr(out), nx, ny, dx, dy, x0, y0, mx, my, dxo, dyo, xo0, yo0,
+                           wavelength, z, kind, int(bool(adjoint)))
+    if st != 0:
+        raise ValueError("orc_asczt: bad arguments")
+    return out

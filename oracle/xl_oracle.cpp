@@ -990,6 +990,103 @@ double orc_mse(const double* I, const double* target, int64_t P, double* dI) {
   return s / (double)P;
 }
 
+// Angular-spectrum CZT: the exact-RS reading of the chirped z-transform propagator (Methods,
+// "Features and performance"; Hu et al.): the angular spectrum of the sampled field, times the
+// free-space transfer function, summed back onto an arbitrary output window.
+//   U^(f, g) = sum_{n,m} u[n][m] exp(-2 pi i (f x_m + g y_n)),  f = j / (nx dx), g = l / (ny dy),
+//              j, l over the signed frequency indices [-n/2, n/2) of an n-point DFT,
+//   H = exp(i z kz), kz = sqrt(k^2 - (2 pi f)^2 - (2 pi g)^2) (kz = i sqrt(-...) beyond the
+//       light cone: evanescent decay),
+//   U1(X_p, Y_q) = 1 / (nx ny) sum_{f,g} U^ H exp(2 pi i (f X_p + g Y_q)).
+// kind 0: H; kind 1: dH/dz = i kz H (the distance derivative). adjoint: the conjugate-transpose
+// map (window -> input grid). The spectrum uses the FFT (sizes: powers of two); the sums onto the
+// window are direct and separable.
+static cd as_transfer(double f, double g, double k, double z, int kind) {
+  const double a = k * k - 4.0 * PI * PI * (f * f + g * g);
+  cd kz = a >= 0.0 ? cd(std::sqrt(a), 0.0) : cd(0.0, std::sqrt(-a));
+  cd H = std::exp(cd(0.0, 1.0) * kz * z);
+  return kind == 1 ? cd(0.0, 1.0) * kz * H : H;
+}
+
+static double as_freq(int64_t k, int64_t n, double d) {  // FFT bin k -> signed frequency
+  const int64_t j = k < n / 2 ? k : k - n;
+  return (double)j / ((double)n * d);
+}
+
+int orc_asczt(const double* u_in, double* u_out, int64_t nx, int64_t ny, double dx, double dy,
+              double x0, double y0, int64_t mx, int64_t my, double dxo, double dyo, double xo0,
+              double yo0, double wavelength, double z, int kind, int adjoint) {
+  if (!is_pow2(nx) || !is_pow2(ny) || mx < 1 || my < 1 || kind < 0 || kind > 1) return -1;
+  const double k = 2.0 * PI / wavelength;
+  std::vector<double> fx(nx), fy(ny);
+  for (int64_t i = 0; i < nx; ++i) fx[i] = as_freq(i, nx, dx);
+  for (int64_t i = 0; i < ny; ++i) fy[i] = as_freq(i, ny, dy);
+  // window exponentials Ex[p][j] = exp(2 pi i f_j X_p), Ey[q][l] = exp(2 pi i g_l Y_q)
+  std::vector<cd> Ex((size_t)(mx * nx)), Ey((size_t)(my * ny));
+  for (int64_t p = 0; p < mx; ++p)
+    for (int64_t j = 0; j < nx; ++j) Ex[p * nx + j] = std::exp(cd(0.0, 2.0 * PI * fx[j] * (xo0 + p * dxo)));
+  for (int64_t q = 0; q < my; ++q)
+    for (int64_t l = 0; l < ny; ++l) Ey[q * ny + l] = std::exp(cd(0.0, 2.0 * PI * fy[l] * (yo0 + q * dyo)));
+  const double norm = 1.0 / ((double)nx * (double)ny);
+  std::vector<cd> W((size_t)(nx * ny));
+  if (!adjoint) {
+    // spectrum: FFT, then the phase of the grid origin
+    for (int64_t i = 0; i < nx * ny; ++i) W[i] = ld(u_in, i);
+    fft2_inplace(W, ny, nx, -1);
+    for (int64_t l = 0; l < ny; ++l)
+      for (int64_t j = 0; j < nx; ++j)
+        W[l * nx + j] *= std::exp(cd(0.0, -2.0 * PI * (fx[j] * x0 + fy[l] * y0))) *
+                         as_transfer(fx[j], fy[l], k, z, kind);
+    // onto the window: V[l][p] = sum_j W[l][j] Ex[p][j]; out[q][p] = norm sum_l V[l][p] Ey[q][l]
+    std::vector<cd> V((size_t)(ny * mx));
+    parallel_for(ny, [&](int64_t b, int64_t e) {
+      for (int64_t l = b; l < e; ++l)
+        for (int64_t p = 0; p < mx; ++p) {
+          cd s(0.0, 0.0);
+          for (int64_t j = 0; j < nx; ++j) s += W[l * nx + j] * Ex[p * nx + j];
+          V[l * mx + p] = s;
+        }
+    });
+    parallel_for(my, [&](int64_t b, int64_t e) {
+      for (int64_t q = b; q < e; ++q)
+        for (int64_t p = 0; p < mx; ++p) {
+          cd s(0.0, 0.0);
+          for (int64_t l = 0; l < ny; ++l) s += V[l * mx + p] * Ey[q * ny + l];
+          st(u_out, q * mx + p, norm * s);
+        }
+    });
+  } else {
+    // adjoint of the window sums: V[l][p] = sum_q G[q][p] conj(Ey[q][l]);
+    // W[l][j] = norm sum_p V[l][p] conj(Ex[p][j])
+    std::vector<cd> V((size_t)(ny * mx));
+    parallel_for(ny, [&](int64_t b, int64_t e) {
+      for (int64_t l = b; l < e; ++l)
+        for (int64_t p = 0; p < mx; ++p) {
+          cd s(0.0, 0.0);
+          for (int64_t q = 0; q < my; ++q) s += ld(u_in, q * mx + p) * std::conj(Ey[q * ny + l]);
+          V[l * mx + p] = s;
+        }
+    });
+    parallel_for(ny, [&](int64_t b, int64_t e) {
+      for (int64_t l = b; l < e; ++l)
+        for (int64_t j = 0; j < nx; ++j) {
+          cd s(0.0, 0.0);
+          for (int64_t p = 0; p < mx; ++p) s += V[l * mx + p] * std::conj(Ex[p * nx + j]);
+          W[l * nx + j] = norm * s;
+        }
+    });
+    // adjoint of the spectrum step: conj(H) and the conjugate origin phase, then the
+    // unnormalised inverse transform
+    for (int64_t l = 0; l < ny; ++l)
+      for (int64_t j = 0; j < nx; ++j)
+        W[l * nx + j] *= std::exp(cd(0.0, 2.0 * PI * (fx[j] * x0 + fy[l] * y0))) *
+                         std::conj(as_transfer(fx[j], fy[l], k, z, kind));
+    fft2_inplace(W, ny, nx, +1);
+    for (int64_t i = 0; i < nx * ny; ++i) st(u_out, i, W[i]);
+  }
+  return 0;
+}
+
 // Lossless, non-polarising beam splitter (Results, "Towards large-scale discovery", and Methods,
 // "The large-scale search space": beam splitters with a continuous ratio in [0, 1] connect the
 // paths of the optical table). Reading: R is the reflected intensity fraction, amplitudes
