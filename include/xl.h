@@ -219,6 +219,33 @@ xl_status xl_czt_propagate_backward(const void* g_out, void* g_in, int32_t batch
                                     int32_t flags, int32_t dtype, void* stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Angular-spectrum CZT: the exact-RS reading of the CZT propagator (Methods, "Features and
+ * performance": propagation onto an arbitrarily placed and sampled window; the CZT of Hu et al.
+ * evaluates the inverse transform of the propagated angular spectrum on the window).
+ * Reading: with signed DFT frequencies f = j / (nx dx), g = l / (ny dy), j, l in [-n/2, n/2),
+ *   U^(f, g) = sum_{n,m} u_in[n][m] exp(-2 pi i (f x_m + g y_n)),
+ *   u_out[q][p] = 1/(nx ny) sum_{f,g} U^(f, g) exp(i z kz) exp(2 pi i (f X_p + g Y_q)),
+ *   kz = sqrt(k^2 - (2 pi f)^2 - (2 pi g)^2) (kz = i sqrt(...) beyond the light cone: decay).
+ * On the native grid (window = grid) this is the angular-spectrum method; there is no paraxial
+ * approximation. Realised by two spectrum passes (the field times (-1)^(x+y), row and column
+ * transforms, the transfer function cached per distance) and the two Bluestein window passes.
+ * u_in: [batch][ny][nx], u_out: [batch][my][mx] (complex dtype, device, not aliasing).
+ * z: [batch] distances >= 0 (host, or device with XL_Z_DEVICE).
+ * Supported: nx, ny powers of two in [64, 4096]; mx, my >= 1 with N + M - 1 <= 8192 per axis.
+ * -------------------------------------------------------------------------------------------*/
+xl_status xl_asczt_propagate(const void* u_in, void* u_out, int32_t batch, const xl_grid* grid,
+                             const xl_window* window, double wavelength, const double* z,
+                             int32_t flags, int32_t dtype, void* stream);
+
+/* Adjoint of xl_asczt_propagate: g_out [batch][my][mx] -> g_in [batch][ny][nx] (nullable) and
+ * g_z[b] = Re sum conj(g_out) du_out/dz (device doubles, nullable; needs u_in), the distance
+ * derivative of the transfer function being i kz exp(i z kz). */
+xl_status xl_asczt_propagate_backward(const void* g_out, const void* u_in, void* g_in,
+                                      double* g_z, int32_t batch, const xl_grid* grid,
+                                      const xl_window* window, double wavelength, const double* z,
+                                      int32_t flags, int32_t dtype, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
  * Optical elements (Methods, "Features and performance": SLMs (one free phase per pixel), the
  * super-SLM (independent phases on the horizontal and vertical components), polarisers, variable
  * retarders / wave plates, planar lenses). A chain of up to 8 elements is applied in one pass.

@@ -113,4 +113,20 @@ xl_status czt_tables<XL_REAL>(void* tab, const CztTabArgs& a, cudaStream_t s) {
   return XL_OK;
 }
 
+template <>
+xl_status asczt_tables<XL_REAL>(void* tab, const CztTabArgs& a, cudaStream_t s) {
+  typedef cplx<XL_REAL> C;
+  const int64_t total = (int64_t)a.nx + a.mx + a.Lx + a.ny + a.my + a.Ly;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 1024);
+  {
+    LaunchScope ls("asczt_tables", s);
+    k_asczt_tables<XL_REAL><<<blocks, 256, 0, s>>>((C*)tab, a);
+  }
+  XL_CUDA_TRY(cudaGetLastError());
+  C* t = (C*)tab;
+  XL_TRY(bhat<XL_REAL>(a.Lx, t + a.nx + a.mx, a.Lx, s));
+  XL_TRY(bhat<XL_REAL>(a.Ly, t + a.off_y + a.ny + a.my, a.Ly, s));
+  return XL_OK;
+}
+
 }  // namespace xl

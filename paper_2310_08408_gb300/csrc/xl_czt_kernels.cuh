@@ -462,6 +462,56 @@ __global__ void k_czt_tables(cplx<T>* __restrict__ tab, CztTabArgs a) {
   }
 }
 
+// Chirp tables of the angular-spectrum reading (the window sums of the inverse transform of a
+// centred spectrum; same layout as k_czt_tables). Per axis, bin m (signed index m' = m - N/2,
+// frequency f = m' / (N D)), window (S0, dd), grid origin s0, beta = 2 pi dd / (N D):
+//   pre(m)  = exp(i [2 pi f (S0 - s0) + beta m'^2 / 2]),
+//   post(p) = exp(i beta p^2 / 2) / N,
+//   b(j)    = exp(-i beta (j + N/2)^2 / 2) for -(N-1) <= j <= M-1, placed mod L,
+// so that post(p) sum_m a[m] pre(m) b(p - m) = (1/N) sum_m a[m] exp(2 pi i f (X_p - s0)): the
+// 1/N of the inverse transform and the phase of the grid origin are in the tables. No distance.
+template <typename T>
+__global__ void k_asczt_tables(cplx<T>* __restrict__ tab, CztTabArgs a) {
+  typedef cplx<T> C;
+  const int64_t tx = (int64_t)a.nx + a.mx + a.Lx;
+  const int64_t ty = (int64_t)a.ny + a.my + a.Ly;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tx + ty;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const bool isy = i >= tx;
+    const int64_t j = isy ? i - tx : i;
+    const int N = isy ? a.ny : a.nx, M = isy ? a.my : a.mx, L = isy ? a.Ly : a.Lx;
+    const double s0 = isy ? a.y0 : a.x0, D = isy ? a.dy : a.dx;
+    const double S0 = isy ? a.yo0 : a.xo0, dd = isy ? a.dyo : a.dxo;
+    const double beta = kTwoPi * dd / ((double)N * D);
+    double ph, amp = 1.0;
+    bool zero = false;
+    if (j < N) {  // pre(m)
+      const double mp = (double)(j - N / 2);
+      ph = red2pi(kTwoPi * (mp / ((double)N * D)) * (S0 - s0)) + red2pi(0.5 * beta * mp * mp);
+    } else if (j < N + M) {  // post(p)
+      const double p = (double)(j - N);
+      ph = red2pi(0.5 * beta * p * p);
+      amp = 1.0 / (double)N;
+    } else {  // b placed mod L for -(N-1) <= jj <= M-1
+      const int64_t idx = j - N - M;
+      const int64_t jj = idx <= M - 1 ? idx : idx - L;
+      zero = jj < -(N - 1);
+      const double o = (double)(jj + N / 2);
+      ph = -red2pi(0.5 * beta * o * o);
+    }
+    C v;
+    if (zero) {
+      v = mk((T)0, (T)0);
+    } else {
+      ph = red2pi(ph);
+      T sn, cs;
+      xsincos((T)ph, &sn, &cs);
+      v = mk((T)(cs * amp), (T)(sn * amp));
+    }
+    tab[(isy ? a.off_y : 0) + j] = v;
+  }
+}
+
 // In-place DFT of rows of length L (one team per row), scaled by 1/L: the chirp kernels.
 template <typename T, int L>
 __global__ void __launch_bounds__(L / 16) k_czt_bhat(cplx<T>* __restrict__ rows, int64_t stride,

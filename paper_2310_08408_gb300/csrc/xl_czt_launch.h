@@ -16,5 +16,8 @@ xl_status czt_pass(int which, bool vec, int L, const void* src, void* dst, const
 // Fills the chirp tables (both axes) and transforms the b rows in place.
 template <typename T>
 xl_status czt_tables(void* tab, const CztTabArgs& a, cudaStream_t s);
+// The same for the angular-spectrum reading (window sums of a centred spectrum; no distance).
+template <typename T>
+xl_status asczt_tables(void* tab, const CztTabArgs& a, cudaStream_t s);
 
 }  // namespace xl

@@ -114,6 +114,8 @@ SIGNATURES = {
                                        _P, _I, _P], _I),
     "xl_softmin": ([_P, _I, _I, _D, _P, _P, _P], _I),
     "xl_device_status": ([_P], _I),
+    "xl_asczt_propagate": ([_P, _P, _I, _GP, _WP, _D, _P, _I, _I, _P], _I),
+    "xl_asczt_propagate_backward": ([_P, _P, _P, _P, _I, _GP, _WP, _D, _P, _I, _I, _P], _I),
     "xl_beam_splitter": ([_P, _P, _P, _P, _I, ctypes.c_int64, _P, _I, _P], _I),
     "xl_beam_splitter_backward": ([_P, _P, _P, _P, _P, _P, _P, _I, ctypes.c_int64, _P, _I, _P], _I),
     "xl_adam_step": ([_P, _P, _P, _P, ctypes.c_int64, _I, _D, _D, _D, _D, _P, _I, _P], _I),
@@ -581,6 +583,43 @@ def softmin(losses: torch.Tensor, beta: float, want_weights: bool = True):
 def device_status() -> None:
     """Raises XLError(ERR_NONFINITE) if a loss became non-finite since the last check."""
     _check(load().xl_device_status(_stream()))
+
+
+# ----------------------------------------------------------------------------- angular-spectrum CZT
+def asczt_propagate(u: torch.Tensor, grid, window, wavelength: float, z,
+                    out: torch.Tensor | None = None):
+    """Angular-spectrum CZT: [B][ny][nx] (or [ny][nx]) -> [B][my][mx] on the window."""
+    _dev(u, "u")
+    B, ny, nx = _planes(u, 1, "u")
+    g, w = Grid.of(grid), Window.of(window)
+    if out is None:
+        shape = (w.my, w.mx) if u.dim() == 2 else (B, w.my, w.mx)
+        out = torch.empty(shape, dtype=u.dtype, device=u.device)
+    zz = _Z(z, B)
+    _check(load().xl_asczt_propagate(u.data_ptr(), _dev(out, "out").data_ptr(), B, ctypes.byref(g),
+                                     ctypes.byref(w), float(wavelength), zz.ptr, zz.flags,
+                                     _dtype(u), _stream()))
+    return out
+
+
+def asczt_propagate_backward(g_out: torch.Tensor, u_in: torch.Tensor | None, grid, window,
+                             wavelength: float, z, want_field: bool = True, want_dz: bool = False):
+    """Adjoint of asczt_propagate: returns (g_in [B][ny][nx] or None, g_z [B] or None)."""
+    _dev(g_out, "g_out")
+    g, w = Grid.of(grid), Window.of(window)
+    B = g_out.shape[0] if g_out.dim() == 3 else 1
+    g_in = None
+    if want_field:
+        shape = (g.ny, g.nx) if g_out.dim() == 2 else (B, g.ny, g.nx)
+        g_in = torch.empty(shape, dtype=g_out.dtype, device=g_out.device)
+    g_z = torch.empty(B, dtype=torch.float64, device=g_out.device) if want_dz else None
+    zz = _Z(z, B)
+    _check(load().xl_asczt_propagate_backward(
+        g_out.data_ptr(), _dev(u_in, "u_in").data_ptr() if u_in is not None else None,
+        g_in.data_ptr() if g_in is not None else None, g_z.data_ptr() if g_z is not None else None,
+        B, ctypes.byref(g), ctypes.byref(w), float(wavelength), zz.ptr, zz.flags, _dtype(g_out),
+        _stream()))
+    return g_in, g_z
 
 
 # ----------------------------------------------------------------------------- beam splitters
