@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--impl", default="xl", choices=["xl", "reference"])
     p.add_argument("--batch", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-next", action="store_true", help="skip the angular-spectrum CZT and "
+                   "beam-splitter measurements")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-table", action="store_true", help="skip the batched optical-table section")
     p.add_argument("--table-setups", type=int, default=256)
@@ -255,6 +257,60 @@ def table_section(xl, torch, setups: int, steps: int, seed: int):
             "fp64_ms_per_setup": f64,
             "table1024_grads_per_s": 1000.0 / ms1024,
             "speedup_vs_fp64_single_instance": t64 / ms}
+
+
+# ----------------------------------------------------------------------------- further rows
+def next_rows_section(xl, torch, g, w, U_dev, zs, hbm_gbs: float, steps: int = 10):
+    """Device throughput of the rows beyond the headline step, on the same 2048^2 inputs:
+    the angular-spectrum CZT onto the 512^2 window (forward + adjoint with distance gradient)
+    and the beam splitter (forward and adjoint with the ratio gradient) on [B][2][2048^2]
+    fields, the latter against the measured HBM bandwidth (it moves each pixel once)."""
+    from paper_2310_08408_gb300 import inputs
+    B = U_dev.shape[0]
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    G = torch.from_numpy(inputs.random_unit(9, (1, M, M)).astype(np.complex64)).cuda().expand(B, M, M).contiguous()
+
+    def timed(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    def as_step():
+        xl.asczt_propagate(U_dev, g, w, LAM, zs)
+        xl.asczt_propagate_backward(G, U_dev, g, w, LAM, zs, want_field=True, want_dz=True)
+
+    ms_as = timed(as_step, steps)
+    xl.profile_enable(True)
+    as_step()
+    torch.cuda.synchronize()
+    prof = xl.profile_report()
+    xl.profile_enable(False)
+    kern = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}
+    # beam splitter on two-component fields
+    a = U_dev.unsqueeze(1).expand(B, 2, N, N).contiguous()
+    b = torch.flip(a, dims=[3]).contiguous()
+    ot, orr = torch.empty_like(a), torch.empty_like(a)
+    R = torch.linspace(0.2, 0.8, B, dtype=torch.float64, device="cuda")
+    nbytes = a.numel() * a.element_size()
+    ms_f = timed(lambda: xl.beam_splitter(a, b, R, out_t=ot, out_r=orr), steps)
+    ms_b = timed(lambda: xl.beam_splitter_backward(ot, orr, a, b, R), steps)
+    del a, b, ot, orr
+    fwd_gbs = 4 * nbytes / (ms_f / 1000.0) / 1e9
+    bwd_gbs = 6 * nbytes / (ms_b / 1000.0) / 1e9
+    return {"asczt": {"workload": f"{B} x 2048^2 -> 512^2 over 64 um, z cycling {{0.5, 2, 10}} mm, "
+                                  "forward + adjoint + dz", "propagations_per_s": 2 * B / (ms_as / 1000.0),
+                      "ms_per_step": ms_as, "kernels": kern},
+            "beam_splitter": {"workload": f"{B} x 2 x 2048^2 complex64 per port",
+                              "fwd_ms": ms_f, "fwd_gbs": fwd_gbs, "bwd_ms": ms_b, "bwd_gbs": bwd_gbs,
+                              "fwd_frac_of_measured_hbm": fwd_gbs / hbm_gbs,
+                              "bwd_frac_of_measured_hbm": bwd_gbs / hbm_gbs,
+                              "bytes": "fwd 2 fields read + 2 written; bwd 4 read + 2 written"}}
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -477,6 +533,10 @@ def main():
                "d2h_bytes_per_step": int(A_h.numel() * 8 + C_h.numel() * 8 + gz_h.numel() * 8),
                "ms_per_step": ems / ke}
 
+    nxt = None
+    if not a.no_next:
+        nxt = next_rows_section(xl, torch, g, w, U_dev, zs, hbm)
+
     table = None
     if not a.no_table:
         table = table_section(xl, torch, a.table_setups, a.table_steps, inputs_seed(rank))
@@ -501,6 +561,7 @@ def main():
             "grads_per_s": grads,
             "batch1": batch1,
             "tables": table,
+            "next_rows": nxt,
             "step_parts": step_parts(xl),
             "gpu_launches": int(launches),
             "clocks": ck,

@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(kThreads) k_bs_bwd(const cplx<T>* __restrict__
   const T t = (T)td, r = (T)rd;
   const T dt = (T)(-0.5 / td), dr = (T)(0.5 / rd);
   const int64_t base = (int64_t)e * n;
-  double acc = 0.0;
+  // per-thread sums in T (a few tens of terms), the block and batch sums in double
+  T acc = (T)0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const C gt = g_t ? g_t[base + i] : mk((T)0, (T)0);
     const C gr = g_r ? g_r[base + i] : mk((T)0, (T)0);
@@ -74,11 +75,11 @@ __global__ void __launch_bounds__(kThreads) k_bs_bwd(const cplx<T>* __restrict__
       const C bv = b ? b[base + i] : mk((T)0, (T)0);
       const C dot = mk(dt * av.x - dr * bv.y, dt * av.y + dr * bv.x);   // dt a + i dr b
       const C dor = mk(dt * bv.x - dr * av.y, dt * bv.y + dr * av.x);   // i dr a + dt b
-      acc += (double)(gt.x * dot.x + gt.y * dot.y) + (double)(gr.x * dor.x + gr.y * dor.y);
+      acc += (gt.x * dot.x + gt.y * dot.y) + (gr.x * dor.x + gr.y * dor.y);
     }
   }
   if (part) {
-    const double s = warp_block_sum(acc, sbuf);
+    const double s = warp_block_sum((double)acc, sbuf);
     if (threadIdx.x == 0) part[(int64_t)e * gridDim.x + blockIdx.x] = s;
   }
 }
