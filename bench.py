@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--impl", default="xl", choices=["xl", "reference"])
     p.add_argument("--batch", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-autotune", action="store_true", help="run the built-in launch plan")
     p.add_argument("--no-next", action="store_true", help="skip the angular-spectrum CZT and "
                    "beam-splitter measurements")
     p.add_argument("--no-e2e", action="store_true")
@@ -200,6 +201,13 @@ class GpuStep:
 # ----------------------------------------------------------------------------- optical tables
 TABLE_CFG = dict(wavelength=0.6328, extent=1024.0, w0=200.0, f=5000.0, cam_m=256, cam_width=64.0,
                  lr=0.01, lr_z=1.0)
+TABLE_WINDOW = (256, 256, 0.25, 0.25, -32.0, -32.0)  # the tables' camera window
+
+
+def inputs_grid(n: int):
+    """The centred grid of side n: pitch 0.5 um at the headline size, 1024 um / n for the tables."""
+    from paper_2310_08408_gb300 import inputs
+    return inputs.Grid.centred(n, PITCH if n == N else 1024.0 / n)
 
 
 def table_section(xl, torch, setups: int, steps: int, seed: int):
@@ -404,6 +412,20 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    # launch plan: the autotuner's rows-per-block choice for every pass of this grid and window
+    # (untimed set-up; results are identical for every choice)
+    tune = None
+    if not a.no_autotune:
+        for grid_n in ((N,) if a.no_table else (N, 512, 1024)):
+            gt = inputs_grid(grid_n)
+            xl.autotune(gt, w if grid_n == N else TABLE_WINDOW, xl.C64, reps=5)
+        import tempfile
+        fd, tpath = tempfile.mkstemp(suffix=".txt")
+        os.close(fd)
+        xl.tune_save(tpath)
+        tune = [ln for ln in open(tpath).read().splitlines() if not ln.startswith("#")]
+        os.unlink(tpath)
+
     clocks = Clocks(local)
     for _ in range(a.warmup):
         step()
@@ -562,6 +584,7 @@ def main():
             "batch1": batch1,
             "tables": table,
             "next_rows": nxt,
+            "autotune": tune,
             "step_parts": step_parts(xl),
             "gpu_launches": int(launches),
             "clocks": ck,

@@ -361,6 +361,36 @@ xl_status xl_softmin(const double* losses, int32_t batch, int32_t n_det, double 
 xl_status xl_device_status(void* stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Autotuner of the transposing row passes (the batch scheduler's launch plan; the paper has no
+ * counterpart: its JAX/XLA back end picks launch shapes itself). Families (XL_TUNE_*): RS passes
+ * 1 and 3 and the four CZT window passes; variants: 0 the built-in rows per block, 1 half as
+ * many, 2 twice as many where a block stays within 1024 threads and an SM's shared memory. All
+ * variants give bit-identical results; only speed differs. Rows shorter than 1024 always use
+ * variant 0. Choices are process-wide (host memory).
+ * -------------------------------------------------------------------------------------------*/
+#define XL_TUNE_RS_PASS1 0
+#define XL_TUNE_RS_PASS3 1
+#define XL_TUNE_CZT_FWD_X 2
+#define XL_TUNE_CZT_FWD_Y 3
+#define XL_TUNE_CZT_ADJ_X 4
+#define XL_TUNE_CZT_ADJ_Y 5
+
+/* Times every variant of the passes a grid (and, when window is non-NULL, a CZT onto that
+ * window) uses, `reps` launches each on `stream` with synthetic data (allocates and frees its own
+ * device buffers, synchronises `stream`), and keeps the fastest. */
+xl_status xl_autotune(const xl_grid* grid, const xl_window* window, int32_t dtype, int32_t reps,
+                      void* stream);
+/* The variant used for (family, row length L, dtype): 0..2, or -1 for an unknown family. */
+int32_t xl_tune_get(int32_t family, int32_t L, int32_t dtype);
+/* Sets a variant by hand (XL_ERR_ARG for an unknown family, L, dtype or variant). */
+xl_status xl_tune_set(int32_t family, int32_t L, int32_t dtype, int32_t variant);
+xl_status xl_tune_clear(void);
+/* Text file of the choices, one "family L dtype variant microseconds" line each. Loading a
+ * malformed file returns XL_ERR_ARG and applies nothing. */
+xl_status xl_tune_save(const char* path);
+xl_status xl_tune_load(const char* path);
+
+/* ---------------------------------------------------------------------------------------------
  * Beam splitters (Results, "Towards large-scale discovery"; Methods, "The large-scale search
  * space": beam splitters with a continuous ratio in [0, 1] connect the paths of the table).
  * Reading: lossless and non-polarising, R = reflected intensity fraction, t = sqrt(1 - R),

@@ -1,49 +1,51 @@
 // Definitions of the CZT launchers for one precision; included with XL_REAL defined.
+// The window-pass kernels of each transform length are instantiated in part files
+// (XL_CZT_LENGTHS defined: xl_czt_c64_*.cu / xl_czt_c128_*.cu) so that they compile in
+// parallel; the dispatching file (XL_CZT_LENGTHS undefined) holds the switch, the chirp-table
+// launchers and extern declarations of those instantiations.
 #include "xl_czt_launch.h"
 
 namespace xl {
 
-namespace {
-
-template <typename T, int L, bool VEC>
-xl_status pass_LV(int which, const void* src, void* dst, const CztDims& d, const Axis<cplx<T>>& ax,
-                  int nb, cudaStream_t s) {
-  constexpr int ROWS = czt_rows<L, sizeof(cplx<T>), VEC>();
-  const size_t sm = czt_smem_bytes<L, sizeof(cplx<T>), VEC>();
+template <typename T, int L, bool VEC, int V>
+xl_status pass_LVV(int which, const void* src, void* dst, const CztDims& d, const Axis<cplx<T>>& ax,
+                   int nb, cudaStream_t s) {
+  constexpr int ROWS = czt_rows<L, sizeof(cplx<T>), VEC, V>();
+  const size_t sm = czt_smem_bytes<L, sizeof(cplx<T>), VEC, V>();
   const void* tw;
   XL_TRY(twiddles(L, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
   const cplx<T>* twc = (const cplx<T>*)tw;
   const dim3 blk(ROWS * (L / 16));
   switch (which) {
     case CZT_FWD_X:
-      XL_TRY(smem_attr((const void*)k_czt_fwd_x<T, L, VEC>, sm));
+      XL_TRY(smem_attr((const void*)k_czt_fwd_x<T, L, VEC, V>, sm));
       {
       LaunchScope ls(std::string("czt_fwd_x") + (VEC ? "_vec<" : "<") + std::to_string(L) + ">", s);
-      k_czt_fwd_x<T, L, VEC><<<dim3((d.ny + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
+      k_czt_fwd_x<T, L, VEC, V><<<dim3((d.ny + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
           (const cplx<T>*)src, (cplx<T>*)dst, d, ax, twc);
       }
       break;
     case CZT_FWD_Y:
-      XL_TRY(smem_attr((const void*)k_czt_fwd_y<T, L, VEC>, sm));
+      XL_TRY(smem_attr((const void*)k_czt_fwd_y<T, L, VEC, V>, sm));
       {
       LaunchScope ls(std::string("czt_fwd_y") + (VEC ? "_vec<" : "<") + std::to_string(L) + ">", s);
-      k_czt_fwd_y<T, L, VEC><<<dim3((d.mx + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
+      k_czt_fwd_y<T, L, VEC, V><<<dim3((d.mx + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
           (const cplx<T>*)src, (cplx<T>*)dst, d, ax, twc);
       }
       break;
     case CZT_ADJ_Y:
-      XL_TRY(smem_attr((const void*)k_czt_adj_y<T, L, VEC>, sm));
+      XL_TRY(smem_attr((const void*)k_czt_adj_y<T, L, VEC, V>, sm));
       {
       LaunchScope ls(std::string("czt_adj_y") + (VEC ? "_vec<" : "<") + std::to_string(L) + ">", s);
-      k_czt_adj_y<T, L, VEC><<<dim3((d.mx + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
+      k_czt_adj_y<T, L, VEC, V><<<dim3((d.mx + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
           (const cplx<T>*)src, (cplx<T>*)dst, d, ax, twc);
       }
       break;
     case CZT_ADJ_X:
-      XL_TRY(smem_attr((const void*)k_czt_adj_x<T, L, VEC>, sm));
+      XL_TRY(smem_attr((const void*)k_czt_adj_x<T, L, VEC, V>, sm));
       {
       LaunchScope ls(std::string("czt_adj_x") + (VEC ? "_vec<" : "<") + std::to_string(L) + ">", s);
-      k_czt_adj_x<T, L, VEC><<<dim3((d.ny + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
+      k_czt_adj_x<T, L, VEC, V><<<dim3((d.ny + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
           (const cplx<T>*)src, (cplx<T>*)dst, d, ax, twc);
       }
       break;
@@ -53,6 +55,40 @@ xl_status pass_LV(int which, const void* src, void* dst, const CztDims& d, const
   XL_CUDA_TRY(cudaGetLastError());
   return XL_OK;
 }
+
+// The autotuner's variant for this pass and length (scalar passes of long rows only).
+template <typename T, int L, bool VEC>
+xl_status pass_LV(int which, const void* src, void* dst, const CztDims& d, const Axis<cplx<T>>& ax,
+                  int nb, cudaStream_t s) {
+  if constexpr (!VEC && L >= kTuneMinL) {
+    const int fam = which == CZT_FWD_X ? TUNE_CZT_FWD_X : which == CZT_FWD_Y ? TUNE_CZT_FWD_Y
+                  : which == CZT_ADJ_X ? TUNE_CZT_ADJ_X : TUNE_CZT_ADJ_Y;
+    switch (tuned_variant(fam, L, sizeof(T) == 8 ? XL_C128 : XL_C64)) {
+      case 1: return pass_LVV<T, L, VEC, 1>(which, src, dst, d, ax, nb, s);
+      case 2: return pass_LVV<T, L, VEC, 2>(which, src, dst, d, ax, nb, s);
+    }
+  }
+  return pass_LVV<T, L, VEC, 0>(which, src, dst, d, ax, nb, s);
+}
+
+#define XL_CZT_PASS_SIG(LL, VV)                                                                    \
+  xl_status pass_LV<XL_REAL, LL, VV>(int, const void*, void*, const CztDims&, const Axis<cplx<XL_REAL>>&, \
+                                     int, cudaStream_t)
+#define XL_CZT_INSTANTIATE(LL) \
+  template XL_CZT_PASS_SIG(LL, false); \
+  template XL_CZT_PASS_SIG(LL, true);
+#define XL_CZT_EXTERN(LL) \
+  extern template XL_CZT_PASS_SIG(LL, false); \
+  extern template XL_CZT_PASS_SIG(LL, true);
+
+#ifdef XL_CZT_LENGTHS
+XL_CZT_LENGTHS(XL_CZT_INSTANTIATE)
+}  // namespace xl
+#else
+XL_CZT_EXTERN(64) XL_CZT_EXTERN(128) XL_CZT_EXTERN(256) XL_CZT_EXTERN(512)
+XL_CZT_EXTERN(1024) XL_CZT_EXTERN(2048) XL_CZT_EXTERN(4096) XL_CZT_EXTERN(8192)
+
+namespace {
 
 template <typename T, int L>
 xl_status bhat_L(cplx<T>* rows, int64_t stride, cudaStream_t s) {
@@ -130,3 +166,4 @@ xl_status asczt_tables<XL_REAL>(void* tab, const CztTabArgs& a, cudaStream_t s) 
 }
 
 }  // namespace xl
+#endif  // XL_CZT_LENGTHS

@@ -57,25 +57,29 @@ struct CztDims {
 // fits (in registers otherwise), so that the transforms do not spill. Their loops over the 2-3
 // planes are unrolled on purpose: as runtime loops, the compiler hoisted loop-invariant work of
 // the transforms out of them and spilled 400-600 bytes a thread.
-template <int L, int CS, bool VEC = false> __host__ __device__ constexpr int czt_rows() {
+// Scalar passes also build the autotuner's variants V (rows per block: 1 = half the default,
+// 2 = twice the default where a block stays within 1024 threads and an SM's shared memory).
+template <int L, int CS, bool VEC = false, int V = 0> __host__ __device__ constexpr int czt_rows() {
   constexpr int r = CS == 8 ? (L >= 4096 ? 2 : ((4096 / L) > 4 ? 4096 / L : 4))
                             : (L >= 8192 ? 1 : ((4096 / L) > 2 ? 4096 / L : 2));
-  return VEC ? (r / 4 > 1 ? r / 4 : 1) : r;
+  constexpr bool dbl = 2 * r * (L / 16) <= 1024 && (size_t)2 * r * rpitch(L) * CS <= (size_t)227 * 1024 &&
+                       team_barriers_fit<L>(2 * r * (L / 16));
+  return VEC ? (r / 4 > 1 ? r / 4 : 1) : (V == 1 ? (r / 2 > 1 ? r / 2 : 1) : (V == 2 && dbl ? 2 * r : r));
 }
-template <int L, int CS, bool VEC> __host__ __device__ constexpr bool czt_stash_smem() {
-  return VEC && (size_t)2 * czt_rows<L, CS, VEC>() * rpitch(L) * CS <= (size_t)227 * 1024;
+template <int L, int CS, bool VEC, int V = 0> __host__ __device__ constexpr bool czt_stash_smem() {
+  return VEC && (size_t)2 * czt_rows<L, CS, VEC, V>() * rpitch(L) * CS <= (size_t)227 * 1024;
 }
-template <int L, int CS, bool VEC> __host__ __device__ constexpr size_t czt_smem_bytes() {
-  return (size_t)czt_rows<L, CS, VEC>() * (czt_stash_smem<L, CS, VEC>() ? 2 : 1) * rpitch(L) * CS;
+template <int L, int CS, bool VEC, int V = 0> __host__ __device__ constexpr size_t czt_smem_bytes() {
+  return (size_t)czt_rows<L, CS, VEC, V>() * (czt_stash_smem<L, CS, VEC, V>() ? 2 : 1) * rpitch(L) * CS;
 }
-template <int L, int CS, bool VEC> __host__ __device__ constexpr int czt_threads() {
-  return czt_rows<L, CS, VEC>() * (L / 16);
+template <int L, int CS, bool VEC, int V = 0> __host__ __device__ constexpr int czt_threads() {
+  return czt_rows<L, CS, VEC, V>() * (L / 16);
 }
 // Resident blocks per SM the register budget aims at: up to 1024 threads, as shared memory allows
 // (1 KB of each block's shared memory is reserved by the runtime).
-template <int L, int CS, bool VEC> __host__ __device__ constexpr int czt_min_blocks() {
-  constexpr int by_threads = 1024 / czt_threads<L, CS, VEC>() > 1 ? 1024 / czt_threads<L, CS, VEC>() : 1;
-  constexpr int by_smem = (int)(((size_t)228 * 1024) / (czt_smem_bytes<L, CS, VEC>() + 1024));
+template <int L, int CS, bool VEC, int V = 0> __host__ __device__ constexpr int czt_min_blocks() {
+  constexpr int by_threads = 1024 / czt_threads<L, CS, VEC, V>() > 1 ? 1024 / czt_threads<L, CS, VEC, V>() : 1;
+  constexpr int by_smem = (int)(((size_t)228 * 1024) / (czt_smem_bytes<L, CS, VEC, V>() + 1024));
   return by_smem < 1 ? 1 : (by_smem < by_threads ? by_smem : by_threads);
 }
 
@@ -134,8 +138,8 @@ __device__ __forceinline__ void load_transposed(C (&v)[16], C* sm, int team, int
 
 __device__ __forceinline__ double czt_z(const CztDims& d) { return d.zdev ? *d.zdev : d.zval; }
 
-#define XL_CZT_BOUNDS(T, L, VEC) \
-  __launch_bounds__(czt_threads<L, sizeof(cplx<T>), VEC>(), czt_min_blocks<L, sizeof(cplx<T>), VEC>())
+#define XL_CZT_BOUNDS(T, L, VEC, V) \
+  __launch_bounds__(czt_threads<L, sizeof(cplx<T>), VEC, V>(), czt_min_blocks<L, sizeof(cplx<T>), VEC, V>())
 
 // Coordinates of the samples a thread holds, s0 + (t + q L/16) D, as base + q step in T (one
 // double-precision operation per row instead of one per sample: FP64 runs at a small fraction
@@ -150,12 +154,12 @@ template <typename T> struct Coord {
 // Forward x pass. Planes of element b: input cin (1 or 2), T planes cT (1 or 3). For VEC the
 // third T plane is the transform of S = x Ex + y Ey.
 // grid: (ceil(ny / ROWS), nbatch). T plane layout: [mx][ny] (row p holds all n).
-template <typename T, int L, bool VEC>
-__global__ void XL_CZT_BOUNDS(T, L, VEC)
+template <typename T, int L, bool VEC, int V = 0>
+__global__ void XL_CZT_BOUNDS(T, L, VEC, V)
 k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d, Axis<cplx<T>> ax,
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
-  constexpr int ROWS = czt_rows<L, sizeof(C), VEC>();
+  constexpr int ROWS = czt_rows<L, sizeof(C), VEC, V>();
   static_assert(team_barriers_fit<L>(ROWS * (L / 16)), "too many teams for the named barriers");
   constexpr int TT = L / 16;
   constexpr int SR = rpitch(L);
@@ -200,12 +204,12 @@ k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d,
 // For VEC the y pass forms Ez' = -(1/z)(X_p Ex' + Y_q Ey' - S'), accumulating X_p Ex' + Y_q Ey'
 // in the thread's stash.
 // grid: (ceil(mx / ROWS), nbatch).
-template <typename T, int L, bool VEC>
-__global__ void XL_CZT_BOUNDS(T, L, VEC)
+template <typename T, int L, bool VEC, int V = 0>
+__global__ void XL_CZT_BOUNDS(T, L, VEC, V)
 k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d, Axis<cplx<T>> ay,
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
-  constexpr int ROWS = czt_rows<L, sizeof(C), VEC>();
+  constexpr int ROWS = czt_rows<L, sizeof(C), VEC, V>();
   static_assert(team_barriers_fit<L>(ROWS * (L / 16)), "too many teams for the named barriers");
   constexpr int TT = L / 16;
   constexpr int SR = rpitch(L);
@@ -218,7 +222,7 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
   const int cT = VEC ? 3 : 1;
   const int64_t tplane = (int64_t)d.mx * d.ny, oplane = (int64_t)d.mx * d.my;
   C* row = sm + team * SR;
-  Stash<C, TT, czt_stash_smem<L, sizeof(C), VEC>()> acc;
+  Stash<C, TT, czt_stash_smem<L, sizeof(C), VEC, V>()> acc;
   acc.init(sm + (ROWS + team) * SR, t);
   T Xp = (T)0, iz = (T)0;
   if constexpr (VEC) {
@@ -262,14 +266,14 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
 // VEC: T planes A = C_y^H(Gx - (X_p/z) Gz), B = C_y^H(Gy - (Y_q/z) Gz), Z = C_y^H(Gz); Gz is
 // loaded once into the thread's stash.
 // grid: (ceil(mx / ROWS), nbatch).
-template <typename T, int L, bool VEC>
-__global__ void XL_CZT_BOUNDS(T, L, VEC)
+template <typename T, int L, bool VEC, int V = 0>
+__global__ void XL_CZT_BOUNDS(T, L, VEC, V)
 k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, Axis<cplx<T>> ay,
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
-  constexpr int ROWS = czt_rows<L, sizeof(C), VEC>();
+  constexpr int ROWS = czt_rows<L, sizeof(C), VEC, V>();
   static_assert(team_barriers_fit<L>(ROWS * (L / 16)), "too many teams for the named barriers");
-  constexpr bool SMST = czt_stash_smem<L, sizeof(C), VEC>();
+  constexpr bool SMST = czt_stash_smem<L, sizeof(C), VEC, V>();
   constexpr int TT = L / 16;
   constexpr int SR = rpitch(L);
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -336,12 +340,12 @@ k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, 
 // VEC: g_Ex = C_x^H(A) + (x/z) C_x^H(Z), g_Ey = C_x^H(B) + (y/z) C_x^H(Z); (1/z) C_x^H(Z) is
 // transformed first and kept in the thread's stash.
 // grid: (ceil(ny / ROWS), nbatch).
-template <typename T, int L, bool VEC>
-__global__ void XL_CZT_BOUNDS(T, L, VEC)
+template <typename T, int L, bool VEC, int V = 0>
+__global__ void XL_CZT_BOUNDS(T, L, VEC, V)
 k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d, Axis<cplx<T>> ax,
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
-  constexpr int ROWS = czt_rows<L, sizeof(C), VEC>();
+  constexpr int ROWS = czt_rows<L, sizeof(C), VEC, V>();
   static_assert(team_barriers_fit<L>(ROWS * (L / 16)), "too many teams for the named barriers");
   constexpr int TT = L / 16;
   constexpr int SR = rpitch(L);
@@ -355,7 +359,7 @@ k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d
   const int cT = VEC ? 3 : 1, cout = VEC ? 2 : 1;
   const int64_t tplane = (int64_t)d.mx * d.ny, plane = (int64_t)d.nx * d.ny;
   C* row = sm + team * SR;
-  Stash<C, TT, czt_stash_smem<L, sizeof(C), VEC>()> zz;
+  Stash<C, TT, czt_stash_smem<L, sizeof(C), VEC, V>()> zz;
   zz.init(sm + (ROWS + team) * SR, t);
   const Coord<T> xm(d.x0, d.dx, t, TT);
   const T yn = (T)(d.y0 + n * d.dy);

@@ -6,17 +6,45 @@ namespace xl {
 
 namespace {
 
-template <typename T, int LX>
-xl_status pass1_L(const void* in, void* Tb, int nx, int ny, int cin, int cT, int np, cudaStream_t s) {
-  constexpr int ROWS = rows_transp<LX, sizeof(cplx<T>)>();
+template <typename T, int LX, int V>
+xl_status pass1_LV(const void* in, void* Tb, int nx, int ny, int cin, int cT, int np, cudaStream_t s) {
+  constexpr int ROWS = rows_p1v<LX, sizeof(cplx<T>), V>();
   const size_t sm = (size_t)ROWS * rpitch(LX) * sizeof(cplx<T>);
   const void* tw;
   XL_TRY(twiddles(LX, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
-  XL_TRY(smem_attr((const void*)k_rs_pass1<T, LX>, sm));
+  XL_TRY(smem_attr((const void*)k_rs_pass1<T, LX, V>, sm));
   dim3 grid((ny + ROWS - 1) / ROWS, np);
   LaunchScope ls("rs_pass1<" + std::to_string(LX) + ">", s);
-  k_rs_pass1<T, LX><<<grid, ROWS * (LX / 16), sm, s>>>(
+  k_rs_pass1<T, LX, V><<<grid, ROWS * (LX / 16), sm, s>>>(
       (const cplx<T>*)in, (cplx<T>*)Tb, nx, ny, cin, cT, (const cplx<T>*)tw);
+  XL_CUDA_TRY(cudaGetLastError());
+  return XL_OK;
+}
+
+// the autotuner's variant of this length (only long rows have more than the default)
+template <typename T, int LX>
+xl_status pass1_L(const void* in, void* Tb, int nx, int ny, int cin, int cT, int np, cudaStream_t s) {
+  if constexpr (LX >= kTuneMinL) {
+    switch (tuned_variant(TUNE_RS_PASS1, LX, sizeof(T) == 8 ? XL_C128 : XL_C64)) {
+      case 1: return pass1_LV<T, LX, 1>(in, Tb, nx, ny, cin, cT, np, s);
+      case 2: return pass1_LV<T, LX, 2>(in, Tb, nx, ny, cin, cT, np, s);
+    }
+  }
+  return pass1_LV<T, LX, 0>(in, Tb, nx, ny, cin, cT, np, s);
+}
+
+template <typename T, int LX, int V>
+xl_status pass3_LV(const void* Tb, void* out, int nx, int ny, int cout, int cT, int np, cudaStream_t s,
+                   DzReduce red) {
+  constexpr int ROWS = rows_p3v<LX, sizeof(cplx<T>), V>();
+  const size_t sm = (size_t)ROWS * rpitch(LX) * sizeof(cplx<T>);
+  const void* tw;
+  XL_TRY(twiddles(LX, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
+  XL_TRY(smem_attr((const void*)k_rs_pass3<T, LX, V>, sm));
+  dim3 grid((ny + ROWS - 1) / ROWS, np);
+  LaunchScope ls("rs_pass3<" + std::to_string(LX) + ">", s);
+  k_rs_pass3<T, LX, V><<<grid, ROWS * (LX / 16), sm, s>>>(
+      (const cplx<T>*)Tb, (cplx<T>*)out, nx, ny, cout, cT, (const cplx<T>*)tw, red);
   XL_CUDA_TRY(cudaGetLastError());
   return XL_OK;
 }
@@ -24,17 +52,13 @@ xl_status pass1_L(const void* in, void* Tb, int nx, int ny, int cin, int cT, int
 template <typename T, int LX>
 xl_status pass3_L(const void* Tb, void* out, int nx, int ny, int cout, int cT, int np, cudaStream_t s,
                   DzReduce red) {
-  constexpr int ROWS = rows_p3<LX, sizeof(cplx<T>)>();
-  const size_t sm = (size_t)ROWS * rpitch(LX) * sizeof(cplx<T>);
-  const void* tw;
-  XL_TRY(twiddles(LX, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
-  XL_TRY(smem_attr((const void*)k_rs_pass3<T, LX>, sm));
-  dim3 grid((ny + ROWS - 1) / ROWS, np);
-  LaunchScope ls("rs_pass3<" + std::to_string(LX) + ">", s);
-  k_rs_pass3<T, LX><<<grid, ROWS * (LX / 16), sm, s>>>(
-      (const cplx<T>*)Tb, (cplx<T>*)out, nx, ny, cout, cT, (const cplx<T>*)tw, red);
-  XL_CUDA_TRY(cudaGetLastError());
-  return XL_OK;
+  if constexpr (LX >= kTuneMinL) {
+    switch (tuned_variant(TUNE_RS_PASS3, LX, sizeof(T) == 8 ? XL_C128 : XL_C64)) {
+      case 1: return pass3_LV<T, LX, 1>(Tb, out, nx, ny, cout, cT, np, s, red);
+      case 2: return pass3_LV<T, LX, 2>(Tb, out, nx, ny, cout, cT, np, s, red);
+    }
+  }
+  return pass3_LV<T, LX, 0>(Tb, out, nx, ny, cout, cT, np, s, red);
 }
 
 template <typename T, int LY, int MODE>

@@ -49,6 +49,23 @@ template <int THREADS, int CS> __host__ __device__ constexpr int min_blocks_rows
 }
 template <int L> __host__ __device__ constexpr int rows_cols() { return (4096 / L) > 1 ? 4096 / L : 1; }
 
+// Rows per block of autotuner variant V of a transposing pass whose default is R rows: 0 the
+// default, 1 half as many, 2 twice as many when the block stays within 1024 threads, the shared
+// memory of an SM and the named team barriers (otherwise the default).
+template <int R, int L, int CS, int V> __host__ __device__ constexpr int rows_variant() {
+  return V == 1 ? (R / 2 > 1 ? R / 2 : 1)
+                : (V == 2 && 2 * R * (L / 16) <= 1024 && (size_t)2 * R * rpitch(L) * CS <= (size_t)227 * 1024 &&
+                           team_barriers_fit<L>(2 * R * (L / 16))
+                       ? 2 * R
+                       : R);
+}
+template <int L, int CS, int V> __host__ __device__ constexpr int rows_p1v() {
+  return rows_variant<rows_transp<L, CS>(), L, CS, V>();
+}
+template <int L, int CS, int V> __host__ __device__ constexpr int rows_p3v() {
+  return rows_variant<rows_p3<L, CS>(), L, CS, V>();
+}
+
 // ---------------------------------------------------------------------------------------------
 // Spectrum access: value of spectrum `kind` at full-grid frequency (kx, ky), kx < LX, ky < LY.
 template <typename C>
@@ -65,13 +82,13 @@ __device__ __forceinline__ C spec_at(const C* __restrict__ Hk, int kx, int ky, i
 // ---------------------------------------------------------------------------------------------
 // Pass 1: row FFT (forward) of planes [ny][nx] into T[kx][y].
 // Plane p of the input maps to plane (p / cin) * cT + (p % cin) of the T buffer.
-template <typename T, int LX>
-__global__ void __launch_bounds__(rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16),
-                                  min_blocks_rows<rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16), sizeof(cplx<T>)>())
+template <typename T, int LX, int V = 0>
+__global__ void __launch_bounds__(rows_p1v<LX, sizeof(cplx<T>), V>() * (LX / 16),
+                                  min_blocks_rows<rows_p1v<LX, sizeof(cplx<T>), V>() * (LX / 16), sizeof(cplx<T>)>())
 k_rs_pass1(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, int nx, int ny, int cin,
            int cT, const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
-  constexpr int ROWS = rows_transp<LX, sizeof(C)>();
+  constexpr int ROWS = rows_p1v<LX, sizeof(C), V>();
   static_assert(team_barriers_fit<LX>(ROWS * (LX / 16)), "too many teams for the named barriers");
   constexpr int TT = LX / 16;
   constexpr int P = rpitch(LX);
@@ -120,13 +137,13 @@ struct DzReduce {
 
 // Pass 3: inverse row FFT from T[kx][y] into planes [ny][nx] (crop to x < nx).
 // Plane p of the output maps to plane (p / cout) * cT + (p % cout) of T.
-template <typename T, int LX>
-__global__ void __launch_bounds__(rows_p3<LX, sizeof(cplx<T>)>() * (LX / 16),
-                                  min_blocks_rows<rows_p3<LX, sizeof(cplx<T>)>() * (LX / 16), sizeof(cplx<T>)>())
+template <typename T, int LX, int V = 0>
+__global__ void __launch_bounds__(rows_p3v<LX, sizeof(cplx<T>), V>() * (LX / 16),
+                                  min_blocks_rows<rows_p3v<LX, sizeof(cplx<T>), V>() * (LX / 16), sizeof(cplx<T>)>())
 k_rs_pass3(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, int nx, int ny, int cout,
            int cT, const cplx<T>* __restrict__ tw, DzReduce red) {
   typedef cplx<T> C;
-  constexpr int ROWS = rows_p3<LX, sizeof(C)>();
+  constexpr int ROWS = rows_p3v<LX, sizeof(C), V>();
   static_assert(team_barriers_fit<LX>(ROWS * (LX / 16)), "too many teams for the named barriers");
   constexpr int TT = LX / 16;
   constexpr int P = rpitch(LX);

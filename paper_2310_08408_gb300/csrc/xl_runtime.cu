@@ -3,6 +3,7 @@
 #include <cstring>
 #include <list>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <unordered_map>
 #include <vector>
@@ -70,6 +71,54 @@ DeviceState& cur(int* dev_out = nullptr) {
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// Autotuner choices: (family, L, dtype) -> (variant, measured microseconds). Process-wide (the
+// variants are properties of the kernels, and the library serves one GPU model per process).
+namespace {
+struct TuneEntry {
+  int variant;
+  double us;
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, TuneEntry> g_tune;
+const char* const kTuneNames[TUNE_NFAMILY] = {"rs_pass1", "rs_pass3", "czt_fwd_x",
+                                              "czt_fwd_y", "czt_adj_x", "czt_adj_y"};
+}  // namespace
+
+const char* tune_family_name(int family) {
+  return family >= 0 && family < TUNE_NFAMILY ? kTuneNames[family] : "?";
+}
+
+int tuned_variant(int family, int L, int dtype) {
+  if (L < kTuneMinL) return 0;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(std::make_tuple(family, L, dtype));
+  return it == g_tune.end() ? 0 : it->second.variant;
+}
+
+void set_tuned_variant(int family, int L, int dtype, int variant, double us) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[std::make_tuple(family, L, dtype)] = TuneEntry{variant, us};
+}
+
+std::string tune_table_text() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  std::string out;
+  char line[160];
+  for (const auto& kv : g_tune) {
+    std::snprintf(line, sizeof(line), "%s %d %s %d %.3f\n", tune_family_name(std::get<0>(kv.first)),
+                  std::get<1>(kv.first), std::get<2>(kv.first) == XL_C128 ? "c128" : "c64",
+                  kv.second.variant, kv.second.us);
+    out += line;
+  }
+  return out;
+}
+
+void tune_clear() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+}
 
 xl_status smem_attr(const void* func, size_t bytes) {
   std::lock_guard<std::mutex> lk(g_mu);

@@ -37,6 +37,28 @@ xl_status smem_attr(const void* func, size_t bytes);
 
 size_t dtype_csize(int dtype);  // bytes of one complex element
 
+// Launch variants chosen by the autotuner (xl_autotune): for each tunable kernel family, row
+// length L and dtype, the variant index (0 = the built-in default). Families: the transposing
+// row passes, whose variants differ in rows per block (threads per block, register budget and
+// shared memory): 1 = half the default rows, 2 = twice the default rows (where that fits).
+enum TuneFamily {
+  TUNE_RS_PASS1 = 0,
+  TUNE_RS_PASS3 = 1,
+  TUNE_CZT_FWD_X = 2,
+  TUNE_CZT_FWD_Y = 3,
+  TUNE_CZT_ADJ_X = 4,
+  TUNE_CZT_ADJ_Y = 5,
+  TUNE_NFAMILY = 6
+};
+constexpr int kTuneVariants = 3;
+constexpr int kTuneMinL = 1024;  // shorter rows build only the default variant
+const char* tune_family_name(int family);
+int tuned_variant(int family, int L, int dtype);
+void set_tuned_variant(int family, int L, int dtype, int variant, double us);
+// The recorded choices as text lines "family L dtype variant microseconds".
+std::string tune_table_text();
+void tune_clear();
+
 // Brackets one kernel launch: counts it and, while profiling is enabled, records CUDA events on
 // its stream before and after it (name = kernel family, e.g. "rs_pass2<4096>").
 class LaunchScope {

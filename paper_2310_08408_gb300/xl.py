@@ -116,6 +116,12 @@ SIGNATURES = {
     "xl_device_status": ([_P], _I),
     "xl_asczt_propagate": ([_P, _P, _I, _GP, _WP, _D, _P, _I, _I, _P], _I),
     "xl_asczt_propagate_backward": ([_P, _P, _P, _P, _I, _GP, _WP, _D, _P, _I, _I, _P], _I),
+    "xl_autotune": ([_GP, _WP, _I, _I, _P], _I),
+    "xl_tune_get": ([_I, _I, _I], _I),
+    "xl_tune_set": ([_I, _I, _I, _I], _I),
+    "xl_tune_clear": ([], _I),
+    "xl_tune_save": ([ctypes.c_char_p], _I),
+    "xl_tune_load": ([ctypes.c_char_p], _I),
     "xl_beam_splitter": ([_P, _P, _P, _P, _I, ctypes.c_int64, _P, _I, _P], _I),
     "xl_beam_splitter_backward": ([_P, _P, _P, _P, _P, _P, _P, _I, ctypes.c_int64, _P, _I, _P], _I),
     "xl_adam_step": ([_P, _P, _P, _P, ctypes.c_int64, _I, _D, _D, _D, _D, _P, _I, _P], _I),
@@ -620,6 +626,39 @@ def asczt_propagate_backward(g_out: torch.Tensor, u_in: torch.Tensor | None, gri
         B, ctypes.byref(g), ctypes.byref(w), float(wavelength), zz.ptr, zz.flags, _dtype(g_out),
         _stream()))
     return g_in, g_z
+
+
+# ----------------------------------------------------------------------------- autotuner
+TUNE_RS_PASS1, TUNE_RS_PASS3, TUNE_CZT_FWD_X, TUNE_CZT_FWD_Y, TUNE_CZT_ADJ_X, TUNE_CZT_ADJ_Y = range(6)
+
+
+def autotune(grid, window=None, dtype: int = C64, reps: int = 5) -> None:
+    """Times the launch variants of the passes `grid` (and a CZT onto `window`) uses and keeps
+    the fastest for this process (xl_autotune)."""
+    g = Grid.of(grid)
+    w = Window.of(window) if window is not None else None
+    _check(load().xl_autotune(ctypes.byref(g), ctypes.byref(w) if w is not None else None,
+                              int(dtype), int(reps), _stream()))
+
+
+def tune_get(family: int, L: int, dtype: int = C64) -> int:
+    return int(load().xl_tune_get(int(family), int(L), int(dtype)))
+
+
+def tune_set(family: int, L: int, dtype: int, variant: int) -> None:
+    _check(load().xl_tune_set(int(family), int(L), int(dtype), int(variant)))
+
+
+def tune_clear() -> None:
+    _check(load().xl_tune_clear())
+
+
+def tune_save(path: str) -> None:
+    _check(load().xl_tune_save(os.fsencode(path)))
+
+
+def tune_load(path: str) -> None:
+    _check(load().xl_tune_load(os.fsencode(path)))
 
 
 # ----------------------------------------------------------------------------- beam splitters
