@@ -49,7 +49,11 @@ def parse():
     p.add_argument("--impl", default="xl", choices=["xl", "reference"])
     p.add_argument("--batch", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--no-autotune", action="store_true", help="run the built-in launch plan")
+    p.add_argument("--autotune", action="store_true", help="time the launch variants here "
+                   "instead of loading --plan")
+    p.add_argument("--plan", default=os.path.join(ROOT, "paper_2310_08408_gb300", "plans",
+                                                  "gb300_c64.txt"),
+                   help="launch plan file (xl_tune_load); empty: the built-in plan")
     p.add_argument("--no-next", action="store_true", help="skip the angular-spectrum CZT and "
                    "beam-splitter measurements")
     p.add_argument("--no-e2e", action="store_true")
@@ -412,13 +416,17 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # launch plan: the autotuner's rows-per-block choice for every pass of this grid and window
-    # (untimed set-up; results are identical for every choice)
+    # launch plan: the autotuner's rows-per-block choice for every pass of this grid and window,
+    # from the packaged GB300 plan or (--autotune) timed here; untimed set-up, results identical
+    # for every choice
     tune = None
-    if not a.no_autotune:
+    if a.autotune:
         for grid_n in ((N,) if a.no_table else (N, 512, 1024)):
             gt = inputs_grid(grid_n)
             xl.autotune(gt, w if grid_n == N else TABLE_WINDOW, xl.C64, reps=5)
+    elif a.plan:
+        xl.tune_load(a.plan)
+    if a.autotune or a.plan:
         import tempfile
         fd, tpath = tempfile.mkstemp(suffix=".txt")
         os.close(fd)

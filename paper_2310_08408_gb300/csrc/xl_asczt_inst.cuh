@@ -13,7 +13,7 @@ xl_status fwd_L(const void* in, void* out, int nrows, const void* Hc, int64_t h_
                 cudaStream_t s) {
   typedef cplx<T> C;
   constexpr int ROWS = as_rows<L, sizeof(C), false>();
-  const size_t sm = (size_t)ROWS * rpitch(L) * sizeof(C);
+  const size_t sm = (size_t)ROWS * tpitch(L, sizeof(C), ROWS) * sizeof(C);
   const void* tw;
   XL_TRY(twiddles(L, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
   XL_TRY(smem_attr((const void*)k_as_fwd<T, L, STAGE>, sm));
@@ -30,7 +30,7 @@ xl_status adj_L(const void* in, void* out, int nrows, const void* Hc, const void
                 int64_t h_stride, const void* TU, double* dz_part, int nb, cudaStream_t s) {
   typedef cplx<T> C;
   constexpr int ROWS = as_rows<L, sizeof(C), DZ>();
-  const size_t sm = (size_t)ROWS * (DZ ? 2 : 1) * rpitch(L) * sizeof(C);
+  const size_t sm = (size_t)ROWS * (DZ ? 2 : 1) * tpitch(L, sizeof(C), ROWS) * sizeof(C);
   const void* tw;
   XL_TRY(twiddles(L, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
   XL_TRY(smem_attr((const void*)k_as_adj<T, L, STAGE, DZ>, sm));

@@ -83,7 +83,7 @@ k_as_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nrows,
   constexpr int ROWS = as_rows<L, sizeof(C), false>();
   static_assert(team_barriers_fit<L>(ROWS * (L / 16)), "too many teams for the named barriers");
   constexpr int TT = L / 16;
-  constexpr int P = rpitch(L);
+  constexpr int P = tpitch(L, sizeof(C), ROWS);
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
@@ -131,7 +131,7 @@ k_as_adj(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nrows,
   constexpr int ROWS = as_rows<L, sizeof(C), DZ>();
   static_assert(team_barriers_fit<L>(ROWS * (L / 16)), "too many teams for the named barriers");
   constexpr int TT = L / 16;
-  constexpr int P = rpitch(L);
+  constexpr int P = tpitch(L, sizeof(C), ROWS);
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   __shared__ double red[32];

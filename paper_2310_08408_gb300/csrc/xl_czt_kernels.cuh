@@ -62,15 +62,15 @@ struct CztDims {
 template <int L, int CS, bool VEC = false, int V = 0> __host__ __device__ constexpr int czt_rows() {
   constexpr int r = CS == 8 ? (L >= 4096 ? 2 : ((4096 / L) > 4 ? 4096 / L : 4))
                             : (L >= 8192 ? 1 : ((4096 / L) > 2 ? 4096 / L : 2));
-  constexpr bool dbl = 2 * r * (L / 16) <= 1024 && (size_t)2 * r * rpitch(L) * CS <= (size_t)227 * 1024 &&
+  constexpr bool dbl = 2 * r * (L / 16) <= 1024 && (size_t)2 * r * tpitch(L, CS, 2 * r) * CS <= (size_t)227 * 1024 &&
                        team_barriers_fit<L>(2 * r * (L / 16));
   return VEC ? (r / 4 > 1 ? r / 4 : 1) : (V == 1 ? (r / 2 > 1 ? r / 2 : 1) : (V == 2 && dbl ? 2 * r : r));
 }
 template <int L, int CS, bool VEC, int V = 0> __host__ __device__ constexpr bool czt_stash_smem() {
-  return VEC && (size_t)2 * czt_rows<L, CS, VEC, V>() * rpitch(L) * CS <= (size_t)227 * 1024;
+  return VEC && (size_t)2 * czt_rows<L, CS, VEC, V>() * tpitch(L, CS, czt_rows<L, CS, VEC, V>()) * CS <= (size_t)227 * 1024;
 }
 template <int L, int CS, bool VEC, int V = 0> __host__ __device__ constexpr size_t czt_smem_bytes() {
-  return (size_t)czt_rows<L, CS, VEC, V>() * (czt_stash_smem<L, CS, VEC, V>() ? 2 : 1) * rpitch(L) * CS;
+  return (size_t)czt_rows<L, CS, VEC, V>() * (czt_stash_smem<L, CS, VEC, V>() ? 2 : 1) * tpitch(L, CS, czt_rows<L, CS, VEC, V>()) * CS;
 }
 template <int L, int CS, bool VEC, int V = 0> __host__ __device__ constexpr int czt_threads() {
   return czt_rows<L, CS, VEC, V>() * (L / 16);
@@ -104,14 +104,14 @@ __device__ __forceinline__ void chirp_conv(C (&v)[16], C* row, int t, const C* _
   team_fft<L, +1>(v, row, t, tw);
 }
 
-// Writes the team's register row to its shared-memory row (pitch rpitch(L)), then the block
+// Writes the team's register row to its shared-memory row (pitch tpitch), then the block
 // stores the first n_out entries of its ROWS rows transposed: dst[j * ld + c0 + r]. Ends with a
 // barrier: callers that transform again reuse the same rows.
 template <int L, int ROWS, typename C>
 __device__ __forceinline__ void store_transposed(const C (&v)[16], C* sm, int team, int t, int n_out,
                                                  C* __restrict__ dst, int64_t ld, int c0, int n_cols) {
   constexpr int TT = L / 16;
-  constexpr int P = rpitch(L);
+  constexpr int P = tpitch(L, sizeof(C), ROWS);
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < 16; ++q) sm[team * P + spad(t + q * TT)] = v[q];
@@ -127,7 +127,7 @@ __device__ __forceinline__ void load_transposed(C (&v)[16], C* sm, int team, int
                                                 const C* __restrict__ src, int64_t ld, int c0,
                                                 int n_cols) {
   constexpr int TT = L / 16;
-  constexpr int P = rpitch(L);
+  constexpr int P = tpitch(L, sizeof(C), ROWS);
   __syncthreads();
   load_rows_transposed<ROWS, P>(sm, n_in, L, src, ld, c0, n_cols);
   __syncthreads();
@@ -162,7 +162,7 @@ k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d,
   constexpr int ROWS = czt_rows<L, sizeof(C), VEC, V>();
   static_assert(team_barriers_fit<L>(ROWS * (L / 16)), "too many teams for the named barriers");
   constexpr int TT = L / 16;
-  constexpr int SR = rpitch(L);
+  constexpr int SR = tpitch(L, sizeof(C), ROWS);
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
@@ -212,7 +212,7 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
   constexpr int ROWS = czt_rows<L, sizeof(C), VEC, V>();
   static_assert(team_barriers_fit<L>(ROWS * (L / 16)), "too many teams for the named barriers");
   constexpr int TT = L / 16;
-  constexpr int SR = rpitch(L);
+  constexpr int SR = tpitch(L, sizeof(C), ROWS);
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
@@ -275,7 +275,7 @@ k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, 
   static_assert(team_barriers_fit<L>(ROWS * (L / 16)), "too many teams for the named barriers");
   constexpr bool SMST = czt_stash_smem<L, sizeof(C), VEC, V>();
   constexpr int TT = L / 16;
-  constexpr int SR = rpitch(L);
+  constexpr int SR = tpitch(L, sizeof(C), ROWS);
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
@@ -348,7 +348,7 @@ k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d
   constexpr int ROWS = czt_rows<L, sizeof(C), VEC, V>();
   static_assert(team_barriers_fit<L>(ROWS * (L / 16)), "too many teams for the named barriers");
   constexpr int TT = L / 16;
-  constexpr int SR = rpitch(L);
+  constexpr int SR = tpitch(L, sizeof(C), ROWS);
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;

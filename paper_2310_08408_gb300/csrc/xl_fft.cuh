@@ -203,10 +203,14 @@ __device__ __forceinline__ void fft_stage(C (&v)[16], C* sm, int t, const C* __r
   }
 }
 
-// Row pitch (in elements) of a block's shared-memory rows: at least srow(L) and congruent to
-// 4 modulo 16, so that lanes reading the same column of 4 consecutive rows (the transposed
-// stores and loads) fall in distinct banks.
-__host__ __device__ constexpr int rpitch(int L) { return srow(L) + ((4 - srow(L) % 16) + 16) % 16; }
+// Row pitch (in elements) of a block's shared-memory rows: at least srow(L), with the residue
+// modulo 16 that puts the rows one warp phase touches in the transposed stores and loads in
+// distinct banks. Those loops give each group of G = min(32 / element bytes, ROWS) lanes one
+// 32-byte sector (G consecutive rows of one column): G = 4 (complex64) and G = 2 (complex128)
+// want rows 4 elements apart modulo 16, G = 2 for complex64 wants 8.
+__host__ __device__ constexpr int tpitch(int L, int CS, int ROWS) {
+  return srow(L) + ((((CS == 8 && (32 / CS < ROWS ? 32 / CS : ROWS) == 2) ? 8 : 4) - srow(L) % 16) + 16) % 16;
+}
 
 // Transposed block store: rows 0..ROWS-1 of the block's shared memory (pitch P) hold the
 // first n_out entries of ROWS transforms; element j of row r goes to dst[j * ld + c0 + r]
@@ -227,8 +231,11 @@ __device__ __forceinline__ void store_rows_transposed(const C* sm, int n_out, C*
 }
 
 // Transposed block load (inverse of the store): row r of shared memory gets
-// src[j * ld + c0 + r] for j < n_in and zero for n_in <= j < n_fill.
-template <int ROWS, int P, typename C>
+// src[j * ld + c0 + r] for j < n_in and zero for n_in <= j < n_fill. Callers synchronise the
+// block before reading the rows. ASYNC: asynchronous global-to-shared copies (zero-filled where
+// there is no source element), so that a thread issues all of its copies before it waits once
+// (measured faster for RS pass 3, slower for the CZT adjoint passes, which keep plain loads).
+template <int ROWS, int P, typename C, bool ASYNC = false>
 __device__ __forceinline__ void load_rows_transposed(C* sm, int n_in, int n_fill,
                                                      const C* __restrict__ src, int64_t ld, int c0,
                                                      int n_cols) {
@@ -240,8 +247,21 @@ __device__ __forceinline__ void load_rows_transposed(C* sm, int n_in, int n_fill
   for (int grp = 0; grp < ROWS / G; ++grp)
     for (int e = threadIdx.x; e < n_fill * G; e += blockDim.x) {
       const int r = grp * G + (e & (G - 1)), j = e >> LG;
-      sm[r * P + spad(j)] = (j < n_in && c0 + r < n_cols) ? src[(int64_t)j * ld + c0 + r] : mk((T)0, (T)0);
+      const bool ok = j < n_in && c0 + r < n_cols;
+      if constexpr (ASYNC) {
+        const C* g = ok ? src + (int64_t)j * ld + c0 + r : src;  // a valid address; 0 bytes read
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(sm + r * P + spad(j));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(sa), "l"(g),
+                     "n"((int)sizeof(C)), "r"(ok ? (int)sizeof(C) : 0)
+                     : "memory");
+      } else {
+        sm[r * P + spad(j)] = ok ? src[(int64_t)j * ld + c0 + r] : mk((T)0, (T)0);
+      }
     }
+  if constexpr (ASYNC) {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  }
 }
 
 // Thread-private 16-element stash (element q of thread t is row element t + q L/16), in a shared

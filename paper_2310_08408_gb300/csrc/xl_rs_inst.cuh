@@ -9,7 +9,7 @@ namespace {
 template <typename T, int LX, int V>
 xl_status pass1_LV(const void* in, void* Tb, int nx, int ny, int cin, int cT, int np, cudaStream_t s) {
   constexpr int ROWS = rows_p1v<LX, sizeof(cplx<T>), V>();
-  const size_t sm = (size_t)ROWS * rpitch(LX) * sizeof(cplx<T>);
+  const size_t sm = (size_t)ROWS * tpitch(LX, sizeof(cplx<T>), ROWS) * sizeof(cplx<T>);
   const void* tw;
   XL_TRY(twiddles(LX, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
   XL_TRY(smem_attr((const void*)k_rs_pass1<T, LX, V>, sm));
@@ -37,7 +37,7 @@ template <typename T, int LX, int V>
 xl_status pass3_LV(const void* Tb, void* out, int nx, int ny, int cout, int cT, int np, cudaStream_t s,
                    DzReduce red) {
   constexpr int ROWS = rows_p3v<LX, sizeof(cplx<T>), V>();
-  const size_t sm = (size_t)ROWS * rpitch(LX) * sizeof(cplx<T>);
+  const size_t sm = (size_t)ROWS * tpitch(LX, sizeof(cplx<T>), ROWS) * sizeof(cplx<T>);
   const void* tw;
   XL_TRY(twiddles(LX, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
   XL_TRY(smem_attr((const void*)k_rs_pass3<T, LX, V>, sm));
@@ -98,7 +98,7 @@ template <typename T, int LX, int LY>
 xl_status gen_LL(void* S, void* Hq, const GenArgs& g, cudaStream_t s) {
   constexpr int RA = rows_transp<LX, sizeof(cplx<T>)>();
   constexpr int RB = rows_cols<LY>();
-  const size_t sa = (size_t)RA * rpitch(LX) * sizeof(cplx<T>);
+  const size_t sa = (size_t)RA * tpitch(LX, sizeof(cplx<T>), RA) * sizeof(cplx<T>);
   const size_t sb = (size_t)RB * srow(LY) * sizeof(cplx<T>);
   const void *twx, *twy;
   XL_TRY(twiddles(LX, sizeof(T) == 8 ? XL_C128 : XL_C64, &twx));

@@ -54,7 +54,7 @@ template <int L> __host__ __device__ constexpr int rows_cols() { return (4096 / 
 // memory of an SM and the named team barriers (otherwise the default).
 template <int R, int L, int CS, int V> __host__ __device__ constexpr int rows_variant() {
   return V == 1 ? (R / 2 > 1 ? R / 2 : 1)
-                : (V == 2 && 2 * R * (L / 16) <= 1024 && (size_t)2 * R * rpitch(L) * CS <= (size_t)227 * 1024 &&
+                : (V == 2 && 2 * R * (L / 16) <= 1024 && (size_t)2 * R * tpitch(L, CS, 2 * R) * CS <= (size_t)227 * 1024 &&
                            team_barriers_fit<L>(2 * R * (L / 16))
                        ? 2 * R
                        : R);
@@ -91,7 +91,7 @@ k_rs_pass1(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, int nx, int
   constexpr int ROWS = rows_p1v<LX, sizeof(C), V>();
   static_assert(team_barriers_fit<LX>(ROWS * (LX / 16)), "too many teams for the named barriers");
   constexpr int TT = LX / 16;
-  constexpr int P = rpitch(LX);
+  constexpr int P = tpitch(LX, sizeof(C), ROWS);
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
@@ -146,7 +146,7 @@ k_rs_pass3(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, int nx, in
   constexpr int ROWS = rows_p3v<LX, sizeof(C), V>();
   static_assert(team_barriers_fit<LX>(ROWS * (LX / 16)), "too many teams for the named barriers");
   constexpr int TT = LX / 16;
-  constexpr int P = rpitch(LX);
+  constexpr int P = tpitch(LX, sizeof(C), ROWS);
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
@@ -161,7 +161,7 @@ k_rs_pass3(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, int nx, in
     if (threadIdx.x == 0) red.out[b] = acc;
   }
   const C* src = Tb + ((int64_t)(p / cout) * cT + (p % cout)) * (int64_t)LX * ny;
-  load_rows_transposed<ROWS, P>(sm, LX, LX, src, ny, y0, ny);
+  load_rows_transposed<ROWS, P, C, true>(sm, LX, LX, src, ny, y0, ny);
   __syncthreads();
   C* row = sm + team * P;
   C v[16];
@@ -625,7 +625,7 @@ k_gen_pass_a(cplx<T>* __restrict__ S, GenArgs g, const cplx<T>* __restrict__ tw)
   constexpr int ROWS = rows_transp<LX, sizeof(C)>();
   static_assert(team_barriers_fit<LX>(ROWS * (LX / 16)), "too many teams for the named barriers");
   constexpr int TT = LX / 16;
-  constexpr int P = rpitch(LX);
+  constexpr int P = tpitch(LX, sizeof(C), ROWS);
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;

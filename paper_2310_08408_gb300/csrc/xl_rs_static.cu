@@ -129,11 +129,11 @@ xl_status run_static(const float2* in, float2* out, int32_t batch, const xl_grid
   // every launch below needs less than 48 KB of shared memory (transform lengths <= 512)
   constexpr int RA = rows_transp<LX, 8>(), R3 = rows_p3<LX, 8>(), RB = rows_cols<LY>(),
                 RC = rows_cols<LY>();
-  const size_t smA = (size_t)RA * rpitch(LX) * sizeof(float2);
-  const size_t sm3 = (size_t)R3 * rpitch(LX) * sizeof(float2);
+  const size_t smA = (size_t)RA * tpitch(LX, 8, RA) * sizeof(float2);
+  const size_t sm3 = (size_t)R3 * tpitch(LX, 8, R3) * sizeof(float2);
   const size_t smB = (size_t)RB * srow(LY) * sizeof(float2);
   const size_t smP2 = (size_t)RC * srow(LY) * sizeof(float2);
-  static_assert(RA * rpitch(LX) * 8 <= 48 * 1024 && R3 * rpitch(LX) * 8 <= 48 * 1024 &&
+  static_assert(RA * tpitch(LX, 8, RA) * 8 <= 48 * 1024 && R3 * tpitch(LX, 8, R3) * 8 <= 48 * 1024 &&
                     RB * srow(LY) * 8 <= 48 * 1024, "smem");
   const int64_t plane = (int64_t)nx * ny;
   for (int32_t b = 0; b < batch; ++b) {
