@@ -38,7 +38,7 @@ LAM = 0.633
 ZS = (500.0, 2000.0, 10_000.0)
 N, PITCH, W0 = 2048, 0.5, 200.0
 M, WIN_W = 512, 64.0
-E2E_CHUNK = 4  # fields per device pass of the end-to-end (host-staged) measurement
+E2E_CHUNK = 2  # fields per device pass of the end-to-end (host-staged) measurement
 
 
 def parse():
@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--impl", default="xl", choices=["xl", "reference"])
     p.add_argument("--batch", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-chunk", type=int, default=E2E_CHUNK,
+                   help="fields per device pass of the end-to-end measurement")
     p.add_argument("--autotune", action="store_true", help="time the launch variants here "
                    "instead of loading --plan")
     p.add_argument("--plan", default=os.path.join(ROOT, "paper_2310_08408_gb300", "plans",
@@ -525,7 +527,7 @@ def main():
         C_h = torch.empty(step.C.shape, dtype=step.C.dtype).pin_memory()
         gz_h = torch.empty((B,), dtype=torch.float64).pin_memory()
         ke = max(3, a.steps // 4)
-        ch = min(E2E_CHUNK, B)
+        ch = min(a.e2e_chunk, B)
         pipe = HostPipeline([((N, N), U_pin.dtype)],
                             [((N, N), step.A.dtype), ((M, M), step.C.dtype), ((), torch.float64)],
                             chunk=ch)
