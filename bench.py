@@ -155,7 +155,8 @@ def make_inputs(rank: int, batch: int):
     from paper_2310_08408_gb300 import inputs
     g = inputs.Grid.centred(N, PITCH)
     w = inputs.Window.centred(M, WIN_W)
-    seed = inputs.SEED0 + 2 + 1000 * rank
+    from paper_2310_08408_gb300.replicas import rank_seed
+    seed = rank_seed(inputs.SEED0 + 2, rank)
     U = np.stack([inputs.gaussian_random_phase(g, W0, seed + b) for b in range(batch)]
                  ).astype(np.complex64)
     zs = [ZS[b % 3] for b in range(batch)]
@@ -164,7 +165,8 @@ def make_inputs(rank: int, batch: int):
 
 def inputs_seed(rank: int) -> int:
     from paper_2310_08408_gb300 import inputs
-    return inputs.SEED0 + 5 + 1000 * rank
+    from paper_2310_08408_gb300.replicas import rank_seed
+    return rank_seed(inputs.SEED0 + 5, rank)
 
 
 def step_parts(xl):
@@ -413,10 +415,10 @@ def main():
     torch.cuda.synchronize()
     step = GpuStep(xl, torch, g, w, U_dev, zs)
 
+    from paper_2310_08408_gb300 import replicas
+
     def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
+        replicas.barrier("cuda")
 
     # launch plan: the autotuner's rows-per-block choice for every pass of this grid and window,
     # from the packaged GB300 plan or (--autotune) timed here; untimed set-up, results identical
@@ -451,12 +453,9 @@ def main():
     ms = e0.elapsed_time(e1)
     launches = (xl.launch_count() - n0) // max(a.steps, 1)
     ck = clocks.stop()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
-    value = step.props * world * a.steps / (ms / 1000.0)
-    grads = B * world * a.steps / (ms / 1000.0)
+    ms = replicas.max_over_ranks(ms, "cuda")
+    value = replicas.whole_job_rate(step.props, world, a.steps, ms)
+    grads = replicas.whole_job_rate(B, world, a.steps, ms)
 
     # batch 1 (one field per step, z = 0.5 mm): the latency-bound end of the same step
     batch1 = None
@@ -556,11 +555,8 @@ def main():
         e1.record(stream)
         barrier()
         ems = e0.elapsed_time(e1)
-        t = torch.tensor([ems], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ems = float(t.item())
-        e2e = {"value": step.props * world * ke / (ems / 1000.0), "unit": "propagations/s",
+        ems = replicas.max_over_ranks(ems, "cuda")
+        e2e = {"value": replicas.whole_job_rate(step.props, world, ke, ems), "unit": "propagations/s",
                "h2d_bytes_per_step": int(U_pin.numel() * 8),
                "d2h_bytes_per_step": int(A_h.numel() * 8 + C_h.numel() * 8 + gz_h.numel() * 8),
                "ms_per_step": ems / ke}
