@@ -123,8 +123,12 @@ def kernel_model(name: str, dims: dict):
         return nb * n * fft_flops(L), nb * (n * n + 2 * n * n) * cs
     if name.startswith("rs_pass3"):
         return nb * n * fft_flops(L), nb * (2 * n * n + n * n) * cs
+    if name.startswith("rs_pass2_m0_save"):  # also stores the input's 2D spectrum (4 n^2)
+        return nb * 2 * n * (2 * fft_flops(L) + 6 * L), nb * (8 * n * n + (n + 1) ** 2) * cs
     if name.startswith("rs_pass2_m0"):
         return nb * 2 * n * (2 * fft_flops(L) + 6 * L), nb * (4 * n * n + (n + 1) ** 2) * cs
+    if name.startswith("rs_pass2_m4"):  # adjoint with the saved spectrum: T in/out, spectrum in
+        return nb * 2 * n * (2 * fft_flops(L) + 14 * L), nb * (8 * n * n + 2 * (n + 1) ** 2) * cs
     if name.startswith("rs_pass2_m2"):
         return nb * 2 * n * (3 * fft_flops(L) + 14 * L), nb * (6 * n * n + 2 * (n + 1) ** 2) * cs
     if name.startswith("czt_fwd_x") or name.startswith("czt_adj_x"):

@@ -125,20 +125,23 @@ xl_status xl_rs_propagate_backward(const void* g_out, const void* u_in, void* g_
                                    int32_t batch, const xl_grid* grid, double wavelength,
                                    const double* z, int32_t flags, int32_t dtype, void* stream);
 
-/* Forward RS that also keeps what the adjoint's distance gradient needs from the input: the row
- * transforms of the zero-padded input planes (the first pass of the convolution), so that
- * xl_rs_propagate_backward_saved does not recompute them. The paper computes the same gradient
- * by reverse-mode differentiation (which keeps its forward intermediates in the same way).
- *   saved: [batch][2 nx][ny] complex (dtype), caller-owned device memory of
- *          batch * 2 * nx * ny * (8 or 16) bytes, overwritten; may not alias u_in or u_out.
+/* Forward RS that also keeps what the adjoint's distance gradient needs from the input: the 2D
+ * spectrum of the zero-padded input (the column transforms the convolution computes anyway), so
+ * that xl_rs_propagate_backward_saved transforms nothing of the input again. The paper computes
+ * the same gradient by reverse-mode differentiation (which keeps its forward intermediates in the
+ * same way).
+ *   saved: [batch][2 nx][2 ny] complex (dtype; row kx holds the spectrum's column kx), caller-owned
+ *          device memory of batch * 4 * nx * ny * (8 or 16) bytes, overwritten; may not alias
+ *          u_in or u_out.
  * Everything else as xl_rs_propagate (u_out is bit-identical to its result). */
 xl_status xl_rs_propagate_save(const void* u_in, void* u_out, void* saved, int32_t batch,
                                const xl_grid* grid, double wavelength, const double* z,
                                int32_t flags, int32_t dtype, void* stream);
 
-/* Adjoint of xl_rs_propagate taking the row transforms saved by xl_rs_propagate_save (same grid,
- * wavelength, distances and dtype) in place of u_in; the results are bit-identical to those of
- * xl_rs_propagate_backward. saved may be NULL when g_z is NULL. */
+/* Adjoint of xl_rs_propagate taking the spectra saved by xl_rs_propagate_save (same grid,
+ * wavelength, distances and dtype) in place of u_in; g_in is bit-identical to that of
+ * xl_rs_propagate_backward, g_z equal to it up to rounding (its sum runs in another kernel).
+ * saved may be NULL when g_z is NULL. */
 xl_status xl_rs_propagate_backward_saved(const void* g_out, const void* saved, void* g_in,
                                          double* g_z, int32_t batch, const xl_grid* grid,
                                          double wavelength, const double* z, int32_t flags,
@@ -180,7 +183,7 @@ xl_status xl_vrs_propagate_backward(const void* g_exyz, const void* exy_in, void
                                     int32_t dtype, void* stream);
 
 /* VRS counterparts of xl_rs_propagate_save / xl_rs_propagate_backward_saved:
- * saved: [batch][2][2 nx][ny] complex (the row transforms of Ex and Ey). */
+ * saved: [batch][2][2 nx][2 ny] complex (the spectra of Ex and Ey). */
 xl_status xl_vrs_propagate_save(const void* exy_in, void* exyz_out, void* saved, int32_t batch,
                                 const xl_grid* grid, double wavelength, const double* z,
                                 int32_t flags, int32_t dtype, void* stream);

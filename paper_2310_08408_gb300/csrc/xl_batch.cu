@@ -34,7 +34,7 @@ struct Group {
   void *src = nullptr, *a0 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *a4 = nullptr,
        *a5 = nullptr;
   void *g5 = nullptr, *g4 = nullptr, *g3 = nullptr, *g2 = nullptr, *g1 = nullptr, *g0 = nullptr;
-  void *s1 = nullptr, *s2 = nullptr;  // row transforms the RS / VRS forwards keep for the adjoints
+  void *s1 = nullptr, *s2 = nullptr;  // spectra the RS / VRS forwards keep for the adjoints
   void *phi1 = nullptr, *phi2 = nullptr, *gphi1 = nullptr, *gphi2 = nullptr;  // real T [count][n][n]
   void *m1 = nullptr, *v1 = nullptr, *m2 = nullptr, *v2 = nullptr;            // Adam moments (real T)
   double *p1 = nullptr, *p2 = nullptr, *pl = nullptr;  // element params [count][n_el][4]
@@ -134,7 +134,7 @@ xl_status group_alloc(xl_batch* b, Group& G, const double* init, uint64_t seed, 
       {&G.a2, cnt * 2 * plane * cs},  {&G.a3, cnt * 3 * plane * cs}, {&G.a4, cnt * 3 * plane * cs},
       {&G.a5, cnt * 3 * cam * cs},    {&G.g5, cnt * 3 * cam * cs},   {&G.g4, cnt * 3 * plane * cs},
       {&G.g3, cnt * 3 * plane * cs},  {&G.g2, cnt * 2 * plane * cs}, {&G.g1, cnt * plane * cs},
-      {&G.g0, cnt * plane * cs},      {&G.s1, cnt * 2 * plane * cs}, {&G.s2, cnt * 4 * plane * cs},
+      {&G.g0, cnt * plane * cs},      {&G.s1, cnt * 4 * plane * cs}, {&G.s2, cnt * 8 * plane * cs},
       {&G.phi1, cnt * plane * rs},    {&G.phi2, cnt * plane * rs},
       {&G.gphi1, cnt * plane * rs},   {&G.gphi2, cnt * plane * rs},  {&G.m1, cnt * plane * rs},
       {&G.v1, cnt * plane * rs},      {&G.m2, cnt * plane * rs},     {&G.v2, cnt * plane * rs},

@@ -117,7 +117,8 @@ P2Args p2_args(const xl_grid* g, const Spectra& sp, int cT, int cU) {
   a.want_dz = 0;
   a.conj = 0;
   for (int i = 0; i < NKIND; ++i) a.slot[i] = sp.slot[i];
-  a.src = nullptr;
+  a.spec_out = nullptr;
+  a.spec_in = nullptr;
   a.cS = 0;
   return a;
 }
@@ -140,8 +141,9 @@ int chunk_size(int64_t t_bytes_per_elem, int32_t remaining) {
 
 enum Op { OP_RS_FWD, OP_RS_BWD, OP_VRS_FWD, OP_VRS_BWD };
 
-// save_out (forward): receives the row transforms of the input planes, [batch][cin][2nx][ny];
-// save_in (adjoint): those row transforms in place of u_in for the distance gradient.
+// save_out (forward): receives the 2D spectra of the zero-padded input planes (the column
+// transforms pass 2 computes anyway), [batch][cin][2nx][2ny];
+// save_in (adjoint): those spectra in place of u_in for the distance gradient.
 template <typename T>
 xl_status run_op(Op op, const void* in, const void* u_in, void* out, double* g_z, int32_t batch,
                  const xl_grid* g, double wavelength, const double* z, int32_t flags, int32_t dtype,
@@ -165,6 +167,7 @@ xl_status run_op(Op op, const void* in, const void* u_in, void* out, double* g_z
   const size_t cs = sizeof(cplx<T>);
   const int64_t t_plane = (int64_t)2 * nx * ny;
   const int64_t plane = (int64_t)nx * ny;
+  const int64_t spec_plane = (int64_t)4 * nx * ny;  // one 2nx x 2ny spectrum
   // planes per element: input to pass 1, T planes, U planes (dz), output of pass 3
   const int cin = op == OP_RS_FWD || op == OP_RS_BWD ? 1 : (op == OP_VRS_FWD ? 2 : 3);
   const int cT = vec ? 3 : 1;
@@ -202,26 +205,25 @@ xl_status run_op(Op op, const void* in, const void* u_in, void* out, double* g_z
     const void* Hq = nullptr;
     XL_TRY(get_spectra(g, wavelength, sp, dtype, z + b0, flags, dev_s, dev_hq, s, &Hq));
     P2Args a = p2_args(g, sp, cT, cU);
-    if (save_out) {
-      // the row transforms go to the caller's buffer, which pass 2 reads without overwriting
-      char* sv = (char*)save_out + (size_t)b0 * cin * t_plane * cs;
-      XL_TRY(rs_pass1<T>(src + (size_t)b0 * cin * plane * cs, sv, nx, ny, cin, cin, nb * cin, s));
-      a.src = sv;
+    XL_TRY(rs_pass1<T>(src + (size_t)b0 * cin * plane * cs, Tb, nx, ny, cin, cT, nb * cin, s));
+    if (save_out) {  // pass 2 also stores the column spectra of the inputs
+      a.spec_out = (char*)save_out + (size_t)b0 * cin * spec_plane * cs;
       a.cS = cin;
-    } else {
-      XL_TRY(rs_pass1<T>(src + (size_t)b0 * cin * plane * cs, Tb, nx, ny, cin, cT, nb * cin, s));
     }
     const void* Ucur = Ub;
     if (want_dz) {
-      if (save_in)
-        Ucur = (const char*)save_in + (size_t)b0 * cU * t_plane * cs;
-      else
+      if (save_in) {
+        a.spec_in = (const char*)save_in + (size_t)b0 * cU * spec_plane * cs;
+        a.cS = cU;
+      } else {
         XL_TRY(rs_pass1<T>(usrc + (size_t)b0 * cU * plane * cs, Ub, nx, ny, cU, cU, nb * cU, s));
+      }
     }
     a.want_field = want_field;
     a.want_dz = want_dz;
     int mode = op == OP_RS_FWD ? P2_RS : op == OP_VRS_FWD ? P2_VRS : op == OP_RS_BWD ? P2_RS_BWD
                                                                                     : P2_VRS_BWD;
+    if (want_dz && save_in) mode = op == OP_RS_BWD ? P2_RS_BWD_S : P2_VRS_BWD_S;
     XL_TRY(rs_pass2<T>(mode, Tb, Ucur, Hq, dzp, a, nb, s));
     // the distance partials are summed by pass 3 when it runs, else by their own launch
     if (want_dz && !want_field) XL_TRY(launch_reduce<T>(dzp, p2blocks, g_z + b0, nb, s));

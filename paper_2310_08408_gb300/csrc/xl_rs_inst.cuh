@@ -75,7 +75,7 @@ xl_status pass2_LM(void* Tb, const void* Ub, const void* Hq, double* dz, const P
   XL_TRY(smem_attr((const void*)k_rs_pass2<T, LY, MODE>, sm));
   const int LX = 2 * a.nx;
   dim3 grid((LX + ROWS - 1) / ROWS, nb);
-  LaunchScope ls("rs_pass2_m" + std::to_string(MODE) + "<" + std::to_string(LY) + ">", s);
+  LaunchScope ls("rs_pass2_m" + std::to_string(MODE) + (a.spec_out ? "_save<" : "<") + std::to_string(LY) + ">", s);
   k_rs_pass2<T, LY, MODE><<<grid, ROWS * (LY / 16), sm, s>>>(
       (cplx<T>*)Tb, (const cplx<T>*)Ub, (const cplx<T>*)Hq, dz, a, (const cplx<T>*)tw);
   XL_CUDA_TRY(cudaGetLastError());
@@ -90,6 +90,8 @@ xl_status pass2_L(int mode, void* Tb, const void* Ub, const void* Hq, double* dz
     case P2_VRS: return pass2_LM<T, LY, P2_VRS>(Tb, Ub, Hq, dz, a, nb, s);
     case P2_RS_BWD: return pass2_LM<T, LY, P2_RS_BWD>(Tb, Ub, Hq, dz, a, nb, s);
     case P2_VRS_BWD: return pass2_LM<T, LY, P2_VRS_BWD>(Tb, Ub, Hq, dz, a, nb, s);
+    case P2_RS_BWD_S: return pass2_LM<T, LY, P2_RS_BWD_S>(Tb, Ub, Hq, dz, a, nb, s);
+    case P2_VRS_BWD_S: return pass2_LM<T, LY, P2_VRS_BWD_S>(Tb, Ub, Hq, dz, a, nb, s);
   }
   return fail(XL_ERR_ARG, "rs_pass2: bad mode");
 }

@@ -184,6 +184,8 @@ enum {
   P2_VRS = 1,       // T0,T1,T2 <- from T0,T1: x*Hz, y*Hz, x*Hx + y*Hy
   P2_RS_BWD = 2,    // T0 <- IFFT(FFT(T0) conj Hz); dz partial from T0, U0 (optional)
   P2_VRS_BWD = 3,   // T0,T1 <- from T0,T1,T2 (gx, gy, gz) with conj spectra; dz from U0,U1
+  P2_RS_BWD_S = 4,  // P2_RS_BWD with U's column spectra read from saved spectra (no transform)
+  P2_VRS_BWD_S = 5, // P2_VRS_BWD likewise
 };
 
 struct P2Args {
@@ -196,9 +198,10 @@ struct P2Args {
   int want_dz;          // accumulate the dz partials
   int conj;             // P2_RS: use conj(H) (adjoint without dz)
   int slot[NKIND];      // spectrum kind -> slot in the Hq buffer (-1: absent)
-  const void* src;      // forward modes: read the row transforms from here ([b][cS][LX][ny])
-                        // instead of T, which then only receives the results (nullable)
-  int cS;               // planes per batch element of src
+  void* spec_out;       // forward modes: also store the input planes' column spectra (before
+                        // the transfer spectrum) here, [b][cS][LX][LY] (nullable)
+  const void* spec_in;  // *_BWD_S modes: U's column spectra saved by a forward, same layout
+  int cS;               // planes per batch element of spec_out / spec_in
 };
 
 // Spectrum `Hk` along one kx row at ky = t + q TT (TT = LY / 16, ny = 8 TT): the quadrant row
@@ -244,10 +247,15 @@ __device__ __forceinline__ void store_col(const C (&v)[16], C* __restrict__ dst,
 #pragma unroll
   for (int q = 0; q < 8; ++q) dst[t + q * TT] = v[q];
 }
+template <typename C>
+__device__ __forceinline__ void store_full(const C (&v)[16], C* __restrict__ dst, int t, int TT) {
+#pragma unroll
+  for (int q = 0; q < 16; ++q) dst[t + q * TT] = v[q];
+}
 
 // Blocks per SM the register budget of each pass-2 mode aims at (256-thread blocks).
 template <int MODE> __host__ __device__ constexpr int p2_min_blocks() {
-  return MODE == P2_RS ? 4 : (MODE == P2_RS_BWD ? 3 : 2);
+  return MODE == P2_RS || MODE == P2_RS_BWD_S ? 4 : (MODE == P2_RS_BWD ? 3 : 2);
 }
 // Shared-memory rows per team of each mode. VRS modes keep the Ez or Gz spectrum in a second
 // row; the adjoints with a distance gradient park U's column spectrum (times the dz spectrum for
@@ -259,7 +267,8 @@ template <typename T, int LY, int MODE> __host__ __device__ constexpr bool p2_us
              (size_t)227 * 1024;
 }
 template <typename T, int LY, int MODE> __host__ __device__ constexpr int p2_rows_per_team() {
-  return (MODE == P2_VRS || MODE == P2_VRS_BWD ? 2 : 1) + (p2_ustash_smem<T, LY, MODE>() ? 1 : 0);
+  return (MODE == P2_VRS || MODE == P2_VRS_BWD || MODE == P2_VRS_BWD_S ? 2 : 1) +
+         (p2_ustash_smem<T, LY, MODE>() ? 1 : 0);
 }
 
 // grid: (ceil(LX / ROWS), nbatch). Hq: spectra [slots][nx+1][ny+1].
@@ -297,13 +306,18 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
   C v[16];
   double dz = 0.0;
 
-  // forward modes may read their inputs from a separate, preserved buffer
-  const C* S0 = a.src ? reinterpret_cast<const C*>(a.src) + (int64_t)b * a.cS * a.t_plane +
-                            (int64_t)kx * a.ny
-                      : T0;
+  // saved column spectra: [b][cS][LX][LY], column kx of plane c
+  const int64_t spec_plane = (int64_t)LX * LY;
+  auto spec_out = [&](int c) {
+    return reinterpret_cast<C*>(a.spec_out) + ((int64_t)b * a.cS + c) * spec_plane + (int64_t)kx * LY;
+  };
+  auto spec_in = [&](int c) {
+    return reinterpret_cast<const C*>(a.spec_in) + ((int64_t)b * a.cS + c) * spec_plane + (int64_t)kx * LY;
+  };
   if constexpr (MODE == P2_RS) {
-    load_col(v, S0, t, TT);
+    load_col(v, T0, t, TT);
     team_fft<LY, -1>(v, row, t, tw);
+    if (a.spec_out && live) store_full(v, spec_out(0), t, TT);
     const C* h = H(KH);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
@@ -319,8 +333,9 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
     C* T2 = T1 + a.t_plane;
     C* zr = sm + ROWS * SR + team * SR;
     const C *hz = H(KH), *hx = H(KHX), *hy = H(KHY);
-    load_col(v, S0, t, TT);
+    load_col(v, T0, t, TT);
     team_fft<LY, -1>(v, row, t, tw);
+    if (a.spec_out && live) store_full(v, spec_out(0), t, TT);
     transform_fence();
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
@@ -331,8 +346,9 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
     team_fft<LY, +1>(v, row, t, tw);
     transform_fence();
     if (live) store_col(v, T0, t, TT);
-    load_col(v, S0 + a.t_plane, t, TT);
+    load_col(v, T1, t, TT);
     team_fft<LY, -1>(v, row, t, tw);
+    if (a.spec_out && live) store_full(v, spec_out(1), t, TT);
     transform_fence();
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
@@ -431,8 +447,73 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
         if (live) store_col(v, Tc, t, TT);
       }
     }
+  } else if constexpr (MODE == P2_RS_BWD_S) {
+    // U's column spectrum comes from the forward's saved spectra: one transform fewer and no
+    // parked row (the products are formed as the saved values stream in)
+    load_col(v, T0, t, TT);
+    team_fft<LY, -1>(v, row, t, tw);
+    if (a.want_dz) {
+      const C* su = spec_in(0);
+      const C* hd = H(KDH);
+      T acc = (T)0;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        acc += cdot_re(v[q], cmul(su[t + q * TT], spec_row(hd, q, t, TT, flipx, false, false)));
+        XL_GROUP_FENCE(q);
+      }
+      dz = (double)acc;
+    }
+    if (a.want_field) {
+      const C* h = H(KH);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = cmulc(v[q], spec_row(h, q, t, TT, flipx, false, false));
+      team_fft<LY, +1>(v, row, t, tw);
+      if (live) store_col(v, T0, t, TT);
+    }
+  } else if constexpr (MODE == P2_VRS_BWD_S) {
+    // as P2_VRS_BWD with U_c's column spectra read from the saved spectra
+    C* T1 = T0 + a.t_plane;
+    C* T2 = T1 + a.t_plane;
+    C* zr = sm + ROWS * SR + team * SR;
+    load_col(v, T2, t, TT);
+    team_fft<LY, -1>(v, row, t, tw);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) zr[spad(t + q * TT)] = v[q];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      C* Tc = c == 0 ? T0 : T1;
+      const bool ox = c == 0, oy = c == 1;
+      load_col(v, Tc, t, TT);
+      team_fft<LY, -1>(v, row, t, tw);
+      if (a.want_dz) {
+        const C* su = spec_in(c);
+        const C *hd = H(KDH), *ho = H(c == 0 ? KDHX : KDHY);
+        T acc = (T)0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const C u = su[t + q * TT];
+          acc += cdot_re(v[q], cmul(u, spec_row(hd, q, t, TT, flipx, false, false))) +
+                 cdot_re(zr[spad(t + q * TT)], cmul(u, spec_row(ho, q, t, TT, flipx, ox, oy)));
+          XL_GROUP_FENCE(q);
+        }
+        dz += (double)acc;
+      }
+      if (a.want_field) {
+        const C *hz = H(KH), *ho = H(c == 0 ? KHX : KHY);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          v[q] = cadd(cmulc(v[q], spec_row(hz, q, t, TT, flipx, false, false)),
+                      cmulc(zr[spad(t + q * TT)], spec_row(ho, q, t, TT, flipx, ox, oy)));
+          XL_GROUP_FENCE(q);
+        }
+        team_fft<LY, +1>(v, row, t, tw);
+        transform_fence();
+        if (live) store_col(v, Tc, t, TT);
+      }
+    }
   }
-  if constexpr (MODE == P2_RS_BWD || MODE == P2_VRS_BWD) {
+  if constexpr (MODE == P2_RS_BWD || MODE == P2_VRS_BWD || MODE == P2_RS_BWD_S ||
+                MODE == P2_VRS_BWD_S) {
     if (a.want_dz) {
       double s = block_sum(live ? dz : 0.0, red);
       if (threadIdx.x == 0) dz_part[(int64_t)b * gridDim.x + blockIdx.x] = s;

@@ -123,7 +123,8 @@ xl_status run_static(const float2* in, float2* out, int32_t batch, const xl_grid
   pa.conj = 0;
   for (int i = 0; i < NKIND; ++i) pa.slot[i] = -1;
   pa.slot[KH] = 0;
-  pa.src = nullptr;
+  pa.spec_out = nullptr;
+  pa.spec_in = nullptr;
   pa.cS = 0;
 
   // every launch below needs less than 48 KB of shared memory (transform lengths <= 512)

@@ -252,8 +252,8 @@ def _planes(u: torch.Tensor, comps: int, name: str):
 def rs_propagate(u: torch.Tensor, grid, wavelength: float, z, out: torch.Tensor | None = None,
                  saved: torch.Tensor | None = None):
     """Scalar RS propagation of [B][ny][nx] (or [ny][nx]) planes; returns the same shape.
-    saved: optional [B][2nx][ny] tensor that receives the row transforms of the input for
-    rs_propagate_backward(..., saved=...) (xl_rs_propagate_save); see save_buffer()."""
+    saved: optional [B][2nx][2ny] tensor that receives the 2D spectra of the zero-padded input
+    for rs_propagate_backward(..., saved=...) (xl_rs_propagate_save); see save_buffer()."""
     _dev(u, "u")
     B, ny, nx = _planes(u, 1, "u")
     g = Grid.of(grid)
@@ -272,10 +272,10 @@ def rs_propagate(u: torch.Tensor, grid, wavelength: float, z, out: torch.Tensor 
 
 
 def save_buffer(field: torch.Tensor, comps: int = 1) -> torch.Tensor:
-    """Buffer for the row transforms a forward RS (comps 1) or VRS (comps 2) call saves for its
-    adjoint: [B][comps][2nx][ny] of the field's dtype."""
+    """Buffer for the spectra a forward RS (comps 1) or VRS (comps 2) call saves for its
+    adjoint: [B][comps][2nx][2ny] of the field's dtype."""
     B, ny, nx = _planes(field, comps, "field")
-    return torch.empty((B, comps, 2 * nx, ny), dtype=field.dtype, device=field.device)
+    return torch.empty((B, comps, 2 * nx, 2 * ny), dtype=field.dtype, device=field.device)
 
 
 def rs_propagate_static(u: torch.Tensor, grid, wavelength: float, z,
@@ -300,7 +300,7 @@ def rs_propagate_backward(g_out: torch.Tensor, u_in: torch.Tensor | None, grid, 
                           phase_invariant: bool = False, saved: torch.Tensor | None = None):
     """Adjoint of rs_propagate: returns (g_in or None, g_z [B] float64 or None).
     phase_invariant: the loss ignores a constant phase on the output (XL_PHASE_INVARIANT).
-    saved: the row transforms a forward call saved; used in place of u_in."""
+    saved: the spectra a forward call saved; used in place of u_in."""
     _dev(g_out, "g_out")
     B, ny, nx = _planes(g_out, 1, "g_out")
     g = Grid.of(grid)
@@ -321,7 +321,7 @@ def rs_propagate_backward(g_out: torch.Tensor, u_in: torch.Tensor | None, grid, 
 def vrs_propagate(exy: torch.Tensor, grid, wavelength: float, z, out: torch.Tensor | None = None,
                   saved: torch.Tensor | None = None):
     """Vectorial RS: [B][2][ny][nx] -> [B][3][ny][nx] (also [2][ny][nx] -> [3][ny][nx]).
-    saved: optional [B][2][2nx][ny] tensor for vrs_propagate_backward(..., saved=...)."""
+    saved: optional [B][2][2nx][2ny] tensor for vrs_propagate_backward(..., saved=...)."""
     _dev(exy, "exy")
     B, ny, nx = _planes(exy, 2, "exy")
     g = Grid.of(grid)

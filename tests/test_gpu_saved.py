@@ -1,10 +1,12 @@
-"""RS / VRS forwards that keep the input's row transforms, and the adjoints that use them.
+"""RS / VRS forwards that keep the spectra of their zero-padded inputs, and the adjoints that use
+them.
 
-The saved-transform entry points compute exactly what xl_rs_propagate / xl_vrs_propagate and
-their adjoints compute (the same kernels on the same values, only the first pass of the adjoint's
-distance gradient is taken from the buffer instead of being recomputed), so both are compared
-bit for bit with the plain entry points, and the plain entry points are compared with the FP64
-oracle in test_gpu_rs.py. One case per precision also goes to the oracle directly.
+The saved-spectrum entry points compute what xl_rs_propagate / xl_vrs_propagate and their
+adjoints compute: the forwards and the adjoints' field gradients with the same kernels on the same
+values (compared bit for bit), the distance gradient from the saved spectra instead of transforming
+the input again (the same products, summed in another kernel: compared to rounding). The plain
+entry points are compared with the FP64 oracle in test_gpu_rs.py; one case per precision also
+goes to the oracle directly here.
 """
 import ctypes
 
@@ -48,7 +50,7 @@ def test_rs_saved_bit_identical(dtype):
     gi_s, gz_s = xl.rs_propagate_backward(G, None, g, LAM, zs, want_field=True, want_dz=True,
                                           saved=S)
     assert torch.equal(gi_p, gi_s)
-    assert torch.equal(gz_p, gz_s)
+    assert torch.allclose(gz_p, gz_s, rtol=1e-5 if dtype == np.complex64 else 1e-12, atol=0)
     # only the distance gradient
     _, gz_o = xl.rs_propagate_backward(G, None, g, LAM, zs, want_field=False, want_dz=True, saved=S)
     assert np.allclose(to_np(gz_o), to_np(gz_s), rtol=1e-12 if dtype == np.complex128 else 1e-6)
@@ -76,7 +78,7 @@ def test_vrs_saved_bit_identical(dtype):
         gi_s, gz_s = xl.vrs_propagate_backward(G, None, g, LAM, zs, want_field=True, want_dz=True,
                                                phase_invariant=pinv, saved=S)
         assert torch.equal(gi_p, gi_s)
-        assert torch.equal(gz_p, gz_s)
+        assert torch.allclose(gz_p, gz_s, rtol=1e-5 if dtype == np.complex64 else 1e-12, atol=0)
     ref = oracle.vrs(u[1].astype(np.complex128), g.dx, g.dy, LAM, zs[1])
     assert rel(to_np(out_save)[1], ref) < (TOL_C64 if dtype == np.complex64 else TOL_C128)
 
@@ -94,7 +96,8 @@ def test_rs_saved_device_distances():
     G = to_dev(inputs.random_unit(4301, (2, 64, 64)).astype(np.complex64), np.complex64)
     gi_p, gz_p = xl.rs_propagate_backward(G, U, g, LAM, zd, want_field=True, want_dz=True)
     gi_s, gz_s = xl.rs_propagate_backward(G, None, g, LAM, zd, want_field=True, want_dz=True, saved=S)
-    assert torch.equal(gi_p, gi_s) and torch.equal(gz_p, gz_s)
+    assert torch.equal(gi_p, gi_s)
+    assert torch.allclose(gz_p, gz_s, rtol=1e-5, atol=0)
 
 
 def test_saved_argument_errors():
@@ -122,7 +125,7 @@ def test_saved_argument_errors():
     assert st == xl.ERR_ARG
 
 
-def test_autograd_uses_saved_transforms():
+def test_autograd_uses_saved_spectra():
     """The autograd wrapper's distance gradient equals the explicit adjoint with u_in."""
     import torch
     xl = lib()
@@ -137,4 +140,4 @@ def test_autograd_uses_saved_transforms():
     loss.backward()
     gi, gz = xl.rs_propagate_backward(W, U, g, LAM, z.detach(), want_field=True, want_dz=True)
     assert torch.equal(Ur.grad, gi)
-    assert torch.equal(z.grad, gz)
+    assert torch.allclose(z.grad, gz, rtol=1e-5, atol=0)
