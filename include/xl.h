@@ -380,7 +380,8 @@ xl_status xl_device_status(void* stream);
 
 /* Times every variant of the passes a grid (and, when window is non-NULL, a CZT onto that
  * window) uses, `reps` launches each on `stream` with synthetic data (allocates and frees its own
- * device buffers, synchronises `stream`), and keeps the fastest. */
+ * device buffers, synchronises `stream`), and keeps the fastest. Each timed launch processes
+ * enough planes (up to 16) that its data exceeds L2, as batched calls do. */
 xl_status xl_autotune(const xl_grid* grid, const xl_window* window, int32_t dtype, int32_t reps,
                       void* stream);
 /* The variant used for (family, row length L, dtype): 0..2, or -1 for an unknown family. */

@@ -79,12 +79,12 @@ xl_status run(bool adjoint, const void* in, const void* u_in, void* out, double*
   void* tab = nullptr;
   XL_TRY(cached_table(key, (size_t)tab_n * cs, s,
                       [&](void* buf) { return asczt_tables<T>(buf, ta, s); }, &tab));
-  Axis<C> ax, ay;
+  AxisRun<C> ax, ay;  // one table for every element (no distance in the window sums)
   {
     const C* t = (const C*)tab;
-    ax.pre = t; ax.post = t + nx; ax.bhat = t + nx + mx;
     const C* u = t + ta.off_y;
-    ay.pre = u; ay.post = u + ny; ay.bhat = u + ny + my;
+    ax = axis_run(Axis<C>{t, t + nx, t + nx + mx});
+    ay = axis_run(Axis<C>{u, u + ny, u + ny + my});
   }
   // launches take runs of equal distances, up to ~48 MB of spectrum planes
   int chunk = (int)std::max<int64_t>(1, ((int64_t)48 << 20) / (plane * (int64_t)cs));
@@ -110,7 +110,7 @@ xl_status run(bool adjoint, const void* in, const void* u_in, void* out, double*
   d.x0 = g->x0; d.dx = g->dx; d.y0 = g->y0; d.dy = g->dy;
   d.xo0 = w->xo0; d.dxo = w->dxo; d.yo0 = w->yo0; d.dyo = w->dyo;
   d.zdev = nullptr;
-  d.zval = 0.0;
+  for (int i = 0; i < kCztRun; ++i) d.z[i] = 0.0;
   d.in_planes = 1;
   d.adjoint = adjoint ? 1 : 0;
 

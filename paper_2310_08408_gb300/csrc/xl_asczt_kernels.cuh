@@ -113,7 +113,7 @@ k_as_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nrows,
 #pragma unroll
   for (int q = 0; q < 16; ++q) rowp[spad(t + q * TT)] = v[q];
   __syncthreads();
-  store_rows_transposed<ROWS, P>(sm, L, out + b * plane, nrows, r0, nrows);
+  store_rows_transposed<L, ROWS, P>(sm, L, out + b * plane, nrows, r0, nrows);
 }
 
 // Adjoint spectrum pass. in: [batch][L][nrows] (the transposed layout); out: [batch][nrows][L].
@@ -155,7 +155,7 @@ k_as_adj(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nrows,
     for (int q = 0; q < 16; ++q) ur[spad(t + q * TT)] = cmul(v[q], __ldg(dh + t + q * TT));
   }
   __syncthreads();
-  load_rows_transposed<ROWS, P>(sm, L, L, in + b * plane, nrows, r0, nrows);
+  load_rows_transposed<L, ROWS, P>(sm, L, L, in + b * plane, nrows, r0, nrows);
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = rowp[spad(t + q * TT)];

@@ -3,6 +3,7 @@
 // onto an arbitrarily selected and sampled region of interest.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <string>
 
 #include "xl_czt_launch.h"
@@ -101,18 +102,24 @@ xl_status run(bool adjoint, const void* in, void* out, int32_t batch, bool vec, 
   const size_t cs = sizeof(cplx<T>);
   const int64_t tplane = (int64_t)w->mx * g->ny;
   const int64_t in_plane = (int64_t)g->nx * g->ny, win_plane = (int64_t)w->mx * w->my;
-  // batch elements per launch: T planes within ~48 MB (L2-resident between the passes)
-  int chunk = (int)std::max<int64_t>(1, ((int64_t)48 << 20) / (cT * tplane * (int64_t)cs));
+  // Batch elements per launch: up to kCztRun, whatever their distances (each element reads the
+  // chirp tables of its own distance), within 2 GB of T planes; the chunk's tables stay within
+  // half of the table cache, so that filling one never evicts another of the same launch.
+  const size_t tab_bytes1 = (size_t)tab_elems(ta) * cs;
+  int64_t chunk = std::max<int64_t>(1, ((int64_t)2048 << 20) / (cT * tplane * (int64_t)cs));
+  chunk = std::min<int64_t>(chunk, std::max<int64_t>(1, (int64_t)(table_cache_cap() / 2 / tab_bytes1)));
+  chunk = std::min<int64_t>(chunk, kCztRun);
   if (zdev) chunk = 1;
-  chunk = std::min<int>(chunk, batch);
+  chunk = std::min<int64_t>(chunk, batch);
   auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
   const size_t t_bytes = (size_t)chunk * cT * tplane * cs;
-  const size_t tab_bytes = zdev ? (size_t)tab_elems(ta) * cs : 0;
+  const size_t tab_bytes = zdev ? tab_bytes1 : 0;
   void* ws = nullptr;
   XL_TRY(workspace(s, al(t_bytes) + al(tab_bytes), &ws));
   void* Tb = ws;
   void* dev_tab = (char*)ws + al(t_bytes);
   CztDims d;
+  std::memset(&d, 0, sizeof(d));
   d.nx = g->nx; d.ny = g->ny; d.mx = w->mx; d.my = w->my;
   d.x0 = g->x0; d.dx = g->dx; d.y0 = g->y0; d.dy = g->dy;
   d.xo0 = w->xo0; d.dxo = w->dxo; d.yo0 = w->yo0; d.dyo = w->dyo;
@@ -120,15 +127,25 @@ xl_status run(bool adjoint, const void* in, void* out, int32_t batch, bool vec, 
   d.in_planes = in_planes;
   d.adjoint = adjoint ? 1 : 0;
   for (int32_t b0 = 0; b0 < batch;) {
-    int nb = 1;
-    if (!zdev)
-      while (nb < chunk && b0 + nb < batch && z[b0 + nb] == z[b0]) ++nb;
+    const int nb = (int)std::min<int64_t>(chunk, batch - b0);
+    AxisRun<cplx<T>> ax, ay;
+    const void* tab0 = nullptr;  // element 0's tables: the base of the shifts
     const void* tab = nullptr;
-    XL_TRY(get_tables<T>(g, w, wavelength, z + b0, flags, dtype, dev_tab, s, &tab));
-    Axis<cplx<T>> ax, ay;
-    axes<T>(tab, ta, &ax, &ay);
+    for (int e = 0; e < nb; ++e) {  // (nb is 1 with device distances)
+      if (e == 0 || z[b0 + e] != z[b0 + e - 1])
+        XL_TRY(get_tables<T>(g, w, wavelength, z + b0 + e, flags, dtype, dev_tab, s, &tab));
+      if (e == 0) {
+        Axis<cplx<T>> x1, y1;
+        axes<T>(tab, ta, &x1, &y1);
+        ax = axis_run(x1);
+        ay = axis_run(y1);
+        ax.per_elem = ay.per_elem = 1;
+        tab0 = tab;
+      }
+      ax.shift[e] = ay.shift[e] = (const cplx<T>*)tab - (const cplx<T>*)tab0;
+      d.z[e] = zdev ? 0.0 : z[b0 + e];
+    }
     d.zdev = zdev ? z + b0 : nullptr;
-    d.zval = zdev ? 0.0 : z[b0];
     if (!adjoint) {
       const char* src = (const char*)in + (size_t)b0 * cin * in_plane * cs;
       char* dst = (char*)out + (size_t)b0 * cwin * win_plane * cs;

@@ -8,7 +8,7 @@
 namespace xl {
 
 template <typename T, int L, bool VEC, int V>
-xl_status pass_LVV(int which, const void* src, void* dst, const CztDims& d, const Axis<cplx<T>>& ax,
+xl_status pass_LVV(int which, const void* src, void* dst, const CztDims& d, const AxisRun<cplx<T>>& ax,
                    int nb, cudaStream_t s) {
   constexpr int ROWS = czt_rows<L, sizeof(cplx<T>), VEC, V>();
   const size_t sm = czt_smem_bytes<L, sizeof(cplx<T>), VEC, V>();
@@ -58,7 +58,7 @@ xl_status pass_LVV(int which, const void* src, void* dst, const CztDims& d, cons
 
 // The autotuner's variant for this pass and length (scalar passes of long rows only).
 template <typename T, int L, bool VEC>
-xl_status pass_LV(int which, const void* src, void* dst, const CztDims& d, const Axis<cplx<T>>& ax,
+xl_status pass_LV(int which, const void* src, void* dst, const CztDims& d, const AxisRun<cplx<T>>& ax,
                   int nb, cudaStream_t s) {
   if constexpr (!VEC && L >= kTuneMinL) {
     const int fam = which == CZT_FWD_X ? TUNE_CZT_FWD_X : which == CZT_FWD_Y ? TUNE_CZT_FWD_Y
@@ -72,7 +72,7 @@ xl_status pass_LV(int which, const void* src, void* dst, const CztDims& d, const
 }
 
 #define XL_CZT_PASS_SIG(LL, VV)                                                                    \
-  xl_status pass_LV<XL_REAL, LL, VV>(int, const void*, void*, const CztDims&, const Axis<cplx<XL_REAL>>&, \
+  xl_status pass_LV<XL_REAL, LL, VV>(int, const void*, void*, const CztDims&, const AxisRun<cplx<XL_REAL>>&, \
                                      int, cudaStream_t)
 #define XL_CZT_INSTANTIATE(LL) \
   template XL_CZT_PASS_SIG(LL, false); \
@@ -121,7 +121,7 @@ xl_status bhat(int L, cplx<T>* rows, int64_t stride, cudaStream_t s) {
 
 template <>
 xl_status czt_pass<XL_REAL>(int which, bool vec, int L, const void* src, void* dst,
-                            const CztDims& d, const Axis<cplx<XL_REAL>>& ax, int nb, cudaStream_t s) {
+                            const CztDims& d, const AxisRun<cplx<XL_REAL>>& ax, int nb, cudaStream_t s) {
 #define CP(LL)                                                                           \
   case LL:                                                                               \
     return vec ? pass_LV<XL_REAL, LL, true>(which, src, dst, d, ax, nb, s)              \

@@ -38,12 +38,35 @@ template <typename C> struct Axis {
   const C* bhat;
 };
 
+// Batch elements of one launch with their own distance (and so their own chirp tables).
+constexpr int kCztRun = 32;
+
+// The axis tables of every batch element of a launch: element b's tables start shift[b] elements
+// after the first element's (all zero, and b unbounded, when per_elem is 0).
+template <typename C> struct AxisRun : Axis<C> {
+  int per_elem;
+  int64_t shift[kCztRun];
+  __device__ __forceinline__ Axis<C> at(int b) const {
+    const int64_t s = per_elem ? shift[b < kCztRun ? b : kCztRun - 1] : 0;
+    return Axis<C>{this->pre + s, this->post + s, this->bhat + s};
+  }
+};
+template <typename C> inline AxisRun<C> axis_run(const Axis<C>& a) {
+  AxisRun<C> r;
+  r.pre = a.pre;
+  r.post = a.post;
+  r.bhat = a.bhat;
+  r.per_elem = 0;
+  for (int i = 0; i < kCztRun; ++i) r.shift[i] = 0;
+  return r;
+}
+
 struct CztDims {
   int nx, ny, mx, my;
   double x0, dx, y0, dy;      // input grid
   double xo0, dxo, yo0, dyo;  // output window
-  const double* zdev;         // device z (or nullptr)
-  double zval;
+  const double* zdev;         // device z of the launch's single element (or nullptr)
+  double z[kCztRun];          // host distance of each batch element of the launch
   int adjoint;                // 1 for the adjoint passes: the chirp spectrum is conj(bhat)
   int in_planes;              // planes per batch element of the input-grid field (fwd x input,
                               // adjoint x output): 1, 2, or 3 (a vector field whose Ez is unused)
@@ -114,14 +137,16 @@ __device__ __forceinline__ void store_transposed(const C (&v)[16], C* sm, int te
   constexpr int P = tpitch(L, sizeof(C), ROWS);
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < 16; ++q) sm[team * P + spad(t + q * TT)] = v[q];
+  for (int q = 0; q < 16; ++q)
+    if (q * TT < n_out) sm[team * P + spad(t + q * TT)] = v[q];  // block-uniform test
   __syncthreads();
-  store_rows_transposed<ROWS, P>(sm, n_out, dst, ld, c0, n_cols);
+  store_rows_transposed<L, ROWS, P>(sm, n_out, dst, ld, c0, n_cols);
   __syncthreads();
 }
 
-// Loads ROWS columns transposed: the team's row r gets src[j * ld + c0 + r] for j < n_in (zero
-// up to L), into registers.
+// Loads ROWS columns transposed: the team's row r gets src[j * ld + c0 + r] for j < n_in, into
+// registers. Entries at j >= n_in are not defined (left over in shared memory): every caller
+// masks them right after the load.
 template <int L, int ROWS, typename C>
 __device__ __forceinline__ void load_transposed(C (&v)[16], C* sm, int team, int t, int n_in,
                                                 const C* __restrict__ src, int64_t ld, int c0,
@@ -129,14 +154,17 @@ __device__ __forceinline__ void load_transposed(C (&v)[16], C* sm, int team, int
   constexpr int TT = L / 16;
   constexpr int P = tpitch(L, sizeof(C), ROWS);
   __syncthreads();
-  load_rows_transposed<ROWS, P>(sm, n_in, L, src, ld, c0, n_cols);
+  load_rows_transposed<L, ROWS, P>(sm, n_in, n_in, src, ld, c0, n_cols);
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = sm[team * P + spad(t + q * TT)];
+  for (int q = 0; q < 16; ++q)
+    v[q] = sm[team * P + spad(t + q * TT)];
   __syncthreads();
 }
 
-__device__ __forceinline__ double czt_z(const CztDims& d) { return d.zdev ? *d.zdev : d.zval; }
+__device__ __forceinline__ double czt_z(const CztDims& d, int b) {
+  return d.zdev ? *d.zdev : d.z[b < kCztRun ? b : kCztRun - 1];
+}
 
 #define XL_CZT_BOUNDS(T, L, VEC, V) \
   __launch_bounds__(czt_threads<L, sizeof(cplx<T>), VEC, V>(), czt_min_blocks<L, sizeof(cplx<T>), VEC, V>())
@@ -156,7 +184,7 @@ template <typename T> struct Coord {
 // grid: (ceil(ny / ROWS), nbatch). T plane layout: [mx][ny] (row p holds all n).
 template <typename T, int L, bool VEC, int V = 0>
 __global__ void XL_CZT_BOUNDS(T, L, VEC, V)
-k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d, Axis<cplx<T>> ax,
+k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d, AxisRun<cplx<T>> ax_run,
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
   constexpr int ROWS = czt_rows<L, sizeof(C), VEC, V>();
@@ -167,6 +195,7 @@ k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d,
   C* sm = reinterpret_cast<C*>(smraw);
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
   const int b = blockIdx.y;
+  const Axis<C> ax = ax_run.at(b);
   const int n0 = blockIdx.x * ROWS;
   const int n = min(n0 + team, d.ny - 1);  // teams past the edge compute a valid row, store nothing
   const int cT = VEC ? 3 : 1;
@@ -182,7 +211,7 @@ k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d,
     for (int q = 0; q < 16; ++q) {
       const int m = t + q * TT;
       C a = mk((T)0, (T)0);
-      if (m < d.nx) {
+      if (q * TT < d.nx && m < d.nx) {
         if (c < 2) a = s0[c * plane + m];
         else a = cadd(cscale(s0[m], xm.at(q)), cscale(s0[plane + m], yn));
         a = cmul(a, __ldg(ax.pre + m));
@@ -193,7 +222,7 @@ k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d,
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int p = t + q * TT;
-      if (p < d.mx) v[q] = cmul(v[q], __ldg(ax.post + p));
+      if (q * TT < d.mx && p < d.mx) v[q] = cmul(v[q], __ldg(ax.post + p));
     }
     store_transposed<L, ROWS>(v, sm, team, t, d.mx, Tb + ((int64_t)b * cT + c) * tplane, d.ny, n0,
                               d.ny);
@@ -206,7 +235,7 @@ k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d,
 // grid: (ceil(mx / ROWS), nbatch).
 template <typename T, int L, bool VEC, int V = 0>
 __global__ void XL_CZT_BOUNDS(T, L, VEC, V)
-k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d, Axis<cplx<T>> ay,
+k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d, AxisRun<cplx<T>> ay_run,
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
   constexpr int ROWS = czt_rows<L, sizeof(C), VEC, V>();
@@ -217,6 +246,7 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
   C* sm = reinterpret_cast<C*>(smraw);
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
   const int b = blockIdx.y;
+  const Axis<C> ay = ay_run.at(b);
   const int p0 = blockIdx.x * ROWS;
   const int p = min(p0 + team, d.mx - 1);
   const int cT = VEC ? 3 : 1;
@@ -227,7 +257,7 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
   T Xp = (T)0, iz = (T)0;
   if constexpr (VEC) {
     Xp = (T)(d.xo0 + p * d.dxo);
-    iz = (T)(-1.0 / czt_z(d));
+    iz = (T)(-1.0 / czt_z(d, b));
   }
   const Coord<T> yq(d.yo0, d.dyo, t, TT);
 #pragma unroll
@@ -237,13 +267,13 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int n = t + q * TT;
-      v[q] = n < d.ny ? cmul(s[n], __ldg(ay.pre + n)) : mk((T)0, (T)0);
+      v[q] = q * TT < d.ny && n < d.ny ? cmul(s[n], __ldg(ay.pre + n)) : mk((T)0, (T)0);
     }
     chirp_conv<L>(v, row, t, tw, ay.bhat, d.adjoint);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int qq = t + q * TT;
-      if (qq < d.my) v[q] = cmul(v[q], __ldg(ay.post + qq));
+      if (q * TT < d.my && qq < d.my) v[q] = cmul(v[q], __ldg(ay.post + qq));
     }
     if constexpr (VEC) {
       if (c == 0) {
@@ -268,7 +298,7 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
 // grid: (ceil(mx / ROWS), nbatch).
 template <typename T, int L, bool VEC, int V = 0>
 __global__ void XL_CZT_BOUNDS(T, L, VEC, V)
-k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, Axis<cplx<T>> ay,
+k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, AxisRun<cplx<T>> ay_run,
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
   constexpr int ROWS = czt_rows<L, sizeof(C), VEC, V>();
@@ -280,6 +310,7 @@ k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, 
   C* sm = reinterpret_cast<C*>(smraw);
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
   const int b = blockIdx.y;
+  const Axis<C> ay = ay_run.at(b);
   const int p0 = blockIdx.x * ROWS;
   const int p = min(p0 + team, d.mx - 1);
   const bool live = p0 + team < d.mx;
@@ -291,10 +322,10 @@ k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, 
   T Xp = (T)0, iz = (T)0;
   if constexpr (VEC) {
     Xp = (T)(d.xo0 + p * d.dxo);
-    iz = (T)(1.0 / czt_z(d));
+    iz = (T)(1.0 / czt_z(d, b));
     const C* gzsrc = G + ((int64_t)b * 3 + 2) * oplane;
     if constexpr (SMST) {
-      load_rows_transposed<ROWS, SR>(sm + ROWS * SR, d.my, L, gzsrc, d.mx, p0, d.mx);
+      load_rows_transposed<L, ROWS, SR>(sm + ROWS * SR, d.my, d.my, gzsrc, d.mx, p0, d.mx);
       __syncthreads();
     } else {
       load_transposed<L, ROWS>(gz.r, sm, team, t, d.my, gzsrc, d.mx, p0, d.mx);
@@ -322,7 +353,7 @@ k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, 
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int qq = t + q * TT;
-      v[q] = qq < d.my ? cmulc(v[q], __ldg(ay.post + qq)) : mk((T)0, (T)0);
+      v[q] = q * TT < d.my && qq < d.my ? cmulc(v[q], __ldg(ay.post + qq)) : mk((T)0, (T)0);
     }
     chirp_conv<L>(v, row, t, tw, ay.bhat, d.adjoint);
     if (live) {
@@ -330,7 +361,7 @@ k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, 
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int n = t + q * TT;
-        if (n < d.ny) dst[n] = cmulc(v[q], __ldg(ay.pre + n));
+        if (q * TT < d.ny && n < d.ny) dst[n] = cmulc(v[q], __ldg(ay.pre + n));
       }
     }
   }
@@ -342,7 +373,7 @@ k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, 
 // grid: (ceil(ny / ROWS), nbatch).
 template <typename T, int L, bool VEC, int V = 0>
 __global__ void XL_CZT_BOUNDS(T, L, VEC, V)
-k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d, Axis<cplx<T>> ax,
+k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d, AxisRun<cplx<T>> ax_run,
             const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
   constexpr int ROWS = czt_rows<L, sizeof(C), VEC, V>();
@@ -353,6 +384,7 @@ k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d
   C* sm = reinterpret_cast<C*>(smraw);
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
   const int b = blockIdx.y;
+  const Axis<C> ax = ax_run.at(b);
   const int n0 = blockIdx.x * ROWS;
   const int n = min(n0 + team, d.ny - 1);
   const bool live = n0 + team < d.ny;
@@ -364,19 +396,19 @@ k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d
   const Coord<T> xm(d.x0, d.dx, t, TT);
   const T yn = (T)(d.y0 + n * d.dy);
   if constexpr (VEC) {
-    const T iz = (T)(1.0 / czt_z(d));
+    const T iz = (T)(1.0 / czt_z(d, b));
     C v[16];
     load_transposed<L, ROWS>(v, sm, team, t, d.mx, Tb + ((int64_t)b * 3 + 2) * tplane, d.ny, n0, d.ny);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int pp = t + q * TT;
-      v[q] = pp < d.mx ? cmulc(v[q], __ldg(ax.post + pp)) : mk((T)0, (T)0);
+      v[q] = q * TT < d.mx && pp < d.mx ? cmulc(v[q], __ldg(ax.post + pp)) : mk((T)0, (T)0);
     }
     chirp_conv<L>(v, row, t, tw, ax.bhat, d.adjoint);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int m = t + q * TT;
-      zz.set(q, m < d.nx ? cscale(cmulc(v[q], __ldg(ax.pre + m)), iz) : mk((T)0, (T)0));
+      zz.set(q, q * TT < d.nx && m < d.nx ? cscale(cmulc(v[q], __ldg(ax.pre + m)), iz) : mk((T)0, (T)0));
     }
   }
 #pragma unroll
@@ -386,7 +418,7 @@ k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int pp = t + q * TT;
-      v[q] = pp < d.mx ? cmulc(v[q], __ldg(ax.post + pp)) : mk((T)0, (T)0);
+      v[q] = q * TT < d.mx && pp < d.mx ? cmulc(v[q], __ldg(ax.post + pp)) : mk((T)0, (T)0);
     }
     chirp_conv<L>(v, row, t, tw, ax.bhat, d.adjoint);
     if (live) {
@@ -394,7 +426,7 @@ k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int m = t + q * TT;
-        if (m < d.nx) {
+        if (q * TT < d.nx && m < d.nx) {
           C r = cmulc(v[q], __ldg(ax.pre + m));
           if constexpr (VEC) r = cadd(r, cscale(zz.get(q), c == 0 ? xm.at(q) : yn));
           dst[m] = r;

@@ -12,7 +12,7 @@ enum { CZT_FWD_X = 0, CZT_FWD_Y = 1, CZT_ADJ_Y = 2, CZT_ADJ_X = 3 };
 // One pass of length L (64..8192) over nbatch elements.
 template <typename T>
 xl_status czt_pass(int which, bool vec, int L, const void* src, void* dst, const CztDims& d,
-                   const Axis<cplx<T>>& axis, int nbatch, cudaStream_t s);
+                   const AxisRun<cplx<T>>& axis, int nbatch, cudaStream_t s);
 // Fills the chirp tables (both axes) and transforms the b rows in place.
 template <typename T>
 xl_status czt_tables(void* tab, const CztTabArgs& a, cudaStream_t s);

@@ -212,52 +212,88 @@ __host__ __device__ constexpr int tpitch(int L, int CS, int ROWS) {
   return srow(L) + ((((CS == 8 && (32 / CS < ROWS ? 32 / CS : ROWS) == 2) ? 8 : 4) - srow(L) % 16) + 16) % 16;
 }
 
-// Transposed block store: rows 0..ROWS-1 of the block's shared memory (pitch P) hold the
-// first n_out entries of ROWS transforms; element j of row r goes to dst[j * ld + c0 + r]
-// (r with c0 + r < n_cols). Lanes are grouped so that each warp instruction writes whole
-// 32-byte sectors (G = 32 / sizeof(C) consecutive rows of one j per group of lanes).
-template <int ROWS, int P, typename C>
+// Transposed block store by a block of ROWS teams of length-L transforms (ROWS * L / 16 threads):
+// rows 0..ROWS-1 of the block's shared memory (pitch P) hold the first n_out entries of ROWS
+// transforms; element j of row r goes to dst[j * ld + c0 + r] (r with c0 + r < n_cols). Lanes
+// are grouped so that each warp instruction writes whole 32-byte sectors (G = 32 / sizeof(C)
+// consecutive rows of one j per group of lanes). A thread keeps one row r and steps j by
+// JS = threads / G, so its row test, addresses and padding are computed once and advanced by
+// fixed steps; with n_out known at compile time the loop unrolls completely.
+template <int L, int ROWS, int P, typename C>
 __device__ __forceinline__ void store_rows_transposed(const C* sm, int n_out, C* __restrict__ dst,
                                                       int64_t ld, int c0, int n_cols) {
+  constexpr int NT = ROWS * (L / 16);
   constexpr int G0 = 32 / (int)sizeof(C);
   constexpr int G = G0 < ROWS ? G0 : ROWS;
   constexpr int LG = G == 4 ? 2 : (G == 2 ? 1 : 0);
+  constexpr int JS = NT / G;
+  static_assert(NT % G == 0, "transposed store: thread count and sector groups");
+  const int rr = threadIdx.x & (G - 1), j0 = threadIdx.x >> LG;
+  auto soff = [&](int k) {  // padded offset of j0 + k JS from j0
+    if constexpr (JS % 16 == 0) return k * (JS + JS / 16);
+    else return spad(j0 + k * JS) - spad(j0);
+  };
+  const int nfull = n_out / JS;  // iterations in which every thread's j is below n_out
+  const int64_t dstep = (int64_t)JS * ld;
 #pragma unroll 1
-  for (int grp = 0; grp < ROWS / G; ++grp)
-    for (int e = threadIdx.x; e < n_out * G; e += blockDim.x) {
-      const int r = grp * G + (e & (G - 1)), j = e >> LG;
-      if (c0 + r < n_cols) dst[(int64_t)j * ld + c0 + r] = sm[r * P + spad(j)];
+  for (int grp = 0; grp < ROWS / G; ++grp) {
+    const int r = grp * G + rr;
+    if (c0 + r < n_cols) {
+      const C* s = sm + r * P + spad(j0);
+      C* d = dst + (int64_t)j0 * ld + c0 + r;
+#pragma unroll 4
+      for (int k = 0; k < nfull; ++k) d[k * dstep] = s[soff(k)];
+      if (j0 + nfull * JS < n_out) d[nfull * dstep] = s[soff(nfull)];
     }
+  }
 }
 
-// Transposed block load (inverse of the store): row r of shared memory gets
+// Transposed block load (inverse of the store, same block shape): row r of shared memory gets
 // src[j * ld + c0 + r] for j < n_in and zero for n_in <= j < n_fill. Callers synchronise the
 // block before reading the rows. ASYNC: asynchronous global-to-shared copies (zero-filled where
 // there is no source element), so that a thread issues all of its copies before it waits once
 // (measured faster for RS pass 3, slower for the CZT adjoint passes, which keep plain loads).
-template <int ROWS, int P, typename C, bool ASYNC = false>
+template <int L, int ROWS, int P, typename C, bool ASYNC = false>
 __device__ __forceinline__ void load_rows_transposed(C* sm, int n_in, int n_fill,
                                                      const C* __restrict__ src, int64_t ld, int c0,
                                                      int n_cols) {
   typedef decltype(sm[0].x) T;
+  constexpr int NT = ROWS * (L / 16);
   constexpr int G0 = 32 / (int)sizeof(C);
   constexpr int G = G0 < ROWS ? G0 : ROWS;
   constexpr int LG = G == 4 ? 2 : (G == 2 ? 1 : 0);
-#pragma unroll 1
-  for (int grp = 0; grp < ROWS / G; ++grp)
-    for (int e = threadIdx.x; e < n_fill * G; e += blockDim.x) {
-      const int r = grp * G + (e & (G - 1)), j = e >> LG;
-      const bool ok = j < n_in && c0 + r < n_cols;
-      if constexpr (ASYNC) {
-        const C* g = ok ? src + (int64_t)j * ld + c0 + r : src;  // a valid address; 0 bytes read
-        const unsigned sa = (unsigned)__cvta_generic_to_shared(sm + r * P + spad(j));
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(sa), "l"(g),
-                     "n"((int)sizeof(C)), "r"(ok ? (int)sizeof(C) : 0)
-                     : "memory");
-      } else {
-        sm[r * P + spad(j)] = ok ? src[(int64_t)j * ld + c0 + r] : mk((T)0, (T)0);
-      }
+  constexpr int JS = NT / G;
+  static_assert(NT % G == 0, "transposed load: thread count and sector groups");
+  const int rr = threadIdx.x & (G - 1), j0 = threadIdx.x >> LG;
+  auto soff = [&](int k) {
+    if constexpr (JS % 16 == 0) return k * (JS + JS / 16);
+    else return spad(j0 + k * JS) - spad(j0);
+  };
+  const int nfull = n_fill / JS;
+  const int64_t sstep = (int64_t)JS * ld;
+  auto one = [&](C* s, const C* g, bool ok) {
+    if constexpr (ASYNC) {
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(sa),
+                   "l"(ok ? g : src),  // a valid address when nothing is read
+                   "n"((int)sizeof(C)), "r"(ok ? (int)sizeof(C) : 0)
+                   : "memory");
+    } else {
+      *s = ok ? *g : mk((T)0, (T)0);
     }
+  };
+#pragma unroll 1
+  for (int grp = 0; grp < ROWS / G; ++grp) {
+    const int r = grp * G + rr;
+    const bool col = c0 + r < n_cols;
+    C* s = sm + r * P + spad(j0);
+    const C* g = src + (int64_t)j0 * ld + c0 + r;
+#pragma unroll 4
+    for (int k = 0; k < nfull; ++k)
+      one(s + soff(k), g + k * sstep, col && j0 + k * JS < n_in);
+    if (j0 + nfull * JS < n_fill)
+      one(s + soff(nfull), g + nfull * sstep, col && j0 + nfull * JS < n_in);
+  }
   if constexpr (ASYNC) {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");

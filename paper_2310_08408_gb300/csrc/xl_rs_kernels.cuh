@@ -109,7 +109,7 @@ k_rs_pass1(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, int nx, int
 #pragma unroll
   for (int q = 0; q < 16; ++q) row[spad(t + q * TT)] = v[q];
   __syncthreads();
-  store_rows_transposed<ROWS, P>(sm, LX, dst, ny, y0, ny);
+  store_rows_transposed<LX, ROWS, P>(sm, LX, dst, ny, y0, ny);
 }
 
 // Block-wide sum of a double (one value per thread) -> thread 0; sbuf holds 32 doubles.
@@ -161,7 +161,7 @@ k_rs_pass3(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, int nx, in
     if (threadIdx.x == 0) red.out[b] = acc;
   }
   const C* src = Tb + ((int64_t)(p / cout) * cT + (p % cout)) * (int64_t)LX * ny;
-  load_rows_transposed<ROWS, P, C, true>(sm, LX, LX, src, ny, y0, ny);
+  load_rows_transposed<LX, ROWS, P, C, true>(sm, LX, LX, src, ny, y0, ny);
   __syncthreads();
   C* row = sm + team * P;
   C v[16];
@@ -729,7 +729,7 @@ k_gen_pass_a(cplx<T>* __restrict__ S, GenArgs g, const cplx<T>* __restrict__ tw)
 #pragma unroll
     for (int q = 0; q < 16; ++q) row[spad(t + q * TT)] = v[q];
     __syncthreads();
-    store_rows_transposed<ROWS, P>(sm, g.nx + 1, S + (int64_t)g.slot[kind] * g.s_plane, g.ny, b0, g.ny);
+    store_rows_transposed<LX, ROWS, P>(sm, g.nx + 1, S + (int64_t)g.slot[kind] * g.s_plane, g.ny, b0, g.ny);
     __syncthreads();
   }
 }

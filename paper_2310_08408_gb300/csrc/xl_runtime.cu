@@ -72,6 +72,8 @@ DeviceState& cur(int* dev_out = nullptr) {
 
 }  // namespace
 
+size_t table_cache_cap() { return cache_cap(); }
+
 // ---------------------------------------------------------------------------------------------
 // Autotuner choices: (family, L, dtype) -> (variant, measured microseconds). Process-wide (the
 // variants are properties of the kernels, and the library serves one GPU model per process).

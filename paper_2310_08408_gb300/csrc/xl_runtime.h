@@ -27,6 +27,10 @@ xl_status workspace(cudaStream_t stream, size_t bytes, void** out, int slot = 0)
 xl_status cached_table(const std::string& key, size_t bytes, cudaStream_t stream,
                        const std::function<xl_status(void*)>& gen, void** out);
 
+// Byte cap of that cache (XL_CACHE_BYTES, default 8 GiB). A caller that holds several entries
+// for one launch keeps their total within half of it, so that filling one never evicts another.
+size_t table_cache_cap();
+
 // Key helper: appends the raw bytes of a value.
 template <typename V> inline void key_put(std::string& k, const V& v) {
   k.append(reinterpret_cast<const char*>(&v), sizeof(V));

@@ -1,6 +1,6 @@
 // Autotuner of the transposing row passes: for a grid (and output window) it times the launch
 // variants of RS passes 1 and 3 and of the four CZT window passes on synthetic data on the
-// current device, keeps the fastest per (kernel family, row length, dtype) for the launchers,
+// current device (launches over several planes, as batched calls make them), keeps the fastest per (kernel family, row length, dtype) for the launchers,
 // and saves / loads the choices as text. Variants differ only in how many rows a block holds
 // (threads per block, register budget, shared memory), so every variant computes bit-identical
 // results; the choice only changes speed.
@@ -70,6 +70,15 @@ xl_status tune_one(int family, int L, int dtype, int reps, cudaStream_t s, F run
   return st;
 }
 
+// Planes one timed launch processes: enough that its data exceeds L2 (256 MB of the larger
+// per-plane buffer), as in the batched calls, which run the row passes over whole chunks of the
+// batch (at most 16 planes).
+int tune_planes(size_t plane_bytes) {
+  const size_t want = (size_t)256 << 20;
+  const size_t n = (want + plane_bytes - 1) / (plane_bytes ? plane_bytes : 1);
+  return (int)std::min<size_t>(std::max<size_t>(n, 1), 16);
+}
+
 template <typename T>
 xl_status tune_grid(const xl_grid* g, const xl_window* w, int dtype, int reps, cudaStream_t s) {
   typedef cplx<T> C;
@@ -77,46 +86,49 @@ xl_status tune_grid(const xl_grid* g, const xl_window* w, int dtype, int reps, c
   const size_t cs = sizeof(C);
   const int LX = 2 * nx;
   if (LX >= kTuneMinL && LX <= 8192) {
+    const int np = tune_planes((size_t)LX * ny * cs);
     DevBuf in, Tb;
-    XL_TRY(in.alloc((size_t)nx * ny * cs, s));
-    XL_TRY(Tb.alloc((size_t)LX * ny * cs, s));
+    XL_TRY(in.alloc((size_t)np * nx * ny * cs, s));
+    XL_TRY(Tb.alloc((size_t)np * LX * ny * cs, s));
     XL_TRY(tune_one(TUNE_RS_PASS1, LX, dtype, reps, s,
-                    [&] { return rs_pass1<T>(in.p, Tb.p, nx, ny, 1, 1, 1, s); }));
+                    [&] { return rs_pass1<T>(in.p, Tb.p, nx, ny, 1, 1, np, s); }));
     XL_TRY(tune_one(TUNE_RS_PASS3, LX, dtype, reps, s,
-                    [&] { return rs_pass3<T>(Tb.p, in.p, nx, ny, 1, 1, 1, s); }));
+                    [&] { return rs_pass3<T>(Tb.p, in.p, nx, ny, 1, 1, np, s); }));
   }
   if (w) {
     const int mx = w->mx, my = w->my;
     const int Lx = czt_length(nx, mx), Ly = czt_length(ny, my);
     if (Lx > 8192 || Ly > 8192) return fail(XL_ERR_UNSUPPORTED, "autotune: N + M - 1 > 8192");
     const int tab_n = std::max(std::max(nx, ny), std::max(std::max(mx, my), std::max(Lx, Ly)));
+    const int np = std::min(tune_planes((size_t)std::max(nx, mx) * ny * cs), kCztRun);
     DevBuf in, Tb, out, tab;
-    XL_TRY(in.alloc((size_t)nx * ny * cs, s));
-    XL_TRY(Tb.alloc((size_t)mx * ny * cs, s));
-    XL_TRY(out.alloc((size_t)mx * my * cs, s));
+    XL_TRY(in.alloc((size_t)np * nx * ny * cs, s));
+    XL_TRY(Tb.alloc((size_t)np * mx * ny * cs, s));
+    XL_TRY(out.alloc((size_t)np * mx * my * cs, s));
     XL_TRY(tab.alloc((size_t)tab_n * cs, s));  // zero chirps: the timing does not depend on values
-    Axis<C> ax;
-    ax.pre = ax.post = ax.bhat = (const C*)tab.p;
+    Axis<C> ax1;
+    ax1.pre = ax1.post = ax1.bhat = (const C*)tab.p;
+    const AxisRun<C> ax = axis_run(ax1);
     CztDims d;
     std::memset(&d, 0, sizeof(d));
     d.nx = nx; d.ny = ny; d.mx = mx; d.my = my;
     d.dx = g->dx; d.dy = g->dy; d.dxo = w->dxo; d.dyo = w->dyo;
-    d.zval = 1.0;
+    d.z[0] = 1.0;
     d.in_planes = 1;
     if (Lx >= kTuneMinL) {
       XL_TRY(tune_one(TUNE_CZT_FWD_X, Lx, dtype, reps, s,
-                      [&] { return czt_pass<T>(CZT_FWD_X, false, Lx, in.p, Tb.p, d, ax, 1, s); }));
+                      [&] { return czt_pass<T>(CZT_FWD_X, false, Lx, in.p, Tb.p, d, ax, np, s); }));
       d.adjoint = 1;
       XL_TRY(tune_one(TUNE_CZT_ADJ_X, Lx, dtype, reps, s,
-                      [&] { return czt_pass<T>(CZT_ADJ_X, false, Lx, Tb.p, in.p, d, ax, 1, s); }));
+                      [&] { return czt_pass<T>(CZT_ADJ_X, false, Lx, Tb.p, in.p, d, ax, np, s); }));
       d.adjoint = 0;
     }
     if (Ly >= kTuneMinL) {
       XL_TRY(tune_one(TUNE_CZT_FWD_Y, Ly, dtype, reps, s,
-                      [&] { return czt_pass<T>(CZT_FWD_Y, false, Ly, Tb.p, out.p, d, ax, 1, s); }));
+                      [&] { return czt_pass<T>(CZT_FWD_Y, false, Ly, Tb.p, out.p, d, ax, np, s); }));
       d.adjoint = 1;
       XL_TRY(tune_one(TUNE_CZT_ADJ_Y, Ly, dtype, reps, s,
-                      [&] { return czt_pass<T>(CZT_ADJ_Y, false, Ly, out.p, Tb.p, d, ax, 1, s); }));
+                      [&] { return czt_pass<T>(CZT_ADJ_Y, false, Ly, out.p, Tb.p, d, ax, np, s); }));
       d.adjoint = 0;
     }
   }
