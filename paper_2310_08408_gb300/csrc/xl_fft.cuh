@@ -300,6 +300,17 @@ __device__ __forceinline__ void load_rows_transposed(C* sm, int n_in, int n_fill
   }
 }
 
+// Asks L2 to fetch the bytes [p, p + bytes) ahead of their loads (one bulk prefetch: no
+// registers held, no completion to wait for). The range is shrunk to whole 16-byte units inside
+// it, as the instruction requires; the ends are read by the loads themselves.
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+  const uintptr_t s = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+  const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+  if (e > s)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(s), "r"((unsigned)(e - s))
+                 : "memory");
+}
+
 // Thread-private 16-element stash (element q of thread t is row element t + q L/16), in a shared
 // memory row or in registers.
 template <typename C, int TT, bool SMEM> struct Stash {

@@ -314,6 +314,26 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
   auto spec_in = [&](int c) {
     return reinterpret_cast<const C*>(a.spec_in) + ((int64_t)b * a.cS + c) * spec_plane + (int64_t)kx * LY;
   };
+  // One thread of the team asks L2 for the spectrum rows and saved spectra this column reads
+  // after its first transform, so that those loads do not wait on DRAM.
+  if (t == 0) {
+    const size_t row_bytes = (size_t)(a.ny + 1) * sizeof(C), col_bytes = (size_t)LY * sizeof(C);
+    auto pf = [&](int kind) { prefetch_l2(H(kind), row_bytes); };
+    if constexpr (MODE == P2_RS) {
+      pf(KH);
+    } else if constexpr (MODE == P2_VRS) {
+      pf(KH); pf(KHX); pf(KHY);
+    } else if constexpr (MODE == P2_RS_BWD_S) {
+      if (a.want_dz) { prefetch_l2(spec_in(0), col_bytes); pf(KDH); }
+      if (a.want_field) pf(KH);
+    } else if constexpr (MODE == P2_VRS_BWD_S) {
+      if (a.want_dz) {
+        prefetch_l2(spec_in(0), col_bytes); prefetch_l2(spec_in(1), col_bytes);
+        pf(KDH); pf(KDHX); pf(KDHY);
+      }
+      if (a.want_field) { pf(KH); pf(KHX); pf(KHY); }
+    }
+  }
   if constexpr (MODE == P2_RS) {
     load_col(v, T0, t, TT);
     team_fft<LY, -1>(v, row, t, tw);
