@@ -495,10 +495,18 @@ def main():
         peaks = json.load(open(pk_path))
     hbm = peaks.get("hbm_gbs", 6800.0)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
+    def fields_per_launch(name, cnt):
+        """Fields one launch of kernel family `name` processed: the step makes two passes of
+        the row kernels (forward and adjoint RS) and one of every other kernel per field; the
+        library batches the fields of a call into fewer launches."""
+        per_step = (2 if name.startswith(("rs_pass1", "rs_pass3")) else 1) * B
+        return per_step / (cnt / 3)
+
     if top is not None:
         name, (cnt, tot) = top
         avg_s = tot / cnt / 1000.0
-        flops, nbytes = kernel_model(name, {"n": N, "m": M, "per_launch": 1})
+        flops, nbytes = kernel_model(name, {"n": N, "m": M,
+                                            "per_launch": fields_per_launch(name, cnt)})
         clk = ck.get("sm_mhz") or 1900.0
         fp32_peak = sms * 128 * 2 * clk * 1e6 / 1e12  # TFLOP/s, CUDA-core FMA rate at the sampled clock
         traffic = load_traffic().get(name)
@@ -519,7 +527,8 @@ def main():
                         "frac": ach / hbm, "traffic": traffic, "kernel": name,
                         "share": tot / total if total else None,
                         "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
-    kernels = {k: {"launches": v[0] // 3, "ms_per_step": v[1] / 3} for k, v in prof.items()}
+    kernels = {k: {"launches": v[0] // 3, "ms_per_step": v[1] / 3,
+                   "fields_per_launch": fields_per_launch(k, v[0])} for k, v in prof.items()}
 
     # end to end: pinned host input -> device, the step, results back to pinned host buffers,
     # streamed in chunks of E2E_CHUNK fields so that the copies overlap the kernels

@@ -1,6 +1,7 @@
 // C ABI of scalar and vectorial RS propagation and their adjoints (host orchestration of the
 // kernels in xl_rs_kernels.cuh). Methods, "Features and performance": FFT-based numerical
 // integration of the Rayleigh-Sommerfeld integral, scalar (RS) and vectorial (VRS).
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -121,6 +122,8 @@ P2Args p2_args(const xl_grid* g, const Spectra& sp, int cT, int cU) {
   a.spec_out = nullptr;
   a.spec_in = nullptr;
   a.cS = 0;
+  a.per_elem = 0;
+  for (int i = 0; i < kP2Run; ++i) a.hshift[i] = 0;
   return a;
 }
 
@@ -133,10 +136,11 @@ xl_status launch_reduce(const double* part, int n, double* out, int nb, cudaStre
 }
 
 // How many batch elements the row passes (1 and 3) process per launch: as many as fit a byte
-// budget for their T planes (XL_RS_CHUNK_MB, default 2048 MB). Pass 2 runs once per run of equal
-// distances in the chunk. Measured on 16 fields of 2048^2 (T planes of 67 MB each): one chunk of
-// all 16 runs the row passes 25% faster than chunks of one field kept resident in L2, because
-// the row passes then fill every SM for many waves; pass 2 is unaffected by reading T from DRAM.
+// budget for their T planes (XL_RS_CHUNK_MB, default 2048 MB); pass 2 takes the chunk in groups
+// of up to kP2Run elements, each reading the spectra of its own distance. Measured on 16 fields of
+// 2048^2 (T planes of 67 MB each): one chunk of all 16 runs the row passes 25% faster than chunks
+// of one field kept resident in L2, because the row passes then fill every SM for many waves;
+// pass 2 is unaffected by reading T from DRAM.
 int chunk_size(int64_t t_bytes_per_elem, int32_t remaining) {
   int64_t budget = (int64_t)2048 << 20;
   if (const char* e = getenv("XL_RS_CHUNK_MB")) {
@@ -187,6 +191,12 @@ xl_status run_op(Op op, const void* in, const void* u_in, void* out, double* g_z
   const int cUw = save_in ? 0 : cU;  // U planes computed into the workspace
   const int64_t elem_ws = (int64_t)(cT + cUw) * t_plane * cs;
   const int chunk_max = zdev ? 1 : chunk_size(elem_ws, batch);
+  // pass-2 group: up to kP2Run elements whose spectra together stay within half of the table
+  // cache, so that fetching one never evicts another of the same launch
+  const size_t hq_bytes1 = (size_t)sp.count * (nx + 1) * (ny + 1) * cs;
+  const int group_max = zdev ? 1
+                             : (int)std::max<int64_t>(1, std::min<int64_t>(kP2Run,
+                                   (int64_t)(table_cache_cap() / 2 / hq_bytes1)));
   // workspace: T (chunk * cT planes) | U (chunk * cU planes) | dz partials | [S | Hq] (device z)
   const size_t t_bytes = (size_t)chunk_max * cT * t_plane * cs;
   const size_t u_bytes = (size_t)chunk_max * cUw * t_plane * cs;
@@ -215,14 +225,21 @@ xl_status run_op(Op op, const void* in, const void* u_in, void* out, double* g_z
     XL_TRY(rs_pass1<T>(src + (size_t)b0 * cin * plane * cs, Tb, nx, ny, cin, cT, nc * cin, s));
     if (want_dz && !save_in)
       XL_TRY(rs_pass1<T>(usrc + (size_t)b0 * cU * plane * cs, Ub, nx, ny, cU, cU, nc * cU, s));
+    // pass 2 over groups of up to kP2Run elements, each element with the spectra of its own
+    // distance (one group per element with device distances)
     for (int32_t r0 = b0; r0 < b0 + nc;) {
-      int nb = 1;
-      if (!zdev)
-        while (r0 + nb < b0 + nc && z[r0 + nb] == z[r0]) ++nb;
-      const int64_t e0 = r0 - b0;  // first element of the run within the chunk
-      const void* Hq = nullptr;
-      XL_TRY(get_spectra(g, wavelength, sp, dtype, z + r0, flags, dev_s, dev_hq, s, &Hq));
+      const int nb = (int)std::min<int64_t>(group_max, b0 + nc - r0);
+      const int64_t e0 = r0 - b0;  // first element of the group within the chunk
       P2Args a = p2_args(g, sp, cT, cU);
+      const void* Hq0 = nullptr;
+      const void* Hq = nullptr;
+      for (int e = 0; e < nb; ++e) {
+        if (e == 0 || z[r0 + e] != z[r0 + e - 1])
+          XL_TRY(get_spectra(g, wavelength, sp, dtype, z + r0 + e, flags, dev_s, dev_hq, s, &Hq));
+        if (e == 0) Hq0 = Hq;
+        a.hshift[e] = (const cplx<T>*)Hq - (const cplx<T>*)Hq0;
+      }
+      a.per_elem = nb > 1 ? 1 : 0;
       if (save_out) {  // pass 2 also stores the column spectra of the inputs
         a.spec_out = (char*)save_out + (size_t)r0 * cin * spec_plane * cs;
         a.cS = cin;
@@ -234,7 +251,7 @@ xl_status run_op(Op op, const void* in, const void* u_in, void* out, double* g_z
       a.want_field = want_field;
       a.want_dz = want_dz;
       XL_TRY(rs_pass2<T>(mode, (char*)Tb + e0 * cT * t_plane * cs,
-                         (const char*)Ub + e0 * cUw * t_plane * cs, Hq, dzp + e0 * p2blocks, a, nb,
+                         (const char*)Ub + e0 * cUw * t_plane * cs, Hq0, dzp + e0 * p2blocks, a, nb,
                          s));
       // the distance partials are summed by pass 3 when it runs, else by their own launch
       if (want_dz && !want_field)

@@ -188,6 +188,9 @@ enum {
   P2_VRS_BWD_S = 5, // P2_VRS_BWD likewise
 };
 
+// Batch elements of one pass-2 launch with their own distance (and so their own spectra).
+constexpr int kP2Run = 32;
+
 struct P2Args {
   int nx, ny;
   int64_t t_plane;      // elements of one T plane (LX * ny)
@@ -202,6 +205,9 @@ struct P2Args {
                         // the transfer spectrum) here, [b][cS][LX][LY] (nullable)
   const void* spec_in;  // *_BWD_S modes: U's column spectra saved by a forward, same layout
   int cS;               // planes per batch element of spec_out / spec_in
+  int per_elem;         // 1: element b's spectra start hshift[b] elements after Hq (its own
+                        // distance); 0: every element uses Hq
+  int64_t hshift[kP2Run];
 };
 
 // Spectrum `Hk` along one kx row at ky = t + q TT (TT = LY / 16, ny = 8 TT): the quadrant row
@@ -302,7 +308,8 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
   C* T0 = Tb + (int64_t)b * a.cT * a.t_plane + (int64_t)kx * a.ny;
   const bool flipx = kx > a.nx;
   const int64_t hrow_off = (int64_t)(flipx ? LX - kx : kx) * (a.ny + 1);
-  auto H = [&](int kind) { return Hq + a.slot[kind] * a.hq_kind + hrow_off; };
+  const cplx<T>* Hqb = Hq + (a.per_elem ? a.hshift[b < kP2Run ? b : kP2Run - 1] : 0);
+  auto H = [&](int kind) { return Hqb + a.slot[kind] * a.hq_kind + hrow_off; };
   C v[16];
   double dz = 0.0;
 

@@ -126,6 +126,8 @@ xl_status run_static(const float2* in, float2* out, int32_t batch, const xl_grid
   pa.spec_out = nullptr;
   pa.spec_in = nullptr;
   pa.cS = 0;
+  pa.per_elem = 0;
+  for (int i = 0; i < kP2Run; ++i) pa.hshift[i] = 0;
 
   // every launch below needs less than 48 KB of shared memory (transform lengths <= 512)
   constexpr int RA = rows_transp<LX, 8>(), R3 = rows_p3<LX, 8>(), RB = rows_cols<LY>(),
