@@ -139,8 +139,9 @@ def kernel_model(name: str, dims: dict):
 
 
 def load_traffic():
-    """Per-launch DRAM traffic of kernel families from the committed ncu summary, valid only
-    while the kernel sources are unchanged (hash recorded with the counters)."""
+    """Per-field DRAM traffic of kernel families from the committed ncu summary (a launch moves
+    that many bytes for each field it processes), valid only while the kernel sources are
+    unchanged (hash recorded with the counters)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return {}
@@ -149,7 +150,7 @@ def load_traffic():
         from paper_2310_08408_gb300 import build
         if data.get("csrc_hash") != build.source_hash():
             return {}
-        return data.get("bytes_per_launch", {})
+        return data.get("bytes_per_field", {})
     except Exception:
         return {}
 
@@ -509,7 +510,8 @@ def main():
                                             "per_launch": fields_per_launch(name, cnt)})
         clk = ck.get("sm_mhz") or 1900.0
         fp32_peak = sms * 128 * 2 * clk * 1e6 / 1e12  # TFLOP/s, CUDA-core FMA rate at the sampled clock
-        traffic = load_traffic().get(name)
+        per_field = load_traffic().get(name)
+        traffic = per_field * fields_per_launch(name, cnt) if per_field is not None else None
         if flops is not None:
             t_alu = flops / (fp32_peak * 1e12)
             t_mem = nbytes / (hbm * 1e9)
