@@ -571,10 +571,20 @@ def main():
         barrier()
         ems = e0.elapsed_time(e1)
         ems = replicas.max_over_ranks(ems, "cuda")
+        # the host link alone on this machine: one whole-batch pinned upload and download
+        link = {}
+        for name, dst, src in (("h2d_gbs", step.U, U_pin), ("d2h_gbs", A_h, step.A)):
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            link[name] = src.numel() * src.element_size() / (e0.elapsed_time(e1) / 1000.0) / 1e9
         e2e = {"value": replicas.whole_job_rate(step.props, world, ke, ems), "unit": "propagations/s",
                "h2d_bytes_per_step": int(U_pin.numel() * 8),
                "d2h_bytes_per_step": int(A_h.numel() * 8 + C_h.numel() * 8 + gz_h.numel() * 8),
-               "ms_per_step": ems / ke}
+               "ms_per_step": ems / ke, "host_link": link}
 
     nxt = None
     if not a.no_next:
