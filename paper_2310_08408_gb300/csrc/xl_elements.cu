@@ -110,10 +110,10 @@ __device__ __forceinline__ void japply_h(const Jones2<T>& J, cplx<T>& g0, cplx<T
 }
 // Re(conj(g) . (J u))
 template <typename T>
-__device__ __forceinline__ double jre(const Jones2<T>& J, cplx<T> g0, cplx<T> g1, cplx<T> u0, cplx<T> u1) {
+__device__ __forceinline__ T jre(const Jones2<T>& J, cplx<T> g0, cplx<T> g1, cplx<T> u0, cplx<T> u1) {
   cplx<T> a = cadd(cmul(J.a, u0), cmul(J.b, u1));
   cplx<T> b = cadd(cmul(J.c, u0), cmul(J.d, u1));
-  return (double)cdot_re(g0, a) + (double)cdot_re(g1, b);
+  return cdot_re(g0, a) + cdot_re(g1, b);
 }
 
 __device__ __forceinline__ double eparam(const ElemSet& E, const ElemDims& d, int b, int e, int j) {
@@ -156,11 +156,35 @@ __device__ __forceinline__ cplx<T> lens_factor(const cplx<T>* tab, int s, int b,
   return cmul(t[m], t[d.nx + n]);
 }
 
-// Applies element e to (c0, c1). Returns the state after it.
+// Jones matrices of the polarisers and wave plates of batch element b (and their parameter
+// derivatives), one entry per element: they depend on the element's parameters only, so a block
+// whose pixels share b forms them once in shared memory instead of once per pixel.
+template <typename T> struct JonesTab {
+  Jones2<T> J[kMaxElem], dA[kMaxElem], dB[kMaxElem];  // dA: d/dalpha or d/deta; dB: d/dtheta
+  T lens_c[kMaxElem];  // lenses: k / (2 f^2), so that d out / d f = i lens_c (x^2 + y^2) out
+};
+// Threads 0..E.n-1 fill entry e = threadIdx.x for batch element b; callers synchronise after.
+template <typename T>
+__device__ __forceinline__ void jones_fill(JonesTab<T>& jt, const ElemSet& E, const ElemDims& d, int b,
+                                           bool derivs) {
+  const int e = threadIdx.x;
+  if (e >= E.n) return;
+  if (E.kind[e] == XL_LENS) {
+    const double f = eparam(E, d, b, e, 0);
+    jt.lens_c[e] = (T)(d.k / (2.0 * f * f));
+  } else if (E.kind[e] == XL_POLARIZER) {
+    polarizer<T>(eparam(E, d, b, e, 1), &jt.J[e], derivs ? &jt.dA[e] : nullptr);
+  } else if (E.kind[e] == XL_WAVEPLATE) {
+    waveplate<T>(eparam(E, d, b, e, 2), eparam(E, d, b, e, 3), &jt.J[e], derivs ? &jt.dA[e] : nullptr,
+                 derivs ? &jt.dB[e] : nullptr);
+  }
+}
+
+// Applies element e to (c0, c1). Returns the state after it. jt: the element's Jones matrices.
 template <typename T>
 __device__ __forceinline__ void elem_fwd(const ElemSet& E, const ElemDims& d, const cplx<T>* lens,
                                          int nlens, int e, int b, int64_t i, int m, int n,
-                                         cplx<T>& c0, cplx<T>& c1, cplx<T>& c2) {
+                                         cplx<T>& c0, cplx<T>& c1, cplx<T>& c2, const JonesTab<T>& jt) {
   switch (E.kind[e]) {
     case XL_SLM: {
       T s, c;
@@ -185,18 +209,10 @@ __device__ __forceinline__ void elem_fwd(const ElemSet& E, const ElemDims& d, co
       c2 = cmul(c2, L);
       break;
     }
-    case XL_POLARIZER: {
-      Jones2<T> J;
-      polarizer<T>(eparam(E, d, b, e, 1), &J, nullptr);
-      japply(J, c0, c1);
+    case XL_POLARIZER:
+    case XL_WAVEPLATE:
+      japply(jt.J[e], c0, c1);
       break;
-    }
-    case XL_WAVEPLATE: {
-      Jones2<T> J;
-      waveplate<T>(eparam(E, d, b, e, 2), eparam(E, d, b, e, 3), &J, nullptr, nullptr);
-      japply(J, c0, c1);
-      break;
-    }
     case XL_TO_VECTOR:
       c1 = mk((T)0, (T)0);
       break;
@@ -209,14 +225,17 @@ __global__ void __launch_bounds__(256) k_elem_fwd(const cplx<T>* __restrict__ in
                                                   ElemSet E, ElemDims d, const cplx<T>* __restrict__ lens,
                                                   int nlens) {
   const int b = blockIdx.y;
+  __shared__ JonesTab<T> jt;
+  jones_fill<T>(jt, E, d, b, false);
+  __syncthreads();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= d.plane) return;
-  const int m = (int)(i % d.nx), n = (int)(i / d.nx);
+  const int m = (int)i % d.nx, n = (int)i / d.nx;  // plane < 2^31: 32-bit division
   const cplx<T>* src = in + (int64_t)b * d.comps_in * d.plane;
   cplx<T> c0 = src[i];
   cplx<T> c1 = d.comps_in >= 2 ? src[d.plane + i] : mk((T)0, (T)0);
   cplx<T> c2 = d.comps_in == 3 ? src[2 * d.plane + i] : mk((T)0, (T)0);
-  for (int e = 0; e < E.n; ++e) elem_fwd<T>(E, d, lens, nlens, e, b, i, m, n, c0, c1, c2);
+  for (int e = 0; e < E.n; ++e) elem_fwd<T>(E, d, lens, nlens, e, b, i, m, n, c0, c1, c2, jt);
   cplx<T>* dst = out + (int64_t)b * d.comps_out * d.plane;
   dst[i] = c0;
   if (d.comps_out >= 2) dst[d.plane + i] = c1;
@@ -230,121 +249,141 @@ struct ElemGrad {
   int accumulate_shared;  // masks with stride 0 are shared: sum over the batch inside the thread
 };
 
-// Backward. grid: (ceil(plane / 256), batch or 1). When masks are shared (stride 0) the batch
-// loop runs inside the thread so that dL/dphi sums over the batch without atomics.
+// Whether element kind `kind` has scalar parameter j (0 f, 1 alpha, 2 eta, 3 theta).
+__host__ __device__ __forceinline__ bool has_scalar(int kind, int j) {
+  return (kind == XL_LENS && j == 0) || (kind == XL_POLARIZER && j == 1) ||
+         (kind == XL_WAVEPLATE && (j == 2 || j == 3));
+}
+
+// Pixels a thread of the per-element backward takes (the block reductions of the scalar
+// gradients then cover 256 * kPixBwd pixels each).
+constexpr int kPixBwd = 8;
+
+// Backward. grid: (ceil(plane / (256 pix)), batch), or (ceil(plane / 256), 1) with pix = 1 when
+// masks are shared (stride 0): the batch loop then runs inside the thread so that dL/dphi sums
+// over the batch without atomics.
 template <typename T>
 __global__ void __launch_bounds__(256) k_elem_bwd(const cplx<T>* __restrict__ gout, const cplx<T>* __restrict__ in,
                                                   cplx<T>* __restrict__ gin, ElemSet E, ElemDims d,
                                                   const cplx<T>* __restrict__ lens, int nlens,
-                                                  ElemGrad G, int batch) {
+                                                  ElemGrad G, int batch, int pix) {
   __shared__ double red[32];
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const bool live = i < d.plane;
-  const int64_t ii = live ? i : d.plane - 1;
-  const int m = (int)(ii % d.nx), n = (int)(ii / d.nx);
   const int b_lo = G.accumulate_shared ? 0 : blockIdx.y;
   const int b_hi = G.accumulate_shared ? batch : blockIdx.y + 1;
   T gphx_acc[kMaxElem], gphy_acc[kMaxElem];
 #pragma unroll
   for (int e = 0; e < kMaxElem; ++e) gphx_acc[e] = gphy_acc[e] = (T)0;
+  __shared__ JonesTab<T> jt;
   for (int b = b_lo; b < b_hi; ++b) {
-    cplx<T> s0[kMaxElem + 1], s1[kMaxElem + 1], s2[kMaxElem + 1];
-    const cplx<T>* src = in + (int64_t)b * d.comps_in * d.plane;
-    s0[0] = src[ii];
-    s1[0] = d.comps_in >= 2 ? src[d.plane + ii] : mk((T)0, (T)0);
-    s2[0] = d.comps_in == 3 ? src[2 * d.plane + ii] : mk((T)0, (T)0);
+    jones_fill<T>(jt, E, d, b, true);
+    __syncthreads();
+    // this thread's sums of the scalar gradients over its pixels (in T: FP64 runs at a small
+    // fraction of the FP32 rate; the block sums below are in double)
+    T sg[kMaxElem][4];
 #pragma unroll
-    for (int e = 0; e < kMaxElem; ++e) {
-      if (e >= E.n) break;
-      s0[e + 1] = s0[e];
-      s1[e + 1] = s1[e];
-      s2[e + 1] = s2[e];
-      elem_fwd<T>(E, d, lens, nlens, e, b, ii, m, n, s0[e + 1], s1[e + 1], s2[e + 1]);
-    }
-    const cplx<T>* gsrc = gout + (int64_t)b * d.comps_out * d.plane;
-    cplx<T> g0 = gsrc[ii];
-    cplx<T> g1 = d.comps_out >= 2 ? gsrc[d.plane + ii] : mk((T)0, (T)0);
-    cplx<T> g2 = d.comps_out == 3 ? gsrc[2 * d.plane + ii] : mk((T)0, (T)0);
-    double sg[kMaxElem][4];
-#pragma unroll
-    for (int e = 0; e < kMaxElem; ++e) sg[e][0] = sg[e][1] = sg[e][2] = sg[e][3] = 0.0;
-#pragma unroll
-    for (int e = kMaxElem - 1; e >= 0; --e) {
-      if (e >= E.n) continue;
-      const cplx<T> u0 = s0[e], u1 = s1[e], o0 = s0[e + 1], o1 = s1[e + 1], o2 = s2[e + 1];
-      switch (E.kind[e]) {
-        case XL_SLM: {
-          gphx_acc[e] += cmulc(g0, o0).y + cmulc(g1, o1).y + cmulc(g2, o2).y;
-          T s, c;
-          xsincos(phase_at<T>(E.phx[e], E.phstride[e], b, ii), &s, &c);
-          g0 = cmul(g0, mk(c, -s));
-          g1 = cmul(g1, mk(c, -s));
-          g2 = cmul(g2, mk(c, -s));
-          break;
-        }
-        case XL_SSLM: {
-          gphx_acc[e] += cmulc(g0, o0).y;
-          gphy_acc[e] += cmulc(g1, o1).y;
-          T s, c;
-          xsincos(phase_at<T>(E.phx[e], E.phstride[e], b, ii), &s, &c);
-          g0 = cmul(g0, mk(c, -s));
-          xsincos(phase_at<T>(E.phy[e], E.phstride[e], b, ii), &s, &c);
-          g1 = cmul(g1, mk(c, -s));
-          break;
-        }
-        case XL_LENS: {
-          const double f = eparam(E, d, b, e, 0);
-          const T xm = (T)(d.x0 + m * d.dx), yn = (T)(d.y0 + n * d.dy);
-          const T coef = (T)(d.k / (2.0 * f * f)) * (xm * xm + yn * yn);  // d out / d f = i coef out
-          sg[e][0] += (double)cdot_re(g0, mk(-o0.y * coef, o0.x * coef)) +
-                      (double)cdot_re(g1, mk(-o1.y * coef, o1.x * coef)) +
-                      (double)cdot_re(g2, mk(-o2.y * coef, o2.x * coef));
-          cplx<T> L = lens_factor<T>(lens, E.lens_slot[e], d.params_dev ? b : 0, nlens, d, m, n);
-          g0 = cmulc(g0, L);
-          g1 = cmulc(g1, L);
-          g2 = cmulc(g2, L);
-          break;
-        }
-        case XL_POLARIZER: {
-          Jones2<T> J, dJ;
-          polarizer<T>(eparam(E, d, b, e, 1), &J, &dJ);
-          sg[e][1] += jre(dJ, g0, g1, u0, u1);
-          japply_h(J, g0, g1);
-          break;
-        }
-        case XL_WAVEPLATE: {
-          Jones2<T> J, dJe, dJt;
-          waveplate<T>(eparam(E, d, b, e, 2), eparam(E, d, b, e, 3), &J, &dJe, &dJt);
-          sg[e][2] += jre(dJe, g0, g1, u0, u1);
-          sg[e][3] += jre(dJt, g0, g1, u0, u1);
-          japply_h(J, g0, g1);
-          break;
-        }
-        case XL_TO_VECTOR:
-          g1 = mk((T)0, (T)0);
-          break;
-      }
-    }
-    if (live && gin) {
-      cplx<T>* dst = gin + (int64_t)b * d.comps_in * d.plane;
-      dst[i] = g0;
-      if (d.comps_in >= 2) dst[d.plane + i] = g1;
-      if (d.comps_in == 3) dst[2 * d.plane + i] = g2;
-    }
-    if (!G.accumulate_shared && live) {
+    for (int e = 0; e < kMaxElem; ++e) sg[e][0] = sg[e][1] = sg[e][2] = sg[e][3] = (T)0;
+    for (int k = 0; k < pix; ++k) {
+      const int64_t i = ((int64_t)blockIdx.x * pix + k) * blockDim.x + threadIdx.x;
+      const bool live = i < d.plane;
+      const int64_t ii = live ? i : d.plane - 1;
+      const int m = (int)ii % d.nx, n = (int)ii / d.nx;
+      cplx<T> s0[kMaxElem + 1], s1[kMaxElem + 1], s2[kMaxElem + 1];
+      const cplx<T>* src = in + (int64_t)b * d.comps_in * d.plane;
+      s0[0] = src[ii];
+      s1[0] = d.comps_in >= 2 ? src[d.plane + ii] : mk((T)0, (T)0);
+      s2[0] = d.comps_in == 3 ? src[2 * d.plane + ii] : mk((T)0, (T)0);
 #pragma unroll
       for (int e = 0; e < kMaxElem; ++e) {
         if (e >= E.n) break;
-        if (G.gphx[e]) ((T*)G.gphx[e])[(int64_t)b * E.phstride[e] + i] = gphx_acc[e];
-        if (G.gphy[e]) ((T*)G.gphy[e])[(int64_t)b * E.phstride[e] + i] = gphy_acc[e];
-        gphx_acc[e] = gphy_acc[e] = (T)0;
+        s0[e + 1] = s0[e];
+        s1[e + 1] = s1[e];
+        s2[e + 1] = s2[e];
+        elem_fwd<T>(E, d, lens, nlens, e, b, ii, m, n, s0[e + 1], s1[e + 1], s2[e + 1], jt);
+      }
+      const cplx<T>* gsrc = gout + (int64_t)b * d.comps_out * d.plane;
+      cplx<T> g0 = gsrc[ii];
+      cplx<T> g1 = d.comps_out >= 2 ? gsrc[d.plane + ii] : mk((T)0, (T)0);
+      cplx<T> g2 = d.comps_out == 3 ? gsrc[2 * d.plane + ii] : mk((T)0, (T)0);
+      const T wlive = live ? (T)1 : (T)0;  // dead lanes add nothing to the scalar gradients
+#pragma unroll
+      for (int e = kMaxElem - 1; e >= 0; --e) {
+        if (e >= E.n) continue;
+        const cplx<T> u0 = s0[e], u1 = s1[e], o0 = s0[e + 1], o1 = s1[e + 1], o2 = s2[e + 1];
+        switch (E.kind[e]) {
+          case XL_SLM: {
+            gphx_acc[e] += cmulc(g0, o0).y + cmulc(g1, o1).y + cmulc(g2, o2).y;
+            T s, c;
+            xsincos(phase_at<T>(E.phx[e], E.phstride[e], b, ii), &s, &c);
+            g0 = cmul(g0, mk(c, -s));
+            g1 = cmul(g1, mk(c, -s));
+            g2 = cmul(g2, mk(c, -s));
+            break;
+          }
+          case XL_SSLM: {
+            gphx_acc[e] += cmulc(g0, o0).y;
+            gphy_acc[e] += cmulc(g1, o1).y;
+            T s, c;
+            xsincos(phase_at<T>(E.phx[e], E.phstride[e], b, ii), &s, &c);
+            g0 = cmul(g0, mk(c, -s));
+            xsincos(phase_at<T>(E.phy[e], E.phstride[e], b, ii), &s, &c);
+            g1 = cmul(g1, mk(c, -s));
+            break;
+          }
+          case XL_LENS: {
+            const T xm = (T)d.x0 + (T)m * (T)d.dx, yn = (T)d.y0 + (T)n * (T)d.dy;
+            const T coef = jt.lens_c[e] * (xm * xm + yn * yn);  // d out / d f = i coef out
+            sg[e][0] += wlive * (cdot_re(g0, mk(-o0.y * coef, o0.x * coef)) +
+                                 cdot_re(g1, mk(-o1.y * coef, o1.x * coef)) +
+                                 cdot_re(g2, mk(-o2.y * coef, o2.x * coef)));
+            cplx<T> L = lens_factor<T>(lens, E.lens_slot[e], d.params_dev ? b : 0, nlens, d, m, n);
+            g0 = cmulc(g0, L);
+            g1 = cmulc(g1, L);
+            g2 = cmulc(g2, L);
+            break;
+          }
+          case XL_POLARIZER: {
+            sg[e][1] += wlive * jre(jt.dA[e], g0, g1, u0, u1);
+            japply_h(jt.J[e], g0, g1);
+            break;
+          }
+          case XL_WAVEPLATE: {
+            sg[e][2] += wlive * jre(jt.dA[e], g0, g1, u0, u1);
+            sg[e][3] += wlive * jre(jt.dB[e], g0, g1, u0, u1);
+            japply_h(jt.J[e], g0, g1);
+            break;
+          }
+          case XL_TO_VECTOR:
+            g1 = mk((T)0, (T)0);
+            break;
+        }
+      }
+      if (live && gin) {
+        cplx<T>* dst = gin + (int64_t)b * d.comps_in * d.plane;
+        dst[i] = g0;
+        if (d.comps_in >= 2) dst[d.plane + i] = g1;
+        if (d.comps_in == 3) dst[2 * d.plane + i] = g2;
+      }
+      if (!G.accumulate_shared) {
+#pragma unroll
+        for (int e = 0; e < kMaxElem; ++e) {
+          if (e >= E.n) break;
+          if (live && G.gphx[e]) ((T*)G.gphx[e])[(int64_t)b * E.phstride[e] + i] = gphx_acc[e];
+          if (live && G.gphy[e]) ((T*)G.gphy[e])[(int64_t)b * E.phstride[e] + i] = gphy_acc[e];
+          gphx_acc[e] = gphy_acc[e] = (T)0;
+        }
       }
     }
     if (G.partial) {
-      // block reduction of every scalar gradient of this batch element, fixed order
+      // block reduction of the scalar gradients this batch element has, fixed order; the rows
+      // of parameters an element does not have get zero
       for (int e = 0; e < E.n; ++e)
         for (int j = 0; j < 4; ++j) {
-          double v = live ? sg[e][j] : 0.0;
+          double* dst = &G.partial[(((int64_t)b * E.n + e) * 4 + j) * gridDim.x + blockIdx.x];
+          if (!has_scalar(E.kind[e], j)) {  // uniform over the block
+            if (threadIdx.x == 0) *dst = 0.0;
+            continue;
+          }
+          double v = (double)sg[e][j];
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
           __syncthreads();
@@ -353,17 +392,21 @@ __global__ void __launch_bounds__(256) k_elem_bwd(const cplx<T>* __restrict__ go
           if (threadIdx.x == 0) {
             double s = 0;
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-            G.partial[(((int64_t)b * E.n + e) * 4 + j) * gridDim.x + blockIdx.x] = s;
+            *dst = s;
           }
         }
     }
+    __syncthreads();  // every thread is done with this element's Jones matrices
   }
-  if (G.accumulate_shared && live) {
+  if (G.accumulate_shared) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < d.plane) {
 #pragma unroll
-    for (int e = 0; e < kMaxElem; ++e) {
-      if (e >= E.n) break;
-      if (G.gphx[e]) ((T*)G.gphx[e])[i] = gphx_acc[e];
-      if (G.gphy[e]) ((T*)G.gphy[e])[i] = gphy_acc[e];
+      for (int e = 0; e < kMaxElem; ++e) {
+        if (e >= E.n) break;
+        if (G.gphx[e]) ((T*)G.gphx[e])[i] = gphx_acc[e];
+        if (G.gphy[e]) ((T*)G.gphy[e])[i] = gphy_acc[e];
+      }
     }
   }
 }
@@ -494,7 +537,8 @@ xl_status run_bwd(const void* gout, const void* in, void* gin, int32_t batch, co
   if (any_shared && any_batched && batch > 1)
     return fail(XL_ERR_UNSUPPORTED, "elements backward: mixing shared and per-batch masks");
   G.accumulate_shared = any_shared && batch > 1;
-  const int nblk = (int)((d.plane + 255) / 256);
+  const int pix = G.accumulate_shared ? 1 : kPixBwd;
+  const int nblk = (int)((d.plane + 256 * pix - 1) / (256 * pix));
   const int lb = d.params_dev ? batch : 1;
   const size_t cs = sizeof(cplx<T>);
   auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
@@ -509,7 +553,7 @@ xl_status run_bwd(const void* gout, const void* in, void* gin, int32_t batch, co
   {
     LaunchScope ls("elements_bwd", s);
     k_elem_bwd<T><<<grid, 256, 0, s>>>((const cplx<T>*)gout, (const cplx<T>*)in, (cplx<T>*)gin, E, d,
-                                       (const cplx<T>*)lens, nlens, G, batch);
+                                       (const cplx<T>*)lens, nlens, G, batch, pix);
     XL_CUDA_TRY(cudaGetLastError());
   }
   if (gparams && E.n > 0) {

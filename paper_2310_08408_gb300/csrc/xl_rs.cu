@@ -61,28 +61,32 @@ GenArgs gen_args(const xl_grid* g, double wavelength, const Spectra& sp) {
   a.scale = 1.0 / (4.0 * (double)g->nx * (double)g->ny);
   for (int i = 0; i < NKIND; ++i) a.slot[i] = sp.slot[i];
   a.dz_rest = 0;
+  a.s_elem = a.h_elem = 0;
   return a;
 }
 
 template <typename T>
-xl_status generate(void* S, void* Hq, const GenArgs& a, cudaStream_t s) {
-  return rs_generate<T>(S, Hq, a, s);
+xl_status generate(void* S, void* Hq, const GenArgs& a, int nb, cudaStream_t s) {
+  return rs_generate<T>(S, Hq, a, nb, s);
 }
 
-// Spectra for one distance: cached (host z) or generated into `dev_hq` (device z).
+// Spectra for one distance: cached (host z), or generated into `dev_hq` (device z) for the nb
+// consecutive distances z[0..nb-1], element e's spectra at e * count * (nx+1)(ny+1).
 xl_status get_spectra(const xl_grid* g, double wavelength, const Spectra& sp, int32_t dtype,
                       const double* z, int32_t flags, void* dev_s, void* dev_hq, cudaStream_t s,
-                      const void** out) {
+                      const void** out, int nb = 1) {
   GenArgs a = gen_args(g, wavelength, sp);
   a.dz_rest = (flags & XL_PHASE_INVARIANT) ? 1 : 0;
   const size_t cs = dtype_csize(dtype);
   const size_t hq_bytes = (size_t)sp.count * a.hq_kind * cs;
-  auto run = [&](void* S, void* Hq) -> xl_status {
-    return dtype == XL_C128 ? generate<double>(S, Hq, a, s) : generate<float>(S, Hq, a, s);
+  auto run = [&](void* S, void* Hq, int n) -> xl_status {
+    return dtype == XL_C128 ? generate<double>(S, Hq, a, n, s) : generate<float>(S, Hq, a, n, s);
   };
   if (flags & XL_Z_DEVICE) {
     a.zdev = z;
-    XL_TRY(run(dev_s, dev_hq));
+    a.s_elem = (int64_t)sp.count * a.s_plane;
+    a.h_elem = (int64_t)sp.count * a.hq_kind;
+    XL_TRY(run(dev_s, dev_hq, nb));
     *out = dev_hq;
     return XL_OK;
   }
@@ -101,7 +105,7 @@ xl_status get_spectra(const xl_grid* g, double wavelength, const Spectra& sp, in
   XL_TRY(cached_table(key, hq_bytes, s, [&](void* Hq) -> xl_status {
     void* S = nullptr;
     XL_TRY(workspace(s, (size_t)sp.count * a.s_plane * cs, &S, 1));
-    return run(S, Hq);
+    return run(S, Hq, 1);
   }, &p));
   *out = p;
   return XL_OK;
@@ -189,20 +193,23 @@ xl_status run_op(Op op, const void* in, const void* u_in, void* out, double* g_z
   const int p2blocks = rs_pass2_blocks<T>(nx, ny);
   const bool zdev = (flags & XL_Z_DEVICE) != 0;
   const int cUw = save_in ? 0 : cU;  // U planes computed into the workspace
-  const int64_t elem_ws = (int64_t)(cT + cUw) * t_plane * cs;
-  const int chunk_max = zdev ? 1 : chunk_size(elem_ws, batch);
-  // pass-2 group: up to kP2Run elements whose spectra together stay within half of the table
-  // cache, so that fetching one never evicts another of the same launch
   const size_t hq_bytes1 = (size_t)sp.count * (nx + 1) * (ny + 1) * cs;
-  const int group_max = zdev ? 1
+  const size_t s_bytes1 = (size_t)sp.count * (nx + 1) * ny * cs;
+  // device distances: every element of a chunk gets its spectra generated into the workspace
+  const int64_t elem_ws = (int64_t)(cT + cUw) * t_plane * cs + (zdev ? (int64_t)(s_bytes1 + hq_bytes1) : 0);
+  const int chunk_max = zdev ? std::min(chunk_size(elem_ws, batch), kP2Run) : chunk_size(elem_ws, batch);
+  // pass-2 group: up to kP2Run elements whose spectra together stay within half of the table
+  // cache, so that fetching one never evicts another of the same launch (device distances: the
+  // chunk, whose spectra live in the workspace)
+  const int group_max = zdev ? chunk_max
                              : (int)std::max<int64_t>(1, std::min<int64_t>(kP2Run,
                                    (int64_t)(table_cache_cap() / 2 / hq_bytes1)));
   // workspace: T (chunk * cT planes) | U (chunk * cU planes) | dz partials | [S | Hq] (device z)
   const size_t t_bytes = (size_t)chunk_max * cT * t_plane * cs;
   const size_t u_bytes = (size_t)chunk_max * cUw * t_plane * cs;
   const size_t dz_bytes = want_dz ? (size_t)chunk_max * p2blocks * sizeof(double) : 0;
-  const size_t s_bytes = zdev ? (size_t)sp.count * (nx + 1) * ny * cs : 0;
-  const size_t hq_bytes = zdev ? (size_t)sp.count * (nx + 1) * (ny + 1) * cs : 0;
+  const size_t s_bytes = zdev ? (size_t)chunk_max * s_bytes1 : 0;
+  const size_t hq_bytes = zdev ? (size_t)chunk_max * hq_bytes1 : 0;
   auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
   void* ws = nullptr;
   XL_TRY(workspace(s, al(t_bytes) + al(u_bytes) + al(dz_bytes) + al(s_bytes) + al(hq_bytes), &ws));
@@ -226,18 +233,23 @@ xl_status run_op(Op op, const void* in, const void* u_in, void* out, double* g_z
     if (want_dz && !save_in)
       XL_TRY(rs_pass1<T>(usrc + (size_t)b0 * cU * plane * cs, Ub, nx, ny, cU, cU, nc * cU, s));
     // pass 2 over groups of up to kP2Run elements, each element with the spectra of its own
-    // distance (one group per element with device distances)
+    // distance (device distances: the whole chunk, its spectra generated by one launch pair)
     for (int32_t r0 = b0; r0 < b0 + nc;) {
       const int nb = (int)std::min<int64_t>(group_max, b0 + nc - r0);
       const int64_t e0 = r0 - b0;  // first element of the group within the chunk
       P2Args a = p2_args(g, sp, cT, cU);
       const void* Hq0 = nullptr;
       const void* Hq = nullptr;
-      for (int e = 0; e < nb; ++e) {
-        if (e == 0 || z[r0 + e] != z[r0 + e - 1])
-          XL_TRY(get_spectra(g, wavelength, sp, dtype, z + r0 + e, flags, dev_s, dev_hq, s, &Hq));
-        if (e == 0) Hq0 = Hq;
-        a.hshift[e] = (const cplx<T>*)Hq - (const cplx<T>*)Hq0;
+      if (zdev) {  // one generation for the group, element e's spectra at e * count * quadrant
+        XL_TRY(get_spectra(g, wavelength, sp, dtype, z + r0, flags, dev_s, dev_hq, s, &Hq0, nb));
+        for (int e = 0; e < nb; ++e) a.hshift[e] = (int64_t)e * sp.count * (nx + 1) * (ny + 1);
+      } else {
+        for (int e = 0; e < nb; ++e) {
+          if (e == 0 || z[r0 + e] != z[r0 + e - 1])
+            XL_TRY(get_spectra(g, wavelength, sp, dtype, z + r0 + e, flags, dev_s, dev_hq, s, &Hq));
+          if (e == 0) Hq0 = Hq;
+          a.hshift[e] = (const cplx<T>*)Hq - (const cplx<T>*)Hq0;
+        }
       }
       a.per_elem = nb > 1 ? 1 : 0;
       if (save_out) {  // pass 2 also stores the column spectra of the inputs

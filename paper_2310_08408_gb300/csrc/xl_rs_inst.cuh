@@ -97,10 +97,10 @@ xl_status pass2_L(int mode, void* Tb, const void* Ub, const void* Hq, double* dz
 }
 
 template <typename T, int LX, int LY>
-xl_status gen_LL(void* S, void* Hq, const GenArgs& g, cudaStream_t s) {
+xl_status gen_LL(void* S, void* Hq, const GenArgs& g, int nb, cudaStream_t s) {
   constexpr int RA = rows_transp<LX, sizeof(cplx<T>)>();
   constexpr int RB = rows_cols<LY>();
-  const size_t sa = (size_t)RA * tpitch(LX, sizeof(cplx<T>), RA) * sizeof(cplx<T>);
+  const size_t sa = (size_t)RA * (tpitch(LX, sizeof(cplx<T>), RA) + LX / 2) * sizeof(cplx<T>);
   const size_t sb = (size_t)RB * srow(LY) * sizeof(cplx<T>);
   const void *twx, *twy;
   XL_TRY(twiddles(LX, sizeof(T) == 8 ? XL_C128 : XL_C64, &twx));
@@ -109,28 +109,28 @@ xl_status gen_LL(void* S, void* Hq, const GenArgs& g, cudaStream_t s) {
   XL_TRY(smem_attr((const void*)k_gen_pass_b<T, LY>, sb));
   {
   LaunchScope ls("rs_gen_a<" + std::to_string(LX) + ">", s);
-  k_gen_pass_a<T, LX><<<(g.ny + RA - 1) / RA, RA * (LX / 16), sa, s>>>((cplx<T>*)S, g,
-                                                                      (const cplx<T>*)twx);
+  k_gen_pass_a<T, LX><<<dim3((g.ny + RA - 1) / RA, nb), RA * (LX / 16), sa, s>>>(
+      (cplx<T>*)S, g, (const cplx<T>*)twx);
   }
   XL_CUDA_TRY(cudaGetLastError());
   LaunchScope lsb("rs_gen_b<" + std::to_string(LY) + ">", s);
-  k_gen_pass_b<T, LY><<<(g.nx + 1 + RB - 1) / RB, RB * (LY / 16), sb, s>>>(
+  k_gen_pass_b<T, LY><<<dim3((g.nx + 1 + RB - 1) / RB, nb), RB * (LY / 16), sb, s>>>(
       (const cplx<T>*)S, (cplx<T>*)Hq, g, (const cplx<T>*)twy);
   XL_CUDA_TRY(cudaGetLastError());
   return XL_OK;
 }
 
 template <typename T, int LX>
-xl_status gen_L(void* S, void* Hq, const GenArgs& g, cudaStream_t s) {
+xl_status gen_L(void* S, void* Hq, const GenArgs& g, int nb, cudaStream_t s) {
   switch (2 * g.ny) {
-    case 64: return gen_LL<T, LX, 64>(S, Hq, g, s);
-    case 128: return gen_LL<T, LX, 128>(S, Hq, g, s);
-    case 256: return gen_LL<T, LX, 256>(S, Hq, g, s);
-    case 512: return gen_LL<T, LX, 512>(S, Hq, g, s);
-    case 1024: return gen_LL<T, LX, 1024>(S, Hq, g, s);
-    case 2048: return gen_LL<T, LX, 2048>(S, Hq, g, s);
-    case 4096: return gen_LL<T, LX, 4096>(S, Hq, g, s);
-    case 8192: return gen_LL<T, LX, 8192>(S, Hq, g, s);
+    case 64: return gen_LL<T, LX, 64>(S, Hq, g, nb, s);
+    case 128: return gen_LL<T, LX, 128>(S, Hq, g, nb, s);
+    case 256: return gen_LL<T, LX, 256>(S, Hq, g, nb, s);
+    case 512: return gen_LL<T, LX, 512>(S, Hq, g, nb, s);
+    case 1024: return gen_LL<T, LX, 1024>(S, Hq, g, nb, s);
+    case 2048: return gen_LL<T, LX, 2048>(S, Hq, g, nb, s);
+    case 4096: return gen_LL<T, LX, 4096>(S, Hq, g, nb, s);
+    case 8192: return gen_LL<T, LX, 8192>(S, Hq, g, nb, s);
   }
   return fail(XL_ERR_UNSUPPORTED, "rs_generate: unsupported ny");
 }
@@ -184,8 +184,8 @@ int rs_pass2_blocks<XL_REAL>(int nx, int ny) {
 }
 
 template <>
-xl_status rs_generate<XL_REAL>(void* S, void* Hq, const GenArgs& g, cudaStream_t s) {
-#define CG(L) gen_L<XL_REAL, L>(S, Hq, g, s)
+xl_status rs_generate<XL_REAL>(void* S, void* Hq, const GenArgs& g, int nb, cudaStream_t s) {
+#define CG(L) gen_L<XL_REAL, L>(S, Hq, g, nb, s)
   XL_SWITCH_L(2 * g.nx, CG)
 #undef CG
   return fail(XL_ERR_UNSUPPORTED, "rs_generate: unsupported nx");

@@ -571,6 +571,8 @@ struct GenArgs {
   double scale;           // 1 / (LX LY)
   int slot[NKIND];        // kind -> slot of the S / Hq buffers (-1: not produced)
   int dz_rest;            // distance-derivative kinds carry dh/dz - i k h (phase-invariant losses)
+  int64_t s_elem, h_elem; // device distances: element blockIdx.y reads zdev[blockIdx.y] and
+                          // writes its S and Hq at these element strides
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -647,9 +649,10 @@ template <> struct RsPhase<float> {
   }
 };
 template <> struct RsPhase<double> {
-  double kz_red;
+  double kz_red, z;
   __device__ RsPhase(const GenArgs& g, double zz) {
     kz_red = g.k * zz - kTwoPi * rint(g.k * zz / kTwoPi);
+    z = zz;
   }
 };
 
@@ -685,47 +688,56 @@ __device__ __forceinline__ cplx<T> rs_kinds(int kind, cplx<T> e, T r, T X, T Y, 
   return cscale(dmh, kind == KDHX ? -X / z : -Y / z);
 }
 
-// Kernel sample of spectrum `kind` at pixel offset (a, b). Single precision: r and the phase
-// k (r - z) = k rho^2 / (r + z) in double-float (exact a^2, b^2 times dx^2, dy^2), reduced
-// modulo 2 pi before adding k z mod 2 pi and one sincosf. Double precision: the same formula in
-// double.
-template <typename T>
-__device__ __forceinline__ cplx<T> rs_sample(int kind, int a, int b, const GenArgs& g, double z,
-                                             const RsPhase<T>& P);
-
-template <>
-__device__ __forceinline__ cplx<float> rs_sample<float>(int kind, int a, int b, const GenArgs& g,
-                                                        double z, const RsPhase<float>& P) {
+// The parts of a kernel sample at pixel offset (a, b) that every kind shares: the unit phasor
+// exp(i k r) and r; rs_kinds then forms any kind from them. Single precision: r and the phase
+// k (r - z) = k rho^2 / (r + z) in double-float (exact a^2, b^2 times dx^2, dy^2), reduced modulo
+// 2 pi before adding k z mod 2 pi and one sincosf (the costly part). Double precision: the same
+// formula in double.
+__device__ __forceinline__ void rs_phasor(int a, int b, const GenArgs& g, double, const RsPhase<float>& P,
+                                          float2* e, float* r) {
   const float A = (float)(a * a), B = (float)(b * b);  // exact (|a|, |b| < 4096)
   const df rho2 = df_add(df_mul_f(P.dx2, A), df_mul_f(P.dy2, B));
-  const df r = df_sqrt(df_add(rho2, P.z2));
-  const df ph = df_div(df_mul(P.k, rho2), df_add(r, P.z));
+  const df rr = df_sqrt(df_add(rho2, P.z2));
+  const df ph = df_div(df_mul(P.k, rho2), df_add(rr, P.z));
   const float n = rintf(ph.hi * 0.15915494309189535f);
   const df red = df_add(ph, df_neg(df_mul_f(P.twopi, n)));
   float sn, cs;
   sincosf(red.hi + red.lo + P.kz_red, &sn, &cs);
-  const float X = (float)a * P.dxf, Y = (float)b * P.dyf;
-  return rs_kinds<float>(kind, make_float2(cs, sn), r.hi, X, Y, P.zf, P.kf, P.c0, g.dz_rest != 0);
+  *e = make_float2(cs, sn);
+  *r = rr.hi;
 }
-
-template <>
-__device__ __forceinline__ cplx<double> rs_sample<double>(int kind, int a, int b, const GenArgs& g,
-                                                          double z, const RsPhase<double>& P) {
+__device__ __forceinline__ void rs_phasor(int a, int b, const GenArgs& g, double z, const RsPhase<double>& P,
+                                          double2* e, double* r) {
   const double X = a * g.dx, Y = b * g.dy;
   const double rho2 = X * X + Y * Y;
-  const double r = sqrt(rho2 + z * z);
-  double ph = g.k * rho2 / (r + z);
+  *r = sqrt(rho2 + z * z);
+  double ph = g.k * rho2 / (*r + z);
   ph -= kTwoPi * rint(ph * (1.0 / kTwoPi));
   double sn, cs;
   sincos(ph + P.kz_red, &sn, &cs);
-  return rs_kinds<double>(kind, make_double2(cs, sn), r, X, Y, z, g.k, g.dx * g.dy / kTwoPi,
-                          g.dz_rest != 0);
+  *e = make_double2(cs, sn);
+}
+// Kind `kind` at offset (a, b) from its phasor e; r from the offsets (plain precision is enough:
+// r only scales amplitudes).
+__device__ __forceinline__ float2 rs_from_phasor(int kind, float2 e, int a, int b, const GenArgs& g,
+                                                 const RsPhase<float>& P, float r) {
+  const float X = (float)a * P.dxf, Y = (float)b * P.dyf;
+  if (r < 0.f) r = sqrtf(fmaf(X, X, fmaf(Y, Y, P.zf * P.zf)));
+  return rs_kinds<float>(kind, e, r, X, Y, P.zf, P.kf, P.c0, g.dz_rest != 0);
+}
+__device__ __forceinline__ double2 rs_from_phasor(int kind, double2 e, int a, int b, const GenArgs& g,
+                                                  const RsPhase<double>& P, double r) {
+  const double X = a * g.dx, Y = b * g.dy;
+  const double z = P.z;
+  if (r < 0.0) r = sqrt(X * X + Y * Y + z * z);
+  return rs_kinds<double>(kind, e, r, X, Y, z, g.k, g.dx * g.dy / kTwoPi, g.dz_rest != 0);
 }
 
-
 // Generator pass A: for each b in [0, ny) and each kind, FFT along a of the kernel row placed
-// mod LX; keep kx in [0, nx]; store transposed S[kind][kx][b].
-template <typename T, int LX>
+// mod LX; keep kx in [0, nx]; store transposed S[kind][kx][b]. CACHE: the phasors of the row are
+// evaluated once per |a| < nx into shared memory after the transform rows, and every kind starts
+// from them (the phase is the costly part of a sample).
+template <typename T, int LX, bool CACHE = true>
 __global__ void __launch_bounds__(rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16),
                                   min_blocks_rows<rows_transp<LX, sizeof(cplx<T>)>() * (LX / 16), sizeof(cplx<T>)>())
 k_gen_pass_a(cplx<T>* __restrict__ S, GenArgs g, const cplx<T>* __restrict__ tw) {
@@ -739,9 +751,23 @@ k_gen_pass_a(cplx<T>* __restrict__ S, GenArgs g, const cplx<T>* __restrict__ tw)
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
   const int b0 = blockIdx.x * ROWS;
   const int b = b0 + team;
-  const double z = g.zdev ? *g.zdev : g.zval;
+  const double z = g.zdev ? g.zdev[blockIdx.y] : g.zval;
+  S += (int64_t)blockIdx.y * g.s_elem;
   const RsPhase<T> ph(g, z);
   C* row = sm + team * P;
+  C* phc = sm + ROWS * P + team * (LX / 2);  // phasors of |a| < nx (CACHE)
+  if constexpr (CACHE) {
+    // the row's phasors, once per |a| (the kernel is even in a): thread t takes a = t + q TT
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+      const int a = t + q * TT;
+      C e;
+      T r;
+      rs_phasor(a, b < g.ny ? b : 0, g, z, ph, &e, &r);
+      phc[a] = e;
+    }
+    team_sync<LX>();
+  }
   for (int kind = 0; kind < NKIND; ++kind) {
     if (!(g.kinds & (1u << kind))) continue;  // uniform over the block
     C v[16];
@@ -749,7 +775,16 @@ k_gen_pass_a(cplx<T>* __restrict__ S, GenArgs g, const cplx<T>* __restrict__ tw)
     for (int q = 0; q < 16; ++q) {
       const int i = t + q * TT;
       const int a = i < g.nx ? i : i - LX;
-      v[q] = (i == g.nx || b >= g.ny) ? mk((T)0, (T)0) : rs_sample<T>(kind, a, b, g, z, ph);
+      if (i == g.nx || b >= g.ny) {
+        v[q] = mk((T)0, (T)0);
+      } else if constexpr (CACHE) {
+        v[q] = rs_from_phasor(kind, phc[a >= 0 ? a : -a], a, b, g, ph, (T)-1);
+      } else {
+        C e;
+        T r;
+        rs_phasor(a, b, g, z, ph, &e, &r);
+        v[q] = rs_from_phasor(kind, e, a, b, g, ph, r);
+      }
     }
     team_fft<LX, -1>(v, row, t, tw);
     __syncthreads();
@@ -778,6 +813,8 @@ k_gen_pass_b(const cplx<T>* __restrict__ S, cplx<T>* __restrict__ Hq, GenArgs g,
   const int kx_raw = blockIdx.x * ROWS + team;
   const bool live = kx_raw <= g.nx;
   const int kx = live ? kx_raw : g.nx;
+  S += (int64_t)blockIdx.y * g.s_elem;
+  Hq += (int64_t)blockIdx.y * g.h_elem;
   C* row = sm + team * SR;
   for (int kind = 0; kind < NKIND; ++kind) {
     if (!(g.kinds & (1u << kind))) continue;

@@ -23,6 +23,6 @@ xl_status rs_pass2(int mode, void* Tb, const void* Ub, const void* Hq, double* d
 template <typename T> int rs_pass2_blocks(int nx, int ny);
 // spectrum generation: S scratch ((nx+1) * ny per produced kind), Hq output
 template <typename T>
-xl_status rs_generate(void* S, void* Hq, const GenArgs& g, cudaStream_t s);
+xl_status rs_generate(void* S, void* Hq, const GenArgs& g, int nb, cudaStream_t s);
 
 }  // namespace xl

@@ -105,6 +105,7 @@ xl_status run_static(const float2* in, float2* out, int32_t batch, const xl_grid
   ga.zdev = nullptr;
   ga.kinds = 1u << KH;
   ga.s_plane = (int64_t)(nx + 1) * ny;
+  ga.s_elem = ga.h_elem = 0;
   ga.hq_kind = (int64_t)(nx + 1) * (ny + 1);
   ga.scale = 1.0 / (4.0 * (double)nx * (double)ny);
   for (int i = 0; i < NKIND; ++i) ga.slot[i] = -1;
@@ -142,7 +143,7 @@ xl_status run_static(const float2* in, float2* out, int32_t batch, const xl_grid
   for (int32_t b = 0; b < batch; ++b) {
     if (b == 0 || z[b] != z[b - 1]) {
       ga.zval = z[b];
-      k_gen_pass_a<float, LX><<<(ny + RA - 1) / RA, RA * (LX / 16), smA, s>>>(S, ga, twx);
+      k_gen_pass_a<float, LX, false><<<(ny + RA - 1) / RA, RA * (LX / 16), smA, s>>>(S, ga, twx);
       XL_CUDA_TRY(cudaGetLastError());
       k_gen_pass_b<float, LY><<<(nx + 1 + RB - 1) / RB, RB * (LY / 16), smB, s>>>(S, Hq, ga, twy);
       XL_CUDA_TRY(cudaGetLastError());
