@@ -262,7 +262,9 @@ constexpr int kPixBwd = 8;
 // Backward. grid: (ceil(plane / (256 pix)), batch), or (ceil(plane / 256), 1) with pix = 1 when
 // masks are shared (stride 0): the batch loop then runs inside the thread so that dL/dphi sums
 // over the batch without atomics.
-template <typename T>
+// NE: the number of elements (E.n), a compile-time bound so that the per-pixel states take
+// registers for NE elements only.
+template <typename T, int NE>
 __global__ void __launch_bounds__(256) k_elem_bwd(const cplx<T>* __restrict__ gout, const cplx<T>* __restrict__ in,
                                                   cplx<T>* __restrict__ gin, ElemSet E, ElemDims d,
                                                   const cplx<T>* __restrict__ lens, int nlens,
@@ -270,31 +272,30 @@ __global__ void __launch_bounds__(256) k_elem_bwd(const cplx<T>* __restrict__ go
   __shared__ double red[32];
   const int b_lo = G.accumulate_shared ? 0 : blockIdx.y;
   const int b_hi = G.accumulate_shared ? batch : blockIdx.y + 1;
-  T gphx_acc[kMaxElem], gphy_acc[kMaxElem];
+  T gphx_acc[NE > 0 ? NE : 1], gphy_acc[NE > 0 ? NE : 1];
 #pragma unroll
-  for (int e = 0; e < kMaxElem; ++e) gphx_acc[e] = gphy_acc[e] = (T)0;
+  for (int e = 0; e < NE; ++e) gphx_acc[e] = gphy_acc[e] = (T)0;
   __shared__ JonesTab<T> jt;
   for (int b = b_lo; b < b_hi; ++b) {
     jones_fill<T>(jt, E, d, b, true);
     __syncthreads();
     // this thread's sums of the scalar gradients over its pixels (in T: FP64 runs at a small
     // fraction of the FP32 rate; the block sums below are in double)
-    T sg[kMaxElem][4];
+    T sg[NE > 0 ? NE : 1][4];
 #pragma unroll
-    for (int e = 0; e < kMaxElem; ++e) sg[e][0] = sg[e][1] = sg[e][2] = sg[e][3] = (T)0;
+    for (int e = 0; e < NE; ++e) sg[e][0] = sg[e][1] = sg[e][2] = sg[e][3] = (T)0;
     for (int k = 0; k < pix; ++k) {
       const int64_t i = ((int64_t)blockIdx.x * pix + k) * blockDim.x + threadIdx.x;
       const bool live = i < d.plane;
       const int64_t ii = live ? i : d.plane - 1;
       const int m = (int)ii % d.nx, n = (int)ii / d.nx;
-      cplx<T> s0[kMaxElem + 1], s1[kMaxElem + 1], s2[kMaxElem + 1];
+      cplx<T> s0[NE + 1], s1[NE + 1], s2[NE + 1];
       const cplx<T>* src = in + (int64_t)b * d.comps_in * d.plane;
       s0[0] = src[ii];
       s1[0] = d.comps_in >= 2 ? src[d.plane + ii] : mk((T)0, (T)0);
       s2[0] = d.comps_in == 3 ? src[2 * d.plane + ii] : mk((T)0, (T)0);
 #pragma unroll
-      for (int e = 0; e < kMaxElem; ++e) {
-        if (e >= E.n) break;
+      for (int e = 0; e < NE; ++e) {
         s0[e + 1] = s0[e];
         s1[e + 1] = s1[e];
         s2[e + 1] = s2[e];
@@ -306,8 +307,7 @@ __global__ void __launch_bounds__(256) k_elem_bwd(const cplx<T>* __restrict__ go
       cplx<T> g2 = d.comps_out == 3 ? gsrc[2 * d.plane + ii] : mk((T)0, (T)0);
       const T wlive = live ? (T)1 : (T)0;  // dead lanes add nothing to the scalar gradients
 #pragma unroll
-      for (int e = kMaxElem - 1; e >= 0; --e) {
-        if (e >= E.n) continue;
+      for (int e = NE - 1; e >= 0; --e) {
         const cplx<T> u0 = s0[e], u1 = s1[e], o0 = s0[e + 1], o1 = s1[e + 1], o2 = s2[e + 1];
         switch (E.kind[e]) {
           case XL_SLM: {
@@ -365,8 +365,7 @@ __global__ void __launch_bounds__(256) k_elem_bwd(const cplx<T>* __restrict__ go
       }
       if (!G.accumulate_shared) {
 #pragma unroll
-        for (int e = 0; e < kMaxElem; ++e) {
-          if (e >= E.n) break;
+        for (int e = 0; e < NE; ++e) {
           if (live && G.gphx[e]) ((T*)G.gphx[e])[(int64_t)b * E.phstride[e] + i] = gphx_acc[e];
           if (live && G.gphy[e]) ((T*)G.gphy[e])[(int64_t)b * E.phstride[e] + i] = gphy_acc[e];
           gphx_acc[e] = gphy_acc[e] = (T)0;
@@ -376,7 +375,7 @@ __global__ void __launch_bounds__(256) k_elem_bwd(const cplx<T>* __restrict__ go
     if (G.partial) {
       // block reduction of the scalar gradients this batch element has, fixed order; the rows
       // of parameters an element does not have get zero
-      for (int e = 0; e < E.n; ++e)
+      for (int e = 0; e < NE; ++e)
         for (int j = 0; j < 4; ++j) {
           double* dst = &G.partial[(((int64_t)b * E.n + e) * 4 + j) * gridDim.x + blockIdx.x];
           if (!has_scalar(E.kind[e], j)) {  // uniform over the block
@@ -402,8 +401,7 @@ __global__ void __launch_bounds__(256) k_elem_bwd(const cplx<T>* __restrict__ go
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < d.plane) {
 #pragma unroll
-      for (int e = 0; e < kMaxElem; ++e) {
-        if (e >= E.n) break;
+      for (int e = 0; e < NE; ++e) {
         if (G.gphx[e]) ((T*)G.gphx[e])[i] = gphx_acc[e];
         if (G.gphy[e]) ((T*)G.gphy[e])[i] = gphy_acc[e];
       }
@@ -552,8 +550,16 @@ xl_status run_bwd(const void* gout, const void* in, void* gin, int32_t batch, co
   dim3 grid(nblk, G.accumulate_shared ? 1 : batch);
   {
     LaunchScope ls("elements_bwd", s);
-    k_elem_bwd<T><<<grid, 256, 0, s>>>((const cplx<T>*)gout, (const cplx<T>*)in, (cplx<T>*)gin, E, d,
-                                       (const cplx<T>*)lens, nlens, G, batch, pix);
+#define XL_EBWD(NE)                                                                                 \
+  case NE:                                                                                          \
+    k_elem_bwd<T, NE><<<grid, 256, 0, s>>>((const cplx<T>*)gout, (const cplx<T>*)in, (cplx<T>*)gin, \
+                                           E, d, (const cplx<T>*)lens, nlens, G, batch, pix);     \
+    break;
+    switch (E.n) {
+      XL_EBWD(0) XL_EBWD(1) XL_EBWD(2) XL_EBWD(3) XL_EBWD(4) XL_EBWD(5) XL_EBWD(6) XL_EBWD(7) XL_EBWD(8)
+      default: return fail(XL_ERR_ARG, "elements backward: element count");
+    }
+#undef XL_EBWD
     XL_CUDA_TRY(cudaGetLastError());
   }
   if (gparams && E.n > 0) {
