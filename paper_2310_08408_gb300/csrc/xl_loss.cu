@@ -470,6 +470,9 @@ xl_status xl_device_status(void* stream) {
   XL_CUDA_TRY(cudaMemcpyFromSymbol(&bits, g_status_bits, sizeof(bits)));
   XL_CUDA_TRY(cudaMemcpyToSymbol(g_status_bits, &zero, sizeof(zero)));
   if (bits & 1u) return fail(XL_ERR_NONFINITE, "a loss reduction produced a non-finite value");
+  unsigned int w = 0;
+  XL_TRY(status_word_take((cudaStream_t)stream, &w));
+  if (w & 2u) return fail(XL_ERR_CUDA, "a kernel gave up waiting for a bulk copy");
   return XL_OK;
 }
 

@@ -49,9 +49,43 @@ xl_status pass3_LV(const void* Tb, void* out, int nx, int ny, int cout, int cT, 
   return XL_OK;
 }
 
+// Pass 3 with the bulk-tensor gather (complex64, the default two rows per block).
+template <int LX>
+xl_status pass3_tma(const void* Tb, void* out, int nx, int ny, int cout, int cT, int np, cudaStream_t s,
+                    DzReduce red) {
+  constexpr int ROWS = kP3TmaRows;
+  const size_t sm = (size_t)ROWS * srow(LX) * sizeof(float2) + 128;  // + alignment slack
+  const void* tw;
+  XL_TRY(twiddles(LX, XL_C64, &tw));
+  XL_TRY(smem_attr((const void*)k_rs_pass3_tma<LX>, sm));
+  const int last = ((np - 1) / cout) * cT + (np - 1) % cout;  // highest T plane read
+  alignas(64) unsigned char map[128];
+  XL_TRY(tensor_map_2d_u64(Tb, (uint64_t)ny, (uint64_t)(last + 1) * LX, (uint64_t)ny * sizeof(float2),
+                           ROWS, 256, map));
+  unsigned int* status = nullptr;
+  XL_TRY(status_word(&status));
+  dim3 grid((ny + ROWS - 1) / ROWS, np);
+  LaunchScope ls("rs_pass3<" + std::to_string(LX) + ">", s);
+  k_rs_pass3_tma<LX><<<grid, ROWS * (LX / 16), sm, s>>>(*reinterpret_cast<const CUtensorMap*>(map),
+                                                        (float2*)out, nx, ny, cout, cT,
+                                                        (const float2*)tw, red, status);
+  XL_CUDA_TRY(cudaGetLastError());
+  return XL_OK;
+}
+
+inline bool pass3_tma_enabled() {
+  const char* e = getenv("XL_P3_TMA");
+  return !(e && e[0] == '0');
+}
+
 template <typename T, int LX>
 xl_status pass3_L(const void* Tb, void* out, int nx, int ny, int cout, int cT, int np, cudaStream_t s,
                   DzReduce red) {
+  if constexpr (sizeof(T) == 4 && LX >= 256) {
+    if ((LX < kTuneMinL || tuned_variant(TUNE_RS_PASS3, LX, XL_C64) == 0) && ny % 2 == 0 &&
+        pass3_tma_enabled())
+      return pass3_tma<LX>(Tb, out, nx, ny, cout, cT, np, s, red);
+  }
   if constexpr (LX >= kTuneMinL) {
     switch (tuned_variant(TUNE_RS_PASS3, LX, sizeof(T) == 8 ? XL_C128 : XL_C64)) {
       case 1: return pass3_LV<T, LX, 1>(Tb, out, nx, ny, cout, cT, np, s, red);

@@ -20,6 +20,8 @@
 // modulo 2 pi, before a single-precision sincos; it then runs the same two-pass FFT.
 #pragma once
 
+#include <cuda.h>
+
 #include "xl_fft.cuh"
 
 namespace xl {
@@ -169,6 +171,87 @@ k_rs_pass3(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, int nx, in
   for (int q = 0; q < 16; ++q) v[q] = row[spad(t + q * TT)];
   __syncthreads();
   team_fft<LX, +1>(v, row, t, tw);
+  const int y = y0 + team;
+  if (y < ny) {
+    C* d = out + (int64_t)p * nx * ny + (int64_t)y * nx;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) d[t + q * TT] = v[q];
+  }
+}
+
+// Pass 3 for complex64 with the gather done by the tensor-memory accelerator: one thread issues
+// LX / 256 tiled bulk copies of a box of 2 y by 256 kx each (4 KB; the tensor map sees T as rows
+// of ny 8-byte elements, one row per kx of every plane), completing on one shared-memory barrier.
+// The tile lands kx-major ([kx][2 y]), is read into registers and the same shared memory then
+// serves as the two transform rows. Two rows per block, as the asynchronous-copy gather.
+// A wait that does not complete within a bound sets bit 1 of `status` and ends the block.
+constexpr int kP3TmaRows = 2;
+constexpr unsigned kWaitLimit = 1u << 26;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+template <int LX>
+__global__ void __launch_bounds__(kP3TmaRows * (LX / 16), min_blocks_rows<kP3TmaRows * (LX / 16), 8>())
+k_rs_pass3_tma(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ out, int nx, int ny,
+               int cout, int cT, const float2* __restrict__ tw, DzReduce red,
+               unsigned* __restrict__ status) {
+  typedef float2 C;
+  constexpr int ROWS = kP3TmaRows;
+  constexpr int TT = LX / 16;
+  constexpr int NCOPY = LX / 256;
+  static_assert(ROWS * LX <= ROWS * srow(LX), "the gathered tile fits the transform rows");
+  extern __shared__ __align__(128) unsigned char smraw[];
+  // bulk tensor copies land on 128-byte boundaries: the launch adds 128 bytes for the shift
+  C* sm = reinterpret_cast<C*>(smraw + ((128u - (smem_addr(smraw) & 127u)) & 127u));
+  __shared__ __align__(8) unsigned long long bar;
+  const int team = threadIdx.x / TT, t = threadIdx.x % TT;
+  const int p = blockIdx.y;
+  const int y0 = blockIdx.x * ROWS;
+  if (red.part != nullptr && blockIdx.x == 0 && p % cout == 0) {
+    __shared__ double rbuf[32];
+    const int b = p / cout;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < red.n; i += blockDim.x) acc += red.part[(int64_t)b * red.n + i];
+    acc = block_sum(acc, rbuf);
+    if (threadIdx.x == 0) red.out[b] = acc;
+  }
+  const unsigned ba = smem_addr(&bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(ba) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(ba),
+                 "r"((unsigned)(NCOPY * 256 * ROWS * sizeof(C)))
+                 : "memory");
+    const int row0 = ((p / cout) * cT + (p % cout)) * LX;  // first kx row of the T plane
+#pragma unroll 1
+    for (int c = 0; c < NCOPY; ++c)
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::
+              "r"(smem_addr(sm + c * 256 * ROWS)),
+          "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(y0), "r"(row0 + c * 256), "r"(ba)
+          : "memory");
+  }
+  unsigned done = 0;
+  for (unsigned it = 0; !done && it < kWaitLimit; ++it)
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(ba)
+        : "memory");
+  if (__syncthreads_or(!done)) {  // the whole block gives up together
+    if (threadIdx.x == 0) atomicOr(status, 2u);
+    return;
+  }
+  C v[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = sm[(t + q * TT) * ROWS + team];
+  __syncthreads();  // every thread has its inputs before the transforms reuse the tile's memory
+  team_fft<LX, +1>(v, sm + team * srow(LX), t, tw);
   const int y = y0 + team;
   if (y < ny) {
     C* d = out + (int64_t)p * nx * ny + (int64_t)y * nx;

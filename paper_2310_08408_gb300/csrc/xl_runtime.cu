@@ -1,4 +1,7 @@
 // Host runtime: error strings, twiddle tables, workspaces, table cache.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cstdlib>
 #include <cstring>
 #include <list>
@@ -128,6 +131,59 @@ xl_status smem_attr(const void* func, size_t bytes) {
   if (it != g_smem_set.end() && it->second >= bytes) return XL_OK;
   XL_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   g_smem_set[func] = bytes;
+  return XL_OK;
+}
+
+xl_status tensor_map_2d_u64(const void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
+                            uint32_t box_inner, uint32_t box_outer, void* map_out) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!encode) {
+      void* fn = nullptr;
+      cudaDriverEntryPointQueryResult q;
+      XL_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                   cudaEnableDefault, &q));
+      if (q != cudaDriverEntryPointSuccess || !fn)
+        return fail(XL_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+      encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+  }
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {row_bytes};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode((CUtensorMap*)map_out, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+                            const_cast<void*>(base), dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(XL_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  return XL_OK;
+}
+
+xl_status status_word(unsigned int** out) {
+  static std::map<int, unsigned int*> words;
+  int dev = 0;
+  XL_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = words.find(dev);
+  if (it == words.end()) {
+    unsigned int* w = nullptr;
+    XL_CUDA_TRY(cudaMalloc(&w, sizeof(unsigned int)));
+    XL_CUDA_TRY(cudaMemset(w, 0, sizeof(unsigned int)));
+    XL_CUDA_TRY(cudaDeviceSynchronize());
+    it = words.emplace(dev, w).first;
+  }
+  *out = it->second;
+  return XL_OK;
+}
+
+xl_status status_word_take(cudaStream_t s, unsigned int* bits) {
+  unsigned int* w = nullptr;
+  XL_TRY(status_word(&w));
+  XL_CUDA_TRY(cudaMemcpyAsync(bits, w, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+  XL_CUDA_TRY(cudaMemsetAsync(w, 0, sizeof(unsigned int), s));
+  XL_CUDA_TRY(cudaStreamSynchronize(s));
   return XL_OK;
 }
 

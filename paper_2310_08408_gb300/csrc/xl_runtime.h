@@ -39,6 +39,17 @@ template <typename V> inline void key_put(std::string& k, const V& v) {
 // Sets the dynamic shared memory limit of a kernel once (per process).
 xl_status smem_attr(const void* func, size_t bytes);
 
+// Tensor map of a row-major 2D array of 8-byte elements (inner extent `inner`, `outer` rows of
+// `row_bytes` each) for tiled bulk copies of box_inner x box_outer elements; out-of-range
+// elements read as zero. The base must be 16-byte aligned and row_bytes a multiple of 16.
+xl_status tensor_map_2d_u64(const void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
+                            uint32_t box_inner, uint32_t box_outer, void* map_out /* 128 bytes */);
+
+// Device word of error bits that kernels set (bit 1: a wait on a bulk copy gave up); read and
+// cleared by xl_device_status().
+xl_status status_word(unsigned int** out);
+xl_status status_word_take(cudaStream_t s, unsigned int* bits);
+
 size_t dtype_csize(int dtype);  // bytes of one complex element
 
 // Launch variants chosen by the autotuner (xl_autotune): for each tunable kernel family, row
