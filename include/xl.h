@@ -360,7 +360,9 @@ xl_status xl_softmin(const double* losses, int32_t batch, int32_t n_det, double 
                      double* weights, void* stream);
 
 /* Synchronises `stream`, then returns and clears the device status: XL_ERR_NONFINITE if a loss
- * reduction produced a non-finite value since the last call, else XL_OK. */
+ * reduction produced a non-finite value since the last call, XL_ERR_TIMEOUT if a kernel gave up
+ * waiting for a bulk tensor copy (a bounded wait; the kernel's outputs are then incomplete),
+ * else XL_OK. */
 xl_status xl_device_status(void* stream);
 
 /* ---------------------------------------------------------------------------------------------

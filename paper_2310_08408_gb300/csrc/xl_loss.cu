@@ -472,7 +472,7 @@ xl_status xl_device_status(void* stream) {
   if (bits & 1u) return fail(XL_ERR_NONFINITE, "a loss reduction produced a non-finite value");
   unsigned int w = 0;
   XL_TRY(status_word_take((cudaStream_t)stream, &w));
-  if (w & 2u) return fail(XL_ERR_CUDA, "a kernel gave up waiting for a bulk copy");
+  if (w & 2u) return fail(XL_ERR_TIMEOUT, "a kernel gave up waiting for a bulk copy");
   return XL_OK;
 }
 
