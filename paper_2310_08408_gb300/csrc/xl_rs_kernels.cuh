@@ -715,7 +715,7 @@ __device__ __forceinline__ df df_sqrt(df x) {
 template <typename T> struct RsPhase;
 template <> struct RsPhase<float> {
   df dx2, dy2, z, z2, k, twopi;
-  float kz_red, zf, kf, c0, dxf, dyf;
+  float kz_red, zf, izf, kf, c0, dxf, dyf;
   __device__ RsPhase(const GenArgs& g, double zz) {
     dxf = (float)g.dx;
     dyf = (float)g.dy;
@@ -727,6 +727,7 @@ template <> struct RsPhase<float> {
     twopi = df_of(kTwoPi);
     kz_red = (float)(g.k * zz - kTwoPi * rint(g.k * zz / kTwoPi));
     zf = (float)zz;
+    izf = (float)(1.0 / zz);
     kf = (float)g.k;
     c0 = (float)(g.dx * g.dy / kTwoPi);
   }
@@ -740,16 +741,18 @@ template <> struct RsPhase<double> {
 };
 
 // dh/dz and the odd kinds from h, r and the unit phasor (shared by both precisions).
+// ir = 1 / r and iz = 1 / z come in precomputed (a sample then needs no division but the one of
+// the phase-invariant dz kinds).
 template <typename T>
-__device__ __forceinline__ cplx<T> rs_kinds(int kind, cplx<T> e, T r, T X, T Y, T z, T k, T c0,
-                                            bool rest) {
+__device__ __forceinline__ cplx<T> rs_kinds(int kind, cplx<T> e, T r, T ir, T X, T Y, T z, T iz, T k,
+                                            T c0, bool rest) {
   typedef cplx<T> C;
-  const T ir = (T)1 / r, ir2 = ir * ir, ir3 = ir2 * ir;
+  const T ir2 = ir * ir, ir3 = ir2 * ir;
   // h = c0 z (1/r - i k) e / r^2
   const C h = cmul(e, mk(c0 * z * ir3, -c0 * z * k * ir2));
   if (kind == KH) return h;
-  if (kind == KHX) return cscale(h, -X / z);
-  if (kind == KHY) return cscale(h, -Y / z);
+  if (kind == KHX) return cscale(h, -X * iz);
+  if (kind == KHY) return cscale(h, -Y * iz);
   // dh/dz = c0 e [(1/r^3 - i k / r^2) + z^2 (k^2/r^3 + 3 i k / r^4 - 3 / r^5)]
   const T z2 = z * z;
   const T re = ir3 + z2 * (k * k * ir3 - (T)3 * ir3 * ir2);
@@ -767,8 +770,8 @@ __device__ __forceinline__ cplx<T> rs_kinds(int kind, cplx<T> e, T r, T X, T Y, 
   }
   if (kind == KDH) return dh;
   // d/dz[-(X/z) h] = -(X/z)(dh - h/z)
-  const C dmh = csub(dh, cscale(h, (T)1 / z));
-  return cscale(dmh, kind == KDHX ? -X / z : -Y / z);
+  const C dmh = csub(dh, cscale(h, iz));
+  return cscale(dmh, kind == KDHX ? -X * iz : -Y * iz);
 }
 
 // The parts of a kernel sample at pixel offset (a, b) that every kind shares: the unit phasor
@@ -805,15 +808,23 @@ __device__ __forceinline__ void rs_phasor(int a, int b, const GenArgs& g, double
 __device__ __forceinline__ float2 rs_from_phasor(int kind, float2 e, int a, int b, const GenArgs& g,
                                                  const RsPhase<float>& P, float r) {
   const float X = (float)a * P.dxf, Y = (float)b * P.dyf;
-  if (r < 0.f) r = sqrtf(fmaf(X, X, fmaf(Y, Y, P.zf * P.zf)));
-  return rs_kinds<float>(kind, e, r, X, Y, P.zf, P.kf, P.c0, g.dz_rest != 0);
+  float ir;
+  if (r < 0.f) {  // r from the offsets: one reciprocal square root
+    const float r2 = fmaf(X, X, fmaf(Y, Y, P.zf * P.zf));
+    ir = rsqrtf(r2);
+    r = r2 * ir;
+  } else {
+    ir = 1.f / r;
+  }
+  return rs_kinds<float>(kind, e, r, ir, X, Y, P.zf, P.izf, P.kf, P.c0, g.dz_rest != 0);
 }
 __device__ __forceinline__ double2 rs_from_phasor(int kind, double2 e, int a, int b, const GenArgs& g,
                                                   const RsPhase<double>& P, double r) {
   const double X = a * g.dx, Y = b * g.dy;
   const double z = P.z;
   if (r < 0.0) r = sqrt(X * X + Y * Y + z * z);
-  return rs_kinds<double>(kind, e, r, X, Y, z, g.k, g.dx * g.dy / kTwoPi, g.dz_rest != 0);
+  return rs_kinds<double>(kind, e, r, 1.0 / r, X, Y, z, 1.0 / z, g.k, g.dx * g.dy / kTwoPi,
+                          g.dz_rest != 0);
 }
 
 // Generator pass A: for each b in [0, ny) and each kind, FFT along a of the kernel row placed
