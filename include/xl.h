@@ -24,6 +24,14 @@
  *     released by xl_cache_clear(). Calls that would allocate must not run inside stream
  *     capture: warm them up (same sizes) before capturing a CUDA graph.
  *
+ * Environment (read by the library; none is needed)
+ *   - XL_CACHE_BYTES: byte cap of the spectrum / chirp cache (default 8 GiB; least recently used
+ *     entries are freed above it).
+ *   - XL_RS_CHUNK_MB: budget of the RS intermediate planes one chunk of a batch may use (default
+ *     2048): the row passes run over a chunk per launch, pass 2 over up to 32 elements per launch.
+ *   - XL_P3_TMA=0: RS pass 3 gathers its rows with per-thread asynchronous copies instead of
+ *     tiled bulk tensor copies (complex64). Results are bit-identical either way.
+ *
  * Errors
  *   - Argument checks happen on the host before any launch and return XL_ERR_ARG or
  *     XL_ERR_UNSUPPORTED with nothing enqueued.
