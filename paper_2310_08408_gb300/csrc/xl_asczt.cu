@@ -86,10 +86,16 @@ xl_status run(bool adjoint, const void* in, const void* u_in, void* out, double*
     ax = axis_run(Axis<C>{t, t + nx, t + nx + mx});
     ay = axis_run(Axis<C>{u, u + ny, u + ny + my});
   }
-  // launches take runs of equal distances, up to ~48 MB of spectrum planes
-  int chunk = (int)std::max<int64_t>(1, ((int64_t)48 << 20) / (plane * (int64_t)cs));
+  // Batch elements per launch: up to kCztRun whatever their distances (each element reads the
+  // transfer tables of its own distance), within 2 GB of spectrum planes; the chunk's transfer
+  // tables stay within half of the table cache, so that filling one never evicts another of the
+  // same launch.
+  const size_t h_bytes1 = (size_t)2 * plane * cs;
+  int64_t chunk = std::max<int64_t>(1, ((int64_t)2048 << 20) / ((2 * plane + tplane + plane) * (int64_t)cs));
+  chunk = std::min<int64_t>(chunk, std::max<int64_t>(1, (int64_t)(table_cache_cap() / 2 / h_bytes1)));
+  chunk = std::min<int64_t>(chunk, kCztRun);
   if (zdev) chunk = 1;
-  chunk = std::min<int>(chunk, batch);
+  chunk = std::min<int64_t>(chunk, batch);
   const int nblk = want_dz ? as_dz_blocks<T>(ny, nx) : 0;
   auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
   const size_t b_plane = (size_t)chunk * plane * cs, b_t2 = (size_t)chunk * tplane * cs;
@@ -117,39 +123,46 @@ xl_status run(bool adjoint, const void* in, const void* u_in, void* out, double*
   AsTransferArgs tr;
   tr.nx = nx; tr.ny = ny; tr.dx = g->dx; tr.dy = g->dy; tr.k = kTwoPi / wavelength;
   for (int32_t b0 = 0; b0 < batch;) {
-    int nb = 1;
-    if (!zdev)
-      while (nb < chunk && b0 + nb < batch && z[b0 + nb] == z[b0]) ++nb;
-    // transfer tables Hc | dHc of this distance
+    const int nb = (int)std::min<int64_t>(chunk, batch - b0);
+    // transfer tables Hc | dHc of each element's distance
     const void* H = nullptr;
+    AsShift hs = as_shared();
     if (zdev) {
       tr.zdev = z + b0;
       tr.zval = 0.0;
       XL_TRY(as_transfer<T>(Hdev, (char*)Hdev + plane * cs, tr, s));
       H = Hdev;
     } else {
-      tr.zdev = nullptr;
-      tr.zval = z[b0];
-      std::string hk = "asczt_h";
-      key_put(hk, nx);
-      key_put(hk, ny);
-      key_put(hk, g->dx);
-      key_put(hk, g->dy);
-      key_put(hk, wavelength);
-      key_put(hk, z[b0]);
-      key_put(hk, dtype);
-      void* hp = nullptr;
-      XL_TRY(cached_table(hk, (size_t)2 * plane * cs, s, [&](void* buf) {
-        return as_transfer<T>(buf, (char*)buf + plane * cs, tr, s);
-      }, &hp));
-      H = hp;
+      const void* he = nullptr;
+      for (int e = 0; e < nb; ++e) {
+        if (e == 0 || z[b0 + e] != z[b0 + e - 1]) {
+          tr.zdev = nullptr;
+          tr.zval = z[b0 + e];
+          std::string hk = "asczt_h";
+          key_put(hk, nx);
+          key_put(hk, ny);
+          key_put(hk, g->dx);
+          key_put(hk, g->dy);
+          key_put(hk, wavelength);
+          key_put(hk, z[b0 + e]);
+          key_put(hk, dtype);
+          void* hp = nullptr;
+          XL_TRY(cached_table(hk, h_bytes1, s, [&](void* buf) {
+            return as_transfer<T>(buf, (char*)buf + plane * cs, tr, s);
+          }, &hp));
+          he = hp;
+        }
+        if (e == 0) H = he;
+        hs.s[e] = (const C*)he - (const C*)H;
+      }
+      hs.per_elem = nb > 1 ? 1 : 0;
     }
     const void* dH = (const char*)H + plane * cs;
     if (!adjoint) {
       const char* src = (const char*)in + (size_t)b0 * plane * cs;
       char* dst = (char*)out + (size_t)b0 * wplane * cs;
-      XL_TRY(as_fwd_pass<T>(AS_STAGE_A, nx, src, Tb, ny, nullptr, 0, nb, s));
-      XL_TRY(as_fwd_pass<T>(AS_STAGE_B, ny, Tb, Sb, nx, H, 0, nb, s));
+      XL_TRY(as_fwd_pass<T>(AS_STAGE_A, nx, src, Tb, ny, nullptr, as_shared(), nb, s));
+      XL_TRY(as_fwd_pass<T>(AS_STAGE_B, ny, Tb, Sb, nx, H, hs, nb, s));
       XL_TRY(czt_pass<T>(CZT_FWD_X, false, ta.Lx, Sb, T2, d, ax, nb, s));
       XL_TRY(czt_pass<T>(CZT_FWD_Y, false, ta.Ly, T2, dst, d, ay, nb, s));
     } else {
@@ -158,12 +171,12 @@ xl_status run(bool adjoint, const void* in, const void* u_in, void* out, double*
       XL_TRY(czt_pass<T>(CZT_ADJ_X, false, ta.Lx, T2, Sb, d, ax, nb, s));
       if (want_dz)
         XL_TRY(as_fwd_pass<T>(AS_STAGE_A, nx, (const char*)u_in + (size_t)b0 * plane * cs, TU, ny,
-                              nullptr, 0, nb, s));
-      XL_TRY(as_adj_pass<T>(AS_STAGE_B, ny, Sb, Tb, nx, H, dH, 0, want_dz ? TU : nullptr,
+                              nullptr, as_shared(), nb, s));
+      XL_TRY(as_adj_pass<T>(AS_STAGE_B, ny, Sb, Tb, nx, H, dH, hs, want_dz ? TU : nullptr,
                             want_dz ? dzp : nullptr, nb, s));
       if (want_field)
         XL_TRY(as_adj_pass<T>(AS_STAGE_A, nx, Tb, (char*)out + (size_t)b0 * plane * cs, ny, nullptr,
-                              nullptr, 0, nullptr, nullptr, nb, s));
+                              nullptr, as_shared(), nullptr, nullptr, nb, s));
       if (want_dz) {
         LaunchScope ls("asczt_reduce", s);
         k_as_reduce<<<nb, 256, 0, s>>>(dzp, nblk, g_z + b0);

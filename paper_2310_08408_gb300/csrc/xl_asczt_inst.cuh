@@ -9,7 +9,7 @@ namespace xl {
 namespace {
 
 template <typename T, int L, int STAGE>
-xl_status fwd_L(const void* in, void* out, int nrows, const void* Hc, int64_t h_stride, int nb,
+xl_status fwd_L(const void* in, void* out, int nrows, const void* Hc, const AsShift& hs, int nb,
                 cudaStream_t s) {
   typedef cplx<T> C;
   constexpr int ROWS = as_rows<L, sizeof(C), false>();
@@ -20,14 +20,14 @@ xl_status fwd_L(const void* in, void* out, int nrows, const void* Hc, int64_t h_
   LaunchScope ls(std::string(STAGE == AS_STAGE_A ? "asczt_spec_a<" : "asczt_spec_b<") +
                      std::to_string(L) + ">", s);
   k_as_fwd<T, L, STAGE><<<dim3((nrows + ROWS - 1) / ROWS, nb), ROWS * (L / 16), sm, s>>>(
-      (const C*)in, (C*)out, nrows, (const C*)Hc, h_stride, (const C*)tw);
+      (const C*)in, (C*)out, nrows, (const C*)Hc, hs, (const C*)tw);
   XL_CUDA_TRY(cudaGetLastError());
   return XL_OK;
 }
 
 template <typename T, int L, int STAGE, bool DZ>
 xl_status adj_L(const void* in, void* out, int nrows, const void* Hc, const void* dHc,
-                int64_t h_stride, const void* TU, double* dz_part, int nb, cudaStream_t s) {
+                const AsShift& hs, const void* TU, double* dz_part, int nb, cudaStream_t s) {
   typedef cplx<T> C;
   constexpr int ROWS = as_rows<L, sizeof(C), DZ>();
   const size_t sm = (size_t)ROWS * (DZ ? 2 : 1) * tpitch(L, sizeof(C), ROWS) * sizeof(C);
@@ -37,7 +37,7 @@ xl_status adj_L(const void* in, void* out, int nrows, const void* Hc, const void
   LaunchScope ls(std::string(STAGE == AS_STAGE_A ? "asczt_spec_a_adj<" : (DZ ? "asczt_spec_b_adj_dz<" : "asczt_spec_b_adj<")) +
                      std::to_string(L) + ">", s);
   k_as_adj<T, L, STAGE, DZ><<<dim3((nrows + ROWS - 1) / ROWS, nb), ROWS * (L / 16), sm, s>>>(
-      (const C*)in, (C*)out, nrows, (const C*)Hc, (const C*)dHc, h_stride, (const C*)TU, dz_part,
+      (const C*)in, (C*)out, nrows, (const C*)Hc, (const C*)dHc, hs, (const C*)TU, dz_part,
       (const C*)tw);
   XL_CUDA_TRY(cudaGetLastError());
   return XL_OK;
@@ -58,9 +58,9 @@ xl_status adj_L(const void* in, void* out, int nrows, const void* Hc, const void
 
 template <>
 xl_status as_fwd_pass<XL_REAL>(int stage, int L, const void* in, void* out, int nrows,
-                               const void* Hc, int64_t h_stride, int nb, cudaStream_t s) {
-#define FA(LL) fwd_L<XL_REAL, LL, AS_STAGE_A>(in, out, nrows, Hc, h_stride, nb, s)
-#define FB(LL) fwd_L<XL_REAL, LL, AS_STAGE_B>(in, out, nrows, Hc, h_stride, nb, s)
+                               const void* Hc, const AsShift& hs, int nb, cudaStream_t s) {
+#define FA(LL) fwd_L<XL_REAL, LL, AS_STAGE_A>(in, out, nrows, Hc, hs, nb, s)
+#define FB(LL) fwd_L<XL_REAL, LL, AS_STAGE_B>(in, out, nrows, Hc, hs, nb, s)
   if (stage == AS_STAGE_A) {
     XL_AS_SWITCH(L, FA)
   } else {
@@ -73,11 +73,11 @@ xl_status as_fwd_pass<XL_REAL>(int stage, int L, const void* in, void* out, int 
 
 template <>
 xl_status as_adj_pass<XL_REAL>(int stage, int L, const void* in, void* out, int nrows,
-                               const void* Hc, const void* dHc, int64_t h_stride, const void* TU,
+                               const void* Hc, const void* dHc, const AsShift& hs, const void* TU,
                                double* dz_part, int nb, cudaStream_t s) {
-#define AA(LL) adj_L<XL_REAL, LL, AS_STAGE_A, false>(in, out, nrows, Hc, dHc, h_stride, TU, dz_part, nb, s)
-#define AB(LL) adj_L<XL_REAL, LL, AS_STAGE_B, false>(in, out, nrows, Hc, dHc, h_stride, TU, dz_part, nb, s)
-#define AD(LL) adj_L<XL_REAL, LL, AS_STAGE_B, true>(in, out, nrows, Hc, dHc, h_stride, TU, dz_part, nb, s)
+#define AA(LL) adj_L<XL_REAL, LL, AS_STAGE_A, false>(in, out, nrows, Hc, dHc, hs, TU, dz_part, nb, s)
+#define AB(LL) adj_L<XL_REAL, LL, AS_STAGE_B, false>(in, out, nrows, Hc, dHc, hs, TU, dz_part, nb, s)
+#define AD(LL) adj_L<XL_REAL, LL, AS_STAGE_B, true>(in, out, nrows, Hc, dHc, hs, TU, dz_part, nb, s)
   if (stage == AS_STAGE_A) {
     XL_AS_SWITCH(L, AA)
   } else if (!dz_part) {

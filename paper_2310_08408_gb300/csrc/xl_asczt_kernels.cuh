@@ -17,6 +17,21 @@
 
 namespace xl {
 
+// Per-element offsets of the transfer tables of one launch (up to kCztRun elements).
+struct AsShift {
+  int per_elem;
+  int64_t s[kCztRun];
+  __host__ __device__ __forceinline__ int64_t at(int b) const {
+    return per_elem ? s[b < kCztRun ? b : kCztRun - 1] : 0;
+  }
+};
+inline AsShift as_shared() {
+  AsShift h;
+  h.per_elem = 0;
+  for (int i = 0; i < kCztRun; ++i) h.s[i] = 0;
+  return h;
+}
+
 // Teams (rows) per block: as in the transposing RS passes, whole 32-byte sectors per column when
 // possible; the adjoint with a distance gradient keeps a second row per team, so it holds half as
 // many teams. Register budget: 1024 threads an SM for complex64, 512 for complex128.
@@ -72,13 +87,14 @@ enum { AS_STAGE_A = 0, AS_STAGE_B = 1 };
 
 // Forward spectrum pass. in: [batch][nrows][L] rows; out: [batch][L][nrows] (transposed).
 // STAGE_A multiplies the input by (-1)^(column + row); STAGE_B multiplies the transform by
-// Hc[row][.] (h_stride elements between the tables of consecutive batch elements, 0: shared).
+// Hc[row][.] of batch element b at hs.at(b) elements from Hc (each element's distance has its
+// own tables; all elements share Hc when per_elem is 0).
 // grid: (ceil(nrows / ROWS), batch).
 template <typename T, int L, int STAGE>
 __global__ void __launch_bounds__(as_rows<L, sizeof(cplx<T>), false>() * (L / 16),
                                   as_min_blocks<L, sizeof(cplx<T>), false>())
 k_as_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nrows,
-         const cplx<T>* __restrict__ Hc, int64_t h_stride, const cplx<T>* __restrict__ tw) {
+         const cplx<T>* __restrict__ Hc, AsShift hs, const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
   constexpr int ROWS = as_rows<L, sizeof(C), false>();
   static_assert(team_barriers_fit<L>(ROWS * (L / 16)), "too many teams for the named barriers");
@@ -105,7 +121,7 @@ k_as_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nrows,
   C* rowp = sm + team * P;
   team_fft<L, -1>(v, rowp, t, tw);
   if constexpr (STAGE == AS_STAGE_B) {
-    const C* h = Hc + b * h_stride + (int64_t)row * L;
+    const C* h = Hc + hs.at(b) + (int64_t)row * L;
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = cmul(v[q], __ldg(h + t + q * TT));
   }
@@ -125,7 +141,7 @@ template <typename T, int L, int STAGE, bool DZ>
 __global__ void __launch_bounds__(as_rows<L, sizeof(cplx<T>), DZ>() * (L / 16),
                                   as_min_blocks<L, sizeof(cplx<T>), DZ>())
 k_as_adj(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nrows,
-         const cplx<T>* __restrict__ Hc, const cplx<T>* __restrict__ dHc, int64_t h_stride,
+         const cplx<T>* __restrict__ Hc, const cplx<T>* __restrict__ dHc, AsShift hs,
          const cplx<T>* __restrict__ TU, double* __restrict__ dz_part, const cplx<T>* __restrict__ tw) {
   typedef cplx<T> C;
   constexpr int ROWS = as_rows<L, sizeof(C), DZ>();
@@ -150,7 +166,7 @@ k_as_adj(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nrows,
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = us[t + q * TT];
     team_fft<L, -1>(v, rowp, t, tw);
-    const C* dh = dHc + b * h_stride + (int64_t)row * L;
+    const C* dh = dHc + hs.at(b) + (int64_t)row * L;
 #pragma unroll
     for (int q = 0; q < 16; ++q) ur[spad(t + q * TT)] = cmul(v[q], __ldg(dh + t + q * TT));
   }
@@ -176,7 +192,7 @@ k_as_adj(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int nrows,
         dz_part[(int64_t)b * gridDim.x + blockIdx.x] = tot;
       }
     }
-    const C* h = Hc + b * h_stride + (int64_t)row * L;
+    const C* h = Hc + hs.at(b) + (int64_t)row * L;
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = cmulc(v[q], __ldg(h + t + q * TT));
   }
