@@ -542,8 +542,21 @@ def main():
                         "frac": ach / hbm, "traffic": traffic, "kernel": name,
                         "share": tot / total if total else None,
                         "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
-    kernels = {k: {"launches": v[0] // 3, "ms_per_step": v[1] / 3,
-                   "fields_per_launch": fields_per_launch(k, v[0])} for k, v in prof.items()}
+    kernels = {}
+    clk_k = ck.get("sm_mhz") or 1900.0
+    fp32_k = sms * 128 * 2 * clk_k * 1e6 / 1e12
+    for k, (cnt_k, tot_k) in prof.items():
+        fpl = fields_per_launch(k, cnt_k)
+        ent = {"launches": cnt_k // 3, "ms_per_step": tot_k / 3, "fields_per_launch": fpl}
+        fl, nb = kernel_model(k, {"n": N, "m": M, "per_launch": fpl})
+        if fl is not None:  # each kernel against the roof its model says bounds it
+            avg = tot_k / cnt_k / 1000.0
+            alu = fl / (fp32_k * 1e12) >= nb / (hbm * 1e9)
+            ent["bound"] = "alu" if alu else "hbm"
+            ent["frac"] = (fl / avg / 1e12 / fp32_k) if alu else (nb / avg / 1e9 / hbm)
+            ent["hbm_gbs"] = nb / avg / 1e9
+            ent["tflops"] = fl / avg / 1e12
+        kernels[k] = ent
 
     # end to end: pinned host input -> device, the step, results back to pinned host buffers,
     # streamed in chunks of E2E_CHUNK fields so that the copies overlap the kernels
