@@ -128,6 +128,7 @@ P2Args p2_args(const xl_grid* g, const Spectra& sp, int cT, int cU) {
   a.cS = 0;
   a.per_elem = 0;
   for (int i = 0; i < kP2Run; ++i) a.hshift[i] = 0;
+  a.status = nullptr;
   return a;
 }
 
@@ -196,7 +197,17 @@ xl_status run_op(Op op, const void* in, const void* u_in, void* out, double* g_z
   const size_t hq_bytes1 = (size_t)sp.count * (nx + 1) * (ny + 1) * cs;
   const size_t s_bytes1 = (size_t)sp.count * (nx + 1) * ny * cs;
   // device distances: every element of a chunk gets its spectra generated into the workspace
-  const int64_t elem_ws = (int64_t)(cT + cUw) * t_plane * cs + (zdev ? (int64_t)(s_bytes1 + hq_bytes1) : 0);
+  // Row-major intermediate (complex64 scalar forward and saved-spectrum adjoint, rows of 256 and
+  // more): pass 1 stores each row's transform as it stands, pass 2 gathers its columns with bulk
+  // tensor copies (XL_RS_RM=0 keeps the transposing pass 1).
+  int mode = op == OP_RS_FWD ? P2_RS : op == OP_VRS_FWD ? P2_VRS : op == OP_RS_BWD ? P2_RS_BWD
+                                                                                  : P2_VRS_BWD;
+  if (want_dz && save_in) mode = op == OP_RS_BWD ? P2_RS_BWD_S : P2_VRS_BWD_S;
+  const char* rm_env = getenv("XL_RS_RM");
+  const bool rm = sizeof(T) == 4 && (mode == P2_RS || mode == P2_RS_BWD_S) && 2 * nx >= 256 &&
+                  !(rm_env && rm_env[0] == '0');
+  const int64_t elem_ws = (int64_t)(cT * (rm ? 2 : 1) + cUw) * t_plane * cs +
+                          (zdev ? (int64_t)(s_bytes1 + hq_bytes1) : 0);
   const int chunk_max = zdev ? std::min(chunk_size(elem_ws, batch), kP2Run) : chunk_size(elem_ws, batch);
   // pass-2 group: up to kP2Run elements whose spectra together stay within half of the table
   // cache, so that fetching one never evicts another of the same launch (device distances: the
@@ -212,24 +223,27 @@ xl_status run_op(Op op, const void* in, const void* u_in, void* out, double* g_z
   const size_t hq_bytes = zdev ? (size_t)chunk_max * hq_bytes1 : 0;
   auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
   void* ws = nullptr;
-  XL_TRY(workspace(s, al(t_bytes) + al(u_bytes) + al(dz_bytes) + al(s_bytes) + al(hq_bytes), &ws));
+  const size_t r_bytes = rm ? t_bytes : 0;
+  XL_TRY(workspace(s, al(t_bytes) + al(u_bytes) + al(dz_bytes) + al(s_bytes) + al(hq_bytes) + al(r_bytes),
+                   &ws));
   char* w = (char*)ws;
   void* Tb = w;
   void* Ub = w + al(t_bytes);
   double* dzp = (double*)(w + al(t_bytes) + al(u_bytes));
   void* dev_s = w + al(t_bytes) + al(u_bytes) + al(dz_bytes);
   void* dev_hq = (char*)dev_s + al(s_bytes);
+  void* Tr = rm ? (char*)dev_hq + al(hq_bytes) : nullptr;
 
   const char* src = (const char*)in;
   const char* usrc = (const char*)u_in;
   char* dst = (char*)out;
-  int mode = op == OP_RS_FWD ? P2_RS : op == OP_VRS_FWD ? P2_VRS : op == OP_RS_BWD ? P2_RS_BWD
-                                                                                  : P2_VRS_BWD;
-  if (want_dz && save_in) mode = op == OP_RS_BWD ? P2_RS_BWD_S : P2_VRS_BWD_S;
   for (int32_t b0 = 0; b0 < batch;) {
     // a chunk of elements: row passes over all of it, pass 2 per run of equal distances
     const int nc = chunk_max < batch - b0 ? chunk_max : batch - b0;
-    XL_TRY(rs_pass1<T>(src + (size_t)b0 * cin * plane * cs, Tb, nx, ny, cin, cT, nc * cin, s));
+    if (rm)
+      XL_TRY(rs_pass1_rm<T>(src + (size_t)b0 * cin * plane * cs, Tr, nx, ny, cin, cT, nc * cin, s));
+    else
+      XL_TRY(rs_pass1<T>(src + (size_t)b0 * cin * plane * cs, Tb, nx, ny, cin, cT, nc * cin, s));
     if (want_dz && !save_in)
       XL_TRY(rs_pass1<T>(usrc + (size_t)b0 * cU * plane * cs, Ub, nx, ny, cU, cU, nc * cU, s));
     // pass 2 over groups of up to kP2Run elements, each element with the spectra of its own
@@ -264,7 +278,7 @@ xl_status run_op(Op op, const void* in, const void* u_in, void* out, double* g_z
       a.want_dz = want_dz;
       XL_TRY(rs_pass2<T>(mode, (char*)Tb + e0 * cT * t_plane * cs,
                          (const char*)Ub + e0 * cUw * t_plane * cs, Hq0, dzp + e0 * p2blocks, a, nb,
-                         s));
+                         s, rm ? (const char*)Tr + e0 * cT * t_plane * cs : nullptr));
       // the distance partials are summed by pass 3 when it runs, else by their own launch
       if (want_dz && !want_field)
         XL_TRY(launch_reduce<T>(dzp + e0 * p2blocks, p2blocks, g_z + r0, nb, s));

@@ -97,37 +97,73 @@ xl_status pass3_L(const void* Tb, void* out, int nx, int ny, int cout, int cT, i
 
 template <typename T, int LY, int MODE>
 xl_status pass2_LM(void* Tb, const void* Ub, const void* Hq, double* dz, const P2Args& a, int nb,
-                   cudaStream_t s) {
+                   cudaStream_t s, const void* Tr) {
   constexpr int ROWS = rows_cols<LY>();
-  const size_t sm = (size_t)p2_rows_per_team<T, LY, MODE>() * ROWS * srow(LY) * sizeof(cplx<T>);
+  size_t sm = (size_t)p2_rows_per_team<T, LY, MODE>() * ROWS * srow(LY) * sizeof(cplx<T>);
   if (sm > (size_t)227 * 1024)
     return fail(XL_ERR_UNSUPPORTED,
                 "vectorial RS: a column of this length needs more shared memory than an SM has "
                 "(complex128 with nx = 4096)");
   const void* tw;
   XL_TRY(twiddles(LY, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
-  XL_TRY(smem_attr((const void*)k_rs_pass2<T, LY, MODE>, sm));
   const int LX = 2 * a.nx;
   dim3 grid((LX + ROWS - 1) / ROWS, nb);
   LaunchScope ls("rs_pass2_m" + std::to_string(MODE) + (a.spec_out ? "_save<" : "<") + std::to_string(LY) + ">", s);
+  alignas(64) unsigned char map[128] = {};
+  if constexpr (sizeof(T) == 4 && (MODE == P2_RS || MODE == P2_RS_BWD_S)) {
+    if (Tr) {  // input columns gathered from the row-major intermediate by bulk tensor copies
+      constexpr int W = ROWS >= 2 ? ROWS : 2;
+      const int ny = a.ny, boxr = ny < 256 ? ny : 256;
+      XL_TRY(tensor_map_2d_u64(Tr, (uint64_t)LX, (uint64_t)nb * a.cT * ny, (uint64_t)LX * sizeof(float2),
+                               W, boxr, map));
+      P2Args ar = a;
+      XL_TRY(status_word(&ar.status));
+      sm += 128;  // alignment slack of the tile
+      XL_TRY(smem_attr((const void*)k_rs_pass2<T, LY, MODE, true>, sm));
+      k_rs_pass2<T, LY, MODE, true><<<grid, ROWS * (LY / 16), sm, s>>>(
+          (cplx<T>*)Tb, (const cplx<T>*)Ub, (const cplx<T>*)Hq, dz, ar, (const cplx<T>*)tw,
+          *reinterpret_cast<const CUtensorMap*>(map));
+      XL_CUDA_TRY(cudaGetLastError());
+      return XL_OK;
+    }
+  }
+  if (Tr) return fail(XL_ERR_ARG, "rs_pass2: row-major input for this mode / precision");
+  XL_TRY(smem_attr((const void*)k_rs_pass2<T, LY, MODE>, sm));
   k_rs_pass2<T, LY, MODE><<<grid, ROWS * (LY / 16), sm, s>>>(
-      (cplx<T>*)Tb, (const cplx<T>*)Ub, (const cplx<T>*)Hq, dz, a, (const cplx<T>*)tw);
+      (cplx<T>*)Tb, (const cplx<T>*)Ub, (const cplx<T>*)Hq, dz, a, (const cplx<T>*)tw,
+      *reinterpret_cast<const CUtensorMap*>(map));
   XL_CUDA_TRY(cudaGetLastError());
   return XL_OK;
 }
 
 template <typename T, int LY>
 xl_status pass2_L(int mode, void* Tb, const void* Ub, const void* Hq, double* dz, const P2Args& a,
-                  int nb, cudaStream_t s) {
+                  int nb, cudaStream_t s, const void* Tr) {
   switch (mode) {
-    case P2_RS: return pass2_LM<T, LY, P2_RS>(Tb, Ub, Hq, dz, a, nb, s);
-    case P2_VRS: return pass2_LM<T, LY, P2_VRS>(Tb, Ub, Hq, dz, a, nb, s);
-    case P2_RS_BWD: return pass2_LM<T, LY, P2_RS_BWD>(Tb, Ub, Hq, dz, a, nb, s);
-    case P2_VRS_BWD: return pass2_LM<T, LY, P2_VRS_BWD>(Tb, Ub, Hq, dz, a, nb, s);
-    case P2_RS_BWD_S: return pass2_LM<T, LY, P2_RS_BWD_S>(Tb, Ub, Hq, dz, a, nb, s);
-    case P2_VRS_BWD_S: return pass2_LM<T, LY, P2_VRS_BWD_S>(Tb, Ub, Hq, dz, a, nb, s);
+    case P2_RS: return pass2_LM<T, LY, P2_RS>(Tb, Ub, Hq, dz, a, nb, s, Tr);
+    case P2_VRS: return pass2_LM<T, LY, P2_VRS>(Tb, Ub, Hq, dz, a, nb, s, Tr);
+    case P2_RS_BWD: return pass2_LM<T, LY, P2_RS_BWD>(Tb, Ub, Hq, dz, a, nb, s, Tr);
+    case P2_VRS_BWD: return pass2_LM<T, LY, P2_VRS_BWD>(Tb, Ub, Hq, dz, a, nb, s, Tr);
+    case P2_RS_BWD_S: return pass2_LM<T, LY, P2_RS_BWD_S>(Tb, Ub, Hq, dz, a, nb, s, Tr);
+    case P2_VRS_BWD_S: return pass2_LM<T, LY, P2_VRS_BWD_S>(Tb, Ub, Hq, dz, a, nb, s, Tr);
   }
   return fail(XL_ERR_ARG, "rs_pass2: bad mode");
+}
+
+// Pass 1 into the row-major intermediate (complex64).
+template <int LX>
+xl_status pass1_rm_L(const void* in, void* Tr, int nx, int ny, int cin, int cT, int np, cudaStream_t s) {
+  constexpr int ROWS = rows_cols<LX>();
+  const size_t sm = (size_t)ROWS * srow(LX) * sizeof(float2);
+  const void* tw;
+  XL_TRY(twiddles(LX, XL_C64, &tw));
+  XL_TRY(smem_attr((const void*)k_rs_pass1_rm<LX>, sm));
+  dim3 grid((ny + ROWS - 1) / ROWS, np);
+  LaunchScope ls("rs_pass1<" + std::to_string(LX) + ">", s);
+  k_rs_pass1_rm<LX><<<grid, ROWS * (LX / 16), sm, s>>>((const float2*)in, (float2*)Tr, nx, ny, cin,
+                                                      cT, (const float2*)tw);
+  XL_CUDA_TRY(cudaGetLastError());
+  return XL_OK;
 }
 
 template <typename T, int LX, int LY>
@@ -184,6 +220,22 @@ xl_status gen_L(void* S, void* Hq, const GenArgs& g, int nb, cudaStream_t s) {
   }
 
 template <>
+xl_status rs_pass1_rm<XL_REAL>(const void* in, void* Tr, int nx, int ny, int cin, int cT, int np,
+                               cudaStream_t s) {
+  if constexpr (sizeof(XL_REAL) == 4) {
+    switch (2 * nx) {
+      case 256: return pass1_rm_L<256>(in, Tr, nx, ny, cin, cT, np, s);
+      case 512: return pass1_rm_L<512>(in, Tr, nx, ny, cin, cT, np, s);
+      case 1024: return pass1_rm_L<1024>(in, Tr, nx, ny, cin, cT, np, s);
+      case 2048: return pass1_rm_L<2048>(in, Tr, nx, ny, cin, cT, np, s);
+      case 4096: return pass1_rm_L<4096>(in, Tr, nx, ny, cin, cT, np, s);
+      case 8192: return pass1_rm_L<8192>(in, Tr, nx, ny, cin, cT, np, s);
+    }
+  }
+  return fail(XL_ERR_UNSUPPORTED, "rs_pass1_rm: complex64 rows of 256..8192");
+}
+
+template <>
 xl_status rs_pass1<XL_REAL>(const void* in, void* Tb, int nx, int ny, int cin, int cT, int np,
                             cudaStream_t s) {
 #define C1(L) pass1_L<XL_REAL, L>(in, Tb, nx, ny, cin, cT, np, s)
@@ -203,8 +255,8 @@ xl_status rs_pass3<XL_REAL>(const void* Tb, void* out, int nx, int ny, int cout,
 
 template <>
 xl_status rs_pass2<XL_REAL>(int mode, void* Tb, const void* Ub, const void* Hq, double* dz,
-                            const P2Args& a, int nb, cudaStream_t s) {
-#define C2(L) pass2_L<XL_REAL, L>(mode, Tb, Ub, Hq, dz, a, nb, s)
+                            const P2Args& a, int nb, cudaStream_t s, const void* Tr) {
+#define C2(L) pass2_L<XL_REAL, L>(mode, Tb, Ub, Hq, dz, a, nb, s, Tr)
   XL_SWITCH_L(2 * a.ny, C2)
 #undef C2
   return fail(XL_ERR_UNSUPPORTED, "rs_pass2: unsupported ny");

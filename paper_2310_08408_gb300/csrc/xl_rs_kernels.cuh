@@ -114,6 +114,34 @@ k_rs_pass1(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, int nx, int
   store_rows_transposed<LX, ROWS, P>(sm, LX, dst, ny, y0, ny);
 }
 
+// Pass 1 into the row-major intermediate Tr[plane][y][kx] (complex64; read by pass 2 through
+// bulk tensor copies): one row per team, the transform's registers stored straight to the row.
+template <int LX>
+__global__ void __launch_bounds__(rows_cols<LX>() * (LX / 16),
+                                  (1024 / (rows_cols<LX>() * (LX / 16))) > 0 ? 1024 / (rows_cols<LX>() * (LX / 16)) : 1)
+k_rs_pass1_rm(const float2* __restrict__ in, float2* __restrict__ Tr, int nx, int ny, int cin,
+              int cT, const float2* __restrict__ tw) {
+  constexpr int ROWS = rows_cols<LX>();
+  constexpr int TT = LX / 16;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  const int team = threadIdx.x / TT, t = threadIdx.x % TT;
+  const int p = blockIdx.y;
+  const int y_raw = blockIdx.x * ROWS + team;
+  const bool live = y_raw < ny;
+  const int y = live ? y_raw : ny - 1;  // dead teams transform a valid row and store nothing
+  const float2* src = in + (int64_t)p * nx * ny + (int64_t)y * nx;
+  float2 v[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = q < 8 ? src[t + q * TT] : make_float2(0.f, 0.f);
+  team_fft<LX, -1>(v, sm + team * srow(LX), t, tw);
+  if (live) {
+    float2* d = Tr + ((int64_t)(p / cin) * cT + (p % cin)) * (int64_t)LX * ny + (int64_t)y * LX;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) d[t + q * TT] = v[q];
+  }
+}
+
 // Block-wide sum of a double (one value per thread) -> thread 0; sbuf holds 32 doubles.
 __device__ __forceinline__ double block_sum(double v, double* sbuf) {
 #pragma unroll
@@ -291,6 +319,7 @@ struct P2Args {
   int per_elem;         // 1: element b's spectra start hshift[b] elements after Hq (its own
                         // distance); 0: every element uses Hq
   int64_t hshift[kP2Run];
+  unsigned* status;     // device status word (bulk-copy gather of row-major input)
 };
 
 // Spectrum `Hk` along one kx row at ky = t + q TT (TT = LY / 16, ny = 8 TT): the quadrant row
@@ -342,6 +371,56 @@ __device__ __forceinline__ void store_full(const C (&v)[16], C* __restrict__ dst
   for (int q = 0; q < 16; ++q) dst[t + q * TT] = v[q];
 }
 
+// Column gather of pass 2 from the row-major layout Tr[plane][y][kx] that pass 1 writes for the
+// scalar forward and saved-spectrum adjoint (complex64): one thread issues ny / box tiled bulk
+// tensor copies of W x box elements (W = max(ROWS, 2) consecutive kx, box <= 256 rows of y)
+// completing on one shared-memory barrier; each team reads its kx from the tile, which then
+// gives its memory back to the transform rows. Returns false (every thread of the block) when the
+// bounded wait gave up; bit 1 of `status` is set.
+template <int LY, int ROWS>
+__device__ __forceinline__ bool gather_col_rm(float2 (&v)[16], float2* tile, const CUtensorMap& map,
+                                              unsigned long long* bar, int kx, int row0, int ny,
+                                              int t, unsigned* status) {
+  constexpr int TT = LY / 16;
+  constexpr int W = ROWS >= 2 ? ROWS : 2;
+  const int kx0 = (int)(blockIdx.x * ROWS) & ~(W - 1);
+  const int boxr = ny < 256 ? ny : 256;
+  const int ncopy = ny / boxr;
+  const unsigned ba = smem_addr(bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(ba) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(ba),
+                 "r"((unsigned)(ncopy * boxr * W * sizeof(float2)))
+                 : "memory");
+#pragma unroll 1
+    for (int c = 0; c < ncopy; ++c)
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::
+              "r"(smem_addr(tile + c * boxr * W)),
+          "l"(reinterpret_cast<uint64_t>(&map)), "r"(kx0), "r"(row0 + c * boxr), "r"(ba)
+          : "memory");
+  }
+  unsigned done = 0;
+  for (unsigned it = 0; !done && it < kWaitLimit; ++it)
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(ba)
+        : "memory");
+  if (__syncthreads_or(!done)) {
+    if (threadIdx.x == 0) atomicOr(status, 2u);
+    return false;
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = q < 8 ? tile[(t + q * TT) * W + (kx - kx0)] : make_float2(0.f, 0.f);
+  __syncthreads();  // every team has its column before the transforms reuse the tile's memory
+  return true;
+}
+
 // Blocks per SM the register budget of each pass-2 mode aims at (256-thread blocks).
 template <int MODE> __host__ __device__ constexpr int p2_min_blocks() {
   return MODE == P2_RS || MODE == P2_RS_BWD_S ? 4 : (MODE == P2_RS_BWD ? 3 : 2);
@@ -369,17 +448,23 @@ template <typename T, int LY, int MODE> __host__ __device__ constexpr int p2_lau
              : 1;
 }
 
-template <typename T, int LY, int MODE>
+// RM: the input columns (T0 of the scalar forward and saved-spectrum adjoint, complex64) come
+// from the row-major intermediate through the tensor map `tin` (gather_col_rm); the results go
+// to the column-major Tb as usual.
+template <typename T, int LY, int MODE, bool RM = false>
 __global__ void __launch_bounds__(rows_cols<LY>() * (LY / 16), p2_launch_min_blocks<T, LY, MODE>())
 k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<T>* __restrict__ Hq,
-           double* __restrict__ dz_part, P2Args a, const cplx<T>* __restrict__ tw) {
+           double* __restrict__ dz_part, P2Args a, const cplx<T>* __restrict__ tw,
+           const __grid_constant__ CUtensorMap tin) {
   typedef cplx<T> C;
   constexpr int ROWS = rows_cols<LY>();
   static_assert(team_barriers_fit<LY>(ROWS * (LY / 16)), "too many teams for the named barriers");
   constexpr int TT = LY / 16;
   constexpr int SR = srow(LY);
-  extern __shared__ __align__(16) unsigned char smraw[];
-  C* sm = reinterpret_cast<C*>(smraw);
+  extern __shared__ __align__(128) unsigned char smraw[];
+  // with RM the tile of the bulk copies starts on a 128-byte boundary (the launch adds 128 bytes)
+  C* sm = reinterpret_cast<C*>(RM ? smraw + ((128u - (smem_addr(smraw) & 127u)) & 127u) : smraw);
+  __shared__ __align__(8) unsigned long long rm_bar;
   __shared__ double red[32];
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
   const int LX = 2 * a.nx;
@@ -425,7 +510,11 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
     }
   }
   if constexpr (MODE == P2_RS) {
-    load_col(v, T0, t, TT);
+    if constexpr (RM) {
+      if (!gather_col_rm<LY, ROWS>(v, sm, tin, &rm_bar, kx, b * a.cT * a.ny, a.ny, t, a.status)) return;
+    } else {
+      load_col(v, T0, t, TT);
+    }
     team_fft<LY, -1>(v, row, t, tw);
     if (a.spec_out && live) store_full(v, spec_out(0), t, TT);
     const C* h = H(KH);
@@ -560,7 +649,11 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
   } else if constexpr (MODE == P2_RS_BWD_S) {
     // U's column spectrum comes from the forward's saved spectra: one transform fewer and no
     // parked row (the products are formed as the saved values stream in)
-    load_col(v, T0, t, TT);
+    if constexpr (RM) {
+      if (!gather_col_rm<LY, ROWS>(v, sm, tin, &rm_bar, kx, b * a.cT * a.ny, a.ny, t, a.status)) return;
+    } else {
+      load_col(v, T0, t, TT);
+    }
     team_fft<LY, -1>(v, row, t, tw);
     if (a.want_dz) {
       const C* su = spec_in(0);

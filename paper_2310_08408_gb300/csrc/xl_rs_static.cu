@@ -8,6 +8,7 @@
 // The computation is the same as xl_rs_propagate (same kernels, same discrete definition), for
 // complex64 fields up to 256 x 256; the transfer spectrum is regenerated for every run of equal
 // consecutive distances instead of being cached.
+#include <cstring>
 #include <cmath>
 #include <mutex>
 
@@ -129,6 +130,9 @@ xl_status run_static(const float2* in, float2* out, int32_t batch, const xl_grid
   pa.cS = 0;
   pa.per_elem = 0;
   for (int i = 0; i < kP2Run; ++i) pa.hshift[i] = 0;
+  pa.status = nullptr;
+  CUtensorMap no_map;  // pass 2 reads its columns directly here
+  std::memset(&no_map, 0, sizeof(no_map));
 
   // every launch below needs less than 48 KB of shared memory (transform lengths <= 512)
   constexpr int RA = rows_transp<LX, 8>(), R3 = rows_p3<LX, 8>(), RB = rows_cols<LY>(),
@@ -152,7 +156,7 @@ xl_status run_static(const float2* in, float2* out, int32_t batch, const xl_grid
         in + b * plane, T, nx, ny, 1, 1, twx);
     XL_CUDA_TRY(cudaGetLastError());
     k_rs_pass2<float, LY, P2_RS><<<dim3((LX + RC - 1) / RC, 1), RC * (LY / 16), smP2, s>>>(
-        T, nullptr, Hq, nullptr, pa, twy);
+        T, nullptr, Hq, nullptr, pa, twy, no_map);
     XL_CUDA_TRY(cudaGetLastError());
     k_rs_pass3<float, LX><<<dim3((ny + R3 - 1) / R3, 1), R3 * (LX / 16), sm3, s>>>(
         T, out + b * plane, nx, ny, 1, 1, twx, DzReduce{nullptr, 0, nullptr});

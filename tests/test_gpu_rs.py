@@ -282,3 +282,33 @@ def test_pass3_bulk_copy_gather_matches_async_gather(vectorial, monkeypatch):
     ref = oracle.vrs(u[0].astype(np.complex128), 0.5, 0.5, LAM, zs[0]) if vectorial else \
         oracle.rs_conv(u[0].astype(np.complex128), 0.5, 0.5, LAM, zs[0])
     assert rel(to_np(tma[0])[0], ref) < TOL_C64
+
+
+def test_row_major_intermediate_matches_transposed(monkeypatch):
+    """The scalar forward and the saved-spectrum adjoint of complex64 grids store the row
+    transforms row-major and gather pass 2's columns with bulk tensor copies; the transposing
+    pass 1 (XL_RS_RM=0) gives bit-identical fields, saved spectra and distance gradients."""
+    import torch
+    xl = lib()
+    g = inputs.Grid.centred(128, 0.5)
+    zs = [50.0, 20.0, 20.0, 75.0]
+    B = len(zs)
+    u = np.stack([inputs.gaussian_random_phase(g, 15.0, 900 + i) for i in range(B)]).astype(np.complex64)
+    G = inputs.random_unit(910, (B, 128, 128)).astype(np.complex64)
+    U, Gd = to_dev(u, np.complex64), to_dev(G, np.complex64)
+
+    def run():
+        S = xl.save_buffer(U)
+        out = xl.rs_propagate(U, g, LAM, zs, saved=S)
+        gi, gz = xl.rs_propagate_backward(Gd, None, g, LAM, zs, want_field=True, want_dz=True, saved=S)
+        torch.cuda.synchronize()
+        return out, S, gi, gz
+
+    rm = run()
+    monkeypatch.setenv("XL_RS_RM", "0")
+    tr = run()
+    for a, b in zip(rm, tr):
+        assert torch.equal(a, b)
+    xl.device_status()
+    for i, z in enumerate(zs):
+        assert rel(to_np(rm[0])[i], oracle.rs_conv(u[i].astype(np.complex128), 0.5, 0.5, LAM, z)) < TOL_C64
