@@ -31,6 +31,8 @@
  *     2048): the row passes run over a chunk per launch, pass 2 over up to 32 elements per launch.
  *   - XL_P3_TMA=0: RS pass 3 gathers its rows with per-thread asynchronous copies instead of
  *     tiled bulk tensor copies (complex64). Results are bit-identical either way.
+ *   - XL_RS_RM=0: the complex64 scalar forward and saved-spectrum adjoint keep the transposing
+ *     pass 1 instead of the row-major intermediate gathered by pass 2. Bit-identical either way.
  *
  * Errors
  *   - Argument checks happen on the host before any launch and return XL_ERR_ARG or
