@@ -33,6 +33,9 @@
  *     tiled bulk tensor copies (complex64). Results are bit-identical either way.
  *   - XL_RS_RM=0: the complex64 scalar forward and saved-spectrum adjoint keep the transposing
  *     pass 1 instead of the row-major intermediate gathered by pass 2. Bit-identical either way.
+ *   - XL_CZT_RM=0: the complex64 scalar CZT forward (window lengths 256..8192, even window
+ *     width) keeps the transposing x pass instead of the row-major intermediate whose columns
+ *     the y pass gathers with tiled bulk tensor copies. Bit-identical either way.
  *
  * Errors
  *   - Argument checks happen on the host before any launch and return XL_ERR_ARG or

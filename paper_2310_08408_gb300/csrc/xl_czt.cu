@@ -3,6 +3,7 @@
 // onto an arbitrarily selected and sampled region of interest.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -124,6 +125,10 @@ xl_status run(bool adjoint, const void* in, void* out, int32_t batch, bool vec, 
   d.x0 = g->x0; d.dx = g->dx; d.y0 = g->y0; d.dy = g->dy;
   d.xo0 = w->xo0; d.dxo = w->dxo; d.yo0 = w->yo0; d.dyo = w->dyo;
   const int cin = in_planes, cwin = vec ? 3 : 1;
+  // scalar complex64 forward: row-major intermediate (XL_CZT_RM=0 keeps the transposed one)
+  const char* rm_env = getenv("XL_CZT_RM");
+  const bool rm = !adjoint && !vec && sizeof(T) == 4 && ta.Lx >= 256 && ta.Ly >= 256 &&
+                  ta.Lx <= 8192 && ta.Ly <= 8192 && w->mx % 2 == 0 && !(rm_env && rm_env[0] == '0');
   d.in_planes = in_planes;
   d.adjoint = adjoint ? 1 : 0;
   for (int32_t b0 = 0; b0 < batch;) {
@@ -149,8 +154,12 @@ xl_status run(bool adjoint, const void* in, void* out, int32_t batch, bool vec, 
     if (!adjoint) {
       const char* src = (const char*)in + (size_t)b0 * cin * in_plane * cs;
       char* dst = (char*)out + (size_t)b0 * cwin * win_plane * cs;
-      XL_TRY(czt_pass<T>(CZT_FWD_X, vec, ta.Lx, src, Tb, d, ax, nb, s));
-      XL_TRY(czt_pass<T>(CZT_FWD_Y, vec, ta.Ly, Tb, dst, d, ay, nb, s));
+      if (rm) {  // the x pass stores row-major, the y pass gathers columns by bulk tensor copies
+        XL_TRY(czt_fwd_rm<T>(ta.Lx, ta.Ly, src, Tb, dst, d, ax, ay, nb, s));
+      } else {
+        XL_TRY(czt_pass<T>(CZT_FWD_X, vec, ta.Lx, src, Tb, d, ax, nb, s));
+        XL_TRY(czt_pass<T>(CZT_FWD_Y, vec, ta.Ly, Tb, dst, d, ay, nb, s));
+      }
     } else {
       const char* src = (const char*)in + (size_t)b0 * cwin * win_plane * cs;
       char* dst = (char*)out + (size_t)b0 * cin * in_plane * cs;

@@ -117,7 +117,71 @@ xl_status bhat(int L, cplx<T>* rows, int64_t stride, cudaStream_t s) {
   return fail(XL_ERR_UNSUPPORTED, "czt: unsupported transform length");
 }
 
+// Scalar complex64 forward with the row-major intermediate: x pass and y pass of one length each.
+template <int L>
+xl_status rm_x_L(const void* src, void* Tr, const CztDims& d, const AxisRun<float2>& ax, int nb,
+                 cudaStream_t s) {
+  constexpr int ROWS = czt_rm_rows<L>();
+  const size_t sm = (size_t)ROWS * srow(L) * sizeof(float2);
+  const void* tw;
+  XL_TRY(twiddles(L, XL_C64, &tw));
+  XL_TRY(smem_attr((const void*)k_czt_fwd_x_rm<L>, sm));
+  LaunchScope ls("czt_fwd_x<" + std::to_string(L) + ">", s);
+  k_czt_fwd_x_rm<L><<<dim3((d.ny + ROWS - 1) / ROWS, nb), ROWS * (L / 16), sm, s>>>(
+      (const float2*)src, (float2*)Tr, d, ax, (const float2*)tw);
+  XL_CUDA_TRY(cudaGetLastError());
+  return XL_OK;
+}
+
+template <int L>
+xl_status rm_y_L(const void* Tr, void* dst, const CztDims& d, const AxisRun<float2>& ay, int nb,
+                 cudaStream_t s) {
+  constexpr int ROWS = czt_rows<L, 8, false, 0>();
+  constexpr int W = ROWS >= 2 ? ROWS : 2;
+  const size_t sm = (size_t)ROWS * tpitch(L, 8, ROWS) * sizeof(float2) + 128;  // + alignment slack
+  const void* tw;
+  XL_TRY(twiddles(L, XL_C64, &tw));
+  XL_TRY(smem_attr((const void*)k_czt_fwd_y_rm<L, ROWS>, sm));
+  alignas(64) unsigned char map[128];
+  XL_TRY(tensor_map_2d_u64(Tr, (uint64_t)d.mx, (uint64_t)nb * d.ny, (uint64_t)d.mx * sizeof(float2), W,
+                           d.ny < 256 ? d.ny : 256, map));
+  unsigned int* status = nullptr;
+  XL_TRY(status_word(&status));
+  LaunchScope ls("czt_fwd_y<" + std::to_string(L) + ">", s);
+  k_czt_fwd_y_rm<L, ROWS><<<dim3((d.mx + ROWS - 1) / ROWS, nb), ROWS * (L / 16), sm, s>>>(
+      *reinterpret_cast<const CUtensorMap*>(map), (float2*)dst, d, ay, (const float2*)tw, status);
+  XL_CUDA_TRY(cudaGetLastError());
+  return XL_OK;
+}
+
+template <typename T>
+xl_status fwd_rm(int Lx, int Ly, const void* src, void* Tr, void* dst, const CztDims& d,
+                 const AxisRun<cplx<T>>& ax, const AxisRun<cplx<T>>& ay, int nb, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    xl_status st = XL_ERR_UNSUPPORTED;
+#define RX(LL) case LL: st = rm_x_L<LL>(src, Tr, d, ax, nb, s); break;
+#define RY(LL) case LL: st = rm_y_L<LL>(Tr, dst, d, ay, nb, s); break;
+    switch (Lx) { RX(256) RX(512) RX(1024) RX(2048) RX(4096) RX(8192) }
+    if (st != XL_OK) return st == XL_ERR_UNSUPPORTED ? fail(st, "czt rm: unsupported length") : st;
+    st = XL_ERR_UNSUPPORTED;
+    switch (Ly) { RY(256) RY(512) RY(1024) RY(2048) RY(4096) RY(8192) }
+#undef RX
+#undef RY
+    if (st != XL_OK) return st == XL_ERR_UNSUPPORTED ? fail(st, "czt rm: unsupported length") : st;
+    return XL_OK;
+  } else {
+    return fail(XL_ERR_UNSUPPORTED, "czt rm: complex64 only");
+  }
+}
+
 }  // namespace
+
+template <>
+xl_status czt_fwd_rm<XL_REAL>(int Lx, int Ly, const void* src, void* Tr, void* dst, const CztDims& d,
+                              const AxisRun<cplx<XL_REAL>>& ax, const AxisRun<cplx<XL_REAL>>& ay,
+                              int nb, cudaStream_t s) {
+  return fwd_rm<XL_REAL>(Lx, Ly, src, Tr, dst, d, ax, ay, nb, s);
+}
 
 template <>
 xl_status czt_pass<XL_REAL>(int which, bool vec, int L, const void* src, void* dst,

@@ -26,6 +26,8 @@
 // Vectorial adjoint: g_Ex = C^H(Gx - (X/z) Gz) + (x/z) C^H(Gz), g_Ey likewise with y.
 #pragma once
 
+#include <cuda.h>
+
 #include "xl_fft.cuh"
 
 namespace xl {
@@ -290,6 +292,116 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
     store_transposed<L, ROWS>(v, sm, team, t, d.my, out + ((int64_t)b * cT + c) * oplane, d.mx, p0,
                               d.mx);
   }
+}
+
+// Scalar forward of complex64 with a row-major intermediate Tr[ny][mx] (the x pass stores each
+// row's window values as they stand; the y pass gathers its columns with tiled bulk tensor
+// copies). Teams per block of the x pass: one 256-thread team at L = 4096.
+template <int L> __host__ __device__ constexpr int czt_rm_rows() { return (4096 / L) > 1 ? 4096 / L : 1; }
+
+template <int L>
+__global__ void __launch_bounds__(czt_rm_rows<L>() * (L / 16),
+                                  (1024 / (czt_rm_rows<L>() * (L / 16))) > 0 ? 1024 / (czt_rm_rows<L>() * (L / 16)) : 1)
+k_czt_fwd_x_rm(const float2* __restrict__ in, float2* __restrict__ Tr, CztDims d,
+               AxisRun<float2> ax_run, const float2* __restrict__ tw) {
+  constexpr int ROWS = czt_rm_rows<L>();
+  constexpr int TT = L / 16;
+  static_assert(team_barriers_fit<L>(ROWS * TT), "too many teams for the named barriers");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  const int team = threadIdx.x / TT, t = threadIdx.x % TT;
+  const int b = blockIdx.y;
+  const Axis<float2> ax = ax_run.at(b);
+  const int n_raw = blockIdx.x * ROWS + team;
+  const bool live = n_raw < d.ny;
+  const int n = live ? n_raw : d.ny - 1;
+  const int64_t plane = (int64_t)d.nx * d.ny;
+  const float2* s0 = in + ((int64_t)b * d.in_planes) * plane + (int64_t)n * d.nx;
+  float2 v[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int m = t + q * TT;
+    v[q] = q * TT < d.nx && m < d.nx ? cmul(s0[m], __ldg(ax.pre + m)) : make_float2(0.f, 0.f);
+  }
+  chirp_conv<L>(v, sm + team * srow(L), t, tw, ax.bhat, d.adjoint);
+  if (live) {
+    float2* dst = Tr + ((int64_t)b * d.ny + n) * d.mx;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int p = t + q * TT;
+      if (q * TT < d.mx && p < d.mx) dst[p] = cmul(v[q], __ldg(ax.post + p));
+    }
+  }
+}
+
+// The y pass of that forward: ROWS teams take window columns p0..p0+ROWS-1; one thread issues
+// ceil(ny / box) tiled bulk tensor copies of W x box elements (W = max(ROWS, 2) consecutive p,
+// box <= 256 rows of n) from Tr, completing on one shared-memory barrier (bounded wait: bit 1 of
+// `status` and the block ends); each team reads its column from the tile, which then gives its
+// memory back to the transform rows; the window values are stored transposed as before.
+template <int L, int ROWS>
+__global__ void __launch_bounds__(ROWS * (L / 16), (1024 / (ROWS * (L / 16))) > 0 ? 1024 / (ROWS * (L / 16)) : 1)
+k_czt_fwd_y_rm(const __grid_constant__ CUtensorMap tin, float2* __restrict__ out, CztDims d,
+               AxisRun<float2> ay_run, const float2* __restrict__ tw, unsigned* __restrict__ status) {
+  constexpr int TT = L / 16;
+  constexpr int W = ROWS >= 2 ? ROWS : 2;
+  constexpr int P = tpitch(L, sizeof(float2), ROWS);
+  static_assert(ROWS >= 2 && W * L <= ROWS * P, "the gathered columns fit the transform rows");
+  static_assert(team_barriers_fit<L>(ROWS * TT), "too many teams for the named barriers");
+  extern __shared__ __align__(128) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw + ((128u - (smem_addr(smraw) & 127u)) & 127u));
+  __shared__ __align__(8) unsigned long long bar;
+  const int team = threadIdx.x / TT, t = threadIdx.x % TT;
+  const int b = blockIdx.y;
+  const Axis<float2> ay = ay_run.at(b);
+  const int p0 = blockIdx.x * ROWS;
+  const int pw0 = p0 & ~(W - 1);
+  const int p = min(p0 + team, d.mx - 1);
+  const int boxr = d.ny < 256 ? d.ny : 256;
+  const int ncopy = (d.ny + boxr - 1) / boxr;
+  const unsigned ba = smem_addr(&bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(ba) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(ba),
+                 "r"((unsigned)(ncopy * boxr * W * sizeof(float2)))
+                 : "memory");
+#pragma unroll 1
+    for (int c = 0; c < ncopy; ++c)
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::
+              "r"(smem_addr(sm + c * boxr * W)),
+          "l"(reinterpret_cast<uint64_t>(&tin)), "r"(pw0), "r"(b * d.ny + c * boxr), "r"(ba)
+          : "memory");
+  }
+  unsigned done = 0;
+  for (unsigned it = 0; !done && it < kWaitLimit; ++it)
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(ba)
+        : "memory");
+  if (__syncthreads_or(!done)) {
+    if (threadIdx.x == 0) atomicOr(status, 2u);
+    return;
+  }
+  float2 v[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int n = t + q * TT;
+    v[q] = q * TT < d.ny && n < d.ny ? cmul(sm[n * W + (p - pw0)], __ldg(ay.pre + n)) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();  // every team has its column before the transforms reuse the tile's memory
+  chirp_conv<L>(v, sm + team * P, t, tw, ay.bhat, d.adjoint);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int qq = t + q * TT;
+    if (q * TT < d.my && qq < d.my) v[q] = cmul(v[q], __ldg(ay.post + qq));
+  }
+  store_transposed<L, ROWS>(v, sm, team, t, d.my, out + (int64_t)b * d.mx * d.my, d.mx, p0, d.mx);
 }
 
 // Adjoint y pass: columns p of the window gradient planes [my][mx] -> T planes [mx][ny] (rows).

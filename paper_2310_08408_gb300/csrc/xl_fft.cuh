@@ -311,6 +311,13 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
                  : "memory");
 }
 
+// Shared-memory address of a generic pointer (for bulk copies and barriers).
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+// Iteration bound of the waits on bulk-copy barriers (a wait that runs out reports an error).
+constexpr unsigned kWaitLimit = 1u << 26;
+
 // Thread-private 16-element stash (element q of thread t is row element t + q L/16), in a shared
 // memory row or in registers.
 template <typename C, int TT, bool SMEM> struct Stash {

@@ -214,11 +214,6 @@ k_rs_pass3(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, int nx, in
 // serves as the two transform rows. Two rows per block, as the asynchronous-copy gather.
 // A wait that does not complete within a bound sets bit 1 of `status` and ends the block.
 constexpr int kP3TmaRows = 2;
-constexpr unsigned kWaitLimit = 1u << 26;
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
 
 template <int LX>
 __global__ void __launch_bounds__(kP3TmaRows * (LX / 16), min_blocks_rows<kP3TmaRows * (LX / 16), 8>())
