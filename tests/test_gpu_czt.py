@@ -139,6 +139,7 @@ def test_mixed_distance_batch_one_launch(vectorial):
     (200, 150, 0.5, 120, 90, 40.0, 30.0, 400.0),    # one column tile of 150 rows per copy
     (180, 300, 0.5, 96, 100, 30.0, 40.0, 600.0),    # 300 rows: two copies, the second ragged
     (300, 260, 0.7, 702, 40, 400.0, 20.0, 900.0),   # wide window: several column blocks
+    (160, 700, 0.5, 64, 400, 30.0, 300.0, 800.0),   # y length 2048: three copies, the last ragged
 ])
 def test_row_major_forward_matches_transposed(case, monkeypatch):
     """The scalar complex64 forward stores the x transforms row-major and gathers the y pass's
