@@ -120,3 +120,29 @@ def test_batch_256_mixed_grids_sampled_setups():
         errs = [abs(a - r) / abs(r) for a, r in zip(gs, (gr["theta"], gr["z1"], gr["z2"]))]
         assert max(errs) < 1e-3, (s, errs)
     b.close()
+
+
+def test_maximum_transform_length_4096_grid_sampled():
+    """The largest transform length the kernels build (8192): RS forward and adjoint of a 4096^2
+    complex64 field (padded to 8192^2, both through the row-major intermediate) and CZT 4096^2 ->
+    1024^2 (Bluestein length 8192, row-major forward pair), at sampled pixels against the
+    oracle's direct sums."""
+    xl = lib()
+    g = inputs.Grid.centred(4096, 0.5)
+    lam, z = 0.6328, 3000.0
+    u = inputs.gaussian_random_phase(g, 400.0, 4242).astype(np.complex64)[None]
+    U = to_dev(u, np.complex64)
+    pts = _points(4096, 43, k=12)
+    u0 = u[0].astype(np.complex128)
+    out = to_np(xl.rs_propagate(U, g, lam, [z]))[0]
+    ref = oracle.rs_points(u0, g.dx, g.dy, lam, z, pts)
+    assert rel(np.array([out[q, p] for p, q in pts]), ref) < TOL_C64
+    gi = to_np(xl.rs_propagate_backward(U, None, g, lam, [z], want_field=True)[0])[0]
+    ref = oracle.rs_points(u0, g.dx, g.dy, lam, z, pts, oracle.K_H, True)
+    assert rel(np.array([gi[q, p] for p, q in pts]), ref) < TOL_C64
+    w = inputs.Window(1024, 1024, 0.25, 0.25, -128.0 + 0.3, -128.0 - 0.2)
+    c = to_np(xl.czt_propagate(U, g, w, lam, [z]))[0]
+    wp = _points(1024, 44, k=12)
+    ref = oracle.czt_points(u0, g.astuple(), w.astuple(), lam, z, wp)
+    assert rel(np.array([c[q, p] for p, q in wp]), ref) < TOL_C64
+    lib().device_status()
