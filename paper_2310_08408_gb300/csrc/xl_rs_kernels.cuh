@@ -372,13 +372,23 @@ __device__ __forceinline__ void store_full(const C (&v)[16], C* __restrict__ dst
 // completing on one shared-memory barrier; each team reads its kx from the tile, which then
 // gives its memory back to the transform rows. Returns false (every thread of the block) when the
 // bounded wait gave up; bit 1 of `status` is set.
+// Column group of a pass-2 block. With PAIR, groups run in the order 0, n-1, 1, n-2, 2, ...: the
+// columns kx and LX - kx read the same spectrum rows (the quadrant's mirror), so the second read
+// finds them in L2. It pays in the modes that read several spectra (measured: the saved-spectrum
+// adjoint 1.47 -> 1.44 ms a step; the forward, one spectrum, 1.29 -> 1.31 ms: launch order there).
+template <bool PAIR> __device__ __forceinline__ int p2_group() {
+  if constexpr (!PAIR) return (int)blockIdx.x;
+  const int ng = (int)gridDim.x, i = (int)blockIdx.x;
+  return (i & 1) ? ng - (i + 1) / 2 : i / 2;
+}
+
 template <int LY, int ROWS>
 __device__ __forceinline__ bool gather_col_rm(float2 (&v)[16], float2* tile, const CUtensorMap& map,
-                                              unsigned long long* bar, int kx, int row0, int ny,
-                                              int t, unsigned* status) {
+                                              unsigned long long* bar, int kx, int gx, int row0,
+                                              int ny, int t, unsigned* status) {
   constexpr int TT = LY / 16;
   constexpr int W = ROWS >= 2 ? ROWS : 2;
-  const int kx0 = (int)(blockIdx.x * ROWS) & ~(W - 1);
+  const int kx0 = (gx * ROWS) & ~(W - 1);  // first column of the block's group gx
   const int boxr = ny < 256 ? ny : 256;
   const int ncopy = ny / boxr;
   const unsigned ba = smem_addr(bar);
@@ -463,7 +473,9 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
   __shared__ double red[32];
   const int team = threadIdx.x / TT, t = threadIdx.x % TT;
   const int LX = 2 * a.nx;
-  const int kx_raw = blockIdx.x * ROWS + team;
+  constexpr bool PAIR = MODE != P2_RS;
+  const int gx = p2_group<PAIR>();
+  const int kx_raw = gx * ROWS + team;
   const bool live = kx_raw < LX;
   const int kx = live ? kx_raw : LX - 1;  // dead teams run the same code on a valid row, no stores
   const int b = blockIdx.y;
@@ -506,7 +518,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
   }
   if constexpr (MODE == P2_RS) {
     if constexpr (RM) {
-      if (!gather_col_rm<LY, ROWS>(v, sm, tin, &rm_bar, kx, b * a.cT * a.ny, a.ny, t, a.status)) return;
+      if (!gather_col_rm<LY, ROWS>(v, sm, tin, &rm_bar, kx, gx, b * a.cT * a.ny, a.ny, t, a.status)) return;
     } else {
       load_col(v, T0, t, TT);
     }
@@ -645,7 +657,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
     // U's column spectrum comes from the forward's saved spectra: one transform fewer and no
     // parked row (the products are formed as the saved values stream in)
     if constexpr (RM) {
-      if (!gather_col_rm<LY, ROWS>(v, sm, tin, &rm_bar, kx, b * a.cT * a.ny, a.ny, t, a.status)) return;
+      if (!gather_col_rm<LY, ROWS>(v, sm, tin, &rm_bar, kx, gx, b * a.cT * a.ny, a.ny, t, a.status)) return;
     } else {
       load_col(v, T0, t, TT);
     }
@@ -714,7 +726,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
                 MODE == P2_VRS_BWD_S) {
     if (a.want_dz) {
       double s = block_sum(live ? dz : 0.0, red);
-      if (threadIdx.x == 0) dz_part[(int64_t)b * gridDim.x + blockIdx.x] = s;
+      if (threadIdx.x == 0) dz_part[(int64_t)b * gridDim.x + p2_group<PAIR>()] = s;
     }
   }
 }
