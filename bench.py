@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--no-next", action="store_true", help="skip the angular-spectrum CZT and "
                    "beam-splitter measurements")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--e2e-eager", action="store_true",
+                   help="end-to-end steps as eager launches instead of one CUDA graph replay")
     p.add_argument("--no-table", action="store_true", help="skip the batched optical-table section")
     p.add_argument("--table-setups", type=int, default=256)
     p.add_argument("--table-steps", type=int, default=4)
@@ -566,7 +568,7 @@ def main():
         A_h = torch.empty(step.A.shape, dtype=step.A.dtype).pin_memory()
         C_h = torch.empty(step.C.shape, dtype=step.C.dtype).pin_memory()
         gz_h = torch.empty((B,), dtype=torch.float64).pin_memory()
-        ke = max(3, a.steps // 4)
+        ke = max(10, a.steps // 2)  # timed end-to-end steps (after a.warmup untimed ones)
         ch = min(a.e2e_chunk, B)
         pipe = HostPipeline([((N, N), U_pin.dtype)],
                             [((N, N), step.A.dtype), ((M, M), step.C.dtype), ((), torch.float64)],
@@ -589,10 +591,29 @@ def main():
             pipe.run([U_pin], [A_h, C_h, gz_h], chunk_step)
 
         e2e_step()
+        # the whole step (uploads, the chunks' propagations, downloads) as one CUDA graph, so that
+        # each timed step is one launch and host-side enqueue jitter cannot stall the pipeline;
+        # eager launches if the capture fails
+        launch, mode = e2e_step, "eager"
+        if not a.e2e_eager:
+            torch.cuda.synchronize()
+            try:
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph, capture_error_mode="thread_local"):
+                    e2e_step()
+                graph.replay()
+                torch.cuda.synchronize()
+                launch, mode = graph.replay, "cuda_graph"
+            except Exception as ex:  # noqa: BLE001 - reported in the JSON line
+                torch.cuda.synchronize()
+                mode = f"eager (graph capture failed: {type(ex).__name__})"
+        for _ in range(a.warmup):
+            launch()
+        torch.cuda.synchronize()
         barrier()
         e0.record(stream)
         for _ in range(ke):
-            e2e_step()
+            launch()
         e1.record(stream)
         barrier()
         ems = e0.elapsed_time(e1)
@@ -610,7 +631,7 @@ def main():
         e2e = {"value": replicas.whole_job_rate(step.props, world, ke, ems), "unit": "propagations/s",
                "h2d_bytes_per_step": int(U_pin.numel() * 8),
                "d2h_bytes_per_step": int(A_h.numel() * 8 + C_h.numel() * 8 + gz_h.numel() * 8),
-               "ms_per_step": ems / ke, "host_link": link}
+               "ms_per_step": ems / ke, "host_link": link, "launch": mode, "chunk": ch, "steps": ke}
 
     nxt = None
     if not a.no_next:
