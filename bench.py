@@ -607,6 +607,7 @@ def main():
             except Exception as ex:  # noqa: BLE001 - reported in the JSON line
                 torch.cuda.synchronize()
                 mode = f"eager (graph capture failed: {type(ex).__name__})"
+        ck_e2e = Clocks(local)  # clocks of the end-to-end region, reported with it
         for _ in range(a.warmup):
             launch()
         torch.cuda.synchronize()
@@ -616,6 +617,7 @@ def main():
             launch()
         e1.record(stream)
         barrier()
+        e2e_clocks = ck_e2e.stop()
         ems = e0.elapsed_time(e1)
         ems = replicas.max_over_ranks(ems, "cuda")
         # the host link alone on this machine: one whole-batch pinned upload and download
@@ -631,7 +633,7 @@ def main():
         e2e = {"value": replicas.whole_job_rate(step.props, world, ke, ems), "unit": "propagations/s",
                "h2d_bytes_per_step": int(U_pin.numel() * 8),
                "d2h_bytes_per_step": int(A_h.numel() * 8 + C_h.numel() * 8 + gz_h.numel() * 8),
-               "ms_per_step": ems / ke, "host_link": link, "launch": mode, "chunk": ch, "steps": ke}
+               "ms_per_step": ems / ke, "host_link": link, "launch": mode, "chunk": ch, "steps": ke, "clocks": e2e_clocks}
 
     nxt = None
     if not a.no_next:
