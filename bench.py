@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--no-next", action="store_true", help="skip the angular-spectrum CZT and "
                    "beam-splitter measurements")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--e2e-depth", type=int, default=3,
+                   help="staging slots of the end-to-end pipeline (3: a late download of chunk i does not stall chunk i + 2)")
     p.add_argument("--e2e-eager", action="store_true",
                    help="end-to-end steps as eager launches instead of one CUDA graph replay")
     p.add_argument("--no-table", action="store_true", help="skip the batched optical-table section")
@@ -572,7 +574,7 @@ def main():
         ch = min(a.e2e_chunk, B)
         pipe = HostPipeline([((N, N), U_pin.dtype)],
                             [((N, N), step.A.dtype), ((M, M), step.C.dtype), ((), torch.float64)],
-                            chunk=ch)
+                            chunk=ch, depth=a.e2e_depth)
         with torch.cuda.stream(pipe.compute_stream):
             S_c = xl.save_buffer(step.U[:ch])
         GA_c, GC_c = step.GA[:ch], step.GC[:ch]
@@ -633,7 +635,8 @@ def main():
         e2e = {"value": replicas.whole_job_rate(step.props, world, ke, ems), "unit": "propagations/s",
                "h2d_bytes_per_step": int(U_pin.numel() * 8),
                "d2h_bytes_per_step": int(A_h.numel() * 8 + C_h.numel() * 8 + gz_h.numel() * 8),
-               "ms_per_step": ems / ke, "host_link": link, "launch": mode, "chunk": ch, "steps": ke, "clocks": e2e_clocks}
+               "ms_per_step": ems / ke, "host_link": link, "launch": mode, "chunk": ch, "depth": a.e2e_depth, "steps": ke,
+               "clocks": e2e_clocks}
 
     nxt = None
     if not a.no_next:
