@@ -285,6 +285,54 @@ def table_section(xl, torch, setups: int, steps: int, seed: int):
 
 
 # ----------------------------------------------------------------------------- further rows
+def cufft_comparison(xl, torch, g, U_dev, zs, steps: int = 10):
+    """Timing comparison only (not the product path): the RS forward of the same batch through
+    torch.fft (cuFFT, complex64): zero-pad to 2N, 2D FFT, multiply by a 2N x 2N spectrum per
+    distance, inverse 2D FFT, crop. The spectra are placeholders (unit-modulus values), so only
+    the time is compared, against the library's xl.rs_propagate of the same fields, both after
+    warm-up, CUDA events on the current stream."""
+    B, n = U_dev.shape[0], U_dev.shape[-1]
+    L = 2 * n
+    dev = U_dev.device
+    dists = sorted(set(zs))
+    gen = torch.Generator(device="cpu").manual_seed(11)
+    H = torch.polar(torch.ones(len(dists), L, L), 6.283185307179586 * torch.rand(len(dists), L, L, generator=gen)
+                    ).to(torch.complex64).to(dev)
+    idx = [dists.index(z) for z in zs]
+    X = torch.zeros((B, L, L), dtype=torch.complex64, device=dev)
+    out = torch.empty_like(U_dev)
+
+    def cufft_step():
+        X.zero_()
+        X[:, :n, :n] = U_dev
+        F = torch.fft.fft2(X)
+        for i in range(B):
+            F[i].mul_(H[idx[i]])
+        out.copy_(torch.fft.ifft2(F)[:, :n, :n])
+
+    A = torch.empty_like(U_dev)
+    ours = lambda: xl.rs_propagate(U_dev, g, LAM, zs, out=A)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    for name, f in (("cufft_ms", cufft_step), ("xl_ms", ours)):
+        for _ in range(3):
+            f()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            f()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = e0.elapsed_time(e1) / steps
+    del X, H
+    torch.cuda.empty_cache()
+    return {"workload": f"RS forward, {B} x {n}^2 complex64 padded to {L}^2, z cycling {dists}",
+            "cufft_ms": res["cufft_ms"], "xl_ms": res["xl_ms"],
+            "xl_speedup": res["cufft_ms"] / res["xl_ms"],
+            "note": "torch.fft (cuFFT) pipeline with placeholder spectra: timing comparison only"}
+
+
 def next_rows_section(xl, torch, g, w, U_dev, zs, hbm_gbs: float, steps: int = 10):
     """Device throughput of the rows beyond the headline step, on the same 2048^2 inputs:
     the angular-spectrum CZT onto the 512^2 window (forward + adjoint with distance gradient)
@@ -641,6 +689,7 @@ def main():
     nxt = None
     if not a.no_next:
         nxt = next_rows_section(xl, torch, g, w, U_dev, zs, hbm)
+        nxt["cufft_comparison"] = cufft_comparison(xl, torch, g, U_dev, zs)
 
     table = None
     if not a.no_table:
