@@ -163,8 +163,9 @@ xl_status xl_rs_propagate_backward_saved(const void* g_out, const void* saved, v
 /* Scalar RS propagation that allocates nothing. The paper has no counterpart: this entry point
  * serves callers that cannot let a library allocate device memory (memory owned by another
  * runtime's allocator, hosts that reserve all device memory up front, sandboxes without the
- * allocation API). It computes exactly what xl_rs_propagate computes, for complex64 fields with
- * nx, ny powers of two in [32, 256]; larger grids return XL_ERR_UNSUPPORTED. Its scratch
+ * allocation API). It computes the discrete RS convolution of xl_rs_propagate, equal to it within
+ * rounding (not bit for bit: other kernel variants, see xl_rs_static.cu), for complex64 fields
+ * with nx, ny powers of two in [32, 256]; larger grids return XL_ERR_UNSUPPORTED. Its scratch
  * (twiddles, spectra, the transposed intermediate) is one fixed 2,136,320-byte static device array
  * that every GPU loading the library keeps until the process exits. No cudaMalloc / cudaFree is
  * called; the transfer spectrum is regenerated for every run of equal consecutive distances.
@@ -173,6 +174,8 @@ xl_status xl_rs_propagate_backward_saved(const void* g_out, const void* saved, v
  *    stream capture.
  *  - Every call uses the same array: calls that overlap on the GPU (different streams, or
  *    threads without ordering) race and corrupt each other's results. Order them.
+ *  - The set-up is kept for the life of the process: a cudaDeviceReset after the first call is
+ *    not supported (the array's contents are lost with the context).
  * u_in, u_out: [batch][ny][nx] complex64 device arrays (not aliasing); z: host [batch] (> 0). */
 xl_status xl_rs_propagate_static(const void* u_in, void* u_out, int32_t batch, const xl_grid* grid,
                                  double wavelength, const double* z, void* stream);
@@ -374,8 +377,10 @@ xl_status xl_softmin(const double* losses, int32_t batch, int32_t n_det, double 
 
 /* Synchronises `stream`, then returns and clears the device status: XL_ERR_NONFINITE if a loss
  * reduction produced a non-finite value since the last call, XL_ERR_TIMEOUT if a kernel gave up
- * waiting for a bulk tensor copy (a bounded wait; the kernel's outputs are then incomplete),
- * else XL_OK. */
+ * waiting for a bulk tensor copy (a bounded wait), else XL_OK. After XL_ERR_TIMEOUT every output
+ * of that launch and of every later launch is undefined, not only the rows that were skipped: a
+ * block that gave up may still have copies in flight into shared memory that a later block is
+ * given. */
 xl_status xl_device_status(void* stream);
 
 /* ---------------------------------------------------------------------------------------------

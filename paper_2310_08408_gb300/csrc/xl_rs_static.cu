@@ -5,9 +5,16 @@
 // output (twiddle tables, the kernel-row spectra, the transfer-spectrum quadrant and the
 // transposed intermediate) lives in one fixed static device array in this file.
 //
-// The computation is the same as xl_rs_propagate (same kernels, same discrete definition), for
-// complex64 fields up to 256 x 256; the transfer spectrum is regenerated for every run of equal
-// consecutive distances instead of being cached.
+// It computes the same discrete RS convolution as xl_rs_propagate, for complex64 fields up to
+// 256 x 256, equal to it within rounding but not bit for bit: the twiddle tables are filled here
+// on the device in double precision, the transfer spectrum comes from the generator variant
+// without a per-row cache (k_gen_pass_a<..., false>, which keeps each launch under 48 KB of
+// shared memory), and the passes are the transposing pass 1 and pass 3 with a pass 2 that reads
+// its columns directly (no tensor maps, which would have to be encoded per call), not the
+// row-major intermediate of the default complex64 path. The transfer spectrum is regenerated for
+// every run of equal consecutive distances instead of being cached. A device reset
+// (cudaDeviceReset) after the first call is not supported: the set-up below is done once per
+// device for the life of the process.
 #include <cstring>
 #include <cmath>
 #include <mutex>
