@@ -1,20 +1,28 @@
 #!/usr/bin/env python3
 """Throughput benchmark of the GB300 RS / CZT hot path (XLuminA, arXiv 2310.08408).
 
-Workload (rs2048): a batch of 16 complex64 fields on a 2048 x 2048 grid (pitch 0.5 um,
-lambda 0.633 um), each a Gaussian (w0 = 200 um) times a seeded uniform [0, 2 pi) phase; the
-distances cycle through z = 0.5, 2 and 10 mm; CZT maps onto a 512 x 512 window over the central
-64 um. Inputs are synthetic (the paper's propagation benchmark uses a Gaussian beam at 2048^2,
-Fig. 1b); all 16 inputs (537 MB) exceed the 126 MB L2, so no flush is needed between steps.
+Workload (rs2048): a batch of 16 complex64 source fields on a 2048 x 2048 grid (pitch 0.5 um,
+lambda 0.633 um), each a Gaussian (w0 = 200 um) times a seeded uniform [0, 2 pi) phase, shaped by
+an SLM phase mask per field (the trained parameters, starting flat); the distances cycle through
+z = 0.5, 2 and 10 mm; CZT maps onto a 512 x 512 window over the central 64 um. Inputs are
+synthetic (the paper's benchmarks use a Gaussian beam through a phase mask at 2048^2,
+Introduction and Methods, "Features and performance"); all 16 inputs (537 MB) and the step's
+intermediates exceed the 126 MB L2, so no flush is needed between steps.
 
-One step is one gradient evaluation of every field through both propagators:
-    A = RS(U, z),  C = CZT(U, z)                              (forward propagations)
-    L = S(|A|^2) + S(|C|^2)  (second-moment spot size of each plane)
-    dL/dU = RS^H(dL/dA) + CZT^H(dL/dC),  dL/dz from the dh/dz spectrum
-with U = SLM(phi) applied to the source, dL/dphi from the element adjoint and an Adam step on phi.
-Parts not yet present in the library are skipped and listed in the JSON ("step_parts").
-`value` = RS/CZT propagations per second (forward and adjoint, whole job), `grads_per_s` = field
-gradient evaluations per second.
+One step is one gradient evaluation of every field through both propagators and an Adam step
+on the masks, every stage a library call:
+    U = SLM(src, phi)                              xl_apply_elements
+    A = RS(U, z)  (input spectrum saved)           xl_rs_propagate_save
+    C = CZT(U, z) (distance-gradient sums saved)   xl_czt_propagate_save
+    L = S(|A|^2) + S(|C|^2)                        xl_intensity_loss (second-moment spot sizes)
+    gA, gC = dL/dA, dL/dC                          xl_intensity_loss_backward
+    gU, dL/dz = RS^H gA                            xl_rs_propagate_backward_saved
+    gU, dL/dz += CZT^H gC                          xl_czt_propagate_backward_saved (accumulate)
+    dL/dphi = SLM^H gU                             xl_apply_elements_backward
+    phi <- Adam(phi, dL/dphi)                      xl_step_advance, xl_adam_step
+(the distances are differentiated but not stepped: the propagation tables stay cached).
+`value` = RS/CZT propagations per second (four a field: RS, CZT and their adjoints; whole job),
+`grads_per_s` = gradient evaluations (fields) per second.
 
 `--impl reference` times the FP64 CPU oracle (the only reference this build has) on the host
 cores: each step is the same composition for ONE field of the batch.
@@ -23,6 +31,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import re
 import subprocess
@@ -38,7 +47,9 @@ LAM = 0.633
 ZS = (500.0, 2000.0, 10_000.0)
 N, PITCH, W0 = 2048, 0.5, 200.0
 M, WIN_W = 512, 64.0
+LR = 0.01
 E2E_CHUNK = 2  # fields per device pass of the end-to-end (host-staged) measurement
+MB = 1e6
 
 
 def parse():
@@ -56,8 +67,10 @@ def parse():
     p.add_argument("--plan", default=os.path.join(ROOT, "paper_2310_08408_gb300", "plans",
                                                   "gb300_c64.txt"),
                    help="launch plan file (xl_tune_load); empty: the built-in plan")
-    p.add_argument("--no-next", action="store_true", help="skip the angular-spectrum CZT and "
-                   "beam-splitter measurements")
+    p.add_argument("--no-next", action="store_true", help="skip the angular-spectrum CZT, "
+                   "beam-splitter and cuFFT-comparison measurements")
+    p.add_argument("--no-configs", action="store_true", help="skip the other workloads "
+                   "(complex128 RS 256^2, VRS / VCZT 2048^2)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--e2e-depth", type=int, default=3,
                    help="staging slots of the end-to-end pipeline (3: a late download of chunk i does not stall chunk i + 2)")
@@ -113,16 +126,53 @@ class Clocks:
 # ----------------------------------------------------------------------------- roofline
 def fft_flops(L: int) -> float:
     """Algorithmic flops of one complex FFT of length L (5 L log2 L convention)."""
-    return 5.0 * L * np.log2(L)
+    return 5.0 * L * math.log2(L)
 
 
-def kernel_model(name: str, dims: dict):
+def czt_plan(n: int, m: int):
+    """(L, S) of one CZT axis, the rule the library applies (xl_czt.cu czt_axis_plan): the grid
+    side in S segments, each a cyclic convolution of length L = 2^ceil(log2(ceil(n/S) + m - 1)),
+    the least (S + 1) L log2 L + 4 S L."""
+    best, cost, S = None, math.inf, 1
+    while S <= 64 and S <= n:
+        seg = -(-n // S)
+        if (S - 1) * seg < n:
+            L = 64
+            while L < seg + m - 1:
+                L *= 2
+            if L <= 8192:
+                c = (S + 1) * L * math.log2(L) + 4 * S * L
+                if c < cost * (1 - 1e-9):
+                    best, cost = (L, S), c
+        S *= 2
+    return best
+
+
+# Algorithmic bytes of one 2048^2 field (SURVEY-style per-unit figures: what the method must
+# read and write, complex64 = 8 B, float32 masks = 4 B): the four propagations and the rest of the
+# gradient step.
+UNIT_BYTES = {
+    "rs": 3 * N * N * 8 + (N + 1) ** 2 * 8,             # in + out + transfer-spectrum quadrant
+    "rs_adj_dz": 4 * N * N * 8 + 2 * (N + 1) ** 2 * 8,  # + the input and the dh/dz quadrant
+    "czt": N * N * 8 + M * M * 8,                       # in + window out (chirps ~0)
+    "czt_adj_dz": 2 * N * N * 8 + M * M * 8,            # + the input for dL/dz
+    "slm": N * N * (8 + 4 + 8),                         # src, phi in; U out
+    "loss": N * N * 8 + M * M * 8,                      # |A|^2, |C|^2 sums
+    "loss_bwd": 2 * (N * N + M * M) * 8,                # fields in, gradients out
+    "slm_bwd": N * N * (8 + 8 + 4 + 4),                 # gU, src, phi in; dL/dphi out
+    "adam": N * N * 4 * 7,                              # p, m, v, g in; p, m, v out
+}
+UNIT_FLOPS_RS = 2 * N * fft_flops(2 * N) + 2 * (2 * N) * (2 * fft_flops(2 * N) + 6 * 2 * N)
+
+
+def kernel_model(name: str, fields: float):
     """(algorithmic flops, algorithmic bytes) of ONE launch of kernel family `name` on the
-    benchmark workload (complex64). Bytes are the compulsory reads + writes of that pass;
-    flops count every FFT at its padded length plus 6 flops per complex multiply."""
-    n, m, cs = dims["n"], dims["m"], 8
+    benchmark workload (complex64) processing `fields` 2048^2 fields. Bytes are the compulsory
+    reads + writes of that pass; flops count every FFT at its padded length (5 L log2 L) plus 6
+    flops per complex multiply."""
+    n, m, cs = N, M, 8
     L = int(re.search(r"<(\d+)>", name).group(1)) if "<" in name else 0
-    nb = dims.get("per_launch", 1)
+    nb = fields
     if name.startswith("rs_pass1"):
         return nb * n * fft_flops(L), nb * (n * n + 2 * n * n) * cs
     if name.startswith("rs_pass3"):
@@ -135,10 +185,30 @@ def kernel_model(name: str, dims: dict):
         return nb * 2 * n * (2 * fft_flops(L) + 14 * L), nb * (8 * n * n + 2 * (n + 1) ** 2) * cs
     if name.startswith("rs_pass2_m2"):
         return nb * 2 * n * (3 * fft_flops(L) + 14 * L), nb * (6 * n * n + 2 * (n + 1) ** 2) * cs
-    if name.startswith("czt_fwd_x") or name.startswith("czt_adj_x"):
-        return nb * n * (2 * fft_flops(L) + 18 * L), nb * (n * n + n * m) * cs
-    if name.startswith("czt_fwd_y") or name.startswith("czt_adj_y"):
-        return nb * m * (2 * fft_flops(L) + 18 * L), nb * (n * m + m * m) * cs
+    if name.startswith("czt_") and L:
+        _, S = czt_plan(n, m)
+        dz = name.endswith("_dz")
+        rows = n if "_x" in name else m  # rows the pass transforms (x: grid rows; y: window columns)
+        fl = rows * ((S + 1) * fft_flops(L) + (S * (12 if dz else 6) + 12) * L)
+        if name.startswith("czt_fwd_x"):
+            by = n * n + n * m + (n * L if dz else 0)
+        elif name.startswith("czt_fwd_y"):
+            by = n * m + m * m + (m * L + m * m if dz else 0)
+        elif name.startswith("czt_adj_y"):
+            by = m * m + n * m + (m * m + n * m + m * L if dz else 0)
+        else:
+            by = n * m + n * n + (n * n + n * m + n * L if dz else 0)
+        return nb * fl, nb * by * cs
+    if name == "elements_fwd":
+        return None, nb * UNIT_BYTES["slm"]
+    if name == "elements_bwd":
+        return None, nb * UNIT_BYTES["slm_bwd"]
+    if name == "adam":
+        return None, nb * UNIT_BYTES["adam"]
+    if name == "loss_grad":  # the step runs it on A (2048^2) and on C (512^2)
+        return None, nb * (n * n + m * m) * 2 * cs / 2
+    if name.startswith("loss_sweep"):
+        return None, nb * (n * n + m * m) * cs / 2
     return None, None
 
 
@@ -178,42 +248,68 @@ def inputs_seed(rank: int) -> int:
     return rank_seed(inputs.SEED0 + 5, rank)
 
 
-def step_parts(xl):
-    have = {"rs": True, "czt": True}
-    for fn in ("apply_elements", "intensity_loss", "adam_step"):
-        have[fn] = hasattr(xl, fn)
-    return have
+# Library entry points one step calls, in order (the bench line's `step_parts`).
+STEP_PARTS = ["xl_step_advance", "xl_apply_elements (SLM)", "xl_rs_propagate_save",
+              "xl_czt_propagate_save", "xl_intensity_loss (A, C)",
+              "xl_intensity_loss_backward (A, C)", "xl_rs_propagate_backward_saved (+ dL/dz)",
+              "xl_czt_propagate_backward_saved (+ dL/dz, accumulate)",
+              "xl_apply_elements_backward (dL/dphi)", "xl_adam_step (phi)"]
 
 
 class GpuStep:
-    """The benchmark step on device-resident buffers (all through the C ABI)."""
+    """The benchmark step (module docstring) on device-resident buffers, all through the C ABI.
+    run(lo, n) steps fields lo..lo+n-1 (their masks and moments); src / zs override the sources
+    and distances of those fields (the end-to-end pipeline passes its staged chunk)."""
 
-    def __init__(self, xl, torch, g, w, U_dev, zs):
-        self.xl, self.torch, self.g, self.w, self.zs = xl, torch, g, w, zs
-        self.U = U_dev
-        B = U_dev.shape[0]
-        dev = U_dev.device
-        from paper_2310_08408_gb300 import inputs
-        # fixed seeded cotangents (the loss gradients until the loss kernels are present)
-        self.GA = torch.from_numpy(inputs.random_unit(7, (1, N, N)).astype(np.complex64)).to(dev).expand(B, N, N).contiguous()
-        self.GC = torch.from_numpy(inputs.random_unit(8, (1, M, M)).astype(np.complex64)).to(dev).expand(B, M, M).contiguous()
-        self.A = torch.empty_like(U_dev)
-        self.C = torch.empty((B, M, M), dtype=U_dev.dtype, device=dev)
-        # the forward RS keeps the row transforms of U for the adjoint's distance gradient
-        self.S = xl.save_buffer(U_dev)
+    def __init__(self, xl, torch, g, w, src_dev, zs, chunk=None):
+        self.xl, self.torch, self.g, self.w, self.zs = xl, torch, g, w, list(zs)
+        self.src = src_dev
+        B = src_dev.shape[0]
+        cap = chunk or B  # fields per run()
+        dev = src_dev.device
+        self.wg = (M, M, w.dxo, w.dyo, w.xo0, w.yo0)  # the camera grid of the window field
+        self.phi = torch.zeros((B, N, N), dtype=torch.float32, device=dev)
+        self.m, self.v = torch.zeros_like(self.phi), torch.zeros_like(self.phi)
+        self.t = torch.zeros(1, dtype=torch.int32, device=dev)
+        e = lambda *s: torch.empty(*s, dtype=torch.complex64, device=dev)
+        self.U, self.A, self.gA = (e((cap, N, N)) for _ in range(3))
+        self.C, self.gC = e((cap, M, M)), e((cap, M, M))
+        self.S_rs = xl.save_buffer(self.U)
+        self.S_czt = xl.czt_save_buffer(self.U, g, w)
         self.props = 4 * B
+        self.last = None
+
+    def run(self, lo=0, n=None, src=None, zs=None, advance=True):
+        xl, g, w = self.xl, self.g, self.w
+        n = self.src.shape[0] - lo if n is None else n
+        s = slice(lo, lo + n)
+        src = self.src[s] if src is None else src
+        zs = self.zs[s] if zs is None else zs
+        U, A, C, gA, gC = (b[:n] for b in (self.U, self.A, self.C, self.gA, self.gC))
+        q4 = lambda t: t.view(t.shape[0], 1, t.shape[-2], t.shape[-1])
+        slm = [dict(kind=xl.SLM, phi_x=self.phi[s])]
+        if advance:
+            xl.step_advance(self.t)
+        xl.apply_elements(q4(src), g, LAM, slm, out=q4(U))
+        xl.rs_propagate(U, g, LAM, zs, out=A, saved=self.S_rs[:n])
+        xl.czt_propagate(U, g, w, LAM, zs, out=C, saved=self.S_czt[:n])
+        lA, _ = xl.intensity_loss(q4(A), g, 1)
+        lC, _ = xl.intensity_loss(q4(C), self.wg, 1)
+        xl.intensity_loss_backward(q4(A), g, 1, out=q4(gA))
+        xl.intensity_loss_backward(q4(C), self.wg, 1, out=q4(gC))
+        # the spot-size losses are blind to a constant phase on A and C: phase-invariant dL/dz
+        gU_rs, gz_rs = xl.rs_propagate_backward(gA, None, g, LAM, zs, want_field=True, want_dz=True,
+                                                phase_invariant=True, saved=self.S_rs[:n])
+        xl.czt_propagate_backward(gC, g, w, LAM, zs, u_in=U, want_dz=True, phase_invariant=True,
+                                  saved=self.S_czt[:n], g_in=gU_rs, g_z=gz_rs, accumulate=True)
+        _, gpx, _, _ = xl.apply_elements_backward(q4(gU_rs), q4(src), g, LAM, slm, want_field=False,
+                                                  want_phi=True, want_params=False)
+        xl.adam_step(self.phi[s], self.m[s], self.v[s], gpx[0], LR, self.t)
+        self.last = (lA, lC, gz_rs, gpx[0])
+        return self.last
 
     def __call__(self):
-        xl = self.xl
-        xl.rs_propagate(self.U, self.g, LAM, self.zs, out=self.A, saved=self.S)
-        xl.czt_propagate(self.U, self.g, self.w, LAM, self.zs, out=self.C)
-        gc = xl.czt_propagate_backward(self.GC, self.g, self.w, LAM, self.zs)
-        ga, gz = xl.rs_propagate_backward(self.GA, None, self.g, LAM, self.zs, want_field=True,
-                                          want_dz=True, saved=self.S)
-        self.gA, self.gC = ga, gc
-        self.gz = gz
-        return self.A, self.C, self.gz
-
+        return self.run()
 
 # ----------------------------------------------------------------------------- optical tables
 TABLE_CFG = dict(wavelength=0.6328, extent=1024.0, w0=200.0, f=5000.0, cam_m=256, cam_width=64.0,
@@ -249,6 +345,15 @@ def table_section(xl, torch, setups: int, steps: int, seed: int):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    # launch gaps: the graph replay against the sum of its kernels' own durations (one eager step
+    # with every launch bracketed by CUDA events on its stream)
+    xl.profile_enable(True)
+    b.step(use_graph=False)
+    torch.cuda.synchronize()
+    prof = xl.profile_report()
+    xl.profile_enable(False)
+    k_ms = sum(v[1] for v in prof.values())
+    k_n = sum(v[0] for v in prof.values())
     b.close()
     # one table of 1024^2 (complex64, graph replay): the single-setup rate
     one = xl.Batch(TABLE_CFG, [1024], [[0.3, 20_000.0, 20_000.0]], seed)
@@ -281,6 +386,10 @@ def table_section(xl, torch, setups: int, steps: int, seed: int):
             "fp64_single_instance_grads_per_s": setups / (t64 / 1000.0),
             "fp64_ms_per_setup": f64,
             "table1024_grads_per_s": 1000.0 / ms1024,
+            "launches_per_step": k_n, "kernel_ms_per_step": k_ms,
+            "launch_gap_frac": max(0.0, 1.0 - k_ms / ms),
+            "launch_gap_note": "1 - (sum of the step's kernel durations, CUDA events per launch) / "
+                               "(graph replay time per step)",
             "speedup_vs_fp64_single_instance": t64 / ms}
 
 
@@ -386,35 +495,116 @@ def next_rows_section(xl, torch, g, w, U_dev, zs, hbm_gbs: float, steps: int = 1
                               "bytes": "fwd 2 fields read + 2 written; bwd 4 read + 2 written"}}
 
 
+# ----------------------------------------------------------------------------- other workloads
+def configs_section(xl, torch, steps: int = 10):
+    """The other workloads of the benchmark set, device-timed (CUDA events, after warm-up):
+    complex128 RS at 256^2 (z = 10 mm, one field) and the vectorial workload at 2048^2 (VRS and
+    VCZT onto 512^2, z = 5 mm, a radially polarised Gaussian and a random Jones field; forward with
+    saved sums, adjoint with dL/dz)."""
+    from paper_2310_08408_gb300 import inputs
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, k):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    out = {}
+    w1 = inputs.WORKLOADS["rs256_c128"]
+    g1 = inputs.Grid.centred(w1["n"], w1["pitch"])
+    x, y = g1.coords()
+    lens = np.exp(-1j * (2 * np.pi / w1["wavelength"]) * (x[None, :] ** 2 + y[:, None] ** 2) / (2 * w1["f"]))
+    u1 = (inputs.gaussian(g1, w1["w0"]) * lens * np.exp(1j * inputs.random_phase(g1, w1["seed"])))
+    U1 = torch.from_numpy(u1[None].astype(np.complex128)).cuda()
+    ms1 = timed(lambda: xl.rs_propagate(U1, g1, w1["wavelength"], [w1["z"]]), 4 * steps)
+    out["rs256_c128"] = {"workload": "RS 256^2 complex128, pitch 1 um, z = 10 mm, one field "
+                                     "(padded 512^2)", "propagations_per_s": 1000.0 / ms1,
+                         "ms_per_propagation": ms1}
+    w3 = inputs.WORKLOADS["vrs2048"]
+    g3 = inputs.Grid.centred(w3["n"], w3["pitch"])
+    win3 = inputs.Window.centred(w3["window_m"], w3["window_w"])
+    exy = np.stack([inputs.radial_gaussian(g3, w3["w0"]),
+                    inputs.random_jones(g3, w3["w0"], w3["seed"])]).astype(np.complex64)
+    E = torch.from_numpy(exy).cuda()
+    z3 = [w3["z"]] * 2
+    Sv = xl.save_buffer(E, 2)
+    Sc = xl.czt_save_buffer(E, g3, win3, vectorial=1)
+    Gv = torch.from_numpy(inputs.random_unit(31, (2, 3, N, N)).astype(np.complex64)).cuda()
+    Gc = torch.from_numpy(inputs.random_unit(32, (2, 3, M, M)).astype(np.complex64)).cuda()
+    lam3 = w3["wavelength"]
+
+    def vstep():
+        xl.vrs_propagate(E, g3, lam3, z3, saved=Sv)
+        xl.vrs_propagate_backward(Gv, None, g3, lam3, z3, want_field=True, want_dz=True, saved=Sv)
+        xl.czt_propagate(E, g3, win3, lam3, z3, vectorial=1, saved=Sc)
+        xl.czt_propagate_backward(Gc, g3, win3, lam3, z3, vectorial=1, u_in=E, want_dz=True, saved=Sc)
+
+    ms3 = timed(vstep, steps)
+    xl.profile_enable(True)
+    vstep()
+    torch.cuda.synchronize()
+    prof = xl.profile_report()
+    xl.profile_enable(False)
+    out["vrs2048"] = {"workload": "VRS and VCZT (512^2 over 64 um) at 2048^2 complex64, z = 5 mm, "
+                                  "2 fields (radial Gaussian, random Jones), forward with saved "
+                                  "sums + adjoint with dL/dz",
+                      "propagations_per_s": 4 * 2 / (ms3 / 1000.0), "ms_per_step": ms3,
+                      "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
+    del E, Sv, Sc, Gv, Gc
+    torch.cuda.empty_cache()
+    return out
+
+
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_step(U1, g, w, z, GA, GC):
-    """The step's composition for one field with the FP64 oracle."""
+def oracle_step(src, phi, g, w, z, adam_state):
+    """The step's composition for one field with the FP64 oracle (module docstring). Returns the
+    stepped mask, the Adam state and the step's losses, dL/dz and dL/dphi."""
     import oracle
-    u = U1.astype(np.complex128)
-    A = oracle.rs_conv(u, g.dx, g.dy, LAM, z)
-    C = oracle.czt_conv(u, g.astuple(), w.astuple(), LAM, z)
-    gc = oracle.czt_conv(GC, g.astuple(), w.astuple(), LAM, z, adjoint=True)
-    ga = oracle.rs_conv(GA, g.dx, g.dy, LAM, z, oracle.K_H, adjoint=True)
-    dz = np.real(np.vdot(GA, oracle.rs_conv(u, g.dx, g.dy, LAM, z, oracle.K_DH)))
-    return A, C, ga + gc, dz
+    wg = (M, M, w.dxo, w.dyo, w.xo0, w.yo0)
+    slm = [dict(kind=oracle.SLM, phi_x=phi)]
+    src = src.astype(np.complex128)[None]
+    U = oracle.apply_elements(src, g.astuple(), LAM, slm)[0]
+    A = oracle.rs_conv(U, g.dx, g.dy, LAM, z)
+    C = oracle.czt_conv(U, g.astuple(), w.astuple(), LAM, z)
+    lA, _ = oracle.intensity_loss(A[None], g.astuple(), 1)
+    lC, _ = oracle.intensity_loss(C[None], wg, 1)
+    gA = oracle.intensity_loss_backward(A[None], g.astuple(), 1)[0]
+    gC = oracle.intensity_loss_backward(C[None], wg, 1)[0]
+    gU = (oracle.rs_conv(gA, g.dx, g.dy, LAM, z, oracle.K_H, adjoint=True)
+          + oracle.czt_conv(gC, g.astuple(), w.astuple(), LAM, z, adjoint=True))
+    k = 2 * np.pi / LAM
+    # phase-invariant distance gradients (the losses ignore a constant phase on A and C)
+    dz = (np.real(np.vdot(gA, oracle.rs_conv(U, g.dx, g.dy, LAM, z, oracle.K_DH))) - np.real(1j * k * np.vdot(gA, A))
+          + np.real(np.vdot(gC, oracle.czt_conv(U, g.astuple(), w.astuple(), LAM, z, 3)))
+          - np.real(1j * k * np.vdot(gC, C)))
+    _, gpx, _, _ = oracle.apply_elements_backward(gU[None], src, g.astuple(), LAM, slm)
+    m, v, t = adam_state
+    t += 1
+    oracle.adam(phi, m, v, gpx[0], LR, t)  # in place
+    return phi, (m, v, t), {"loss_a": lA, "loss_c": lC, "dz": float(dz), "gphi": gpx[0]}
 
 
 def cpu_sample(U, g, w, zs, steps=1):
     import oracle
-    from paper_2310_08408_gb300 import inputs
-    GA = inputs.random_unit(7, (N, N)).astype(np.complex64).astype(np.complex128)
-    GC = inputs.random_unit(8, (M, M)).astype(np.complex64).astype(np.complex128)
     oracle.build()
+    phi = np.zeros((N, N))
+    st = (np.zeros((N, N)), np.zeros((N, N)), 0)
     t0 = time.perf_counter()
     for i in range(steps):
-        oracle_step(U[i % len(U)], g, w, zs[i % len(zs)], GA, GC)
+        phi, st, _ = oracle_step(U[i % len(U)], phi, g, w, zs[i % len(zs)], st)
     dt = time.perf_counter() - t0
-    # the oracle step holds 5 propagation-sized sums per field (4 propagations + the dz one);
-    # count the 4 propagations as in the GPU step
     return {"value": 4 * steps / dt, "unit": "propagations/s", "cores": oracle.get_threads(),
             "kind": "oracle",
-            "sample": f"{steps} of the {len(U)} fields of one step (RS, CZT, CZT^H, RS^H + dz at "
-                      f"2048^2 -> 512^2, FP64 C++ oracle), {dt:.1f} s"}
+            "sample": f"{steps} of the {len(U)} fields of one step (SLM, RS, CZT, losses, their "
+                      f"adjoints with dL/dz, SLM adjoint, Adam at 2048^2 -> 512^2, FP64 C++ "
+                      f"oracle), {dt:.1f} s"}
 
 
 # ----------------------------------------------------------------------------- main
@@ -423,9 +613,10 @@ METRIC = "RS/CZT propagations/s at 2048^2 (fwd + adjoint) and grads/s"
 
 def bench_config(batch: int, world: int) -> dict:
     """The workload both arms report (the reference arm times a bounded sample of it)."""
-    return {"workload": "rs2048: batch 16 x 2048^2 complex64, pitch 0.5 um, "
-                        "lambda 0.633 um, z cycling {0.5, 2, 10} mm; RS (4096^2 padded) "
-                        "and CZT to 512^2 over 64 um; forward + adjoint + dz",
+    return {"workload": "rs2048 gradient step: batch 16 x 2048^2 complex64 sources, pitch 0.5 um, "
+                        "lambda 0.633 um, z cycling {0.5, 2, 10} mm; SLM mask -> RS (4096^2 padded) "
+                        "and CZT to 512^2 over 64 um -> second-moment spot sizes -> adjoints with "
+                        "dL/dz -> mask gradient -> Adam on the masks",
             "global_batch": batch * world, "grid": N, "window": M,
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
             "l2": "inputs (537 MB per GPU) exceed L2; no flush"}
@@ -438,14 +629,13 @@ def run_reference(a):
     g, w, U, zs = make_inputs(0, 3)
     import oracle
     oracle.build()
-    from paper_2310_08408_gb300 import inputs
-    GA = inputs.random_unit(7, (N, N)).astype(np.complex64).astype(np.complex128)
-    GC = inputs.random_unit(8, (M, M)).astype(np.complex64).astype(np.complex128)
+    phi = np.zeros((N, N))
+    st = (np.zeros((N, N)), np.zeros((N, N)), 0)
     for i in range(a.warmup):
-        oracle_step(U[i % 3], g, w, zs[i % 3], GA, GC)
+        phi, st, _ = oracle_step(U[i % 3], phi, g, w, zs[i % 3], st)
     t0 = time.perf_counter()
     for i in range(a.steps):
-        oracle_step(U[i % 3], g, w, zs[i % 3], GA, GC)
+        phi, st, _ = oracle_step(U[i % 3], phi, g, w, zs[i % 3], st)
     dt = time.perf_counter() - t0
     v = 4 * a.steps / dt
     line = {
@@ -456,8 +646,9 @@ def run_reference(a):
         "config": bench_config(a.batch, 1),
         "cpu_baseline": {"value": v, "unit": "propagations/s", "cores": oracle.get_threads(),
                          "kind": "oracle",
-                         "sample": "one field of the batch per step (RS, CZT, CZT^H, RS^H + dz in "
-                                   "FP64 on the host cores), the fields and distances cycling"},
+                         "sample": "one field of the batch per step (SLM, RS, CZT, losses, their "
+                                   "adjoints with dL/dz, SLM adjoint, Adam in FP64 on the host "
+                                   "cores), the fields and distances cycling"},
         "e2e": {"value": v, "unit": "propagations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -526,24 +717,29 @@ def main():
     ms = replicas.max_over_ranks(ms, "cuda")
     value = replicas.whole_job_rate(step.props, world, a.steps, ms)
     grads = replicas.whole_job_rate(B, world, a.steps, ms)
+    ms_step = ms / a.steps
 
-    # batch 1 (one field per step, z = 0.5 mm): the latency-bound end of the same step
+    # batch 1 (one field per step) at each distance: the latency-bound end of the same step
     batch1 = None
     if B > 1:
-        s1 = GpuStep(xl, torch, g, w, U_dev[:1].contiguous(), zs[:1])
-        for _ in range(3):
-            s1()
-        barrier()
-        k1 = max(10, a.steps // 2)
-        e0.record(stream)
-        for _ in range(k1):
-            s1()
-        e1.record(stream)
-        barrier()
-        ms1 = e0.elapsed_time(e1) / k1
-        batch1 = {"value": s1.props / (ms1 / 1000.0), "unit": "propagations/s", "ms_per_step": ms1,
-                  "steps": k1, "note": "one 2048^2 field, z = 0.5 mm, same four propagations"}
-        del s1
+        batch1 = {}
+        for z in ZS:
+            i = zs.index(z)
+            s1 = GpuStep(xl, torch, g, w, U_dev[i:i + 1].contiguous(), [z])
+            for _ in range(3):
+                s1()
+            barrier()
+            k1 = max(10, a.steps // 2)
+            e0.record(stream)
+            for _ in range(k1):
+                s1()
+            e1.record(stream)
+            barrier()
+            ms1 = e0.elapsed_time(e1) / k1
+            batch1[f"z{z / 1000:g}mm"] = {"value": s1.props / (ms1 / 1000.0), "unit": "propagations/s",
+                                          "ms_per_step": ms1, "steps": k1}
+            del s1
+        torch.cuda.empty_cache()
 
     # per-kernel durations (CUDA events recorded by the library on its launch stream)
     xl.profile_enable(True)
@@ -553,97 +749,105 @@ def main():
     prof = xl.profile_report()
     xl.profile_enable(False)
     total = sum(v[1] for v in prof.values())
-    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
-    roof = None
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
         peaks = json.load(open(pk_path))
     hbm = peaks.get("hbm_gbs", 6800.0)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
+    clk = ck.get("sm_mhz") or 1900.0
+    fp32_peak = sms * 128 * 2 * clk * 1e6 / 1e12  # TFLOP/s, CUDA-core FMA rate at the sampled clock
+    traffic_pf = load_traffic()
+
     def fields_per_launch(name, cnt):
         """Fields one launch of kernel family `name` processed: the step makes two passes of
-        the row kernels (forward and adjoint RS) and one of every other kernel per field; the
-        library batches the fields of a call into fewer launches."""
-        per_step = (2 if name.startswith(("rs_pass1", "rs_pass3")) else 1) * B
-        return per_step / (cnt / 3)
+        the RS row kernels (forward and adjoint) and of the loss kernels (A and C), one of every
+        other kernel per field; the library batches the fields of a call into fewer launches."""
+        twice = name.startswith(("rs_pass1", "rs_pass3", "loss_"))
+        return (2 if twice else 1) * B / (cnt / 3)
 
-    if top is not None:
-        name, (cnt, tot) = top
-        avg_s = tot / cnt / 1000.0
-        flops, nbytes = kernel_model(name, {"n": N, "m": M,
-                                            "per_launch": fields_per_launch(name, cnt)})
-        clk = ck.get("sm_mhz") or 1900.0
-        fp32_peak = sms * 128 * 2 * clk * 1e6 / 1e12  # TFLOP/s, CUDA-core FMA rate at the sampled clock
-        per_field = load_traffic().get(name)
-        traffic = per_field * fields_per_launch(name, cnt) if per_field is not None else None
-        if flops is not None:
-            t_alu = flops / (fp32_peak * 1e12)
-            t_mem = nbytes / (hbm * 1e9)
-            if t_alu >= t_mem:
-                ach = flops / avg_s / 1e12
-                roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                        "frac": ach / fp32_peak, "traffic": traffic, "kernel": name,
-                        "share": tot / total if total else None,
-                        "peak_note": f"FP32 CUDA-core FMA rate: {sms} SMs x 128 lanes x 2 x "
-                                     f"{clk:.0f} MHz (median sampled clock)",
-                        "hbm_frac_of_measured": nbytes / avg_s / 1e9 / hbm}
-            else:
-                ach = nbytes / avg_s / 1e9
-                roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                        "frac": ach / hbm, "traffic": traffic, "kernel": name,
-                        "share": tot / total if total else None,
-                        "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     kernels = {}
-    clk_k = ck.get("sm_mhz") or 1900.0
-    fp32_k = sms * 128 * 2 * clk_k * 1e6 / 1e12
-    for k, (cnt_k, tot_k) in prof.items():
-        fpl = fields_per_launch(k, cnt_k)
-        ent = {"launches": cnt_k // 3, "ms_per_step": tot_k / 3, "fields_per_launch": fpl}
-        fl, nb = kernel_model(k, {"n": N, "m": M, "per_launch": fpl})
-        if fl is not None:  # each kernel against the roof its model says bounds it
-            avg = tot_k / cnt_k / 1000.0
-            alu = fl / (fp32_k * 1e12) >= nb / (hbm * 1e9)
-            ent["bound"] = "alu" if alu else "hbm"
-            ent["frac"] = (fl / avg / 1e12 / fp32_k) if alu else (nb / avg / 1e9 / hbm)
+    for k_, (cnt_k, tot_k) in prof.items():
+        fpl = fields_per_launch(k_, cnt_k)
+        ent = {"launches": cnt_k // 3, "ms_per_step": tot_k / 3, "share": tot_k / total if total else None}
+        fl, nb = kernel_model(k_, fpl)
+        avg = tot_k / cnt_k / 1000.0
+        if nb is not None:
+            ent["fields_per_launch"] = fpl
             ent["hbm_gbs"] = nb / avg / 1e9
+            ent["hbm_frac"] = nb / avg / 1e9 / hbm
+        if fl is not None:
             ent["tflops"] = fl / avg / 1e12
-        kernels[k] = ent
+            ent["alu_frac"] = fl / avg / 1e12 / fp32_peak
+            ent["bound"] = "alu" if fl / (fp32_peak * 1e12) >= nb / (hbm * 1e9) else "hbm"
+        elif nb is not None:
+            ent["bound"] = "hbm"
+        if k_ in traffic_pf and nb:
+            ent["traffic_ratio"] = traffic_pf[k_] * fpl / nb
+        kernels[k_] = ent
 
-    # end to end: pinned host input -> device, the step, results back to pinned host buffers,
-    # streamed in chunks of E2E_CHUNK fields so that the copies overlap the kernels
+    # roofline of the dominant kernel: its algorithmic flops against the FP32 CUDA-core peak (the
+    # RS / CZT units are ALU-bound at their algorithmic bytes), with the HBM fraction of the
+    # per-unit algorithmic bytes beside it
+    roof = None
+    if prof:
+        name, (cnt, tot) = max(prof.items(), key=lambda kv: kv[1][1])
+        avg_s = tot / cnt / 1000.0
+        fpl = fields_per_launch(name, cnt)
+        fl, nb = kernel_model(name, fpl)
+        unit = "rs" if name.startswith("rs_") else "czt"
+        unit_bytes = fpl * (UNIT_BYTES["rs_adj_dz"] if "m4" in name else UNIT_BYTES[unit])
+        traffic = traffic_pf[name] * fpl if name in traffic_pf else None
+        if fl is not None:
+            ach = fl / avg_s / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": ach / fp32_peak, "traffic": traffic, "kernel": name,
+                    "share": tot / total if total else None,
+                    "peak_note": f"FP32 CUDA-core FMA rate derived from unit counts and clock: {sms} SMs "
+                                 f"x 128 lanes x 2 x {clk:.0f} MHz (median sampled clock)",
+                    "alg_flops_per_launch": fl, "alg_bytes_per_launch": nb,
+                    "unit_bytes_per_launch": unit_bytes,
+                    "unit_hbm_frac": unit_bytes / avg_s / 1e9 / hbm,
+                    "unit_hbm_note": "the per-unit algorithmic bytes of the fields this launch "
+                                     "processes (whole propagation) / its duration / measured HBM",
+                    "traffic_ratio": (traffic / nb) if traffic else None}
+    step_bytes = B * sum(UNIT_BYTES.values())
+    e2e_alg = {"bytes_per_step": step_bytes, "frac_of_measured_hbm": step_bytes / (ms_step / 1000.0) / 1e9 / hbm,
+               "note": "the step's algorithmic bytes (every stage's compulsory reads and writes) / "
+                       "ms_per_step / measured HBM"}
+
+    # end to end: pinned host sources -> device, the step, the losses, distance gradients and
+    # mask gradients back to pinned host buffers, streamed in chunks of E2E_CHUNK fields so that
+    # the copies overlap the kernels
     e2e = None
     if not a.no_e2e:
         from paper_2310_08408_gb300.pipeline import HostPipeline
-        A_h = torch.empty(step.A.shape, dtype=step.A.dtype).pin_memory()
-        C_h = torch.empty(step.C.shape, dtype=step.C.dtype).pin_memory()
-        gz_h = torch.empty((B,), dtype=torch.float64).pin_memory()
-        ke = max(10, a.steps // 2)  # timed end-to-end steps (after a.warmup untimed ones)
         ch = min(a.e2e_chunk, B)
+        loss_h = torch.empty((B, 2), dtype=torch.float64).pin_memory()
+        gz_h = torch.empty((B,), dtype=torch.float64).pin_memory()
+        gphi_h = torch.empty((B, N, N), dtype=torch.float32).pin_memory()
+        ke = max(10, a.steps // 2)  # timed end-to-end steps (after a.warmup untimed ones)
         pipe = HostPipeline([((N, N), U_pin.dtype)],
-                            [((N, N), step.A.dtype), ((M, M), step.C.dtype), ((), torch.float64)],
+                            [((2,), torch.float64), ((), torch.float64), ((N, N), torch.float32)],
                             chunk=ch, depth=a.e2e_depth)
         with torch.cuda.stream(pipe.compute_stream):
-            S_c = xl.save_buffer(step.U[:ch])
-        GA_c, GC_c = step.GA[:ch], step.GC[:ch]
+            sc = GpuStep(xl, torch, g, w, U_dev, zs, chunk=ch)
 
         def chunk_step(ins, outs, lo, n):
-            (U,), (A, C, gz) = ins, outs
-            zc = zs[lo:lo + n]
-            xl.rs_propagate(U, g, LAM, zc, out=A, saved=S_c[:n])
-            xl.czt_propagate(U, g, w, LAM, zc, out=C)
-            xl.czt_propagate_backward(GC_c[:n], g, w, LAM, zc)
-            _, gzc = xl.rs_propagate_backward(GA_c[:n], None, g, LAM, zc, want_field=True,
-                                              want_dz=True, saved=S_c[:n])
+            (src,), (lo_, gz, gphi) = ins, outs
+            lA, lC, gzc, gpc = sc.run(lo, n, src=src, zs=zs[lo:lo + n], advance=(lo == 0))
+            lo_[:, 0].copy_(lA)
+            lo_[:, 1].copy_(lC)
             gz.copy_(gzc)
+            gphi.copy_(gpc)
 
         def e2e_step():
-            pipe.run([U_pin], [A_h, C_h, gz_h], chunk_step)
+            pipe.run([U_pin], [loss_h, gz_h, gphi_h], chunk_step)
 
         e2e_step()
-        # the whole step (uploads, the chunks' propagations, downloads) as one CUDA graph, so that
-        # each timed step is one launch and host-side enqueue jitter cannot stall the pipeline;
-        # eager launches if the capture fails
+        # the whole step (uploads, the chunks' calls, downloads) as one CUDA graph, so that each
+        # timed step is one launch and host-side enqueue jitter cannot stall the pipeline; eager
+        # launches if the capture fails
         launch, mode = e2e_step, "eager"
         if not a.e2e_eager:
             torch.cuda.synchronize()
@@ -672,7 +876,7 @@ def main():
         ems = replicas.max_over_ranks(ems, "cuda")
         # the host link alone on this machine: one whole-batch pinned upload and download
         link = {}
-        for name, dst, src in (("h2d_gbs", step.U, U_pin), ("d2h_gbs", A_h, step.A)):
+        for name, dst, src in (("h2d_gbs", U_dev, U_pin), ("d2h_gbs", gphi_h, step.phi)):
             dst.copy_(src, non_blocking=True)
             torch.cuda.synchronize()
             e0.record(stream)
@@ -682,9 +886,16 @@ def main():
             link[name] = src.numel() * src.element_size() / (e0.elapsed_time(e1) / 1000.0) / 1e9
         e2e = {"value": replicas.whole_job_rate(step.props, world, ke, ems), "unit": "propagations/s",
                "h2d_bytes_per_step": int(U_pin.numel() * 8),
-               "d2h_bytes_per_step": int(A_h.numel() * 8 + C_h.numel() * 8 + gz_h.numel() * 8),
-               "ms_per_step": ems / ke, "host_link": link, "launch": mode, "chunk": ch, "depth": a.e2e_depth, "steps": ke,
-               "clocks": e2e_clocks}
+               "d2h_bytes_per_step": int(loss_h.numel() * 8 + gz_h.numel() * 8 + gphi_h.numel() * 4),
+               "d2h": "losses, dL/dz and dL/dphi of every field",
+               "ms_per_step": ems / ke, "host_link": link, "launch": mode, "chunk": ch,
+               "depth": a.e2e_depth, "steps": ke, "clocks": e2e_clocks}
+        del sc, pipe
+        torch.cuda.empty_cache()
+
+    cfgs = None
+    if not a.no_configs:
+        cfgs = configs_section(xl, torch)
 
     nxt = None
     if not a.no_next:
@@ -703,22 +914,24 @@ def main():
         line = {
             "metric": METRIC,
             "value": value, "unit": "propagations/s", "n_gpus": world, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
+            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32, f64 phases)",
             "data": "synthetic",
             "config": bench_config(B, world),
             "grads_per_s": grads,
-            "batch1": batch1,
-            "tables": table,
-            "next_rows": nxt,
-            "autotune": tune,
-            "step_parts": step_parts(xl),
             "gpu_launches": int(launches),
             "clocks": ck,
             "roofline": roof,
-            "kernels": kernels,
+            "e2e_alg": e2e_alg,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "step_parts": STEP_PARTS,
+            "batch1": batch1,
+            "configs": cfgs,
+            "tables": table,
+            "next_rows": nxt,
+            "autotune": tune,
+            "kernels": kernels,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

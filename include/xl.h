@@ -73,6 +73,9 @@ typedef int32_t xl_status;
  * in single precision, adds rounding noise up to k |g_out| |u_out| to a derivative that is often
  * four orders of magnitude smaller. The distance derivative uses the spectrum of dh/dz - ik h. */
 #define XL_PHASE_INVARIANT 2
+/* CZT backward calls only: add the field gradient and g_z to what g_in and g_z hold instead of
+ * overwriting them (the gradient of a field that feeds several propagators). */
+#define XL_ACCUMULATE 4
 
 /* Sampling grid: x_m = x0 + m dx, y_n = y0 + n dy. */
 typedef struct xl_grid {
@@ -216,8 +219,10 @@ xl_status xl_vrs_propagate_backward_saved(const void* g_exyz, const void* saved,
  * Reading: the Fresnel form of the RS integral evaluated on the window,
  *   u_out[q][p] = exp(ikz)/(i lambda z) dx dy sum_{n,m} u_in[n][m]
  *                 exp(i k [(X_p - x_m)^2 + (Y_q - y_n)^2] / (2 z)),
- * realised by Bluestein chirp multiplies and padded FFT convolutions (length 2^ceil(log2(N+M-1)))
- * separately along x and y.
+ * realised by Bluestein chirp multiplies and padded FFT convolutions separately along x and y.
+ * Each axis's grid side is cut into S segments whose transforms are summed before one inverse
+ * transform (length L = 2^ceil(log2(ceil(N/S) + M - 1))); S is chosen per axis to minimise the
+ * transform work (2048 -> 512: S = 4, L = 1024).
  * vectorial = 0: u_in [batch][ny][nx] -> u_out [batch][my][mx].
  * vectorial = 1: u_in [batch][2][ny][nx] (Ex, Ey) -> u_out [batch][3][my][mx] (Ex', Ey', Ez'),
  *   Ez' = sum [-(X_p - x_m)/z Ex - (Y_q - y_n)/z Ey] K (the VRS kernel ratio applied to CZT).
@@ -230,12 +235,46 @@ xl_status xl_czt_propagate(const void* u_in, void* u_out, int32_t batch, int32_t
                            const xl_grid* grid, const xl_window* window, double wavelength,
                            const double* z, int32_t flags, int32_t dtype, void* stream);
 
-/* Adjoint of xl_czt_propagate: g_out [batch][1 or 3][my][mx] -> g_in [batch][1, 2 or 3][ny][nx]
- * (the conjugate-chirp convolutions in reverse order). */
-xl_status xl_czt_propagate_backward(const void* g_out, void* g_in, int32_t batch,
-                                    int32_t vectorial, const xl_grid* grid,
+/* Adjoint of xl_czt_propagate and its distance gradient:
+ *   g_in = C^H g_out: g_out [batch][1 or 3][my][mx] -> g_in [batch][1, 2 or 3][ny][nx]
+ *     (the conjugate-chirp convolutions in reverse order); g_in may be NULL.
+ *   g_z[b] = Re sum conj(g_out) du_out/dz (device doubles, nullable; needs u_in, the forward's
+ *     input), from dK/dz = K [ik - 1/z - ik ((X_p - x_m)^2 + (Y_q - y_n)^2) / (2 z^2)] (and, for
+ *     vectorial fields, the z-dependence of the Ez kernel ratio). This call forms the forward's
+ *     saved sums itself (the cost of one forward with them); xl_czt_propagate_backward_saved
+ *     reads those of an earlier xl_czt_propagate_save instead.
+ * flags: XL_Z_DEVICE; XL_PHASE_INVARIANT (the loss is blind to a constant phase on u_out) drops
+ * the Re(ik <g_out, u_out>) term of g_z; XL_ACCUMULATE adds to g_in and g_z (the Ez plane of a
+ * 3-component g_in is then left as it is). */
+xl_status xl_czt_propagate_backward(const void* g_out, const void* u_in, void* g_in, double* g_z,
+                                    int32_t batch, int32_t vectorial, const xl_grid* grid,
                                     const xl_window* window, double wavelength, const double* z,
                                     int32_t flags, int32_t dtype, void* stream);
+
+/* Complex elements (of dtype) per batch element of the buffer xl_czt_propagate_save fills: the
+ * x-pass intermediate, the forward's distance-gradient sums along x and y and the per-component
+ * window fields. -1 for unsupported sizes. The layout depends on the sizes, vectorial and dtype
+ * only. */
+int64_t xl_czt_save_elems(const xl_grid* grid, const xl_window* window, int32_t vectorial,
+                          int32_t dtype);
+
+/* Forward CZT that also writes, into the caller's `saved` buffer ([batch][xl_czt_save_elems]
+ * complex elements, device), what the adjoint's distance gradient needs from the forward, so that
+ * xl_czt_propagate_backward_saved transforms nothing of the input again. u_out as
+ * xl_czt_propagate. saved may not alias u_in or u_out. */
+xl_status xl_czt_propagate_save(const void* u_in, void* u_out, void* saved, int32_t batch,
+                                int32_t vectorial, const xl_grid* grid, const xl_window* window,
+                                double wavelength, const double* z, int32_t flags, int32_t dtype,
+                                void* stream);
+
+/* xl_czt_propagate_backward with the sums an earlier xl_czt_propagate_save (same sizes, distances
+ * and dtype) left in `saved`; u_in (its input) is still read for g_z. saved may be NULL when g_z
+ * is NULL. */
+xl_status xl_czt_propagate_backward_saved(const void* g_out, const void* u_in, const void* saved,
+                                          void* g_in, double* g_z, int32_t batch, int32_t vectorial,
+                                          const xl_grid* grid, const xl_window* window,
+                                          double wavelength, const double* z, int32_t flags,
+                                          int32_t dtype, void* stream);
 
 /* ---------------------------------------------------------------------------------------------
  * Angular-spectrum CZT: the exact-RS reading of the CZT propagator (Methods, "Features and
@@ -484,6 +523,11 @@ typedef struct xl_table_config {
   double lr_z;       /* Adam step size for z1 and z2 */
   int32_t cam_m;     /* camera pixels per side */
   int32_t dtype;     /* XL_C64 or XL_C128 */
+  int32_t checkpoint; /* what the RS / VRS adjoints read for their distance gradients (per-plane
+                         checkpointing): 0 = the 2D spectra of their zero-padded inputs, kept by
+                         the forwards (12 field planes a setup, no input transform in the
+                         adjoints); 1 = only the fields at the optical planes, the adjoints
+                         transforming their inputs again (about half the memory a setup). */
 } xl_table_config;
 
 typedef struct xl_batch xl_batch; /* opaque; owns all per-setup device buffers */
@@ -505,6 +549,10 @@ xl_status xl_batch_step(xl_batch* batch, int32_t use_graph, void* stream);
 #define XL_BATCH_GRAD_PHI2 6
 
 /* Copies one quantity of one setup to host memory (synchronises the stream). */
+/* Device bytes the batch's own buffers hold (fields, gradients, masks, moments, parameters; the
+ * library's shared workspaces and table cache are reported by xl_cache_bytes). -1 for NULL. */
+int64_t xl_batch_memory(xl_batch* batch);
+
 xl_status xl_batch_read(xl_batch* batch, int32_t what, int32_t setup, void* host_out, void* stream);
 
 /* Grid size N of a setup (-1 if out of range). */

@@ -23,73 +23,93 @@ def _dev_z(z: torch.Tensor, batch: int) -> torch.Tensor:
 class RSPropagate(torch.autograd.Function):
     """u [B][ny][nx] -> RS(u, z); z: float64 CUDA tensor [B] (or [1]). phase_invariant: the loss
     ignores a constant phase on the output (intensity losses behind linear optics), which lets
-    the distance derivative drop an exactly-zero, noise-prone term (XL_PHASE_INVARIANT)."""
+    the distance derivative drop an exactly-zero, noise-prone term (XL_PHASE_INVARIANT).
+    checkpoint: for the distance gradient keep the input field (one plane) instead of the 2D
+    spectrum of the zero-padded input (four planes), which the adjoint then recomputes."""
 
     @staticmethod
-    def forward(ctx, u, z, grid, wavelength, phase_invariant=False):
+    def forward(ctx, u, z, grid, wavelength, phase_invariant=False, checkpoint=False):
         zz = _dev_z(z.detach(), u.shape[0])
         u = u.contiguous()
-        # a distance gradient needs the input's row transforms, which the forward keeps
-        saved = xl.save_buffer(u) if ctx.needs_input_grad[1] else u.new_empty(0)
-        ctx.save_for_backward(saved, zz)
+        need_z = ctx.needs_input_grad[1]
+        # a distance gradient needs the input's spectrum: kept by the forward, or recomputed
+        saved = xl.save_buffer(u) if need_z and not checkpoint else u.new_empty(0)
+        ctx.save_for_backward(saved, zz, u if need_z and checkpoint else u.new_empty(0))
         ctx.grid, ctx.wl, ctx.zshape, ctx.pinv = grid, wavelength, z.shape, phase_invariant
         return xl.rs_propagate(u, grid, wavelength, zz, saved=saved if saved.numel() else None)
 
     @staticmethod
     def backward(ctx, g):
-        saved, zz = ctx.saved_tensors
+        saved, zz, u = ctx.saved_tensors
         need_u, need_z = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
-        g_in, g_z = xl.rs_propagate_backward(g.contiguous(), None, ctx.grid, ctx.wl, zz,
-                                             want_field=need_u, want_dz=need_z,
+        g_in, g_z = xl.rs_propagate_backward(g.contiguous(), u if u.numel() else None, ctx.grid,
+                                             ctx.wl, zz, want_field=need_u, want_dz=need_z,
                                              phase_invariant=ctx.pinv,
-                                             saved=saved if need_z else None)
+                                             saved=saved if need_z and saved.numel() else None)
         if g_z is not None:
             g_z = g_z.reshape(-1).sum().reshape(ctx.zshape) if ctx.zshape.numel() == 1 else g_z.reshape(ctx.zshape)
-        return g_in, g_z, None, None, None
+        return g_in, g_z, None, None, None, None
 
 
 class VRSPropagate(torch.autograd.Function):
-    """exy [B][2][ny][nx] -> [B][3][ny][nx] (phase_invariant as in RSPropagate)."""
+    """exy [B][2][ny][nx] -> [B][3][ny][nx] (phase_invariant and checkpoint as in RSPropagate:
+    two input planes kept instead of eight spectrum planes)."""
 
     @staticmethod
-    def forward(ctx, exy, z, grid, wavelength, phase_invariant=False):
+    def forward(ctx, exy, z, grid, wavelength, phase_invariant=False, checkpoint=False):
         zz = _dev_z(z.detach(), exy.shape[0])
         exy = exy.contiguous()
-        saved = xl.save_buffer(exy, 2) if ctx.needs_input_grad[1] else exy.new_empty(0)
-        ctx.save_for_backward(saved, zz)
+        need_z = ctx.needs_input_grad[1]
+        saved = xl.save_buffer(exy, 2) if need_z and not checkpoint else exy.new_empty(0)
+        ctx.save_for_backward(saved, zz, exy if need_z and checkpoint else exy.new_empty(0))
         ctx.grid, ctx.wl, ctx.zshape, ctx.pinv = grid, wavelength, z.shape, phase_invariant
         return xl.vrs_propagate(exy, grid, wavelength, zz, saved=saved if saved.numel() else None)
 
     @staticmethod
     def backward(ctx, g):
-        saved, zz = ctx.saved_tensors
+        saved, zz, exy = ctx.saved_tensors
         need_u, need_z = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
-        g_in, g_z = xl.vrs_propagate_backward(g.contiguous(), None, ctx.grid, ctx.wl, zz,
-                                              want_field=need_u, want_dz=need_z,
+        g_in, g_z = xl.vrs_propagate_backward(g.contiguous(), exy if exy.numel() else None, ctx.grid,
+                                              ctx.wl, zz, want_field=need_u, want_dz=need_z,
                                               phase_invariant=ctx.pinv,
-                                              saved=saved if need_z else None)
+                                              saved=saved if need_z and saved.numel() else None)
         if g_z is not None:
             g_z = g_z.reshape(-1).sum().reshape(ctx.zshape) if ctx.zshape.numel() == 1 else g_z.reshape(ctx.zshape)
-        return g_in, g_z, None, None, None
+        return g_in, g_z, None, None, None, None
 
 
 class CZTPropagate(torch.autograd.Function):
-    """CZT onto a window (scalar [B][ny][nx] or vectorial [B][2][ny][nx]); z is not
-    differentiated (the CZT distance is the lens focal length in the optical tables)."""
+    """CZT onto a window (scalar [B][ny][nx] or vectorial [B][2][ny][nx]); z: float64 CUDA
+    tensor [B] (or [1]). When z requires a gradient the forward saves the sums the distance
+    gradient needs (xl_czt_propagate_save) and keeps its input. phase_invariant as in
+    RSPropagate."""
 
     @staticmethod
-    def forward(ctx, u, z, grid, window, wavelength, vectorial):
+    def forward(ctx, u, z, grid, window, wavelength, vectorial, phase_invariant=False):
         zz = _dev_z(z.detach(), u.shape[0])
-        ctx.save_for_backward(zz)
+        u = u.contiguous()
+        need_z = ctx.needs_input_grad[1]
+        saved = xl.czt_save_buffer(u, grid, window, vectorial) if need_z else u.new_empty(0)
+        ctx.save_for_backward(zz, saved, u if need_z else u.new_empty(0))
         ctx.grid, ctx.window, ctx.wl, ctx.vec = grid, window, wavelength, vectorial
-        return xl.czt_propagate(u.contiguous(), grid, window, wavelength, zz, vectorial=vectorial)
+        ctx.zshape, ctx.pinv = z.shape, phase_invariant
+        return xl.czt_propagate(u, grid, window, wavelength, zz, vectorial=vectorial,
+                                saved=saved if need_z else None)
 
     @staticmethod
     def backward(ctx, g):
-        (zz,) = ctx.saved_tensors
-        g_in = xl.czt_propagate_backward(g.contiguous(), ctx.grid, ctx.window, ctx.wl, zz,
-                                         vectorial=ctx.vec)
-        return g_in, None, None, None, None, None
+        zz, saved, u = ctx.saved_tensors
+        need_u, need_z = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if not need_z:
+            g_in = xl.czt_propagate_backward(g.contiguous(), ctx.grid, ctx.window, ctx.wl, zz,
+                                             vectorial=ctx.vec)
+            return g_in, None, None, None, None, None, None
+        g_in, g_z = xl.czt_propagate_backward(g.contiguous(), ctx.grid, ctx.window, ctx.wl, zz,
+                                              vectorial=ctx.vec, u_in=u, want_dz=True,
+                                              want_field=need_u, phase_invariant=ctx.pinv,
+                                              saved=saved)
+        g_z = g_z.reshape(-1).sum().reshape(ctx.zshape) if ctx.zshape.numel() == 1 else g_z.reshape(ctx.zshape)
+        return g_in, g_z, None, None, None, None, None
 
 
 class BeamSplitter(torch.autograd.Function):

@@ -4,6 +4,7 @@
 // sampled field times exp(i z kz), evaluated on an arbitrary window.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <string>
 
 #include "xl_asczt_launch.h"
@@ -11,12 +12,6 @@
 
 namespace xl {
 namespace {
-
-int window_len(int n, int m) {
-  int L = 64;
-  while (L < n + m - 1) L <<= 1;
-  return L;
-}
 
 xl_status check(const xl_grid* g, const xl_window* w, double wavelength, int32_t batch,
                 const double* z, int32_t flags, int32_t dtype) {
@@ -43,18 +38,25 @@ xl_status check(const xl_grid* g, const xl_window* w, double wavelength, int32_t
   return XL_OK;
 }
 
-CztTabArgs tab_args(const xl_grid* g, const xl_window* w, double wavelength) {
+// Window-pass tables with the segment plan of each axis (no distance: no b2 rows).
+CztTabArgs tab_args(const xl_grid* g, const xl_window* w, double wavelength, int dtype) {
+  const int cs = dtype == XL_C128 ? 16 : 8;
+  const CztAxisPlan px = czt_axis_plan(g->nx, w->mx, cs, false, false);
+  const CztAxisPlan py = czt_axis_plan(g->ny, w->my, cs, false, false);
   CztTabArgs a;
   a.nx = g->nx; a.ny = g->ny; a.mx = w->mx; a.my = w->my;
-  a.Lx = window_len(g->nx, w->mx);
-  a.Ly = window_len(g->ny, w->my);
+  a.Lx = px.L; a.Ly = py.L;
+  a.Sx = px.S; a.Sy = py.S;
+  a.segx = px.seg; a.segy = py.seg;
+  a.dz = 0;
+  a.jcx = a.jcy = 0;
   a.x0 = g->x0; a.dx = g->dx; a.y0 = g->y0; a.dy = g->dy;
   a.xo0 = w->xo0; a.dxo = w->dxo; a.yo0 = w->yo0; a.dyo = w->dyo;
   a.k = kTwoPi / wavelength;
   a.lambda = wavelength;
   a.zdev = nullptr;
   a.zval = 0;
-  a.off_y = (int64_t)a.nx + a.mx + a.Lx;
+  a.off_y = czt_axis_elems(a.nx, a.mx, a.Lx, a.Sx, 0);
   return a;
 }
 
@@ -69,10 +71,11 @@ xl_status run(bool adjoint, const void* in, const void* u_in, void* out, double*
   const bool zdev = (flags & XL_Z_DEVICE) != 0;
   const bool want_field = !adjoint || out != nullptr;
   const bool want_dz = adjoint && g_z != nullptr;
-  const CztTabArgs ta = tab_args(g, w, wavelength);
+  const CztTabArgs ta = tab_args(g, w, wavelength, dtype);
+  if (ta.Lx == 0 || ta.Ly == 0) return fail(XL_ERR_UNSUPPORTED, "asczt: no transform plan fits");
   // window tables: no distance in them, cached per (grid, window, dtype)
-  const int64_t tab_n = ta.off_y + ta.ny + ta.my + ta.Ly;
-  std::string key = "asczt";
+  const int64_t tab_n = ta.off_y + czt_axis_elems(ta.ny, ta.my, ta.Ly, ta.Sy, 0);
+  std::string key = "asczt2";
   key_put(key, *g);
   key_put(key, *w);
   key_put(key, dtype);
@@ -83,8 +86,8 @@ xl_status run(bool adjoint, const void* in, const void* u_in, void* out, double*
   {
     const C* t = (const C*)tab;
     const C* u = t + ta.off_y;
-    ax = axis_run(Axis<C>{t, t + nx, t + nx + mx});
-    ay = axis_run(Axis<C>{u, u + ny, u + ny + my});
+    ax = axis_run(Axis<C>{t, t + nx, t + nx + mx, nullptr}, ta.Sx, ta.segx);
+    ay = axis_run(Axis<C>{u, u + ny, u + ny + my, nullptr}, ta.Sy, ta.segy);
   }
   // Batch elements per launch: up to kCztRun whatever their distances (each element reads the
   // transfer tables of its own distance), within 2 GB of spectrum planes; the chunk's transfer
@@ -112,6 +115,7 @@ xl_status run(bool adjoint, const void* in, const void* u_in, void* out, double*
   void* Hdev = p + 2 * al(b_plane) + al(b_t2) + al(b_tu) + al(b_dz);
 
   CztDims d;
+  std::memset(&d, 0, sizeof(d));
   d.nx = nx; d.ny = ny; d.mx = mx; d.my = my;
   d.x0 = g->x0; d.dx = g->dx; d.y0 = g->y0; d.dy = g->dy;
   d.xo0 = w->xo0; d.dxo = w->dxo; d.yo0 = w->yo0; d.dyo = w->dyo;
@@ -119,6 +123,7 @@ xl_status run(bool adjoint, const void* in, const void* u_in, void* out, double*
   for (int i = 0; i < kCztRun; ++i) d.z[i] = 0.0;
   d.in_planes = 1;
   d.adjoint = adjoint ? 1 : 0;
+  d.tb_elem = tplane;
 
   AsTransferArgs tr;
   tr.nx = nx; tr.ny = ny; tr.dx = g->dx; tr.dy = g->dy; tr.k = kTwoPi / wavelength;

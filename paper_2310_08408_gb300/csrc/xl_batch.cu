@@ -12,8 +12,14 @@
 // whole step can be captured once into a CUDA graph and replayed: after one eager warm-up step
 // every workspace has its final size, so the captured calls allocate nothing.
 //
-// Memory per setup keeps one checkpoint per optical plane (source, after SLM1, after RS, after
-// the wave plate, after VRS, after the lens, camera) plus gradients and Adam moments.
+// Memory per setup: the fields at the optical planes the adjoints read (source, after SLM1,
+// after RS, after the wave plate, after VRS, the camera), two 3-component gradient buffers used in
+// turn by the backward stages (the field after the lens shares one of them: nothing reads it
+// after the forward), masks, their gradients and Adam moments. cfg.checkpoint selects what the
+// RS and VRS adjoints read for their distance gradients: 0 keeps the 2D spectra of their zero-
+// padded inputs (4 and 8 field planes a setup; no input transform in the adjoints), 1 keeps only
+// the plane fields and the adjoints transform their inputs again (about half the memory, one
+// more column transform in each adjoint's pass 2).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -33,8 +39,9 @@ struct Group {
   // device buffers (complex T unless noted)
   void *src = nullptr, *a0 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *a4 = nullptr,
        *a5 = nullptr;
-  void *g5 = nullptr, *g4 = nullptr, *g3 = nullptr, *g2 = nullptr, *g1 = nullptr, *g0 = nullptr;
-  void *s1 = nullptr, *s2 = nullptr;  // spectra the RS / VRS forwards keep for the adjoints
+  void *g5 = nullptr;                 // camera gradient
+  void *gx = nullptr, *gy = nullptr;  // 3-component gradient buffers (a4 lives in gx)
+  void *s1 = nullptr, *s2 = nullptr;  // spectra the RS / VRS forwards keep (checkpoint 0)
   void *phi1 = nullptr, *phi2 = nullptr, *gphi1 = nullptr, *gphi2 = nullptr;  // real T [count][n][n]
   void *m1 = nullptr, *v1 = nullptr, *m2 = nullptr, *v2 = nullptr;            // Adam moments (real T)
   double *p1 = nullptr, *p2 = nullptr, *pl = nullptr;  // element params [count][n_el][4]
@@ -50,6 +57,7 @@ struct Group {
 struct xl_batch {
   xl_table_config cfg{};
   int n_setups = 0;
+  int64_t bytes = 0;        // device memory the batch holds
   int32_t* step = nullptr;  // device step counter
   std::vector<xl::Group> groups;
   std::vector<void*> allocs;
@@ -68,6 +76,7 @@ xl_status dalloc(xl_batch* b, void** p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) return cuda_status(e, "batch cudaMalloc");
   b->allocs.push_back(*p);
+  b->bytes += (int64_t)bytes;
   return XL_OK;
 }
 
@@ -126,15 +135,16 @@ xl_status group_alloc(xl_batch* b, Group& G, const double* init, uint64_t seed, 
   const size_t cs = sizeof(cplx<T>), rs = sizeof(T);
   const int64_t plane = (int64_t)G.n * G.n, cnt = G.count;
   const int64_t cam = (int64_t)b->cfg.cam_m * b->cfg.cam_m;
+  const bool spectra = b->cfg.checkpoint == 0;
   struct {
     void** p;
     size_t bytes;
   } bufs[] = {
       {&G.src, cnt * plane * cs},     {&G.a0, cnt * plane * cs},     {&G.a1, cnt * plane * cs},
-      {&G.a2, cnt * 2 * plane * cs},  {&G.a3, cnt * 3 * plane * cs}, {&G.a4, cnt * 3 * plane * cs},
-      {&G.a5, cnt * 3 * cam * cs},    {&G.g5, cnt * 3 * cam * cs},   {&G.g4, cnt * 3 * plane * cs},
-      {&G.g3, cnt * 3 * plane * cs},  {&G.g2, cnt * 2 * plane * cs}, {&G.g1, cnt * plane * cs},
-      {&G.g0, cnt * plane * cs},      {&G.s1, cnt * 4 * plane * cs}, {&G.s2, cnt * 8 * plane * cs},
+      {&G.a2, cnt * 2 * plane * cs},  {&G.a3, cnt * 3 * plane * cs},
+      {&G.a5, cnt * 3 * cam * cs},    {&G.g5, cnt * 3 * cam * cs},
+      {&G.gx, cnt * 3 * plane * cs},  {&G.gy, cnt * 3 * plane * cs},
+      {&G.s1, spectra ? cnt * 4 * plane * cs : 0}, {&G.s2, spectra ? cnt * 8 * plane * cs : 0},
       {&G.phi1, cnt * plane * rs},    {&G.phi2, cnt * plane * rs},
       {&G.gphi1, cnt * plane * rs},   {&G.gphi2, cnt * plane * rs},  {&G.m1, cnt * plane * rs},
       {&G.v1, cnt * plane * rs},      {&G.m2, cnt * plane * rs},     {&G.v2, cnt * plane * rs},
@@ -143,7 +153,9 @@ xl_status group_alloc(xl_batch* b, Group& G, const double* init, uint64_t seed, 
       {(void**)&G.gp2, cnt * 12 * 8}, {(void**)&G.gz1, cnt * 8},     {(void**)&G.gz2, cnt * 8},
       {(void**)&G.sm, cnt * 3 * 8},   {(void**)&G.sv, cnt * 3 * 8},  {(void**)&G.loss, cnt * 8},
   };
-  for (auto& bf : bufs) XL_TRY(dalloc(b, bf.p, bf.bytes));
+  for (auto& bf : bufs)
+    if (bf.bytes) XL_TRY(dalloc(b, bf.p, bf.bytes));
+  G.a4 = G.gx;  // the field after the lens: read by the VCZT forward only
   for (void* p : {G.m1, G.v1, G.m2, G.v2}) XL_CUDA_TRY(cudaMemsetAsync(p, 0, cnt * plane * rs, s));
   XL_CUDA_TRY(cudaMemsetAsync(G.sm, 0, cnt * 3 * 8, s));
   XL_CUDA_TRY(cudaMemsetAsync(G.sv, 0, cnt * 3 * 8, s));
@@ -203,30 +215,39 @@ xl_status group_step(xl_batch* b, Group& G, cudaStream_t s) {
   xl_element e_mid[3] = {el(XL_SLM, G.phi2, plane), el(XL_TO_VECTOR), el(XL_WAVEPLATE)};
   xl_element e_lens[1] = {el(XL_LENS)};
   // forward
-  XL_TRY(xl_apply_elements(G.src, G.a0, cnt, 1, g, lam, e_slm1, 1, G.p1, XL_Z_DEVICE, dt, s));
-  XL_TRY(xl_rs_propagate_save(G.a0, G.a1, G.s1, cnt, g, lam, G.z1, XL_Z_DEVICE, dt, s));
-  XL_TRY(xl_apply_elements(G.a1, G.a2, cnt, 1, g, lam, e_mid, 3, G.p2, XL_Z_DEVICE, dt, s));
-  XL_TRY(xl_vrs_propagate_save(G.a2, G.a3, G.s2, cnt, g, lam, G.z2, XL_Z_DEVICE, dt, s));
-  XL_TRY(xl_apply_elements(G.a3, G.a4, cnt, 3, g, lam, e_lens, 1, G.pl, XL_Z_DEVICE, dt, s));
+  const bool spectra = c.checkpoint == 0;
+  const int32_t zf = XL_Z_DEVICE, zfb = XL_Z_DEVICE | XL_PHASE_INVARIANT;
+  XL_TRY(xl_apply_elements(G.src, G.a0, cnt, 1, g, lam, e_slm1, 1, G.p1, zf, dt, s));
+  if (spectra) XL_TRY(xl_rs_propagate_save(G.a0, G.a1, G.s1, cnt, g, lam, G.z1, zf, dt, s));
+  else XL_TRY(xl_rs_propagate(G.a0, G.a1, cnt, g, lam, G.z1, zf, dt, s));
+  XL_TRY(xl_apply_elements(G.a1, G.a2, cnt, 1, g, lam, e_mid, 3, G.p2, zf, dt, s));
+  if (spectra) XL_TRY(xl_vrs_propagate_save(G.a2, G.a3, G.s2, cnt, g, lam, G.z2, zf, dt, s));
+  else XL_TRY(xl_vrs_propagate(G.a2, G.a3, cnt, g, lam, G.z2, zf, dt, s));
+  XL_TRY(xl_apply_elements(G.a3, G.a4, cnt, 3, g, lam, e_lens, 1, G.pl, zf, dt, s));
   // the VCZT distance is the fixed focal length: host distances, cached chirp tables
   XL_TRY(xl_czt_propagate(G.a4, G.a5, cnt, 2, g, &win, lam, G.zf.data(), 0, dt, s));
   XL_TRY(xl_intensity_loss(G.a5, cnt, 3, 7u, &wg, XL_SECOND_MOMENT, 0.0, G.loss, nullptr, dt, s));
-  // backward
+  // backward; the gradients alternate between gx and gy (a4, in gx, is not read any more)
   XL_TRY(xl_intensity_loss_backward(G.a5, cnt, 3, 7u, &wg, XL_SECOND_MOMENT, 0.0, nullptr, G.g5, dt, s));
-  XL_TRY(xl_czt_propagate_backward(G.g5, G.g4, cnt, 2, g, &win, lam, G.zf.data(), 0, dt, s));
-  XL_TRY(xl_apply_elements_backward(G.g4, G.a3, G.g3, cnt, 3, g, lam, e_lens, 1, G.pl, XL_Z_DEVICE,
+  XL_TRY(xl_czt_propagate_backward(G.g5, nullptr, G.gx, nullptr, cnt, 2, g, &win, lam, G.zf.data(), 0,
+                                   dt, s));
+  XL_TRY(xl_apply_elements_backward(G.gx, G.a3, G.gy, cnt, 3, g, lam, e_lens, 1, G.pl, zf,
                                     nullptr, nullptr, nullptr, dt, s));
   // the camera loss is invariant under a constant phase on every plane: drop the e^{ikz} term
-  XL_TRY(xl_vrs_propagate_backward_saved(G.g3, G.s2, G.g2, G.gz2, cnt, g, lam, G.z2,
-                                         XL_Z_DEVICE | XL_PHASE_INVARIANT, dt, s));
+  if (spectra)
+    XL_TRY(xl_vrs_propagate_backward_saved(G.gy, G.s2, G.gx, G.gz2, cnt, g, lam, G.z2, zfb, dt, s));
+  else
+    XL_TRY(xl_vrs_propagate_backward(G.gy, G.a2, G.gx, G.gz2, cnt, g, lam, G.z2, zfb, dt, s));
   void* gpx_mid[3] = {G.gphi2, nullptr, nullptr};
-  XL_TRY(xl_apply_elements_backward(G.g2, G.a1, G.g1, cnt, 1, g, lam, e_mid, 3, G.p2, XL_Z_DEVICE,
+  XL_TRY(xl_apply_elements_backward(G.gx, G.a1, G.gy, cnt, 1, g, lam, e_mid, 3, G.p2, zf,
                                     gpx_mid, nullptr, G.gp2, dt, s));
-  XL_TRY(xl_rs_propagate_backward_saved(G.g1, G.s1, G.g0, G.gz1, cnt, g, lam, G.z1,
-                                        XL_Z_DEVICE | XL_PHASE_INVARIANT, dt, s));
+  if (spectra)
+    XL_TRY(xl_rs_propagate_backward_saved(G.gy, G.s1, G.gx, G.gz1, cnt, g, lam, G.z1, zfb, dt, s));
+  else
+    XL_TRY(xl_rs_propagate_backward(G.gy, G.a0, G.gx, G.gz1, cnt, g, lam, G.z1, zfb, dt, s));
   void* gpx1[1] = {G.gphi1};
-  XL_TRY(xl_apply_elements_backward(G.g0, G.src, nullptr, cnt, 1, g, lam, e_slm1, 1, G.p1,
-                                    XL_Z_DEVICE, gpx1, nullptr, nullptr, dt, s));
+  XL_TRY(xl_apply_elements_backward(G.gx, G.src, nullptr, cnt, 1, g, lam, e_slm1, 1, G.p1,
+                                    zf, gpx1, nullptr, nullptr, dt, s));
   // Adam on the masks and the scalars
   const int rd = dt == XL_C128 ? 1 : 0;
   XL_TRY(xl_adam_step(G.phi1, G.m1, G.v1, G.gphi1, cnt * plane, rd, c.lr, 0.9, 0.999, 1e-8, b->step, 0, s));
@@ -258,6 +279,7 @@ xl_status xl_batch_create(const xl_table_config* cfg, int32_t n_setups, const in
   if (!cfg || !grid_n || !init || !out) return fail(XL_ERR_ARG, "batch: NULL argument");
   if (n_setups < 1) return fail(XL_ERR_ARG, "batch: n_setups must be >= 1");
   if (cfg->dtype != XL_C64 && cfg->dtype != XL_C128) return fail(XL_ERR_ARG, "batch: bad dtype");
+  if (cfg->checkpoint != 0 && cfg->checkpoint != 1) return fail(XL_ERR_ARG, "batch: checkpoint must be 0 or 1");
   if (!(cfg->extent > 0) || !(cfg->wavelength > 0) || !(cfg->w0 > 0) || !(cfg->f > 0) ||
       cfg->cam_m < 1 || !(cfg->cam_width > 0))
     return fail(XL_ERR_ARG, "batch: bad table configuration");
@@ -383,6 +405,8 @@ xl_status xl_batch_read(xl_batch* b, int32_t what, int32_t setup, void* host_out
     }
   return fail(XL_ERR_ARG, "batch read: setup not found");
 }
+
+int64_t xl_batch_memory(xl_batch* b) { return b ? b->bytes : -1; }
 
 int32_t xl_batch_grid(xl_batch* b, int32_t setup) {
   if (!b) return -1;

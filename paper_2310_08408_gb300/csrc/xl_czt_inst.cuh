@@ -7,73 +7,93 @@
 
 namespace xl {
 
-template <typename T, int L, bool VEC, int V>
+template <typename T, int L, bool VEC, int V, bool DZ>
 xl_status pass_LVV(int which, const void* src, void* dst, const CztDims& d, const AxisRun<cplx<T>>& ax,
-                   int nb, cudaStream_t s) {
-  constexpr int ROWS = czt_rows<L, sizeof(cplx<T>), VEC, V>();
-  const size_t sm = czt_smem_bytes<L, sizeof(cplx<T>), VEC, V>();
+                   int nb, cudaStream_t s, const CztDzArgs<cplx<T>>* dz, int* blocks) {
+  typedef cplx<T> C;
+  constexpr int ROWS = czt_rows<L, sizeof(C), VEC, V>();
+  const bool fwd = which == CZT_FWD_X || which == CZT_FWD_Y;
+  const size_t sm = czt_smem_bytes<L, sizeof(C), VEC, V>(ax.nseg > 1, DZ && fwd);
+  if (sm > (size_t)227 * 1024) return fail(XL_ERR_UNSUPPORTED, "czt: segment plan exceeds shared memory");
   const void* tw;
   XL_TRY(twiddles(L, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
-  const cplx<T>* twc = (const cplx<T>*)tw;
+  const C* twc = (const C*)tw;
   const dim3 blk(ROWS * (L / 16));
+  const CztSaved<C> sv = dz ? dz->sv : CztSaved<C>{nullptr, 0, 0, 0, 0};
+  double* dzp = dz ? dz->dzp : nullptr;
+  const std::string tag = std::string(VEC ? "_vec<" : "<") + std::to_string(L) + ">" + (DZ ? "_dz" : "");
+  int gx = 0;
   switch (which) {
     case CZT_FWD_X:
-      XL_TRY(smem_attr((const void*)k_czt_fwd_x<T, L, VEC, V>, sm));
+      gx = (d.ny + ROWS - 1) / ROWS;
+      XL_TRY(smem_attr((const void*)k_czt_fwd_x<T, L, VEC, V, DZ>, sm));
       {
-      LaunchScope ls(std::string("czt_fwd_x") + (VEC ? "_vec<" : "<") + std::to_string(L) + ">", s);
-      k_czt_fwd_x<T, L, VEC, V><<<dim3((d.ny + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
-          (const cplx<T>*)src, (cplx<T>*)dst, d, ax, twc);
+        LaunchScope ls("czt_fwd_x" + tag, s);
+        k_czt_fwd_x<T, L, VEC, V, DZ><<<dim3(gx, nb), blk, sm, s>>>((const C*)src, (C*)dst, d, ax, twc, sv);
       }
       break;
     case CZT_FWD_Y:
-      XL_TRY(smem_attr((const void*)k_czt_fwd_y<T, L, VEC, V>, sm));
+      gx = (d.mx + ROWS - 1) / ROWS;
+      XL_TRY(smem_attr((const void*)k_czt_fwd_y<T, L, VEC, V, DZ>, sm));
       {
-      LaunchScope ls(std::string("czt_fwd_y") + (VEC ? "_vec<" : "<") + std::to_string(L) + ">", s);
-      k_czt_fwd_y<T, L, VEC, V><<<dim3((d.mx + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
-          (const cplx<T>*)src, (cplx<T>*)dst, d, ax, twc);
+        LaunchScope ls("czt_fwd_y" + tag, s);
+        k_czt_fwd_y<T, L, VEC, V, DZ><<<dim3(gx, nb), blk, sm, s>>>((const C*)src, (C*)dst, d, ax, twc, sv);
       }
       break;
     case CZT_ADJ_Y:
-      XL_TRY(smem_attr((const void*)k_czt_adj_y<T, L, VEC, V>, sm));
+      gx = (d.mx + ROWS - 1) / ROWS;
+      XL_TRY(smem_attr((const void*)k_czt_adj_y<T, L, VEC, V, DZ>, sm));
       {
-      LaunchScope ls(std::string("czt_adj_y") + (VEC ? "_vec<" : "<") + std::to_string(L) + ">", s);
-      k_czt_adj_y<T, L, VEC, V><<<dim3((d.mx + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
-          (const cplx<T>*)src, (cplx<T>*)dst, d, ax, twc);
+        LaunchScope ls("czt_adj_y" + tag, s);
+        k_czt_adj_y<T, L, VEC, V, DZ><<<dim3(gx, nb), blk, sm, s>>>((const C*)src, (C*)dst, d, ax, twc, sv,
+                                                                    dzp);
       }
       break;
     case CZT_ADJ_X:
-      XL_TRY(smem_attr((const void*)k_czt_adj_x<T, L, VEC, V>, sm));
+      gx = (d.ny + ROWS - 1) / ROWS;
+      XL_TRY(smem_attr((const void*)k_czt_adj_x<T, L, VEC, V, DZ>, sm));
       {
-      LaunchScope ls(std::string("czt_adj_x") + (VEC ? "_vec<" : "<") + std::to_string(L) + ">", s);
-      k_czt_adj_x<T, L, VEC, V><<<dim3((d.ny + ROWS - 1) / ROWS, nb), blk, sm, s>>>(
-          (const cplx<T>*)src, (cplx<T>*)dst, d, ax, twc);
+        LaunchScope ls("czt_adj_x" + tag, s);
+        k_czt_adj_x<T, L, VEC, V, DZ><<<dim3(gx, nb), blk, sm, s>>>((const C*)src, (C*)dst, d, ax, twc, sv,
+                                                                    dzp, dz ? dz->u_in : nullptr);
       }
       break;
     default:
       return fail(XL_ERR_ARG, "czt_pass: bad pass");
   }
   XL_CUDA_TRY(cudaGetLastError());
+  if (blocks) *blocks = gx;
   return XL_OK;
 }
 
-// The autotuner's variant for this pass and length (scalar passes of long rows only).
+// The autotuner's variant for this pass and length (scalar passes of long rows only; the
+// distance-gradient forms use the default shape).
 template <typename T, int L, bool VEC>
 xl_status pass_LV(int which, const void* src, void* dst, const CztDims& d, const AxisRun<cplx<T>>& ax,
-                  int nb, cudaStream_t s) {
+                  int nb, cudaStream_t s, const CztDzArgs<cplx<T>>* dz, int* blocks) {
+  if (dz && dz->on) return pass_LVV<T, L, VEC, 0, true>(which, src, dst, d, ax, nb, s, dz, blocks);
   if constexpr (!VEC && L >= kTuneMinL) {
     const int fam = which == CZT_FWD_X ? TUNE_CZT_FWD_X : which == CZT_FWD_Y ? TUNE_CZT_FWD_Y
                   : which == CZT_ADJ_X ? TUNE_CZT_ADJ_X : TUNE_CZT_ADJ_Y;
+    constexpr int CS = sizeof(cplx<T>);
+    const bool multi = ax.nseg > 1;
     switch (tuned_variant(fam, L, sizeof(T) == 8 ? XL_C128 : XL_C64)) {
-      case 1: return pass_LVV<T, L, VEC, 1>(which, src, dst, d, ax, nb, s);
-      case 2: return pass_LVV<T, L, VEC, 2>(which, src, dst, d, ax, nb, s);
+      case 1:
+        if (czt_smem_bytes<L, CS, VEC, 1>(multi) <= (size_t)227 * 1024)
+          return pass_LVV<T, L, VEC, 1, false>(which, src, dst, d, ax, nb, s, nullptr, blocks);
+        break;
+      case 2:
+        if (czt_smem_bytes<L, CS, VEC, 2>(multi) <= (size_t)227 * 1024)
+          return pass_LVV<T, L, VEC, 2, false>(which, src, dst, d, ax, nb, s, nullptr, blocks);
+        break;
     }
   }
-  return pass_LVV<T, L, VEC, 0>(which, src, dst, d, ax, nb, s);
+  return pass_LVV<T, L, VEC, 0, false>(which, src, dst, d, ax, nb, s, nullptr, blocks);
 }
 
 #define XL_CZT_PASS_SIG(LL, VV)                                                                    \
   xl_status pass_LV<XL_REAL, LL, VV>(int, const void*, void*, const CztDims&, const AxisRun<cplx<XL_REAL>>&, \
-                                     int, cudaStream_t)
+                                     int, cudaStream_t, const CztDzArgs<cplx<XL_REAL>>*, int*)
 #define XL_CZT_INSTANTIATE(LL) \
   template XL_CZT_PASS_SIG(LL, false); \
   template XL_CZT_PASS_SIG(LL, true);
@@ -91,28 +111,28 @@ XL_CZT_EXTERN(1024) XL_CZT_EXTERN(2048) XL_CZT_EXTERN(4096) XL_CZT_EXTERN(8192)
 namespace {
 
 template <typename T, int L>
-xl_status bhat_L(cplx<T>* rows, int64_t stride, cudaStream_t s) {
+xl_status bhat_L(cplx<T>* rows, int64_t stride, int nrows, cudaStream_t s) {
   const size_t sm = (size_t)srow(L) * sizeof(cplx<T>);
   const void* tw;
   XL_TRY(twiddles(L, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
   XL_TRY(smem_attr((const void*)k_czt_bhat<T, L>, sm));
   LaunchScope ls("czt_bhat<" + std::to_string(L) + ">", s);
-  k_czt_bhat<T, L><<<1, L / 16, sm, s>>>(rows, stride, (const cplx<T>*)tw);
+  k_czt_bhat<T, L><<<nrows, L / 16, sm, s>>>(rows, stride, (const cplx<T>*)tw);
   XL_CUDA_TRY(cudaGetLastError());
   return XL_OK;
 }
 
 template <typename T>
-xl_status bhat(int L, cplx<T>* rows, int64_t stride, cudaStream_t s) {
+xl_status bhat(int L, cplx<T>* rows, int64_t stride, int nrows, cudaStream_t s) {
   switch (L) {
-    case 64: return bhat_L<T, 64>(rows, stride, s);
-    case 128: return bhat_L<T, 128>(rows, stride, s);
-    case 256: return bhat_L<T, 256>(rows, stride, s);
-    case 512: return bhat_L<T, 512>(rows, stride, s);
-    case 1024: return bhat_L<T, 1024>(rows, stride, s);
-    case 2048: return bhat_L<T, 2048>(rows, stride, s);
-    case 4096: return bhat_L<T, 4096>(rows, stride, s);
-    case 8192: return bhat_L<T, 8192>(rows, stride, s);
+    case 64: return bhat_L<T, 64>(rows, stride, nrows, s);
+    case 128: return bhat_L<T, 128>(rows, stride, nrows, s);
+    case 256: return bhat_L<T, 256>(rows, stride, nrows, s);
+    case 512: return bhat_L<T, 512>(rows, stride, nrows, s);
+    case 1024: return bhat_L<T, 1024>(rows, stride, nrows, s);
+    case 2048: return bhat_L<T, 2048>(rows, stride, nrows, s);
+    case 4096: return bhat_L<T, 4096>(rows, stride, nrows, s);
+    case 8192: return bhat_L<T, 8192>(rows, stride, nrows, s);
   }
   return fail(XL_ERR_UNSUPPORTED, "czt: unsupported transform length");
 }
@@ -185,11 +205,12 @@ xl_status czt_fwd_rm<XL_REAL>(int Lx, int Ly, const void* src, void* Tr, void* d
 
 template <>
 xl_status czt_pass<XL_REAL>(int which, bool vec, int L, const void* src, void* dst,
-                            const CztDims& d, const AxisRun<cplx<XL_REAL>>& ax, int nb, cudaStream_t s) {
+                            const CztDims& d, const AxisRun<cplx<XL_REAL>>& ax, int nb, cudaStream_t s,
+                            const CztDzArgs<cplx<XL_REAL>>* dz, int* blocks) {
 #define CP(LL)                                                                           \
   case LL:                                                                               \
-    return vec ? pass_LV<XL_REAL, LL, true>(which, src, dst, d, ax, nb, s)              \
-               : pass_LV<XL_REAL, LL, false>(which, src, dst, d, ax, nb, s);
+    return vec ? pass_LV<XL_REAL, LL, true>(which, src, dst, d, ax, nb, s, dz, blocks)  \
+               : pass_LV<XL_REAL, LL, false>(which, src, dst, d, ax, nb, s, dz, blocks);
   switch (L) {
     CP(64) CP(128) CP(256) CP(512) CP(1024) CP(2048) CP(4096) CP(8192)
   }
@@ -200,7 +221,7 @@ xl_status czt_pass<XL_REAL>(int which, bool vec, int L, const void* src, void* d
 template <>
 xl_status czt_tables<XL_REAL>(void* tab, const CztTabArgs& a, cudaStream_t s) {
   typedef cplx<XL_REAL> C;
-  const int64_t total = (int64_t)a.nx + a.mx + a.Lx + a.ny + a.my + a.Ly;
+  const int64_t total = czt_axis_elems(a.nx, a.mx, a.Lx, a.Sx, a.dz) + czt_axis_elems(a.ny, a.my, a.Ly, a.Sy, a.dz);
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 1024);
   {
   LaunchScope ls("czt_tables", s);
@@ -208,15 +229,16 @@ xl_status czt_tables<XL_REAL>(void* tab, const CztTabArgs& a, cudaStream_t s) {
   }
   XL_CUDA_TRY(cudaGetLastError());
   C* t = (C*)tab;
-  XL_TRY(bhat<XL_REAL>(a.Lx, t + a.nx + a.mx, a.Lx, s));
-  XL_TRY(bhat<XL_REAL>(a.Ly, t + a.off_y + a.ny + a.my, a.Ly, s));
+  const int rx = (a.dz ? 2 : 1) * a.Sx, ry = (a.dz ? 2 : 1) * a.Sy;
+  XL_TRY(bhat<XL_REAL>(a.Lx, t + a.nx + a.mx, a.Lx, rx, s));
+  XL_TRY(bhat<XL_REAL>(a.Ly, t + a.off_y + a.ny + a.my, a.Ly, ry, s));
   return XL_OK;
 }
 
 template <>
 xl_status asczt_tables<XL_REAL>(void* tab, const CztTabArgs& a, cudaStream_t s) {
   typedef cplx<XL_REAL> C;
-  const int64_t total = (int64_t)a.nx + a.mx + a.Lx + a.ny + a.my + a.Ly;
+  const int64_t total = czt_axis_elems(a.nx, a.mx, a.Lx, a.Sx, 0) + czt_axis_elems(a.ny, a.my, a.Ly, a.Sy, 0);
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 1024);
   {
     LaunchScope ls("asczt_tables", s);
@@ -224,8 +246,8 @@ xl_status asczt_tables<XL_REAL>(void* tab, const CztTabArgs& a, cudaStream_t s) 
   }
   XL_CUDA_TRY(cudaGetLastError());
   C* t = (C*)tab;
-  XL_TRY(bhat<XL_REAL>(a.Lx, t + a.nx + a.mx, a.Lx, s));
-  XL_TRY(bhat<XL_REAL>(a.Ly, t + a.off_y + a.ny + a.my, a.Ly, s));
+  XL_TRY(bhat<XL_REAL>(a.Lx, t + a.nx + a.mx, a.Lx, a.Sx, s));
+  XL_TRY(bhat<XL_REAL>(a.Ly, t + a.off_y + a.ny + a.my, a.Ly, a.Sy, s));
   return XL_OK;
 }
 

@@ -18,12 +18,6 @@
 namespace xl {
 namespace {
 
-int czt_length(int n, int m) {
-  int L = 64;
-  while (L < n + m - 1) L <<= 1;
-  return L;
-}
-
 struct DevBuf {
   void* p = nullptr;
   ~DevBuf() {
@@ -97,9 +91,12 @@ xl_status tune_grid(const xl_grid* g, const xl_window* w, int dtype, int reps, c
   }
   if (w) {
     const int mx = w->mx, my = w->my;
-    const int Lx = czt_length(nx, mx), Ly = czt_length(ny, my);
-    if (Lx > 8192 || Ly > 8192) return fail(XL_ERR_UNSUPPORTED, "autotune: N + M - 1 > 8192");
-    const int tab_n = std::max(std::max(nx, ny), std::max(std::max(mx, my), std::max(Lx, Ly)));
+    const CztAxisPlan px = czt_axis_plan(nx, mx, (int)cs, false, false);
+    const CztAxisPlan py = czt_axis_plan(ny, my, (int)cs, false, false);
+    if (px.L == 0 || py.L == 0) return fail(XL_ERR_UNSUPPORTED, "autotune: no CZT plan fits");
+    const int Lx = px.L, Ly = py.L;
+    const int64_t tab_n = std::max<int64_t>(std::max(std::max(nx, ny), std::max(mx, my)),
+                                            std::max((int64_t)px.S * Lx, (int64_t)py.S * Ly));
     const int np = std::min(tune_planes((size_t)std::max(nx, mx) * ny * cs), kCztRun);
     DevBuf in, Tb, out, tab;
     XL_TRY(in.alloc((size_t)np * nx * ny * cs, s));
@@ -108,13 +105,16 @@ xl_status tune_grid(const xl_grid* g, const xl_window* w, int dtype, int reps, c
     XL_TRY(tab.alloc((size_t)tab_n * cs, s));  // zero chirps: the timing does not depend on values
     Axis<C> ax1;
     ax1.pre = ax1.post = ax1.bhat = (const C*)tab.p;
-    const AxisRun<C> ax = axis_run(ax1);
+    ax1.b2hat = nullptr;
+    const AxisRun<C> ax = axis_run(ax1, px.S, px.seg);
+    const AxisRun<C> ay = axis_run(ax1, py.S, py.seg);
     CztDims d;
     std::memset(&d, 0, sizeof(d));
     d.nx = nx; d.ny = ny; d.mx = mx; d.my = my;
     d.dx = g->dx; d.dy = g->dy; d.dxo = w->dxo; d.dyo = w->dyo;
     d.z[0] = 1.0;
     d.in_planes = 1;
+    d.tb_elem = (int64_t)mx * ny;
     if (Lx >= kTuneMinL) {
       XL_TRY(tune_one(TUNE_CZT_FWD_X, Lx, dtype, reps, s,
                       [&] { return czt_pass<T>(CZT_FWD_X, false, Lx, in.p, Tb.p, d, ax, np, s); }));
@@ -125,10 +125,10 @@ xl_status tune_grid(const xl_grid* g, const xl_window* w, int dtype, int reps, c
     }
     if (Ly >= kTuneMinL) {
       XL_TRY(tune_one(TUNE_CZT_FWD_Y, Ly, dtype, reps, s,
-                      [&] { return czt_pass<T>(CZT_FWD_Y, false, Ly, Tb.p, out.p, d, ax, np, s); }));
+                      [&] { return czt_pass<T>(CZT_FWD_Y, false, Ly, Tb.p, out.p, d, ay, np, s); }));
       d.adjoint = 1;
       XL_TRY(tune_one(TUNE_CZT_ADJ_Y, Ly, dtype, reps, s,
-                      [&] { return czt_pass<T>(CZT_ADJ_Y, false, Ly, out.p, Tb.p, d, ax, np, s); }));
+                      [&] { return czt_pass<T>(CZT_ADJ_Y, false, Ly, out.p, Tb.p, d, ay, np, s); }));
       d.adjoint = 0;
     }
   }

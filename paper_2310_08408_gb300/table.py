@@ -30,9 +30,11 @@ class TableGeometry:
     f: float             # lens focal length = VCZT distance
 
 
-def table_loss(geo: TableGeometry, src, phi1, phi2, theta, z1, z2):
+def table_loss(geo: TableGeometry, src, phi1, phi2, theta, z1, z2, checkpoint=False):
     """src [B][1][ny][nx] complex; phi1, phi2 [B][ny][nx] real; theta, z1, z2 float64 [B].
-    Returns the loss per setup [B] (float64)."""
+    Returns the loss per setup [B] (float64). checkpoint: the RS and VRS stages keep their input
+    fields for the distance gradients instead of their input spectra (three planes a setup
+    instead of twelve; the adjoints transform the inputs again)."""
     B = src.shape[0]
     dev = src.device
     zero = torch.zeros(B, dtype=torch.float64, device=dev)
@@ -42,7 +44,7 @@ def table_loss(geo: TableGeometry, src, phi1, phi2, theta, z1, z2):
     a0 = A.elements(src, g, lam, [xl.SLM], [(phi1, None)], p1, 1)
     # RS over z1
     # the camera loss ignores a constant phase on every plane (phase_invariant distance gradients)
-    a1 = A.RSPropagate.apply(a0[:, 0], z1, g, lam, True)[:, None]
+    a1 = A.RSPropagate.apply(a0[:, 0], z1, g, lam, True, checkpoint)[:, None]
     # SLM2, to-vector, half-wave plate (eta = pi) at theta
     wp = torch.stack([zero, zero, zero + math.pi, theta], dim=1)
     p2 = torch.stack([torch.zeros_like(wp), torch.zeros_like(wp), wp], dim=1).contiguous()
@@ -50,7 +52,7 @@ def table_loss(geo: TableGeometry, src, phi1, phi2, theta, z1, z2):
                                                                        (None, None)], p2, 1)
     # VRS over z2 (Ex, Ey, Ez); the lens acts on all three components; VCZT propagates the
     # transverse ones and re-forms Ez on the camera window (the input Ez plane is not used)
-    a3 = A.VRSPropagate.apply(a2, z2, g, lam, True)
+    a3 = A.VRSPropagate.apply(a2, z2, g, lam, True, checkpoint)
     pl = torch.zeros((B, 1, 4), dtype=torch.float64, device=dev)
     pl[:, 0, 0] = geo.f
     a4 = A.elements(a3, g, lam, [xl.LENS], [(None, None)], pl, 3)

@@ -22,6 +22,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_UNSUPPORTED, ERR_TIMEOUT, ERR_NONFINITE = 
 C64, C128 = 0, 1
 Z_DEVICE = 1
 PHASE_INVARIANT = 2
+ACCUMULATE = 4
 
 _lock = threading.Lock()
 _lib = None
@@ -74,7 +75,8 @@ class TableConfig(ctypes.Structure):
     """xl_table_config of the batched optical-table optimiser."""
     _fields_ = [("wavelength", ctypes.c_double), ("extent", ctypes.c_double), ("w0", ctypes.c_double),
                 ("f", ctypes.c_double), ("cam_width", ctypes.c_double), ("lr", ctypes.c_double),
-                ("lr_z", ctypes.c_double), ("cam_m", ctypes.c_int32), ("dtype", ctypes.c_int32)]
+                ("lr_z", ctypes.c_double), ("cam_m", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("checkpoint", ctypes.c_int32)]
 
 
 BATCH_LOSS, BATCH_SCALARS, BATCH_GRAD_SCALARS, BATCH_PHI1, BATCH_PHI2, BATCH_GRAD_PHI1, BATCH_GRAD_PHI2 = range(7)
@@ -132,8 +134,12 @@ SIGNATURES = {
     "xl_batch_step": ([_P, _I, _P], _I),
     "xl_batch_read": ([_P, _I, _I, _P, _P], _I),
     "xl_batch_grid": ([_P, _I], _I),
+    "xl_batch_memory": ([_P], ctypes.c_int64),
     "xl_batch_destroy": ([_P], _I),
-    "xl_czt_propagate_backward": ([_P, _P, _I, _I, _GP, _WP, _D, _P, _I, _I, _P], _I),
+    "xl_czt_propagate_backward": ([_P, _P, _P, _P, _I, _I, _GP, _WP, _D, _P, _I, _I, _P], _I),
+    "xl_czt_save_elems": ([_GP, _WP, _I, _I], ctypes.c_int64),
+    "xl_czt_propagate_save": ([_P, _P, _P, _I, _I, _GP, _WP, _D, _P, _I, _I, _P], _I),
+    "xl_czt_propagate_backward_saved": ([_P, _P, _P, _P, _P, _I, _I, _GP, _WP, _D, _P, _I, _I, _P], _I),
 }
 
 
@@ -366,9 +372,11 @@ def vrs_propagate_backward(g_exyz: torch.Tensor, exy_in: torch.Tensor | None, gr
 
 
 def czt_propagate(u: torch.Tensor, grid, window, wavelength: float, z, vectorial=False,
-                  out: torch.Tensor | None = None):
+                  out: torch.Tensor | None = None, saved: torch.Tensor | None = None):
     """CZT onto a window: [B][ny][nx] -> [B][my][mx]; vectorial (1): [B][2][ny][nx] ->
-    [B][3][my][mx]; vectorial 2: [B][3][ny][nx] (Ez unused) -> [B][3][my][mx]."""
+    [B][3][my][mx]; vectorial 2: [B][3][ny][nx] (Ez unused) -> [B][3][my][mx].
+    saved: optional buffer (czt_save_buffer) that receives what the adjoint's distance gradient
+    needs (xl_czt_propagate_save)."""
     _dev(u, "u")
     vectorial = int(vectorial)
     comps = {0: 1, 1: 2, 2: 3}[vectorial]
@@ -378,27 +386,75 @@ def czt_propagate(u: torch.Tensor, grid, window, wavelength: float, z, vectorial
         lead = u.shape[:-2] if not vectorial else (u.shape[:-3] + (3,))
         out = torch.empty(tuple(lead) + (w.my, w.mx), dtype=u.dtype, device=u.device)
     zz = _Z(z, B)
+    if saved is not None:
+        _check(load().xl_czt_propagate_save(u.data_ptr(), _dev(out, "out").data_ptr(),
+                                            _dev(saved, "saved").data_ptr(), B, int(vectorial),
+                                            ctypes.byref(g), ctypes.byref(w), float(wavelength),
+                                            zz.ptr, zz.flags, _dtype(u), _stream()))
+        return out
     _check(load().xl_czt_propagate(u.data_ptr(), _dev(out, "out").data_ptr(), B, int(vectorial),
                                    ctypes.byref(g), ctypes.byref(w), float(wavelength), zz.ptr,
                                    zz.flags, _dtype(u), _stream()))
     return out
 
 
+def czt_save_buffer(u: torch.Tensor, grid, window, vectorial=False) -> torch.Tensor:
+    """Buffer for what a forward CZT saves for its adjoint's distance gradient:
+    [B][xl_czt_save_elems] of the field's dtype."""
+    vectorial = int(vectorial)
+    comps = {0: 1, 1: 2, 2: 3}[vectorial]
+    B, ny, nx = _planes(u, comps, "u")
+    g, w = Grid.of(grid), Window.of(window)
+    n = int(load().xl_czt_save_elems(ctypes.byref(g), ctypes.byref(w), vectorial, _dtype(u)))
+    if n < 0:
+        raise XLError(ERR_UNSUPPORTED, "czt_save_buffer: unsupported sizes")
+    return torch.empty((B, n), dtype=u.dtype, device=u.device)
+
+
 def czt_propagate_backward(g_out: torch.Tensor, grid, window, wavelength: float, z,
-                           vectorial=False):
-    """Adjoint of czt_propagate: window gradient -> input-grid gradient."""
+                           vectorial=False, u_in: torch.Tensor | None = None,
+                           want_dz: bool = False, want_field: bool = True,
+                           phase_invariant: bool = False, saved: torch.Tensor | None = None,
+                           g_in: torch.Tensor | None = None, g_z: torch.Tensor | None = None,
+                           accumulate: bool = False):
+    """Adjoint of czt_propagate: window gradient -> input-grid gradient. With want_dz (needs
+    u_in, the forward's input) returns (g_in or None, g_z [B] float64); otherwise g_in.
+    saved: the buffer a czt_propagate(..., saved=...) call filled (else the sums are formed
+    here, at the cost of one forward). g_in / g_z: output tensors to use; accumulate: add the
+    results to them (XL_ACCUMULATE)."""
     _dev(g_out, "g_out")
     vectorial = int(vectorial)
     comps = 3 if vectorial else 1
     B, my, mx = _planes(g_out, comps, "g_out")
     g, w = Grid.of(grid), Window.of(window)
     lead = g_out.shape[:-2] if not vectorial else (g_out.shape[:-3] + ({1: 2, 2: 3}[vectorial],))
-    g_in = torch.empty(tuple(lead) + (g.ny, g.nx), dtype=g_out.dtype, device=g_out.device)
+    if accumulate and ((want_field or not want_dz) and g_in is None or want_dz and g_z is None):
+        raise ValueError("czt_propagate_backward: accumulate needs the output tensors")
+    if (want_field or not want_dz) and g_in is None:
+        g_in = torch.empty(tuple(lead) + (g.ny, g.nx), dtype=g_out.dtype, device=g_out.device)
+    if not (want_field or not want_dz):
+        g_in = None
+    if want_dz and g_z is None:
+        g_z = torch.empty(B, dtype=torch.float64, device=g_out.device)
+    if not want_dz:
+        g_z = None
+    if want_dz and u_in is None:
+        raise ValueError("czt_propagate_backward: want_dz needs u_in")
     zz = _Z(z, B)
-    _check(load().xl_czt_propagate_backward(g_out.data_ptr(), g_in.data_ptr(), B, int(vectorial),
-                                            ctypes.byref(g), ctypes.byref(w), float(wavelength),
-                                            zz.ptr, zz.flags, _dtype(g_out), _stream()))
-    return g_in
+    flags = zz.flags | (PHASE_INVARIANT if phase_invariant else 0) | (ACCUMULATE if accumulate else 0)
+    uptr = _dev(u_in, "u_in").data_ptr() if u_in is not None else None
+    gin_ptr = g_in.data_ptr() if g_in is not None else None
+    gz_ptr = g_z.data_ptr() if g_z is not None else None
+    if saved is not None:
+        _check(load().xl_czt_propagate_backward_saved(
+            g_out.data_ptr(), uptr, _dev(saved, "saved").data_ptr(), gin_ptr, gz_ptr, B,
+            int(vectorial), ctypes.byref(g), ctypes.byref(w), float(wavelength), zz.ptr, flags,
+            _dtype(g_out), _stream()))
+    else:
+        _check(load().xl_czt_propagate_backward(
+            g_out.data_ptr(), uptr, gin_ptr, gz_ptr, B, int(vectorial), ctypes.byref(g),
+            ctypes.byref(w), float(wavelength), zz.ptr, flags, _dtype(g_out), _stream()))
+    return (g_in, g_z) if want_dz else g_in
 
 
 # ----------------------------------------------------------------------------- elements
@@ -739,14 +795,17 @@ def step_advance(t: torch.Tensor) -> None:
 # ----------------------------------------------------------------------------- batched tables
 class Batch:
     """Many optical-table setups optimised together (xl_batch_*). cfg: dict with wavelength,
-    extent, w0, f, cam_m, cam_width, lr, lr_z, dtype ("c64" / "c128"); grid_n: list of N per
-    setup; init: [n][3] = (theta, z1, z2)."""
+    extent, w0, f, cam_m, cam_width, lr, lr_z, dtype ("c64" / "c128"), checkpoint (0: the RS /
+    VRS adjoints read spectra the forwards keep; 1: only the plane fields are kept and the
+    adjoints transform their inputs again); grid_n: list of N per setup; init: [n][3] =
+    (theta, z1, z2)."""
 
     def __init__(self, cfg: dict, grid_n, init, seed: int):
         self.cfg = TableConfig(float(cfg["wavelength"]), float(cfg["extent"]), float(cfg["w0"]),
                                float(cfg["f"]), float(cfg["cam_width"]), float(cfg["lr"]),
                                float(cfg["lr_z"]), int(cfg["cam_m"]),
-                               C128 if cfg.get("dtype", "c64") == "c128" else C64)
+                               C128 if cfg.get("dtype", "c64") == "c128" else C64,
+                               int(cfg.get("checkpoint", 0)))
         self.n = len(grid_n)
         gn = np.ascontiguousarray(grid_n, dtype=np.int32)
         ini = np.ascontiguousarray(init, dtype=np.float64).reshape(self.n, 3)
@@ -761,6 +820,10 @@ class Batch:
 
     def grid(self, setup: int) -> int:
         return int(load().xl_batch_grid(self.h, setup))
+
+    def memory(self) -> int:
+        """Device bytes the batch's own buffers hold."""
+        return int(load().xl_batch_memory(self.h))
 
     def read(self, what: int, setup: int) -> np.ndarray:
         n = self.grid(setup)

@@ -34,10 +34,12 @@ def _oracle(setup, phi1, phi2, dtype):
     return L, otable.backward(t, src, phi1, phi2, th, z1, z2, planes)
 
 
+@pytest.mark.parametrize("checkpoint", [0, 1])
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
-def test_batch_step_matches_oracle_table(dtype):
+def test_batch_step_matches_oracle_table(dtype, checkpoint):
+    """Both checkpointing modes: spectra kept by the forwards (0), plane fields only (1)."""
     xl = lib()
-    b = xl.Batch(dict(CFG, dtype=dtype), GRIDS, INIT, SEED)
+    b = xl.Batch(dict(CFG, dtype=dtype, checkpoint=checkpoint), GRIDS, INIT, SEED)
     tol_l, tol_g = (TOL_LOSS, 1e-3) if dtype == "c64" else (1e-10, 1e-8)
     phis = []
     for s in range(len(GRIDS)):
@@ -78,3 +80,22 @@ def test_batch_graph_replay_equals_eager_steps():
         assert eager.read(xl.BATCH_LOSS, s)[0] == graph.read(xl.BATCH_LOSS, s)[0]
     eager.close()
     graph.close()
+
+
+def test_batch_checkpoint_mode_memory_and_steps():
+    """Plane-field checkpointing holds about half the memory of the spectra mode (12 of its 29
+    field planes a setup are the kept spectra) and steps to the same optimiser state within the
+    complex64 gradient tolerance after several steps."""
+    xl = lib()
+    a = xl.Batch(dict(CFG, checkpoint=0), GRIDS, INIT, SEED)
+    c = xl.Batch(dict(CFG, checkpoint=1), GRIDS, INIT, SEED)
+    assert c.memory() < 0.6 * a.memory(), (c.memory(), a.memory())
+    for _ in range(3):
+        a.step(use_graph=True)
+        c.step(use_graph=True)
+    for s in range(len(GRIDS)):
+        assert abs(a.read(xl.BATCH_LOSS, s)[0] - c.read(xl.BATCH_LOSS, s)[0]) <= TOL_LOSS * a.read(xl.BATCH_LOSS, s)[0]
+        assert rel(c.read(xl.BATCH_GRAD_PHI1, s), a.read(xl.BATCH_GRAD_PHI1, s)) < 1e-3
+        assert np.allclose(c.read(xl.BATCH_SCALARS, s), a.read(xl.BATCH_SCALARS, s), rtol=1e-6, atol=1e-9)
+    a.close()
+    c.close()

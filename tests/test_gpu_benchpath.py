@@ -8,8 +8,9 @@ at z = 0.5, 2 and 10 mm in ONE batched call (so the per-element spectra and chir
 mixed-distance launches are exercised), are compared pixel by pixel with the oracle's FFT
 realisation of the RS convolution and its direct separable CZT sums. The vectorial workload
 (VRS and VCZT at 2048^2, z = 5 mm, radially polarised Gaussian and a random Jones field) is
-compared the same way. Paper passages: Methods, "Features and performance" (RS, VRS, CZT on
-2048^2 grids; the propagation benchmark of the Introduction's speed-up figure).
+compared the same way, and so is one whole gradient step of the benchmark (its own step object)
+against the oracle's composition. Paper passages: Methods, "Features and performance" (RS, VRS,
+CZT on 2048^2 grids; the propagation benchmark of the Introduction's speed-up figure).
 
 Bars: relative L2 over every pixel <= 2e-5 for fields; <= 1e-3 relative for distance gradients.
 """
@@ -127,3 +128,24 @@ def test_vczt_2048_to_512_full_window_forward_adjoint():
         assert rel(out[b], oracle.vczt(e, g.astuple(), win.astuple(), lam, z)) < TOL_C64, b
         ref = oracle.vczt_adjoint(Gh[b].astype(np.complex128), g.astuple(), win.astuple(), lam, z)
         assert rel(gi[b], ref) < TOL_C64, b
+
+
+def test_benchmark_gradient_step_against_oracle_composition():
+    """One step of the benchmark's gradient evaluation (SLM -> RS and CZT -> spot-size losses ->
+    adjoints with dL/dz -> mask gradient -> Adam) on the three fields at 0.5, 2 and 10 mm, run by
+    the benchmark's own step object, against the same composition in FP64 by the oracle: the two
+    losses (1e-4), the phase-invariant dL/dz (1e-3) and the mask gradient (relative L2 1e-3)."""
+    import torch
+    import bench
+    xl = lib()
+    g, win, u, _, _ = _rs2048_fields()
+    step = bench.GpuStep(xl, torch, g, win, to_dev(u, np.complex64), ZS)
+    lA, lC, gz, gphi = (to_np(t) for t in step.run())
+    xl.device_status()
+    for b in range(len(ZS)):
+        st = (np.zeros((g.ny, g.nx)), np.zeros((g.ny, g.nx)), 0)
+        _, _, ref = bench.oracle_step(u[b], np.zeros((g.ny, g.nx)), g, win, ZS[b], st)
+        assert abs(lA[b] - ref["loss_a"]) <= 1e-4 * abs(ref["loss_a"]), b
+        assert abs(lC[b] - ref["loss_c"]) <= 1e-4 * abs(ref["loss_c"]), b
+        assert abs(gz[b] - ref["dz"]) <= 1e-3 * abs(ref["dz"]), (b, gz[b], ref["dz"])
+        assert rel(gphi[b], ref["gphi"]) < 1e-3, b

@@ -16,7 +16,7 @@ from gpu_util import TOL_LOSS, lib, rel, to_dev, to_np
 pytestmark = pytest.mark.gpu
 
 
-def _run(n, pitch, lam, w0, z1, z2, theta, f, m, width, seed, dtype, rdtype):
+def _run(n, pitch, lam, w0, z1, z2, theta, f, m, width, seed, dtype, rdtype, checkpoint=False):
     import torch
     lib()
     from paper_2310_08408_gb300 import table
@@ -32,7 +32,7 @@ def _run(n, pitch, lam, w0, z1, z2, theta, f, m, width, seed, dtype, rdtype):
     Z1 = torch.tensor([z1], dtype=torch.float64, device="cuda", requires_grad=True)
     Z2 = torch.tensor([z2], dtype=torch.float64, device="cuda", requires_grad=True)
     S = to_dev(src[None, None].astype(dtype), dtype)
-    loss = table.table_loss(geo, S, P1, P2, th, Z1, Z2)
+    loss = table.table_loss(geo, S, P1, P2, th, Z1, Z2, checkpoint=checkpoint)
     loss.sum().backward()
     # oracle on the same rounded inputs
     t = otable.Table(g.astuple(), win.astuple(), lam, f)
@@ -46,10 +46,13 @@ def _run(n, pitch, lam, w0, z1, z2, theta, f, m, width, seed, dtype, rdtype):
             float(to_np(Z2.grad)[0]), gr["z2"])
 
 
+@pytest.mark.parametrize("checkpoint", [False, True])
 @pytest.mark.parametrize("dtype,rdtype,tl,tg", [(np.complex64, np.float32, TOL_LOSS, 1e-3),
                                                 (np.complex128, np.float64, 1e-10, 1e-8)])
-def test_table_small(dtype, rdtype, tl, tg):
-    r = _run(64, 1.0, 0.6328, 12.0, 300.0, 250.0, 0.3, 800.0, 40, 48.0, 31, dtype, rdtype)
+def test_table_small(dtype, rdtype, tl, tg, checkpoint):
+    """Both ways of keeping what the distance gradients need: input spectra, or the plane fields
+    with the spectra recomputed in the adjoints (checkpoint)."""
+    r = _run(64, 1.0, 0.6328, 12.0, 300.0, 250.0, 0.3, 800.0, 40, 48.0, 31, dtype, rdtype, checkpoint)
     Lg, Lo, g1, o1, g2, o2, gt, ot, gz1, oz1, gz2, oz2 = r
     assert abs(Lg - Lo) / abs(Lo) < tl
     assert rel(g1, o1) < tg and rel(g2, o2) < tg
