@@ -790,15 +790,22 @@ def main():
     # RS / CZT units are ALU-bound at their algorithmic bytes), with the HBM fraction of the
     # per-unit algorithmic bytes beside it
     roof = None
-    if prof:
-        name, (cnt, tot) = max(prof.items(), key=lambda kv: kv[1][1])
+    modelled = {k: v for k, v in prof.items() if kernel_model(k, 1.0)[1] is not None}
+    if modelled:
+        name, (cnt, tot) = max(modelled.items(), key=lambda kv: kv[1][1])
         avg_s = tot / cnt / 1000.0
         fpl = fields_per_launch(name, cnt)
         fl, nb = kernel_model(name, fpl)
         unit = "rs" if name.startswith("rs_") else "czt"
         unit_bytes = fpl * (UNIT_BYTES["rs_adj_dz"] if "m4" in name else UNIT_BYTES[unit])
         traffic = traffic_pf[name] * fpl if name in traffic_pf else None
-        if fl is not None:
+        if fl is None:  # a bandwidth kernel (elements, loss, Adam): its bytes against HBM
+            ach = nb / avg_s / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "traffic": traffic, "kernel": name, "share": tot / total if total else None,
+                    "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                    "traffic_ratio": (traffic / nb) if traffic else None}
+        else:
             ach = fl / avg_s / 1e12
             roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": ach / fp32_peak, "traffic": traffic, "kernel": name,

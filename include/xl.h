@@ -426,9 +426,11 @@ xl_status xl_device_status(void* stream);
  * Autotuner of the transposing row passes (the batch scheduler's launch plan; the paper has no
  * counterpart: its JAX/XLA back end picks launch shapes itself). Families (XL_TUNE_*): RS passes
  * 1 and 3 and the four CZT window passes; variants: 0 the built-in rows per block, 1 half as
- * many, 2 twice as many where a block stays within 1024 threads and an SM's shared memory. All
- * variants give bit-identical results; only speed differs. Rows shorter than 1024 always use
- * variant 0. Choices are process-wide (host memory).
+ * many, 2 twice as many where a block stays within 1024 threads and an SM's shared memory; these
+ * give bit-identical results (rows shorter than 1024 always use variant 0). The complex64 scalar
+ * CZT passes of lengths 512, 1024 and 2048 have two more: the built-in rows with FFT radix plan 1
+ * (3) or plan 2 (4), the transform's radix-2/4/8 stage first or second instead of last (equal
+ * results within rounding). Choices are process-wide (host memory).
  * -------------------------------------------------------------------------------------------*/
 #define XL_TUNE_RS_PASS1 0
 #define XL_TUNE_RS_PASS3 1
@@ -443,7 +445,7 @@ xl_status xl_device_status(void* stream);
  * enough planes (up to 16) that its data exceeds L2, as batched calls do. */
 xl_status xl_autotune(const xl_grid* grid, const xl_window* window, int32_t dtype, int32_t reps,
                       void* stream);
-/* The variant used for (family, row length L, dtype): 0..2, or -1 for an unknown family. */
+/* The variant used for (family, row length L, dtype): 0..4, or -1 for an unknown family. */
 int32_t xl_tune_get(int32_t family, int32_t L, int32_t dtype);
 /* Sets a variant by hand (XL_ERR_ARG for an unknown family, L, dtype or variant). */
 xl_status xl_tune_set(int32_t family, int32_t L, int32_t dtype, int32_t variant);

@@ -16,12 +16,13 @@ xl_status pass_LVV(int which, const void* src, void* dst, const CztDims& d, cons
   const size_t sm = czt_smem_bytes<L, sizeof(C), VEC, V>(ax.nseg > 1, DZ && fwd);
   if (sm > (size_t)227 * 1024) return fail(XL_ERR_UNSUPPORTED, "czt: segment plan exceeds shared memory");
   const void* tw;
-  XL_TRY(twiddles(L, sizeof(T) == 8 ? XL_C128 : XL_C64, &tw));
+  XL_TRY(twiddles(L, sizeof(T) == 8 ? XL_C128 : XL_C64, czt_plan_of<V>(), &tw));
   const C* twc = (const C*)tw;
   const dim3 blk(ROWS * (L / 16));
   const CztSaved<C> sv = dz ? dz->sv : CztSaved<C>{nullptr, 0, 0, 0, 0};
   double* dzp = dz ? dz->dzp : nullptr;
-  const std::string tag = std::string(VEC ? "_vec<" : "<") + std::to_string(L) + ">" + (DZ ? "_dz" : "");
+  const std::string tag = std::string(VEC ? "_vec<" : "<") + std::to_string(L) + ">" + (DZ ? "_dz" : "") +
+                          (czt_plan_of<V>() ? "_p" + std::to_string(czt_plan_of<V>()) : "");
   int gx = 0;
   switch (which) {
     case CZT_FWD_X:
@@ -71,13 +72,27 @@ xl_status pass_LVV(int which, const void* src, void* dst, const CztDims& d, cons
 template <typename T, int L, bool VEC>
 xl_status pass_LV(int which, const void* src, void* dst, const CztDims& d, const AxisRun<cplx<T>>& ax,
                   int nb, cudaStream_t s, const CztDzArgs<cplx<T>>* dz, int* blocks) {
-  if (dz && dz->on) return pass_LVV<T, L, VEC, 0, true>(which, src, dst, d, ax, nb, s, dz, blocks);
+  constexpr int CS = sizeof(cplx<T>);
+  const int fam = which == CZT_FWD_X ? TUNE_CZT_FWD_X : which == CZT_FWD_Y ? TUNE_CZT_FWD_Y
+                : which == CZT_ADJ_X ? TUNE_CZT_ADJ_X : TUNE_CZT_ADJ_Y;
+  const int var = (!VEC && L >= 512) ? tuned_variant(fam, L, sizeof(T) == 8 ? XL_C128 : XL_C64) : 0;
+  // radix-plan variants (complex64 scalar passes of the lengths with an odd stage); the
+  // distance-gradient forms follow the plan, not the rows variants
+  constexpr bool PLANS = CS == 8 && !VEC && (L == 512 || L == 1024 || L == 2048);
+  if (dz && dz->on) {
+    if constexpr (PLANS) {
+      if (var == 3) return pass_LVV<T, L, VEC, 3, true>(which, src, dst, d, ax, nb, s, dz, blocks);
+      if (var == 4) return pass_LVV<T, L, VEC, 4, true>(which, src, dst, d, ax, nb, s, dz, blocks);
+    }
+    return pass_LVV<T, L, VEC, 0, true>(which, src, dst, d, ax, nb, s, dz, blocks);
+  }
+  if constexpr (PLANS) {
+    if (var == 3) return pass_LVV<T, L, VEC, 3, false>(which, src, dst, d, ax, nb, s, nullptr, blocks);
+    if (var == 4) return pass_LVV<T, L, VEC, 4, false>(which, src, dst, d, ax, nb, s, nullptr, blocks);
+  }
   if constexpr (!VEC && L >= kTuneMinL) {
-    const int fam = which == CZT_FWD_X ? TUNE_CZT_FWD_X : which == CZT_FWD_Y ? TUNE_CZT_FWD_Y
-                  : which == CZT_ADJ_X ? TUNE_CZT_ADJ_X : TUNE_CZT_ADJ_Y;
-    constexpr int CS = sizeof(cplx<T>);
     const bool multi = ax.nseg > 1;
-    switch (tuned_variant(fam, L, sizeof(T) == 8 ? XL_C128 : XL_C64)) {
+    switch (var) {
       case 1:
         if (czt_smem_bytes<L, CS, VEC, 1>(multi) <= (size_t)227 * 1024)
           return pass_LVV<T, L, VEC, 1, false>(which, src, dst, d, ax, nb, s, nullptr, blocks);

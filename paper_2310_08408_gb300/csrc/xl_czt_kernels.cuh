@@ -139,6 +139,8 @@ template <typename C> struct CztSaved {
 // spilled 400-600 bytes a thread.
 // Scalar passes also build the autotuner's variants V (rows per block: 1 = half the default,
 // 2 = twice the default where a block stays within 1024 threads and an SM's shared memory).
+// Variants 3 and 4 keep the default rows and use radix plans 1 and 2 (xl_fft.cuh).
+template <int V> __host__ __device__ constexpr int czt_plan_of() { return V >= 3 ? V - 2 : 0; }
 template <int L, int CS, bool VEC = false, int V = 0> __host__ __device__ constexpr int czt_rows() {
   constexpr int r = CS == 8 ? (L >= 4096 ? 2 : ((4096 / L) > 4 ? 4096 / L : 4))
                             : (L >= 8192 ? 1 : ((4096 / L) > 2 ? 4096 / L : 2));
@@ -179,11 +181,11 @@ template <int L, int CS, bool VEC, int V = 0, bool DZ = false> __host__ __device
 // the inverse transform's loads and address arithmetic into the forward transform (with both
 // transforms in one block, two back-to-back transforms of length 4096 spilled about 500 bytes a
 // thread at the 64-register budget that two 512-thread blocks per SM allow).
-template <int L, typename C>
+template <int L, int PLAN = 0, typename C>
 __device__ __forceinline__ void chirp_conv(C (&v)[16], C* row, int t, const C* __restrict__ tw,
                                            const C* __restrict__ bhat, bool cj) {
   constexpr int TT = L / 16;
-  team_fft<L, -1>(v, row, t, tw);
+  team_fft<L, -1, PLAN>(v, row, t, tw);
   if (cj) {
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = cmulc(v[q], __ldg(bhat + t + q * TT));
@@ -191,20 +193,20 @@ __device__ __forceinline__ void chirp_conv(C (&v)[16], C* row, int t, const C* _
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = cmul(v[q], __ldg(bhat + t + q * TT));
   }
-  team_fft<L, +1>(v, row, t, tw);
+  team_fft<L, +1, PLAN>(v, row, t, tw);
 }
 
 // Segmented convolution in the forward direction (grid side in, window side out):
 // v = IDFT(sum_s bhat_s DFT(a_s)), where load(s, v) fills v with segment s of the pre-chirped
 // input (zero beyond the segment). With more than one segment the running sum lives in the
 // thread's stash row `acc`. DZ: also a2 = sum_s b2hat_s DFT(a_s) in stash row `a2`.
-template <int L, bool DZ, typename C, typename Load, typename St>
+template <int L, bool DZ, int PLAN = 0, typename C, typename Load, typename St>
 __device__ __forceinline__ void seg_conv_fwd(C (&v)[16], C* row, int t, const C* __restrict__ tw,
                                              const Axis<C>& ax, int nseg, bool cj, Load&& load,
                                              St& acc, St& a2) {
   constexpr int TT = L / 16;
   load(0, v);
-  team_fft<L, -1>(v, row, t, tw);
+  team_fft<L, -1, PLAN>(v, row, t, tw);
   if constexpr (DZ) {
 #pragma unroll
     for (int q = 0; q < 16; ++q) a2.set(q, cmul(v[q], __ldg(ax.b2hat + t + q * TT)));
@@ -222,7 +224,7 @@ __device__ __forceinline__ void seg_conv_fwd(C (&v)[16], C* row, int t, const C*
 #pragma unroll 1
     for (int s = 1; s < nseg; ++s) {
       load(s, v);
-      team_fft<L, -1>(v, row, t, tw);
+      team_fft<L, -1, PLAN>(v, row, t, tw);
       if constexpr (DZ) {
         const C* b2 = ax.b2hat + (int64_t)s * L;
 #pragma unroll
@@ -240,19 +242,19 @@ __device__ __forceinline__ void seg_conv_fwd(C (&v)[16], C* row, int t, const C*
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = acc.get(q);
   }
-  team_fft<L, +1>(v, row, t, tw);
+  team_fft<L, +1, PLAN>(v, row, t, tw);
 }
 
 // Segmented convolution in the adjoint direction (window side in, grid side out): F = DFT(v),
 // then per segment s, v = IDFT(F conj(bhat_s)) handed to store(s, v). spec(F) sees the
 // transform first (the distance gradient's Parseval term). With more than one segment F is kept
 // in the thread's stash row.
-template <int L, typename C, typename Spec, typename Store, typename St>
+template <int L, int PLAN = 0, typename C, typename Spec, typename Store, typename St>
 __device__ __forceinline__ void seg_conv_adj(C (&v)[16], C* row, int t, const C* __restrict__ tw,
                                              const Axis<C>& ax, int nseg, bool cj, Spec&& spec,
                                              Store&& store, St& F) {
   constexpr int TT = L / 16;
-  team_fft<L, -1>(v, row, t, tw);
+  team_fft<L, -1, PLAN>(v, row, t, tw);
   spec(v);
   if (nseg > 1) {
 #pragma unroll
@@ -272,7 +274,7 @@ __device__ __forceinline__ void seg_conv_adj(C (&v)[16], C* row, int t, const C*
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[q] = cmul(v[q], __ldg(bs + t + q * TT));
     }
-    team_fft<L, +1>(v, row, t, tw);
+    team_fft<L, +1, PLAN>(v, row, t, tw);
     store(s, v);
   }
 }
@@ -421,7 +423,7 @@ k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d,
         u[q] = a;
       }
     };
-    seg_conv_fwd<L, DZ>(v, row, t, tw, ax, nseg, d.adjoint, load, acc, a2);
+    seg_conv_fwd<L, DZ, czt_plan_of<V>()>(v, row, t, tw, ax, nseg, d.adjoint, load, acc, a2);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int p = t + q * TT;
@@ -490,7 +492,7 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
         u[q] = q * TT < ns && j < ns ? cmul(src[m0 + j], __ldg(ay.pre + m0 + j)) : mk((T)0, (T)0);
       }
     };
-    seg_conv_fwd<L, DZ>(v, row, t, tw, ay, nseg, d.adjoint, load, acc, a2);
+    seg_conv_fwd<L, DZ, czt_plan_of<V>()>(v, row, t, tw, ay, nseg, d.adjoint, load, acc, a2);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int qq = t + q * TT;
@@ -638,7 +640,7 @@ k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, 
         }
       }
     };
-    seg_conv_adj<L>(v, row, t, tw, ay, nseg, d.adjoint, spec, store, F);
+    seg_conv_adj<L, czt_plan_of<V>()>(v, row, t, tw, ay, nseg, d.adjoint, spec, store, F);
   }
   if constexpr (DZ) {
     __shared__ double rbuf[32 * 6];
@@ -755,7 +757,7 @@ k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d
         }
       }
     };
-    seg_conv_adj<L>(v, row, t, tw, ax, nseg, d.adjoint, spec, store, F);
+    seg_conv_adj<L, czt_plan_of<V>()>(v, row, t, tw, ax, nseg, d.adjoint, spec, store, F);
   }
   if constexpr (DZ) {
     __shared__ double rbuf[32 * 2];

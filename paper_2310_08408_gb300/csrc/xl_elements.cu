@@ -219,7 +219,11 @@ __device__ __forceinline__ void elem_fwd(const ElemSet& E, const ElemDims& d, co
   }
 }
 
-// grid: (ceil(plane / 256), batch)
+// Pixels a thread of the forward takes (kPixFwd pixels blockDim.x apart: coalesced, and the
+// block's Jones table is formed once for 256 * kPixFwd pixels).
+constexpr int kPixFwd = 4;
+
+// grid: (ceil(plane / (256 kPixFwd)), batch)
 template <typename T>
 __global__ void __launch_bounds__(256) k_elem_fwd(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out,
                                                   ElemSet E, ElemDims d, const cplx<T>* __restrict__ lens,
@@ -228,18 +232,21 @@ __global__ void __launch_bounds__(256) k_elem_fwd(const cplx<T>* __restrict__ in
   __shared__ JonesTab<T> jt;
   jones_fill<T>(jt, E, d, b, false);
   __syncthreads();
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= d.plane) return;
-  const int m = (int)i % d.nx, n = (int)i / d.nx;  // plane < 2^31: 32-bit division
   const cplx<T>* src = in + (int64_t)b * d.comps_in * d.plane;
-  cplx<T> c0 = src[i];
-  cplx<T> c1 = d.comps_in >= 2 ? src[d.plane + i] : mk((T)0, (T)0);
-  cplx<T> c2 = d.comps_in == 3 ? src[2 * d.plane + i] : mk((T)0, (T)0);
-  for (int e = 0; e < E.n; ++e) elem_fwd<T>(E, d, lens, nlens, e, b, i, m, n, c0, c1, c2, jt);
   cplx<T>* dst = out + (int64_t)b * d.comps_out * d.plane;
-  dst[i] = c0;
-  if (d.comps_out >= 2) dst[d.plane + i] = c1;
-  if (d.comps_out == 3) dst[2 * d.plane + i] = c2;
+#pragma unroll
+  for (int k = 0; k < kPixFwd; ++k) {
+    const int64_t i = ((int64_t)blockIdx.x * kPixFwd + k) * blockDim.x + threadIdx.x;
+    if (i >= d.plane) break;
+    const int m = (int)i % d.nx, n = (int)i / d.nx;  // plane < 2^31: 32-bit division
+    cplx<T> c0 = src[i];
+    cplx<T> c1 = d.comps_in >= 2 ? src[d.plane + i] : mk((T)0, (T)0);
+    cplx<T> c2 = d.comps_in == 3 ? src[2 * d.plane + i] : mk((T)0, (T)0);
+    for (int e = 0; e < E.n; ++e) elem_fwd<T>(E, d, lens, nlens, e, b, i, m, n, c0, c1, c2, jt);
+    dst[i] = c0;
+    if (d.comps_out >= 2) dst[d.plane + i] = c1;
+    if (d.comps_out == 3) dst[2 * d.plane + i] = c2;
+  }
 }
 
 struct ElemGrad {
@@ -513,7 +520,7 @@ xl_status run_fwd(const void* in, void* out, int32_t batch, const ElemSet& E, co
     XL_TRY(workspace(s, ((size_t)d.nx + d.ny) * nlens * lb * sizeof(cplx<T>), &lens, 2));
     XL_TRY(lens_tables<T>(E, d, lb, nlens, lens, s));
   }
-  dim3 grid((unsigned)((d.plane + 255) / 256), batch);
+  dim3 grid((unsigned)((d.plane + 256 * kPixFwd - 1) / (256 * kPixFwd)), batch);
   LaunchScope ls("elements_fwd", s);
   k_elem_fwd<T><<<grid, 256, 0, s>>>((const cplx<T>*)in, (cplx<T>*)out, E, d, (const cplx<T>*)lens, nlens);
   XL_CUDA_TRY(cudaGetLastError());

@@ -1,4 +1,5 @@
-// Shared-memory Stockham FFT engine (radix 16 stages, one final radix 2/4/8 stage).
+// Shared-memory Stockham FFT engine (radix 16 stages and at most one radix 2/4/8 stage, whose
+// position the radix plan chooses).
 //
 // A "team" of L/16 threads transforms one row of length L (a power of two, 64..8192). Each
 // thread keeps 16 complex values in registers; on entry and on exit thread t holds element
@@ -41,13 +42,30 @@ template <int DIR, typename C> __device__ __forceinline__ void dft2(C& a, C& b) 
   b = csub(t, b);
 }
 
-template <int DIR, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
-  C s02 = cadd(a0, a2), d02 = csub(a0, a2);
-  C s13 = cadd(a1, a3), d13 = rot90<DIR>(csub(a1, a3));
-  a0 = cadd(s02, s13);
-  a2 = csub(s02, s13);
-  a1 = cadd(d02, d13);
-  a3 = csub(d02, d13);
+// Pruned forms (HIN: the upper half of the inputs is zero and not read; HOUT: only the lower
+// half of the outputs is formed, the upper half is left undefined). Exact: with zero inputs the
+// full butterfly's additions of +0 would only turn a -0 into +0.
+template <int DIR, bool HIN = false, bool HOUT = false, typename C>
+__device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+  if constexpr (HIN) {
+    const C d13 = rot90<DIR>(a1);
+    const C x0 = a0, x1 = a1;
+    a0 = cadd(x0, x1);
+    a1 = cadd(x0, d13);
+    if constexpr (!HOUT) {
+      a2 = csub(x0, x1);
+      a3 = csub(x0, d13);
+    }
+  } else {
+    C s02 = cadd(a0, a2), d02 = csub(a0, a2);
+    C s13 = cadd(a1, a3), d13 = rot90<DIR>(csub(a1, a3));
+    a0 = cadd(s02, s13);
+    a1 = cadd(d02, d13);
+    if constexpr (!HOUT) {
+      a2 = csub(s02, s13);
+      a3 = csub(d02, d13);
+    }
+  }
 }
 
 // x * exp(DIR i pi/4)
@@ -63,37 +81,47 @@ template <int DIR, typename C> __device__ __forceinline__ C w8_3(C a) {
   return DIR < 0 ? mk((-a.x + a.y) * h, (-a.y - a.x) * h) : mk((-a.x - a.y) * h, (-a.y + a.x) * h);
 }
 
-// In-place 8-point DFT of v[o + s*k], k = 0..7 (natural order in and out).
-template <int DIR, int S, typename C> __device__ __forceinline__ void dft8s(C* v) {
-  C e0 = v[0], e1 = v[2 * S], e2 = v[4 * S], e3 = v[6 * S];
-  C o0 = v[S], o1 = v[3 * S], o2 = v[5 * S], o3 = v[7 * S];
-  dft4<DIR>(e0, e1, e2, e3);
-  dft4<DIR>(o0, o1, o2, o3);
+// In-place 8-point DFT of v[o + s*k], k = 0..7 (natural order in and out); HIN / HOUT as dft4.
+template <int DIR, int S, bool HIN = false, bool HOUT = false, typename C>
+__device__ __forceinline__ void dft8s(C* v) {
+  C e0 = v[0], e1 = v[2 * S], e2, e3;
+  C o0 = v[S], o1 = v[3 * S], o2, o3;
+  if constexpr (!HIN) {
+    e2 = v[4 * S];
+    e3 = v[6 * S];
+    o2 = v[5 * S];
+    o3 = v[7 * S];
+  }
+  dft4<DIR, HIN>(e0, e1, e2, e3);
+  dft4<DIR, HIN>(o0, o1, o2, o3);
   o1 = w8_1<DIR>(o1);
   o2 = rot90<DIR>(o2);
   o3 = w8_3<DIR>(o3);
   v[0] = cadd(e0, o0);
-  v[4 * S] = csub(e0, o0);
   v[S] = cadd(e1, o1);
-  v[5 * S] = csub(e1, o1);
   v[2 * S] = cadd(e2, o2);
-  v[6 * S] = csub(e2, o2);
   v[3 * S] = cadd(e3, o3);
-  v[7 * S] = csub(e3, o3);
+  if constexpr (!HOUT) {
+    v[4 * S] = csub(e0, o0);
+    v[5 * S] = csub(e1, o1);
+    v[6 * S] = csub(e2, o2);
+    v[7 * S] = csub(e3, o3);
+  }
 }
 
 // In-place 16-point DFT of v[s*k], k = 0..15: two 8-point DFTs of the even and odd samples
-// and the W_16^k combination.
-template <int DIR, int S, typename C> __device__ __forceinline__ void dft16s(C* v) {
+// and the W_16^k combination; HIN / HOUT as dft4.
+template <int DIR, int S, bool HIN = false, bool HOUT = false, typename C>
+__device__ __forceinline__ void dft16s(C* v) {
   typedef decltype(v[0].x) T;
   C e[8], o[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < (HIN ? 4 : 8); ++k) {
     e[k] = v[2 * k * S];
     o[k] = v[(2 * k + 1) * S];
   }
-  dft8s<DIR, 1>(e);
-  dft8s<DIR, 1>(o);
+  dft8s<DIR, 1, HIN>(e);
+  dft8s<DIR, 1, HIN>(o);
   const T c1 = (T)0.92387953251128675612818318939678829;  // cos(pi/8)
   const T s1 = (T)0.38268343236508977172845998403039887;  // sin(pi/8)
   const T sd = (T)DIR;
@@ -108,37 +136,56 @@ template <int DIR, int S, typename C> __device__ __forceinline__ void dft16s(C* 
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     v[k * S] = cadd(e[k], o[k]);
-    v[(k + 8) * S] = csub(e[k], o[k]);
+    if constexpr (!HOUT) v[(k + 8) * S] = csub(e[k], o[k]);
   }
 }
 
-template <int R, int DIR, int S, typename C> __device__ __forceinline__ void dftR(C* v) {
-  if constexpr (R == 16) dft16s<DIR, S>(v);
-  else if constexpr (R == 8) dft8s<DIR, S>(v);
-  else if constexpr (R == 4) dft4<DIR>(v[0], v[S], v[2 * S], v[3 * S]);
-  else if constexpr (R == 2) dft2<DIR>(v[0], v[S]);
+template <int R, int DIR, int S, bool HIN = false, bool HOUT = false, typename C>
+__device__ __forceinline__ void dftR(C* v) {
+  if constexpr (R == 16) dft16s<DIR, S, HIN, HOUT>(v);
+  else if constexpr (R == 8) dft8s<DIR, S, HIN, HOUT>(v);
+  else if constexpr (R == 4) dft4<DIR, HIN, HOUT>(v[0], v[S], v[2 * S], v[3 * S]);
+  else if constexpr (HIN) v[S] = v[0];  // R == 2 with a zero second input
+  else if constexpr (HOUT) v[0] = cadd(v[0], v[S]);
+  else dft2<DIR>(v[0], v[S]);
 }
 
-template <int L> struct FFTShape {
+// Pruning of a whole transform (template argument PRUNE of team_fft): PRUNE_IN, the inputs
+// q >= 8 (the upper half of the row) are zero and not read; PRUNE_OUT, only the outputs q < 8
+// (the lower half) are formed, v[8..15] are left undefined. The zero-padded transforms of the RS
+// convolution take both: half of every input row is padding and half of every output is cropped.
+constexpr int PRUNE_IN = 1, PRUNE_OUT = 2;
+
+// Radix plan of a length-L transform: L = 16^a 2^REM (REM = log2 L mod 4). Every stage has radix
+// 16 except one of radix 2^REM (when REM > 0), which sits last (PLAN 0), first (PLAN 1) or second
+// (PLAN 2; the same as PLAN 0 for two-stage lengths). Each thread keeps 16 values, so a stage of
+// radix R runs 16 / R butterflies a thread; all plans take the same number of stages, shared-
+// memory exchanges and flops and differ in their twiddle and bank patterns (the autotuner picks).
+template <int L, int PLAN = 0> struct FFTShape {
   static constexpr int LOG = cilog2(L);
   static constexpr int N16 = LOG / 4;              // radix-16 stages
-  static constexpr int REM = LOG % 4;              // log2 of the last stage's radix (0: none)
+  static constexpr int REM = LOG % 4;              // log2 of the odd stage's radix (0: none)
   static constexpr int NST = N16 + (REM ? 1 : 0);  // number of stages
   static constexpr int TT = L / 16;                // threads per team
+  static constexpr int POS = REM == 0 ? -1 : (PLAN == 1 ? 0 : (PLAN == 2 && NST > 2 ? 1 : NST - 1));
+  static constexpr int radix(int s) { return s == POS ? (1 << REM) : 16; }
+  static constexpr int ns(int s) {  // sub-transform size before stage s
+    int n = 1;
+    for (int i = 0; i < s; ++i) n *= radix(i);
+    return n;
+  }
   static_assert((1 << LOG) == L && L >= 64 && L <= 8192, "FFT length: power of two in [64, 8192]");
+  static_assert(PLAN >= 0 && PLAN <= 2, "radix plan: 0, 1 or 2");
 };
 
 // Twiddle table layout: for every stage S >= 1 (sub-transform size Ns, radix R) a block of
 // R x Ns entries tw[off_S + r Ns + k] = exp(-2 pi i k r / (Ns R)), each rounded once from double
 // precision on the host. For a fixed r the lanes of a warp (consecutive butterflies, consecutive
 // k) read consecutive entries, so every twiddle load is coalesced.
-__host__ __device__ constexpr int tw_stage_offset(int L, int S) {
-  int off = 0, Ns = 16;
-  for (int s = 1; s < S; ++s) {
-    const int R = (Ns * 16 <= L) ? 16 : L / Ns;
-    off += Ns * R;
-    Ns *= R;
-  }
+template <int L, int PLAN = 0> __host__ __device__ constexpr int tw_stage_offset(int S) {
+  typedef FFTShape<L, PLAN> Sh;
+  int off = 0;
+  for (int s = 1; s < S; ++s) off += Sh::radix(s) * Sh::ns(s);
   return off;
 }
 
@@ -169,14 +216,14 @@ template <int L> __host__ __device__ constexpr bool team_barriers_fit(int thread
   return L / 16 <= 32 || threads / (L / 16) <= 15;
 }
 
-// Stage S (>= 1) of the transform; Ns = 16^S for the radix-16 prefix.
-template <int L, int DIR, int S, typename C>
+// Stage S (>= 1) of the transform under radix plan PLAN.
+template <int L, int DIR, int S, int PLAN, int PRUNE, typename C>
 __device__ __forceinline__ void fft_stage(C (&v)[16], C* sm, int t, const C* __restrict__ tw) {
-  typedef FFTShape<L> Sh;
+  typedef FFTShape<L, PLAN> Sh;
   constexpr bool last = (S == Sh::NST - 1);
-  constexpr int R = (last && Sh::REM) ? (1 << Sh::REM) : 16;
+  constexpr int R = Sh::radix(S);
   constexpr int B = 16 / R;
-  constexpr int Ns = 1 << (4 * S);
+  constexpr int Ns = Sh::ns(S);
   constexpr int TT = Sh::TT;
   team_sync<L>();
 #pragma unroll
@@ -188,8 +235,8 @@ __device__ __forceinline__ void fft_stage(C (&v)[16], C* sm, int t, const C* __r
   for (int b = 0; b < B; ++b) {
     const int j = t + b * TT;
     const int k = j & (Ns - 1);
-    apply_twiddles<R, B, Ns>(v + b, tw + tw_stage_offset(L, S) + k, DIR > 0);
-    dftR<R, DIR, B>(v + b);
+    apply_twiddles<R, B, Ns>(v + b, tw + tw_stage_offset<L, PLAN>(S) + k, DIR > 0);
+    dftR<R, DIR, B, false, last && (PRUNE & PRUNE_OUT) != 0>(v + b);
   }
   if constexpr (!last) {
 #pragma unroll
@@ -199,7 +246,7 @@ __device__ __forceinline__ void fft_stage(C (&v)[16], C* sm, int t, const C* __r
 #pragma unroll
       for (int r = 0; r < R; ++r) sm[spad(base + r * Ns)] = v[b + B * r];
     }
-    fft_stage<L, DIR, (S + 1 < Sh::NST ? S + 1 : S)>(v, sm, t, tw);
+    fft_stage<L, DIR, (S + 1 < Sh::NST ? S + 1 : S), PLAN, PRUNE>(v, sm, t, tw);
   }
 }
 
@@ -335,17 +382,24 @@ template <typename C, int TT> struct Stash<C, TT, true> {
 };
 
 // Full length-L transform of one row held by a team (see the file comment for the layout).
-// sm: the team's padded shared-memory row (srow(L) elements).
+// sm: the team's padded shared-memory row (srow(L) elements); tw: the twiddle table of plan PLAN.
 // The team barrier after the register-only first stage orders its shared-memory writes after
 // every read of the row by a previous transform (a forward transform's last stage reads the row just
 // before a caller multiplies and runs the inverse transform on the same row).
-template <int L, int DIR, typename C>
+template <int L, int DIR, int PLAN = 0, int PRUNE = 0, typename C>
 __device__ __forceinline__ void team_fft(C (&v)[16], C* sm, int t, const C* __restrict__ tw) {
-  dft16s<DIR, 1>(v);  // stage 0: radix 16, Ns = 1, no twiddles
+  typedef FFTShape<L, PLAN> Sh;
+  constexpr int R0 = Sh::radix(0), B0 = 16 / R0, TT = Sh::TT;
+  // stage 0 (Ns = 1, no twiddles) on the registers: butterfly j = t + b TT writes y[j R0 + r];
+  // with PRUNE_IN its inputs r >= R0 / 2 (q = b + B0 r >= 8) are the zero padding
+#pragma unroll
+  for (int b = 0; b < B0; ++b) dftR<R0, DIR, B0, (PRUNE & PRUNE_IN) != 0>(v + b);
   team_sync<L>();
 #pragma unroll
-  for (int r = 0; r < 16; ++r) sm[spad(t * 16 + r)] = v[r];
-  fft_stage<L, DIR, 1>(v, sm, t, tw);
+  for (int b = 0; b < B0; ++b)
+#pragma unroll
+    for (int r = 0; r < R0; ++r) sm[spad((t + b * TT) * R0 + r)] = v[b + B0 * r];
+  fft_stage<L, DIR, 1, PLAN, PRUNE>(v, sm, t, tw);
 }
 
 }  // namespace xl

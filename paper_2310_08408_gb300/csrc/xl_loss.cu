@@ -28,7 +28,6 @@ namespace xl {
 __device__ unsigned int g_status_bits = 0;  // bit 0: non-finite loss
 
 constexpr int kLossThreads = 256;
-constexpr int kLossBlocks = 152 * 2;  // per batch element: two blocks per SM on 152 SMs
 
 struct LossDims {
   int nx, ny, comps;
@@ -91,7 +90,23 @@ __device__ __forceinline__ double bmax(double v, double* red) {
   return s;
 }
 
-// Sweep 1. partial: [batch][blocks][3]. grid (kLossBlocks, batch).
+// Pixels of a block: the rows [r0, r1) of gridDim.x equal row ranges, each row swept by the
+// block's threads in coalesced steps; fn(i, x, y) gets the pixel index and its coordinates,
+// formed in T from per-launch bases (no per-pixel integer division or double arithmetic).
+template <typename T, typename F>
+__device__ __forceinline__ void for_pixels(const LossDims& d, F&& fn) {
+  const int rpb = (d.ny + gridDim.x - 1) / gridDim.x;
+  const int r0 = blockIdx.x * rpb, r1 = min(d.ny, r0 + rpb);
+  const T X0 = (T)d.x0, DX = (T)d.dx, Y0 = (T)d.y0, DY = (T)d.dy;
+  for (int r = r0; r < r1; ++r) {
+    const T y = Y0 + (T)r * DY;
+    const int64_t base = (int64_t)r * d.nx;
+#pragma unroll 4
+    for (int xi = threadIdx.x; xi < d.nx; xi += blockDim.x) fn(base + xi, X0 + (T)xi * DX, y);
+  }
+}
+
+// Sweep 1. partial: [batch][blocks][3]. grid (loss_blocks, batch).
 template <typename T>
 __global__ void __launch_bounds__(kLossThreads) k_loss_sweep1(const cplx<T>* __restrict__ field, LossDims d,
                                                               double* __restrict__ partial,
@@ -100,12 +115,10 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_sweep1(const cplx<T>* __r
   const int b = blockIdx.y;
   const cplx<T>* f = field + (int64_t)b * d.comps * d.plane;
   T s0 = 0, s1 = 0, s2 = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.plane;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for_pixels<T>(d, [&](int64_t i, T x, T y) {
     const T I = intensity<T>(f, d, i, b);
     if (inten) inten[(int64_t)b * d.plane + i] = I;
     if (d.mode == XL_SECOND_MOMENT) {
-      const T x = (T)(d.x0 + (i % d.nx) * d.dx), y = (T)(d.y0 + (i / d.nx) * d.dy);
       s0 += I;
       s1 += I * x;
       s2 += I * y;
@@ -115,7 +128,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_sweep1(const cplx<T>* __r
     } else {
       s0 = fmax(s0, I);
     }
-  }
+  });
   double* p = partial + ((int64_t)b * gridDim.x + blockIdx.x) * 3;
   if (d.mode == XL_SECOND_MOMENT || d.mode == XL_MSE) {
     double a = bsum((double)s0, red), bx = bsum((double)s1, red), by = bsum((double)s2, red);
@@ -144,22 +157,20 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_sweep2(const cplx<T>* __r
     // single sweep: nothing to add
   } else if (d.mode == XL_SECOND_MOMENT) {
     const T xb = (T)sb[1], yb = (T)sb[2];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.plane;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for_pixels<T>(d, [&](int64_t i, T x, T y) {
       const T I = intensity<T>(f, d, i, b);
-      const T ex = (T)(d.x0 + (i % d.nx) * d.dx) - xb, ey = (T)(d.y0 + (i / d.nx) * d.dy) - yb;
+      const T ex = x - xb, ey = y - yb;
       s0 += I * (ex * ex + ey * ey);
-    }
+    });
   } else {
     const T thr = (T)sb[3];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.plane;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for_pixels<T>(d, [&](int64_t i, T, T) {
       const T I = intensity<T>(f, d, i, b);
       if (I > thr) {
         s0 += (T)1;
         s1 += I;
       }
-    }
+    });
   }
   double a = bsum((double)s0, red), c = bsum((double)s1, red);
   if (threadIdx.x == 0) {
@@ -253,11 +264,10 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_grad(const cplx<T>* __res
   const T xb = (T)sb[1], yb = (T)sb[2], L = (T)sb[5], iP = (T)(1.0 / sb[0]);
   const T thr = (T)sb[3], dens = (T)(-sb[6] / (sb[7] * sb[7]));
   const T beta = (T)d.beta;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.plane;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for_pixels<T>(d, [&](int64_t i, T x, T y) {
     T dI;
     if (d.mode == XL_SECOND_MOMENT) {
-      const T ex = (T)(d.x0 + (i % d.nx) * d.dx) - xb, ey = (T)(d.y0 + (i / d.nx) * d.dy) - yb;
+      const T ex = x - xb, ey = y - yb;
       dI = (ex * ex + ey * ey - L) * iP;
     } else if (d.mode == XL_MSE) {
       dI = (T)2 * (intensity<T>(f, d, i, b) - ((const T*)d.target)[(int64_t)b * d.plane + i]) /
@@ -281,7 +291,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_grad(const cplx<T>* __res
       g[c * d.plane + i] = on ? cscale(f[c * d.plane + i], wex) : mk((T)0, (T)0);
       if (gd) gd[c * d.plane + i] = on ? cscale(fd[c * d.plane + i], wdp) : mk((T)0, (T)0);
     }
-  }
+  });
 }
 
 // softmin over detectors: out[b] = -log(sum_d exp(-beta l[b][d])) / beta (minimum subtracted),
@@ -336,7 +346,9 @@ xl_status loss_check(const void* field, int32_t batch, int32_t comps, uint32_t m
 
 int loss_blocks(const LossDims& d) {
   int64_t need = (d.plane + kLossThreads * 4 - 1) / (kLossThreads * 4);
-  return (int)std::max<int64_t>(1, std::min<int64_t>(need, kLossBlocks));
+  // per batch element at most two blocks per SM of the device, and at most one per row
+  need = std::min<int64_t>(need, d.ny);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(need, 2 * (int64_t)sm_count()));
 }
 
 // Both sweeps and finalisers; st / loss in the workspace or caller memory.

@@ -106,7 +106,7 @@ k_rs_pass1(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, int nx, int
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = (q < 8 && y < ny) ? src[t + q * TT] : mk((T)0, (T)0);
   C* row = sm + team * P;
-  team_fft<LX, -1>(v, row, t, tw);
+  team_fft<LX, -1, 0, PRUNE_IN>(v, row, t, tw);
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < 16; ++q) row[spad(t + q * TT)] = v[q];
@@ -134,7 +134,7 @@ k_rs_pass1_rm(const float2* __restrict__ in, float2* __restrict__ Tr, int nx, in
   float2 v[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = q < 8 ? src[t + q * TT] : make_float2(0.f, 0.f);
-  team_fft<LX, -1>(v, sm + team * srow(LX), t, tw);
+  team_fft<LX, -1, 0, PRUNE_IN>(v, sm + team * srow(LX), t, tw);
   if (live) {
     float2* d = Tr + ((int64_t)(p / cin) * cT + (p % cin)) * (int64_t)LX * ny + (int64_t)y * LX;
 #pragma unroll
@@ -198,7 +198,7 @@ k_rs_pass3(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, int nx, in
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = row[spad(t + q * TT)];
   __syncthreads();
-  team_fft<LX, +1>(v, row, t, tw);
+  team_fft<LX, +1, 0, PRUNE_OUT>(v, row, t, tw);
   const int y = y0 + team;
   if (y < ny) {
     C* d = out + (int64_t)p * nx * ny + (int64_t)y * nx;
@@ -274,7 +274,7 @@ k_rs_pass3_tma(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ ou
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = sm[(t + q * TT) * ROWS + team];
   __syncthreads();  // every thread has its inputs before the transforms reuse the tile's memory
-  team_fft<LX, +1>(v, sm + team * srow(LX), t, tw);
+  team_fft<LX, +1, 0, PRUNE_OUT>(v, sm + team * srow(LX), t, tw);
   const int y = y0 + team;
   if (y < ny) {
     C* d = out + (int64_t)p * nx * ny + (int64_t)y * nx;
@@ -522,7 +522,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
     } else {
       load_col(v, T0, t, TT);
     }
-    team_fft<LY, -1>(v, row, t, tw);
+    team_fft<LY, -1, 0, PRUNE_IN>(v, row, t, tw);
     if (a.spec_out && live) store_full(v, spec_out(0), t, TT);
     const C* h = H(KH);
 #pragma unroll
@@ -530,7 +530,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
       const C hv = spec_row(h, q, t, TT, flipx, false, false);
       v[q] = a.conj ? cmulc(v[q], hv) : cmul(v[q], hv);
     }
-    team_fft<LY, +1>(v, row, t, tw);
+    team_fft<LY, +1, 0, PRUNE_OUT>(v, row, t, tw);
     if (live) store_col(v, T0, t, TT);
   } else if constexpr (MODE == P2_VRS) {
     // Ez accumulates in a second shared-memory row of the team (each thread touches only its
@@ -540,7 +540,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
     C* zr = sm + ROWS * SR + team * SR;
     const C *hz = H(KH), *hx = H(KHX), *hy = H(KHY);
     load_col(v, T0, t, TT);
-    team_fft<LY, -1>(v, row, t, tw);
+    team_fft<LY, -1, 0, PRUNE_IN>(v, row, t, tw);
     if (a.spec_out && live) store_full(v, spec_out(0), t, TT);
     transform_fence();
 #pragma unroll
@@ -549,11 +549,11 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
       v[q] = cmul(v[q], spec_row(hz, q, t, TT, flipx, false, false));
       XL_GROUP_FENCE(q);
     }
-    team_fft<LY, +1>(v, row, t, tw);
+    team_fft<LY, +1, 0, PRUNE_OUT>(v, row, t, tw);
     transform_fence();
     if (live) store_col(v, T0, t, TT);
     load_col(v, T1, t, TT);
-    team_fft<LY, -1>(v, row, t, tw);
+    team_fft<LY, -1, 0, PRUNE_IN>(v, row, t, tw);
     if (a.spec_out && live) store_full(v, spec_out(1), t, TT);
     transform_fence();
 #pragma unroll
@@ -563,12 +563,12 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
       v[q] = cmul(v[q], spec_row(hz, q, t, TT, flipx, false, false));
       XL_GROUP_FENCE(q);
     }
-    team_fft<LY, +1>(v, row, t, tw);
+    team_fft<LY, +1, 0, PRUNE_OUT>(v, row, t, tw);
     transform_fence();
     if (live) store_col(v, T1, t, TT);
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = zr[spad(t + q * TT)];
-    team_fft<LY, +1>(v, row, t, tw);
+    team_fft<LY, +1, 0, PRUNE_OUT>(v, row, t, tw);
     transform_fence();
     if (live) store_col(v, T2, t, TT);
   } else if constexpr (MODE == P2_RS_BWD) {
@@ -580,7 +580,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
     if (a.want_dz) {
       const C* U0 = Ub + (int64_t)b * a.cU * a.t_plane + (int64_t)kx * a.ny;
       load_col(v, U0, t, TT);
-      team_fft<LY, -1>(v, row, t, tw);
+      team_fft<LY, -1, 0, PRUNE_IN>(v, row, t, tw);
       const C* hd = H(KDH);
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
@@ -589,7 +589,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
       }
     }
     load_col(v, T0, t, TT);
-    team_fft<LY, -1>(v, row, t, tw);
+    team_fft<LY, -1, 0, PRUNE_IN>(v, row, t, tw);
     if (a.want_dz) {
       T acc = (T)0;
 #pragma unroll
@@ -600,7 +600,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
       const C* h = H(KH);
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[q] = cmulc(v[q], spec_row(h, q, t, TT, flipx, false, false));
-      team_fft<LY, +1>(v, row, t, tw);
+      team_fft<LY, +1, 0, PRUNE_OUT>(v, row, t, tw);
       if (live) store_col(v, T0, t, TT);
     }
   } else if constexpr (MODE == P2_VRS_BWD) {
@@ -613,7 +613,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
     Stash<C, TT, p2_ustash_smem<T, LY, MODE>()> ur;
     ur.init(sm + 2 * ROWS * SR + team * SR, t);
     load_col(v, T2, t, TT);
-    team_fft<LY, -1>(v, row, t, tw);
+    team_fft<LY, -1, 0, PRUNE_IN>(v, row, t, tw);
 #pragma unroll
     for (int q = 0; q < 16; ++q) zr[spad(t + q * TT)] = v[q];
 #pragma unroll
@@ -623,12 +623,12 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
       if (a.want_dz) {
         const C* Uc = Ub + ((int64_t)b * a.cU + c) * a.t_plane + (int64_t)kx * a.ny;
         load_col(v, Uc, t, TT);
-        team_fft<LY, -1>(v, row, t, tw);
+        team_fft<LY, -1, 0, PRUNE_IN>(v, row, t, tw);
 #pragma unroll
         for (int q = 0; q < 16; ++q) ur.set(q, v[q]);
       }
       load_col(v, Tc, t, TT);
-      team_fft<LY, -1>(v, row, t, tw);
+      team_fft<LY, -1, 0, PRUNE_IN>(v, row, t, tw);
       if (a.want_dz) {
         const C *hd = H(KDH), *ho = H(c == 0 ? KDHX : KDHY);
         T acc = (T)0;
@@ -649,7 +649,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
                       cmulc(zr[spad(t + q * TT)], spec_row(ho, q, t, TT, flipx, ox, oy)));
           XL_GROUP_FENCE(q);
         }
-        team_fft<LY, +1>(v, row, t, tw);
+        team_fft<LY, +1, 0, PRUNE_OUT>(v, row, t, tw);
         if (live) store_col(v, Tc, t, TT);
       }
     }
@@ -661,7 +661,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
     } else {
       load_col(v, T0, t, TT);
     }
-    team_fft<LY, -1>(v, row, t, tw);
+    team_fft<LY, -1, 0, PRUNE_IN>(v, row, t, tw);
     if (a.want_dz) {
       const C* su = spec_in(0);
       const C* hd = H(KDH);
@@ -677,7 +677,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
       const C* h = H(KH);
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[q] = cmulc(v[q], spec_row(h, q, t, TT, flipx, false, false));
-      team_fft<LY, +1>(v, row, t, tw);
+      team_fft<LY, +1, 0, PRUNE_OUT>(v, row, t, tw);
       if (live) store_col(v, T0, t, TT);
     }
   } else if constexpr (MODE == P2_VRS_BWD_S) {
@@ -686,7 +686,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
     C* T2 = T1 + a.t_plane;
     C* zr = sm + ROWS * SR + team * SR;
     load_col(v, T2, t, TT);
-    team_fft<LY, -1>(v, row, t, tw);
+    team_fft<LY, -1, 0, PRUNE_IN>(v, row, t, tw);
 #pragma unroll
     for (int q = 0; q < 16; ++q) zr[spad(t + q * TT)] = v[q];
 #pragma unroll
@@ -694,7 +694,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
       C* Tc = c == 0 ? T0 : T1;
       const bool ox = c == 0, oy = c == 1;
       load_col(v, Tc, t, TT);
-      team_fft<LY, -1>(v, row, t, tw);
+      team_fft<LY, -1, 0, PRUNE_IN>(v, row, t, tw);
       if (a.want_dz) {
         const C* su = spec_in(c);
         const C *hd = H(KDH), *ho = H(c == 0 ? KDHX : KDHY);
@@ -716,7 +716,7 @@ k_rs_pass2(cplx<T>* __restrict__ Tb, const cplx<T>* __restrict__ Ub, const cplx<
                       cmulc(zr[spad(t + q * TT)], spec_row(ho, q, t, TT, flipx, ox, oy)));
           XL_GROUP_FENCE(q);
         }
-        team_fft<LY, +1>(v, row, t, tw);
+        team_fft<LY, +1, 0, PRUNE_OUT>(v, row, t, tw);
         transform_fence();
         if (live) store_col(v, Tc, t, TT);
       }

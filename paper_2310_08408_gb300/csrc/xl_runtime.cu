@@ -96,7 +96,7 @@ const char* tune_family_name(int family) {
 }
 
 int tuned_variant(int family, int L, int dtype) {
-  if (L < kTuneMinL) return 0;
+  if (L < kTuneMinL && !(family >= TUNE_CZT_FWD_X && czt_plan_lengths(L))) return 0;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tune.find(std::make_tuple(family, L, dtype));
   return it == g_tune.end() ? 0 : it->second.variant;
@@ -123,6 +123,18 @@ std::string tune_table_text() {
 void tune_clear() {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune.clear();
+}
+
+int sm_count() {
+  static int counts[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (counts[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 152;
+    counts[dev] = n;
+  }
+  return counts[dev];
 }
 
 xl_status smem_attr(const void* func, size_t bytes) {
@@ -187,21 +199,26 @@ xl_status status_word_take(cudaStream_t s, unsigned int* bits) {
   return XL_OK;
 }
 
-xl_status twiddles(int L, int dtype, const void** out) {
+xl_status twiddles(int L, int dtype, const void** out) { return twiddles(L, dtype, 0, out); }
+
+xl_status twiddles(int L, int dtype, int plan, const void** out) {
   std::lock_guard<std::mutex> lk(g_mu);
   DeviceState& st = cur();
-  auto key = std::make_pair(L, dtype);
+  auto key = std::make_pair(L, dtype + 16 * plan);
   auto it = st.tw.find(key);
   if (it != st.tw.end()) {
     *out = it->second;
     return XL_OK;
   }
   // per-stage blocks: stage s >= 1 has R x Ns entries exp(-2 pi i k r / (Ns R)), r-major (the
-  // layout read by apply_twiddles in xl_fft.cuh)
+  // layout read by apply_twiddles in xl_fft.cuh); the stages' radices follow the plan (all 16
+  // but one of 2^(log2 L mod 4), which sits last, first or second)
+  const int lg = ilog2(L), rem = lg % 4, nst = lg / 4 + (rem ? 1 : 0);
+  const int pos = rem == 0 ? -1 : (plan == 1 ? 0 : (plan == 2 && nst > 2 ? 1 : nst - 1));
   std::vector<double> w;
-  int Ns = 16;
-  while (Ns < L) {
-    const int R = (Ns * 16 <= L) ? 16 : L / Ns;
+  int Ns = pos == 0 ? (1 << rem) : 16;
+  for (int s = 1; s < nst; ++s) {
+    const int R = s == pos ? (1 << rem) : 16;
     for (int r = 0; r < R; ++r)
       for (int k = 0; k < Ns; ++k) {
         const double ang = -kTwoPi * (double)k * (double)r / ((double)Ns * (double)R);

@@ -16,6 +16,8 @@ namespace xl {
 // stage s >= 1 (sub-transform size Ns, radix R) the R x Ns values exp(-2 pi i k r / (Ns R)),
 // computed in double precision on the host. Created on first use (synchronous upload).
 xl_status twiddles(int L, int dtype, const void** out);
+// The same for radix plan `plan` of xl_fft.cuh (0 is the table above).
+xl_status twiddles(int L, int dtype, int plan, const void** out);
 
 // Workspace of at least `bytes` for `stream` on the current device. Growing it synchronises the
 // device (cudaFree); the pointer stays valid until the next call that grows it or xl_cache_clear.
@@ -52,6 +54,9 @@ xl_status status_word_take(cudaStream_t s, unsigned int* bits);
 
 size_t dtype_csize(int dtype);  // bytes of one complex element
 
+// Streaming multiprocessors of the current device (queried once per device; 152 on a GB300).
+int sm_count();
+
 // Launch variants chosen by the autotuner (xl_autotune): for each tunable kernel family, row
 // length L and dtype, the variant index (0 = the built-in default). Families: the transposing
 // row passes, whose variants differ in rows per block (threads per block, register budget and
@@ -67,6 +72,11 @@ enum TuneFamily {
 };
 constexpr int kTuneVariants = 3;
 constexpr int kTuneMinL = 1024;  // shorter rows build only the default variant
+// The CZT window passes of complex64 scalar fields at the lengths with a radix-2/4/8 stage
+// (512, 1024, 2048) have two more variants: the default rows with radix plan 1 (3) and plan 2 (4)
+// (the odd stage first or second instead of last).
+constexpr int kTuneVariantsPlans = 5;
+inline bool czt_plan_lengths(int L) { return L == 512 || L == 1024 || L == 2048; }
 const char* tune_family_name(int family);
 int tuned_variant(int family, int L, int dtype);
 void set_tuned_variant(int family, int L, int dtype, int variant, double us);

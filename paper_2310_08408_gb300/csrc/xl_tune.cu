@@ -1,9 +1,11 @@
-// Autotuner of the transposing row passes: for a grid (and output window) it times the launch
-// variants of RS passes 1 and 3 and of the four CZT window passes on synthetic data on the
-// current device (launches over several planes, as batched calls make them), keeps the fastest per (kernel family, row length, dtype) for the launchers,
-// and saves / loads the choices as text. Variants differ only in how many rows a block holds
-// (threads per block, register budget, shared memory), so every variant computes bit-identical
-// results; the choice only changes speed.
+// Autotuner of the row passes: for a grid (and output window) it times the launch variants of RS
+// passes 1 and 3 and of the four CZT window passes on synthetic data on the current device
+// (launches over several planes, as batched calls make them), keeps the fastest per (kernel
+// family, row length, dtype) for the launchers, and saves / loads the choices as text. Variants
+// 0-2 differ in how many rows a block holds (threads per block, register budget, shared memory)
+// and compute bit-identical results; variants 3 and 4 of the complex64 CZT passes at lengths
+// 512, 1024 and 2048 change the FFT radix plan (where the radix-2/4/8 stage sits), which changes
+// the rounding order only (results equal within rounding).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -34,14 +36,15 @@ struct DevBuf {
 
 // Times `run` (one launch of the family's kernel) for each variant and records the fastest.
 template <typename F>
-xl_status tune_one(int family, int L, int dtype, int reps, cudaStream_t s, F run) {
+xl_status tune_one(int family, int L, int dtype, int reps, cudaStream_t s, F run,
+                   int nvar = kTuneVariants) {
   cudaEvent_t e0, e1;
   XL_CUDA_TRY(cudaEventCreate(&e0));
   XL_CUDA_TRY(cudaEventCreate(&e1));
   int best = 0;
   double best_us = 1e300;
   xl_status st = XL_OK;
-  for (int v = 0; v < kTuneVariants && st == XL_OK; ++v) {
+  for (int v = 0; v < nvar && st == XL_OK; ++v) {
     set_tuned_variant(family, L, dtype, v, 0.0);
     st = run();  // warm-up (also sets the kernel's shared-memory limit)
     if (st != XL_OK) break;
@@ -115,20 +118,24 @@ xl_status tune_grid(const xl_grid* g, const xl_window* w, int dtype, int reps, c
     d.z[0] = 1.0;
     d.in_planes = 1;
     d.tb_elem = (int64_t)mx * ny;
-    if (Lx >= kTuneMinL) {
+    // rows variants from kTuneMinL up; radix plans at the complex64 lengths that have them
+    auto nv = [&](int L) {
+      return (sizeof(T) == 4 && czt_plan_lengths(L)) ? kTuneVariantsPlans : (L >= kTuneMinL ? kTuneVariants : 1);
+    };
+    if (nv(Lx) > 1) {
       XL_TRY(tune_one(TUNE_CZT_FWD_X, Lx, dtype, reps, s,
-                      [&] { return czt_pass<T>(CZT_FWD_X, false, Lx, in.p, Tb.p, d, ax, np, s); }));
+                      [&] { return czt_pass<T>(CZT_FWD_X, false, Lx, in.p, Tb.p, d, ax, np, s); }, nv(Lx)));
       d.adjoint = 1;
       XL_TRY(tune_one(TUNE_CZT_ADJ_X, Lx, dtype, reps, s,
-                      [&] { return czt_pass<T>(CZT_ADJ_X, false, Lx, Tb.p, in.p, d, ax, np, s); }));
+                      [&] { return czt_pass<T>(CZT_ADJ_X, false, Lx, Tb.p, in.p, d, ax, np, s); }, nv(Lx)));
       d.adjoint = 0;
     }
-    if (Ly >= kTuneMinL) {
+    if (nv(Ly) > 1) {
       XL_TRY(tune_one(TUNE_CZT_FWD_Y, Ly, dtype, reps, s,
-                      [&] { return czt_pass<T>(CZT_FWD_Y, false, Ly, Tb.p, out.p, d, ay, np, s); }));
+                      [&] { return czt_pass<T>(CZT_FWD_Y, false, Ly, Tb.p, out.p, d, ay, np, s); }, nv(Ly)));
       d.adjoint = 1;
       XL_TRY(tune_one(TUNE_CZT_ADJ_Y, Ly, dtype, reps, s,
-                      [&] { return czt_pass<T>(CZT_ADJ_Y, false, Ly, out.p, Tb.p, d, ay, np, s); }));
+                      [&] { return czt_pass<T>(CZT_ADJ_Y, false, Ly, out.p, Tb.p, d, ay, np, s); }, nv(Ly)));
       d.adjoint = 0;
     }
   }
@@ -171,7 +178,9 @@ xl_status xl_tune_set(int32_t family, int32_t L, int32_t dtype, int32_t variant)
   if (family < 0 || family >= TUNE_NFAMILY) return fail(XL_ERR_ARG, "unknown tuning family");
   if (!is_pow2(L) || L < 64 || L > 8192) return fail(XL_ERR_ARG, "L must be a power of two in [64, 8192]");
   if (dtype != XL_C64 && dtype != XL_C128) return fail(XL_ERR_ARG, "bad dtype");
-  if (variant < 0 || variant >= kTuneVariants) return fail(XL_ERR_ARG, "variant must be 0, 1 or 2");
+  const int nmax = family >= TUNE_CZT_FWD_X ? kTuneVariantsPlans : kTuneVariants;
+  if (variant < 0 || variant >= nmax)
+    return fail(XL_ERR_ARG, nmax == kTuneVariants ? "variant must be 0, 1 or 2" : "variant must be 0 to 4");
   set_tuned_variant(family, L, dtype, variant, 0.0);
   return XL_OK;
 }
@@ -212,7 +221,8 @@ xl_status xl_tune_load(const char* path) {
     }
     const int fi = family_index(fam);
     const int dtype = std::strcmp(dt, "c64") == 0 ? XL_C64 : (std::strcmp(dt, "c128") == 0 ? XL_C128 : -1);
-    if (fi < 0 || dtype < 0 || v < 0 || v >= kTuneVariants || !is_pow2(L) || L < 64 || L > 8192) {
+    const int nmax = fi >= TUNE_CZT_FWD_X ? kTuneVariantsPlans : kTuneVariants;
+    if (fi < 0 || dtype < 0 || v < 0 || v >= nmax || !is_pow2(L) || L < 64 || L > 8192) {
       st = fail(XL_ERR_ARG, "autotune file: bad entry on line " + std::to_string(lineno));
       break;
     }

@@ -83,13 +83,14 @@ def test_batch_graph_replay_equals_eager_steps():
 
 
 def test_batch_checkpoint_mode_memory_and_steps():
-    """Plane-field checkpointing holds about half the memory of the spectra mode (12 of its 29
-    field planes a setup are the kept spectra) and steps to the same optimiser state within the
-    complex64 gradient tolerance after several steps."""
+    """Plane-field checkpointing holds 0.6 of the spectra mode's memory per pixel (14 complex
+    field planes and 8 real mask / moment planes a setup against 26 and 8; the camera buffers add
+    a little at these small grids) and steps to the same optimiser state within the complex64
+    gradient tolerance after several steps."""
     xl = lib()
     a = xl.Batch(dict(CFG, checkpoint=0), GRIDS, INIT, SEED)
     c = xl.Batch(dict(CFG, checkpoint=1), GRIDS, INIT, SEED)
-    assert c.memory() < 0.6 * a.memory(), (c.memory(), a.memory())
+    assert c.memory() < 0.65 * a.memory(), (c.memory(), a.memory())
     for _ in range(3):
         a.step(use_graph=True)
         c.step(use_graph=True)
