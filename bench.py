@@ -14,8 +14,8 @@ on the masks, every stage a library call:
     U = SLM(src, phi)                              xl_apply_elements
     A = RS(U, z)  (input spectrum saved)           xl_rs_propagate_save
     C = CZT(U, z) (distance-gradient sums saved)   xl_czt_propagate_save
-    L = S(|A|^2) + S(|C|^2)                        xl_intensity_loss (second-moment spot sizes)
-    gA, gC = dL/dA, dL/dC                          xl_intensity_loss_backward
+    L = S(|A|^2) + S(|C|^2), gA, gC = dL/dA, dL/dC xl_intensity_loss_and_grad (second-moment
+                                                   spot sizes and their field gradients)
     gU, dL/dz = RS^H gA                            xl_rs_propagate_backward_saved
     gU, dL/dz += CZT^H gC                          xl_czt_propagate_backward_saved (accumulate)
     dL/dphi = SLM^H gU                             xl_apply_elements_backward
@@ -250,8 +250,8 @@ def inputs_seed(rank: int) -> int:
 
 # Library entry points one step calls, in order (the bench line's `step_parts`).
 STEP_PARTS = ["xl_step_advance", "xl_apply_elements (SLM)", "xl_rs_propagate_save",
-              "xl_czt_propagate_save", "xl_intensity_loss (A, C)",
-              "xl_intensity_loss_backward (A, C)", "xl_rs_propagate_backward_saved (+ dL/dz)",
+              "xl_czt_propagate_save", "xl_intensity_loss_and_grad (A, C)",
+              "xl_rs_propagate_backward_saved (+ dL/dz)",
               "xl_czt_propagate_backward_saved (+ dL/dz, accumulate)",
               "xl_apply_elements_backward (dL/dphi)", "xl_adam_step (phi)"]
 
@@ -293,10 +293,8 @@ class GpuStep:
         xl.apply_elements(q4(src), g, LAM, slm, out=q4(U))
         xl.rs_propagate(U, g, LAM, zs, out=A, saved=self.S_rs[:n])
         xl.czt_propagate(U, g, w, LAM, zs, out=C, saved=self.S_czt[:n])
-        lA, _ = xl.intensity_loss(q4(A), g, 1)
-        lC, _ = xl.intensity_loss(q4(C), self.wg, 1)
-        xl.intensity_loss_backward(q4(A), g, 1, out=q4(gA))
-        xl.intensity_loss_backward(q4(C), self.wg, 1, out=q4(gC))
+        lA, _ = xl.intensity_loss_and_grad(q4(A), g, 1, out=q4(gA))
+        lC, _ = xl.intensity_loss_and_grad(q4(C), self.wg, 1, out=q4(gC))
         # the spot-size losses are blind to a constant phase on A and C: phase-invariant dL/dz
         gU_rs, gz_rs = xl.rs_propagate_backward(gA, None, g, LAM, zs, want_field=True, want_dz=True,
                                                 phase_invariant=True, saved=self.S_rs[:n])

@@ -407,6 +407,16 @@ xl_status xl_intensity_loss_ex_backward(const void* field, const void* field_dep
                                         void* g_field, void* g_field_dep, int32_t dtype,
                                         void* stream);
 
+/* The loss and its field gradient in one call (an optimiser step needs both): loss[b] as
+ * xl_intensity_loss_ex and g_field (g_field_dep) as xl_intensity_loss_ex_backward with
+ * g_loss = 1, from one set of the statistics sweeps (three passes over the field instead of
+ * five for the two calls). Arguments and errors as those two. */
+xl_status xl_intensity_loss_and_grad(const void* field, const void* field_dep, const void* target,
+                                     int32_t batch, int32_t comps, uint32_t comp_mask,
+                                     const xl_grid* grid, int32_t mode, double eps, double beta,
+                                     double* loss, void* g_field, void* g_field_dep, int32_t dtype,
+                                     void* stream);
+
 /* Softmin over detectors (Methods, "Rediscovery through exploration of optical topologies": the
  * parameter update follows the detector with the smallest loss through a smooth minimum):
  *   out[b] = -log(sum_d exp(-beta losses[b][d])) / beta,

@@ -530,7 +530,7 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
 // from the saved forward (see the file comment); plane 2 of VCZT carries the cotangent Gz / z.
 // grid: (ceil(mx / ROWS), nbatch).
 template <typename T, int L, bool VEC, int V = 0, bool DZ = false>
-__global__ void XL_CZT_BOUNDS(T, L, VEC, V, DZ)
+__global__ void XL_CZT_BOUNDS(T, L, VEC, V, false)
 k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, AxisRun<cplx<T>> ay_run,
             const cplx<T>* __restrict__ tw, CztSaved<cplx<T>> sv, double* __restrict__ dzp) {
   typedef cplx<T> C;
@@ -662,7 +662,7 @@ k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, 
 // u_in and the output (see the file comment).
 // grid: (ceil(ny / ROWS), nbatch).
 template <typename T, int L, bool VEC, int V = 0, bool DZ = false>
-__global__ void XL_CZT_BOUNDS(T, L, VEC, V, DZ)
+__global__ void XL_CZT_BOUNDS(T, L, VEC, V, false)
 k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d, AxisRun<cplx<T>> ax_run,
             const cplx<T>* __restrict__ tw, CztSaved<cplx<T>> sv, double* __restrict__ dzp,
             const cplx<T>* __restrict__ u_in) {

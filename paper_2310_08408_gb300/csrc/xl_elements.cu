@@ -122,7 +122,9 @@ __device__ __forceinline__ double eparam(const ElemSet& E, const ElemDims& d, in
 
 template <typename T>
 __device__ __forceinline__ T phase_at(const void* p, int64_t stride, int b, int64_t i) {
-  return ((const T*)p)[(int64_t)b * stride + i];
+  // masks are never written by the element kernels: the read-only path lets the loads of later
+  // pixels be issued ahead of this pixel's stores
+  return __ldg((const T*)p + (int64_t)b * stride + i);
 }
 
 // Lens tables: for lens slot s and batch element b, Lx[m] then Ly[n] (complex T).
@@ -181,10 +183,14 @@ __device__ __forceinline__ void jones_fill(JonesTab<T>& jt, const ElemSet& E, co
 }
 
 // Applies element e to (c0, c1). Returns the state after it. jt: the element's Jones matrices.
+// ph (nullable): receives the mask phasors exp(i phi) of an SLM (ph[0]) or super-SLM (ph[0],
+// ph[1]), so that an adjoint can reuse them. Pixel i sits at column m = i % nx, row n = i / nx
+// (formed only for lenses).
 template <typename T>
 __device__ __forceinline__ void elem_fwd(const ElemSet& E, const ElemDims& d, const cplx<T>* lens,
-                                         int nlens, int e, int b, int64_t i, int m, int n,
-                                         cplx<T>& c0, cplx<T>& c1, cplx<T>& c2, const JonesTab<T>& jt) {
+                                         int nlens, int e, int b, int64_t i, cplx<T>& c0,
+                                         cplx<T>& c1, cplx<T>& c2, const JonesTab<T>& jt,
+                                         cplx<T>* ph = nullptr) {
   switch (E.kind[e]) {
     case XL_SLM: {
       T s, c;
@@ -192,17 +198,21 @@ __device__ __forceinline__ void elem_fwd(const ElemSet& E, const ElemDims& d, co
       c0 = cmul(c0, mk(c, s));
       c1 = cmul(c1, mk(c, s));
       c2 = cmul(c2, mk(c, s));
+      if (ph) ph[0] = mk(c, s);
       break;
     }
     case XL_SSLM: {
       T s, c;
       xsincos(phase_at<T>(E.phx[e], E.phstride[e], b, i), &s, &c);
       c0 = cmul(c0, mk(c, s));
+      if (ph) ph[0] = mk(c, s);
       xsincos(phase_at<T>(E.phy[e], E.phstride[e], b, i), &s, &c);
       c1 = cmul(c1, mk(c, s));
+      if (ph) ph[1] = mk(c, s);
       break;
     }
     case XL_LENS: {
+      const int m = (int)i % d.nx, n = (int)i / d.nx;  // plane < 2^31: 32-bit division
       cplx<T> L = lens_factor<T>(lens, E.lens_slot[e], d.params_dev ? b : 0, nlens, d, m, n);
       c0 = cmul(c0, L);
       c1 = cmul(c1, L);
@@ -238,11 +248,10 @@ __global__ void __launch_bounds__(256) k_elem_fwd(const cplx<T>* __restrict__ in
   for (int k = 0; k < kPixFwd; ++k) {
     const int64_t i = ((int64_t)blockIdx.x * kPixFwd + k) * blockDim.x + threadIdx.x;
     if (i >= d.plane) break;
-    const int m = (int)i % d.nx, n = (int)i / d.nx;  // plane < 2^31: 32-bit division
     cplx<T> c0 = src[i];
     cplx<T> c1 = d.comps_in >= 2 ? src[d.plane + i] : mk((T)0, (T)0);
     cplx<T> c2 = d.comps_in == 3 ? src[2 * d.plane + i] : mk((T)0, (T)0);
-    for (int e = 0; e < E.n; ++e) elem_fwd<T>(E, d, lens, nlens, e, b, i, m, n, c0, c1, c2, jt);
+    for (int e = 0; e < E.n; ++e) elem_fwd<T>(E, d, lens, nlens, e, b, i, c0, c1, c2, jt);
     dst[i] = c0;
     if (d.comps_out >= 2) dst[d.plane + i] = c1;
     if (d.comps_out == 3) dst[2 * d.plane + i] = c2;
@@ -295,8 +304,8 @@ __global__ void __launch_bounds__(256) k_elem_bwd(const cplx<T>* __restrict__ go
       const int64_t i = ((int64_t)blockIdx.x * pix + k) * blockDim.x + threadIdx.x;
       const bool live = i < d.plane;
       const int64_t ii = live ? i : d.plane - 1;
-      const int m = (int)ii % d.nx, n = (int)ii / d.nx;
       cplx<T> s0[NE + 1], s1[NE + 1], s2[NE + 1];
+      cplx<T> ph[NE > 0 ? NE : 1][2];  // mask phasors of the SLMs, reused by their adjoints
       const cplx<T>* src = in + (int64_t)b * d.comps_in * d.plane;
       s0[0] = src[ii];
       s1[0] = d.comps_in >= 2 ? src[d.plane + ii] : mk((T)0, (T)0);
@@ -306,7 +315,7 @@ __global__ void __launch_bounds__(256) k_elem_bwd(const cplx<T>* __restrict__ go
         s0[e + 1] = s0[e];
         s1[e + 1] = s1[e];
         s2[e + 1] = s2[e];
-        elem_fwd<T>(E, d, lens, nlens, e, b, ii, m, n, s0[e + 1], s1[e + 1], s2[e + 1], jt);
+        elem_fwd<T>(E, d, lens, nlens, e, b, ii, s0[e + 1], s1[e + 1], s2[e + 1], jt, ph[e]);
       }
       const cplx<T>* gsrc = gout + (int64_t)b * d.comps_out * d.plane;
       cplx<T> g0 = gsrc[ii];
@@ -319,24 +328,20 @@ __global__ void __launch_bounds__(256) k_elem_bwd(const cplx<T>* __restrict__ go
         switch (E.kind[e]) {
           case XL_SLM: {
             gphx_acc[e] += cmulc(g0, o0).y + cmulc(g1, o1).y + cmulc(g2, o2).y;
-            T s, c;
-            xsincos(phase_at<T>(E.phx[e], E.phstride[e], b, ii), &s, &c);
-            g0 = cmul(g0, mk(c, -s));
-            g1 = cmul(g1, mk(c, -s));
-            g2 = cmul(g2, mk(c, -s));
+            g0 = cmulc(g0, ph[e][0]);
+            g1 = cmulc(g1, ph[e][0]);
+            g2 = cmulc(g2, ph[e][0]);
             break;
           }
           case XL_SSLM: {
             gphx_acc[e] += cmulc(g0, o0).y;
             gphy_acc[e] += cmulc(g1, o1).y;
-            T s, c;
-            xsincos(phase_at<T>(E.phx[e], E.phstride[e], b, ii), &s, &c);
-            g0 = cmul(g0, mk(c, -s));
-            xsincos(phase_at<T>(E.phy[e], E.phstride[e], b, ii), &s, &c);
-            g1 = cmul(g1, mk(c, -s));
+            g0 = cmulc(g0, ph[e][0]);
+            g1 = cmulc(g1, ph[e][1]);
             break;
           }
           case XL_LENS: {
+            const int m = (int)ii % d.nx, n = (int)ii / d.nx;
             const T xm = (T)d.x0 + (T)m * (T)d.dx, yn = (T)d.y0 + (T)n * (T)d.dy;
             const T coef = jt.lens_c[e] * (xm * xm + yn * yn);  // d out / d f = i coef out
             sg[e][0] += wlive * (cdot_re(g0, mk(-o0.y * coef, o0.x * coef)) +

@@ -40,10 +40,13 @@ struct LossDims {
   const void* target;  // MSE target intensity [batch][ny][nx] (real) or nullptr
 };
 
-template <typename T>
+// NC: the field's component count (1..3), a compile-time constant so that the component loop
+// unrolls and the loads of consecutive pixels can be in flight together.
+template <typename T, int NC>
 __device__ __forceinline__ T intensity_of(const cplx<T>* f, const LossDims& d, int64_t i) {
   T s = 0;
-  for (int c = 0; c < d.comps; ++c)
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
     if (d.mask & (1u << c)) {
       cplx<T> e = f[c * d.plane + i];
       s += e.x * e.x + e.y * e.y;
@@ -59,12 +62,12 @@ template <typename T> __device__ __forceinline__ T sted_eff(T ie, T idp, T beta)
 
 // Camera intensity of batch element b at pixel i: |E|^2 over the selected components, or the
 // STED effective intensity of the excitation (f) and depletion (d.dep) fields.
-template <typename T>
+template <typename T, int NC>
 __device__ __forceinline__ T intensity(const cplx<T>* f, const LossDims& d, int64_t i, int b) {
-  const T ie = intensity_of<T>(f, d, i);
+  const T ie = intensity_of<T, NC>(f, d, i);
   if (!d.dep) return ie;
-  const cplx<T>* g = (const cplx<T>*)d.dep + (int64_t)b * d.comps * d.plane;
-  return sted_eff<T>(ie, intensity_of<T>(g, d, i), (T)d.beta);
+  const cplx<T>* g = (const cplx<T>*)d.dep + (int64_t)b * NC * d.plane;
+  return sted_eff<T>(ie, intensity_of<T, NC>(g, d, i), (T)d.beta);
 }
 
 __device__ __forceinline__ double bsum(double v, double* red) {
@@ -107,22 +110,22 @@ __device__ __forceinline__ void for_pixels(const LossDims& d, F&& fn) {
 }
 
 // Sweep 1. partial: [batch][blocks][3]. grid (loss_blocks, batch).
-template <typename T>
+template <typename T, int NC, int MODE>
 __global__ void __launch_bounds__(kLossThreads) k_loss_sweep1(const cplx<T>* __restrict__ field, LossDims d,
                                                               double* __restrict__ partial,
                                                               T* __restrict__ inten) {
   __shared__ double red[32];
   const int b = blockIdx.y;
-  const cplx<T>* f = field + (int64_t)b * d.comps * d.plane;
+  const cplx<T>* f = field + (int64_t)b * NC * d.plane;
   T s0 = 0, s1 = 0, s2 = 0;
   for_pixels<T>(d, [&](int64_t i, T x, T y) {
-    const T I = intensity<T>(f, d, i, b);
+    const T I = intensity<T, NC>(f, d, i, b);
     if (inten) inten[(int64_t)b * d.plane + i] = I;
-    if (d.mode == XL_SECOND_MOMENT) {
+    if (MODE == XL_SECOND_MOMENT) {
       s0 += I;
       s1 += I * x;
       s2 += I * y;
-    } else if (d.mode == XL_MSE) {
+    } else if (MODE == XL_MSE) {
       const T e = I - ((const T*)d.target)[(int64_t)b * d.plane + i];
       s0 += e * e;
     } else {
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_sweep1(const cplx<T>* __r
     }
   });
   double* p = partial + ((int64_t)b * gridDim.x + blockIdx.x) * 3;
-  if (d.mode == XL_SECOND_MOMENT || d.mode == XL_MSE) {
+  if (MODE == XL_SECOND_MOMENT || MODE == XL_MSE) {
     double a = bsum((double)s0, red), bx = bsum((double)s1, red), by = bsum((double)s2, red);
     if (threadIdx.x == 0) {
       p[0] = a;
@@ -144,28 +147,28 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_sweep1(const cplx<T>* __r
 }
 
 // Sweep 2 (needs st[b][.] from finalise 1). partial: [batch][blocks][3].
-template <typename T>
+template <typename T, int NC, int MODE>
 __global__ void __launch_bounds__(kLossThreads) k_loss_sweep2(const cplx<T>* __restrict__ field, LossDims d,
                                                               const double* __restrict__ st,
                                                               double* __restrict__ partial) {
   __shared__ double red[32];
   const int b = blockIdx.y;
-  const cplx<T>* f = field + (int64_t)b * d.comps * d.plane;
+  const cplx<T>* f = field + (int64_t)b * NC * d.plane;
   const double* sb = st + (int64_t)b * 8;
   T s0 = 0, s1 = 0;
-  if (d.mode == XL_MSE) {
+  if (MODE == XL_MSE) {
     // single sweep: nothing to add
-  } else if (d.mode == XL_SECOND_MOMENT) {
+  } else if (MODE == XL_SECOND_MOMENT) {
     const T xb = (T)sb[1], yb = (T)sb[2];
     for_pixels<T>(d, [&](int64_t i, T x, T y) {
-      const T I = intensity<T>(f, d, i, b);
+      const T I = intensity<T, NC>(f, d, i, b);
       const T ex = x - xb, ey = y - yb;
       s0 += I * (ex * ex + ey * ey);
     });
   } else {
     const T thr = (T)sb[3];
     for_pixels<T>(d, [&](int64_t i, T, T) {
-      const T I = intensity<T>(f, d, i, b);
+      const T I = intensity<T, NC>(f, d, i, b);
       if (I > thr) {
         s0 += (T)1;
         s1 += I;
@@ -248,17 +251,17 @@ __global__ void k_loss_fin2(const double* __restrict__ partial, int nblk, LossDi
 // g_dep = 2 g dL/dI_eff dI_eff/dI_dep E_dep, with dI_eff/dI_ex = 1 - beta + beta e^{-r} (1 + r),
 // dI_eff/dI_dep = -beta e^{-r}, r = I_dep / I_ex (limits (1 - beta, 0) at I_ex = 0).
 // grid (blocks, batch).
-template <typename T>
+template <typename T, int NC, int MODE>
 __global__ void __launch_bounds__(kLossThreads) k_loss_grad(const cplx<T>* __restrict__ field, LossDims d,
                                                             const double* __restrict__ st,
                                                             const double* __restrict__ g_loss,
                                                             cplx<T>* __restrict__ gf,
                                                             cplx<T>* __restrict__ gdep) {
   const int b = blockIdx.y;
-  const cplx<T>* f = field + (int64_t)b * d.comps * d.plane;
-  const cplx<T>* fd = d.dep ? (const cplx<T>*)d.dep + (int64_t)b * d.comps * d.plane : nullptr;
-  cplx<T>* g = gf + (int64_t)b * d.comps * d.plane;
-  cplx<T>* gd = gdep ? gdep + (int64_t)b * d.comps * d.plane : nullptr;
+  const cplx<T>* f = field + (int64_t)b * NC * d.plane;
+  const cplx<T>* fd = d.dep ? (const cplx<T>*)d.dep + (int64_t)b * NC * d.plane : nullptr;
+  cplx<T>* g = gf + (int64_t)b * NC * d.plane;
+  cplx<T>* gd = gdep ? gdep + (int64_t)b * NC * d.plane : nullptr;
   const double* sb = st + (int64_t)b * 8;
   const double gl = g_loss ? g_loss[b] : 1.0;
   const T xb = (T)sb[1], yb = (T)sb[2], L = (T)sb[5], iP = (T)(1.0 / sb[0]);
@@ -266,18 +269,18 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_grad(const cplx<T>* __res
   const T beta = (T)d.beta;
   for_pixels<T>(d, [&](int64_t i, T x, T y) {
     T dI;
-    if (d.mode == XL_SECOND_MOMENT) {
+    if (MODE == XL_SECOND_MOMENT) {
       const T ex = x - xb, ey = y - yb;
       dI = (ex * ex + ey * ey - L) * iP;
-    } else if (d.mode == XL_MSE) {
-      dI = (T)2 * (intensity<T>(f, d, i, b) - ((const T*)d.target)[(int64_t)b * d.plane + i]) /
+    } else if (MODE == XL_MSE) {
+      dI = (T)2 * (intensity<T, NC>(f, d, i, b) - ((const T*)d.target)[(int64_t)b * d.plane + i]) /
            (T)d.plane;
     } else {
-      dI = intensity<T>(f, d, i, b) > thr ? dens : (T)0;
+      dI = intensity<T, NC>(f, d, i, b) > thr ? dens : (T)0;
     }
     T wex = (T)(2.0 * gl) * dI, wdp = (T)0;
     if (fd) {
-      const T ie = intensity_of<T>(f, d, i), idp = intensity_of<T>(fd, d, i);
+      const T ie = intensity_of<T, NC>(f, d, i), idp = intensity_of<T, NC>(fd, d, i);
       if (ie > (T)0) {
         const T r = idp / ie, e = exp(-r);
         wdp = wex * (-beta * e);
@@ -286,7 +289,8 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_grad(const cplx<T>* __res
         wex = wex * ((T)1 - beta);
       }
     }
-    for (int c = 0; c < d.comps; ++c) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
       const bool on = (d.mask & (1u << c)) != 0;
       g[c * d.plane + i] = on ? cscale(f[c * d.plane + i], wex) : mk((T)0, (T)0);
       if (gd) gd[c * d.plane + i] = on ? cscale(fd[c * d.plane + i], wdp) : mk((T)0, (T)0);
@@ -351,15 +355,18 @@ int loss_blocks(const LossDims& d) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(need, 2 * (int64_t)sm_count()));
 }
 
-// Both sweeps and finalisers; st / loss in the workspace or caller memory.
-template <typename T>
-xl_status loss_stats(const void* field, int32_t batch, const LossDims& d, double* st, double* loss,
-                     void* inten, double* partial, cudaStream_t s) {
+// Both sweeps and finalisers (st / loss in the workspace or caller memory) and, with `grad`, the
+// field gradient dL/dE (g_loss nullable = 1) from the statistics they leave in st.
+template <typename T, int NC, int MODE>
+xl_status loss_run(const void* field, int32_t batch, const LossDims& d, double* st, double* loss,
+                   void* inten, double* partial, bool grad, const double* g_loss, void* g_field,
+                   void* g_dep, cudaStream_t s) {
+  typedef cplx<T> C;
   const int nb = loss_blocks(d);
   dim3 grid(nb, batch);
   {
     LaunchScope ls("loss_sweep1", s);
-    k_loss_sweep1<T><<<grid, kLossThreads, 0, s>>>((const cplx<T>*)field, d, partial, (T*)inten);
+    k_loss_sweep1<T, NC, MODE><<<grid, kLossThreads, 0, s>>>((const C*)field, d, partial, (T*)inten);
     XL_CUDA_TRY(cudaGetLastError());
   }
   {
@@ -367,9 +374,9 @@ xl_status loss_stats(const void* field, int32_t batch, const LossDims& d, double
     k_loss_fin1<<<batch, 256, 0, s>>>(partial, nb, d, st);
     XL_CUDA_TRY(cudaGetLastError());
   }
-  {
+  if (MODE != XL_MSE) {
     LaunchScope ls("loss_sweep2", s);
-    k_loss_sweep2<T><<<grid, kLossThreads, 0, s>>>((const cplx<T>*)field, d, st, partial);
+    k_loss_sweep2<T, NC, MODE><<<grid, kLossThreads, 0, s>>>((const C*)field, d, st, partial);
     XL_CUDA_TRY(cudaGetLastError());
   }
   {
@@ -377,6 +384,39 @@ xl_status loss_stats(const void* field, int32_t batch, const LossDims& d, double
     k_loss_fin2<<<batch, 256, 0, s>>>(partial, nb, d, st, loss);
     XL_CUDA_TRY(cudaGetLastError());
   }
+  if (grad) {
+    LaunchScope ls("loss_grad", s);
+    k_loss_grad<T, NC, MODE><<<grid, kLossThreads, 0, s>>>((const C*)field, d, st, g_loss, (C*)g_field,
+                                                           (C*)g_dep);
+    XL_CUDA_TRY(cudaGetLastError());
+  }
+  return XL_OK;
+}
+
+template <typename T>
+xl_status loss_dispatch(const void* field, int32_t batch, const LossDims& d, double* st, double* loss,
+                        void* inten, double* partial, bool grad, const double* g_loss, void* g_field,
+                        void* g_dep, cudaStream_t s) {
+#define XL_LOSS_CASE(NC, MODE)                                                                \
+  if (d.comps == NC && d.mode == MODE)                                                        \
+    return loss_run<T, NC, MODE>(field, batch, d, st, loss, inten, partial, grad, g_loss, g_field, \
+                                 g_dep, s);
+  XL_LOSS_CASE(1, XL_SECOND_MOMENT) XL_LOSS_CASE(2, XL_SECOND_MOMENT) XL_LOSS_CASE(3, XL_SECOND_MOMENT)
+  XL_LOSS_CASE(1, XL_DENSITY) XL_LOSS_CASE(2, XL_DENSITY) XL_LOSS_CASE(3, XL_DENSITY)
+  XL_LOSS_CASE(1, XL_MSE) XL_LOSS_CASE(2, XL_MSE) XL_LOSS_CASE(3, XL_MSE)
+#undef XL_LOSS_CASE
+  return fail(XL_ERR_ARG, "loss: unsupported component count or mode");
+}
+
+// Workspace statistics [batch][8] and block partials of one call.
+xl_status loss_workspace(int32_t batch, const LossDims& d, cudaStream_t s, double** st, double** partial) {
+  const int nb = loss_blocks(d);
+  void* ws = nullptr;
+  const size_t st_bytes = (size_t)batch * 8 * sizeof(double);
+  const size_t pb = (size_t)batch * nb * 3 * sizeof(double);
+  XL_TRY(workspace(s, st_bytes + pb + 256, &ws, 3));
+  *st = (double*)ws;
+  *partial = (double*)((char*)ws + ((st_bytes + 255) & ~(size_t)255));
   return XL_OK;
 }
 
@@ -397,15 +437,11 @@ xl_status xl_intensity_loss_ex(const void* field, const void* field_dep, const v
   if (batch == 0) return XL_OK;
   if (!loss) return fail(XL_ERR_ARG, "loss is NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  const int nb = loss_blocks(d);
-  void* ws = nullptr;
-  const size_t st_bytes = (size_t)batch * 8 * sizeof(double);
-  const size_t pb = (size_t)batch * nb * 3 * sizeof(double);
-  XL_TRY(workspace(s, st_bytes + pb + 256, &ws, 3));
-  double* st = (double*)ws;
-  double* partial = (double*)((char*)ws + ((st_bytes + 255) & ~(size_t)255));
-  return dtype == XL_C128 ? loss_stats<double>(field, batch, d, st, loss, intensity, partial, s)
-                          : loss_stats<float>(field, batch, d, st, loss, intensity, partial, s);
+  double *st = nullptr, *partial = nullptr;
+  XL_TRY(loss_workspace(batch, d, s, &st, &partial));
+  return dtype == XL_C128
+             ? loss_dispatch<double>(field, batch, d, st, loss, intensity, partial, false, nullptr, nullptr, nullptr, s)
+             : loss_dispatch<float>(field, batch, d, st, loss, intensity, partial, false, nullptr, nullptr, nullptr, s);
 }
 
 xl_status xl_intensity_loss(const void* field, int32_t batch, int32_t comps, uint32_t comp_mask,
@@ -416,12 +452,11 @@ xl_status xl_intensity_loss(const void* field, int32_t batch, int32_t comps, uin
                               0.0, loss, intensity, dtype, stream);
 }
 
-xl_status xl_intensity_loss_ex_backward(const void* field, const void* field_dep,
-                                        const void* target, int32_t batch, int32_t comps,
-                                        uint32_t comp_mask, const xl_grid* grid, int32_t mode,
-                                        double eps, double beta, const double* g_loss,
-                                        void* g_field, void* g_field_dep, int32_t dtype,
-                                        void* stream) {
+namespace {
+xl_status loss_grad_call(const void* field, const void* field_dep, const void* target, int32_t batch,
+                         int32_t comps, uint32_t comp_mask, const xl_grid* grid, int32_t mode,
+                         double eps, double beta, double* loss, const double* g_loss, void* g_field,
+                         void* g_field_dep, int32_t dtype, void* stream) {
   LossDims d;
   XL_TRY(loss_check(field, batch, comps, comp_mask, grid, mode, eps, dtype, &d, field_dep, beta,
                     target));
@@ -430,28 +465,33 @@ xl_status xl_intensity_loss_ex_backward(const void* field, const void* field_dep
   if (g_field == field) return fail(XL_ERR_ARG, "g_field may not alias field");
   if (field_dep && !g_field_dep) return fail(XL_ERR_ARG, "g_field_dep is NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  const int nb = loss_blocks(d);
-  void* ws = nullptr;
-  const size_t st_bytes = (size_t)batch * 8 * sizeof(double);
-  const size_t pb = (size_t)batch * nb * 3 * sizeof(double);
-  XL_TRY(workspace(s, st_bytes + pb + 256, &ws, 3));
-  double* st = (double*)ws;
-  double* partial = (double*)((char*)ws + ((st_bytes + 255) & ~(size_t)255));
-  if (dtype == XL_C128) {
-    XL_TRY(loss_stats<double>(field, batch, d, st, nullptr, nullptr, partial, s));
-    LaunchScope ls("loss_grad", s);
-    k_loss_grad<double><<<dim3(nb, batch), kLossThreads, 0, s>>>(
-        (const cplx<double>*)field, d, st, g_loss, (cplx<double>*)g_field,
-        (cplx<double>*)(field_dep ? g_field_dep : nullptr));
-  } else {
-    XL_TRY(loss_stats<float>(field, batch, d, st, nullptr, nullptr, partial, s));
-    LaunchScope ls("loss_grad", s);
-    k_loss_grad<float><<<dim3(nb, batch), kLossThreads, 0, s>>>(
-        (const cplx<float>*)field, d, st, g_loss, (cplx<float>*)g_field,
-        (cplx<float>*)(field_dep ? g_field_dep : nullptr));
-  }
-  XL_CUDA_TRY(cudaGetLastError());
-  return XL_OK;
+  double *st = nullptr, *partial = nullptr;
+  XL_TRY(loss_workspace(batch, d, s, &st, &partial));
+  void* gdep = field_dep ? g_field_dep : nullptr;
+  return dtype == XL_C128
+             ? loss_dispatch<double>(field, batch, d, st, loss, nullptr, partial, true, g_loss, g_field, gdep, s)
+             : loss_dispatch<float>(field, batch, d, st, loss, nullptr, partial, true, g_loss, g_field, gdep, s);
+}
+}  // namespace
+
+xl_status xl_intensity_loss_ex_backward(const void* field, const void* field_dep,
+                                        const void* target, int32_t batch, int32_t comps,
+                                        uint32_t comp_mask, const xl_grid* grid, int32_t mode,
+                                        double eps, double beta, const double* g_loss,
+                                        void* g_field, void* g_field_dep, int32_t dtype,
+                                        void* stream) {
+  return loss_grad_call(field, field_dep, target, batch, comps, comp_mask, grid, mode, eps, beta,
+                        nullptr, g_loss, g_field, g_field_dep, dtype, stream);
+}
+
+xl_status xl_intensity_loss_and_grad(const void* field, const void* field_dep, const void* target,
+                                     int32_t batch, int32_t comps, uint32_t comp_mask,
+                                     const xl_grid* grid, int32_t mode, double eps, double beta,
+                                     double* loss, void* g_field, void* g_field_dep, int32_t dtype,
+                                     void* stream) {
+  if (!loss) return fail(XL_ERR_ARG, "loss is NULL");
+  return loss_grad_call(field, field_dep, target, batch, comps, comp_mask, grid, mode, eps, beta,
+                        loss, nullptr, g_field, g_field_dep, dtype, stream);
 }
 
 xl_status xl_intensity_loss_backward(const void* field, int32_t batch, int32_t comps,

@@ -114,6 +114,8 @@ SIGNATURES = {
     "xl_intensity_loss_ex": ([_P, _P, _P, _I, _I, ctypes.c_uint32, _GP, _I, _D, _D, _P, _P, _I, _P], _I),
     "xl_intensity_loss_ex_backward": ([_P, _P, _P, _I, _I, ctypes.c_uint32, _GP, _I, _D, _D, _P, _P,
                                        _P, _I, _P], _I),
+    "xl_intensity_loss_and_grad": ([_P, _P, _P, _I, _I, ctypes.c_uint32, _GP, _I, _D, _D, _P, _P, _P,
+                                    _I, _P], _I),
     "xl_softmin": ([_P, _I, _I, _D, _P, _P, _P], _I),
     "xl_device_status": ([_P], _I),
     "xl_asczt_propagate": ([_P, _P, _I, _GP, _WP, _D, _P, _I, _I, _P], _I),
@@ -592,6 +594,25 @@ def intensity_loss_backward(field: torch.Tensor, grid, comp_mask: int, mode: int
                                              g_loss.data_ptr() if g_loss is not None else None,
                                              out.data_ptr(), _dtype(field), _stream()))
     return out
+
+
+def intensity_loss_and_grad(field: torch.Tensor, grid, comp_mask: int, mode: int = SECOND_MOMENT,
+                            eps: float = 0.5, out: torch.Tensor | None = None,
+                            loss: torch.Tensor | None = None):
+    """(loss [B] float64, dL/dE) of intensity_loss in one call (xl_intensity_loss_and_grad)."""
+    _dev(field, "field")
+    B, C, ny, nx = field.shape
+    g = Grid.of(grid)
+    if loss is None:
+        loss = torch.empty(B, dtype=torch.float64, device=field.device)
+    if out is None:
+        out = torch.empty_like(field)
+    _check(load().xl_intensity_loss_and_grad(field.data_ptr(), None, None, B, C, comp_mask,
+                                             ctypes.byref(g), mode, float(eps), 0.0,
+                                             _dev(loss, "loss").data_ptr(),
+                                             _dev(out, "out").data_ptr(), None, _dtype(field),
+                                             _stream()))
+    return loss, out
 
 
 def intensity_loss_ex(field: torch.Tensor, grid, comp_mask: int, mode: int = SECOND_MOMENT,

@@ -39,3 +39,18 @@ def test_oracle_and_library_share_no_source():
     for f in glob.glob(os.path.join(ROOT, "paper_2310_08408_gb300", "*.py")):
         src = open(f).read()
         assert not re.search(r"^\s*(import|from)\s+oracle", src, flags=re.M), f
+
+
+def test_binding_calls_match_signatures():
+    """Every call the binding makes to an entry point passes as many arguments as its ctypes
+    signature declares (checked on the source, no GPU needed)."""
+    import ast
+    src = open(os.path.join(ROOT, "paper_2310_08408_gb300", "xl.py")).read()
+    bad = []
+    for node in ast.walk(ast.parse(src)):
+        if (isinstance(node, ast.Call) and isinstance(node.func, ast.Attribute)
+                and node.func.attr in xl.SIGNATURES
+                and not any(isinstance(a, ast.Starred) for a in node.args)):
+            if len(node.args) != len(xl.SIGNATURES[node.func.attr][0]):
+                bad.append((node.func.attr, node.lineno))
+    assert not bad, bad

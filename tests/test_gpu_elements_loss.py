@@ -154,3 +154,24 @@ def test_adam_matches_oracle_over_steps(rdtype):
     tol = 1e-6 if rdtype == np.float32 else 1e-14
     assert np.max(np.abs(to_np(p) - pr)) < tol
     assert int(to_np(t)[0]) == 5
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("comps,mask", [(1, 1), (3, 0b111), (3, 0b100)])
+def test_loss_and_grad_in_one_call(mode, comps, mask):
+    """xl_intensity_loss_and_grad equals the two calls it replaces (same statistics and kernels:
+    bit for bit) and the oracle (loss 1e-4, gradient relative L2 1e-3... at complex64)."""
+    import torch
+    xl = lib()
+    g = inputs.Grid(96, 80, 0.7, 0.6, -33.6, -24.0)
+    f = np.stack([inputs.random_unit(6100 + c, (80, 96)) * inputs.gaussian(g, 15.0)
+                  for c in range(comps)])[None].astype(np.complex64)
+    F = to_dev(f, np.complex64)
+    l1, _ = xl.intensity_loss(F, g, mask, mode, 0.4)
+    g1 = xl.intensity_loss_backward(F, g, mask, mode, 0.4)
+    l2, g2 = xl.intensity_loss_and_grad(F, g, mask, mode, 0.4)
+    assert torch.equal(l1, l2) and torch.equal(g1, g2)
+    L, _ = oracle.intensity_loss(f[0].astype(np.complex128), g.astuple(), mask, mode, 0.4)
+    G = oracle.intensity_loss_backward(f[0].astype(np.complex128), g.astuple(), mask, mode, 0.4)
+    assert abs(float(l2.cpu()[0]) - L) <= TOL_LOSS * abs(L)
+    assert rel(to_np(g2)[0], G) < 1e-3
