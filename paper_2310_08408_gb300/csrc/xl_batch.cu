@@ -226,9 +226,10 @@ xl_status group_step(xl_batch* b, Group& G, cudaStream_t s) {
   XL_TRY(xl_apply_elements(G.a3, G.a4, cnt, 3, g, lam, e_lens, 1, G.pl, zf, dt, s));
   // the VCZT distance is the fixed focal length: host distances, cached chirp tables
   XL_TRY(xl_czt_propagate(G.a4, G.a5, cnt, 2, g, &win, lam, G.zf.data(), 0, dt, s));
-  XL_TRY(xl_intensity_loss(G.a5, cnt, 3, 7u, &wg, XL_SECOND_MOMENT, 0.0, G.loss, nullptr, dt, s));
-  // backward; the gradients alternate between gx and gy (a4, in gx, is not read any more)
-  XL_TRY(xl_intensity_loss_backward(G.a5, cnt, 3, 7u, &wg, XL_SECOND_MOMENT, 0.0, nullptr, G.g5, dt, s));
+  // the loss and, starting the backward, its gradient; the gradients then alternate between gx
+  // and gy (a4, in gx, is not read any more)
+  XL_TRY(xl_intensity_loss_and_grad(G.a5, nullptr, nullptr, cnt, 3, 7u, &wg, XL_SECOND_MOMENT, 0.0, 0.0,
+                                    G.loss, G.g5, nullptr, dt, s));
   XL_TRY(xl_czt_propagate_backward(G.g5, nullptr, G.gx, nullptr, cnt, 2, g, &win, lam, G.zf.data(), 0,
                                    dt, s));
   XL_TRY(xl_apply_elements_backward(G.gx, G.a3, G.gy, cnt, 3, g, lam, e_lens, 1, G.pl, zf,

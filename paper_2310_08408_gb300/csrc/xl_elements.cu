@@ -281,7 +281,7 @@ constexpr int kPixBwd = 8;
 // NE: the number of elements (E.n), a compile-time bound so that the per-pixel states take
 // registers for NE elements only.
 template <typename T, int NE>
-__global__ void __launch_bounds__(256) k_elem_bwd(const cplx<T>* __restrict__ gout, const cplx<T>* __restrict__ in,
+__global__ void __launch_bounds__(256, NE <= 1 && sizeof(T) == 4 ? 4 : 1) k_elem_bwd(const cplx<T>* __restrict__ gout, const cplx<T>* __restrict__ in,
                                                   cplx<T>* __restrict__ gin, ElemSet E, ElemDims d,
                                                   const cplx<T>* __restrict__ lens, int nlens,
                                                   ElemGrad G, int batch, int pix) {
@@ -300,7 +300,10 @@ __global__ void __launch_bounds__(256) k_elem_bwd(const cplx<T>* __restrict__ go
     T sg[NE > 0 ? NE : 1][4];
 #pragma unroll
     for (int e = 0; e < NE; ++e) sg[e][0] = sg[e][1] = sg[e][2] = sg[e][3] = (T)0;
-    for (int k = 0; k < pix; ++k) {
+    // the pixel count is kPixBwd or 1; the constant bound lets the loads of consecutive pixels
+    // be issued together
+#pragma unroll 4
+    for (int k = 0; k < (pix == kPixBwd ? kPixBwd : 1); ++k) {
       const int64_t i = ((int64_t)blockIdx.x * pix + k) * blockDim.x + threadIdx.x;
       const bool live = i < d.plane;
       const int64_t ii = live ? i : d.plane - 1;
