@@ -539,8 +539,14 @@ typedef struct xl_table_config {
                          checkpointing): 0 = the 2D spectra of their zero-padded inputs, kept by
                          the forwards (12 field planes a setup, no input transform in the
                          adjoints); 1 = only the fields at the optical planes, the adjoints
-                         transforming their inputs again (about half the memory a setup). */
+                         transforming their inputs again (about half the memory a setup);
+                         XL_CHECKPOINT_AUTO = 0 when the batch fits in memory_budget, else 1. */
+  int64_t memory_budget; /* 0 = no limit; else the most device memory the batch's own buffers may
+                            hold (the figure xl_batch_memory reports): xl_batch_create returns
+                            XL_ERR_NOMEM, allocating nothing, when the resolved mode needs more */
 } xl_table_config;
+
+#define XL_CHECKPOINT_AUTO 2
 
 typedef struct xl_batch xl_batch; /* opaque; owns all per-setup device buffers */
 
@@ -548,6 +554,12 @@ typedef struct xl_batch xl_batch; /* opaque; owns all per-setup device buffers *
  * Allocates with cudaMalloc (call outside stream capture). */
 xl_status xl_batch_create(const xl_table_config* cfg, int32_t n_setups, const int32_t* grid_n,
                           const double* init, uint64_t seed, xl_batch** out, void* stream);
+
+/* Device bytes xl_batch_create allocates for these setups (what xl_batch_memory then reports) in
+ * the checkpoint mode cfg->checkpoint resolves to; that mode (0 or 1) goes to *mode_out
+ * (nullable). -1 for a NULL or invalid argument. Host arithmetic only: no device call. */
+int64_t xl_batch_plan_memory(const xl_table_config* cfg, int32_t n_setups, const int32_t* grid_n,
+                             int32_t* mode_out);
 
 /* One optimisation step of every setup (see above). */
 xl_status xl_batch_step(xl_batch* batch, int32_t use_graph, void* stream);
@@ -560,11 +572,11 @@ xl_status xl_batch_step(xl_batch* batch, int32_t use_graph, void* stream);
 #define XL_BATCH_GRAD_PHI1 5
 #define XL_BATCH_GRAD_PHI2 6
 
-/* Copies one quantity of one setup to host memory (synchronises the stream). */
 /* Device bytes the batch's own buffers hold (fields, gradients, masks, moments, parameters; the
  * library's shared workspaces and table cache are reported by xl_cache_bytes). -1 for NULL. */
 int64_t xl_batch_memory(xl_batch* batch);
 
+/* Copies one quantity of one setup to host memory (synchronises the stream). */
 xl_status xl_batch_read(xl_batch* batch, int32_t what, int32_t setup, void* host_out, void* stream);
 
 /* Grid size N of a setup (-1 if out of range). */

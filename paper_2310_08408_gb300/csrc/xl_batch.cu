@@ -130,16 +130,19 @@ __global__ void k_batch_scalar_adam(double* p2, double* z1, double* z2, const do
   }
 }
 
+struct Buf {
+  void** p;
+  size_t bytes;
+};
+
+// The device buffers of a group (cnt setups of side n), in allocation order. spectra: keep the
+// RS / VRS input spectra (checkpoint 0).
 template <typename T>
-xl_status group_alloc(xl_batch* b, Group& G, const double* init, uint64_t seed, cudaStream_t s) {
+std::vector<Buf> group_buffers(const xl_table_config& c, Group& G, bool spectra) {
   const size_t cs = sizeof(cplx<T>), rs = sizeof(T);
-  const int64_t plane = (int64_t)G.n * G.n, cnt = G.count;
-  const int64_t cam = (int64_t)b->cfg.cam_m * b->cfg.cam_m;
-  const bool spectra = b->cfg.checkpoint == 0;
-  struct {
-    void** p;
-    size_t bytes;
-  } bufs[] = {
+  const size_t plane = (size_t)G.n * G.n, cnt = (size_t)G.count;
+  const size_t cam = (size_t)c.cam_m * c.cam_m;
+  return {
       {&G.src, cnt * plane * cs},     {&G.a0, cnt * plane * cs},     {&G.a1, cnt * plane * cs},
       {&G.a2, cnt * 2 * plane * cs},  {&G.a3, cnt * 3 * plane * cs},
       {&G.a5, cnt * 3 * cam * cs},    {&G.g5, cnt * 3 * cam * cs},
@@ -153,6 +156,39 @@ xl_status group_alloc(xl_batch* b, Group& G, const double* init, uint64_t seed, 
       {(void**)&G.gp2, cnt * 12 * 8}, {(void**)&G.gz1, cnt * 8},     {(void**)&G.gz2, cnt * 8},
       {(void**)&G.sm, cnt * 3 * 8},   {(void**)&G.sv, cnt * 3 * 8},  {(void**)&G.loss, cnt * 8},
   };
+}
+
+// Bytes xl_batch_create allocates for the setups' grid sizes in checkpoint mode `mode` (0 or 1):
+// every group's buffers, its setup-index table and the step counter.
+int64_t plan_bytes(const xl_table_config& c, int n_setups, const int32_t* grid_n, int mode) {
+  std::map<int, int> counts;
+  for (int i = 0; i < n_setups; ++i) counts[grid_n[i]]++;
+  int64_t total = sizeof(int32_t);
+  for (auto& kv : counts) {
+    Group G;
+    G.n = kv.first;
+    G.count = kv.second;
+    const auto bufs = c.dtype == XL_C128 ? group_buffers<double>(c, G, mode == 0)
+                                         : group_buffers<float>(c, G, mode == 0);
+    for (const Buf& bf : bufs) total += (int64_t)bf.bytes;
+    total += (int64_t)G.count * sizeof(int);
+  }
+  return total;
+}
+
+// cfg.checkpoint as the batch runs it: XL_CHECKPOINT_AUTO keeps the spectra (0) when they fit
+// in cfg.memory_budget (or when there is no budget), else the plane fields only (1).
+int resolve_checkpoint(const xl_table_config& c, int n_setups, const int32_t* grid_n) {
+  if (c.checkpoint != XL_CHECKPOINT_AUTO) return c.checkpoint;
+  if (c.memory_budget <= 0 || plan_bytes(c, n_setups, grid_n, 0) <= c.memory_budget) return 0;
+  return 1;
+}
+
+template <typename T>
+xl_status group_alloc(xl_batch* b, Group& G, const double* init, uint64_t seed, cudaStream_t s) {
+  const size_t rs = sizeof(T);
+  const int64_t plane = (int64_t)G.n * G.n, cnt = G.count;
+  const auto bufs = group_buffers<T>(b->cfg, G, b->cfg.checkpoint == 0);
   for (auto& bf : bufs)
     if (bf.bytes) XL_TRY(dalloc(b, bf.p, bf.bytes));
   G.a4 = G.gx;  // the field after the lens: read by the VCZT forward only
@@ -280,7 +316,9 @@ xl_status xl_batch_create(const xl_table_config* cfg, int32_t n_setups, const in
   if (!cfg || !grid_n || !init || !out) return fail(XL_ERR_ARG, "batch: NULL argument");
   if (n_setups < 1) return fail(XL_ERR_ARG, "batch: n_setups must be >= 1");
   if (cfg->dtype != XL_C64 && cfg->dtype != XL_C128) return fail(XL_ERR_ARG, "batch: bad dtype");
-  if (cfg->checkpoint != 0 && cfg->checkpoint != 1) return fail(XL_ERR_ARG, "batch: checkpoint must be 0 or 1");
+  if (cfg->checkpoint < 0 || cfg->checkpoint > XL_CHECKPOINT_AUTO)
+    return fail(XL_ERR_ARG, "batch: checkpoint must be 0, 1 or XL_CHECKPOINT_AUTO");
+  if (cfg->memory_budget < 0) return fail(XL_ERR_ARG, "batch: memory_budget must be >= 0");
   if (!(cfg->extent > 0) || !(cfg->wavelength > 0) || !(cfg->w0 > 0) || !(cfg->f > 0) ||
       cfg->cam_m < 1 || !(cfg->cam_width > 0))
     return fail(XL_ERR_ARG, "batch: bad table configuration");
@@ -289,9 +327,14 @@ xl_status xl_batch_create(const xl_table_config* cfg, int32_t n_setups, const in
       return fail(XL_ERR_UNSUPPORTED, "batch: grid sizes must be powers of two in [32, 4096]");
     if (!(init[3 * i + 1] > 0) || !(init[3 * i + 2] > 0)) return fail(XL_ERR_ARG, "batch: z must be > 0");
   }
+  const int mode = resolve_checkpoint(*cfg, n_setups, grid_n);
+  const int64_t need = plan_bytes(*cfg, n_setups, grid_n, mode);
+  if (cfg->memory_budget > 0 && need > cfg->memory_budget)
+    return fail(XL_ERR_NOMEM, "batch: the setups need more device memory than memory_budget");
   cudaStream_t s = (cudaStream_t)stream;
   std::unique_ptr<xl_batch> b(new xl_batch);
   b->cfg = *cfg;
+  b->cfg.checkpoint = mode;
   b->n_setups = n_setups;
   std::map<int, std::vector<int>> by_n;
   for (int i = 0; i < n_setups; ++i) by_n[grid_n[i]].push_back(i);
@@ -408,6 +451,19 @@ xl_status xl_batch_read(xl_batch* b, int32_t what, int32_t setup, void* host_out
 }
 
 int64_t xl_batch_memory(xl_batch* b) { return b ? b->bytes : -1; }
+
+int64_t xl_batch_plan_memory(const xl_table_config* cfg, int32_t n_setups, const int32_t* grid_n,
+                             int32_t* mode_out) {
+  if (!cfg || !grid_n || n_setups < 1) return -1;
+  if (cfg->dtype != XL_C64 && cfg->dtype != XL_C128) return -1;
+  if (cfg->checkpoint < 0 || cfg->checkpoint > XL_CHECKPOINT_AUTO || cfg->memory_budget < 0) return -1;
+  if (cfg->cam_m < 1) return -1;
+  for (int i = 0; i < n_setups; ++i)
+    if (!is_pow2(grid_n[i]) || grid_n[i] < 32 || grid_n[i] > 4096) return -1;
+  const int mode = resolve_checkpoint(*cfg, n_setups, grid_n);
+  if (mode_out) *mode_out = mode;
+  return plan_bytes(*cfg, n_setups, grid_n, mode);
+}
 
 int32_t xl_batch_grid(xl_batch* b, int32_t setup) {
   if (!b) return -1;

@@ -199,8 +199,10 @@ __device__ __forceinline__ void chirp_conv(C (&v)[16], C* row, int t, const C* _
 // Segmented convolution in the forward direction (grid side in, window side out):
 // v = IDFT(sum_s bhat_s DFT(a_s)), where load(s, v) fills v with segment s of the pre-chirped
 // input (zero beyond the segment). With more than one segment the running sum lives in the
-// thread's stash row `acc`. DZ: also a2 = sum_s b2hat_s DFT(a_s) in stash row `a2`.
-template <int L, bool DZ, int PLAN = 0, typename C, typename Load, typename St>
+// thread's stash row `acc`. DZ: also a2 = sum_s b2hat_s DFT(a_s) in stash row `a2`; FUSE: both
+// running sums in one loop over the samples (fewer live registers in the scalar passes; the
+// vectorial ones, with more state, allocate better with two loops).
+template <int L, bool DZ, int PLAN = 0, bool FUSE = true, typename C, typename Load, typename St>
 __device__ __forceinline__ void seg_conv_fwd(C (&v)[16], C* row, int t, const C* __restrict__ tw,
                                              const Axis<C>& ax, int nseg, bool cj, Load&& load,
                                              St& acc, St& a2) {
@@ -225,12 +227,21 @@ __device__ __forceinline__ void seg_conv_fwd(C (&v)[16], C* row, int t, const C*
     for (int s = 1; s < nseg; ++s) {
       load(s, v);
       team_fft<L, -1, PLAN>(v, row, t, tw);
+      const C* bs = ax.bhat + (int64_t)s * L;
       if constexpr (DZ) {
         const C* b2 = ax.b2hat + (int64_t)s * L;
+        if constexpr (FUSE) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const C bq = __ldg(bs + t + q * TT);
+            a2.set(q, cadd(a2.get(q), cmul(v[q], __ldg(b2 + t + q * TT))));
+            acc.set(q, cadd(acc.get(q), cj ? cmulc(v[q], bq) : cmul(v[q], bq)));
+          }
+          continue;
+        }
 #pragma unroll
         for (int q = 0; q < 16; ++q) a2.set(q, cadd(a2.get(q), cmul(v[q], __ldg(b2 + t + q * TT))));
       }
-      const C* bs = ax.bhat + (int64_t)s * L;
       if (cj) {
 #pragma unroll
         for (int q = 0; q < 16; ++q) acc.set(q, cadd(acc.get(q), cmulc(v[q], __ldg(bs + t + q * TT))));
@@ -410,6 +421,8 @@ k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d,
     auto load = [&](int s, C (&u)[16]) {
       const int m0 = s * seg, ns = min(seg, d.nx - m0);
       const Coord<T> xm(d.x0 + m0 * d.dx, d.dx, t, TT);
+      // the input samples first, then the chirp (one loop over both keeps twice the loads in
+      // flight, and the extra registers spill in the scalar passes)
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int j = t + q * TT;
@@ -418,12 +431,19 @@ k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d,
           const int m = m0 + j;
           if (c < 2) a = s0[c * plane + m];
           else a = cadd(cscale(s0[m], xm.at(q)), cscale(s0[plane + m], yn));
-          a = cmul(a, __ldg(ax.pre + m));
+          if constexpr (VEC) a = cmul(a, __ldg(ax.pre + m));
         }
         u[q] = a;
       }
+      if constexpr (!VEC) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int j = t + q * TT;
+          if (q * TT < ns && j < ns) u[q] = cmul(u[q], __ldg(ax.pre + m0 + j));
+        }
+      }
     };
-    seg_conv_fwd<L, DZ, czt_plan_of<V>()>(v, row, t, tw, ax, nseg, d.adjoint, load, acc, a2);
+    seg_conv_fwd<L, DZ, czt_plan_of<V>(), !VEC>(v, row, t, tw, ax, nseg, d.adjoint, load, acc, a2);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int p = t + q * TT;
@@ -492,7 +512,7 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
         u[q] = q * TT < ns && j < ns ? cmul(src[m0 + j], __ldg(ay.pre + m0 + j)) : mk((T)0, (T)0);
       }
     };
-    seg_conv_fwd<L, DZ, czt_plan_of<V>()>(v, row, t, tw, ay, nseg, d.adjoint, load, acc, a2);
+    seg_conv_fwd<L, DZ, czt_plan_of<V>(), !VEC>(v, row, t, tw, ay, nseg, d.adjoint, load, acc, a2);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int qq = t + q * TT;
@@ -528,6 +548,8 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
 // loaded once into the thread's stash.
 // DZ: block partial sums [b][block][6] of E1 = <G, U1>, Dy and E0 (VCZT: <Gz, X Ex' + Y Ey' - S'>)
 // from the saved forward (see the file comment); plane 2 of VCZT carries the cotangent Gz / z.
+// The window-side term (i) of Dx is summed here too, into the Dy slot: it weights the same
+// product of this pass's output row with the forward's T row, and the finaliser adds Dx and Dy.
 // grid: (ceil(mx / ROWS), nbatch).
 template <typename T, int L, bool VEC, int V = 0, bool DZ = false>
 __global__ void XL_CZT_BOUNDS(T, L, VEC, V, false)
@@ -613,8 +635,10 @@ k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, 
       v[q] = q * TT < d.my && qq < d.my ? cmulc(v[q], __ldg(ay.post + qq)) : mk((T)0, (T)0);
     }
     C* dst = Tb + (int64_t)b * d.tb_elem + c * tplane + (int64_t)p * d.ny;
-    // the forward's T row p (DZ)
+    // the forward's T row p (DZ) and the x-axis term F_x(p) of this row: the sums over the T
+    // plane of both axes' separable weights are taken here, where T row p meets its cotangent
     const C* vsv = DZ ? sv.base + (int64_t)b * sv.elem + c * tplane + (int64_t)p * d.ny : nullptr;
+    const float fx = DZ ? dz_F(d.dzx, p) : 0.f;
     auto spec = [&](const C (&f)[16]) {
       if constexpr (DZ) {
         if (live) {
@@ -635,7 +659,7 @@ k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, 
           if (q * TT < ns && j < ns) {
             const C w = cmulc(u[q], __ldg(ay.pre + m0 + j));
             dst[m0 + j] = w;
-            if constexpr (DZ) dy = cfma_conj(dy, w, vsv[m0 + j], (float)wc * dz_G(d.dzy, m0 + j));
+            if constexpr (DZ) dy = cfma_conj(dy, w, vsv[m0 + j], (float)wc * (dz_G(d.dzy, m0 + j) + fx));
           }
         }
       }
@@ -658,8 +682,9 @@ k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, 
 // Scalar: g = C_x^H(W). VEC: the Z plane first, writing (x/z) C_x^H(Z) and (y/z) C_x^H(Z) into
 // the two output planes, then g_Ex += C_x^H(A), g_Ey += C_x^H(B) (each thread adds to the
 // elements it wrote). With d.accumulate the results are added to what the output holds.
-// DZ: block partial sums [b][block][2] of Dx from the saved forward T (sv), the forward input
-// u_in and the output (see the file comment).
+// DZ: block partial sums [b][block][2] of the grid-side term (ii) of Dx, from the forward input
+// u_in and the output, and of its kernel term (iii), from the sums a2 the forward saved (see the
+// file comment; the adjoint y pass takes term (i)).
 // grid: (ceil(ny / ROWS), nbatch).
 template <typename T, int L, bool VEC, int V = 0, bool DZ = false>
 __global__ void XL_CZT_BOUNDS(T, L, VEC, V, false)
@@ -695,18 +720,6 @@ k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d
     const T wc = (VEC && c == 2) ? iz : (T)1;
     C v[16];
     load_transposed<L, ROWS>(v, sm, team, t, d.mx, Tb + (int64_t)b * d.tb_elem + c * tplane, d.ny, n0, d.ny);
-    if constexpr (DZ) {
-      C vf[16];
-      load_transposed<L, ROWS>(vf, sm, team, t, d.mx, sv.base + (int64_t)b * sv.elem + c * tplane, d.ny,
-                               n0, d.ny);
-      if (live) {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int pp = t + q * TT;
-          if (q * TT < d.mx && pp < d.mx) dx = cfma_conj(dx, v[q], vf[q], (float)wc * dz_F(d.dzx, pp));
-        }
-      }
-    }
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int pp = t + q * TT;

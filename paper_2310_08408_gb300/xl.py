@@ -76,7 +76,9 @@ class TableConfig(ctypes.Structure):
     _fields_ = [("wavelength", ctypes.c_double), ("extent", ctypes.c_double), ("w0", ctypes.c_double),
                 ("f", ctypes.c_double), ("cam_width", ctypes.c_double), ("lr", ctypes.c_double),
                 ("lr_z", ctypes.c_double), ("cam_m", ctypes.c_int32), ("dtype", ctypes.c_int32),
-                ("checkpoint", ctypes.c_int32)]
+                ("checkpoint", ctypes.c_int32), ("memory_budget", ctypes.c_int64)]
+
+CHECKPOINT_AUTO = 2
 
 
 BATCH_LOSS, BATCH_SCALARS, BATCH_GRAD_SCALARS, BATCH_PHI1, BATCH_PHI2, BATCH_GRAD_PHI1, BATCH_GRAD_PHI2 = range(7)
@@ -133,6 +135,7 @@ SIGNATURES = {
     "xl_step_advance": ([_P, _P], _I),
     "xl_batch_create": ([ctypes.POINTER(TableConfig), _I, _P, _P, ctypes.c_uint64,
                          ctypes.POINTER(ctypes.c_void_p), _P], _I),
+    "xl_batch_plan_memory": ([ctypes.POINTER(TableConfig), _I, _P, ctypes.POINTER(_I)], ctypes.c_int64),
     "xl_batch_step": ([_P, _I, _P], _I),
     "xl_batch_read": ([_P, _I, _I, _P, _P], _I),
     "xl_batch_grid": ([_P, _I], _I),
@@ -814,19 +817,37 @@ def step_advance(t: torch.Tensor) -> None:
 
 
 # ----------------------------------------------------------------------------- batched tables
+def table_config(cfg: dict) -> TableConfig:
+    """The xl_table_config of a Batch configuration dict (see Batch)."""
+    return TableConfig(float(cfg["wavelength"]), float(cfg["extent"]), float(cfg["w0"]),
+                       float(cfg["f"]), float(cfg["cam_width"]), float(cfg["lr"]),
+                       float(cfg["lr_z"]), int(cfg["cam_m"]),
+                       C128 if cfg.get("dtype", "c64") == "c128" else C64,
+                       int(cfg.get("checkpoint", 0)), int(cfg.get("memory_budget", 0)))
+
+
+def batch_plan_memory(cfg: dict, grid_n) -> tuple:
+    """(bytes, checkpoint mode) that a Batch of these setups allocates (xl_batch_plan_memory:
+    host arithmetic, no device call)."""
+    c = table_config(cfg)
+    gn = np.ascontiguousarray(grid_n, dtype=np.int32)
+    mode = ctypes.c_int32(-1)
+    nb = int(load().xl_batch_plan_memory(ctypes.byref(c), len(gn), gn.ctypes.data, ctypes.byref(mode)))
+    if nb < 0:
+        raise XLError(ERR_ARG, "xl_batch_plan_memory: invalid configuration")
+    return nb, int(mode.value)
+
+
 class Batch:
     """Many optical-table setups optimised together (xl_batch_*). cfg: dict with wavelength,
     extent, w0, f, cam_m, cam_width, lr, lr_z, dtype ("c64" / "c128"), checkpoint (0: the RS /
     VRS adjoints read spectra the forwards keep; 1: only the plane fields are kept and the
-    adjoints transform their inputs again); grid_n: list of N per setup; init: [n][3] =
+    adjoints transform their inputs again; CHECKPOINT_AUTO: 0 if it fits in memory_budget),
+    memory_budget (bytes, 0 = no limit); grid_n: list of N per setup; init: [n][3] =
     (theta, z1, z2)."""
 
     def __init__(self, cfg: dict, grid_n, init, seed: int):
-        self.cfg = TableConfig(float(cfg["wavelength"]), float(cfg["extent"]), float(cfg["w0"]),
-                               float(cfg["f"]), float(cfg["cam_width"]), float(cfg["lr"]),
-                               float(cfg["lr_z"]), int(cfg["cam_m"]),
-                               C128 if cfg.get("dtype", "c64") == "c128" else C64,
-                               int(cfg.get("checkpoint", 0)))
+        self.cfg = table_config(cfg)
         self.n = len(grid_n)
         gn = np.ascontiguousarray(grid_n, dtype=np.int32)
         ini = np.ascontiguousarray(init, dtype=np.float64).reshape(self.n, 3)

@@ -100,3 +100,24 @@ def test_batch_checkpoint_mode_memory_and_steps():
         assert np.allclose(c.read(xl.BATCH_SCALARS, s), a.read(xl.BATCH_SCALARS, s), rtol=1e-6, atol=1e-9)
     a.close()
     c.close()
+
+
+def test_batch_memory_budget():
+    """The batch allocates exactly the planned bytes in both modes; XL_CHECKPOINT_AUTO keeps the
+    spectra while they fit in memory_budget and checkpoints the plane fields when they do not;
+    a budget below the checkpointed need fails with XL_ERR_NOMEM before any allocation."""
+    xl = lib()
+    plan0, _ = xl.batch_plan_memory(dict(CFG, checkpoint=0), GRIDS)
+    plan1, _ = xl.batch_plan_memory(dict(CFG, checkpoint=1), GRIDS)
+    auto = dict(CFG, checkpoint=xl.CHECKPOINT_AUTO)
+    a = xl.Batch(dict(auto, memory_budget=plan0), GRIDS, INIT, SEED)
+    assert a.memory() == plan0
+    c = xl.Batch(dict(auto, memory_budget=plan0 - 1), GRIDS, INIT, SEED)
+    assert c.memory() == plan1
+    c.step(use_graph=True)
+    assert np.isfinite(c.read(xl.BATCH_LOSS, 0)[0])
+    a.close()
+    c.close()
+    with pytest.raises(xl.XLError) as e:
+        xl.Batch(dict(auto, memory_budget=plan1 - 1), GRIDS, INIT, SEED)
+    assert e.value.status == xl.ERR_NOMEM
