@@ -196,12 +196,12 @@ def kernel_model(name: str, fields: float):
             by = n * m + m * m + (m * L + m * m if dz else 0)
         elif name.startswith("czt_adj_y"):
             by = m * m + n * m + (m * m + n * m + m * L if dz else 0)
-        else:
-            by = n * m + n * n + (n * n + n * m + n * L if dz else 0)
+        else:  # dz: the forward input and the saved sums a2 (the T-plane term is the y pass's)
+            by = n * m + n * n + (n * n + n * L if dz else 0)
         return nb * fl, nb * by * cs
     if name == "elements_fwd":
         return None, nb * UNIT_BYTES["slm"]
-    if name == "elements_bwd":
+    if name in ("elements_bwd", "elements_bwd_mask"):
         return None, nb * UNIT_BYTES["slm_bwd"]
     if name == "adam":
         return None, nb * UNIT_BYTES["adam"]
@@ -313,6 +313,7 @@ class GpuStep:
 TABLE_CFG = dict(wavelength=0.6328, extent=1024.0, w0=200.0, f=5000.0, cam_m=256, cam_width=64.0,
                  lr=0.01, lr_z=1.0)
 TABLE_WINDOW = (256, 256, 0.25, 0.25, -32.0, -32.0)  # the tables' camera window
+TABLE_BYTES_1024 = 1.2e9  # algorithmic bytes of one 1024^2 table gradient evaluation
 
 
 def inputs_grid(n: int):
@@ -321,7 +322,7 @@ def inputs_grid(n: int):
     return inputs.Grid.centred(n, PITCH if n == N else 1024.0 / n)
 
 
-def table_section(xl, torch, setups: int, steps: int, seed: int):
+def table_section(xl, torch, setups: int, steps: int, seed: int, hbm: float):
     """Batched optical tables: `setups` setups with N drawn from {512, 1024, 2048} (seeded,
     pitch = 1024 um / N), fwd + bwd + Adam per step replayed from one CUDA graph; compared with
     the same library in complex128, one setup per call, eager launches (the plain FP64
@@ -378,17 +379,44 @@ def table_section(xl, torch, setups: int, steps: int, seed: int):
         f64[n] = e0.elapsed_time(e1)
         one.close()
     t64 = sum(f64[n] for n in grid_n)
+    # per-plane checkpointing at 2048^2: step time and bytes a setup in both modes (4 setups)
+    ckpt = {}
+    for mode in (0, 1):
+        cb = xl.Batch(dict(TABLE_CFG, checkpoint=mode), [2048] * 4, [[0.3, 20_000.0, 20_000.0]] * 4, seed)
+        cb.step(use_graph=True)
+        cb.step(use_graph=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(5):
+            cb.step(use_graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ckpt[f"checkpoint{mode}"] = {"ms_per_step": e0.elapsed_time(e1) / 5,
+                                     "bytes_per_setup": cb.memory() / 4}
+        cb.close()
     counts = {n: grid_n.count(n) for n in (512, 1024, 2048)}
+    # HBM bound of a gradient evaluation: TABLE_BYTES_1024 per 1024^2 setup, in proportion to the
+    # pixel count for the other sizes
+    bound_ms = sum(TABLE_BYTES_1024 * (n / 1024) ** 2 for n in grid_n) / (hbm * 1e9) * 1e3
+    bound1024 = TABLE_BYTES_1024 / (hbm * 1e9) * 1e3
     return {"workload": f"{setups} optical tables (N mix {counts}), fwd+bwd+Adam, CUDA graph",
             "grads_per_s": setups / (ms / 1000.0), "ms_per_step": ms,
             "fp64_single_instance_grads_per_s": setups / (t64 / 1000.0),
             "fp64_ms_per_setup": f64,
             "table1024_grads_per_s": 1000.0 / ms1024,
+            "frac_of_hbm_bound": bound_ms / ms, "table1024_frac_of_hbm_bound": bound1024 / ms1024,
+            "hbm_bound_note": f"{TABLE_BYTES_1024 / 1e9:.1f} GB per 1024^2 gradient evaluation (fwd 0.4 + "
+                              "bwd 0.8, with the trained distances' spectrum regeneration), scaled by "
+                              "pixels, at measured HBM",
             "launches_per_step": k_n, "kernel_ms_per_step": k_ms,
+            "top_kernels_ms": {k: round(v[1], 3) for k, v in
+                               sorted(prof.items(), key=lambda kv: -kv[1][1])[:10]},
             "launch_gap_frac": max(0.0, 1.0 - k_ms / ms),
             "launch_gap_note": "1 - (sum of the step's kernel durations, CUDA events per launch) / "
                                "(graph replay time per step)",
-            "speedup_vs_fp64_single_instance": t64 / ms}
+            "speedup_vs_fp64_single_instance": t64 / ms,
+            "checkpointing_2048": dict(ckpt, workload="4 tables of 2048^2, graph replay; "
+                                       "0: RS / VRS input spectra kept, 1: plane fields only")}
 
 
 # ----------------------------------------------------------------------------- further rows
@@ -909,7 +937,7 @@ def main():
 
     table = None
     if not a.no_table:
-        table = table_section(xl, torch, a.table_setups, a.table_steps, inputs_seed(rank))
+        table = table_section(xl, torch, a.table_setups, a.table_steps, inputs_seed(rank), hbm)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -924,6 +952,8 @@ def main():
             "data": "synthetic",
             "config": bench_config(B, world),
             "grads_per_s": grads,
+            "tables_grads_per_s": table["grads_per_s"] if table else None,
+            "tables_frac_of_hbm_bound": table["frac_of_hbm_bound"] if table else None,
             "gpu_launches": int(launches),
             "clocks": ck,
             "roofline": roof,

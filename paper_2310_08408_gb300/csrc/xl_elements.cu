@@ -424,6 +424,74 @@ __global__ void __launch_bounds__(256, NE <= 1 && sizeof(T) == 4 ? 4 : 1) k_elem
   }
 }
 
+// Adjoint of a chain that is a single phase mask (an SLM, or a super-SLM with its x and y
+// masks) with masks per batch element and no scalar parameters: per pixel it reads only the
+// input, the cotangent and the masks (no Jones table, no per-element dispatch), with the
+// arithmetic of k_elem_bwd. kPixMask pixels a thread, a compile-time count: the loads of all of
+// them are issued before the first store (lanes past the plane read its last pixel and store
+// nothing). grid: (ceil(plane / (256 kPixMask)), batch).
+constexpr int kPixMask = 4;
+
+template <typename T, int NC, bool SUPER>
+__global__ void __launch_bounds__(256) k_mask_bwd(const cplx<T>* __restrict__ gout, const cplx<T>* __restrict__ in,
+                                                  cplx<T>* __restrict__ gin, const T* __restrict__ phx,
+                                                  const T* __restrict__ phy, int64_t stride,
+                                                  T* __restrict__ gpx, T* __restrict__ gpy, int64_t plane) {
+  const int b = blockIdx.y;
+  const cplx<T>* u = in + (int64_t)b * NC * plane;
+  const cplx<T>* g = gout + (int64_t)b * NC * plane;
+  const T* px = phx + (int64_t)b * stride;
+  const T* py = SUPER ? phy + (int64_t)b * stride : nullptr;
+  cplx<T> rg[kPixMask][NC];
+  T rx[kPixMask], ry[kPixMask];
+#pragma unroll
+  for (int k = 0; k < kPixMask; ++k) {
+    const int64_t i = ((int64_t)blockIdx.x * kPixMask + k) * blockDim.x + threadIdx.x;
+    const int64_t ii = i < plane ? i : plane - 1;
+    T s, c;
+    xsincos(__ldg(px + ii), &s, &c);
+    const cplx<T> e0 = mk(c, s);
+    cplx<T> e1 = e0;
+    if constexpr (SUPER) {
+      xsincos(__ldg(py + ii), &s, &c);
+      e1 = mk(c, s);
+    }
+    cplx<T> uc[NC], gc[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      uc[q] = u[q * plane + ii];
+      gc[q] = g[q * plane + ii];
+    }
+    if constexpr (SUPER) {
+      // the x mask on Ex, the y mask on Ey, Ez unchanged
+      rx[k] = cmulc(gc[0], cmul(uc[0], e0)).y;
+      ry[k] = cmulc(gc[1], cmul(uc[1], e1)).y;
+      rg[k][0] = cmulc(gc[0], e0);
+      rg[k][1] = cmulc(gc[1], e1);
+      if constexpr (NC == 3) rg[k][2] = gc[2];
+    } else {
+      T acc = cmulc(gc[0], cmul(uc[0], e0)).y;
+#pragma unroll
+      for (int q = 1; q < NC; ++q) acc = acc + cmulc(gc[q], cmul(uc[q], e0)).y;
+      rx[k] = acc;
+      ry[k] = (T)0;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) rg[k][q] = cmulc(gc[q], e0);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kPixMask; ++k) {
+    const int64_t i = ((int64_t)blockIdx.x * kPixMask + k) * blockDim.x + threadIdx.x;
+    if (i >= plane) break;
+    if (gin) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) gin[((int64_t)b * NC + q) * plane + i] = rg[k][q];
+    }
+    if (gpx) gpx[(int64_t)b * stride + i] = rx[k];
+    if (SUPER && gpy) gpy[(int64_t)b * stride + i] = ry[k];
+  }
+}
+
 // g_params[r] = sum_k partial[r][k], r < rows (fixed order).
 __global__ void k_elem_reduce(const double* __restrict__ partial, int nblk, double* __restrict__ out) {
   __shared__ double red[32];
@@ -550,6 +618,25 @@ xl_status run_bwd(const void* gout, const void* in, void* gin, int32_t batch, co
   if (any_shared && any_batched && batch > 1)
     return fail(XL_ERR_UNSUPPORTED, "elements backward: mixing shared and per-batch masks");
   G.accumulate_shared = any_shared && batch > 1;
+  const bool one_mask = E.n == 1 && !gparams && !G.accumulate_shared && d.comps_in == d.comps_out &&
+                        (E.kind[0] == XL_SLM || (E.kind[0] == XL_SSLM && d.comps_in >= 2));
+  if (one_mask) {
+    dim3 grid((unsigned)((d.plane + 256 * kPixMask - 1) / (256 * kPixMask)), batch);
+    LaunchScope ls("elements_bwd_mask", s);
+    const bool sup = E.kind[0] == XL_SSLM;
+#define XL_MBWD(NC, SUP)                                                                            \
+  k_mask_bwd<T, NC, SUP><<<grid, 256, 0, s>>>((const cplx<T>*)gout, (const cplx<T>*)in, (cplx<T>*)gin, \
+                                              (const T*)E.phx[0], (const T*)E.phy[0], E.phstride[0],  \
+                                              (T*)G.gphx[0], (T*)G.gphy[0], d.plane)
+    if (!sup && d.comps_in == 1) XL_MBWD(1, false);
+    else if (!sup && d.comps_in == 2) XL_MBWD(2, false);
+    else if (!sup) XL_MBWD(3, false);
+    else if (d.comps_in == 2) XL_MBWD(2, true);
+    else XL_MBWD(3, true);
+#undef XL_MBWD
+    XL_CUDA_TRY(cudaGetLastError());
+    return XL_OK;
+  }
   const int pix = G.accumulate_shared ? 1 : kPixBwd;
   const int nblk = (int)((d.plane + 256 * pix - 1) / (256 * pix));
   const int lb = d.params_dev ? batch : 1;

@@ -93,9 +93,15 @@ __device__ __forceinline__ double bmax(double v, double* red) {
   return s;
 }
 
+// Pixels a thread visits per step of a row: a compile-time count with no branch between them,
+// so that their loads are all in flight together.
+constexpr int kLossPix = 4;
+
 // Pixels of a block: the rows [r0, r1) of gridDim.x equal row ranges, each row swept by the
-// block's threads in coalesced steps; fn(i, x, y) gets the pixel index and its coordinates,
-// formed in T from per-launch bases (no per-pixel integer division or double arithmetic).
+// block's threads in coalesced steps of kLossPix * blockDim.x pixels; fn(i, x, y, live) gets the
+// pixel index and its coordinates, formed in T from per-launch bases (no per-pixel integer
+// division or double arithmetic). Lanes past the row's end (live false) get the row's last
+// pixel, an in-range index, and must add nothing and store nothing.
 template <typename T, typename F>
 __device__ __forceinline__ void for_pixels(const LossDims& d, F&& fn) {
   const int rpb = (d.ny + gridDim.x - 1) / gridDim.x;
@@ -104,8 +110,15 @@ __device__ __forceinline__ void for_pixels(const LossDims& d, F&& fn) {
   for (int r = r0; r < r1; ++r) {
     const T y = Y0 + (T)r * DY;
     const int64_t base = (int64_t)r * d.nx;
-#pragma unroll 4
-    for (int xi = threadIdx.x; xi < d.nx; xi += blockDim.x) fn(base + xi, X0 + (T)xi * DX, y);
+    for (int c0 = 0; c0 < d.nx; c0 += kLossPix * (int)blockDim.x) {
+#pragma unroll
+      for (int k = 0; k < kLossPix; ++k) {
+        const int xi = c0 + k * (int)blockDim.x + (int)threadIdx.x;
+        const bool live = xi < d.nx;
+        const int xc = live ? xi : d.nx - 1;
+        fn(base + xc, X0 + (T)xc * DX, y, live);
+      }
+    }
   }
 }
 
@@ -118,15 +131,16 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_sweep1(const cplx<T>* __r
   const int b = blockIdx.y;
   const cplx<T>* f = field + (int64_t)b * NC * d.plane;
   T s0 = 0, s1 = 0, s2 = 0;
-  for_pixels<T>(d, [&](int64_t i, T x, T y) {
-    const T I = intensity<T, NC>(f, d, i, b);
-    if (inten) inten[(int64_t)b * d.plane + i] = I;
+  for_pixels<T>(d, [&](int64_t i, T x, T y, bool live) {
+    const T Iv = intensity<T, NC>(f, d, i, b);
+    if (inten && live) inten[(int64_t)b * d.plane + i] = Iv;
+    const T I = live ? Iv : (T)0;
     if (MODE == XL_SECOND_MOMENT) {
       s0 += I;
       s1 += I * x;
       s2 += I * y;
     } else if (MODE == XL_MSE) {
-      const T e = I - ((const T*)d.target)[(int64_t)b * d.plane + i];
+      const T e = live ? I - ((const T*)d.target)[(int64_t)b * d.plane + i] : (T)0;
       s0 += e * e;
     } else {
       s0 = fmax(s0, I);
@@ -160,16 +174,16 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_sweep2(const cplx<T>* __r
     // single sweep: nothing to add
   } else if (MODE == XL_SECOND_MOMENT) {
     const T xb = (T)sb[1], yb = (T)sb[2];
-    for_pixels<T>(d, [&](int64_t i, T x, T y) {
-      const T I = intensity<T, NC>(f, d, i, b);
+    for_pixels<T>(d, [&](int64_t i, T x, T y, bool live) {
+      const T I = live ? intensity<T, NC>(f, d, i, b) : (T)0;
       const T ex = x - xb, ey = y - yb;
       s0 += I * (ex * ex + ey * ey);
     });
   } else {
     const T thr = (T)sb[3];
-    for_pixels<T>(d, [&](int64_t i, T, T) {
+    for_pixels<T>(d, [&](int64_t i, T, T, bool live) {
       const T I = intensity<T, NC>(f, d, i, b);
-      if (I > thr) {
+      if (live && I > thr) {
         s0 += (T)1;
         s1 += I;
       }
@@ -267,7 +281,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_grad(const cplx<T>* __res
   const T xb = (T)sb[1], yb = (T)sb[2], L = (T)sb[5], iP = (T)(1.0 / sb[0]);
   const T thr = (T)sb[3], dens = (T)(-sb[6] / (sb[7] * sb[7]));
   const T beta = (T)d.beta;
-  for_pixels<T>(d, [&](int64_t i, T x, T y) {
+  for_pixels<T>(d, [&](int64_t i, T x, T y, bool live) {
     T dI;
     if (MODE == XL_SECOND_MOMENT) {
       const T ex = x - xb, ey = y - yb;
@@ -292,8 +306,12 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_grad(const cplx<T>* __res
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const bool on = (d.mask & (1u << c)) != 0;
-      g[c * d.plane + i] = on ? cscale(f[c * d.plane + i], wex) : mk((T)0, (T)0);
-      if (gd) gd[c * d.plane + i] = on ? cscale(fd[c * d.plane + i], wdp) : mk((T)0, (T)0);
+      const cplx<T> gv = on ? cscale(f[c * d.plane + i], wex) : mk((T)0, (T)0);
+      if (live) g[c * d.plane + i] = gv;
+      if (gd) {
+        const cplx<T> gdv = on ? cscale(fd[c * d.plane + i], wdp) : mk((T)0, (T)0);
+        if (live) gd[c * d.plane + i] = gdv;
+      }
     }
   });
 }

@@ -71,6 +71,58 @@ def test_element_chain_forward_backward(dtype, rdtype, tol, shared):
             assert rel(to_np(arr[idx]), gsum[k]) < 10 * tol
 
 
+@pytest.mark.parametrize("dtype,rdtype,tol", [(np.complex64, np.float32, TOL_C64),
+                                              (np.complex128, np.float64, TOL_C128)])
+@pytest.mark.parametrize("kind,comps", [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3)])
+@pytest.mark.parametrize("want_field", [True, False])
+def test_single_mask_backward(dtype, rdtype, tol, kind, comps, want_field):
+    """A chain of one SLM (kind 0) or super-SLM (kind 1) with masks per batch element: the
+    adjoint that reads only the input, the cotangent and the masks, on a plane that is not a
+    multiple of the pixels a block takes (37 x 53), against the oracle."""
+    xl = lib()
+    g = inputs.Grid(53, 37, 1.0, 1.0, -26.0, -18.0)
+    B = 3
+    u = inputs.random_unit(91, (B, comps, 37, 53)).astype(dtype)
+    G = inputs.random_unit(92, (B, comps, 37, 53)).astype(dtype)
+    px = np.stack([inputs.random_phase(g, 930 + b) for b in range(B)]).astype(rdtype)
+    py = np.stack([inputs.random_phase(g, 940 + b) for b in range(B)]).astype(rdtype)
+    el = dict(kind=kind, phi_x=to_dev(px, rdtype))
+    if kind == 1:
+        el["phi_y"] = to_dev(py, rdtype)
+    xl.profile_enable(True)
+    g_in, gpx, gpy, gp = xl.apply_elements_backward(to_dev(G, dtype), to_dev(u, dtype), g, LAM, [el],
+                                                    comps_in=comps, want_field=want_field,
+                                                    want_params=False)
+    launched = xl.profile_report()
+    xl.profile_enable(False)
+    assert "elements_bwd_mask" in launched and "elements_bwd" not in launched
+    for b in range(B):
+        oe = dict(kind=oracle.SLM if kind == 0 else oracle.SSLM, phi_x=px[b].astype(np.float64))
+        if kind == 1:
+            oe["phi_y"] = py[b].astype(np.float64)
+        Gb, ub = G[b].astype(np.complex128), u[b].astype(np.complex128)
+        if comps == 3:
+            # the oracle's chains take 1 or 2 components; the masks act on each component on its
+            # own (an SLM on all three, a super-SLM on Ex and Ey with Ez passed through), so the
+            # 3-component adjoint is the per-component (SLM) or (Ex, Ey) (super-SLM) one
+            if kind == 0:
+                parts = [oracle.apply_elements_backward(Gb[c], ub[c], g.astuple(), LAM, [oe])
+                         for c in range(3)]
+                rg = np.stack([p[0][0] for p in parts])
+                rpx = [sum(p[1][0] for p in parts)]
+            else:
+                rg2, rpx, rpy, _ = oracle.apply_elements_backward(Gb[:2], ub[:2], g.astuple(), LAM, [oe])
+                rg = np.concatenate([rg2, Gb[2:]])
+        else:
+            rg, rpx, rpy, _ = oracle.apply_elements_backward(Gb, ub, g.astuple(), LAM, [oe])
+        if want_field:
+            assert rel(to_np(g_in)[b], rg) < tol
+        assert rel(to_np(gpx[0])[b], rpx[0]) < 10 * tol
+        if kind == 1:
+            assert rel(to_np(gpy[0])[b], rpy[0]) < 10 * tol
+    assert (g_in is None) == (not want_field)
+
+
 def test_elements_device_parameters_match_host():
     import torch
     xl = lib()
