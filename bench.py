@@ -187,7 +187,7 @@ def kernel_model(name: str, fields: float):
         return nb * 2 * n * (3 * fft_flops(L) + 14 * L), nb * (6 * n * n + 2 * (n + 1) ** 2) * cs
     if name.startswith("czt_") and L:
         _, S = czt_plan(n, m)
-        dz = name.endswith("_dz")
+        dz = "_dz" in name
         rows = n if "_x" in name else m  # rows the pass transforms (x: grid rows; y: window columns)
         fl = rows * ((S + 1) * fft_flops(L) + (S * (12 if dz else 6) + 12) * L)
         if name.startswith("czt_fwd_x"):
@@ -196,8 +196,9 @@ def kernel_model(name: str, fields: float):
             by = n * m + m * m + (m * L + m * m if dz else 0)
         elif name.startswith("czt_adj_y"):
             by = m * m + n * m + (m * m + n * m + m * L if dz else 0)
-        else:  # dz: the forward input and the saved sums a2 (the T-plane term is the y pass's)
-            by = n * m + n * n + (n * n + n * L if dz else 0)
+        else:  # dz (as the step runs it): the forward input, the saved sums a2 and g_in read
+            # back (the pass adds into the RS adjoint's gradient); the T-plane term is the y pass's
+            by = n * m + n * n + (2 * n * n + n * L if dz else 0)
         return nb * fl, nb * by * cs
     if name == "elements_fwd":
         return None, nb * UNIT_BYTES["slm"]

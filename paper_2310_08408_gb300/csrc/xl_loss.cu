@@ -81,6 +81,27 @@ __device__ __forceinline__ double bsum(double v, double* red) {
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
   return s;
 }
+// Block sums of N values in one pass (each summed in bsum's order); valid in thread 0.
+// red: 32 * N doubles.
+template <int N>
+__device__ __forceinline__ void bsum_n(double (&v)[N], double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int j = 0; j < N; ++j) red[j * 32 + (threadIdx.x >> 5)] = v[j];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      double s = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[j * 32 + w];
+      v[j] = s;
+    }
+}
 __device__ __forceinline__ double bmax(double v, double* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
@@ -95,7 +116,7 @@ __device__ __forceinline__ double bmax(double v, double* red) {
 
 // Pixels a thread visits per step of a row: a compile-time count with no branch between them,
 // so that their loads are all in flight together.
-constexpr int kLossPix = 4;
+constexpr int kLossPix = 8;
 
 // Pixels of a block: the rows [r0, r1) of gridDim.x equal row ranges, each row swept by the
 // block's threads in coalesced steps of kLossPix * blockDim.x pixels; fn(i, x, y, live) gets the
@@ -122,18 +143,19 @@ __device__ __forceinline__ void for_pixels(const LossDims& d, F&& fn) {
   }
 }
 
-// Sweep 1. partial: [batch][blocks][3]. grid (loss_blocks, batch).
-template <typename T, int NC, int MODE>
-__global__ void __launch_bounds__(kLossThreads) k_loss_sweep1(const cplx<T>* __restrict__ field, LossDims d,
+// Sweep 1. partial: [batch][blocks][3]. grid (loss_blocks, batch). INTEN: also store the
+// intensity (a separate instance, so that the sweep without it has no store between its loads).
+template <typename T, int NC, int MODE, bool INTEN>
+__global__ void __launch_bounds__(kLossThreads, NC == 1 && sizeof(T) == 4 && MODE == XL_SECOND_MOMENT ? 8 : 1) k_loss_sweep1(const cplx<T>* __restrict__ field, LossDims d,
                                                               double* __restrict__ partial,
                                                               T* __restrict__ inten) {
-  __shared__ double red[32];
+  __shared__ double red[32 * 3];
   const int b = blockIdx.y;
   const cplx<T>* f = field + (int64_t)b * NC * d.plane;
   T s0 = 0, s1 = 0, s2 = 0;
   for_pixels<T>(d, [&](int64_t i, T x, T y, bool live) {
     const T Iv = intensity<T, NC>(f, d, i, b);
-    if (inten && live) inten[(int64_t)b * d.plane + i] = Iv;
+    if (INTEN && live) inten[(int64_t)b * d.plane + i] = Iv;
     const T I = live ? Iv : (T)0;
     if (MODE == XL_SECOND_MOMENT) {
       s0 += I;
@@ -148,11 +170,12 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_sweep1(const cplx<T>* __r
   });
   double* p = partial + ((int64_t)b * gridDim.x + blockIdx.x) * 3;
   if (MODE == XL_SECOND_MOMENT || MODE == XL_MSE) {
-    double a = bsum((double)s0, red), bx = bsum((double)s1, red), by = bsum((double)s2, red);
+    double v[3] = {(double)s0, (double)s1, (double)s2};
+    bsum_n<3>(v, red);
     if (threadIdx.x == 0) {
-      p[0] = a;
-      p[1] = bx;
-      p[2] = by;
+      p[0] = v[0];
+      p[1] = v[1];
+      p[2] = v[2];
     }
   } else {
     double m = bmax((double)s0, red);
@@ -165,7 +188,7 @@ template <typename T, int NC, int MODE>
 __global__ void __launch_bounds__(kLossThreads) k_loss_sweep2(const cplx<T>* __restrict__ field, LossDims d,
                                                               const double* __restrict__ st,
                                                               double* __restrict__ partial) {
-  __shared__ double red[32];
+  __shared__ double red[32 * 2];
   const int b = blockIdx.y;
   const cplx<T>* f = field + (int64_t)b * NC * d.plane;
   const double* sb = st + (int64_t)b * 8;
@@ -189,11 +212,12 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_sweep2(const cplx<T>* __r
       }
     });
   }
-  double a = bsum((double)s0, red), c = bsum((double)s1, red);
+  double v[2] = {(double)s0, (double)s1};
+  bsum_n<2>(v, red);
   if (threadIdx.x == 0) {
     double* p = partial + ((int64_t)b * gridDim.x + blockIdx.x) * 3;
-    p[0] = a;
-    p[1] = c;
+    p[0] = v[0];
+    p[1] = v[1];
   }
 }
 
@@ -384,7 +408,10 @@ xl_status loss_run(const void* field, int32_t batch, const LossDims& d, double* 
   dim3 grid(nb, batch);
   {
     LaunchScope ls("loss_sweep1", s);
-    k_loss_sweep1<T, NC, MODE><<<grid, kLossThreads, 0, s>>>((const C*)field, d, partial, (T*)inten);
+    if (inten)
+      k_loss_sweep1<T, NC, MODE, true><<<grid, kLossThreads, 0, s>>>((const C*)field, d, partial, (T*)inten);
+    else
+      k_loss_sweep1<T, NC, MODE, false><<<grid, kLossThreads, 0, s>>>((const C*)field, d, partial, nullptr);
     XL_CUDA_TRY(cudaGetLastError());
   }
   {
