@@ -6,6 +6,13 @@ adding to them (the copy engines of each direction and the SMs work at the same 
 Only scheduling lives here: device staging buffers (`depth` slots per input and output), three
 streams and the events that order them. The computation is whatever `fn` launches on the current
 stream, which is where the library's entry points launch.
+
+`run` is one self-contained pass: its first upload and last download have no computation to hide
+behind. For a loop of passes over the same batch (the steps of an optimisation), the overlapped
+mode (`prime`, `run_overlapped`, `finish`) hides them too: every pass uploads the first chunk of the
+next pass after its own first chunk has computed, and downloads the last chunk of the previous pass
+while its own first chunk computes, so that only the loop's first upload and last download are left
+outside the computation.
 """
 from __future__ import annotations
 
@@ -28,6 +35,7 @@ class HostPipeline:
         self.s_up, self.s_comp, self.s_down = (torch.cuda.Stream(device) for _ in range(3))
         ev = lambda: [torch.cuda.Event() for _ in range(self.depth)]
         self.ev_up, self.ev_comp, self.ev_down = ev(), ev(), ev()
+        self._pending = None  # overlapped passes: the last chunk whose download is still due
 
     @property
     def compute_stream(self) -> torch.cuda.Stream:
@@ -72,3 +80,92 @@ class HostPipeline:
         end = torch.cuda.Event()
         end.record(self.s_down)
         caller.wait_event(end)
+
+    # ------------------------------------------------------------------ overlapped passes
+    def _chunks(self, B):
+        n_c = math.ceil(B / self.chunk)
+        if n_c > self.depth:
+            raise ValueError("overlapped passes need a staging slot per chunk (depth >= chunks)")
+        return [(i, i * self.chunk, min(B, (i + 1) * self.chunk) - i * self.chunk) for i in range(n_c)]
+
+    def _join_start(self):
+        caller = torch.cuda.current_stream()
+        start = torch.cuda.Event()
+        start.record(caller)
+        for s in (self.s_up, self.s_comp, self.s_down):
+            s.wait_event(start)
+        return caller
+
+    def _join_end(self, caller):
+        for s in (self.s_up, self.s_comp, self.s_down):
+            ev = torch.cuda.Event()
+            ev.record(s)
+            caller.wait_event(ev)
+
+    def prime(self, host_in) -> None:
+        """Uploads the first chunk of the first overlapped pass (ordered after the caller's
+        stream; the caller's stream waits for it)."""
+        B = int(host_in[0].shape[0])
+        _, lo, n = self._chunks(B)[0]
+        caller = self._join_start()
+        with torch.cuda.stream(self.s_up):
+            for h, d in zip(host_in, self.dev_in[0]):
+                d[:n].copy_(h[lo:lo + n], non_blocking=True)
+        self._join_end(caller)
+        self._pending = None
+
+    def run_overlapped(self, host_in, host_out, fn) -> None:
+        """One pass as `run`, with the first chunk already uploaded (by `prime` or the previous
+        pass) and the last chunk's download left to the next pass (or `finish`). Every chunk has
+        its own staging slot. Work is ordered after the caller's stream, which waits for the pass
+        (so each pass is one unit that a CUDA graph can capture and replay)."""
+        B = int(host_in[0].shape[0])
+        chunks = self._chunks(B)
+        last = len(chunks) - 1
+        caller = self._join_start()
+        pend = None
+        with torch.cuda.stream(self.s_down):  # the previous pass's last chunk
+            if self._pending is not None:
+                k, lo, n, outs = self._pending
+                for h, d in zip(outs, self.dev_out[k]):
+                    h[lo:lo + n].copy_(d[:n], non_blocking=True)
+                pend = torch.cuda.Event()
+                pend.record(self.s_down)
+        with torch.cuda.stream(self.s_up):  # chunks 1..last: their slots are free
+            for i, lo, n in chunks[1:]:
+                for h, d in zip(host_in, self.dev_in[i]):
+                    d[:n].copy_(h[lo:lo + n], non_blocking=True)
+                self.ev_up[i].record(self.s_up)
+        for i, lo, n in chunks:
+            with torch.cuda.stream(self.s_comp):
+                if i > 0:
+                    self.s_comp.wait_event(self.ev_up[i])
+                if i == last and pend is not None:
+                    self.s_comp.wait_event(pend)  # slot `last` is downloaded before it is rewritten
+                fn([d[:n] for d in self.dev_in[i]], [d[:n] for d in self.dev_out[i]], lo, n)
+                self.ev_comp[i].record(self.s_comp)
+            if i == 0:  # the next pass's first chunk, once this pass's first chunk has read slot 0
+                with torch.cuda.stream(self.s_up):
+                    self.s_up.wait_event(self.ev_comp[0])
+                    for h, d in zip(host_in, self.dev_in[0]):
+                        d[:n].copy_(h[lo:lo + n], non_blocking=True)
+            if i < last:
+                with torch.cuda.stream(self.s_down):
+                    self.s_down.wait_event(self.ev_comp[i])
+                    for h, d in zip(host_out, self.dev_out[i]):
+                        h[lo:lo + n].copy_(d[:n], non_blocking=True)
+        _, lo, n = chunks[last]
+        self._pending = (last, lo, n, list(host_out))
+        self._join_end(caller)
+
+    def finish(self) -> None:
+        """Downloads the last chunk of the last overlapped pass (the caller's stream waits)."""
+        if getattr(self, "_pending", None) is None:
+            return
+        caller = self._join_start()
+        k, lo, n, outs = self._pending
+        with torch.cuda.stream(self.s_down):
+            for h, d in zip(outs, self.dev_out[k]):
+                h[lo:lo + n].copy_(d[:n], non_blocking=True)
+        self._join_end(caller)
+        self._pending = None

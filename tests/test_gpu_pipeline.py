@@ -38,3 +38,41 @@ def test_pipeline_matches_direct(chunk, depth):
         torch.cuda.current_stream().synchronize()
         assert torch.equal(out_h, ref_out.cpu())
         assert torch.equal(loss_h, ref_i.cpu())
+
+
+@pytest.mark.parametrize("chunk,depth", [(2, 4), (3, 3), (7, 1)])
+def test_overlapped_passes_keep_each_pass_apart(chunk, depth):
+    """prime / run_overlapped / finish: every pass's chunks carry that pass's values (a pass
+    counter is added to the outputs), the last chunk's values arrive one pass late (during the
+    next pass, or with finish), and the ahead-of-time upload of the next pass's first chunk never
+    overwrites an input the current pass still reads."""
+    import torch
+    xl = lib()
+    from paper_2310_08408_gb300.pipeline import HostPipeline
+    n, B = 64, 7
+    g = inputs.Grid(n, n, 1.0, 1.0, -n / 2, -n / 2)
+    u = np.stack([inputs.gaussian_random_phase(g, 20.0, 4700 + b) for b in range(B)]).astype(np.complex64)
+    zs = [300.0 + 100.0 * (b % 3) for b in range(B)]
+    ref = xl.rs_propagate(to_dev(u, np.complex64), g, LAM, zs).cpu()
+    U_h = torch.from_numpy(u).pin_memory()
+    out_h = torch.zeros((B, n, n), dtype=torch.complex64).pin_memory()
+    pipe = HostPipeline([((n, n), torch.complex64)], [((n, n), torch.complex64)], chunk=chunk, depth=depth)
+    count = torch.zeros((), dtype=torch.float32, device="cuda")
+
+    def fn(ins, outs, lo, k):
+        if lo == 0:
+            count.add_(1.0)
+        xl.rs_propagate(ins[0], g, LAM, zs[lo:lo + k], out=outs[0])
+        outs[0].add_(count)
+
+    last_lo = ((B - 1) // chunk) * chunk
+    pipe.prime([U_h])
+    for p in range(1, 4):
+        pipe.run_overlapped([U_h], [out_h], fn)
+        torch.cuda.current_stream().synchronize()
+        assert torch.equal(out_h[:last_lo], ref[:last_lo] + p) or last_lo == 0
+        if p > 1:
+            assert torch.equal(out_h[last_lo:], ref[last_lo:] + (p - 1))
+    pipe.finish()
+    torch.cuda.current_stream().synchronize()
+    assert torch.equal(out_h, ref + 3)
