@@ -415,6 +415,8 @@ k_czt_fwd_x(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ Tb, CztDims d,
   a2.init(czt_slot(sm, k_acc + (nseg > 1 ? 1 : 0), ROWS, SR, team), t);
   const T yn = (T)(d.y0 + n * d.dy);
   const C* s0 = in + ((int64_t)b * d.in_planes) * plane + (int64_t)n * d.nx;
+  if (t == 0 && live)  // the input row, asked of L2 before the segments read it
+    for (int c = 0; c < d.in_planes; ++c) prefetch_l2(s0 + c * plane, (size_t)d.nx * sizeof(C));
 #pragma unroll
   for (int c = 0; c < cT; ++c) {
     C v[16];
@@ -714,6 +716,7 @@ k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d
   T iz = (T)1;
   if constexpr (VEC) iz = (T)(1.0 / czt_z(d, b));
   C dx = mk((T)0, (T)0);
+
 #pragma unroll
   for (int ci = 0; ci < cT; ++ci) {
     const int c = VEC ? (ci + 2) % 3 : 0;  // VEC: Z (2) first, then A (0) and B (1)
