@@ -42,6 +42,7 @@ struct ElemSet {
 
 struct ElemDims {
   int nx, ny, comps_in, comps_out;
+  int nx_shift;                 // log2(nx) when nx is a power of two, else -1
   int64_t plane;
   double x0, dx, y0, dy, k;
   const double* params_dev;     // [batch][n][4] or nullptr (host parameters)
@@ -158,6 +159,17 @@ __device__ __forceinline__ cplx<T> lens_factor(const cplx<T>* tab, int s, int b,
   return cmul(t[m], t[d.nx + n]);
 }
 
+// Column m and row n of pixel i (a shift and a mask for power-of-two rows, no integer division).
+__device__ __forceinline__ void pix_mn(const ElemDims& d, int64_t i, int& m, int& n) {
+  if (d.nx_shift >= 0) {
+    m = (int)(i & (d.nx - 1));
+    n = (int)(i >> d.nx_shift);
+  } else {  // plane < 2^31: 32-bit division
+    m = (int)i % d.nx;
+    n = (int)i / d.nx;
+  }
+}
+
 // Jones matrices of the polarisers and wave plates of batch element b (and their parameter
 // derivatives), one entry per element: they depend on the element's parameters only, so a block
 // whose pixels share b forms them once in shared memory instead of once per pixel.
@@ -212,7 +224,8 @@ __device__ __forceinline__ void elem_fwd(const ElemSet& E, const ElemDims& d, co
       break;
     }
     case XL_LENS: {
-      const int m = (int)i % d.nx, n = (int)i / d.nx;  // plane < 2^31: 32-bit division
+      int m, n;
+      pix_mn(d, i, m, n);
       cplx<T> L = lens_factor<T>(lens, E.lens_slot[e], d.params_dev ? b : 0, nlens, d, m, n);
       c0 = cmul(c0, L);
       c1 = cmul(c1, L);
@@ -279,9 +292,11 @@ constexpr int kPixBwd = 8;
 // masks are shared (stride 0): the batch loop then runs inside the thread so that dL/dphi sums
 // over the batch without atomics.
 // NE: the number of elements (E.n), a compile-time bound so that the per-pixel states take
-// registers for NE elements only.
-template <typename T, int NE>
-__global__ void __launch_bounds__(256, NE <= 1 && sizeof(T) == 4 ? 4 : 1) k_elem_bwd(const cplx<T>* __restrict__ gout, const cplx<T>* __restrict__ in,
+// registers for NE elements only. ST: some element's mask or scalar gradient is asked for, so the
+// forward states are recomputed from the input; without (ST false) only the cotangent is read and
+// each element's adjoint applied to it, last element first.
+template <typename T, int NE, bool ST = true>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (NE <= 1 ? 4 : 2) : 1) k_elem_bwd(const cplx<T>* __restrict__ gout, const cplx<T>* __restrict__ in,
                                                   cplx<T>* __restrict__ gin, ElemSet E, ElemDims d,
                                                   const cplx<T>* __restrict__ lens, int nlens,
                                                   ElemGrad G, int batch, int pix) {
@@ -302,11 +317,62 @@ __global__ void __launch_bounds__(256, NE <= 1 && sizeof(T) == 4 ? 4 : 1) k_elem
     for (int e = 0; e < NE; ++e) sg[e][0] = sg[e][1] = sg[e][2] = sg[e][3] = (T)0;
     // the pixel count is kPixBwd or 1; the constant bound lets the loads of consecutive pixels
     // be issued together
-#pragma unroll 4
+    constexpr int kUnroll = NE <= 1 ? 4 : 2;  // pixels whose states are live together
+#pragma unroll kUnroll
     for (int k = 0; k < (pix == kPixBwd ? kPixBwd : 1); ++k) {
       const int64_t i = ((int64_t)blockIdx.x * pix + k) * blockDim.x + threadIdx.x;
       const bool live = i < d.plane;
       const int64_t ii = live ? i : d.plane - 1;
+      if constexpr (!ST) {
+        const cplx<T>* gs = gout + (int64_t)b * d.comps_out * d.plane;
+        cplx<T> h0 = gs[ii];
+        cplx<T> h1 = d.comps_out >= 2 ? gs[d.plane + ii] : mk((T)0, (T)0);
+        cplx<T> h2 = d.comps_out == 3 ? gs[2 * d.plane + ii] : mk((T)0, (T)0);
+#pragma unroll
+        for (int e = NE - 1; e >= 0; --e) {
+          switch (E.kind[e]) {
+            case XL_SLM: {
+              T sn, cs;
+              xsincos(phase_at<T>(E.phx[e], E.phstride[e], b, ii), &sn, &cs);
+              h0 = cmulc(h0, mk(cs, sn));
+              h1 = cmulc(h1, mk(cs, sn));
+              h2 = cmulc(h2, mk(cs, sn));
+              break;
+            }
+            case XL_SSLM: {
+              T sn, cs;
+              xsincos(phase_at<T>(E.phx[e], E.phstride[e], b, ii), &sn, &cs);
+              h0 = cmulc(h0, mk(cs, sn));
+              xsincos(phase_at<T>(E.phy[e], E.phstride[e], b, ii), &sn, &cs);
+              h1 = cmulc(h1, mk(cs, sn));
+              break;
+            }
+            case XL_LENS: {
+              int m, n;
+              pix_mn(d, ii, m, n);
+              const cplx<T> L = lens_factor<T>(lens, E.lens_slot[e], d.params_dev ? b : 0, nlens, d, m, n);
+              h0 = cmulc(h0, L);
+              h1 = cmulc(h1, L);
+              h2 = cmulc(h2, L);
+              break;
+            }
+            case XL_POLARIZER:
+            case XL_WAVEPLATE:
+              japply_h(jt.J[e], h0, h1);
+              break;
+            case XL_TO_VECTOR:
+              h1 = mk((T)0, (T)0);
+              break;
+          }
+        }
+        if (live && gin) {
+          cplx<T>* dst = gin + (int64_t)b * d.comps_in * d.plane;
+          dst[i] = h0;
+          if (d.comps_in >= 2) dst[d.plane + i] = h1;
+          if (d.comps_in == 3) dst[2 * d.plane + i] = h2;
+        }
+        continue;
+      }
       cplx<T> s0[NE + 1], s1[NE + 1], s2[NE + 1];
       cplx<T> ph[NE > 0 ? NE : 1][2];  // mask phasors of the SLMs, reused by their adjoints
       const cplx<T>* src = in + (int64_t)b * d.comps_in * d.plane;
@@ -344,7 +410,8 @@ __global__ void __launch_bounds__(256, NE <= 1 && sizeof(T) == 4 ? 4 : 1) k_elem
             break;
           }
           case XL_LENS: {
-            const int m = (int)ii % d.nx, n = (int)ii / d.nx;
+            int m, n;
+            pix_mn(d, ii, m, n);
             const T xm = (T)d.x0 + (T)m * (T)d.dx, yn = (T)d.y0 + (T)n * (T)d.dy;
             const T coef = jt.lens_c[e] * (xm * xm + yn * yn);  // d out / d f = i coef out
             sg[e][0] += wlive * (cdot_re(g0, mk(-o0.y * coef, o0.x * coef)) +
@@ -562,6 +629,7 @@ xl_status prepare(const xl_element* el, int32_t n_el, int32_t comps_in, const xl
     if (x.phi_stride < 0) return fail(XL_ERR_ARG, "phi_stride must be >= 0");
   }
   d->nx = g->nx;
+  d->nx_shift = is_pow2(g->nx) ? ilog2(g->nx) : -1;
   d->ny = g->ny;
   d->comps_in = comps_in;
   d->comps_out = c;
@@ -652,10 +720,18 @@ xl_status run_bwd(const void* gout, const void* in, void* gin, int32_t batch, co
   dim3 grid(nblk, G.accumulate_shared ? 1 : batch);
   {
     LaunchScope ls("elements_bwd", s);
-#define XL_EBWD(NE)                                                                                 \
-  case NE:                                                                                          \
-    k_elem_bwd<T, NE><<<grid, 256, 0, s>>>((const cplx<T>*)gout, (const cplx<T>*)in, (cplx<T>*)gin, \
-                                           E, d, (const cplx<T>*)lens, nlens, G, batch, pix);     \
+    // the forward states are recomputed only when a mask or scalar gradient is asked for
+    const bool st = gparams != nullptr || any_shared || any_batched;
+#define XL_EBWD(NE)                                                                                   \
+  case NE:                                                                                            \
+    if (st)                                                                                           \
+      k_elem_bwd<T, NE, true><<<grid, 256, 0, s>>>((const cplx<T>*)gout, (const cplx<T>*)in,          \
+                                                   (cplx<T>*)gin, E, d, (const cplx<T>*)lens, nlens, \
+                                                   G, batch, pix);                                   \
+    else                                                                                              \
+      k_elem_bwd<T, NE, false><<<grid, 256, 0, s>>>((const cplx<T>*)gout, (const cplx<T>*)in,         \
+                                                    (cplx<T>*)gin, E, d, (const cplx<T>*)lens, nlens, \
+                                                    G, batch, pix);                                  \
     break;
     switch (E.n) {
       XL_EBWD(0) XL_EBWD(1) XL_EBWD(2) XL_EBWD(3) XL_EBWD(4) XL_EBWD(5) XL_EBWD(6) XL_EBWD(7) XL_EBWD(8)
