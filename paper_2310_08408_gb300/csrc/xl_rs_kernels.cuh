@@ -816,6 +816,7 @@ template <typename T> struct RsPhase;
 template <> struct RsPhase<float> {
   df dx2, dy2, z, z2, k, twopi;
   float kz_red, zf, izf, kf, c0, dxf, dyf;
+  RsPhase() = default;
   __device__ RsPhase(const GenArgs& g, double zz) {
     dxf = (float)g.dx;
     dyf = (float)g.dy;
@@ -834,6 +835,7 @@ template <> struct RsPhase<float> {
 };
 template <> struct RsPhase<double> {
   double kz_red, z;
+  RsPhase() = default;
   __device__ RsPhase(const GenArgs& g, double zz) {
     kz_red = g.k * zz - kTwoPi * rint(g.k * zz / kTwoPi);
     z = zz;
@@ -947,7 +949,12 @@ k_gen_pass_a(cplx<T>* __restrict__ S, GenArgs g, const cplx<T>* __restrict__ tw)
   const int b = b0 + team;
   const double z = g.zdev ? g.zdev[blockIdx.y] : g.zval;
   S += (int64_t)blockIdx.y * g.s_elem;
-  const RsPhase<T> ph(g, z);
+  // the distance's constants, formed once for the block (they take double divisions, and FP64
+  // runs at a small fraction of the FP32 rate)
+  __shared__ RsPhase<T> ph_s;
+  if (threadIdx.x == 0) ph_s = RsPhase<T>(g, z);
+  __syncthreads();
+  const RsPhase<T>& ph = ph_s;  // read from shared memory where used (no registers held)
   C* row = sm + team * P;
   C* phc = sm + ROWS * P + team * (LX / 2);  // phasors of |a| < nx (CACHE)
   if constexpr (CACHE) {
