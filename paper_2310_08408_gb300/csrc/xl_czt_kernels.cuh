@@ -329,6 +329,16 @@ __device__ __forceinline__ double czt_z(const CztDims& d, int b) {
   return d.zdev ? *d.zdev : d.z[b < kCztRun ? b : kCztRun - 1];
 }
 
+// 1 / z (times sgn) of batch element b in T, the double division done once for the block (FP64
+// runs at a small fraction of the FP32 rate). Every thread of the block calls it.
+template <typename T>
+__device__ __forceinline__ T czt_inv_z(const CztDims& d, int b, double sgn) {
+  __shared__ T iz_s;
+  if (threadIdx.x == 0) iz_s = (T)(sgn / czt_z(d, b));
+  __syncthreads();
+  return iz_s;
+}
+
 #define XL_CZT_BOUNDS(T, L, VEC, V, DZ) \
   __launch_bounds__(czt_threads<L, sizeof(cplx<T>), VEC, V>(), czt_min_blocks<L, sizeof(cplx<T>), VEC, V, DZ>())
 
@@ -499,7 +509,7 @@ k_czt_fwd_y(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ out, CztDims d
   T Xp = (T)0, iz = (T)0;
   if constexpr (VEC) {
     Xp = (T)(d.xo0 + p * d.dxo);
-    iz = (T)(-1.0 / czt_z(d, b));
+    iz = czt_inv_z<T>(d, b, -1.0);
   }
   const Coord<T> yq(d.yo0, d.dyo, t, TT);
 #pragma unroll
@@ -582,7 +592,7 @@ k_czt_adj_y(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tb, CztDims d, 
   T Xp = (T)0, iz = (T)0;
   if constexpr (VEC) {
     Xp = (T)(d.xo0 + p * d.dxo);
-    iz = (T)(1.0 / czt_z(d, b));
+    iz = czt_inv_z<T>(d, b, 1.0);
     const C* gzsrc = G + ((int64_t)b * 3 + 2) * oplane;
     if constexpr (SMST) {
       load_rows_transposed<L, ROWS, SR>(czt_slot(sm, 1, ROWS, SR, 0), d.my, d.my, gzsrc, d.mx, p0, d.mx);
@@ -714,7 +724,7 @@ k_czt_adj_x(const cplx<T>* __restrict__ Tb, cplx<T>* __restrict__ gin, CztDims d
   F.init(czt_slot(sm, 1 + (czt_stash_smem<L, sizeof(C), VEC, V>() ? 1 : 0), ROWS, SR, team), t);
   const T yn = (T)(d.y0 + n * d.dy);
   T iz = (T)1;
-  if constexpr (VEC) iz = (T)(1.0 / czt_z(d, b));
+  if constexpr (VEC) iz = czt_inv_z<T>(d, b, 1.0);
   C dx = mk((T)0, (T)0);
 
 #pragma unroll

@@ -302,8 +302,16 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_grad(const cplx<T>* __res
   cplx<T>* gd = gdep ? gdep + (int64_t)b * NC * d.plane : nullptr;
   const double* sb = st + (int64_t)b * 8;
   const double gl = g_loss ? g_loss[b] : 1.0;
-  const T xb = (T)sb[1], yb = (T)sb[2], L = (T)sb[5], iP = (T)(1.0 / sb[0]);
-  const T thr = (T)sb[3], dens = (T)(-sb[6] / (sb[7] * sb[7]));
+  // the two quotients in double once for the block (FP64 runs at a small fraction of the FP32
+  // rate; a division in every thread kept its pipe busy)
+  __shared__ T q_s[2];
+  if (threadIdx.x == 0) {
+    q_s[0] = (T)(1.0 / sb[0]);
+    q_s[1] = (T)(-sb[6] / (sb[7] * sb[7]));
+  }
+  __syncthreads();
+  const T xb = (T)sb[1], yb = (T)sb[2], L = (T)sb[5], iP = q_s[0];
+  const T thr = (T)sb[3], dens = q_s[1];
   const T beta = (T)d.beta;
   for_pixels<T>(d, [&](int64_t i, T x, T y, bool live) {
     T dI;
