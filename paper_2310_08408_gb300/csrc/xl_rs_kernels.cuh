@@ -1017,6 +1017,10 @@ k_gen_pass_b(const cplx<T>* __restrict__ S, cplx<T>* __restrict__ Hq, GenArgs g,
   S += (int64_t)blockIdx.y * g.s_elem;
   Hq += (int64_t)blockIdx.y * g.h_elem;
   C* row = sm + team * SR;
+  if (t == 0)  // every kind's column, asked of L2 before the first transform
+    for (int kind = 0; kind < NKIND; ++kind)
+      if (g.kinds & (1u << kind))
+        prefetch_l2(S + (int64_t)g.slot[kind] * g.s_plane + (int64_t)kx * g.ny, (size_t)g.ny * sizeof(C));
   for (int kind = 0; kind < NKIND; ++kind) {
     if (!(g.kinds & (1u << kind))) continue;
     const C* src = S + (int64_t)g.slot[kind] * g.s_plane + (int64_t)kx * g.ny;
