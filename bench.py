@@ -76,6 +76,9 @@ def parse():
     p.add_argument("--e2e-depth", type=int, default=3,
                    help="staging slots of the end-to-end pipeline (at least one per chunk of a step: "
                         "consecutive steps overlap)")
+    p.add_argument("--e2e-mode", default="alternate", choices=["overlap", "alternate"],
+                   help="end-to-end pipeline: chunks with consecutive steps overlapped, or the whole "
+                        "batch alternating between two staging slots")
     p.add_argument("--e2e-eager", action="store_true",
                    help="end-to-end steps as eager launches instead of one CUDA graph replay")
     p.add_argument("--no-table", action="store_true", help="skip the batched optical-table section")
@@ -871,15 +874,17 @@ def main():
     e2e = None
     if not a.no_e2e:
         from paper_2310_08408_gb300.pipeline import HostPipeline
-        ch = min(a.e2e_chunk, B)
+        alt = a.e2e_mode == "alternate"
+        ch = B if alt else min(a.e2e_chunk, B)
         loss_h = torch.empty((B, 2), dtype=torch.float64).pin_memory()
         gz_h = torch.empty((B,), dtype=torch.float64).pin_memory()
         gphi_h = torch.empty((B, N, N), dtype=torch.float32).pin_memory()
+        outs_h = [loss_h, gz_h, gphi_h]
         ke = max(10, a.steps // 2)  # timed end-to-end steps (after a.warmup untimed ones)
         nchunk = -(-B // ch)
         pipe = HostPipeline([((N, N), U_pin.dtype)],
                             [((2,), torch.float64), ((), torch.float64), ((N, N), torch.float32)],
-                            chunk=ch, depth=max(a.e2e_depth, nchunk))
+                            chunk=ch, depth=2 if alt else max(a.e2e_depth, nchunk))
         with torch.cuda.stream(pipe.compute_stream):
             sc = GpuStep(xl, torch, g, w, U_dev, zs, chunk=ch)
 
@@ -891,40 +896,60 @@ def main():
             gz.copy_(gzc)
             gphi.copy_(gpc)
 
-        # consecutive steps overlap: each step uploads the next step's first chunk and downloads
-        # the previous step's last chunk while it computes (the timed region starts with the first
-        # step's first upload and ends with the last step's last download)
-        def e2e_step():
-            pipe.run_overlapped([U_pin], [loss_h, gz_h, gphi_h], chunk_step)
+        # consecutive steps overlap (the timed region starts with the first step's first upload and
+        # ends with the last step's last download). overlap: chunks of the batch, each step
+        # uploading the next step's first chunk and downloading the previous step's last chunk
+        # while it computes; alternate: the whole batch in one chunk, steps alternating between two
+        # staging slots (a step computes from one while the next step's input goes up into the
+        # other and the previous step's results come down from it)
+        def e2e_step(par):
+            if alt:
+                pipe.run_alternating([U_pin], outs_h, chunk_step, par)
+            else:
+                pipe.run_overlapped([U_pin], outs_h, chunk_step)
 
-        pipe.prime([U_pin])
-        e2e_step()
-        # the whole step (uploads, the chunks' calls, downloads) as one CUDA graph, so that each
-        # timed step is one launch and host-side enqueue jitter cannot stall the pipeline; eager
-        # launches if the capture fails
-        launch, mode = e2e_step, "eager"
+        def prime():
+            if alt:
+                pipe.prime_alternating([U_pin], 0)
+            else:
+                pipe.prime([U_pin])
+
+        prime()
+        e2e_step(0)
+        e2e_step(1)
+        # each step (uploads, the chunks' calls, downloads) as one CUDA graph (one per slot parity
+        # when alternating), so that each timed step is one launch and host-side enqueue jitter
+        # cannot stall the pipeline; eager launches if the capture fails
+        launchers, mode = [lambda: e2e_step(0), lambda: e2e_step(1)], "eager"
         if not a.e2e_eager:
             torch.cuda.synchronize()
             try:
-                graph = torch.cuda.CUDAGraph()
-                with torch.cuda.graph(graph, capture_error_mode="thread_local"):
-                    e2e_step()
-                graph.replay()
+                graphs = []
+                for par in ((0, 1) if alt else (0,)):
+                    gr = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(gr, capture_error_mode="thread_local"):
+                        e2e_step(par)
+                    graphs.append(gr)
+                for gr in graphs:
+                    gr.replay()
                 torch.cuda.synchronize()
-                launch, mode = graph.replay, "cuda_graph"
+                launchers = [gr.replay for gr in graphs] * (1 if alt else 2)
+                mode = "cuda_graph"
             except Exception as ex:  # noqa: BLE001 - reported in the JSON line
                 torch.cuda.synchronize()
                 mode = f"eager (graph capture failed: {type(ex).__name__})"
         ck_e2e = Clocks(local)  # clocks of the end-to-end region, reported with it
-        for _ in range(a.warmup):
-            launch()
+        for i in range(a.warmup):
+            launchers[i % 2]()
+        pipe.tail_due(outs_h, B, ((a.warmup - 1) % 2) if alt else None)
         pipe.finish()
         torch.cuda.synchronize()
         barrier()
         e0.record(stream)
-        pipe.prime([U_pin])
-        for _ in range(ke):
-            launch()
+        prime()
+        for i in range(ke):
+            launchers[i % 2]()
+        pipe.tail_due(outs_h, B, ((ke - 1) % 2) if alt else None)
         pipe.finish()
         e1.record(stream)
         barrier()
@@ -946,9 +971,10 @@ def main():
                "d2h_bytes_per_step": int(loss_h.numel() * 8 + gz_h.numel() * 8 + gphi_h.numel() * 4),
                "d2h": "losses, dL/dz and dL/dphi of every field",
                "ms_per_step": ems / ke, "host_link": link, "launch": mode, "chunk": ch,
-               "depth": max(a.e2e_depth, nchunk), "steps": ke, "clocks": e2e_clocks,
-               "overlap": "each step uploads the next step's first chunk and downloads the "
-                          "previous step's last chunk while it computes"}
+               "depth": 2 if alt else max(a.e2e_depth, nchunk), "steps": ke, "clocks": e2e_clocks,
+               "overlap": ("whole batch, steps alternating between two staging slots" if alt else
+                           "each step uploads the next step's first chunk and downloads the "
+                           "previous step's last chunk while it computes")}
         del sc, pipe
         torch.cuda.empty_cache()
 

@@ -12,7 +12,9 @@ behind. For a loop of passes over the same batch (the steps of an optimisation),
 mode (`prime`, `run_overlapped`, `finish`) hides them too: every pass uploads the first chunk of the
 next pass after its own first chunk has computed, and downloads the last chunk of the previous pass
 while its own first chunk computes, so that only the loop's first upload and last download are left
-outside the computation.
+outside the computation. The alternating mode (`prime_alternating`, `run_alternating`, `finish`)
+keeps the whole batch in one chunk and two slots: a pass computes from one slot while the next
+pass's input goes up into the other and the previous pass's results come down from it.
 """
 from __future__ import annotations
 
@@ -157,6 +159,51 @@ class HostPipeline:
         _, lo, n = chunks[last]
         self._pending = (last, lo, n, list(host_out))
         self._join_end(caller)
+
+    def run_alternating(self, host_in, host_out, fn, parity: int) -> None:
+        """One pass over the whole batch as one chunk, the passes of a loop alternating between two
+        staging slots: pass k (parity k % 2) computes from slot `parity`, whose input the previous
+        pass (or `prime_alternating`) uploaded, while the next pass's input is uploaded into the
+        other slot and the previous pass's results are downloaded from it, so that nothing inside a
+        pass waits on a copy. Needs chunk >= batch and depth >= 2; `finish` downloads the last
+        pass's results. Each parity is one unit that a CUDA graph can capture."""
+        B = int(host_in[0].shape[0])
+        if self.chunk < B or self.depth < 2:
+            raise ValueError("alternating passes need the whole batch in one chunk and two slots")
+        p, o = parity & 1, 1 - (parity & 1)
+        caller = self._join_start()
+        with torch.cuda.stream(self.s_down):  # the previous pass's results, from the other slot
+            if self._pending is not None:
+                k, lo, n, outs = self._pending
+                for h, d in zip(outs, self.dev_out[k]):
+                    h[lo:lo + n].copy_(d[:n], non_blocking=True)
+        with torch.cuda.stream(self.s_up):  # the next pass's input, into the other slot
+            for h, d in zip(host_in, self.dev_in[o]):
+                d[:B].copy_(h[:B], non_blocking=True)
+        with torch.cuda.stream(self.s_comp):
+            fn([d[:B] for d in self.dev_in[p]], [d[:B] for d in self.dev_out[p]], 0, B)
+        self._pending = (p, 0, B, list(host_out))
+        self._join_end(caller)
+
+    def prime_alternating(self, host_in, parity: int = 0) -> None:
+        """Uploads the input of the first alternating pass into slot `parity`."""
+        B = int(host_in[0].shape[0])
+        caller = self._join_start()
+        with torch.cuda.stream(self.s_up):
+            for h, d in zip(host_in, self.dev_in[parity & 1]):
+                d[:B].copy_(h[:B], non_blocking=True)
+        self._join_end(caller)
+        self._pending = None
+
+    def tail_due(self, host_out, batch: int, parity=None) -> None:
+        """Marks the last pass's results as still to be downloaded, for a loop of passes replayed
+        from CUDA graphs (a replay does not update this object): overlapped passes (parity None)
+        leave their last chunk, alternating passes their whole batch in slot `parity`."""
+        if parity is None:
+            i, lo, n = self._chunks(batch)[-1]
+            self._pending = (i, lo, n, list(host_out))
+        else:
+            self._pending = (parity & 1, 0, batch, list(host_out))
 
     def finish(self) -> None:
         """Downloads the last chunk of the last overlapped pass (the caller's stream waits)."""

@@ -76,3 +76,39 @@ def test_overlapped_passes_keep_each_pass_apart(chunk, depth):
     pipe.finish()
     torch.cuda.current_stream().synchronize()
     assert torch.equal(out_h, ref + 3)
+
+
+def test_alternating_passes_keep_each_pass_apart():
+    """prime_alternating / run_alternating / finish: the whole batch in one chunk, passes
+    alternating between two staging slots; each pass's results arrive during the next pass (or
+    with finish) and carry that pass's values, and the upload of the next pass's input never
+    overwrites the input the current pass reads. tail_due re-arms the last download after passes
+    replayed from CUDA graphs."""
+    import torch
+    xl = lib()
+    from paper_2310_08408_gb300.pipeline import HostPipeline
+    n, B = 64, 5
+    g = inputs.Grid(n, n, 1.0, 1.0, -n / 2, -n / 2)
+    u = np.stack([inputs.gaussian_random_phase(g, 20.0, 4800 + b) for b in range(B)]).astype(np.complex64)
+    zs = [300.0 + 100.0 * (b % 3) for b in range(B)]
+    ref = xl.rs_propagate(to_dev(u, np.complex64), g, LAM, zs).cpu()
+    U_h = torch.from_numpy(u).pin_memory()
+    out_h = torch.zeros((B, n, n), dtype=torch.complex64).pin_memory()
+    pipe = HostPipeline([((n, n), torch.complex64)], [((n, n), torch.complex64)], chunk=B, depth=2)
+    count = torch.zeros((), dtype=torch.float32, device="cuda")
+
+    def fn(ins, outs, lo, k):
+        count.add_(1.0)
+        xl.rs_propagate(ins[0], g, LAM, zs[lo:lo + k], out=outs[0])
+        outs[0].add_(count)
+
+    pipe.prime_alternating([U_h], 0)
+    for p in range(1, 5):
+        pipe.run_alternating([U_h], [out_h], fn, (p - 1) % 2)
+        torch.cuda.current_stream().synchronize()
+        if p > 1:
+            assert torch.equal(out_h, ref + (p - 1))
+    pipe.tail_due([out_h], B, 1)
+    pipe.finish()
+    torch.cuda.current_stream().synchronize()
+    assert torch.equal(out_h, ref + 4)
