@@ -153,7 +153,7 @@ def czt_plan(n: int, m: int):
     return best
 
 
-# Algorithmic bytes of one 2048^2 field (SURVEY-style per-unit figures: what the method must
+# Algorithmic bytes of one 2048^2 field (per-unit figures: what the method must
 # read and write, complex64 = 8 B, float32 masks = 4 B): the four propagations and the rest of the
 # gradient step.
 UNIT_BYTES = {
